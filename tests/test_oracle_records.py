@@ -1,0 +1,106 @@
+"""Pins for the oracle's training-record generator (Sec. 5.1) and its estimator of the
+indirect in-scattered radiance L_i (Sec. 4)."""
+import math
+
+import numpy as np
+
+from paper_1709_05418_gb300 import workloads as W
+
+N, MU0 = 8, 1.5
+
+
+def ramp(u):
+    return np.clip(np.minimum(u + 1.0, N - u), 0.0, 1.0)
+
+
+def mu(p):
+    u = p * N - 0.5
+    return MU0 * ramp(u[..., 0]) * ramp(u[..., 1]) * ramp(u[..., 2])
+
+
+def exit_dist(p, d):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = np.where(d > 0, (1.0 - p) / d, np.where(d < 0, -p / d, np.inf))
+    return t1.min(axis=-1)
+
+
+def hg(g, c):
+    den = 1 + g * g - 2 * g * c
+    return (1 - g * g) / (4 * math.pi * den ** 1.5)
+
+
+def first_order_Li(x, d_in, wl, g, ndir=1500, ns=160, nl=80):
+    """Brute-force quadrature of the single-collision term of L_i at x:
+    int_S2 p(d_in.d') int_0^b mu T(x, x+s d') p(d'.wl) T_light ds dd'."""
+    i = np.arange(ndir) + 0.5
+    zc = 1 - 2 * i / ndir
+    ph = math.pi * (1 + 5 ** 0.5) * i
+    r = np.sqrt(1 - zc * zc)
+    dirs = np.stack([r * np.cos(ph), r * np.sin(ph), zc], 1)
+    b = exit_dist(np.broadcast_to(x, dirs.shape), dirs)
+    frac = (np.arange(ns) + 0.5) / ns
+    s = b[:, None] * frac[None, :]
+    ds = (b / ns)[:, None]
+    pts = x[None, None, :] + s[..., None] * dirs[:, None, :]
+    m = mu(pts)
+    tau = np.cumsum(m * ds, axis=1) - 0.5 * m * ds
+    bl = exit_dist(pts, np.broadcast_to(wl, pts.shape))
+    fl = (np.arange(nl) + 0.5) / nl
+    lp = pts[..., None, :] + (bl[..., None] * fl)[..., None] * wl
+    taul = mu(lp).sum(-1) * bl / nl
+    inner = (m * np.exp(-tau) * np.exp(-taul) * ds).sum(1)
+    w = hg(g, dirs @ d_in) * hg(g, dirs @ wl)
+    return 4 * math.pi / ndir * (w * inner).sum()
+
+
+def test_first_collision_term_matches_quadrature(orc):
+    g = 0.3
+    v = orc.Volume(np.full((N, N, N), MU0, np.float32), 1.0, g)
+    x = np.array([0.5, 0.5, 0.5])
+    d = np.array([0.0, 0.0, 1.0])
+    wl = np.array([1.0, 1.0, 0.3])
+    wl /= np.linalg.norm(wl)
+    exp = first_order_Li(x, d, wl, g)
+    r, mean, var = v.estimate_Li(123, 0, x, d, wl, 40000, max_bounces=1)
+    se = math.sqrt(var / 40000)
+    assert r == 0
+    assert abs(mean - exp) < 4 * se + 0.01 * exp, (mean, exp, se)
+    # with albedo 1/2 each collision survives with probability 1/2 (analog absorption)
+    v2 = orc.Volume(np.full((N, N, N), MU0, np.float32), 0.5, g)
+    _, m2, var2 = v2.estimate_Li(124, 0, x, d, wl, 40000, max_bounces=1)
+    assert abs(m2 - 0.5 * exp) < 4 * math.sqrt(var2 / 40000) + 0.01 * exp
+    # higher orders only add (non-negative) energy
+    _, mall, _ = v.estimate_Li(123, 0, x, d, wl, 40000, max_bounces=0)
+    assert mall > mean
+
+
+def test_record_sampling(orc):
+    dens = W.blob_cloud(24, seed=21)
+    v = orc.Volume(dens, 0.9, 0.85)
+    ds, wls = [], []
+    for rec in range(64):
+        r = v.gen_record(555, rec, rel_ci=0.2, n_min=16, n_max=512)
+        assert r["status"] == 0
+        x, d, wl = r["x"], r["d"], r["wl"]
+        assert abs(np.linalg.norm(d) - 1) < 1e-12 and abs(np.linalg.norm(wl) - 1) < 1e-12
+        assert np.all(x >= 0) and np.all(x <= 1) and v.density(x) > 0
+        assert r["label"] >= 0 and 16 <= r["npaths"] <= 512
+        if r["npaths"] < 512:
+            assert r["half_width"] <= 0.2 * r["label"] + 1e-15
+        ds.append(d)
+        wls.append(wl)
+    ds, wls = np.array(ds), np.array(wls)
+    # uniform directions: mean ~ 0 (4 sigma = 4 / sqrt(3 * 64))
+    assert np.all(np.abs(ds.mean(0)) < 0.3) and np.all(np.abs(wls.mean(0)) < 0.3)
+
+
+def test_label_stopping_rule(orc):
+    dens = W.blob_cloud(24, seed=22)
+    v = orc.Volume(dens, 0.95, 0.85)
+    r = v.gen_record(7, 3, rel_ci=0.05, n_min=64, n_max=200000)
+    assert r["status"] == 0 and r["label"] > 0
+    assert r["half_width"] <= 0.05 * r["label"]
+    assert r["npaths"] >= 64
+    # re-estimating with the same number of paths reproduces the label (same streams)
+    rr, m, _ = v.estimate_Li(7, 3, r["x"], r["d"], r["wl"], r["npaths"])
+    assert abs(m - r["label"]) < 1e-12 * max(1.0, m)

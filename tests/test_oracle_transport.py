@@ -1,0 +1,122 @@
+"""Pins for the oracle's Monte Carlo transport: Henyey-Greenstein phase function,
+delta tracking, ratio tracking and single scattering (Sec. 3.2 Eq. 1, Sec. 4.4)."""
+import math
+
+import numpy as np
+from scipy import integrate, stats
+
+N, MU0 = 8, 1.5          # constant 8^3 cube, extinction 1.5 per unit
+
+
+def ramp(u):
+    """1-D profile of the trilinear field of a constant grid (voxel centres at integer
+    u, zero outside): rises over [-1, 0], flat on [0, n-1], falls over [n-1, n]."""
+    return np.clip(np.minimum(u + 1.0, N - u), 0.0, 1.0)
+
+
+def tau_axis(x0, x1):
+    """optical depth between world x0 < x1 along an axis through interior voxel centres"""
+    f = lambda x: MU0 * ramp(x * N - 0.5)
+    return integrate.quad(f, x0, x1, points=[0.5 / N, 1 - 0.5 / N], limit=200)[0]
+
+
+def cube(orc, albedo=0.99, g=0.85):
+    return orc.Volume(np.full((N, N, N), MU0, np.float32), albedo, g)
+
+
+def test_hg_normalised_and_mean_cosine(orc):
+    for g in (0.0, 0.3, 0.85, -0.5):
+        norm = integrate.quad(lambda m: 2 * math.pi * orc.hg(g, m), -1, 1, limit=200)[0]
+        mc = integrate.quad(lambda m: 2 * math.pi * m * orc.hg(g, m), -1, 1, limit=200)[0]
+        assert abs(norm - 1.0) < 1e-8 and abs(mc - g) < 1e-8
+
+
+def test_hg_sampling_distribution(orc):
+    g = 0.85
+    rng = np.random.default_rng(5)
+    d = np.array([0.2, -0.5, 0.7])
+    d /= np.linalg.norm(d)
+    cos, phi_ok = [], []
+    for _ in range(4000):
+        o = orc.sample_hg(g, d, rng.random(), rng.random())
+        assert abs(np.linalg.norm(o) - 1) < 1e-12
+        cos.append(np.dot(o, d))
+    cdf = lambda m: (1 - g * g) / (2 * g) * ((1 + g * g - 2 * g * np.asarray(m)) ** -0.5 - 1 / (1 + g))
+    assert stats.kstest(cos, cdf).pvalue > 1e-3
+
+
+def test_ratio_tracking_mean_is_beer_lambert(orc):
+    v = cube(orc)
+    y0 = z0 = 3.5 / N
+    o = np.array([-0.5, y0, z0])
+    d = np.array([1.0, 0.0, 0.0])
+    T = np.array([v.ratio_track(o, d, 77, i, 0) for i in range(4000)])
+    exact = math.exp(-MU0 * (N - 0.25) / N)
+    assert abs(math.exp(-tau_axis(0, 1)) - exact) < 1e-12
+    assert abs(T.mean() - exact) < 4 * T.std() / math.sqrt(T.size)
+    assert np.all(T >= 0) and np.all(T <= 1)
+
+
+def test_delta_tracking_free_path_distribution(orc):
+    v = cube(orc)
+    y0 = z0 = 4.5 / N
+    o = np.array([-0.25, y0, z0])
+    d = np.array([1.0, 0.0, 0.0])
+    hits, xs = 0, []
+    n = 4000
+    for i in range(n):
+        r, x, t = v.delta_track(o, d, 99, i, 0)
+        if r == 1:
+            hits += 1
+            xs.append(x[0])
+            assert abs(t - (x[0] + 0.25)) < 1e-12
+    tau1 = tau_axis(0, 1)
+    p = 1 - math.exp(-tau1)
+    assert abs(hits / n - p) < 4 * math.sqrt(p * (1 - p) / n)
+    grid = np.linspace(0, 1, 401)
+    taus = np.array([tau_axis(0, x) if x > 0 else 0.0 for x in grid])
+    F = lambda x: np.interp(x, grid, (1 - np.exp(-taus)) / p)
+    assert stats.kstest(xs, F).pvalue > 1e-3
+
+
+def test_single_scattering_pixel_matches_quadrature(orc):
+    g, alb = 0.6, 0.8
+    v = cube(orc, alb, g)
+    y0, z0 = 3.5 / N, 4.5 / N
+    wl = np.array([0.0, 1.0, 0.0])
+    cam = {"cam_pos": [-1.0, y0, z0], "cam_fwd": [1.0, 0, 0], "cam_right": [0, 0, -1.0],
+           "cam_up": [0, 1.0, 0], "tan_half_fov_y": 1e-9, "width": 64, "height": 64,
+           "spp": 8, "seed": 4242, "light_dir": wl, "light_E": 1.0}
+    px = v.render_pixels(cam, np.arange(64 * 64), params=None, mode=0)
+    # expectation: alb * int mu(s) T_cam(s) p(d.wl) T_light(s) ds along the pixel ray
+    ty = integrate.quad(lambda y: ramp(y * N - 0.5), y0, 1.0, points=[1 - 0.5 / N])[0] * MU0
+
+    def f(x):
+        rx = ramp(x * N - 0.5)
+        return MU0 * rx * math.exp(-tau_axis(0, x)) * orc.hg(g, 0.0) * math.exp(-rx * ty)
+
+    exp = alb * integrate.quad(f, 0, 1, points=[0.5 / N, 1 - 0.5 / N], limit=200)[0]
+    se = px.std() / math.sqrt(px.size)
+    assert abs(px.mean() - exp) < 4 * se + 1e-9, (px.mean(), exp, se)
+    # plain path tracing adds the (non-negative) indirect part
+    pt = v.render_pixels(cam, np.arange(64 * 64), params=None, mode=1)
+    assert pt.mean() > px.mean()
+
+
+def test_primary_sample_is_consistent(orc):
+    v = cube(orc)
+    cam = {"cam_pos": [0.5, 0.5, -1.5], "cam_fwd": [0, 0, 1.0], "cam_right": [1.0, 0, 0],
+           "cam_up": [0, 1.0, 0], "tan_half_fov_y": 0.2, "width": 16, "height": 16,
+           "spp": 1, "seed": 9, "light_dir": [0.0, 0.6, 0.8], "light_E": 2.0}
+    pix = v.render_pixels(cam, np.arange(256), params=None, mode=0)
+    for p in range(0, 256, 17):
+        hit, x, d, Ld = v.primary(cam, p, 0)
+        if hit == 1:
+            assert abs(np.linalg.norm(d) - 1) < 1e-12
+            assert np.all(x >= 0) and np.all(x <= 1)
+            assert v.density(x) > 0
+            assert abs(pix[p] - 0.99 * Ld) < 1e-15
+            # the shadow ray estimate is bounded by E * p(d . wl)
+            assert 0 <= Ld <= 2.0 * orc.hg(0.85, float(np.dot(d, cam["light_dir"]))) + 1e-15
+        else:
+            assert pix[p] == 0.0
