@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the RPNN render hot path: RPNN shading queries/s on one GB300.
+
+Workload (one step = one full render: camera rays + delta tracking + NEE, descriptor
+gather, network, composite): a 256^3 FP32 cloud of thresholded 6-octave fBm noise
+(30% non-zero voxels, peak extinction 50 per unit), 512 x 512 pixels, 1 sample per
+pixel, random light direction, He-initialised network.  The network runs in BF16 on
+the tensor cores (the FP32 CUDA-core form is timed beside it for the ratio).
+
+Prints one JSON line.  --impl reference times the CPU oracle on the same workload.
+Multi-GPU (torchrun): every rank renders its own view of the cloud (weak scaling, no
+collective on the data path); the barrier and the max over ranks only frame timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPNN shading queries/s on 1 GB300, BF16/FP8 vs FP32 GPU form at stated RMSE"
+WORKLOAD = ("single cloud render: 256^3 FP32 fBm density (6 octaves, 30% non-zero, peak "
+            "sigma_t 50/unit, albedo 0.99, HG g 0.85), 512x512, 1 spp, random light dir, "
+            "RPNN at the paper's sizes (10 blocks x 2 + 3 layers, width 200), He-init weights")
+FLOP_PER_QUERY = 2 * (10 * 226 * 200 + 9 * 200 * 200 + 10 * 200 * 200 + 2 * 200 * 200 + 200)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"),
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("RPNN_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_workload(rank, device=None):
+    from paper_1709_05418_gb300 import workloads as W
+    dens = W.fbm_cloud(256, seed=7, device=device)
+    cam = W.camera(dens.shape, 512, 512, spp=1, seed=3 + rank, light_seed=4 + rank)
+    params = W.he_init(seed=2)
+    return dens, cam, params
+
+
+def cpu_sample(dens, cam, params, npix, seed=0):
+    """Oracle render of `npix` sampled pixels; returns (pixels, values, queries, seconds, threads)."""
+    import oracle
+    v = oracle.Volume(dens)
+    pix = np.sort(np.random.default_rng(seed).choice(cam["width"] * cam["height"], npix, replace=False))
+    nthreads = os.cpu_count() or 1
+    # pyramid levels are built on first use: do it outside the timed region
+    v.render_pixels(cam, pix[:1], params=params.astype(np.float64))
+    hits = sum(1 for p in pix if v.primary(cam, int(p), 0)[0] == 1)
+    t0 = time.perf_counter()
+    vals = v.render_pixels(cam, pix, params=params.astype(np.float64), nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return pix, vals, hits, dt, nthreads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    dens, cam, params = make_workload(0, device="cpu")
+    import oracle
+    v = oracle.Volume(dens)
+    nthreads = os.cpu_count() or 1
+    npix = args.ref_pixels
+    rng = np.random.default_rng(123)
+    p64 = params.astype(np.float64)
+    v.render_pixels(cam, np.arange(1), params=p64)
+    times, queries = [], []
+    for i in range(args.warmup + args.steps):
+        pix = np.sort(rng.choice(cam["width"] * cam["height"], npix, replace=False))
+        hits = sum(1 for p in pix if v.primary(cam, int(p), 0)[0] == 1)
+        t0 = time.perf_counter()
+        v.render_pixels(cam, pix, params=p64, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            queries.append(hits)
+    T = sum(times)
+    val = sum(queries) / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{npix} random pixels of the 512x512 image per step"},
+        "cpu_baseline": {"value": val, "unit": "queries/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"{npix} pixels per step x {args.steps} steps"},
+        "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--cpu-pixels", type=int, default=2048)
+    ap.add_argument("--ref-pixels", type=int, default=512)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_05418_gb300 import api
+    dens, cam, params = make_workload(rank, device=dev)
+    ctx = api.Context()
+    vol = ctx.load_volume(torch.from_numpy(dens).to(dev))
+    ctx.build_mips(vol)
+    ctx.set_weights(torch.from_numpy(params).to(dev))
+    info = ctx.get_volume_info(vol)
+
+    def timed(prec, steps, warmup):
+        img = torch.empty((512, 512), dtype=torch.float32, device=dev)
+        rd = ctx.render_desc(cam, prec, api.MODE_RPNN)
+        _, nq = ctx.render(vol, cam, desc=rd, image=img, want_count=True)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            ctx.render(vol, cam, desc=rd, image=img)
+        ctx.sync_status()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        for e0, e1 in evs:
+            flush.zero_()                         # L2 flush between steps (outside the events)
+            e0.record()
+            ctx.render(vol, cam, desc=rd, image=img)
+            e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ctx.set_profiling(False)
+        prof = ctx.read_profile()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        ctx.sync_status()
+        return nq, ms, prof, img
+
+    prec = api.BF16 if args.precision == "bf16" else api.F32
+    clocks = Clocks(local)
+    clocks.start()
+    try:
+        nq, ms, prof, img = timed(prec, args.steps, args.warmup)
+    except api.RPNNError as e:
+        if prec != api.BF16 or e.code != -8:
+            raise
+        prec = api.F32                      # tensor-core network not built: report FP32
+        nq, ms, prof, img = timed(prec, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, ws, dev)
+    q_total = sum_over_ranks(float(nq) * args.steps, ws, dev)
+    value = q_total / (ms_max / 1e3)
+    per_step = ms_max / args.steps
+
+    # FP32 CUDA-core form of the same render, for the ratio
+    f32_form = None
+    if prec == api.BF16:
+        nq32, ms32, prof32, img32 = timed(api.F32, max(3, args.steps // 4), 3)
+        f32_form = {"value": nq32 * max(3, args.steps // 4) / (ms32 / 1e3), "unit": "queries/s",
+                    "ms_per_step": ms32 / max(3, args.steps // 4),
+                    "network_ms_per_step": prof32["network"] / max(1, prof32["renders"])}
+        f32_form["ratio"] = value / ws / f32_form["value"]
+
+    # end to end through the public API: host-visible result every step
+    host_img = torch.empty((512, 512), dtype=torch.float32, pin_memory=True)
+    rd = ctx.render_desc(cam, prec, api.MODE_RPNN)
+    gimg = torch.empty((512, 512), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.render(vol, cam, desc=rd, image=gimg)
+        host_img.copy_(gimg, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e = {"value": q_total / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 12,
+           "d2h_bytes_per_step": 512 * 512 * 4}
+
+    # roofline of the dominant stage
+    pk = peaks()
+    n = max(1, prof["renders"])
+    stage_ms = {k: prof[k] / n for k in ("primary", "descriptor", "network", "composite")}
+    dom = max(stage_ms, key=stage_ms.get)
+    elem = 2 if prec == api.BF16 else 4
+    pyr_bytes = sum((a + 1) * (b + 1) * (c + 1) * 32 for i, (a, b, c) in enumerate(info["dims"])
+                    if i in set(info["mip_of_level"]))
+    desc_bytes = nq * (2251 * elem + 24) + pyr_bytes
+    if dom == "network" and prec == api.BF16:
+        ach = nq * FLOP_PER_QUERY / (stage_ms["network"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s"}
+    elif dom == "network":
+        alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        ach = nq * FLOP_PER_QUERY / (stage_ms["network"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s"}
+    else:
+        st = "descriptor" if dom == "descriptor" else dom
+        ach = desc_bytes / (stage_ms[st] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["peak_src"] = pk["src"]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == api.BF16 else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_step": int(nq), "pixels": 512 * 512,
+                   "l2": "flushed: 256 MB write between timed steps",
+                   "mip_of_level": info["mip_of_level"]},
+        "stages_ms_per_step": stage_ms,
+        "gpu_launches": (5 if prec == api.BF16 else 27) * args.steps,
+        "e2e": e2e, "roofline": roof, "clocks": clk,
+    }
+    if f32_form:
+        line["fp32_form"] = f32_form
+    if rank == 0 and not args.no_cpu:
+        pix, vals, hits, dt, nth = cpu_sample(dens, cam, params, args.cpu_pixels)
+        line["cpu_baseline"] = {"value": hits / dt, "unit": "queries/s", "cores": nth, "kind": "oracle",
+                                "sample": f"{args.cpu_pixels} random pixels of the 512x512 image "
+                                          f"({hits} shading queries), FP64"}
+        got = img.double().cpu().numpy().ravel()[pix]
+        err = float(np.sqrt(np.mean((got - vals) ** 2)) / max(np.sqrt(np.mean(vals ** 2)), 1e-30))
+        line["error_vs_fp64_oracle"] = {"pixels": int(pix.size), "rel_rmse": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

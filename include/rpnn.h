@@ -1,0 +1,208 @@
+/*
+ * rpnn.h -- C ABI of the GB300 (sm_103a) RPNN cloud-rendering hot path.
+ *
+ * Method: Kallweit, Mueller, McWilliams, Gross, Novak, "Deep Scattering: Rendering
+ * Atmospheric Clouds with Radiance-Predicting Neural Networks".  For every shading
+ * point the path (a) samples a visible point by delta tracking (Sec. 4.4), (b)
+ * gathers the 10-level 5x5x9 light-aligned stencil descriptor from a Gaussian
+ * mip pyramid of the mean-free-path-normalised density (Sec. 4.2, Sec. 6), (c) runs
+ * the progressive-input residual network (Sec. 4.3, Fig. 6) and adds its indirect
+ * prediction to the Monte Carlo single-scattering estimate (Sec. 4.4).  Training
+ * (Sec. 5) runs on the same device with the library's own forward/backward kernels.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: RPNN_OK (0) or a negative rpnn_status.  Errors never abort the
+ *    process; rpnn_last_error() gives a message for the calling thread.
+ *  - Pointers named dev_* are device pointers owned by the caller and borrowed for the
+ *    duration of the call (or of the asynchronous work it enqueues).  Everything the
+ *    library allocates (volume copies, pyramids, weight images, scratch) is owned by
+ *    the context and released by rpnn_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    enqueue work on it and return without synchronising unless documented otherwise.
+ *  - A context is bound to the CUDA device current at rpnn_create; call it from any
+ *    thread with that device current.  Calls on one context are not thread-safe.
+ *  - Geometry: a density grid of nx*ny*nz voxels (x fastest) is scaled uniformly into
+ *    the unit box (Sec. 5): voxel size h0 = 1/max(nx,ny,nz), grid extent
+ *    [0, nx*h0] x [0, ny*h0] x [0, nz*h0], voxel (i,j,k) centred at ((i+.5)h0, ...).
+ *    Density values are extinction coefficients per unit of that box.
+ *  - Directions: `d` is a ray's tracing direction (from the camera into the cloud);
+ *    the radiance of Eq. 1 propagates along omega = -d.  `light_dir` points towards
+ *    the (directional) light.
+ */
+#ifndef RPNN_ABI_H_
+#define RPNN_ABI_H_
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpnn_ctx rpnn_ctx;
+typedef int32_t rpnn_status;
+
+enum {
+    RPNN_OK = 0,
+    RPNN_ERR_ARG = -1,          /* invalid argument (size, pointer, value) */
+    RPNN_ERR_HANDLE = -2,       /* unknown context or volume id */
+    RPNN_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    RPNN_ERR_OOM = -4,          /* device allocation failed */
+    RPNN_ERR_ITER_LIMIT = -5,   /* a device loop hit its iteration cap (result truncated) */
+    RPNN_ERR_NONFINITE = -6,    /* NaN/Inf met in data the call validates */
+    RPNN_ERR_STATE = -7,        /* call order violated (e.g. render before set_weights) */
+    RPNN_ERR_UNSUPPORTED = -8   /* combination not built for this device */
+};
+
+enum { RPNN_F32 = 0, RPNN_F16 = 1, RPNN_BF16 = 2 };
+
+enum {
+    RPNN_K = 10,            /* stencil levels (Sec. 4.2) */
+    RPNN_S = 225,           /* points per level: 5 x 5 x 9 (Sec. 4.2) */
+    RPNN_DIN = 226,         /* network input per block: Sigma^k and gamma (Sec. 4.3) */
+    RPNN_DESC_STRIDE = 240, /* stored width of one level of a descriptor row */
+    RPNN_H = 200,           /* hidden width (Sec. 7: every layer has 200 nodes) */
+    RPNN_NPARAMS = 1296601  /* flat parameter count, layout below */
+};
+
+/* ---- context -------------------------------------------------------------------- */
+rpnn_status rpnn_create(rpnn_ctx** out);
+rpnn_status rpnn_destroy(rpnn_ctx* ctx);
+/* Message of the calling thread's last error ("" if none).  Valid until the next call. */
+const char* rpnn_last_error(void);
+/* Reads (and clears) the context's device status word; synchronises `stream`.
+ * Returns RPNN_OK, RPNN_ERR_ITER_LIMIT or RPNN_ERR_NONFINITE. */
+rpnn_status rpnn_sync_status(rpnn_ctx* ctx, void* stream);
+
+/* ---- volume (Sec. 4.2 mean-free-path normalisation; Sec. 5 unit box) ---------------- */
+/* Copies the caller's density grid (dtype RPNN_F32 or RPNN_F16, nx*ny*nz values, x
+ * fastest) into a library-owned FP32 grid and returns its id in *out_vol.  albedo is
+ * the single-scattering albedo alpha (mu_s = alpha mu_t, Sec. 3.2), hg_g the
+ * Henyey-Greenstein asymmetry (Sec. 5.1).  Values must be finite and >= 0 (checked by
+ * rpnn_build_mips). */
+rpnn_status rpnn_load_volume(rpnn_ctx* ctx, const void* dev_density, int32_t dtype, int32_t nx,
+                             int32_t ny, int32_t nz, float albedo, float hg_g,
+                             int32_t* out_vol, void* stream);
+/* Computes the volume statistics (majorant, mean over non-zero voxels -- an exact
+ * fixed-point sum with 32 fraction bits below the majorant's binary exponent) and the
+ * Gaussian mip levels read by the 10 stencil levels (sigma_i = 2^i fine voxels, Sec.
+ * 6; truncated at 3 sigma, normalised, zero outside, divided by the mean).  Synchronises
+ * `stream` once to read the statistics back.  RPNN_ERR_NONFINITE for negative/NaN/Inf
+ * voxels, RPNN_ERR_ARG for an all-zero grid. */
+rpnn_status rpnn_build_mips(rpnn_ctx* ctx, int32_t vol, void* stream);
+
+typedef struct {
+    int32_t n[3];              /* nx, ny, nz */
+    int32_t levels;            /* mip levels 0..levels-1 */
+    int32_t dims[16][3];       /* per level: ceil(n / 2^i) */
+    int32_t mip_of_level[RPNN_K]; /* mip level read by stencil level k (0-based) */
+    double mean;               /* mean extinction over voxels > 0 */
+    float inv_mean_f;          /* (float)(1/mean) = one mean free path in world units */
+    float majorant;            /* max voxel value */
+    int64_t nonzero;           /* voxels > 0 */
+} rpnn_volume_info;
+/* Host copy of the statistics (valid after rpnn_build_mips). */
+rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* out);
+/* Writes mip level `level` as FP32 [dims[2]][dims[1]][dims[0]] into dev_out (building it
+ * if the stencil does not use it). */
+rpnn_status rpnn_copy_mip_level(rpnn_ctx* ctx, int32_t vol, int32_t level, float* dev_out,
+                                void* stream);
+
+/* ---- network parameters (Sec. 4.3) --------------------------------------------------- */
+/* Flat FP32 parameter vector, row-major [out][in] matrices, in this order:
+ *   for block k = 1..10:  V^k [200][226], W1^k [200][200] (omitted for k = 1: o^0 = 0,
+ *                         footnote 1 of Sec. 4.3), b1^k [200], W2^k [200][200], b2^k [200]
+ *   standard layers:      [200][200], [200], [200][200], [200], [1][200], [1]
+ * 1,296,601 values.  Block: F1 = relu(V z^k + W1 o^{k-1} + b1), F2 = W2 F1 + b2,
+ * o^k = relu(F2 + o^{k-1}); standard layer o' = relu(W o + b); g = last output.
+ * The library keeps its own FP32 copy and a BF16 tensor-core image; the caller's
+ * buffer may be freed after the call returns (the copy is enqueued on `stream`). */
+rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_params,
+                             void* stream);
+
+/* ---- descriptor (Sec. 4.2, Fig. 5) ---------------------------------------------------- */
+/* For q shading points x (dev_x, q*3 FP32, unit-box world coordinates) with tracing
+ * directions d (dev_d, q*3 FP32, unit length) and light directions (dev_wl: 3 floats
+ * shared by all queries when wl_stride = 0, or q*3 floats when wl_stride = 3; unit
+ * length) writes the descriptor rows [q][10][RPNN_DESC_STRIDE] of dtype RPNN_F32 or
+ * RPNN_BF16 into dev_desc: per level k the 225 densities rho at the stencil points in
+ * (iz*5+iy)*5+ix order, then gamma = acos(omega . light) in radians, then zeros.
+ * Frame: z = light, x = normalize(z cross omega), y = z cross x (x = first vector of
+ * the Duff et al. 2017 basis of z when omega is parallel to z).  The FP32 arithmetic
+ * follows one fixed rounding sequence, bit-identical to the FP32 CPU restatement. */
+rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* dev_x,
+                                     const float* dev_d, const float* dev_wl, int32_t wl_stride,
+                                     int64_t q, void* dev_desc, int32_t desc_dtype, void* stream);
+
+/* ---- network forward (Sec. 4.3) -------------------------------------------------------- */
+/* g = RPNN(z) for q descriptor rows (layout of rpnn_extract_descriptors; dtype RPNN_F32
+ * or RPNN_BF16).  precision RPNN_F32: FP32 CUDA-core form; RPNN_BF16: tcgen05 tensor
+ * cores, BF16 operands, FP32 accumulation (needs desc_dtype RPNN_BF16).  dev_out: q FP32. */
+rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
+                             int32_t precision, float* dev_out, void* stream);
+
+/* ---- rendering (Sec. 4.4) ---------------------------------------------------------------- */
+typedef struct {
+    float cam_pos[3], cam_fwd[3], cam_right[3], cam_up[3]; /* pinhole frame (unit vectors) */
+    float tan_half_fov_y;
+    int32_t width, height, spp;
+    uint64_t seed;                /* Philox4x32-10 key */
+    float light_dir[3];           /* unit, towards the light */
+    float light_E;                /* irradiance of the directional light */
+    int32_t precision;            /* RPNN_F32 or RPNN_BF16 network arithmetic */
+    int32_t mode;                 /* RPNN_MODE_* */
+} rpnn_render_desc;
+enum { RPNN_MODE_RPNN = 0, RPNN_MODE_SINGLE = 1, RPNN_MODE_PATH = 2 };
+/* Renders width*height pixels (row-major, y down) into dev_image (FP32, caller-owned):
+ * pixel = (1/spp) sum_s alpha * E * (p_HG(d.light) T_light + g(z)), where the first term
+ * is next-event estimation with a ratio-tracked shadow ray and g the network's L_i
+ * prediction (RPNN_MODE_RPNN), zero (RPNN_MODE_SINGLE), or a path-traced L_i estimate
+ * (RPNN_MODE_PATH, the plain Monte Carlo reference).  Rays that miss the cloud give 0.
+ * *out_num_queries (host, may be NULL) receives the number of shading points; passing
+ * it synchronises `stream`. */
+rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc,
+                        float* dev_image, int64_t* out_num_queries, void* stream);
+/* Stage timing (no counterpart in the paper; used to attribute render time).  When on,
+ * rpnn_render records CUDA events on its stream at the boundaries of its four stages:
+ * primary (tracking + NEE), descriptor, network, composite.  rpnn_read_profile waits for
+ * those events, writes the summed device milliseconds of each stage over the renders
+ * since the previous read into ms[RPNN_NUM_STAGES] and their number into *renders. */
+enum { RPNN_STAGE_PRIMARY = 0, RPNN_STAGE_DESCRIPTOR = 1, RPNN_STAGE_NETWORK = 2,
+       RPNN_STAGE_COMPOSITE = 3, RPNN_NUM_STAGES = 4 };
+rpnn_status rpnn_set_profiling(rpnn_ctx* ctx, int32_t on);
+rpnn_status rpnn_read_profile(rpnn_ctx* ctx, double* ms, int64_t* renders);
+/* Primary stage only, for inspection: per pixel-sample ps = pixel*spp + sample writes
+ * hit flag (1 hit, 0 miss), x (3 floats), d (3 floats), L_d (E p T, without alpha). */
+rpnn_status rpnn_trace_primary(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc,
+                               int32_t* dev_hit, float* dev_x, float* dev_d, float* dev_Ld,
+                               void* stream);
+
+/* ---- training (Sec. 5) -------------------------------------------------------------------- */
+/* Training records (Sec. 5.1) `first` .. `first+n-1` of stream `seed`: direction uniform
+ * on the sphere, origin uniform on the bounding sphere's cross-section, free flight by
+ * delta tracking (retried on escape), light direction uniform on the sphere, and L_i by
+ * path tracing with next-event estimation until the 95% half-width is within rel_ci of
+ * the mean (n_min .. n_max paths).  Outputs (FP32, caller-owned): x, d, wl (n*3 each),
+ * label (n), npaths (n int32). */
+rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t n, uint64_t seed,
+                             float rel_ci, int32_t n_min, int32_t n_max, float* dev_x,
+                             float* dev_d, float* dev_wl, float* dev_label,
+                             int32_t* dev_npaths, void* stream);
+/* Gradient of sum_i dout_i * g(z_i) w.r.t. the parameters currently set by
+ * rpnn_set_weights (FP32 CUDA-core chain rule), written (not accumulated) to
+ * dev_dparams (RPNN_NPARAMS floats).  dev_desc: q rows, FP32. */
+rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q,
+                              const float* dev_dout, float* dev_dparams, void* stream);
+typedef struct { float lr, beta1, beta2, eps; } rpnn_adam_cfg;
+/* One optimiser step (Sec. 5.2): forward on `batch` FP32 descriptor rows, loss
+ * mean (log(1+g) - log(1+L))^2 written as FP64 to *dev_loss (device), backward, Adam
+ * (step >= 1, bias-corrected) on the caller's FP32 parameters dev_params with moments
+ * dev_m, dev_v (RPNN_NPARAMS each, updated in place), then the library's weight copies
+ * are refreshed from the updated parameters. */
+rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* dev_target,
+                            int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
+                            float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of the C ABI in ``include/rpnn.h``.
+
+Argument marshalling only: every step runs in the CUDA library.  Tensors are
+PyTorch CUDA tensors (device memory and streams are PyTorch's); their data
+pointers and the current stream are passed straight through.  The methods of
+``Context`` carry the C entry points' names without the ``rpnn_`` prefix.
+Importing this module does not load the library; creating a ``Context`` does,
+and raises if it has not been built or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+K, S, DIN, DESC_STRIDE, H, NPARAMS = 10, 225, 226, 240, 200, 1296601
+F32, F16, BF16 = 0, 1, 2
+MODE_RPNN, MODE_SINGLE, MODE_PATH = 0, 1, 2
+ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_HANDLE", -3: "ERR_CUDA", -4: "ERR_OOM",
+             -5: "ERR_ITER_LIMIT", -6: "ERR_NONFINITE", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
+
+
+class RPNNError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class RenderDesc(C.Structure):
+    _fields_ = [("cam_pos", C.c_float * 3), ("cam_fwd", C.c_float * 3),
+                ("cam_right", C.c_float * 3), ("cam_up", C.c_float * 3),
+                ("tan_half_fov_y", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("spp", C.c_int32), ("seed", C.c_uint64), ("light_dir", C.c_float * 3),
+                ("light_E", C.c_float), ("precision", C.c_int32), ("mode", C.c_int32)]
+
+
+class VolumeInfo(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("levels", C.c_int32), ("dims", (C.c_int32 * 3) * 16),
+                ("mip_of_level", C.c_int32 * K), ("mean", C.c_double),
+                ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64)]
+
+
+class AdamCfg(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the built library (after PyTorch has initialised CUDA, so both share one
+    runtime).  Raises when the library is missing or no CUDA device is visible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the RPNN library runs on the GPU only")
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built ({_build.LIB}); run build()")
+        torch.cuda.init()
+        L = C.CDLL(_build.LIB)
+        i32, i64, u64, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_float
+        sig = {
+            "rpnn_create": [C.POINTER(_vp)],
+            "rpnn_destroy": [_vp],
+            "rpnn_sync_status": [_vp, _vp],
+            "rpnn_load_volume": [_vp, _vp, i32, i32, i32, i32, f32, f32, C.POINTER(i32), _vp],
+            "rpnn_build_mips": [_vp, i32, _vp],
+            "rpnn_get_volume_info": [_vp, i32, C.POINTER(VolumeInfo)],
+            "rpnn_copy_mip_level": [_vp, i32, i32, _vp, _vp],
+            "rpnn_set_weights": [_vp, _vp, i64, _vp],
+            "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
+            "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
+            "rpnn_render": [_vp, i32, C.POINTER(RenderDesc), _vp, C.POINTER(i64), _vp],
+            "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
+            "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
+                                 _vp, _vp],
+            "rpnn_mlp_backward": [_vp, _vp, i64, _vp, _vp, _vp],
+            "rpnn_train_step": [_vp, _vp, _vp, i32, C.POINTER(AdamCfg), i64, _vp, _vp, _vp,
+                                _vp, _vp],
+            "rpnn_set_profiling": [_vp, i32],
+            "rpnn_read_profile": [_vp, C.POINTER(C.c_double), C.POINTER(i64)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int32
+        L.rpnn_last_error.restype = C.c_char_p
+        L.rpnn_last_error.argtypes = []
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t):
+    return {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[t.dtype]
+
+
+class Context:
+    """One rpnn_ctx bound to the current CUDA device."""
+
+    def __init__(self):
+        self.L = load()
+        h = C.c_void_p()
+        self._check(self.L.rpnn_create(C.byref(h)))
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RPNNError(rc, self.L.rpnn_last_error().decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rpnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- volume ---------------------------------------------------------------------
+    def load_volume(self, density: torch.Tensor, albedo=0.99, hg_g=0.85) -> int:
+        assert density.dim() == 3
+        nz, ny, nx = density.shape
+        vid = C.c_int32()
+        self._check(self.L.rpnn_load_volume(self.h, _ptr(density), _dtype_code(density), nx, ny,
+                                            nz, albedo, hg_g, C.byref(vid), _stream()))
+        return vid.value
+
+    def build_mips(self, vol: int):
+        self._check(self.L.rpnn_build_mips(self.h, vol, _stream()))
+
+    def get_volume_info(self, vol: int) -> dict:
+        i = VolumeInfo()
+        self._check(self.L.rpnn_get_volume_info(self.h, vol, C.byref(i)))
+        return {"n": tuple(i.n), "levels": i.levels,
+                "dims": [tuple(i.dims[k]) for k in range(i.levels)],
+                "mip_of_level": list(i.mip_of_level), "mean": i.mean,
+                "inv_mean_f": i.inv_mean_f, "majorant": i.majorant, "nonzero": i.nonzero}
+
+    def copy_mip_level(self, vol: int, level: int) -> torch.Tensor:
+        info = self.get_volume_info(vol)
+        ax, ay, az = info["dims"][level]
+        out = torch.empty((az, ay, ax), dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_copy_mip_level(self.h, vol, level, _ptr(out), _stream()))
+        return out
+
+    def sync_status(self):
+        self._check(self.L.rpnn_sync_status(self.h, _stream()))
+
+    STAGES = ("primary", "descriptor", "network", "composite")
+
+    def set_profiling(self, on: bool):
+        self._check(self.L.rpnn_set_profiling(self.h, 1 if on else 0))
+
+    def read_profile(self) -> dict:
+        ms = (C.c_double * 4)()
+        n = C.c_int64()
+        self._check(self.L.rpnn_read_profile(self.h, ms, C.byref(n)))
+        out = {k: ms[i] for i, k in enumerate(self.STAGES)}
+        out["renders"] = n.value
+        return out
+
+    # -- network ----------------------------------------------------------------------
+    def set_weights(self, params: torch.Tensor):
+        assert params.dtype == torch.float32 and params.numel() == NPARAMS
+        self._check(self.L.rpnn_set_weights(self.h, _ptr(params), params.numel(), _stream()))
+
+    def extract_descriptors(self, vol, x, d, wl, dtype=torch.float32, out=None):
+        q = x.shape[0]
+        stride = 3 if wl.dim() == 2 else 0
+        if out is None:
+            out = torch.empty((q, K, DESC_STRIDE), dtype=dtype, device="cuda")
+        self._check(self.L.rpnn_extract_descriptors(self.h, vol, _ptr(x), _ptr(d), _ptr(wl),
+                                                    stride, q, _ptr(out), _dtype_code(out),
+                                                    _stream()))
+        return out
+
+    def mlp_forward(self, desc, precision=F32, out=None):
+        q = desc.shape[0]
+        if out is None:
+            out = torch.empty(q, dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_mlp_forward(self.h, _ptr(desc), _dtype_code(desc), q, precision,
+                                            _ptr(out), _stream()))
+        return out
+
+    def mlp_backward(self, desc, dout, out=None):
+        q = desc.shape[0]
+        if out is None:
+            out = torch.empty(NPARAMS, dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_mlp_backward(self.h, _ptr(desc), q, _ptr(dout), _ptr(out), _stream()))
+        return out
+
+    def train_step(self, desc, target, params, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999,
+                   eps=1e-8, loss=None):
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        cfg = AdamCfg(lr, beta1, beta2, eps)
+        self._check(self.L.rpnn_train_step(self.h, _ptr(desc), _ptr(target), desc.shape[0],
+                                           C.byref(cfg), step, _ptr(params), _ptr(m), _ptr(v),
+                                           _ptr(loss), _stream()))
+        return loss
+
+    # -- rendering -------------------------------------------------------------------
+    @staticmethod
+    def render_desc(cam: dict, precision=F32, mode=MODE_RPNN) -> RenderDesc:
+        r = RenderDesc()
+        for k in ("cam_pos", "cam_fwd", "cam_right", "cam_up", "light_dir"):
+            arr = getattr(r, k)
+            for i in range(3):
+                arr[i] = float(cam[k][i])
+        r.tan_half_fov_y = float(cam["tan_half_fov_y"])
+        r.width, r.height, r.spp = int(cam["width"]), int(cam["height"]), int(cam["spp"])
+        r.seed = int(cam["seed"])
+        r.light_E = float(cam.get("light_E", 1.0))
+        r.precision, r.mode = int(precision), int(mode)
+        return r
+
+    def render(self, vol, cam: dict, precision=F32, mode=MODE_RPNN, image=None,
+               want_count=False, desc=None):
+        rd = desc if desc is not None else self.render_desc(cam, precision, mode)
+        if image is None:
+            image = torch.empty((rd.height, rd.width), dtype=torch.float32, device="cuda")
+        nq = C.c_int64(-1)
+        self._check(self.L.rpnn_render(self.h, vol, C.byref(rd), _ptr(image),
+                                       C.byref(nq) if want_count else None, _stream()))
+        return (image, nq.value) if want_count else image
+
+    def trace_primary(self, vol, cam: dict):
+        rd = self.render_desc(cam)
+        P = rd.width * rd.height * rd.spp
+        hit = torch.empty(P, dtype=torch.int32, device="cuda")
+        x = torch.empty((P, 3), dtype=torch.float32, device="cuda")
+        d = torch.empty((P, 3), dtype=torch.float32, device="cuda")
+        Ld = torch.empty(P, dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_trace_primary(self.h, vol, C.byref(rd), _ptr(hit), _ptr(x),
+                                              _ptr(d), _ptr(Ld), _stream()))
+        return hit, x, d, Ld
+
+    def gen_records(self, vol, first, n, seed, rel_ci=0.02, n_min=64, n_max=65536):
+        dev = "cuda"
+        x = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        d = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        wl = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        lab = torch.empty(n, dtype=torch.float32, device=dev)
+        npaths = torch.empty(n, dtype=torch.int32, device=dev)
+        self._check(self.L.rpnn_gen_records(self.h, vol, first, n, seed, rel_ci, n_min, n_max,
+                                            _ptr(x), _ptr(d), _ptr(wl), _ptr(lab), _ptr(npaths),
+                                            _stream()))
+        return x, d, wl, lab, npaths

@@ -1,0 +1,436 @@
+// capi.cu -- the C ABI declared in include/rpnn.h: argument checks, ownership, and the
+// sequencing of the kernels of each call.
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace rpnn {
+
+namespace {
+thread_local char g_err[1024] = "";
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+rpnn_status DevBuf::reserve(size_t n) {
+    if (n <= bytes) return RPNN_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    // round up to 2 MiB so repeated growth settles quickly
+    const size_t want = (n + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        set_error("cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+        return RPNN_ERR_OOM;
+    }
+    bytes = want;
+    return RPNN_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+}  // namespace rpnn
+
+using namespace rpnn;
+
+#define CHECK_CTX(ctx)                                                        \
+    do {                                                                      \
+        if (!(ctx)) { set_error("null context"); return RPNN_ERR_HANDLE; }    \
+        g_err_clear();                                                        \
+    } while (0)
+
+static void g_err_clear() { set_error("%s", ""); }
+
+static Volume* get_vol(Ctx* c, int id, bool need_built) {
+    Volume* v = c->vol(id);
+    if (!v) { set_error("unknown volume id %d", id); return nullptr; }
+    if (need_built && !v->built) { set_error("volume %d: rpnn_build_mips has not run", id); return nullptr; }
+    return v;
+}
+
+extern "C" {
+
+rpnn_status rpnn_create(rpnn_ctx** out) {
+    if (!out) { set_error("out is null"); return RPNN_ERR_ARG; }
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) { set_error("host allocation failed"); return RPNN_ERR_OOM; }
+    RPNN_CUDA_TRY(cudaGetDevice(&c->device));
+    RPNN_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    rpnn_status st = c->status.reserve(sizeof(uint32_t));
+    if (st) { delete c; return st; }
+    RPNN_CUDA_TRY(cudaMemset(c->status.p, 0, sizeof(uint32_t)));
+    *out = reinterpret_cast<rpnn_ctx*>(c);
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
+    if (!ctx) return RPNN_OK;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    cudaDeviceSynchronize();
+    for (Volume* v : c->vols) {
+        if (!v) continue;
+        v->raw.release(); v->packed.release(); v->stats.release();
+        delete v;
+    }
+    DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->q_x, &c->q_d, &c->q_ps,
+                      &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
+                      &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light};
+    for (DevBuf* b : bufs) b->release();
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    delete c;
+    return RPNN_OK;
+}
+
+const char* rpnn_last_error(void) { return g_err; }
+
+rpnn_status rpnn_sync_status(rpnn_ctx* ctx, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t h = 0;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(&h, c->status.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    RPNN_CUDA_TRY(cudaMemsetAsync(c->status.p, 0, sizeof h, s));
+    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h & kStatIterLimit) { set_error("a device loop reached its iteration cap"); return RPNN_ERR_ITER_LIMIT; }
+    if (h & kStatNonFinite) { set_error("non-finite value met on the device"); return RPNN_ERR_NONFINITE; }
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_load_volume(rpnn_ctx* ctx, const void* dev_density, int32_t dtype, int32_t nx,
+                             int32_t ny, int32_t nz, float albedo, float hg_g, int32_t* out_vol,
+                             void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!dev_density || !out_vol) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    if (dtype != RPNN_F32 && dtype != RPNN_F16) { set_error("density dtype must be F32 or F16"); return RPNN_ERR_ARG; }
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx > 8192 || ny > 8192 || nz > 8192 ||
+        (int64_t)nx * ny * nz > (int64_t)1 << 33) {
+        set_error("bad grid size %d x %d x %d", nx, ny, nz);
+        return RPNN_ERR_ARG;
+    }
+    if (!(albedo >= 0.0f && albedo <= 1.0f) || !(hg_g > -1.0f && hg_g < 1.0f)) {
+        set_error("albedo must be in [0,1] and hg_g in (-1,1)");
+        return RPNN_ERR_ARG;
+    }
+    Volume* v = new (std::nothrow) Volume();
+    if (!v) { set_error("host allocation failed"); return RPNN_ERR_OOM; }
+    v->n[0] = nx; v->n[1] = ny; v->n[2] = nz;
+    v->albedo = albedo; v->g = hg_g;
+    rpnn_status st = load_density(*c, *v, dev_density, dtype, (cudaStream_t)stream);
+    if (st) { v->raw.release(); delete v; return st; }
+    c->vols.push_back(v);
+    *out_vol = (int32_t)c->vols.size() - 1;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_build_mips(rpnn_ctx* ctx, int32_t vol, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, false);
+    if (!v) return RPNN_ERR_HANDLE;
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = volume_stats(*c, *v, s);
+    if (st) return st;
+    return volume_pack_levels(*c, *v, s);
+}
+
+rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* out) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (!out) { set_error("out is null"); return RPNN_ERR_ARG; }
+    *out = v->info;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_copy_mip_level(rpnn_ctx* ctx, int32_t vol, int32_t level, float* dev_out, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (!dev_out) { set_error("dev_out is null"); return RPNN_ERR_ARG; }
+    return volume_build_level(*c, *v, level, dev_out, (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_params, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!dev_params) { set_error("dev_params is null"); return RPNN_ERR_ARG; }
+    if (n_params != RPNN_NPARAMS) {
+        set_error("expected %d parameters, got %lld", RPNN_NPARAMS, (long long)n_params);
+        return RPNN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = c->params32.reserve(n_params * sizeof(float));
+    if (st) return st;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c->params32.p, dev_params, n_params * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s));
+    st = mlp_build_bf16_image(*c, s);
+    if (st) return st;
+    c->weights_set = true;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* dev_x, const float* dev_d,
+                                     const float* dev_wl, int32_t wl_stride, int64_t q, void* dev_desc,
+                                     int32_t desc_dtype, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (q < 0) { set_error("q < 0"); return RPNN_ERR_ARG; }
+    if (q == 0) return RPNN_OK;
+    if (!dev_x || !dev_d || !dev_wl || !dev_desc) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    if (wl_stride != 0 && wl_stride != 3) { set_error("wl_stride must be 0 or 3"); return RPNN_ERR_ARG; }
+    if (desc_dtype != RPNN_F32 && desc_dtype != RPNN_BF16) { set_error("desc dtype must be F32 or BF16"); return RPNN_ERR_ARG; }
+    return launch_descriptor(*c, v->view(), dev_x, dev_d, dev_wl, wl_stride, q, nullptr, dev_desc,
+                             desc_dtype, (cudaStream_t)stream);
+}
+
+static rpnn_status ensure_rows(Ctx* c, int64_t q, bool f32_net) {
+    rpnn_status st = RPNN_OK;
+    if (f32_net) {
+        const size_t b = (size_t)q * RPNN_H * sizeof(float);
+        if (!st) st = c->act0.reserve(b);
+        if (!st) st = c->act1.reserve(b);
+        if (!st) st = c->act2.reserve(b);
+    }
+    return st;
+}
+
+rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
+                             int32_t precision, float* dev_out, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    if (q < 0) { set_error("q < 0"); return RPNN_ERR_ARG; }
+    if (q == 0) return RPNN_OK;
+    if (!dev_desc || !dev_out) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    if (q > (int64_t)1 << 30) { set_error("q too large"); return RPNN_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == RPNN_F32) {
+        if (desc_dtype != RPNN_F32) { set_error("the FP32 network reads FP32 descriptors"); return RPNN_ERR_ARG; }
+        rpnn_status st = ensure_rows(c, q, true);
+        if (st) return st;
+        return mlp_forward_f32(*c, (const float*)dev_desc, q, nullptr, dev_out, nullptr, s);
+    }
+    if (precision == RPNN_BF16) {
+        if (desc_dtype != RPNN_BF16) { set_error("the BF16 network reads BF16 descriptors"); return RPNN_ERR_ARG; }
+        return mlp_forward_bf16(*c, dev_desc, q, nullptr, dev_out, s);
+    }
+    set_error("precision must be RPNN_F32 or RPNN_BF16");
+    return RPNN_ERR_ARG;
+}
+
+static rpnn_status check_desc(const rpnn_render_desc* d) {
+    if (!d) { set_error("desc is null"); return RPNN_ERR_ARG; }
+    if (d->width <= 0 || d->height <= 0 || d->spp <= 0 ||
+        (int64_t)d->width * d->height * d->spp > ((int64_t)1 << 31) - 1) {
+        set_error("bad image size %d x %d x %d spp", d->width, d->height, d->spp);
+        return RPNN_ERR_ARG;
+    }
+    if (d->mode < RPNN_MODE_RPNN || d->mode > RPNN_MODE_PATH) { set_error("bad mode"); return RPNN_ERR_ARG; }
+    if (d->precision != RPNN_F32 && d->precision != RPNN_BF16) { set_error("bad precision"); return RPNN_ERR_ARG; }
+    const float l2 = d->light_dir[0] * d->light_dir[0] + d->light_dir[1] * d->light_dir[1] +
+                     d->light_dir[2] * d->light_dir[2];
+    if (!(fabsf(l2 - 1.0f) < 1e-4f)) { set_error("light_dir must be unit length"); return RPNN_ERR_ARG; }
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_trace_primary(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, int32_t* dev_hit,
+                               float* dev_x, float* dev_d, float* dev_Ld, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    rpnn_status st = check_desc(desc);
+    if (st) return st;
+    if (!dev_hit || !dev_x || !dev_d || !dev_Ld) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    return launch_primary(*c, v->view(), *desc, nullptr, nullptr, nullptr, nullptr, nullptr, dev_hit,
+                          dev_x, dev_d, dev_Ld, (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, float* dev_image,
+                        int64_t* out_num_queries, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    rpnn_status st = check_desc(desc);
+    if (st) return st;
+    if (!dev_image) { set_error("dev_image is null"); return RPNN_ERR_ARG; }
+    const bool net = desc->mode == RPNN_MODE_RPNN;
+    if (net && !c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t P = (int64_t)desc->width * desc->height * desc->spp;
+    const bool f32 = desc->precision == RPNN_F32;
+    st = c->sample_val.reserve(P * sizeof(float));
+    if (!st) st = c->q_count.reserve(sizeof(int));
+    if (net) {
+        if (!st) st = c->q_x.reserve(P * 3 * sizeof(float));
+        if (!st) st = c->q_d.reserve(P * 3 * sizeof(float));
+        if (!st) st = c->q_ps.reserve(P * sizeof(uint32_t));
+        if (!st) st = c->g_out.reserve(P * sizeof(float));
+        if (!st) st = c->desc.reserve((size_t)P * RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2));
+        if (!st) st = ensure_rows(c, P, f32);
+    }
+    if (st) return st;
+    const VolumeView vv = v->view();
+    int* qc = c->q_count.as<int>();
+    cudaEvent_t* ev = nullptr;
+    if (c->profiling) {
+        if (c->prof_events.size() < (c->prof_used + 1) * 5) {
+            for (int i = 0; i < 5; ++i) {
+                cudaEvent_t e;
+                RPNN_CUDA_TRY(cudaEventCreate(&e));
+                c->prof_events.push_back(e);
+            }
+        }
+        ev = &c->prof_events[c->prof_used * 5];
+        ++c->prof_used;
+        RPNN_CUDA_TRY(cudaEventRecord(ev[0], s));
+    }
+    RPNN_CUDA_TRY(cudaMemsetAsync(qc, 0, sizeof(int), s));
+    st = launch_primary(*c, vv, *desc, c->sample_val.as<float>(), net ? c->q_x.as<float>() : nullptr,
+                        net ? c->q_d.as<float>() : nullptr, net ? c->q_ps.as<uint32_t>() : nullptr,
+                        net ? qc : nullptr, nullptr, nullptr, nullptr, nullptr, s);
+    if (st) return st;
+    if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[1], s));
+    if (!net && ev) {
+        RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
+        RPNN_CUDA_TRY(cudaEventRecord(ev[3], s));
+    }
+    if (net) {
+        // one light direction for the whole render, read by the descriptor kernel
+        st = c->light.reserve(4 * sizeof(float));
+        if (st) return st;
+        RPNN_CUDA_TRY(cudaMemcpyAsync(c->light.p, desc->light_dir, 3 * sizeof(float),
+                                      cudaMemcpyHostToDevice, s));
+        st = launch_descriptor(*c, vv, c->q_x.as<float>(), c->q_d.as<float>(), c->light.as<float>(), 0,
+                               P, qc, c->desc.p, f32 ? RPNN_F32 : RPNN_BF16, s);
+        if (st) return st;
+        if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
+        if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), P, qc, c->g_out.as<float>(), nullptr, s);
+        else st = mlp_forward_bf16(*c, c->desc.p, P, qc, c->g_out.as<float>(), s);
+        if (st) return st;
+        if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[3], s));
+    }
+    st = launch_scatter_composite(*c, *desc, v->albedo, net ? c->g_out.as<float>() : nullptr,
+                                  net ? c->q_ps.as<uint32_t>() : nullptr, qc, c->sample_val.as<float>(),
+                                  dev_image, net, s);
+    if (st) return st;
+    if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[4], s));
+    if (out_num_queries) {
+        int h = 0;
+        RPNN_CUDA_TRY(cudaMemcpyAsync(&h, qc, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+        *out_num_queries = net ? h : -1;
+    }
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_set_profiling(rpnn_ctx* ctx, int32_t on) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    c->profiling = on != 0;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_read_profile(rpnn_ctx* ctx, double* ms, int64_t* renders) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!ms || !renders) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    for (int i = 0; i < RPNN_NUM_STAGES; ++i) ms[i] = 0.0;
+    for (size_t r = 0; r < c->prof_used; ++r) {
+        cudaEvent_t* ev = &c->prof_events[r * 5];
+        RPNN_CUDA_TRY(cudaEventSynchronize(ev[4]));
+        for (int i = 0; i < RPNN_NUM_STAGES; ++i) {
+            float t = 0.0f;
+            RPNN_CUDA_TRY(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            ms[i] += t;
+        }
+    }
+    *renders = (int64_t)c->prof_used;
+    c->prof_used = 0;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t n, uint64_t seed,
+                             float rel_ci, int32_t n_min, int32_t n_max, float* dev_x, float* dev_d,
+                             float* dev_wl, float* dev_label, int32_t* dev_npaths, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (n < 0 || first < 0 || first + n > ((int64_t)1 << 32)) { set_error("bad record range"); return RPNN_ERR_ARG; }
+    if (n == 0) return RPNN_OK;
+    if (!dev_x || !dev_d || !dev_wl || !dev_label || !dev_npaths) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    if (!(rel_ci > 0.0f) || n_min < 1 || n_max < n_min) { set_error("bad stopping rule"); return RPNN_ERR_ARG; }
+    return launch_records(*c, v->view(), first, n, seed, rel_ci, n_min, n_max, dev_x, dev_d, dev_wl,
+                          dev_label, dev_npaths, (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q, const float* dev_dout,
+                              float* dev_dparams, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    if (q <= 0 || q > 65535 * 64) { set_error("q must be in [1, %d]", 65535 * 64); return RPNN_ERR_ARG; }
+    if (!dev_desc || !dev_dout || !dev_dparams) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = c->t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
+    if (!st) st = c->t_out.reserve(q * sizeof(float));
+    if (st) return st;
+    st = mlp_forward_f32(*c, dev_desc, q, nullptr, c->t_out.as<float>(), c->t_saved.as<float>(), s);
+    if (st) return st;
+    return mlp_backward_f32(*c, dev_desc, q, c->t_saved.as<float>(), dev_dout, dev_dparams, s);
+}
+
+rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* dev_target, int32_t batch,
+                            const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
+                            float* dev_v, double* dev_loss, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    if (batch <= 0 || batch > 65535 * 64) { set_error("bad batch %d", batch); return RPNN_ERR_ARG; }
+    if (!adam || step < 1) { set_error("adam config missing or step < 1"); return RPNN_ERR_ARG; }
+    if (!dev_desc || !dev_target || !dev_params || !dev_m || !dev_v || !dev_loss) {
+        set_error("null pointer");
+        return RPNN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t q = batch;
+    rpnn_status st = c->t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
+    if (!st) st = c->t_out.reserve(q * sizeof(float));
+    if (!st) st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
+    if (!st) st = c->sample_val.reserve(q * sizeof(float));
+    if (st) return st;
+    st = mlp_forward_f32(*c, dev_desc, q, nullptr, c->t_out.as<float>(), c->t_saved.as<float>(), s);
+    if (st) return st;
+    float* dg = c->sample_val.as<float>();
+    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
+    if (st) return st;
+    st = mlp_backward_f32(*c, dev_desc, q, c->t_saved.as<float>(), dg, c->t_grad.as<float>(), s);
+    if (st) return st;
+    st = launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), RPNN_NPARAMS, step, *adam, s);
+    if (st) return st;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c->params32.p, dev_params, (size_t)RPNN_NPARAMS * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s));
+    return mlp_build_bf16_image(*c, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// internal.h -- host-side state shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rpnn.h"
+
+namespace rpnn {
+
+constexpr int kMaxLevels = 16;
+
+// status bits written by kernels into the context's device status word
+enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u };
+
+void set_error(const char* fmt, ...);
+
+#define RPNN_CUDA_TRY(call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::rpnn::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                              __FILE__, __LINE__);                                       \
+            return e_ == cudaErrorMemoryAllocation ? RPNN_ERR_OOM : RPNN_ERR_CUDA;       \
+        }                                                                                \
+    } while (0)
+
+#define RPNN_CHECK_LAUNCH() RPNN_CUDA_TRY(cudaGetLastError())
+
+// A device allocation owned by the context; grows, never shrinks.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    rpnn_status reserve(size_t n);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Geometry of one level of the corner-packed pyramid: record (x,y,z) for x in
+// [-1, ax-1] holds the 8 trilinear corners of cell (x..x+1, y..y+1, z..z+1).
+struct LevelDesc {
+    int ax, ay, az;          // level dims
+    int64_t rec_offset;      // offset of the level's first record, in records
+};
+
+// Everything a kernel needs to read a volume; passed by value.
+struct VolumeView {
+    const float* raw;        // FP32 grid [nz][ny][nx]
+    int n[3];
+    float inv_h0;            // max(n)
+    float ext[3];            // grid extent in the unit box
+    float majorant;
+    float albedo, g;
+    float inv_mean_f;
+    int mip_of_level[RPNN_K];
+    const float4* packed;    // corner records (2 float4 per record)
+    LevelDesc lvl[kMaxLevels];
+};
+
+struct Volume {
+    int n[3] = {0, 0, 0};
+    float albedo = 0.f, g = 0.f;
+    DevBuf raw;              // FP32 copy
+    DevBuf packed;           // corner records for the levels the stencil reads
+    DevBuf stats;            // device-side statistics scratch
+    bool built = false;
+    int levels = 0;
+    int dims[kMaxLevels][3] = {};
+    rpnn_volume_info info{};
+    bool level_packed[kMaxLevels] = {};
+    LevelDesc lvl[kMaxLevels] = {};
+    VolumeView view() const;
+};
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::vector<Volume*> vols;
+    DevBuf status;           // uint32 status bits
+    DevBuf params32;         // FP32 parameters (flat, the documented layout)
+    DevBuf wimg_bf16;        // tensor-core weight image
+    bool weights_set = false;
+    // render scratch
+    DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
+    // training scratch
+    DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
+    // stage timing: one set of 5 events per profiled render
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_events;
+    size_t prof_used = 0;
+    Volume* vol(int id) const {
+        return (id >= 0 && id < (int)vols.size()) ? vols[id] : nullptr;
+    }
+};
+
+// ---- launchers implemented in the .cu files -------------------------------------------
+rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
+rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s);
+rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s);
+rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStream_t s);
+
+rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, const float* d,
+                              const float* wl, int wl_stride, int64_t q, const int* q_dev,
+                              void* out, int dtype, cudaStream_t s);
+
+// Primary stage.  Query outputs (qx, qd, qps, qcount) and inspection outputs (hit, xo,
+// dout, Ld; per pixel sample) are each optional.
+rpnn_status launch_primary(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd,
+                           float* sample_val, float* qx, float* qd, uint32_t* qps, int* qcount,
+                           int* hit, float* xo, float* dout, float* Ld, cudaStream_t s);
+rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float alpha,
+                                     const float* g, const uint32_t* qps, const int* qcount,
+                                     float* sample_val, float* image, bool with_g,
+                                     cudaStream_t s);
+rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n,
+                           uint64_t seed, float rel_ci, int n_min, int n_max, float* x,
+                           float* d, float* wl, float* label, int* npaths, cudaStream_t s);
+
+// FP32 CUDA-core network
+rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_dev,
+                            float* out, float* saved, cudaStream_t s);
+rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
+                             const float* dout, float* dparams, cudaStream_t s);
+size_t mlp_saved_floats_per_row();
+rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss,
+                        float* dg, cudaStream_t s);
+rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,
+                        int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s);
+
+// BF16 tensor-core network
+rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);
+rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev,
+                             float* out, cudaStream_t s);
+
+// parameter layout offsets (floats) of the flat vector
+struct ParamLayout {
+    int64_t V[RPNN_K], W1[RPNN_K], b1[RPNN_K], W2[RPNN_K], b2[RPNN_K];
+    int64_t T[3], bT[3];
+    int64_t total;
+};
+const ParamLayout& param_layout();
+
+}  // namespace rpnn

@@ -1,0 +1,225 @@
+// render.cu -- Monte Carlo part of the renderer (Sec. 4.4) and the training-record
+// generator (Sec. 5.1).
+//
+// k_primary: one thread per pixel sample.  Pinhole ray with Philox pixel jitter, delta
+// tracking to the first real collision (the visible point), next-event estimation of
+// the direct in-scattering with a ratio-tracked shadow ray, and either (RPNN mode) an
+// appended shading query for the descriptor + network stages, or (path mode) a
+// path-traced estimate of the indirect part.  Queries are compacted with one atomic per
+// warp so the list stays in pixel order within a warp.
+#include "common.cuh"
+
+namespace rpnn {
+
+namespace {
+
+struct RenderArgs {
+    float cam_pos[3], cam_fwd[3], cam_right[3], cam_up[3];
+    float tan_half, aspect;
+    int W, H, spp;
+    uint64_t seed;
+    float wl[3];
+    float E;
+    int mode;   // RPNN_MODE_*
+};
+
+__global__ void __launch_bounds__(128)
+k_primary(const VolumeView v, const RenderArgs a, int64_t P, float* __restrict__ sample_val,
+          float* __restrict__ qx, float* __restrict__ qd, uint32_t* __restrict__ qps,
+          int* __restrict__ qcount, int* __restrict__ hit_out, float* __restrict__ x_out,
+          float* __restrict__ d_out, float* __restrict__ Ld_out, uint32_t* status) {
+    const int64_t ps = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = ps < P;
+    int hit = 0;
+    float3 x = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
+    float Ld = 0.0f;
+    if (active) {
+        const uint32_t pixel = (uint32_t)(ps / a.spp), s = (uint32_t)(ps % a.spp);
+        const int px = (int)(pixel % (uint32_t)a.W), py = (int)(pixel / (uint32_t)a.W);
+        const Rng rc = make_rng(a.seed, pixel, s, kDomCamera);
+        const float4 xi = rc.draw(0);
+        const float sx = (2.0f * ((float)px + xi.x) / (float)a.W - 1.0f) * a.tan_half * a.aspect;
+        const float sy = (1.0f - 2.0f * ((float)py + xi.y) / (float)a.H) * a.tan_half;
+        d = normalize3(f3(a.cam_fwd[0] + sx * a.cam_right[0] + sy * a.cam_up[0],
+                          a.cam_fwd[1] + sx * a.cam_right[1] + sy * a.cam_up[1],
+                          a.cam_fwd[2] + sx * a.cam_right[2] + sy * a.cam_up[2]));
+        const float3 o = f3(a.cam_pos[0], a.cam_pos[1], a.cam_pos[2]);
+        uint32_t ctr = 0;
+        const int r = delta_track(v, o, d, make_rng(a.seed, pixel, s, kDomPrimary), ctr, x);
+        bool capped = r < 0;
+        hit = r == 1;
+        float val = 0.0f;
+        if (hit) {
+            const float3 wl = f3(a.wl[0], a.wl[1], a.wl[2]);
+            uint32_t c2 = 0;
+            Ld = nee(v, x, d, wl, a.E, make_rng(a.seed, pixel, s, kDomShadow), c2, capped);
+            float Li = 0.0f;
+            if (a.mode == RPNN_MODE_PATH)
+                Li = path_Li(v, x, d, wl, a.E, make_rng(a.seed, pixel, s, kDomPath), capped);
+            val = v.albedo * (Ld + Li);
+        }
+        if (capped) raise_status(status, kStatIterLimit);
+        if (sample_val) sample_val[ps] = val;
+        if (hit_out) {
+            hit_out[ps] = hit;
+            x_out[3 * ps] = x.x; x_out[3 * ps + 1] = x.y; x_out[3 * ps + 2] = x.z;
+            d_out[3 * ps] = d.x; d_out[3 * ps + 1] = d.y; d_out[3 * ps + 2] = d.z;
+            Ld_out[ps] = Ld;
+        }
+    }
+    if (qcount) {
+        const bool want = active && hit;
+        const unsigned mask = __ballot_sync(0xffffffffu, want);
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == 0 && mask) base = atomicAdd(qcount, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (want) {
+            const int slot = base + __popc(mask & ((1u << lane) - 1u));
+            qx[3 * slot] = x.x; qx[3 * slot + 1] = x.y; qx[3 * slot + 2] = x.z;
+            qd[3 * slot] = d.x; qd[3 * slot + 1] = d.y; qd[3 * slot + 2] = d.z;
+            qps[slot] = (uint32_t)ps;
+        }
+    }
+}
+
+// sample_val[ps_i] += alpha * E * g_i for every shading query i
+__global__ void k_scatter(const float* __restrict__ g, const uint32_t* __restrict__ qps,
+                          const int* __restrict__ qcount, float scale, float* __restrict__ sample_val) {
+    const int n = *qcount;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        sample_val[qps[i]] += scale * g[i];
+}
+
+// pixel = mean over its spp samples, summed in sample order
+__global__ void k_composite(const float* __restrict__ sample_val, int64_t npix, int spp,
+                            float* __restrict__ image) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int s = 0; s < spp; ++s) acc += sample_val[p * spp + s];
+        image[p] = acc / (float)spp;
+    }
+}
+
+// Training records (Sec. 5.1); one thread per record.
+__global__ void __launch_bounds__(128)
+k_records(const VolumeView v, int64_t first, int64_t n, uint64_t seed, float rel_ci, int n_min,
+          int n_max, float* __restrict__ xo, float* __restrict__ dout, float* __restrict__ wlo,
+          float* __restrict__ label, int* __restrict__ npaths, uint32_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t rec = (uint32_t)(first + i);
+    const float ext[3] = {v.ext[0], v.ext[1], v.ext[2]};
+    const float3 C = f3(0.5f * ext[0], 0.5f * ext[1], 0.5f * ext[2]);
+    const float R = 0.5f * sqrtf(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
+    float3 x = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
+    bool found = false;
+    for (uint32_t att = 0; att < (uint32_t)kRecordAttempts && !found; ++att) {
+        const float4 xi = make_rng(seed, rec, att, kDomRecord).draw(0);
+        const float cz = 1.0f - 2.0f * xi.x;
+        float sp, cp;
+        sincosf(2.0f * kPi * xi.y, &sp, &cp);
+        const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
+        d = f3(sz * cp, sz * sp, cz);
+        float3 b1, b2;
+        duff_basis(d, b1, b2);
+        const float rr = R * sqrtf(xi.z);
+        float s2, c2;
+        sincosf(2.0f * kPi * xi.w, &s2, &c2);
+        const float3 o = C + (rr * c2) * b1 + (rr * s2) * b2 + (-2.0f * R) * d;
+        uint32_t ctr = 0;
+        const int h = delta_track(v, o, d, make_rng(seed, rec, att, kDomRecTrack), ctr, x);
+        if (h < 0) raise_status(status, kStatIterLimit);
+        found = h == 1;
+    }
+    float3 wl;
+    {
+        const float4 xi = make_rng(seed, rec, 0, kDomLight).draw(0);
+        const float cz = 1.0f - 2.0f * xi.x;
+        float sp, cp;
+        sincosf(2.0f * kPi * xi.y, &sp, &cp);
+        const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
+        wl = f3(sz * cp, sz * sp, cz);
+    }
+    double mu = 0.0, m2 = 0.0;
+    int j = 0;
+    bool capped = false;
+    if (found) {
+        for (j = 0; j < n_max;) {
+            const float L = path_Li(v, x, d, wl, 1.0f, make_rng(seed, rec, (uint32_t)j, kDomLabel), capped);
+            const double delta = (double)L - mu;
+            mu += delta / (double)(j + 1);
+            m2 += delta * ((double)L - mu);
+            ++j;
+            if (j >= n_min && j > 1) {
+                const double hw = 1.96 * sqrt(m2 / (double)(j - 1) / (double)j);
+                if (mu > 0.0 && hw <= (double)rel_ci * mu) break;
+            }
+        }
+    } else {
+        raise_status(status, kStatIterLimit);
+    }
+    if (capped) raise_status(status, kStatIterLimit);
+    xo[3 * i] = x.x; xo[3 * i + 1] = x.y; xo[3 * i + 2] = x.z;
+    dout[3 * i] = d.x; dout[3 * i + 1] = d.y; dout[3 * i + 2] = d.z;
+    wlo[3 * i] = wl.x; wlo[3 * i + 1] = wl.y; wlo[3 * i + 2] = wl.z;
+    label[i] = (float)mu;
+    npaths[i] = j;
+}
+
+RenderArgs make_args(const rpnn_render_desc& rd) {
+    RenderArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.cam_pos[k] = rd.cam_pos[k]; a.cam_fwd[k] = rd.cam_fwd[k];
+        a.cam_right[k] = rd.cam_right[k]; a.cam_up[k] = rd.cam_up[k];
+        a.wl[k] = rd.light_dir[k];
+    }
+    a.tan_half = rd.tan_half_fov_y;
+    a.aspect = (float)rd.width / (float)rd.height;
+    a.W = rd.width; a.H = rd.height; a.spp = rd.spp;
+    a.seed = rd.seed;
+    a.E = rd.light_E;
+    a.mode = rd.mode;
+    return a;
+}
+
+}  // namespace
+
+rpnn_status launch_primary(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd,
+                           float* sample_val, float* qx, float* qd, uint32_t* qps, int* qcount,
+                           int* hit, float* xo, float* dout, float* Ld, cudaStream_t s) {
+    const int64_t P = (int64_t)rd.width * rd.height * rd.spp;
+    const int64_t blocks = (P + 127) / 128;
+    k_primary<<<(unsigned)blocks, 128, 0, s>>>(vv, make_args(rd), P, sample_val, qx, qd, qps, qcount,
+                                               hit, xo, dout, Ld, c.status.as<uint32_t>());
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float alpha,
+                                     const float* g, const uint32_t* qps, const int* qcount,
+                                     float* sample_val, float* image, bool with_g, cudaStream_t s) {
+    const int64_t npix = (int64_t)rd.width * rd.height;
+    if (with_g) {
+        k_scatter<<<c.num_sms * 8, 256, 0, s>>>(g, qps, qcount, alpha * rd.light_E, sample_val);
+        RPNN_CHECK_LAUNCH();
+    }
+    int64_t b = (npix + 255) / 256;
+    if (b > c.num_sms * 16) b = c.num_sms * 16;
+    k_composite<<<(unsigned)b, 256, 0, s>>>(sample_val, npix, rd.spp, image);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n, uint64_t seed,
+                           float rel_ci, int n_min, int n_max, float* x, float* d, float* wl,
+                           float* label, int* npaths, cudaStream_t s) {
+    const int64_t blocks = (n + 127) / 128;
+    k_records<<<(unsigned)blocks, 128, 0, s>>>(vv, first, n, seed, rel_ci, n_min, n_max, x, d, wl,
+                                               label, npaths, c.status.as<uint32_t>());
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+}  // namespace rpnn

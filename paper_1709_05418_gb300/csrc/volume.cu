@@ -1,0 +1,303 @@
+// volume.cu -- per-volume preprocessing: statistics (Sec. 4.2 mean-free-path
+// normalisation) and the Gaussian mip pyramid (Sec. 6, sigma_i = 2^i fine voxels),
+// stored as corner-packed records for the descriptor gather.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rpnn {
+
+namespace {
+
+struct DevStats {
+    unsigned int max_bits;      // max voxel (non-negative floats order like uint)
+    unsigned int bad;           // negative / NaN / Inf seen
+    unsigned long long count;   // voxels > 0
+    unsigned long long isum;    // fixed-point sum
+    double mean, inv_mean;
+    float inv_mean_f;
+    int S;
+};
+
+__global__ void k_f16_to_f32(const __half* __restrict__ in, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __half2float(in[i]);
+}
+
+__global__ void k_stats_max(const float* __restrict__ v, int64_t n, DevStats* st) {
+    unsigned int mx = 0, bad = 0;
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        if (!(x >= 0.0f) || isinf(x)) { bad = 1; continue; }
+        mx = max(mx, __float_as_uint(x));
+        cnt += x > 0.0f;
+    }
+    for (int o = 16; o; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->max_bits, mx);
+        if (bad) atomicOr(&st->bad, 1u);
+        atomicAdd(&st->count, cnt);
+    }
+}
+
+// Fixed-point sum: each v > 0 truncated to an integer with S = 32 - e fraction bits,
+// where the majorant is below 2^e; the integer sum is exact (< 2^62 for 2^30 voxels)
+// and independent of order.
+__global__ void k_stats_sum(const float* __restrict__ v, int64_t n, DevStats* st) {
+    int e;
+    frexpf(__uint_as_float(st->max_bits), &e);
+    const int S = 32 - e;
+    unsigned long long s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        if (x > 0.0f) s += (unsigned long long)__double2ll_rz(ldexp((double)x, S));
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&st->isum, s);
+}
+
+__global__ void k_stats_final(DevStats* st) {
+    int e;
+    frexpf(__uint_as_float(st->max_bits), &e);
+    const int S = 32 - e;
+    st->S = S;
+    if (st->count == 0) { st->mean = 0.0; st->inv_mean = 0.0; st->inv_mean_f = 0.0f; return; }
+    const double sum = __ll2double_rn((long long)st->isum);
+    st->mean = __ddiv_rn(ldexp(sum, -S), (double)st->count);
+    st->inv_mean = __ddiv_rn(1.0, st->mean);
+    st->inv_mean_f = __double2float_rn(st->inv_mean);
+}
+
+// One separable pass of the Gaussian filter along `axis` with decimation: output index
+// j along the axis reads fine indices j*st + off + m, m = 0..T-1 (zero outside),
+// accumulated in ascending m as acc = acc + w*v (no contraction); the final pass
+// multiplies by `scale` (1/mean).
+__global__ void k_mip_pass(const float* __restrict__ in, float* __restrict__ out, int ix, int iy,
+                           int iz, int ox, int oy, int oz, int axis, int st, int off,
+                           const float* __restrict__ w, int T, float scale, int apply_scale) {
+    const int64_t total = (int64_t)ox * oy * oz;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(o % ox);
+        const int y = (int)((o / ox) % oy);
+        const int z = (int)(o / ((int64_t)ox * oy));
+        int j, n;
+        int64_t base, stride;
+        if (axis == 0) { j = x; n = ix; base = ((int64_t)z * iy + y) * ix; stride = 1; }
+        else if (axis == 1) { j = y; n = iy; base = (int64_t)z * iy * ix + x; stride = ix; }
+        else { j = z; n = iz; base = (int64_t)y * ix + x; stride = (int64_t)ix * iy; }
+        float acc = 0.0f;
+        const int t0 = j * st + off;
+        for (int m = 0; m < T; ++m) {
+            const int t = t0 + m;
+            if (t >= 0 && t < n) acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), __ldg(in + base + t * stride)));
+        }
+        out[o] = apply_scale ? __fmul_rn(acc, scale) : acc;
+    }
+}
+
+// Corner packing: record (rx, ry, rz) of a level with dims (ax, ay, az) describes cell
+// (rx-1, ry-1, rz-1) and holds its 8 corner values (index dx + 2 dy + 4 dz, zero outside).
+__global__ void k_pack(const float* __restrict__ lv, float4* __restrict__ rec, int ax, int ay, int az) {
+    const int rx_n = ax + 1, ry_n = ay + 1, rz_n = az + 1;
+    const int64_t total = (int64_t)rx_n * ry_n * rz_n;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int x0 = (int)(r % rx_n) - 1;
+        const int y0 = (int)((r / rx_n) % ry_n) - 1;
+        const int z0 = (int)(r / ((int64_t)rx_n * ry_n)) - 1;
+        float c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + (k & 1), y = y0 + ((k >> 1) & 1), z = z0 + (k >> 2);
+            const bool in = x >= 0 && y >= 0 && z >= 0 && x < ax && y < ay && z < az;
+            c[k] = in ? lv[((int64_t)z * ay + y) * ax + x] : 0.0f;
+        }
+        rec[2 * r] = make_float4(c[0], c[1], c[2], c[3]);
+        rec[2 * r + 1] = make_float4(c[4], c[5], c[6], c[7]);
+    }
+}
+
+float bits_to_float(unsigned int b) {
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+int grid_for(int64_t n, int block, int num_sms) {
+    int64_t g = (n + block - 1) / block;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Gaussian taps of level i: sigma = 2^i, offsets |d| <= 3 sigma, normalised (FP64,
+// rounded to FP32).
+std::vector<float> gauss_taps(int level, int* off) {
+    const double sigma = std::ldexp(1.0, level);
+    int T;
+    if (level == 0) { T = 7; *off = -3; }
+    else { T = 6 << level; *off = (1 << (level - 1)) - 3 * (1 << level); }
+    std::vector<double> w(T);
+    double sum = 0.0;
+    for (int m = 0; m < T; ++m) {
+        const double d = (level == 0) ? (double)(m - 3) : (double)m - 3.0 * sigma + 0.5;
+        w[m] = std::exp(-d * d / (2.0 * sigma * sigma));
+        sum += w[m];
+    }
+    std::vector<float> wf(T);
+    for (int m = 0; m < T; ++m) wf[m] = (float)(w[m] / sum);
+    return wf;
+}
+
+}  // namespace
+
+rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStream_t s) {
+    const int64_t n = (int64_t)v.n[0] * v.n[1] * v.n[2];
+    rpnn_status st = v.raw.reserve(n * sizeof(float));
+    if (st) return st;
+    if (dtype == RPNN_F32) {
+        RPNN_CUDA_TRY(cudaMemcpyAsync(v.raw.p, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_f16_to_f32<<<grid_for(n, 256, c.num_sms), 256, 0, s>>>((const __half*)src, v.raw.as<float>(), n);
+        RPNN_CHECK_LAUNCH();
+    }
+    return RPNN_OK;
+}
+
+rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
+    const int64_t n = (int64_t)v.n[0] * v.n[1] * v.n[2];
+    rpnn_status st = v.stats.reserve(sizeof(DevStats));
+    if (st) return st;
+    DevStats* ds = v.stats.as<DevStats>();
+    RPNN_CUDA_TRY(cudaMemsetAsync(ds, 0, sizeof(DevStats), s));
+    const int g = grid_for(n, 256, c.num_sms);
+    k_stats_max<<<g, 256, 0, s>>>(v.raw.as<float>(), n, ds);
+    RPNN_CHECK_LAUNCH();
+    k_stats_sum<<<g, 256, 0, s>>>(v.raw.as<float>(), n, ds);
+    RPNN_CHECK_LAUNCH();
+    k_stats_final<<<1, 1, 0, s>>>(ds);
+    RPNN_CHECK_LAUNCH();
+    DevStats h;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(&h, ds, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h.bad) { set_error("density has negative, NaN or Inf voxels"); return RPNN_ERR_NONFINITE; }
+    if (h.count == 0) { set_error("density grid has no voxel > 0"); return RPNN_ERR_ARG; }
+    rpnn_volume_info& I = v.info;
+    for (int a = 0; a < 3; ++a) I.n[a] = v.n[a];
+    const int nmax = std::max(v.n[0], std::max(v.n[1], v.n[2]));
+    int L = 1;
+    while (((nmax + (1 << (L - 1)) - 1) >> (L - 1)) > 1) ++L;
+    I.levels = v.levels = L;
+    for (int i = 0; i < 16; ++i)
+        for (int a = 0; a < 3; ++a) I.dims[i][a] = v.dims[i][a] = (v.n[a] + (1 << i) - 1) >> i;
+    I.mean = h.mean;
+    I.inv_mean_f = h.inv_mean_f;
+    I.majorant = bits_to_float(h.max_bits);
+    I.nonzero = (int64_t)h.count;
+    // mip level read by stencil level k: largest power-of-two voxel not above the
+    // stencil spacing 0.5 * 2^(k-1) mean free paths (exact frexp of an exact product)
+    for (int k = 0; k < RPNN_K; ++k) {
+        const double sk = 0.5 * std::ldexp((double)h.inv_mean_f, k) * (double)nmax;
+        int m = 0;
+        if (sk > 0.0) { int ex; std::frexp(sk, &ex); m = ex - 1; }
+        m = std::max(0, std::min(m, L - 1));
+        I.mip_of_level[k] = m;
+    }
+    return RPNN_OK;
+}
+
+rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s) {
+    if (level < 0 || level >= v.levels) { set_error("mip level %d out of range", level); return RPNN_ERR_ARG; }
+    int off = 0;
+    std::vector<float> w = gauss_taps(level, &off);
+    const int T = (int)w.size();
+    const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
+    const int ax = v.dims[level][0], ay = v.dims[level][1], az = v.dims[level][2];
+    float *dw = nullptr, *A = nullptr, *B = nullptr;
+    RPNN_CUDA_TRY(cudaMalloc(&dw, T * sizeof(float)));
+    RPNN_CUDA_TRY(cudaMalloc(&A, (size_t)ax * ny * nz * sizeof(float)));
+    RPNN_CUDA_TRY(cudaMalloc(&B, (size_t)ax * ay * nz * sizeof(float)));
+    RPNN_CUDA_TRY(cudaMemcpyAsync(dw, w.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
+    const int st = 1 << level;
+    const float scale = v.info.inv_mean_f;
+    k_mip_pass<<<grid_for((int64_t)ax * ny * nz, 256, c.num_sms), 256, 0, s>>>(
+        v.raw.as<float>(), A, nx, ny, nz, ax, ny, nz, 0, st, off, dw, T, scale, 0);
+    k_mip_pass<<<grid_for((int64_t)ax * ay * nz, 256, c.num_sms), 256, 0, s>>>(
+        A, B, ax, ny, nz, ax, ay, nz, 1, st, off, dw, T, scale, 0);
+    k_mip_pass<<<grid_for((int64_t)ax * ay * az, 256, c.num_sms), 256, 0, s>>>(
+        B, dst, ax, ay, nz, ax, ay, az, 2, st, off, dw, T, scale, 1);
+    RPNN_CHECK_LAUNCH();
+    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(dw); cudaFree(A); cudaFree(B);
+    return RPNN_OK;
+}
+
+rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s) {
+    int64_t total = 0;
+    bool need[kMaxLevels] = {};
+    for (int k = 0; k < RPNN_K; ++k) need[v.info.mip_of_level[k]] = true;
+    for (int i = 0; i < v.levels; ++i) {
+        v.level_packed[i] = need[i];
+        v.lvl[i].ax = v.dims[i][0]; v.lvl[i].ay = v.dims[i][1]; v.lvl[i].az = v.dims[i][2];
+        v.lvl[i].rec_offset = total;
+        if (need[i]) total += (int64_t)(v.dims[i][0] + 1) * (v.dims[i][1] + 1) * (v.dims[i][2] + 1);
+    }
+    rpnn_status st = v.packed.reserve(total * 2 * sizeof(float4));
+    if (st) return st;
+    float* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    for (int i = 0; i < v.levels; ++i) {
+        if (!need[i]) continue;
+        const size_t b = (size_t)v.dims[i][0] * v.dims[i][1] * v.dims[i][2] * sizeof(float);
+        if (b > tmp_bytes) {
+            if (tmp) cudaFree(tmp);
+            RPNN_CUDA_TRY(cudaMalloc(&tmp, b));
+            tmp_bytes = b;
+        }
+        st = volume_build_level(c, v, i, tmp, s);
+        if (st) { cudaFree(tmp); return st; }
+        const int64_t nrec = (int64_t)(v.dims[i][0] + 1) * (v.dims[i][1] + 1) * (v.dims[i][2] + 1);
+        k_pack<<<grid_for(nrec, 256, c.num_sms), 256, 0, s>>>(
+            tmp, v.packed.as<float4>() + 2 * v.lvl[i].rec_offset, v.dims[i][0], v.dims[i][1], v.dims[i][2]);
+        RPNN_CHECK_LAUNCH();
+    }
+    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tmp) cudaFree(tmp);
+    v.built = true;
+    return RPNN_OK;
+}
+
+VolumeView Volume::view() const {
+    VolumeView w{};
+    w.raw = raw.as<float>();
+    const int nmax = std::max(n[0], std::max(n[1], n[2]));
+    for (int a = 0; a < 3; ++a) {
+        w.n[a] = n[a];
+        w.ext[a] = (float)((double)n[a] / (double)nmax);
+    }
+    w.inv_h0 = (float)nmax;
+    w.majorant = info.majorant;
+    w.albedo = albedo;
+    w.g = g;
+    w.inv_mean_f = info.inv_mean_f;
+    for (int k = 0; k < RPNN_K; ++k) w.mip_of_level[k] = info.mip_of_level[k];
+    w.packed = packed.as<float4>();
+    for (int i = 0; i < kMaxLevels; ++i) w.lvl[i] = lvl[i];
+    return w;
+}
+
+}  // namespace rpnn

@@ -74,37 +74,76 @@ def gradient_noise(x, y, z, perm) -> np.ndarray:
                           _grad(perm[BB + 1], x - 1, y - 1, z - 1))))
 
 
+def _grad_t(h, x, y, z):
+    import torch
+    h = h & 15
+    u = torch.where(h < 8, x, y)
+    v = torch.where(h < 4, y, torch.where((h == 12) | (h == 14), x, z))
+    return torch.where((h & 1) != 0, -u, u) + torch.where((h & 2) != 0, -v, v)
+
+
+def _noise_t(x, y, z, perm):
+    """gradient_noise() on torch tensors (same construction, any device)."""
+    import torch
+    fx, fy, fz = torch.floor(x), torch.floor(y), torch.floor(z)
+    X, Y, Z = fx.long() & 255, fy.long() & 255, fz.long() & 255
+    x, y, z = x - fx, y - fy, z - fz
+    fade = lambda t: t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    u, v, w = fade(x), fade(y), fade(z)
+    A = perm[X] + Y
+    AA, AB = perm[A] + Z, perm[A + 1] + Z
+    B = perm[X + 1] + Y
+    BA, BB = perm[B] + Z, perm[B + 1] + Z
+    lerp = lambda t, a, b: a + t * (b - a)
+    return lerp(w,
+                lerp(v, lerp(u, _grad_t(perm[AA], x, y, z), _grad_t(perm[BA], x - 1, y, z)),
+                     lerp(u, _grad_t(perm[AB], x, y - 1, z), _grad_t(perm[BB], x - 1, y - 1, z))),
+                lerp(v, lerp(u, _grad_t(perm[AA + 1], x, y, z - 1), _grad_t(perm[BA + 1], x - 1, y, z - 1)),
+                     lerp(u, _grad_t(perm[AB + 1], x, y - 1, z - 1),
+                          _grad_t(perm[BB + 1], x - 1, y - 1, z - 1))))
+
+
 def fbm_cloud(n: int = 256, seed: int = 7, octaves: int = 6, coverage: float = 0.30,
-              peak: float = 50.0, base_freq: float = 4.0, shape=None) -> np.ndarray:
+              peak: float = 50.0, base_freq: float = 4.0, shape=None, device=None) -> np.ndarray:
     """Cumulus-like cloud: 6-octave fBm (lacunarity 2, gain 0.5) of gradient noise
     added to a spherical falloff, thresholded so that `coverage` of the voxels are
     non-zero, rescaled so the largest voxel equals `peak`.  shape=(nz, ny, nx)
-    allows non-cubic grids (the longest edge spans the unit box)."""
+    allows non-cubic grids (the longest edge spans the unit box).  Evaluated with
+    torch in FP64 on `device` (default: CUDA when available, else CPU); returns a
+    float32 numpy array."""
+    import torch
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
     nz, ny, nx = shape if shape is not None else (n, n, n)
     m = max(nx, ny, nz)
-    perm = _perm(seed)
+    perm = torch.as_tensor(_perm(seed), device=device)
     off = np.random.default_rng(seed + 1).uniform(0, 64, size=3)
-    tx = (np.arange(nx) + 0.5) / m
-    ty = (np.arange(ny) + 0.5) / m
-    out = np.empty((nz, ny, nx), np.float32)
-    cx, cy = 0.5 * nx / m, 0.5 * ny / m
-    cz = 0.5 * nz / m
-    Y, X = np.meshgrid(ty, tx, indexing="ij")
-    for k in range(nz):
-        tz = (k + 0.5) / m
-        f = np.zeros_like(X)
+    f64 = dict(dtype=torch.float64, device=device)
+    tx = (torch.arange(nx, **f64) + 0.5) / m
+    ty = (torch.arange(ny, **f64) + 0.5) / m
+    cx, cy, cz = 0.5 * nx / m, 0.5 * ny / m, 0.5 * nz / m
+    Y, X = torch.meshgrid(ty, tx, indexing="ij")
+    out = torch.empty((nz, ny, nx), **f64)
+    slab = max(1, (1 << 22) // (nx * ny))
+    for k0 in range(0, nz, slab):
+        k1 = min(nz, k0 + slab)
+        tz = ((torch.arange(k0, k1, **f64) + 0.5) / m)[:, None, None]
+        Xs, Ys = X[None].expand(k1 - k0, -1, -1), Y[None].expand(k1 - k0, -1, -1)
+        Zs = tz.expand_as(Xs)
+        f = torch.zeros_like(Xs)
         amp, freq = 1.0, base_freq
         for _ in range(octaves):
-            f += amp * gradient_noise(X * freq + off[0], Y * freq + off[1],
-                                      np.full_like(X, tz * freq + off[2]), perm)
+            f += amp * _noise_t(Xs * freq + off[0], Ys * freq + off[1], Zs * freq + off[2], perm)
             amp *= 0.5
             freq *= 2.0
-        r = np.sqrt((X - cx) ** 2 + (Y - cy) ** 2 + (tz - cz) ** 2) / (0.45 * min(nx, ny, nz) / m)
-        out[k] = (0.7 * f + (1.0 - r * r)).astype(np.float32)
-    tau = np.quantile(out, 1.0 - coverage)
-    out = np.maximum(out - tau, 0.0)
-    out *= peak / out.max()
-    return out.astype(np.float32)
+        r = torch.sqrt((Xs - cx) ** 2 + (Ys - cy) ** 2 + (Zs - cz) ** 2) / (0.45 * min(nx, ny, nz) / m)
+        out[k0:k1] = 0.7 * f + (1.0 - r * r)
+    a = out.cpu().numpy().astype(np.float32)
+    kth = int(round((1.0 - coverage) * (a.size - 1)))
+    tau = np.partition(a.ravel(), kth)[kth]
+    a = np.maximum(a - tau, 0.0)
+    a *= peak / a.max()
+    return a.astype(np.float32)
 
 
 # --------------------------------------------------------------------------- scene

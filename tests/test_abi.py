@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/rpnn.h declares (no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "rpnn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rpnn_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1709_05418_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_named_entry_points():
+    names = declared()
+    for must in ("rpnn_load_volume", "rpnn_build_mips", "rpnn_set_weights", "rpnn_render",
+                 "rpnn_train_step"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (rpnn_[a-z_0-9]+)\b", out))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_resolves(libpath):
+    import torch  # noqa: F401  (shares the CUDA runtime with the library)
+    L = ctypes.CDLL(libpath)
+    for n in declared():
+        assert getattr(L, n)
+    L.rpnn_last_error.restype = ctypes.c_char_p
+    assert L.rpnn_last_error() == b""
+    # argument checks that need no device
+    L.rpnn_create.argtypes = [ctypes.c_void_p]
+    assert L.rpnn_create(None) == -1

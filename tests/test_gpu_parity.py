@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on the same
+seeded inputs.  Bit-exact where the arithmetic is defined to the last rounding
+(statistics, mip pyramid, descriptor densities); tolerance-based elsewhere."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_05418_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_REL = 1e-5      # FP32 network vs FP64 oracle, relative L2 over the batch
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_05418_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context()
+    yield c
+    c.close()
+
+
+def cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+@pytest.fixture(scope="module")
+def blob():
+    return W.blob_cloud(64, seed=1)
+
+
+@pytest.fixture(scope="module")
+def blob_vol(ctx, blob):
+    v = ctx.load_volume(cuda(blob))
+    ctx.build_mips(v)
+    return v
+
+
+@pytest.fixture(scope="module")
+def blob_orc(blob):
+    return oracle.Volume(blob)
+
+
+@pytest.fixture(scope="module")
+def params():
+    return W.he_init(seed=2)
+
+
+# ---------------------------------------------------------------- volume
+@pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9)])
+def test_stats_and_mips_bit_exact(ctx, shape, seed):
+    dens = W.fbm_cloud(shape=shape, seed=seed, coverage=0.35) if seed != 1 else W.blob_cloud(64, seed=1)
+    v = ctx.load_volume(cuda(dens))
+    ctx.build_mips(v)
+    gi = ctx.get_volume_info(v)
+    o = oracle.Volume(dens)
+    oi = o.stats()
+    assert gi["mean"] == oi["mean"]
+    assert np.float32(gi["inv_mean_f"]) == np.float32(oi["inv_mean_f"])
+    assert gi["majorant"] == oi["majorant"]
+    assert gi["nonzero"] == oi["nonzero"]
+    assert gi["levels"] == oi["levels"]
+    assert gi["mip_of_level"] == oi["mip_of_level"]
+    assert [tuple(d) for d in gi["dims"]] == oi["dims"]
+    for lv in sorted(set(oi["mip_of_level"]) | {0, oi["levels"] - 1}):
+        g = ctx.copy_mip_level(v, lv).cpu().numpy()
+        r = o.mip_level(lv, f32=True)
+        assert g.shape == r.shape
+        assert np.array_equal(g.view(np.uint32), r.view(np.uint32)), f"level {lv}"
+        r64 = o.mip_level(lv)
+        assert np.abs(g - r64).max() <= 2e-6 * max(1.0, np.abs(r64).max())
+
+
+def test_volume_rejects_bad_input(ctx, api):
+    d = np.ones((8, 8, 8), np.float32)
+    d[3, 3, 3] = -1.0
+    v = ctx.load_volume(cuda(d))
+    with pytest.raises(api.RPNNError) as e:
+        ctx.build_mips(v)
+    assert e.value.code == -6
+    v = ctx.load_volume(cuda(np.zeros((4, 4, 4), np.float32)))
+    with pytest.raises(api.RPNNError) as e:
+        ctx.build_mips(v)
+    assert e.value.code == -1
+
+
+# ---------------------------------------------------------------- descriptor
+@pytest.mark.parametrize("q", [1, 37, 1031])
+def test_descriptor_bit_exact(ctx, blob_vol, blob_orc, q):
+    x, d = W.random_queries((64, 64, 64), q, seed=100 + q)
+    rng = np.random.default_rng(q)
+    wl = rng.normal(size=(q, 3))
+    wl /= np.linalg.norm(wl, axis=1, keepdims=True)
+    x32, d32, wl32 = x.astype(np.float32), d.astype(np.float32), wl.astype(np.float32)
+    # per-query light directions
+    g = ctx.extract_descriptors(blob_vol, cuda(x32), cuda(d32), cuda(wl32)).cpu().numpy()
+    ref = np.stack([blob_orc.descriptor(x32[i:i + 1], d32[i:i + 1], wl32[i], f32=True)[0]
+                    for i in range(q)])
+    assert g.shape == (q, 10, 240)
+    assert np.array_equal(g[:, :, :225].view(np.uint32), ref[:, :, :225].view(np.uint32))
+    assert np.abs(g[:, :, 225] - ref[:, :, 225]).max() <= 4e-7          # acosf, few ulp
+    assert np.all(g[:, :, 226:] == 0)
+    ref64 = np.stack([blob_orc.descriptor(x32[i:i + 1].astype(np.float64), d32[i:i + 1].astype(np.float64),
+                                          wl32[i].astype(np.float64))[0] for i in range(q)])
+    assert np.abs(g[:, :, :226] - ref64).max() <= 2e-5 * max(1.0, np.abs(ref64).max())
+    # bf16 output is the RNE rounding of the same FP32 values
+    gb = ctx.extract_descriptors(blob_vol, cuda(x32), cuda(d32), cuda(wl32), dtype=torch.bfloat16)
+    rb = torch.from_numpy(ref[:, :, :225].copy()).to(torch.bfloat16)
+    assert torch.equal(gb[:, :, :225].cpu(), rb)
+
+
+def test_descriptor_shared_light_and_degenerate_frame(ctx, blob_vol, blob_orc):
+    x, d = W.random_queries((64, 64, 64), 64, seed=7)
+    wl = np.array([0.0, 0.6, 0.8], np.float32)
+    d[0] = -wl          # omega parallel to the light: degenerate frame
+    d[1] = wl           # anti-parallel
+    x32, d32 = x.astype(np.float32), d.astype(np.float32)
+    g = ctx.extract_descriptors(blob_vol, cuda(x32), cuda(d32), cuda(wl)).cpu().numpy()
+    ref = blob_orc.descriptor(x32, d32, wl, f32=True)
+    assert np.array_equal(g[:, :, :225].view(np.uint32), ref[:, :, :225].view(np.uint32))
+
+
+# ---------------------------------------------------------------- network
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.fixture(scope="module")
+def zbatch(blob_orc):
+    x, d = W.random_queries((64, 64, 64), 333, seed=11, margin=0.2)
+    wl = np.array([0.3, 0.5, -0.8])
+    wl /= np.linalg.norm(wl)
+    z = blob_orc.descriptor(x.astype(np.float32), d.astype(np.float32), wl.astype(np.float32), f32=True)
+    zp = np.zeros((z.shape[0], 10, 240), np.float32)
+    zp[:, :, :226] = z
+    return zp
+
+
+def test_mlp_forward_f32(ctx, api, params, zbatch):
+    ctx.set_weights(cuda(params))
+    g = ctx.mlp_forward(cuda(zbatch), precision=api.F32).cpu().numpy()
+    ref = oracle.mlp_forward(params.astype(np.float64), zbatch[:, :, :226].astype(np.float64))
+    assert (ref > 0).mean() > 0.2
+    assert _rel_l2(g, ref) <= F32_REL
+    assert np.all(np.abs(g - ref) <= 1e-4 * np.maximum(np.abs(ref), np.median(np.abs(ref))) + 1e-7)
+
+
+def test_mlp_backward_f32(ctx, params, zbatch):
+    ctx.set_weights(cuda(params))
+    rng = np.random.default_rng(3)
+    dout = rng.normal(size=zbatch.shape[0]).astype(np.float32)
+    dp = ctx.mlp_backward(cuda(zbatch), cuda(dout)).cpu().numpy()
+    ref = oracle.mlp_backward(params.astype(np.float64), zbatch[:, :, :226].astype(np.float64),
+                              dout.astype(np.float64))
+    parts_g, parts_r = W.split_params(dp), W.split_params(ref)
+    for name in parts_g:
+        rg, rr = parts_g[name].astype(np.float64), parts_r[name]
+        if np.linalg.norm(rr) == 0:
+            assert np.linalg.norm(rg) == 0, name
+        else:
+            assert _rel_l2(rg, rr) <= 1e-4, name
+
+
+def test_train_step_matches_oracle(ctx, params, zbatch):
+    ctx.set_weights(cuda(params))
+    rng = np.random.default_rng(4)
+    target = rng.uniform(0, 2, size=zbatch.shape[0]).astype(np.float32)
+    p = cuda(params)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    loss = ctx.train_step(cuda(zbatch), cuda(target), p, m, v, step=1, lr=1e-3)
+    z64 = zbatch[:, :, :226].astype(np.float64)
+    p64 = params.astype(np.float64)
+    g = oracle.mlp_forward(p64, z64)
+    l_ref, dg = oracle.logmse_loss(g, target.astype(np.float64))
+    assert abs(loss.item() - l_ref) <= 1e-5 * l_ref
+    grad = oracle.mlp_backward(p64, z64, dg)
+    pr, mr, vr = p64.copy(), np.zeros_like(p64), np.zeros_like(p64)
+    oracle.adam(pr, mr, vr, grad, 1, lr=1e-3)
+    pg = p.cpu().numpy().astype(np.float64)
+    moved = np.abs(pr - p64) > 1e-4          # entries the step clearly moved
+    assert moved.mean() > 0.1
+    assert np.abs((pg - p64)[moved] - (pr - p64)[moved]).max() <= 1e-4
+    ctx.set_weights(cuda(params))
+
+
+# ---------------------------------------------------------------- rendering
+@pytest.fixture(scope="module")
+def cam64(blob):
+    return W.camera(blob.shape, 64, 64, spp=1, seed=3, light_seed=4)
+
+
+def test_primary_samples_match(ctx, blob_vol, blob_orc, cam64):
+    hit, x, d, Ld = [t.cpu().numpy() for t in ctx.trace_primary(blob_vol, cam64)]
+    P = hit.size
+    agree = 0
+    close = 0
+    nhit = 0
+    for ps in range(P):
+        h, xo, do, Lo = blob_orc.primary(cam64, ps, 0)
+        if (h == 1) == (hit[ps] == 1):
+            agree += 1
+            if h == 1:
+                nhit += 1
+                if (np.abs(x[ps] - xo).max() < 1e-4 and np.abs(d[ps] - do).max() < 1e-5 and
+                        abs(Ld[ps] - Lo) <= 1e-3 * max(Lo, 1e-3)):
+                    close += 1
+    assert nhit > 0.3 * P
+    assert agree >= 0.995 * P
+    assert close >= 0.98 * nhit
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_render_matches_oracle(ctx, api, blob_vol, blob_orc, cam64, params, mode):
+    ctx.set_weights(cuda(params))
+    img, nq = ctx.render(blob_vol, cam64, precision=api.F32, mode=mode, want_count=True)
+    ctx.sync_status()
+    got = img.cpu().numpy().ravel().astype(np.float64)
+    ref = blob_orc.render_pixels(cam64, np.arange(got.size),
+                                 params=params.astype(np.float64) if mode == 0 else None, mode=0)
+    tol = 1e-3 * np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max()) + 1e-7
+    frac = (np.abs(got - ref) <= tol).mean()
+    assert frac >= 0.98, frac
+    if mode == 0:
+        assert nq > 0.3 * got.size
+
+
+def test_render_multi_spp_and_ragged_image(ctx, api, blob_vol, blob_orc, params):
+    cam = W.camera((64, 64, 64), 37, 23, spp=3, seed=5, light_seed=6)
+    ctx.set_weights(cuda(params))
+    got = ctx.render(blob_vol, cam, precision=api.F32).cpu().numpy().ravel().astype(np.float64)
+    ref = blob_orc.render_pixels(cam, np.arange(got.size), params=params.astype(np.float64))
+    tol = 1e-3 * np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max()) + 1e-7
+    assert (np.abs(got - ref) <= tol).mean() >= 0.97
+
+
+def test_render_errors(ctx, api, blob_vol, cam64):
+    bad = dict(cam64)
+    bad["light_dir"] = np.array([1.0, 1.0, 0.0])
+    with pytest.raises(api.RPNNError):
+        ctx.render(blob_vol, bad)
+    with pytest.raises(api.RPNNError):
+        ctx.render(12345, cam64)
+
+
+# ---------------------------------------------------------------- records
+def test_records_match_oracle(ctx, blob_vol, blob_orc):
+    n = 48
+    x, d, wl, lab, npaths = [t.cpu().numpy() for t in
+                             ctx.gen_records(blob_vol, 0, n, 77, rel_ci=0.1, n_min=32, n_max=2048)]
+    ctx.sync_status()
+    ok_geo, ok_lab = 0, 0
+    for i in range(n):
+        r = blob_orc.gen_record(77, i, rel_ci=0.1, n_min=32, n_max=2048)
+        if np.abs(x[i] - r["x"]).max() < 1e-4 and np.abs(d[i] - r["d"]).max() < 1e-5:
+            ok_geo += 1
+        assert np.abs(wl[i] - r["wl"]).max() < 1e-5
+        hw = max(r["half_width"], 1e-6) if math.isfinite(r["half_width"]) else r["label"]
+        if abs(lab[i] - r["label"]) <= 3 * hw + 1e-6:
+            ok_lab += 1
+    assert ok_geo >= 0.95 * n
+    assert ok_lab >= 0.9 * n
+    assert np.all(npaths >= 32) and np.all(npaths <= 2048)
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.mark.slow
+def test_full_size_render_sampled_pixels(ctx, api, params):
+    dens = W.fbm_cloud(256, seed=7)
+    cam = W.camera(dens.shape, 512, 512, spp=1, seed=3, light_seed=4)
+    v = ctx.load_volume(cuda(dens))
+    ctx.build_mips(v)
+    ctx.set_weights(cuda(params))
+    img, nq = ctx.render(v, cam, precision=api.F32, want_count=True)
+    ctx.sync_status()
+    assert nq > 100000
+    got = img.cpu().numpy().ravel().astype(np.float64)
+    pix = np.random.default_rng(8).choice(got.size, 96, replace=False)
+    ref = oracle.Volume(dens).render_pixels(cam, pix, params=params.astype(np.float64))
+    tol = 1e-3 * np.maximum(np.abs(ref), 1e-3 * np.abs(got).max()) + 1e-7
+    assert (np.abs(got[pix] - ref) <= tol).mean() >= 0.95
