@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--cpu-pixels", type=int, default=2048)
     ap.add_argument("--ref-pixels", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="one BF16 and one FP32 render of the workload, no timing (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -216,6 +218,13 @@ def main():
     ctx.build_mips(vol)
     ctx.set_weights(torch.from_numpy(params).to(dev))
     info = ctx.get_volume_info(vol)
+    if args.profile_only:
+        for p in (api.BF16, api.F32):
+            ctx.render(vol, cam, precision=p)
+        ctx.sync_status()
+        torch.cuda.synchronize()
+        ctx.close()
+        return
 
     def timed(prec, steps, warmup):
         img = torch.empty((512, 512), dtype=torch.float32, device=dev)

@@ -49,7 +49,8 @@ enum {
     RPNN_ERR_ITER_LIMIT = -5,   /* a device loop hit its iteration cap (result truncated) */
     RPNN_ERR_NONFINITE = -6,    /* NaN/Inf met in data the call validates */
     RPNN_ERR_STATE = -7,        /* call order violated (e.g. render before set_weights) */
-    RPNN_ERR_UNSUPPORTED = -8   /* combination not built for this device */
+    RPNN_ERR_UNSUPPORTED = -8,  /* combination not built for this device */
+    RPNN_ERR_TIMEOUT = -9       /* a bounded device-side wait gave up (results invalid) */
 };
 
 enum { RPNN_F32 = 0, RPNN_F16 = 1, RPNN_BF16 = 2 };
@@ -69,7 +70,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx);
 /* Message of the calling thread's last error ("" if none).  Valid until the next call. */
 const char* rpnn_last_error(void);
 /* Reads (and clears) the context's device status word; synchronises `stream`.
- * Returns RPNN_OK, RPNN_ERR_ITER_LIMIT or RPNN_ERR_NONFINITE. */
+ * Returns RPNN_OK, RPNN_ERR_ITER_LIMIT, RPNN_ERR_NONFINITE or RPNN_ERR_TIMEOUT. */
 rpnn_status rpnn_sync_status(rpnn_ctx* ctx, void* stream);
 
 /* ---- volume (Sec. 4.2 mean-free-path normalisation; Sec. 5 unit box) ---------------- */

@@ -21,7 +21,8 @@ K, S, DIN, DESC_STRIDE, H, NPARAMS = 10, 225, 226, 240, 200, 1296601
 F32, F16, BF16 = 0, 1, 2
 MODE_RPNN, MODE_SINGLE, MODE_PATH = 0, 1, 2
 ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_HANDLE", -3: "ERR_CUDA", -4: "ERR_OOM",
-             -5: "ERR_ITER_LIMIT", -6: "ERR_NONFINITE", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED"}
+             -5: "ERR_ITER_LIMIT", -6: "ERR_NONFINITE", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED",
+             -9: "ERR_TIMEOUT"}
 
 
 class RPNNError(RuntimeError):

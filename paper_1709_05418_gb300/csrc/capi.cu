@@ -106,6 +106,7 @@ rpnn_status rpnn_sync_status(rpnn_ctx* ctx, void* stream) {
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
     if (h & kStatIterLimit) { set_error("a device loop reached its iteration cap"); return RPNN_ERR_ITER_LIMIT; }
     if (h & kStatNonFinite) { set_error("non-finite value met on the device"); return RPNN_ERR_NONFINITE; }
+    if (h & kStatTimeout) { set_error("a tensor-core pipeline wait timed out; its results are invalid"); return RPNN_ERR_TIMEOUT; }
     return RPNN_OK;
 }
 

@@ -13,7 +13,7 @@ namespace rpnn {
 constexpr int kMaxLevels = 16;
 
 // status bits written by kernels into the context's device status word
-enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u };
+enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u, kStatTimeout = 8u };
 
 void set_error(const char* fmt, ...);
 

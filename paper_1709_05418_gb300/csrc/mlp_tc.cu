@@ -1,20 +1,401 @@
-// mlp_tc.cu -- BF16 tensor-core (tcgen05) form of the RPNN forward.
+// mlp_tc.cu -- BF16 tensor-core (tcgen05) form of the RPNN forward (Sec. 4.3, Fig. 6).
+//
+// One persistent kernel runs all 22 matrix layers of the network for 128-query tiles:
+//   block k:  F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)      (K = 240 + 208)
+//             o^k = relu(F1 W2^T + b2 + o^{k-1})                   (K = 208)
+//   standard: o11 = relu(o10 T1^T + bT1), o12 = relu(o11 T2^T + bT2)
+//   output:   g = relu(T3 . o12 + bT3)  (CUDA cores, in the last epilogue)
+// Widths are padded to N = 208 (zero rows) and the descriptor level to K = 240.
+//
+// Roles (192 threads): warp 0 streams weights (1-D bulk copies of a pre-arranged BF16
+// image through a 4-stage ring) and descriptor tiles (2-D TMA boxes); warp 1 allocates
+// tensor memory and one lane issues tcgen05.mma into two alternating FP32 accumulators
+// (so the z-part of a block's first layer overlaps the previous epilogue); warps 2-5
+// are the epilogue: tensor memory -> registers, bias / residual / ReLU, BF16 operands
+// written back to shared memory for the next layer.
+//
+// Operand layout in shared memory (K-major, no swizzle): element (row, k) at
+// (k/8) * rows * 16 + row * 16 + (k%8) * 2, i.e. 8-row x 16-byte core matrices
+// contiguous, LBO = rows * 16 (next core matrix along K), SBO = 128 (next 8 rows).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace rpnn {
 
+namespace {
+
+constexpr int TM = 128;                 // query rows per tile
+constexpr int NP = 208;                 // padded layer width
+constexpr int NLAYERS = 22;             // tensor-core layers
+constexpr int KG_Z = 30;                // 240 / 8 descriptor k-groups per level
+constexpr int KG_H = 26;                // 208 / 8 hidden k-groups
+constexpr int CHUNK_KG = 4;             // k-groups per weight stage
+constexpr int STAGES = 4;
+constexpr uint32_t KG_BYTES_A = TM * 16;          // 2048
+constexpr uint32_t KG_BYTES_B = NP * 16;          // 3328
+constexpr uint32_t STAGE_BYTES = CHUNK_KG * KG_BYTES_B;   // 13312
+constexpr uint32_t OFF_RING = 0;
+constexpr uint32_t OFF_Z = OFF_RING + STAGES * STAGE_BYTES;   // 53248
+constexpr uint32_t OFF_O = OFF_Z + KG_Z * KG_BYTES_A;         // 114688
+constexpr uint32_t OFF_F = OFF_O + KG_H * KG_BYTES_A;         // 167936
+constexpr uint32_t OFF_BAR = OFF_F + KG_H * KG_BYTES_A;       // 221184
+constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
+constexpr int NTHREADS = 192;
+
+// barrier slots (8 bytes each) from OFF_BAR
+enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ZFULL = 2 * STAGES, B_ZEMPTY, B_ACC, B_ACT, B_COUNT };
+constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + 8 * B_COUNT;
+constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
+
+struct TcArgs {
+    const __nv_bfloat16* img;   // weight image
+    const float* bias;          // [NLAYERS][NP]
+    const float* w3;            // [NP] output layer weights (zero padded), bias in [NP-1]
+    int64_t img_off[NLAYERS];   // element offset of each layer's image
+    int64_t q_host;
+    const int* q_dev;
+    float* out;
+    uint32_t* status;
+};
+
+__host__ __device__ constexpr int layer_kg(int l) {
+    return l == 0 ? KG_Z : (l < 20 ? ((l & 1) ? KG_H : KG_Z + KG_H) : KG_H);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = tc::smem_u32(sm);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_ABORT);
+    auto bar = [&](int i) { return base + OFF_BAR + 8u * (uint32_t)i; };
+    const int64_t Q = a.q_dev ? (int64_t)*a.q_dev : a.q_host;
+    const int ntiles = (int)((Q + TM - 1) / TM);
+
+    if (tid == 0) {
+        *abort_flag = (base & 1023u) ? 1 : 0;
+        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
+        tc::mbar_init(bar(B_ZFULL), 1);
+        tc::mbar_init(bar(B_ZEMPTY), 1);
+        tc::mbar_init(bar(B_ACC), 1);
+        tc::mbar_init(bar(B_ACT), 4 * 32);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(base + OFF_TMEM_SLOT, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + OFF_TMEM_SLOT);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0 && !*abort_flag) {
+            uint32_t fills[STAGES] = {0, 0, 0, 0};
+            uint32_t zfills = 0;
+            int s = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                for (int l = 0; l < NLAYERS && !*abort_flag; ++l) {
+                    if (l < 20 && !(l & 1)) {          // descriptor level of block l/2
+                        if (!tc::mbar_wait(bar(B_ZEMPTY), (zfills & 1u) ^ 1u, abort_flag)) break;
+                        tc::mbar_expect_tx(bar(B_ZFULL), KG_Z * KG_BYTES_A);
+                        for (int g = 0; g < KG_Z; ++g)
+                            tc::tma_load_2d(base + OFF_Z + g * KG_BYTES_A, &zmap, (l / 2) * 240 + 8 * g, t * TM,
+                                            bar(B_ZFULL));
+                        ++zfills;
+                    }
+                    const int kg = layer_kg(l);
+                    for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
+                        const int n = min(CHUNK_KG, kg - g0);
+                        if (!tc::mbar_wait(bar(B_WEMPTY + s), (fills[s] & 1u) ^ 1u, abort_flag)) break;
+                        tc::mbar_expect_tx(bar(B_WFULL + s), n * KG_BYTES_B);
+                        tc::bulk_g2s(base + OFF_RING + s * STAGE_BYTES, a.img + a.img_off[l] + (int64_t)g0 * NP * 8,
+                                     n * KG_BYTES_B, bar(B_WFULL + s));
+                        ++fills[s];
+                        s = (s + 1) % STAGES;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0 && !*abort_flag) {
+            const uint32_t idesc = tc::idesc_bf16(TM, NP);
+            uint32_t uses[STAGES] = {0, 0, 0, 0};
+            uint32_t zuses = 0;
+            uint32_t n = 0;     // layer instance
+            int s = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int l = 0; l < NLAYERS && ok; ++l, ++n) {
+                    const uint32_t acc = tmem + (n & 1u) * 256u;
+                    const bool l1 = l < 20 && !(l & 1);
+                    const int kg = layer_kg(l);
+                    // first k-group that reads an operand written by the previous epilogue
+                    const int dep_from = l == 0 ? kg : (l1 ? KG_Z : 0);
+                    if (l1) ok = tc::mbar_wait(bar(B_ZFULL), zuses & 1u, abort_flag);
+                    bool dep_done = false;
+                    for (int g0 = 0; g0 < kg && ok; g0 += CHUNK_KG) {
+                        const int cnt = min(CHUNK_KG, kg - g0);
+                        ok = tc::mbar_wait(bar(B_WFULL + s), uses[s] & 1u, abort_flag);
+                        if (!ok) break;
+                        tc::tc_fence_after();
+                        for (int j = 0; j < cnt; j += 2) {
+                            const int g = g0 + j;
+                            if (!dep_done && g >= dep_from) {
+                                if (n > 0) ok = tc::mbar_wait(bar(B_ACT), (n - 1) & 1u, abort_flag);
+                                if (!ok) break;
+                                tc::tc_fence_after();
+                                dep_done = true;
+                            }
+                            uint32_t a_addr;
+                            if (l1) a_addr = g < KG_Z ? base + OFF_Z + g * KG_BYTES_A : base + OFF_O + (g - KG_Z) * KG_BYTES_A;
+                            else if (l == 20) a_addr = base + OFF_O + g * KG_BYTES_A;
+                            else a_addr = base + OFF_F + g * KG_BYTES_A;
+                            const uint64_t ad = tc::smem_desc(a_addr, KG_BYTES_A, 128);
+                            const uint64_t bd = tc::smem_desc(base + OFF_RING + s * STAGE_BYTES + j * KG_BYTES_B, KG_BYTES_B, 128);
+                            tc::mma_bf16(acc, ad, bd, idesc, g > 0 ? 1u : 0u);
+                            if (l1 && g + 2 == KG_Z) tc::mma_commit(bar(B_ZEMPTY));
+                        }
+                        if (!ok) break;
+                        tc::mma_commit(bar(B_WEMPTY + s));
+                        ++uses[s];
+                        s = (s + 1) % STAGES;
+                    }
+                    if (!ok) break;
+                    // The first layer of a tile reads no epilogue output, but the issuer
+                    // must not run two phases of the act barrier ahead of the epilogue
+                    // (parity waits would alias): wait for the previous epilogue here.
+                    if (!dep_done && n > 0) {
+                        ok = tc::mbar_wait(bar(B_ACT), (n - 1) & 1u, abort_flag);
+                        if (!ok) break;
+                        tc::tc_fence_after();
+                    }
+                    if (l1) ++zuses;
+                    tc::mma_commit(bar(B_ACC));
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        uint32_t n = 0;
+        unsigned char* Osm = sm + OFF_O;
+        unsigned char* Fsm = sm + OFF_F;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            float dot = 0.0f;
+            bool ok = true;
+            for (int l = 0; l < NLAYERS; ++l, ++n) {
+                ok = tc::mbar_wait(bar(B_ACC), n & 1u, abort_flag);
+                if (!ok) break;
+                tc::tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u;
+                const float* bias = a.bias + l * NP;
+                const bool l1 = l < 20 && !(l & 1);
+                const bool l2 = l < 20 && (l & 1);
+                unsigned char* dst = (l1 || l == 20) ? Fsm : Osm;
+                for (int c0 = 0; c0 < NP; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + c0, v);
+                    const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 b = __ldg(b4 + q);
+                        v[4 * q] += b.x; v[4 * q + 1] += b.y; v[4 * q + 2] += b.z; v[4 * q + 3] += b.w;
+                    }
+                    uint4* d0 = reinterpret_cast<uint4*>(dst + (c0 / 8) * KG_BYTES_A + row * 16);
+                    uint4* d1 = reinterpret_cast<uint4*>(dst + (c0 / 8 + 1) * KG_BYTES_A + row * 16);
+                    if (l2 && l > 1) {
+                        const uint4 r0 = *d0, r1 = *d1;
+                        const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&r0);
+                        const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&r1);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 f0 = __bfloat1622float2(h0[q]), f1 = __bfloat1622float2(h1[q]);
+                            v[2 * q] += f0.x; v[2 * q + 1] += f0.y;
+                            v[8 + 2 * q] += f1.x; v[8 + 2 * q + 1] += f1.y;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = (c0 + i < RPNN_H) ? fmaxf(v[i], 0.0f) : 0.0f;
+                    if (l == 21) {
+                        const float4* w4 = reinterpret_cast<const float4*>(a.w3 + c0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 w = __ldg(w4 + q);
+                            dot = fmaf(v[4 * q], w.x, dot); dot = fmaf(v[4 * q + 1], w.y, dot);
+                            dot = fmaf(v[4 * q + 2], w.z, dot); dot = fmaf(v[4 * q + 3], w.w, dot);
+                        }
+                    } else {
+                        uint4 p0, p1;
+                        __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
+                        __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            q0[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                            q1[q] = __floats2bfloat162_rn(v[8 + 2 * q], v[8 + 2 * q + 1]);
+                        }
+                        *d0 = p0;
+                        *d1 = p1;
+                    }
+                }
+                if (l != 21) tc::fence_proxy_async_smem();
+                tc::tc_fence_before();
+                tc::mbar_arrive(bar(B_ACT));
+            }
+            if (!ok) break;
+            const int64_t r = (int64_t)t * TM + row;
+            if (r < Q) a.out[r] = fmaxf(dot + __ldg(a.w3 + NP - 1), 0.0f);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicOr(a.status, kStatTimeout);
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// BF16 weight image, FP32 bias table and output layer from the FP32 parameters.
+__global__ void k_build_image(const float* __restrict__ P, ParamLayout L, TcArgs a,
+                              __nv_bfloat16* __restrict__ img, float* __restrict__ bias,
+                              float* __restrict__ w3, int64_t total) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int l = NLAYERS - 1;
+        while (l > 0 && a.img_off[l] > e) --l;
+        const int64_t r = e - a.img_off[l];
+        const int kg = (int)(r / (NP * 8));
+        const int n = (int)((r / 8) % NP);
+        const int c = kg * 8 + (int)(r % 8);
+        float v = 0.0f;
+        if (n < RPNN_H) {
+            if (l < 20 && !(l & 1)) {
+                const int k = l / 2;
+                if (c < RPNN_DIN) v = P[L.V[k] + (int64_t)n * RPNN_DIN + c];
+                else if (c >= 240 && c < 240 + RPNN_H) v = P[L.W1[k] + (int64_t)n * RPNN_H + (c - 240)];
+            } else if (c < RPNN_H) {
+                const int64_t off = l < 20 ? L.W2[l / 2] : L.T[l - 20];
+                v = P[off + (int64_t)n * RPNN_H + c];
+            }
+        }
+        img[e] = __float2bfloat16_rn(v);
+    }
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid < NLAYERS * NP) {
+        const int l = (int)(tid / NP), n = (int)(tid % NP);
+        float v = 0.0f;
+        if (n < RPNN_H) {
+            if (l < 20) v = P[((l & 1) ? L.b2[l / 2] : L.b1[l / 2]) + n];
+            else v = P[L.bT[l - 20] + n];
+        }
+        bias[tid] = v;
+    }
+    // output layer weights, zero padded; the output bias rides in the last slot
+    if (tid < NP) w3[tid] = tid < RPNN_H ? P[L.T[2] + tid] : (tid == NP - 1 ? P[L.bT[2]] : 0.0f);
+}
+
+struct ImageLayout {
+    int64_t off[NLAYERS];
+    int64_t img_elems;
+    size_t bias_bytes_off, w3_bytes_off, total_bytes;
+};
+
+ImageLayout image_layout() {
+    ImageLayout I{};
+    int64_t o = 0;
+    for (int l = 0; l < NLAYERS; ++l) {
+        I.off[l] = o;
+        o += (int64_t)layer_kg(l) * NP * 8;
+    }
+    I.img_elems = o;
+    I.bias_bytes_off = ((size_t)o * 2 + 255) & ~(size_t)255;
+    I.w3_bytes_off = I.bias_bytes_off + (size_t)NLAYERS * NP * 4;
+    I.total_bytes = I.w3_bytes_off + NP * 4 + 256;
+    return I;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+}  // namespace
+
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s) {
-    (void)c; (void)s;
+    const ImageLayout I = image_layout();
+    rpnn_status st = c.wimg_bf16.reserve(I.total_bytes);
+    if (st) return st;
+    TcArgs a{};
+    for (int l = 0; l < NLAYERS; ++l) a.img_off[l] = I.off[l];
+    unsigned char* b = c.wimg_bf16.as<unsigned char>();
+    k_build_image<<<c.num_sms * 8, 256, 0, s>>>(c.params32.as<float>(), param_layout(), a,
+                                                 reinterpret_cast<__nv_bfloat16*>(b),
+                                                 reinterpret_cast<float*>(b + I.bias_bytes_off),
+                                                 reinterpret_cast<float*>(b + I.w3_bytes_off), I.img_elems);
+    RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }
 
 rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev, float* out,
                              cudaStream_t s) {
-    (void)c; (void)desc_bf16; (void)q; (void)q_dev; (void)out; (void)s;
-    set_error("the BF16 tensor-core network is not available in this build");
-    return RPNN_ERR_UNSUPPORTED;
+    if (q <= 0) return RPNN_OK;
+    if ((reinterpret_cast<uintptr_t>(desc_bf16) & 15u) != 0) {
+        set_error("descriptor rows must be 16-byte aligned");
+        return RPNN_ERR_ARG;
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) { set_error("cuTensorMapEncodeTiled is unavailable"); return RPNN_ERR_UNSUPPORTED; }
+    CUtensorMap zmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)RPNN_K * RPNN_DESC_STRIDE, (cuuint64_t)q};
+    const cuuint64_t strides[1] = {(cuuint64_t)RPNN_K * RPNN_DESC_STRIDE * 2};
+    const cuuint32_t box[2] = {8, TM};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&zmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(desc_bf16), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return RPNN_ERR_CUDA; }
+    const ImageLayout I = image_layout();
+    unsigned char* b = c.wimg_bf16.as<unsigned char>();
+    TcArgs a{};
+    a.img = reinterpret_cast<const __nv_bfloat16*>(b);
+    a.bias = reinterpret_cast<const float*>(b + I.bias_bytes_off);
+    a.w3 = reinterpret_cast<const float*>(b + I.w3_bytes_off);
+    for (int l = 0; l < NLAYERS; ++l) a.img_off[l] = I.off[l];
+    a.q_host = q;
+    a.q_dev = q_dev;
+    a.out = out;
+    a.status = c.status.as<uint32_t>();
+    static bool attr = false;
+    if (!attr) {
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        attr = true;
+    }
+    const int64_t ntiles = (q + TM - 1) / TM;
+    const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
+    k_rpnn_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
 }
 
 }  // namespace rpnn

@@ -223,13 +223,20 @@ def param_count(**kw) -> int:
     return int(sum(int(np.prod(s)) for _, s, _ in param_shapes(**kw)))
 
 
-def he_init(seed: int = 2, bias: float = 0.0, **kw) -> np.ndarray:
-    """He-normal weights (std sqrt(2/fan_in)), constant biases, float32 flat."""
+def he_init(seed: int = 2, bias: float = 0.0, positive_head: bool = True, **kw) -> np.ndarray:
+    """He-normal weights (std sqrt(2/fan_in)), constant biases, float32 flat.  With
+    positive_head the output layer's weights are taken in absolute value, so the
+    (non-negative, ReLU) hidden state maps to a positive prediction instead of an
+    output ReLU that is dead for every input of a similar-looking batch."""
     rng = np.random.default_rng(seed)
     parts = []
-    for _, shp, fan in param_shapes(**kw):
+    shapes = param_shapes(**kw)
+    for i, (_, shp, fan) in enumerate(shapes):
         if fan:
-            parts.append(rng.normal(0.0, math.sqrt(2.0 / fan), size=shp).ravel())
+            w = rng.normal(0.0, math.sqrt(2.0 / fan), size=shp)
+            if positive_head and i == len(shapes) - 2:
+                w = np.abs(w)
+            parts.append(w.ravel())
         else:
             parts.append(np.full(shp, bias).ravel())
     return np.concatenate(parts).astype(np.float32)

@@ -155,6 +155,51 @@ def test_mlp_forward_f32(ctx, api, params, zbatch):
     assert np.all(np.abs(g - ref) <= 1e-4 * np.maximum(np.abs(ref), np.median(np.abs(ref))) + 1e-7)
 
 
+BF16_REL = 1e-2     # BF16 tensor-core network vs FP64 oracle, relative L2 over the batch
+
+
+@pytest.mark.parametrize("q", [333, 1, 129, 4101])
+def test_mlp_forward_bf16(ctx, api, params, zbatch, q):
+    ctx.set_weights(cuda(params))
+    reps = -(-q // zbatch.shape[0])
+    z = np.concatenate([zbatch] * reps)[:q]
+    g = ctx.mlp_forward(cuda(z, torch.bfloat16), precision=api.BF16).cpu().numpy().astype(np.float64)
+    ref = oracle.mlp_forward(params.astype(np.float64), z[:, :, :226].astype(np.float64))
+    ctx.sync_status()
+    assert np.all(np.isfinite(g))
+    assert _rel_l2(g, ref) <= BF16_REL, _rel_l2(g, ref)
+    scale = np.maximum(np.abs(ref), np.median(np.abs(ref)))
+    assert np.all(np.abs(g - ref) <= 3e-2 * scale)
+
+
+def test_mlp_forward_many_tiles_per_block(ctx, api, params, zbatch):
+    # more 128-row tiles than SMs: every persistent block runs several tiles in a row
+    ctx.set_weights(cuda(params))
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    q = nsm * 128 * 3 + 77
+    src = np.random.default_rng(5).integers(0, zbatch.shape[0], size=q)
+    z = zbatch[src]
+    ref = oracle.mlp_forward(params.astype(np.float64), zbatch[:, :, :226].astype(np.float64))[src]
+    gb = ctx.mlp_forward(cuda(z, torch.bfloat16), precision=api.BF16).cpu().numpy().astype(np.float64)
+    ctx.sync_status()
+    assert _rel_l2(gb, ref) <= BF16_REL
+    assert np.all(np.abs(gb - ref) <= 3e-2 * np.maximum(np.abs(ref), np.median(np.abs(ref))))
+    gf = ctx.mlp_forward(cuda(z), precision=api.F32).cpu().numpy().astype(np.float64)
+    assert _rel_l2(gf, ref) <= F32_REL
+
+
+def test_mlp_forward_bf16_random_inputs(ctx, api):
+    # inputs and weights unrelated to any cloud: every row and column of the tiles matters
+    rng = np.random.default_rng(21)
+    p = W.he_init(seed=22, bias=0.05)
+    z = np.zeros((700, 10, 240), np.float32)
+    z[:, :, :226] = rng.uniform(0, 2, size=(700, 10, 226))
+    ctx.set_weights(cuda(p))
+    g = ctx.mlp_forward(cuda(z, torch.bfloat16), precision=api.BF16).cpu().numpy().astype(np.float64)
+    ref = oracle.mlp_forward(p.astype(np.float64), z[:, :, :226].astype(np.float64))
+    assert _rel_l2(g, ref) <= BF16_REL, _rel_l2(g, ref)
+
+
 def test_mlp_backward_f32(ctx, params, zbatch):
     ctx.set_weights(cuda(params))
     rng = np.random.default_rng(3)
@@ -233,6 +278,17 @@ def test_render_matches_oracle(ctx, api, blob_vol, blob_orc, cam64, params, mode
     assert frac >= 0.98, frac
     if mode == 0:
         assert nq > 0.3 * got.size
+
+
+def test_render_bf16_matches_oracle(ctx, api, blob_vol, blob_orc, cam64, params):
+    ctx.set_weights(cuda(params))
+    img = ctx.render(blob_vol, cam64, precision=api.BF16)
+    ctx.sync_status()
+    got = img.cpu().numpy().ravel().astype(np.float64)
+    ref = blob_orc.render_pixels(cam64, np.arange(got.size), params=params.astype(np.float64))
+    assert _rel_l2(got, ref) <= BF16_REL
+    scale = np.maximum(np.abs(ref), np.median(np.abs(ref[ref > 0])))
+    assert (np.abs(got - ref) <= 3e-2 * scale).mean() >= 0.98
 
 
 def test_render_multi_spp_and_ragged_image(ctx, api, blob_vol, blob_orc, params):
