@@ -95,6 +95,10 @@ __device__ __forceinline__ float lookup(const VolumeView& v, int m, const float 
     return lerp_rn(c0, c1, f[2]);
 }
 
+// Thread t < 250 of the block owns stencil column (ix, iy) = (t%25 % 5, t%25 / 5) of
+// level k = t / 25 and walks its 9 points along z, so the level set-up and the
+// (ox, oy) part of each coordinate are computed once per column; threads 250..255
+// write gamma and the zero padding.
 template <class OutT>
 __global__ void __launch_bounds__(256)
 k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __restrict__ ds,
@@ -102,10 +106,13 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
              const int* __restrict__ q_dev, OutT* __restrict__ out) {
     const int64_t q = q_dev ? (int64_t)*q_dev : q_host;
     const int t = threadIdx.x;
-    const int ix = t % 5, iy = (t / 5) % 5, iz = t / 25;
+    const int k = t / 25, col = t % 25;
+    const int ix = col % 5, iy = col / 5;
     const float ox = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)ix));
     const float oy = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iy));
-    const float oz = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iz));
+    const int m = k < RPNN_K ? v.mip_of_level[k] : 0;
+    const float s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
+    const float gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << (k < RPNN_K ? k : 0))), s);
     for (int64_t qi = blockIdx.x; qi < q; qi += gridDim.x) {
         const float x[3] = {__ldg(xs + 3 * qi), __ldg(xs + 3 * qi + 1), __ldg(xs + 3 * qi + 2)};
         const float d[3] = {__ldg(ds + 3 * qi), __ldg(ds + 3 * qi + 1), __ldg(ds + 3 * qi + 2)};
@@ -113,22 +120,27 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
         const float wl[3] = {__ldg(wp), __ldg(wp + 1), __ldg(wp + 2)};
         const Frame F = make_frame(d, wl);
         OutT* row = out + qi * (int64_t)(RPNN_K * RPNN_DESC_STRIDE);
-#pragma unroll 2
-        for (int k = 0; k < RPNN_K; ++k) {
-            if (t < RPNN_S) {
-                const int m = v.mip_of_level[k];
-                const float s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-                const float g = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), s);
-                float u[3];
+        if (k < RPNN_K) {
+            float P[3], C[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float A = __fmul_rn(g, F.ex[a]), B = __fmul_rn(g, F.ey[a]), C = __fmul_rn(g, F.ez[a]);
-                    const float U0 = __fsub_rn(__fmul_rn(x[a], s), 0.5f);
-                    u[a] = __fmaf_rn(oz, C, __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0)));
-                }
-                row[k * RPNN_DESC_STRIDE + t] = cvt_out<OutT>(lookup(v, m, u));
-            } else if (t < RPNN_DESC_STRIDE) {
-                row[k * RPNN_DESC_STRIDE + t] = cvt_out<OutT>(t == RPNN_S ? F.gamma : 0.0f);
+            for (int a = 0; a < 3; ++a) {
+                const float A = __fmul_rn(gk, F.ex[a]), B = __fmul_rn(gk, F.ey[a]);
+                C[a] = __fmul_rn(gk, F.ez[a]);
+                const float U0 = __fsub_rn(__fmul_rn(x[a], s), 0.5f);
+                P[a] = __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0));
+            }
+            OutT* dst = row + k * RPNN_DESC_STRIDE + col;
+#pragma unroll 3
+            for (int iz = 0; iz < 9; ++iz) {
+                const float oz = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iz));
+                const float u[3] = {__fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
+                                    __fmaf_rn(oz, C[2], P[2])};
+                dst[iz * 25] = cvt_out<OutT>(lookup(v, m, u));
+            }
+        } else {
+            for (int e = t - 250; e < RPNN_K * (RPNN_DESC_STRIDE - RPNN_S); e += 6) {
+                const int kk = e / (RPNN_DESC_STRIDE - RPNN_S), j = e % (RPNN_DESC_STRIDE - RPNN_S);
+                row[kk * RPNN_DESC_STRIDE + RPNN_S + j] = cvt_out<OutT>(j == 0 ? F.gamma : 0.0f);
             }
         }
     }

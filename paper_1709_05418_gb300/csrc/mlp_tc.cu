@@ -8,7 +8,8 @@
 // Widths are padded to N = 208 (zero rows) and the descriptor level to K = 240.
 //
 // Roles (192 threads): warp 0 streams weights (1-D bulk copies of a pre-arranged BF16
-// image through a 4-stage ring) and descriptor tiles (2-D TMA boxes); warp 1 allocates
+// image through a 5-stage ring; a stage of a block's first layer also carries the matching
+// descriptor k-groups as 2-D TMA boxes of 8 columns x 128 queries); warp 1 allocates
 // tensor memory and one lane issues tcgen05.mma into two alternating FP32 accumulators
 // (so the z-part of a block's first layer overlaps the previous epilogue); warps 2-5
 // are the epilogue: tensor memory -> registers, bias / residual / ReLU, BF16 operands
@@ -35,20 +36,22 @@ constexpr int NLAYERS = 22;             // tensor-core layers
 constexpr int KG_Z = 30;                // 240 / 8 descriptor k-groups per level
 constexpr int KG_H = 26;                // 208 / 8 hidden k-groups
 constexpr int CHUNK_KG = 4;             // k-groups per weight stage
-constexpr int STAGES = 4;
+constexpr int STAGES = 5;
 constexpr uint32_t KG_BYTES_A = TM * 16;          // 2048
 constexpr uint32_t KG_BYTES_B = NP * 16;          // 3328
-constexpr uint32_t STAGE_BYTES = CHUNK_KG * KG_BYTES_B;   // 13312
-constexpr uint32_t OFF_RING = 0;
-constexpr uint32_t OFF_Z = OFF_RING + STAGES * STAGE_BYTES;   // 53248
-constexpr uint32_t OFF_O = OFF_Z + KG_Z * KG_BYTES_A;         // 114688
-constexpr uint32_t OFF_F = OFF_O + KG_H * KG_BYTES_A;         // 167936
-constexpr uint32_t OFF_BAR = OFF_F + KG_H * KG_BYTES_A;       // 221184
+// a ring stage holds up to 4 weight k-groups and, for the descriptor part of a block's
+// first layer, the matching 4 k-groups of the 128-query descriptor tile
+constexpr uint32_t STAGE_W = CHUNK_KG * KG_BYTES_B;           // 13312
+constexpr uint32_t STAGE_BYTES = STAGE_W + CHUNK_KG * KG_BYTES_A;   // 21504
+constexpr uint32_t OFF_O = 0;
+constexpr uint32_t OFF_F = OFF_O + KG_H * KG_BYTES_A;         // 53248
+constexpr uint32_t OFF_RING = OFF_F + KG_H * KG_BYTES_A;      // 106496
+constexpr uint32_t OFF_BAR = OFF_RING + STAGES * STAGE_BYTES; // 214016
 constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
 constexpr int NTHREADS = 192;
 
 // barrier slots (8 bytes each) from OFF_BAR
-enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ZFULL = 2 * STAGES, B_ZEMPTY, B_ACC, B_ACT, B_COUNT };
+enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_ACT, B_COUNT };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + 8 * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
 
@@ -80,8 +83,6 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     if (tid == 0) {
         *abort_flag = (base & 1023u) ? 1 : 0;
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
-        tc::mbar_init(bar(B_ZFULL), 1);
-        tc::mbar_init(bar(B_ZEMPTY), 1);
         tc::mbar_init(bar(B_ACC), 1);
         tc::mbar_init(bar(B_ACT), 4 * 32);
         tc::fence_mbar_init();
@@ -98,26 +99,22 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0 && !*abort_flag) {
-            uint32_t fills[STAGES] = {0, 0, 0, 0};
-            uint32_t zfills = 0;
+            uint32_t fills[STAGES] = {};
             int s = 0;
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS && !*abort_flag; ++l) {
-                    if (l < 20 && !(l & 1)) {          // descriptor level of block l/2
-                        if (!tc::mbar_wait(bar(B_ZEMPTY), (zfills & 1u) ^ 1u, abort_flag)) break;
-                        tc::mbar_expect_tx(bar(B_ZFULL), KG_Z * KG_BYTES_A);
-                        for (int g = 0; g < KG_Z; ++g)
-                            tc::tma_load_2d(base + OFF_Z + g * KG_BYTES_A, &zmap, (l / 2) * 240 + 8 * g, t * TM,
-                                            bar(B_ZFULL));
-                        ++zfills;
-                    }
+                    const bool l1 = l < 20 && !(l & 1);      // reads descriptor level l/2
                     const int kg = layer_kg(l);
                     for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
                         const int n = min(CHUNK_KG, kg - g0);
+                        const int nz = l1 ? max(0, min(g0 + n, KG_Z) - g0) : 0;
                         if (!tc::mbar_wait(bar(B_WEMPTY + s), (fills[s] & 1u) ^ 1u, abort_flag)) break;
-                        tc::mbar_expect_tx(bar(B_WFULL + s), n * KG_BYTES_B);
-                        tc::bulk_g2s(base + OFF_RING + s * STAGE_BYTES, a.img + a.img_off[l] + (int64_t)g0 * NP * 8,
-                                     n * KG_BYTES_B, bar(B_WFULL + s));
+                        const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
+                        tc::mbar_expect_tx(bar(B_WFULL + s), n * KG_BYTES_B + nz * KG_BYTES_A);
+                        tc::bulk_g2s(st, a.img + a.img_off[l] + (int64_t)g0 * NP * 8, n * KG_BYTES_B, bar(B_WFULL + s));
+                        for (int i = 0; i < nz; ++i)
+                            tc::tma_load_2d(st + STAGE_W + i * KG_BYTES_A, &zmap, (l / 2) * 240 + 8 * (g0 + i),
+                                            t * TM, bar(B_WFULL + s));
                         ++fills[s];
                         s = (s + 1) % STAGES;
                     }
@@ -128,8 +125,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0 && !*abort_flag) {
             const uint32_t idesc = tc::idesc_bf16(TM, NP);
-            uint32_t uses[STAGES] = {0, 0, 0, 0};
-            uint32_t zuses = 0;
+            uint32_t uses[STAGES] = {};
             uint32_t n = 0;     // layer instance
             int s = 0;
             bool ok = true;
@@ -140,7 +136,6 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     const int kg = layer_kg(l);
                     // first k-group that reads an operand written by the previous epilogue
                     const int dep_from = l == 0 ? kg : (l1 ? KG_Z : 0);
-                    if (l1) ok = tc::mbar_wait(bar(B_ZFULL), zuses & 1u, abort_flag);
                     bool dep_done = false;
                     for (int g0 = 0; g0 < kg && ok; g0 += CHUNK_KG) {
                         const int cnt = min(CHUNK_KG, kg - g0);
@@ -155,14 +150,14 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                                 tc::tc_fence_after();
                                 dep_done = true;
                             }
+                            const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
                             uint32_t a_addr;
-                            if (l1) a_addr = g < KG_Z ? base + OFF_Z + g * KG_BYTES_A : base + OFF_O + (g - KG_Z) * KG_BYTES_A;
+                            if (l1) a_addr = g < KG_Z ? st + STAGE_W + j * KG_BYTES_A : base + OFF_O + (g - KG_Z) * KG_BYTES_A;
                             else if (l == 20) a_addr = base + OFF_O + g * KG_BYTES_A;
                             else a_addr = base + OFF_F + g * KG_BYTES_A;
                             const uint64_t ad = tc::smem_desc(a_addr, KG_BYTES_A, 128);
-                            const uint64_t bd = tc::smem_desc(base + OFF_RING + s * STAGE_BYTES + j * KG_BYTES_B, KG_BYTES_B, 128);
+                            const uint64_t bd = tc::smem_desc(st + j * KG_BYTES_B, KG_BYTES_B, 128);
                             tc::mma_bf16(acc, ad, bd, idesc, g > 0 ? 1u : 0u);
-                            if (l1 && g + 2 == KG_Z) tc::mma_commit(bar(B_ZEMPTY));
                         }
                         if (!ok) break;
                         tc::mma_commit(bar(B_WEMPTY + s));
@@ -178,7 +173,6 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         if (!ok) break;
                         tc::tc_fence_after();
                     }
-                    if (l1) ++zuses;
                     tc::mma_commit(bar(B_ACC));
                 }
             }
