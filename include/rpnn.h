@@ -140,6 +140,30 @@ rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* de
 rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
                              int32_t precision, float* dev_out, void* stream);
 
+/* ---- FP32 network forward without device allocation ----------------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers that must not
+ * allocate device memory at call time: code running while another component captures the
+ * stream into a CUDA graph (an allocation there breaks or serialises the capture), hosts
+ * whose device memory is owned by a foreign allocator or a fixed budget, and real-time loops
+ * that forbid allocation after start-up.  It computes the same g = RPNN(z) as
+ * rpnn_mlp_forward with precision RPNN_F32 (same kernels, same order), for at most
+ * RPNN_STATIC_MAX_ROWS rows of FP32 descriptors, with the caller's FP32 parameter vector
+ * (layout above) and without a context.
+ *  - Scratch: one static device array of 3 * RPNN_STATIC_MAX_ROWS * 200 floats (9.8 MB),
+ *    present on every GPU that loads the library until the process exits.  It keeps the
+ *    last call's contents; nothing in it needs to start at zero (every layer writes its
+ *    output before the next reads it).
+ *  - All calls share that array: calls whose work overlaps on a GPU (two streams, two
+ *    threads) race and give wrong results.  Serialise them on one stream.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any
+ *    stream capture.
+ *  - Errors: RPNN_ERR_ARG for q > RPNN_STATIC_MAX_ROWS or null pointers, RPNN_ERR_CUDA when
+ *    the set-up lookup fails.  It calls no cudaMalloc, cudaFree or other allocating routine. */
+enum { RPNN_STATIC_MAX_ROWS = 4096 };
+rpnn_status rpnn_mlp_forward_f32_static(const float* dev_params, const float* dev_desc, int64_t q,
+                                        float* dev_out, void* stream);
+
 /* ---- rendering (Sec. 4.4) ---------------------------------------------------------------- */
 typedef struct {
     float cam_pos[3], cam_fwd[3], cam_right[3], cam_up[3]; /* pinhole frame (unit vectors) */

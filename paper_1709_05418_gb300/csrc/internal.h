@@ -124,6 +124,9 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
 rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
                              const float* dout, float* dparams, cudaStream_t s);
 size_t mlp_saved_floats_per_row();
+// FP32 forward with caller-provided parameters P and three q x 200 scratch buffers
+rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
+                                 float* s1, float* s2, cudaStream_t s);
 rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss,
                         float* dg, cudaStream_t s);
 rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,

@@ -246,6 +246,34 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
     return RPNN_OK;
 }
 
+rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
+                                 float* s1, float* s2, cudaStream_t s) {
+    const ParamLayout& L = param_layout();
+    const int M = (int)q;
+    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
+    float* o = s0;
+    float* f1 = s1;
+    rpnn_status st;
+    for (int k = 0; k < RPNN_K; ++k) {
+        Seg z = seg(desc + k * RPNN_DESC_STRIDE, ZS, 1, P + L.V[k], 1, RPNN_DIN, RPNN_DIN);
+        if (k > 0) {
+            Seg oo = seg(o, H, 1, P + L.W1[k], 1, H, RPNN_H);
+            st = gemm(M, nullptr, RPNN_H, z, &oo, epi(f1, H, P + L.b1[k], 1), s);
+        } else {
+            st = gemm(M, nullptr, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
+        }
+        if (st) return st;
+        Seg w2 = seg(f1, H, 1, P + L.W2[k], 1, H, RPNN_H);
+        st = gemm(M, nullptr, RPNN_H, w2, nullptr, epi(o, H, P + L.b2[k], 1, k > 0 ? o : nullptr, H), s);
+        if (st) return st;
+    }
+    st = gemm(M, nullptr, RPNN_H, seg(o, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr, epi(s1, H, P + L.bT[0], 1), s);
+    if (st) return st;
+    st = gemm(M, nullptr, RPNN_H, seg(s1, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr, epi(s2, H, P + L.bT[1], 1), s);
+    if (st) return st;
+    return gemm(M, nullptr, 1, seg(s2, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
+}
+
 rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
                              const float* dout, float* dP, cudaStream_t s) {
     const ParamLayout& L = param_layout();
