@@ -198,6 +198,7 @@ rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* de
     if (!dev_x || !dev_d || !dev_wl || !dev_desc) { set_error("null pointer"); return RPNN_ERR_ARG; }
     if (wl_stride != 0 && wl_stride != 3) { set_error("wl_stride must be 0 or 3"); return RPNN_ERR_ARG; }
     if (desc_dtype != RPNN_F32 && desc_dtype != RPNN_BF16) { set_error("desc dtype must be F32 or BF16"); return RPNN_ERR_ARG; }
+    if ((reinterpret_cast<uintptr_t>(dev_desc) & 15u) != 0) { set_error("dev_desc must be 16-byte aligned"); return RPNN_ERR_ARG; }
     return launch_descriptor(*c, v->view(), dev_x, dev_d, dev_wl, wl_stride, q, nullptr, dev_desc,
                              desc_dtype, (cudaStream_t)stream);
 }

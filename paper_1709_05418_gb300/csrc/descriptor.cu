@@ -9,9 +9,8 @@
 //   s = inv_h0 * 2^-m, g = (inv_mean * 2^(k-1)) * s, A = g ex, B = g ey, C = g ez,
 //   U0 = x s - 0.5, u = fma(oz, C, fma(oy, B, fma(ox, A, U0))),
 //   lerp(a, b, f) = fma(f, b - a, a) in x, then y, then z.
-// Layout: one block of 256 threads per shading point (grid-stride over points);
-// thread t < 225 owns stencil point t for all 10 levels, threads 225..239 write gamma
-// and the zero padding.  Each lookup reads one 32-byte corner record (two float4).
+// Layout: one warp per shading point; each lookup reads one 32-byte corner record with a
+// single 256-bit load.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -67,60 +66,81 @@ __device__ __forceinline__ Frame make_frame(const float d[3], const float wl[3])
     return F;
 }
 
-__device__ __forceinline__ float lookup(const VolumeView& v, int m, const float u[3]) {
+// Level geometry in the form one lookup needs: record index of cell (0,0,0) and the
+// record strides (records cover cells -1 .. n-1 on each axis).
+struct LevelGeom {
+    uint32_t ax, ay, az;
+    int64_t r000;
+    int32_t sy, sz;
+};
+
+__device__ __forceinline__ LevelGeom level_geom(const VolumeView& v, int m) {
     const LevelDesc L = v.lvl[m];
-    int i[3];
-    float f[3];
-    const int dims[3] = {L.ax, L.ay, L.az};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float uu = fminf(fmaxf(u[a], -1.0e6f), 1.0e6f);
-        const float fl = floorf(uu);
-        f[a] = __fsub_rn(uu, fl);
-        i[a] = (int)fl;
-    }
-    if (i[0] < -1 || i[0] > dims[0] - 1 || i[1] < -1 || i[1] > dims[1] - 1 || i[2] < -1 ||
-        i[2] > dims[2] - 1)
-        return 0.0f;
-    const int64_t r = L.rec_offset +
-                      ((int64_t)(i[2] + 1) * (L.ay + 1) + (i[1] + 1)) * (L.ax + 1) + (i[0] + 1);
-    const float4 lo = __ldg(v.packed + 2 * r);
-    const float4 hi = __ldg(v.packed + 2 * r + 1);
-    const float c00 = lerp_rn(lo.x, lo.y, f[0]);
-    const float c10 = lerp_rn(lo.z, lo.w, f[0]);
-    const float c01 = lerp_rn(hi.x, hi.y, f[0]);
-    const float c11 = lerp_rn(hi.z, hi.w, f[0]);
-    const float c0 = lerp_rn(c00, c10, f[1]);
-    const float c1 = lerp_rn(c01, c11, f[1]);
-    return lerp_rn(c0, c1, f[2]);
+    LevelGeom g;
+    g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
+    g.sy = L.ax + 1;
+    g.sz = (L.ax + 1) * (L.ay + 1);
+    g.r000 = L.rec_offset + g.sz + g.sy + 1;
+    return g;
 }
 
-// Thread t < 250 of the block owns stencil column (ix, iy) = (t%25 % 5, t%25 / 5) of
-// level k = t / 25 and walks its 9 points along z, so the level set-up and the
-// (ox, oy) part of each coordinate are computed once per column; threads 250..255
-// write gamma and the zero padding.
+// Trilinear lookup from one 32-byte corner record.  floor(u) by a saturating
+// round-down conversion: a cell index outside [-1, n-1] (including |u| huge) reads 0,
+// exactly as the reference clamps |u| to 1e6 first; the fraction is u - floor(u).
+__device__ __forceinline__ float lookup(const float* __restrict__ packed, const LevelGeom& g, const float u[3]) {
+    const int i0 = __float2int_rd(u[0]), i1 = __float2int_rd(u[1]), i2 = __float2int_rd(u[2]);
+    if ((uint32_t)(i0 + 1) > g.ax || (uint32_t)(i1 + 1) > g.ay || (uint32_t)(i2 + 1) > g.az) return 0.0f;
+    const float f0 = __fsub_rn(u[0], (float)i0);
+    const float f1 = __fsub_rn(u[1], (float)i1);
+    const float f2 = __fsub_rn(u[2], (float)i2);
+    const int64_t r = g.r000 + (int64_t)i2 * g.sz + (int64_t)i1 * g.sy + i0;
+    float c[8];
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
+        : "l"(packed + 8 * r));
+    const float c00 = lerp_rn(c[0], c[1], f0);
+    const float c10 = lerp_rn(c[2], c[3], f0);
+    const float c01 = lerp_rn(c[4], c[5], f0);
+    const float c11 = lerp_rn(c[6], c[7], f0);
+    const float c0 = lerp_rn(c00, c10, f1);
+    const float c1 = lerp_rn(c01, c11, f1);
+    return lerp_rn(c0, c1, f2);
+}
+
+// One warp per shading point (8 per block, grid-stride over points, no block-wide
+// barrier).  The 250 column tasks (level k, stencil column (ix, iy)) are dealt to the
+// lanes in order; a task computes its level's set-up and the (ox, oy) part of the
+// coordinate once and walks the 9 points along z.  BF16 rows are assembled in a
+// per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
+// directly (25 consecutive values per level and z-slice).
 template <class OutT>
 __global__ void __launch_bounds__(256)
 k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __restrict__ ds,
              const float* __restrict__ wls, int wl_stride, int64_t q_host,
              const int* __restrict__ q_dev, OutT* __restrict__ out) {
+    constexpr int ROW = RPNN_K * RPNN_DESC_STRIDE;
+    constexpr bool STAGE = sizeof(OutT) == 2;
+    __shared__ __align__(16) OutT rowbuf[STAGE ? 8 : 1][STAGE ? ROW : 8];
     const int64_t q = q_dev ? (int64_t)*q_dev : q_host;
-    const int t = threadIdx.x;
-    const int k = t / 25, col = t % 25;
-    const int ix = col % 5, iy = col / 5;
-    const float ox = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)ix));
-    const float oy = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iy));
-    const int m = k < RPNN_K ? v.mip_of_level[k] : 0;
-    const float s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-    const float gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << (k < RPNN_K ? k : 0))), s);
-    for (int64_t qi = blockIdx.x; qi < q; qi += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* packed = reinterpret_cast<const float*>(v.packed);
+    for (int64_t qi = (int64_t)blockIdx.x * 8 + warp; qi < q; qi += (int64_t)gridDim.x * 8) {
         const float x[3] = {__ldg(xs + 3 * qi), __ldg(xs + 3 * qi + 1), __ldg(xs + 3 * qi + 2)};
         const float d[3] = {__ldg(ds + 3 * qi), __ldg(ds + 3 * qi + 1), __ldg(ds + 3 * qi + 2)};
         const float* wp = wls + (int64_t)wl_stride * qi;
         const float wl[3] = {__ldg(wp), __ldg(wp + 1), __ldg(wp + 2)};
         const Frame F = make_frame(d, wl);
-        OutT* row = out + qi * (int64_t)(RPNN_K * RPNN_DESC_STRIDE);
-        if (k < RPNN_K) {
+        OutT* grow = out + qi * (int64_t)ROW;
+        OutT* row = STAGE ? rowbuf[warp] : grow;
+        for (int task = lane; task < RPNN_K * 25; task += 32) {
+            const int k = task / 25, col = task % 25;
+            const int ix = col % 5, iy = col / 5;
+            const float ox = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)ix));
+            const float oy = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iy));
+            const int m = v.mip_of_level[k];
+            const float s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
+            const float gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), s);
+            const LevelGeom geom = level_geom(v, m);
             float P[3], C[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -135,13 +155,19 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
                 const float oz = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iz));
                 const float u[3] = {__fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
                                     __fmaf_rn(oz, C[2], P[2])};
-                dst[iz * 25] = cvt_out<OutT>(lookup(v, m, u));
+                dst[iz * 25] = cvt_out<OutT>(lookup(packed, geom, u));
             }
-        } else {
-            for (int e = t - 250; e < RPNN_K * (RPNN_DESC_STRIDE - RPNN_S); e += 6) {
-                const int kk = e / (RPNN_DESC_STRIDE - RPNN_S), j = e % (RPNN_DESC_STRIDE - RPNN_S);
-                row[kk * RPNN_DESC_STRIDE + RPNN_S + j] = cvt_out<OutT>(j == 0 ? F.gamma : 0.0f);
-            }
+        }
+        for (int e = lane; e < RPNN_K * (RPNN_DESC_STRIDE - RPNN_S); e += 32) {
+            const int kk = e / (RPNN_DESC_STRIDE - RPNN_S), j = e % (RPNN_DESC_STRIDE - RPNN_S);
+            row[kk * RPNN_DESC_STRIDE + RPNN_S + j] = cvt_out<OutT>(j == 0 ? F.gamma : 0.0f);
+        }
+        if (STAGE) {
+            __syncwarp();
+            uint4* gdst = reinterpret_cast<uint4*>(grow);
+            const uint4* ssrc = reinterpret_cast<const uint4*>(row);
+            for (int e = lane; e < ROW * (int)sizeof(OutT) / 16; e += 32) gdst[e] = ssrc[e];
+            __syncwarp();
         }
     }
 }
@@ -152,8 +178,18 @@ rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, cons
                               const float* wl, int wl_stride, int64_t q, const int* q_dev,
                               void* out, int dtype, cudaStream_t s) {
     if (q <= 0 && !q_dev) return RPNN_OK;
-    int64_t g = q_dev ? (int64_t)c.num_sms * 8 : q;
-    if (g > (int64_t)c.num_sms * 8) g = (int64_t)c.num_sms * 8;
+    // one resident wave of blocks (8 shading points each), grid-stride beyond that
+    static int per_sm[2] = {0, 0};
+    const int ti = dtype == RPNN_F32 ? 0 : 1;
+    if (!per_sm[ti]) {
+        int nb = 0;
+        if (ti == 0) RPNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<float>, 256, 0));
+        else RPNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<__nv_bfloat16>, 256, 0));
+        per_sm[ti] = nb > 0 ? nb : 1;
+    }
+    const int64_t wave = (int64_t)c.num_sms * per_sm[ti];
+    int64_t g = q_dev ? wave : (q + 7) / 8;
+    if (g > wave) g = wave;
     if (dtype == RPNN_F32)
         k_descriptor<float><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (float*)out);
     else

@@ -7,20 +7,23 @@
 //   output:   g = relu(T3 . o12 + bT3)  (CUDA cores, in the last epilogue)
 // Widths are padded to N = 208 (zero rows) and the descriptor level to K = 240.
 //
-// Roles (192 threads): warp 0 streams weights (1-D bulk copies of a pre-arranged BF16
+// Roles (320 threads): warp 0 streams weights (1-D bulk copies of a pre-arranged BF16
 // image through a 5-stage ring; a stage of a block's first layer also carries the matching
 // descriptor k-groups as 2-D TMA boxes of 8 columns x 128 queries); warp 1 allocates
 // tensor memory and one lane issues tcgen05.mma into two alternating FP32 accumulators
-// (so the z-part of a block's first layer overlaps the previous epilogue); warps 2-5
+// (so the z-part of a block's first layer overlaps the previous epilogue); warps 2-9
 // are the epilogue: tensor memory -> registers, bias / residual / ReLU, BF16 operands
 // written back to shared memory for the next layer.
 //
-// Operand layout in shared memory (K-major, no swizzle): element (row, k) at
-// (k/8) * rows * 16 + row * 16 + (k%8) * 2, i.e. 8-row x 16-byte core matrices
-// contiguous, LBO = rows * 16 (next core matrix along K), SBO = 128 (next 8 rows).
+// Operand layout in shared memory (K-major, 64-byte swizzle): blocks of 32 columns; in a
+// block, row r occupies 64 bytes at r * 64 and its 16-byte unit j (columns 8j..8j+7)
+// sits at unit j ^ ((r >> 1) & 3).  The weight image in global memory is stored in
+// exactly this form, and descriptor tiles arrive as 64-byte-swizzled TMA boxes.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "common.cuh"
@@ -37,23 +40,26 @@ constexpr int KG_Z = 30;                // 240 / 8 descriptor k-groups per level
 constexpr int KG_H = 26;                // 208 / 8 hidden k-groups
 constexpr int CHUNK_KG = 4;             // k-groups per weight stage
 constexpr int STAGES = 5;
-constexpr uint32_t KG_BYTES_A = TM * 16;          // 2048
-constexpr uint32_t KG_BYTES_B = NP * 16;          // 3328
+constexpr uint32_t BLK_A = TM * 64;               // 8192: 32 columns of 128 rows
+constexpr uint32_t BLK_B = NP * 64;               // 13312: 32 columns of 208 rows
+constexpr int NBLK_H = 7;                         // 32-column blocks of a 208-wide operand
 // a ring stage holds up to 4 weight k-groups and, for the descriptor part of a block's
 // first layer, the matching 4 k-groups of the 128-query descriptor tile
-constexpr uint32_t STAGE_W = CHUNK_KG * KG_BYTES_B;           // 13312
-constexpr uint32_t STAGE_BYTES = STAGE_W + CHUNK_KG * KG_BYTES_A;   // 21504
+constexpr uint32_t STAGE_W = BLK_B;                            // 13312
+constexpr uint32_t STAGE_BYTES = STAGE_W + BLK_A;              // 21504 (multiple of 512)
 constexpr uint32_t OFF_O = 0;
-constexpr uint32_t OFF_F = OFF_O + KG_H * KG_BYTES_A;         // 53248
-constexpr uint32_t OFF_RING = OFF_F + KG_H * KG_BYTES_A;      // 106496
-constexpr uint32_t OFF_BAR = OFF_RING + STAGES * STAGE_BYTES; // 214016
-constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
-constexpr int NTHREADS = 192;
+constexpr uint32_t OFF_F = OFF_O + NBLK_H * BLK_A;             // 57344
+constexpr uint32_t OFF_RING = OFF_F + NBLK_H * BLK_A;          // 114688
+constexpr uint32_t OFF_BAR = OFF_RING + STAGES * STAGE_BYTES;  // 222208
+constexpr uint32_t SMEM_BYTES = OFF_BAR + 256 + 2 * 128 * 4;
+constexpr int EPI_THREADS = 256;         // 8 epilogue warps
+constexpr int NTHREADS = 64 + EPI_THREADS;
 
 // barrier slots (8 bytes each) from OFF_BAR
-enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_ACT, B_COUNT };
+enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_ACT, B_PART, B_COUNT };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + 8 * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
+constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 128 floats
 
 struct TcArgs {
     const __nv_bfloat16* img;   // weight image
@@ -64,6 +70,7 @@ struct TcArgs {
     const int* q_dev;
     float* out;
     uint32_t* status;
+    unsigned long long* trace;  // optional per-block cycle counters (diagnostics), or null
 };
 
 __host__ __device__ constexpr int layer_kg(int l) {
@@ -77,6 +84,15 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     const uint32_t base = tc::smem_u32(sm);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_ABORT);
     auto bar = [&](int i) { return base + OFF_BAR + 8u * (uint32_t)i; };
+    // diagnostics: cycles spent in each role's waits, when a.trace is set
+    unsigned long long cyc_wait = 0, cyc_wait2 = 0;
+    const long long cyc_start = clock64();
+    auto twait = [&](uint32_t b, uint32_t parity, unsigned long long& acc) {
+        const long long t0 = a.trace ? clock64() : 0;
+        const bool r = tc::mbar_wait(b, parity, abort_flag);
+        if (a.trace) acc += (unsigned long long)(clock64() - t0);
+        return r;
+    };
     const int64_t Q = a.q_dev ? (int64_t)*a.q_dev : a.q_host;
     const int ntiles = (int)((Q + TM - 1) / TM);
 
@@ -84,7 +100,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         *abort_flag = (base & 1023u) ? 1 : 0;
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
         tc::mbar_init(bar(B_ACC), 1);
-        tc::mbar_init(bar(B_ACT), 4 * 32);
+        tc::mbar_init(bar(B_ACT), EPI_THREADS);
+        tc::mbar_init(bar(B_PART), EPI_THREADS / 2);
         tc::fence_mbar_init();
     }
     if (warp == 1) {
@@ -106,15 +123,13 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     const bool l1 = l < 20 && !(l & 1);      // reads descriptor level l/2
                     const int kg = layer_kg(l);
                     for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
-                        const int n = min(CHUNK_KG, kg - g0);
-                        const int nz = l1 ? max(0, min(g0 + n, KG_Z) - g0) : 0;
-                        if (!tc::mbar_wait(bar(B_WEMPTY + s), (fills[s] & 1u) ^ 1u, abort_flag)) break;
+                        const bool hz = l1 && g0 < KG_Z;        // stage carries descriptor columns
+                        if (!twait(bar(B_WEMPTY + s), (fills[s] & 1u) ^ 1u, cyc_wait)) break;
                         const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
-                        tc::mbar_expect_tx(bar(B_WFULL + s), n * KG_BYTES_B + nz * KG_BYTES_A);
-                        tc::bulk_g2s(st, a.img + a.img_off[l] + (int64_t)g0 * NP * 8, n * KG_BYTES_B, bar(B_WFULL + s));
-                        for (int i = 0; i < nz; ++i)
-                            tc::tma_load_2d(st + STAGE_W + i * KG_BYTES_A, &zmap, (l / 2) * 240 + 8 * (g0 + i),
-                                            t * TM, bar(B_WFULL + s));
+                        tc::mbar_expect_tx(bar(B_WFULL + s), BLK_B + (hz ? BLK_A : 0u));
+                        tc::bulk_g2s(st, a.img + a.img_off[l] + (int64_t)(g0 / CHUNK_KG) * (BLK_B / 2), BLK_B,
+                                     bar(B_WFULL + s));
+                        if (hz) tc::tma_load_2d(st + STAGE_W, &zmap, (l / 2) * 240 + 8 * g0, t * TM, bar(B_WFULL + s));
                         ++fills[s];
                         s = (s + 1) % STAGES;
                     }
@@ -139,24 +154,29 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     bool dep_done = false;
                     for (int g0 = 0; g0 < kg && ok; g0 += CHUNK_KG) {
                         const int cnt = min(CHUNK_KG, kg - g0);
-                        ok = tc::mbar_wait(bar(B_WFULL + s), uses[s] & 1u, abort_flag);
+                        ok = twait(bar(B_WFULL + s), uses[s] & 1u, cyc_wait);
                         if (!ok) break;
                         tc::tc_fence_after();
                         for (int j = 0; j < cnt; j += 2) {
                             const int g = g0 + j;
                             if (!dep_done && g >= dep_from) {
-                                if (n > 0) ok = tc::mbar_wait(bar(B_ACT), (n - 1) & 1u, abort_flag);
+                                if (n > 0) ok = twait(bar(B_ACT), (n - 1) & 1u, cyc_wait2);
                                 if (!ok) break;
                                 tc::tc_fence_after();
                                 dep_done = true;
                             }
                             const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
+                            // K-step of 16 columns: 32-byte offset inside a 64-byte swizzled row
+                            const uint32_t koff = (uint32_t)(j >> 1) * 32u;
                             uint32_t a_addr;
-                            if (l1) a_addr = g < KG_Z ? st + STAGE_W + j * KG_BYTES_A : base + OFF_O + (g - KG_Z) * KG_BYTES_A;
-                            else if (l == 20) a_addr = base + OFF_O + g * KG_BYTES_A;
-                            else a_addr = base + OFF_F + g * KG_BYTES_A;
-                            const uint64_t ad = tc::smem_desc(a_addr, KG_BYTES_A, 128);
-                            const uint64_t bd = tc::smem_desc(st + j * KG_BYTES_B, KG_BYTES_B, 128);
+                            if (l1 && g < KG_Z) a_addr = st + STAGE_W + koff;
+                            else {
+                                const int gg = l1 ? g - KG_Z : g;      // k-group inside O or F
+                                const uint32_t buf = (l1 || l == 20) ? base + OFF_O : base + OFF_F;
+                                a_addr = buf + (uint32_t)(gg / CHUNK_KG) * BLK_A + (uint32_t)((gg % CHUNK_KG) >> 1) * 32u;
+                            }
+                            const uint64_t ad = tc::smem_desc_sw64(a_addr);
+                            const uint64_t bd = tc::smem_desc_sw64(st + koff);
                             tc::mma_bf16(acc, ad, bd, idesc, g > 0 ? 1u : 0u);
                         }
                         if (!ok) break;
@@ -169,7 +189,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     // must not run two phases of the act barrier ahead of the epilogue
                     // (parity waits would alias): wait for the previous epilogue here.
                     if (!dep_done && n > 0) {
-                        ok = tc::mbar_wait(bar(B_ACT), (n - 1) & 1u, abort_flag);
+                        ok = twait(bar(B_ACT), (n - 1) & 1u, cyc_wait2);
                         if (!ok) break;
                         tc::tc_fence_after();
                     }
@@ -179,66 +199,83 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         }
     } else {
         // ------------------------------------------------------------ epilogue
+        // 8 warps: warp w reads tensor-memory lanes 32*(w%4) .. +31 (its 32 query rows)
+        // and one column half, [0, 112) or [112, 208), 32 columns per load.
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
+        const int cbeg = half ? 112 : 0, cend = half ? NP : 112;
         uint32_t n = 0;
         unsigned char* Osm = sm + OFF_O;
         unsigned char* Fsm = sm + OFF_F;
+        float* part = reinterpret_cast<float*>(sm + OFF_PART);     // [TM] partial dots
+        uint32_t tile_iter = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             float dot = 0.0f;
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
-                ok = tc::mbar_wait(bar(B_ACC), n & 1u, abort_flag);
+                ok = twait(bar(B_ACC), n & 1u, cyc_wait);
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u;
                 const float* bias = a.bias + l * NP;
                 const bool l1 = l < 20 && !(l & 1);
-                const bool l2 = l < 20 && (l & 1);
+                const bool resid = l < 20 && (l & 1) && l > 1;
                 unsigned char* dst = (l1 || l == 20) ? Fsm : Osm;
-                for (int c0 = 0; c0 < NP; c0 += 16) {
-                    float v[16];
-                    tc::tmem_ld16(taddr + c0, v);
-                    const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+                for (int cb = cbeg; cb < cend; cb += 32) {
+                    const int width = min(32, cend - cb);          // 32 or 16
+                    float v[32];
+                    if (width == 32) tc::tmem_ld32(taddr + cb, v);
+                    else tc::tmem_ld16(taddr + cb, v);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 b = __ldg(b4 + q);
-                        v[4 * q] += b.x; v[4 * q + 1] += b.y; v[4 * q + 2] += b.z; v[4 * q + 3] += b.w;
-                    }
-                    uint4* d0 = reinterpret_cast<uint4*>(dst + (c0 / 8) * KG_BYTES_A + row * 16);
-                    uint4* d1 = reinterpret_cast<uint4*>(dst + (c0 / 8 + 1) * KG_BYTES_A + row * 16);
-                    if (l2 && l > 1) {
-                        const uint4 r0 = *d0, r1 = *d1;
-                        const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&r0);
-                        const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&r1);
+                    for (int h = 0; h < 2; ++h) {
+                        if (h * 16 >= width) break;
+                        float* w = v + 16 * h;
+                        const int c0 = cb + 16 * h;
+                        const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const float2 f0 = __bfloat1622float2(h0[q]), f1 = __bfloat1622float2(h1[q]);
-                            v[2 * q] += f0.x; v[2 * q + 1] += f0.y;
-                            v[8 + 2 * q] += f1.x; v[8 + 2 * q + 1] += f1.y;
+                            const float4 b = __ldg(b4 + q);
+                            w[4 * q] += b.x; w[4 * q + 1] += b.y; w[4 * q + 2] += b.z; w[4 * q + 3] += b.w;
                         }
-                    }
+                        // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
+                        unsigned char* rb = dst + (c0 / 32) * BLK_A + row * 64;
+                        const int u0 = (c0 % 32) / 8, sw = (row >> 1) & 3;
+                        uint4* d0 = reinterpret_cast<uint4*>(rb + ((u0 ^ sw) << 4));
+                        uint4* d1 = reinterpret_cast<uint4*>(rb + (((u0 + 1) ^ sw) << 4));
+                        if (resid) {
+                            const uint4 r0 = *d0, r1 = *d1;
+                            const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&r0);
+                            const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&r1);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = (c0 + i < RPNN_H) ? fmaxf(v[i], 0.0f) : 0.0f;
-                    if (l == 21) {
-                        const float4* w4 = reinterpret_cast<const float4*>(a.w3 + c0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 w = __ldg(w4 + q);
-                            dot = fmaf(v[4 * q], w.x, dot); dot = fmaf(v[4 * q + 1], w.y, dot);
-                            dot = fmaf(v[4 * q + 2], w.z, dot); dot = fmaf(v[4 * q + 3], w.w, dot);
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 f0 = __bfloat1622float2(h0[q]), f1 = __bfloat1622float2(h1[q]);
+                                w[2 * q] += f0.x; w[2 * q + 1] += f0.y;
+                                w[8 + 2 * q] += f1.x; w[8 + 2 * q + 1] += f1.y;
+                            }
                         }
-                    } else {
-                        uint4 p0, p1;
-                        __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
-                        __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            q0[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                            q1[q] = __floats2bfloat162_rn(v[8 + 2 * q], v[8 + 2 * q + 1]);
+                        for (int i = 0; i < 16; ++i) w[i] = (c0 + i < RPNN_H) ? fmaxf(w[i], 0.0f) : 0.0f;
+                        if (l == 21) {
+                            const float4* w4 = reinterpret_cast<const float4*>(a.w3 + c0);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 ww = __ldg(w4 + q);
+                                dot = fmaf(w[4 * q], ww.x, dot); dot = fmaf(w[4 * q + 1], ww.y, dot);
+                                dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
+                            }
+                        } else {
+                            uint4 p0, p1;
+                            __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
+                            __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                q0[q] = __floats2bfloat162_rn(w[2 * q], w[2 * q + 1]);
+                                q1[q] = __floats2bfloat162_rn(w[8 + 2 * q], w[8 + 2 * q + 1]);
+                            }
+                            *d0 = p0;
+                            *d1 = p1;
                         }
-                        *d0 = p0;
-                        *d1 = p1;
                     }
                 }
                 if (l != 21) tc::fence_proxy_async_smem();
@@ -246,9 +283,24 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 tc::mbar_arrive(bar(B_ACT));
             }
             if (!ok) break;
-            const int64_t r = (int64_t)t * TM + row;
-            if (r < Q) a.out[r] = fmaxf(dot + __ldg(a.w3 + NP - 1), 0.0f);
+            // combine the two column halves of the output layer's dot product: the
+            // second half publishes its partial sums, the first half adds them (bounded wait)
+            if (half) {
+                part[row] = dot;
+                tc::mbar_arrive(bar(B_PART));
+            } else {
+                if (!tc::mbar_wait(bar(B_PART), tile_iter & 1u, abort_flag)) break;
+                const int64_t r = (int64_t)t * TM + row;
+                if (r < Q) a.out[r] = fmaxf(dot + part[row] + __ldg(a.w3 + NP - 1), 0.0f);
+            }
+            ++tile_iter;
         }
+    }
+    if (a.trace && lane == 0 && warp <= 2) {
+        unsigned long long* tr = a.trace + (size_t)blockIdx.x * 12 + warp * 3;
+        tr[0] = cyc_wait;
+        tr[1] = cyc_wait2;
+        tr[2] = (unsigned long long)(clock64() - cyc_start);
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -267,10 +319,13 @@ __global__ void k_build_image(const float* __restrict__ P, ParamLayout L, TcArgs
          e += (int64_t)gridDim.x * blockDim.x) {
         int l = NLAYERS - 1;
         while (l > 0 && a.img_off[l] > e) --l;
+        // chunk of 32 columns: 208 rows of 64 bytes, 16-byte unit j of row n stored at
+        // unit j ^ ((n >> 1) & 3) (the shared-memory image of a 64-byte swizzle)
         const int64_t r = e - a.img_off[l];
-        const int kg = (int)(r / (NP * 8));
-        const int n = (int)((r / 8) % NP);
-        const int c = kg * 8 + (int)(r % 8);
+        const int chunk = (int)(r / (BLK_B / 2));
+        const int rem = (int)(r % (BLK_B / 2));
+        const int n = rem / 32, pos = rem % 32;
+        const int c = chunk * 32 + (((pos / 8) ^ ((n >> 1) & 3)) * 8) + pos % 8;
         float v = 0.0f;
         if (n < RPNN_H) {
             if (l < 20 && !(l & 1)) {
@@ -309,7 +364,7 @@ ImageLayout image_layout() {
     int64_t o = 0;
     for (int l = 0; l < NLAYERS; ++l) {
         I.off[l] = o;
-        o += (int64_t)layer_kg(l) * NP * 8;
+        o += (int64_t)((layer_kg(l) + CHUNK_KG - 1) / CHUNK_KG) * (BLK_B / 2);
     }
     I.img_elems = o;
     I.bias_bytes_off = ((size_t)o * 2 + 255) & ~(size_t)255;
@@ -363,10 +418,10 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     CUtensorMap zmap;
     const cuuint64_t dims[2] = {(cuuint64_t)RPNN_K * RPNN_DESC_STRIDE, (cuuint64_t)q};
     const cuuint64_t strides[1] = {(cuuint64_t)RPNN_K * RPNN_DESC_STRIDE * 2};
-    const cuuint32_t box[2] = {8, TM};
+    const cuuint32_t box[2] = {32, TM};
     const cuuint32_t es[2] = {1, 1};
     CUresult r = enc(&zmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(desc_bf16), dims, strides, box,
-                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return RPNN_ERR_CUDA; }
     const ImageLayout I = image_layout();
@@ -380,6 +435,12 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     a.q_dev = q_dev;
     a.out = out;
     a.status = c.status.as<uint32_t>();
+    // RPNN_TC_TRACE=1: per-role wait cycles of every block, summarised on stderr
+    // (synchronises the stream; diagnostics only)
+    static unsigned long long* trace_buf = nullptr;
+    const bool tracing = getenv("RPNN_TC_TRACE") != nullptr;
+    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, 1024 * 12 * sizeof(unsigned long long)));
+    a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;
     if (!attr) {
         RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -387,8 +448,21 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
+    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, 1024 * 12 * sizeof(unsigned long long), s));
     k_rpnn_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
+    if (tracing) {
+        std::vector<unsigned long long> h((size_t)grid * 12);
+        RPNN_CUDA_TRY(cudaMemcpyAsync(h.data(), trace_buf, h.size() * 8, cudaMemcpyDeviceToHost, s));
+        RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+        double acc[12] = {};
+        for (int b = 0; b < grid; ++b)
+            for (int i = 0; i < 12; ++i) acc[i] += (double)h[(size_t)b * 12 + i] / grid;
+        fprintf(stderr,
+                "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: wait_full %.0f "
+                "wait_act %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
+                grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
+    }
     return RPNN_OK;
 }
 

@@ -80,7 +80,174 @@ __global__ void __launch_bounds__(128) k_probe(const __nv_bfloat16* __restrict__
     if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+
+// ---- 64-byte swizzled K-major operands ------------------------------------------
+// Row r of a 32-column (64-byte) block lives at r * 64; its 16-byte unit j (columns
+// 8j .. 8j+7) is stored at unit j ^ ((r >> 1) & 3).  8-row groups are 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                       // leading offset: unused for swizzled K-major
+    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;                       // 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ uint32_t sw64_off(int r, int c) {
+    return (uint32_t)(r * 64 + ((((c & 31) >> 3) ^ ((r >> 1) & 3)) << 4) + (c & 7) * 2);
+}
+
+// A (128 x 64) written by threads in two 32-column blocks of 8 KB; B (208 x 64) arrives
+// by two bulk copies of a pre-swizzled image (13 KB each); a 2-D TMA box {32, 128}
+// with 64-byte swizzle is written out raw for the host to un-swizzle.
+__global__ void __launch_bounds__(128) k_probe_sw64(const __nv_bfloat16* __restrict__ A,
+                                                    const __nv_bfloat16* __restrict__ Bimg,
+                                                    const __grid_constant__ CUtensorMap tmap,
+                                                    float* __restrict__ D, uint4* __restrict__ tma_out,
+                                                    int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    constexpr uint32_t SA = 0, SB = 16384, ST = 45056, SBAR = 65536, SSLOT = 65600;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t base = smem_u32(sm);
+    if ((base & 1023u) != 0) { if (tid == 0) atomicOr(err, 8); return; }
+    const uint32_t bar = base + SBAR, bar_mma = base + SBAR + 8;
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        mbar_init(bar_mma, 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < M * 64; i += 128) {
+        const int r = i / 64, c = i % 64;
+        *reinterpret_cast<__nv_bfloat16*>(sm + SA + (c / 32) * 8192 + sw64_off(r, c)) = A[i];
+    }
+    fence_proxy_async_smem();
+    if (warp == 0) tmem_alloc(base + SSLOT, 256);
+    if (warp == 0) tmem_relinquish();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + SSLOT);
+    if (tid == 0) {
+        mbar_expect_tx(bar, 2 * 13312 + 8192);
+        bulk_g2s(base + SB, Bimg, 13312, bar);
+        bulk_g2s(base + SB + 13312, reinterpret_cast<const unsigned char*>(Bimg) + 13312, 13312, bar);
+        tma_load_2d(base + ST, &tmap, 32, 0, bar);
+        if (!mbar_wait(bar, 0, &abort_flag)) { atomicOr(err, 1); }
+        else {
+            tc_fence_after();
+            const uint32_t id = idesc_bf16(M, N);
+            for (int j = 0; j < 4; ++j) {        // K = 64: blocks of 32, two K=16 steps each
+                const uint64_t a = smem_desc_sw64(base + SA + (j / 2) * 8192 + (j % 2) * 32);
+                const uint64_t b = smem_desc_sw64(base + SB + (j / 2) * 13312 + (j % 2) * 32);
+                mma_bf16(tmem, a, b, id, j > 0);
+            }
+            mma_commit(bar_mma);
+        }
+    }
+    __syncwarp();
+    if (!mbar_wait(bar_mma, 0, &abort_flag)) atomicOr(err, 2);
+    tc_fence_after();
+    if (!abort_flag) {
+        const uint32_t lane_base = (uint32_t)(32 * (warp % 4)) << 16;
+        for (int c = 0; c < N; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + c, v);
+            const int row = 32 * (warp % 4) + lane;
+            for (int i = 0; i < 16; ++i) D[row * N + c + i] = v[i];
+        }
+        for (int i = tid; i < 512; i += 128) tma_out[i] = reinterpret_cast<const uint4*>(sm + ST)[i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+
+// ---- issue-rate measurement: `nmma` back-to-back MMAs on resident operands ----------
+// mode bit 0: commit to an mbarrier after every second MMA; bit 1: N = 256 instead of
+// 208; bit 2: 64-byte swizzled descriptors instead of interleaved.  The operands are
+// zeros (only timing matters); clock64 brackets issue and completion.
+__global__ void __launch_bounds__(128) k_mma_rate(int nmma, int mode, long long* cycles, int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid / 32;
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bar = base + 65536, bar2 = base + 65544;
+    for (int i = tid; i < 65536 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        mbar_init(bar2, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) { tmem_alloc(base + 65600, 256); tmem_relinquish(); }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 65600);
+    if (tid == 0) {
+        const int n = (mode & 2) ? 256 : 208;
+        const uint32_t id = idesc_bf16(128, n);
+        const bool sw = (mode & 4) != 0;
+        const uint64_t a0 = sw ? smem_desc_sw64(base) : smem_desc(base, 2048, 128);
+        const uint64_t b0 = sw ? smem_desc_sw64(base + 16384) : smem_desc(base + 16384, 4096, 128);
+        uint32_t commits = 0;
+        const long long t0 = clock64();
+        for (int i = 0; i < nmma; ++i) {
+            const uint64_t off = (uint64_t)((i & 1) * 2);          // +32 bytes inside the row
+            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
+            if ((mode & 1) && (i & 1)) { mma_commit(bar2); ++commits; }
+        }
+        const long long t1 = clock64();
+        mma_commit(bar);
+        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
+        const long long t2 = clock64();
+        cycles[0] = t1 - t0;
+        cycles[1] = t2 - t0;
+        (void)commits;
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace
+
+extern "C" int tc_mma_rate(int nmma, int mode, long long* cycles, int* err) {
+    if (cudaFuncSetAttribute(k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
+    k_mma_rate<<<1, 128, SMEM>>>(nmma, mode, cycles, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}
+
+
+extern "C" int tc_probe_sw64(const void* A, const void* Bimg, const void* T2d, int t_rows, int t_cols,
+                             float* D, void* tma_out, int* err) {
+    typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess || !fn)
+        return -10;
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)t_cols, (cuuint64_t)t_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)t_cols * 2};
+    const cuuint32_t box[2] = {32, 128};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = ((EncodeFn)fn)(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(T2d), dims, strides,
+                                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -11;
+    if (cudaFuncSetAttribute(k_probe_sw64, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
+    k_probe_sw64<<<1, 128, SMEM>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)Bimg, tmap, D, (uint4*)tma_out, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}
 
 extern "C" int tc_probe(const void* A, const void* Bimg, const void* T2d, int t_rows, int t_cols,
                         float* D, void* tma_out, int* err) {

@@ -60,3 +60,62 @@ def test_mma_tmem_and_copies(probe):
     exp1 = np.zeros((128, 8), np.float32)
     exp1[:36] = Tn[64:100, 8:16]
     assert np.array_equal(boxes[0], exp0) and np.array_equal(boxes[1], exp1)
+
+
+def sw64_image(B):
+    """[rows][64] -> two 32-column blocks, row-major 64-byte rows, 16-byte unit j of row n
+    at unit j ^ ((n >> 1) & 3)."""
+    rows = B.shape[0]
+    img = np.zeros((2, rows, 4, 8), np.float32)
+    for blk in range(2):
+        for n in range(rows):
+            for j in range(4):
+                img[blk, n, j ^ ((n >> 1) & 3)] = B[n, 32 * blk + 8 * j:32 * blk + 8 * j + 8]
+    return img
+
+
+def test_mma_sw64_layouts(probe):
+    probe.tc_probe_sw64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3
+    rng = np.random.default_rng(1)
+    A = bf16(rng.normal(size=(128, 64)))
+    B = bf16(rng.normal(size=(208, 64)))
+    Bimg = bf16(sw64_image(B.float().numpy()).reshape(-1)).cuda()
+    T = bf16(rng.normal(size=(100, 64))).cuda()
+    D = torch.zeros((128, 208), dtype=torch.float32, device="cuda")
+    tma = torch.zeros(8192, dtype=torch.uint8, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Ad = A.cuda()
+    rc = probe.tc_probe_sw64(Ad.data_ptr(), Bimg.data_ptr(), T.data_ptr(), 100, 64, D.data_ptr(),
+                             tma.data_ptr(), err.data_ptr())
+    assert rc == 0 and err.item() == 0, (rc, err.item())
+    ref = A.double().numpy() @ B.double().numpy().T
+    got = D.cpu().double().numpy()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    raw = tma.cpu().view(torch.bfloat16).float().numpy().reshape(128, 4, 8)
+    box = np.zeros((128, 32), np.float32)
+    for r in range(128):
+        for j in range(4):
+            box[r, 8 * j:8 * j + 8] = raw[r, j ^ ((r >> 1) & 3)]
+    exp = np.zeros((128, 32), np.float32)
+    exp[:100] = T.float().cpu().numpy()[:, 32:64]
+    assert np.array_equal(box, exp)
+
+
+def test_mma_issue_rate(probe, capsys):
+    """Back-to-back tcgen05.mma throughput on resident operands (reported, loosely checked)."""
+    probe.tc_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rates = {}
+    for mode, name in [(0, "interleaved N208"), (4, "sw64 N208"), (6, "sw64 N256"), (5, "sw64 N208 commit/2")]:
+        n = 4096
+        assert probe.tc_mma_rate(n, mode, cyc.data_ptr(), err.data_ptr()) == 0
+        assert err.item() == 0
+        issue, done = cyc.cpu().tolist()
+        macs = 128 * (256 if mode & 2 else 208) * 16
+        rates[name] = (issue / n, done / n, macs / (done / n))
+    with capsys.disabled():
+        for k, (i, d, r) in rates.items():
+            print(f"\n[mma rate] {k:22s} issue {i:7.1f} cyc/mma  complete {d:7.1f} cyc/mma  {r:7.0f} MAC/clk")
+    for _, d, _ in rates.values():
+        assert d > 0
