@@ -56,7 +56,7 @@ constexpr int EPI_THREADS = 256;         // 8 epilogue warps
 constexpr int NTHREADS = 64 + EPI_THREADS;
 
 // barrier slots (8 bytes each) from OFF_BAR
-enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_ACT, B_PART, B_COUNT };
+enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_BLK, B_PART = B_BLK + NBLK_H, B_COUNT };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + 8 * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
 constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 128 floats
@@ -84,7 +84,9 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     const uint32_t base = tc::smem_u32(sm);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_ABORT);
     auto bar = [&](int i) { return base + OFF_BAR + 8u * (uint32_t)i; };
-    // diagnostics: cycles spent in each role's waits, when a.trace is set
+    // diagnostics: cycles spent in each role's waits, when a.trace is set, and for block
+    // 0 a timeline of 4 stamps per layer instance (MMA issue start/end, epilogue start/end)
+    long long* tl = (a.trace && blockIdx.x == 0) ? reinterpret_cast<long long*>(a.trace + 1024 * 12) : nullptr;
     unsigned long long cyc_wait = 0, cyc_wait2 = 0;
     const long long cyc_start = clock64();
     auto twait = [&](uint32_t b, uint32_t parity, unsigned long long& acc) {
@@ -100,7 +102,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         *abort_flag = (base & 1023u) ? 1 : 0;
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
         tc::mbar_init(bar(B_ACC), 1);
-        tc::mbar_init(bar(B_ACT), EPI_THREADS);
+        for (int b = 0; b < NBLK_H; ++b) tc::mbar_init(bar(B_BLK + b), EPI_THREADS);
         tc::mbar_init(bar(B_PART), EPI_THREADS / 2);
         tc::fence_mbar_init();
     }
@@ -147,33 +149,37 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS && ok; ++l, ++n) {
                     const uint32_t acc = tmem + (n & 1u) * 256u;
+                    if (tl && n < 512) tl[4 * n] = clock64();
                     const bool l1 = l < 20 && !(l & 1);
                     const int kg = layer_kg(l);
-                    // first k-group that reads an operand written by the previous epilogue
-                    const int dep_from = l == 0 ? kg : (l1 ? KG_Z : 0);
-                    bool dep_done = false;
+                    // Operands written by the previous epilogue (O or F) become ready one
+                    // 32-column block at a time; wait for block b (phase n-1) right before
+                    // the first k-step that reads it.  Every block phase is waited once per
+                    // layer, so the issuer never runs two phases ahead of the epilogue.
+                    int blk_ready = n > 0 ? -1 : NBLK_H - 1;
                     for (int g0 = 0; g0 < kg && ok; g0 += CHUNK_KG) {
                         const int cnt = min(CHUNK_KG, kg - g0);
                         ok = twait(bar(B_WFULL + s), uses[s] & 1u, cyc_wait);
                         if (!ok) break;
                         tc::tc_fence_after();
+                        const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
                         for (int j = 0; j < cnt; j += 2) {
                             const int g = g0 + j;
-                            if (!dep_done && g >= dep_from) {
-                                if (n > 0) ok = twait(bar(B_ACT), (n - 1) & 1u, cyc_wait2);
-                                if (!ok) break;
-                                tc::tc_fence_after();
-                                dep_done = true;
-                            }
-                            const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
                             // K-step of 16 columns: 32-byte offset inside a 64-byte swizzled row
                             const uint32_t koff = (uint32_t)(j >> 1) * 32u;
                             uint32_t a_addr;
                             if (l1 && g < KG_Z) a_addr = st + STAGE_W + koff;
                             else {
                                 const int gg = l1 ? g - KG_Z : g;      // k-group inside O or F
+                                const int blk = gg / CHUNK_KG;
+                                while (blk_ready < blk && ok) {
+                                    ++blk_ready;
+                                    ok = twait(bar(B_BLK + blk_ready), (n - 1) & 1u, cyc_wait2);
+                                }
+                                if (!ok) break;
+                                tc::tc_fence_after();
                                 const uint32_t buf = (l1 || l == 20) ? base + OFF_O : base + OFF_F;
-                                a_addr = buf + (uint32_t)(gg / CHUNK_KG) * BLK_A + (uint32_t)((gg % CHUNK_KG) >> 1) * 32u;
+                                a_addr = buf + (uint32_t)blk * BLK_A + (uint32_t)((gg % CHUNK_KG) >> 1) * 32u;
                             }
                             const uint64_t ad = tc::smem_desc_sw64(a_addr);
                             const uint64_t bd = tc::smem_desc_sw64(st + koff);
@@ -185,26 +191,28 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         s = (s + 1) % STAGES;
                     }
                     if (!ok) break;
-                    // The first layer of a tile reads no epilogue output, but the issuer
-                    // must not run two phases of the act barrier ahead of the epilogue
-                    // (parity waits would alias): wait for the previous epilogue here.
-                    if (!dep_done && n > 0) {
-                        ok = twait(bar(B_ACT), (n - 1) & 1u, cyc_wait2);
-                        if (!ok) break;
-                        tc::tc_fence_after();
+                    while (blk_ready < NBLK_H - 1 && ok) {
+                        ++blk_ready;
+                        ok = twait(bar(B_BLK + blk_ready), (n - 1) & 1u, cyc_wait2);
                     }
+                    if (!ok) break;
+                    tc::tc_fence_after();
                     tc::mma_commit(bar(B_ACC));
+                    if (tl && n < 512) tl[4 * n + 1] = clock64();
                 }
             }
         }
     } else {
         // ------------------------------------------------------------ epilogue
         // 8 warps: warp w reads tensor-memory lanes 32*(w%4) .. +31 (its 32 query rows)
-        // and one column half, [0, 112) or [112, 208), 32 columns per load.
+        // and, in every 32-column block b, the columns 32b + 16*half .. +15 (half = 0 for
+        // warps 2-5, 1 for warps 6-9).  All 7 chunks are loaded in one round trip; each
+        // finished block is published on its own barrier so the next layer's MMAs can
+        // start on it while later blocks are still being written.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
-        const int cbeg = half ? 112 : 0, cend = half ? NP : 112;
+        const int sw = (row >> 1) & 3;
         uint32_t n = 0;
         unsigned char* Osm = sm + OFF_O;
         unsigned char* Fsm = sm + OFF_F;
@@ -215,34 +223,31 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
                 ok = twait(bar(B_ACC), n & 1u, cyc_wait);
+                if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 2] = clock64();
                 if (!ok) break;
                 tc::tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u;
-                const float* bias = a.bias + l * NP;
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
+                float v[NBLK_H * 16];
+                tc::tmem_ld16x7(taddr, v);
                 const bool l1 = l < 20 && !(l & 1);
                 const bool resid = l < 20 && (l & 1) && l > 1;
                 unsigned char* dst = (l1 || l == 20) ? Fsm : Osm;
-                for (int cb = cbeg; cb < cend; cb += 32) {
-                    const int width = min(32, cend - cb);          // 32 or 16
-                    float v[32];
-                    if (width == 32) tc::tmem_ld32(taddr + cb, v);
-                    else tc::tmem_ld16(taddr + cb, v);
+                const float* bias = a.bias + l * NP;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (h * 16 >= width) break;
-                        float* w = v + 16 * h;
-                        const int c0 = cb + 16 * h;
+                for (int b = 0; b < NBLK_H; ++b) {
+                    const int c0 = 32 * b + 16 * half;
+                    float* w = v + 16 * b;
+                    if (c0 < NP) {
                         const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const float4 b = __ldg(b4 + q);
-                            w[4 * q] += b.x; w[4 * q + 1] += b.y; w[4 * q + 2] += b.z; w[4 * q + 3] += b.w;
+                            const float4 bb = __ldg(b4 + q);
+                            w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
                         }
                         // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
-                        unsigned char* rb = dst + (c0 / 32) * BLK_A + row * 64;
-                        const int u0 = (c0 % 32) / 8, sw = (row >> 1) & 3;
-                        uint4* d0 = reinterpret_cast<uint4*>(rb + ((u0 ^ sw) << 4));
-                        uint4* d1 = reinterpret_cast<uint4*>(rb + (((u0 + 1) ^ sw) << 4));
+                        unsigned char* rb = dst + b * BLK_A + row * 64;
+                        uint4* d0 = reinterpret_cast<uint4*>(rb + (((2 * half) ^ sw) << 4));
+                        uint4* d1 = reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ sw) << 4));
                         if (resid) {
                             const uint4 r0 = *d0, r1 = *d1;
                             const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&r0);
@@ -275,12 +280,13 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                             }
                             *d0 = p0;
                             *d1 = p1;
+                            tc::fence_proxy_async_smem();
                         }
                     }
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(bar(B_BLK + b));
                 }
-                if (l != 21) tc::fence_proxy_async_smem();
-                tc::tc_fence_before();
-                tc::mbar_arrive(bar(B_ACT));
+                if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
             if (!ok) break;
             // combine the two column halves of the output layer's dot product: the
@@ -439,7 +445,7 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     // (synchronises the stream; diagnostics only)
     static unsigned long long* trace_buf = nullptr;
     const bool tracing = getenv("RPNN_TC_TRACE") != nullptr;
-    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, 1024 * 12 * sizeof(unsigned long long)));
+    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, (1024 * 12 + 4 * 512) * sizeof(unsigned long long)));
     a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;
     if (!attr) {
@@ -448,7 +454,7 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
-    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, 1024 * 12 * sizeof(unsigned long long), s));
+    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, (1024 * 12 + 4 * 512) * sizeof(unsigned long long), s));
     k_rpnn_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
     if (tracing) {
@@ -462,6 +468,14 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
                 "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: wait_full %.0f "
                 "wait_act %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
                 grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
+        std::vector<long long> tlh(4 * 512);
+        RPNN_CUDA_TRY(cudaMemcpy(tlh.data(), trace_buf + 1024 * 12, tlh.size() * 8, cudaMemcpyDeviceToHost));
+        // block 0, second tile: per layer, issue span, issue->acc ready, epilogue span, gap
+        for (int n = 22; n < 44 && tlh[4 * n + 3]; ++n) {
+            const long long* q = &tlh[4 * n];
+            fprintf(stderr, "[rpnn tc timeline] layer %2d issue %6lld  to-acc %6lld  epi %6lld  next-issue-gap %6lld\n",
+                    n - 22, q[1] - q[0], q[2] - q[0], q[3] - q[2], n < 511 ? q[4] - q[1] : 0LL);
+        }
     }
     return RPNN_OK;
 }
