@@ -140,66 +140,75 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
+        // No shared-memory load and no wait result may sit between MMAs in this thread
+        // (each would stall behind the MMAs in flight): waits are output-free asm loops,
+        // the ring position lives in registers, and the abort flag is read once per tile.
         if (lane == 0 && !*abort_flag) {
             const uint32_t idesc = tc::idesc_bf16(TM, NP);
-            uint32_t uses[STAGES] = {};
-            uint32_t n = 0;     // layer instance
-            int s = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int l = 0; l < NLAYERS && ok; ++l, ++n) {
+            const uint32_t abort_addr = base + OFF_ABORT;
+            const bool trace = a.trace != nullptr;
+            // 64-bit operand descriptors are built once; an MMA only adds constants to them
+            // (the start-address field counts 16-byte units: +2 = +32 bytes = 16 columns)
+            const uint64_t d_ring = tc::smem_desc_sw64(base + OFF_RING);
+            const uint64_t d_O = tc::smem_desc_sw64(base + OFF_O);
+            const uint64_t d_F = tc::smem_desc_sw64(base + OFF_F);
+            constexpr uint64_t kStageStep = STAGE_BYTES >> 4, kZOff = STAGE_W >> 4, kBlkStep = BLK_A >> 4;
+            uint32_t n = 0;         // layer instance
+            uint32_t s = 0, ph = 0; // ring stage and its phase parity
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                for (int l = 0; l < NLAYERS; ++l, ++n) {
                     const uint32_t acc = tmem + (n & 1u) * 256u;
                     if (tl && n < 512) tl[4 * n] = clock64();
                     const bool l1 = l < 20 && !(l & 1);
                     const int kg = layer_kg(l);
+                    const uint64_t d_buf = (l1 || l == 20) ? d_O : d_F;
+                    const int zk = l1 ? KG_Z : 0;          // k-groups read from the descriptor tile
                     // Operands written by the previous epilogue (O or F) become ready one
                     // 32-column block at a time; wait for block b (phase n-1) right before
                     // the first k-step that reads it.  Every block phase is waited once per
                     // layer, so the issuer never runs two phases ahead of the epilogue.
                     int blk_ready = n > 0 ? -1 : NBLK_H - 1;
-                    for (int g0 = 0; g0 < kg && ok; g0 += CHUNK_KG) {
-                        const int cnt = min(CHUNK_KG, kg - g0);
-                        ok = twait(bar(B_WFULL + s), uses[s] & 1u, cyc_wait);
-                        if (!ok) break;
+                    for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
+                        const long long tw = trace ? clock64() : 0;
+                        tc::mbar_wait_issuer(bar(B_WFULL + s), ph, tc::kSpinLimit, abort_addr);
+                        if (trace) cyc_wait += (unsigned long long)(clock64() - tw);
                         tc::tc_fence_after();
-                        const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
-                        for (int j = 0; j < cnt; j += 2) {
+                        const uint64_t d_st = d_ring + s * kStageStep;
+#pragma unroll
+                        for (int j = 0; j < CHUNK_KG; j += 2) {
                             const int g = g0 + j;
-                            // K-step of 16 columns: 32-byte offset inside a 64-byte swizzled row
-                            const uint32_t koff = (uint32_t)(j >> 1) * 32u;
-                            uint32_t a_addr;
-                            if (l1 && g < KG_Z) a_addr = st + STAGE_W + koff;
+                            if (g >= kg) break;
+                            uint64_t d_a;
+                            if (g < zk) d_a = d_st + kZOff + (uint64_t)(j >> 1) * 2u;
                             else {
-                                const int gg = l1 ? g - KG_Z : g;      // k-group inside O or F
-                                const int blk = gg / CHUNK_KG;
-                                while (blk_ready < blk && ok) {
-                                    ++blk_ready;
-                                    ok = twait(bar(B_BLK + blk_ready), (n - 1) & 1u, cyc_wait2);
+                                const int gg = g - zk;             // k-group inside O or F
+                                const int blk = gg >> 2;
+                                if (blk_ready < blk) {
+                                    const long long tb = trace ? clock64() : 0;
+                                    while (blk_ready < blk) {
+                                        ++blk_ready;
+                                        tc::mbar_wait_issuer(bar(B_BLK + blk_ready), (n - 1) & 1u, tc::kSpinLimit,
+                                                             abort_addr);
+                                    }
+                                    if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
+                                    tc::tc_fence_after();
                                 }
-                                if (!ok) break;
-                                tc::tc_fence_after();
-                                const uint32_t buf = (l1 || l == 20) ? base + OFF_O : base + OFF_F;
-                                a_addr = buf + (uint32_t)blk * BLK_A + (uint32_t)((gg % CHUNK_KG) >> 1) * 32u;
+                                d_a = d_buf + (uint64_t)blk * kBlkStep + (uint64_t)((gg >> 1) & 1) * 2u;
                             }
-                            const uint64_t ad = tc::smem_desc_sw64(a_addr);
-                            const uint64_t bd = tc::smem_desc_sw64(st + koff);
-                            tc::mma_bf16(acc, ad, bd, idesc, g > 0 ? 1u : 0u);
+                            tc::mma_bf16(acc, d_a, d_st + (uint64_t)(j >> 1) * 2u, idesc, g > 0 ? 1u : 0u);
                         }
-                        if (!ok) break;
                         tc::mma_commit(bar(B_WEMPTY + s));
-                        ++uses[s];
-                        s = (s + 1) % STAGES;
+                        if (++s == STAGES) { s = 0; ph ^= 1u; }
                     }
-                    if (!ok) break;
-                    while (blk_ready < NBLK_H - 1 && ok) {
+                    while (blk_ready < NBLK_H - 1) {
                         ++blk_ready;
-                        ok = twait(bar(B_BLK + blk_ready), (n - 1) & 1u, cyc_wait2);
+                        tc::mbar_wait_issuer(bar(B_BLK + blk_ready), (n - 1) & 1u, tc::kSpinLimit, abort_addr);
                     }
-                    if (!ok) break;
                     tc::tc_fence_after();
                     tc::mma_commit(bar(B_ACC));
                     if (tl && n < 512) tl[4 * n + 1] = clock64();
                 }
+                if (*abort_flag) break;
             }
         }
     } else {

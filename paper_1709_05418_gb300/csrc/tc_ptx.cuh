@@ -36,11 +36,61 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
         : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
     return ok != 0;
 }
+// Polls the phase with the given parity at most `limit` times inside one asm statement
+// (a C++ loop around a single try_wait costs the issuing thread several hundred cycles
+// per wait, which starves the tensor pipe).  Returns the polls left: 0 = not complete.
+__device__ __forceinline__ uint32_t mbar_poll(uint32_t bar, uint32_t parity, uint32_t limit) {
+    uint32_t left;
+    asm volatile(
+        "{\n"
+        " .reg .pred P1;\n"
+        " mov.u32 %0, %3;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        " @P1 bra DONE_%=;\n"
+        " sub.u32 %0, %0, 1;\n"
+        " setp.ne.u32 P1, %0, 0;\n"
+        " @P1 bra WAIT_%=;\n"
+        "DONE_%=:\n"
+        "}\n"
+        : "=r"(left) : "r"(bar), "r"(parity), "r"(limit) : "memory");
+    return left;
+}
+
+// Wait for the phase with the given parity from the thread that issues tcgen05.mma.
+// The whole poll loop is one asm statement with no outputs: in that thread, a
+// shared-memory load or a wait whose result feeds later code stalls behind the MMAs in
+// flight (hundreds of cycles each), and the tensor pipe runs dry.  A poll that fails
+// reads the block's abort flag (at shared address abort_addr) and leaves if another role
+// has given up; after `limit` failed polls it stores 1 to that flag itself.  Callers
+// check the flag later, outside their issue loop.
+__device__ __forceinline__ void mbar_wait_issuer(uint32_t bar, uint32_t parity, uint32_t limit,
+                                                 uint32_t abort_addr) {
+    asm volatile(
+        "{\n"
+        " .reg .pred P1;\n"
+        " .reg .u32 c, f;\n"
+        " mov.u32 c, %2;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+        " @P1 bra DONE_%=;\n"
+        " ld.volatile.shared.u32 f, [%3];\n"
+        " setp.ne.u32 P1, f, 0;\n"
+        " @P1 bra DONE_%=;\n"
+        " sub.u32 c, c, 1;\n"
+        " setp.ne.u32 P1, c, 0;\n"
+        " @P1 bra WAIT_%=;\n"
+        " st.volatile.shared.u32 [%3], 1;\n"
+        "DONE_%=:\n"
+        "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr) : "memory");
+}
+
 // Bounded wait for the phase with the given parity.  Gives up (returns false) after
-// kSpinLimit polls or as soon as *abort is set by another role of the block.
+// about kSpinLimit polls, or soon after *abort is set by another role of the block.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        if (mbar_test(bar, parity)) return true;
+    constexpr uint32_t kBurst = 1u << 12;
+    for (uint32_t i = 0; i < kSpinLimit / kBurst; ++i) {
+        if (mbar_poll(bar, parity, kBurst)) return true;
         if (*abort) return false;
     }
     *abort = 1;

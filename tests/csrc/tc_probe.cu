@@ -168,24 +168,35 @@ __global__ void __launch_bounds__(128) k_probe_sw64(const __nv_bfloat16* __restr
 // mode bit 0: commit to an mbarrier after every second MMA; bit 1: N = 256 instead of
 // 208; bit 2: 64-byte swizzled descriptors instead of interleaved.  The operands are
 // zeros (only timing matters); clock64 brackets issue and completion.
-__global__ void __launch_bounds__(128) k_mma_rate(int nmma, int mode, long long* cycles, int* err) {
+__global__ void __launch_bounds__(512) k_mma_rate(int nmma, int mode, long long* cycles, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid / 32;
     const uint32_t base = smem_u32(sm);
     const uint32_t bar = base + 65536, bar2 = base + 65544;
-    for (int i = tid; i < 65536 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    // mode bit 5: warps beyond the first four exit at once
+    if ((mode & 32) && warp >= 4) return;
+    const int nthr = (mode & 32) ? min((int)blockDim.x, 128) : (int)blockDim.x;
+    for (int i = tid; i < 65536 / 16; i += nthr) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
     fence_proxy_async_smem();
     if (tid == 0) {
         abort_flag = 0;
         mbar_init(bar, 1);
         mbar_init(bar2, 1);
+        mbar_init(bar2 + 8, 1);
+        mbar_init(bar2 + 16, 1);
         fence_mbar_init();
     }
     if (warp == 0) { tmem_alloc(base + 65600, 256); tmem_relinquish(); }
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 65600);
+    // mode bit 3: warps 1..7 poll an mbarrier that only completes after the timed loop
+    // (warp 4 shares the issuing warp's scheduler)
+    // (the situation of epilogue / producer warps waiting while one thread issues MMAs)
+    if ((mode & 8) && warp > 0) {
+        if (!mbar_wait(bar2 + 8, 0, &abort_flag)) atomicOr(err, 4);
+    }
     if (tid == 0) {
         const int n = (mode & 2) ? 256 : 208;
         const uint32_t id = idesc_bf16(128, n);
@@ -194,9 +205,16 @@ __global__ void __launch_bounds__(128) k_mma_rate(int nmma, int mode, long long*
         const uint64_t b0 = sw ? smem_desc_sw64(base + 16384) : smem_desc(base + 16384, 4096, 128);
         uint32_t commits = 0;
         const long long t0 = clock64();
+        if (mode & 16) mbar_arrive(bar2 + 16);                     // phase 0 of bar3 completes now
         for (int i = 0; i < nmma; ++i) {
+            if ((mode & 16) && !(i & 1)) {
+                // what the network kernel does per ring stage: a (satisfied) wait and a fence
+                if (!mbar_wait(bar2 + 16, 0, &abort_flag)) atomicOr(err, 8);
+                tc_fence_after();
+            }
             const uint64_t off = (uint64_t)((i & 1) * 2);          // +32 bytes inside the row
-            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
+            const uint64_t blk = (mode & 16) ? (uint64_t)(((i >> 1) % 5) * (512 >> 4)) : 0;
+            mma_bf16(tmem, a0 + off + blk, b0 + off + blk, id, i > 0);
             if ((mode & 1) && (i & 1)) { mma_commit(bar2); ++commits; }
         }
         const long long t1 = clock64();
@@ -206,6 +224,203 @@ __global__ void __launch_bounds__(128) k_mma_rate(int nmma, int mode, long long*
         cycles[0] = t1 - t0;
         cycles[1] = t2 - t0;
         (void)commits;
+        if (mode & 8) mbar_arrive(bar2 + 8);
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+
+// ---- variants compiled separately: what in an MMA issue loop slows it down ----------
+// V=0 plain; V=1 satisfied mbarrier wait every 2 MMAs; V=2 tcgen05.fence::after_thread_sync
+// every 2 MMAs; V=3 one fence before the loop; V=4 commit every 2 MMAs; V=5 wait + commit
+// every 2 MMAs (no fence).
+template <int V>
+__global__ void __launch_bounds__(128) k_mma_variant(int nmma, long long* cycles, int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid / 32;
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bar = base + 65536, bar2 = base + 65544, bar3 = base + 65552;
+    for (int i = tid; i < 65536 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        mbar_init(bar2, 1);
+        mbar_init(bar3, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) { tmem_alloc(base + 65600, 256); tmem_relinquish(); }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 65600);
+    if (tid == 0) {
+        const uint32_t id = idesc_bf16(128, 208);
+        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
+        mbar_arrive(bar3);                                   // phase 0 of bar3 is complete
+        *reinterpret_cast<volatile uint32_t*>(sm + 65700) = 1u;   // counter already satisfied
+        if (V == 3) tc_fence_after();
+        const long long t0 = clock64();
+        for (int i = 0; i < nmma; ++i) {
+            if (!(i & 1)) {
+                if (V == 1 || V == 5) { if (!mbar_wait(bar3, 0, &abort_flag)) atomicOr(err, 8); }
+                if (V == 2) tc_fence_after();
+                if (V == 6) {   // relaxed try_wait
+                    uint32_t ok = 0;
+                    for (int it = 0; it < (1 << 20) && !ok; ++it)
+                        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n"
+                                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
+                }
+                if (V == 7 || V == 8) {   // test_wait (acquire / relaxed), non-suspending
+                    uint32_t ok = 0;
+                    for (int it = 0; it < (1 << 20) && !ok; ++it) {
+                        if (V == 7)
+                            asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                                         " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
+                        else
+                            asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n"
+                                         " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
+                    }
+                }
+                if (V == 9) {   // try_wait loop inside one asm statement (no C++ loop around it)
+                    asm volatile("{\n .reg .pred P1;\n WAIT_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+                                 " @!P1 bra WAIT_%=;\n}\n" :: "r"(bar3), "r"(0u) : "memory");
+                }
+            }
+            if (V == 10 && !(i & 3)) { if (!mbar_wait(bar3, 0, &abort_flag)) atomicOr(err, 8); }
+            if ((V == 13 || V == 14) && !(i & 1)) {
+                // poll a shared counter that another thread bumps after its own mbarrier wait
+                uint32_t seen = 0;
+                for (int it = 0; it < (1 << 20); ++it) {
+                    if (V == 13) seen = *reinterpret_cast<volatile uint32_t*>(sm + 65700);
+                    else asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(seen) : "r"(base + 65700) : "memory");
+                    if (seen >= 1u) break;
+                }
+                if (seen < 1u) atomicOr(err, 16);
+            }
+            if (V == 15 && !(i & 3))
+                asm volatile("{\n .reg .pred P1;\n .reg .u32 c;\n mov.u32 c, %2;\n"
+                             "W_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n @P1 bra D_%=;\n"
+                             " sub.u32 c, c, 1;\n setp.ne.u32 P1, c, 0;\n @P1 bra W_%=;\n"
+                             " st.shared.u32 [%3], 1;\n"
+                             "D_%=:\n}\n" :: "r"(bar3), "r"(0u), "r"(1u << 20), "r"(smem_u32(&abort_flag)) : "memory");
+            if ((V == 11 || V == 12) && !(i & 1)) {
+                // bounded poll with no output: on give-up it raises the abort flag itself
+                if (V == 11 || !abort_flag)
+                    asm volatile("{\n .reg .pred P1;\n .reg .u32 c;\n mov.u32 c, %2;\n"
+                                 "W_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n @P1 bra D_%=;\n"
+                                 " sub.u32 c, c, 1;\n setp.ne.u32 P1, c, 0;\n @P1 bra W_%=;\n"
+                                 " st.shared.u32 [%3], 1;\n"
+                                 "D_%=:\n}\n" :: "r"(bar3), "r"(0u), "r"(1u << 20), "r"(smem_u32(&abort_flag)) : "memory");
+            }
+            const uint64_t off = (uint64_t)((i & 1) * 2);
+            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
+            if ((V == 4 || V == 5) && (i & 1)) mma_commit(bar2);
+        }
+        const long long t1 = clock64();
+        mma_commit(bar);
+        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
+        cycles[0] = t1 - t0;
+        cycles[1] = clock64() - t0;
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+template <int V>
+int run_variant(int nmma, long long* cycles, int* err) {
+    if (cudaFuncSetAttribute(k_mma_variant<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
+    k_mma_variant<V><<<1, 128, SMEM>>>(nmma, cycles, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int tc_mma_variant(int v, int nmma, long long* cycles, int* err) {
+    switch (v) {
+        case 0: return run_variant<0>(nmma, cycles, err);
+        case 1: return run_variant<1>(nmma, cycles, err);
+        case 2: return run_variant<2>(nmma, cycles, err);
+        case 3: return run_variant<3>(nmma, cycles, err);
+        case 4: return run_variant<4>(nmma, cycles, err);
+        case 5: return run_variant<5>(nmma, cycles, err);
+        case 6: return run_variant<6>(nmma, cycles, err);
+        case 7: return run_variant<7>(nmma, cycles, err);
+        case 8: return run_variant<8>(nmma, cycles, err);
+        case 9: return run_variant<9>(nmma, cycles, err);
+        case 10: return run_variant<10>(nmma, cycles, err);
+        case 11: return run_variant<11>(nmma, cycles, err);
+        case 12: return run_variant<12>(nmma, cycles, err);
+        case 13: return run_variant<13>(nmma, cycles, err);
+        case 14: return run_variant<14>(nmma, cycles, err);
+        case 15: return run_variant<15>(nmma, cycles, err);
+        default: return -1;
+    }
+}
+
+namespace {
+
+// ---- MMA rate while another warp streams bulk copies into shared memory -------------
+// Warp 0 lane 0 issues nmma MMAs (operands at 0 .. 48 KB); warp 1 lane 0 keeps `inflight`
+// 13,312-byte bulk copies (from an L2-resident global buffer) landing in shared memory
+// at 96 .. 160 KB until the MMAs are done; warps 2-3 optionally (mode & 1) also store to
+// shared memory continuously (epilogue-like traffic).
+__global__ void __launch_bounds__(128) k_mma_with_copies(int nmma, int mode, const unsigned char* __restrict__ src,
+                                                          long long* cycles, int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    __shared__ volatile int done;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bar = base + 180224, barc = base + 180232;
+    for (int i = tid; i < 49152 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        abort_flag = 0;
+        done = 0;
+        mbar_init(bar, 1);
+        mbar_init(barc, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) { tmem_alloc(base + 180300, 256); tmem_relinquish(); }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 180300);
+    if (tid == 0) {
+        const uint32_t id = idesc_bf16(128, 208);
+        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
+        const long long t0 = clock64();
+        for (int i = 0; i < nmma; ++i) {
+            const uint64_t off = (uint64_t)((i & 1) * 2);
+            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
+        }
+        mma_commit(bar);
+        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
+        cycles[1] = clock64() - t0;
+        done = 1;
+    } else if (warp == 1 && lane == 0) {
+        long long copies = 0;
+        uint32_t ph = 0;
+        while (!done) {
+            mbar_expect_tx(barc, 4 * 13312);
+            for (int k = 0; k < 4; ++k)
+                bulk_g2s(base + 98304 + k * 13312, src + (size_t)(copies % 64) * 13312, 13312, barc);
+            if (!mbar_wait(barc, ph, &abort_flag)) { atomicOr(err, 2); break; }
+            ph ^= 1u;
+            copies += 4;
+        }
+        cycles[0] = copies;
+    } else if ((mode & 1) && warp >= 2) {
+        uint4* p = reinterpret_cast<uint4*>(sm + 163840 + (tid - 64) * 16);
+        long long k = 0;
+        while (!done) { p[0] = make_uint4((uint32_t)k, 1, 2, 3); p[64] = p[0]; ++k; }
     }
     __syncwarp();
     tc_fence_before();
@@ -215,9 +430,20 @@ __global__ void __launch_bounds__(128) k_mma_rate(int nmma, int mode, long long*
 
 }  // namespace
 
-extern "C" int tc_mma_rate(int nmma, int mode, long long* cycles, int* err) {
+extern "C" int tc_mma_with_copies(int nmma, int mode, const void* src, long long* cycles, int* err) {
+    if (cudaFuncSetAttribute(k_mma_with_copies, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
+    k_mma_with_copies<<<1, 128, SMEM>>>(nmma, mode, (const unsigned char*)src, cycles, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}
+
+namespace {
+}  // namespace
+
+extern "C" int tc_mma_rate(int nmma, int mode, long long* cycles, int* err, int nthreads) {
     if (cudaFuncSetAttribute(k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
-    k_mma_rate<<<1, 128, SMEM>>>(nmma, mode, cycles, err);
+    k_mma_rate<<<1, nthreads, SMEM>>>(nmma, mode, cycles, err);
     if (cudaGetLastError() != cudaSuccess) return -13;
     if (cudaDeviceSynchronize() != cudaSuccess) return -14;
     return 0;

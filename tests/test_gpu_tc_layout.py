@@ -103,19 +103,55 @@ def test_mma_sw64_layouts(probe):
 
 def test_mma_issue_rate(probe, capsys):
     """Back-to-back tcgen05.mma throughput on resident operands (reported, loosely checked)."""
-    probe.tc_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    probe.tc_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     rates = {}
-    for mode, name in [(0, "interleaved N208"), (4, "sw64 N208"), (6, "sw64 N256"), (5, "sw64 N208 commit/2")]:
+    cases = [(4, 128, "sw64 N208, 4 warps"), (6, 128, "sw64 N256, 4 warps"), (4, 160, "sw64 N208, 5 warps"),
+             (4, 192, "sw64 N208, 6 warps"), (4, 256, "sw64 N208, 8 warps"), (4, 320, "sw64 N208, 10 warps"),
+             (4 | 32, 256, "8 warps, 4 exit early"), (4 | 16, 128, "4 warps, wait+fence per 2"),
+             (4 | 8, 256, "8 warps, 7 polling")]
+    for mode, nt, name in cases:
         n = 4096
-        assert probe.tc_mma_rate(n, mode, cyc.data_ptr(), err.data_ptr()) == 0
+        assert probe.tc_mma_rate(n, mode, cyc.data_ptr(), err.data_ptr(), nt) == 0
         assert err.item() == 0
         issue, done = cyc.cpu().tolist()
         macs = 128 * (256 if mode & 2 else 208) * 16
         rates[name] = (issue / n, done / n, macs / (done / n))
     with capsys.disabled():
         for k, (i, d, r) in rates.items():
-            print(f"\n[mma rate] {k:22s} issue {i:7.1f} cyc/mma  complete {d:7.1f} cyc/mma  {r:7.0f} MAC/clk")
+            print(f"\n[mma rate] {k:28s} issue {i:7.1f} cyc/mma  complete {d:7.1f} cyc/mma  {r:7.0f} MAC/clk")
     for _, d, _ in rates.values():
         assert d > 0
+
+
+def test_mma_issue_loop_variants(probe, capsys):
+    probe.tc_mma_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    names = ["plain", "wait/2", "fence::after/2", "fence before loop", "commit/2", "wait+commit/2",
+             "relaxed try_wait/2", "test_wait/2", "relaxed test_wait/2", "asm try_wait loop/2", "wait/4",
+             "bounded asm, no output/2", "abort check + bounded/2", "volatile counter poll/2",
+             "acquire counter poll/2", "bounded asm, no output/4"]
+    out = []
+    for v, name in enumerate(names):
+        assert probe.tc_mma_variant(v, 4096, cyc.data_ptr(), err.data_ptr()) == 0
+        assert err.item() == 0
+        out.append((name, cyc.cpu().tolist()[1] / 4096))
+    with capsys.disabled():
+        for name, c in out:
+            print(f"\n[mma loop] {name:20s} {c:7.1f} cyc/mma")
+
+
+def test_mma_rate_with_concurrent_copies(probe, capsys):
+    probe.tc_mma_with_copies.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
+    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for mode, name in [(0, "bulk copies"), (1, "bulk copies + smem stores")]:
+        assert probe.tc_mma_with_copies(4096, mode, src.data_ptr(), cyc.data_ptr(), err.data_ptr()) == 0
+        assert err.item() == 0
+        copies, c = cyc.cpu().tolist()
+        with capsys.disabled():
+            print(f"\n[mma + traffic] {name:26s} {c / 4096:7.1f} cyc/mma, {copies} copies of 13 KB "
+                  f"({copies * 13312 / c:5.1f} B/clk)")
