@@ -51,15 +51,19 @@ constexpr uint32_t OFF_O = 0;
 constexpr uint32_t OFF_F = OFF_O + NBLK_H * BLK_A;             // 57344
 constexpr uint32_t OFF_RING = OFF_F + NBLK_H * BLK_A;          // 114688
 constexpr uint32_t OFF_BAR = OFF_RING + STAGES * STAGE_BYTES;  // 222208
-constexpr uint32_t SMEM_BYTES = OFF_BAR + 256 + 2 * 128 * 4;
+// every mbarrier gets its own 128-byte line: barriers the MMA issuer waits on must not
+// share a line with barriers other warps poll or arrive on (those operations serialise)
+constexpr uint32_t BAR_STRIDE = 128;
 constexpr int EPI_THREADS = 256;         // 8 epilogue warps
+constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int NTHREADS = 64 + EPI_THREADS;
 
-// barrier slots (8 bytes each) from OFF_BAR
+// barrier slots from OFF_BAR, BAR_STRIDE bytes apart
 enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_BLK, B_PART = B_BLK + NBLK_H, B_COUNT };
-constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + 8 * B_COUNT;
+constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
 constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 128 floats
+constexpr uint32_t SMEM_BYTES = OFF_PART + 128 * 4 + 64;
 
 struct TcArgs {
     const __nv_bfloat16* img;   // weight image
@@ -83,7 +87,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = tc::smem_u32(sm);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_ABORT);
-    auto bar = [&](int i) { return base + OFF_BAR + 8u * (uint32_t)i; };
+    auto bar = [&](int i) { return base + OFF_BAR + BAR_STRIDE * (uint32_t)i; };
     // diagnostics: cycles spent in each role's waits, when a.trace is set, and for block
     // 0 a timeline of 4 stamps per layer instance (MMA issue start/end, epilogue start/end)
     long long* tl = (a.trace && blockIdx.x == 0) ? reinterpret_cast<long long*>(a.trace + 1024 * 12) : nullptr;
@@ -102,8 +106,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         *abort_flag = (base & 1023u) ? 1 : 0;
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
         tc::mbar_init(bar(B_ACC), 1);
-        for (int b = 0; b < NBLK_H; ++b) tc::mbar_init(bar(B_BLK + b), EPI_THREADS);
-        tc::mbar_init(bar(B_PART), EPI_THREADS / 2);
+        for (int b = 0; b < NBLK_H; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
+        tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
         tc::fence_mbar_init();
     }
     if (warp == 1) {
@@ -159,6 +163,12 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 for (int l = 0; l < NLAYERS; ++l, ++n) {
                     const uint32_t acc = tmem + (n & 1u) * 256u;
                     if (tl && n < 512) tl[4 * n] = clock64();
+                    // One tcgen05 fence per layer orders this layer's MMAs (which overwrite
+                    // accumulator n % 2) after the waits that saw epilogue n-2 finish reading
+                    // it.  Data written by TMA or by the epilogue (fence.proxy.async + mbarrier)
+                    // needs no tcgen05 fence, and a fence after every wait costs the issuing
+                    // thread ~200 cycles each time.
+                    tc::tc_fence_after();
                     const bool l1 = l < 20 && !(l & 1);
                     const int kg = layer_kg(l);
                     const uint64_t d_buf = (l1 || l == 20) ? d_O : d_F;
@@ -168,11 +178,12 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     // the first k-step that reads it.  Every block phase is waited once per
                     // layer, so the issuer never runs two phases ahead of the epilogue.
                     int blk_ready = n > 0 ? -1 : NBLK_H - 1;
+                    long long* cs = (tl && (n == 23 || n == 24)) ? tl + 4 * 512 + (n - 23) * 64 : nullptr;
                     for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
                         const long long tw = trace ? clock64() : 0;
                         tc::mbar_wait_issuer(bar(B_WFULL + s), ph, tc::kSpinLimit, abort_addr);
                         if (trace) cyc_wait += (unsigned long long)(clock64() - tw);
-                        tc::tc_fence_after();
+                        if (cs) { cs[(g0 / 4) * 4] = tw; cs[(g0 / 4) * 4 + 1] = clock64(); }
                         const uint64_t d_st = d_ring + s * kStageStep;
 #pragma unroll
                         for (int j = 0; j < CHUNK_KG; j += 2) {
@@ -191,20 +202,19 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                                                              abort_addr);
                                     }
                                     if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
-                                    tc::tc_fence_after();
                                 }
                                 d_a = d_buf + (uint64_t)blk * kBlkStep + (uint64_t)((gg >> 1) & 1) * 2u;
                             }
                             tc::mma_bf16(acc, d_a, d_st + (uint64_t)(j >> 1) * 2u, idesc, g > 0 ? 1u : 0u);
                         }
                         tc::mma_commit(bar(B_WEMPTY + s));
+                        if (cs) cs[(g0 / 4) * 4 + 2] = clock64();
                         if (++s == STAGES) { s = 0; ph ^= 1u; }
                     }
                     while (blk_ready < NBLK_H - 1) {
                         ++blk_ready;
                         tc::mbar_wait_issuer(bar(B_BLK + blk_ready), (n - 1) & 1u, tc::kSpinLimit, abort_addr);
                     }
-                    tc::tc_fence_after();
                     tc::mma_commit(bar(B_ACC));
                     if (tl && n < 512) tl[4 * n + 1] = clock64();
                 }
@@ -231,7 +241,9 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             float dot = 0.0f;
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
-                ok = twait(bar(B_ACC), n & 1u, cyc_wait);
+                // one poller per warp: lane 0 waits, the warp follows
+                if (lane == 0) ok = twait(bar(B_ACC), n & 1u, cyc_wait);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 2] = clock64();
                 if (!ok) break;
                 tc::tc_fence_after();
@@ -293,7 +305,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         }
                     }
                     tc::tc_fence_before();
-                    tc::mbar_arrive(bar(B_BLK + b));
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bar(B_BLK + b));
                 }
                 if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
@@ -302,7 +315,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             // second half publishes its partial sums, the first half adds them (bounded wait)
             if (half) {
                 part[row] = dot;
-                tc::mbar_arrive(bar(B_PART));
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(bar(B_PART));
             } else {
                 if (!tc::mbar_wait(bar(B_PART), tile_iter & 1u, abort_flag)) break;
                 const int64_t r = (int64_t)t * TM + row;
@@ -454,7 +468,7 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     // (synchronises the stream; diagnostics only)
     static unsigned long long* trace_buf = nullptr;
     const bool tracing = getenv("RPNN_TC_TRACE") != nullptr;
-    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, (1024 * 12 + 4 * 512) * sizeof(unsigned long long)));
+    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long)));
     a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;
     if (!attr) {
@@ -463,7 +477,7 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
-    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, (1024 * 12 + 4 * 512) * sizeof(unsigned long long), s));
+    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long), s));
     k_rpnn_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
     if (tracing) {
@@ -477,8 +491,14 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
                 "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: wait_full %.0f "
                 "wait_act %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
                 grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
-        std::vector<long long> tlh(4 * 512);
+        std::vector<long long> tlh(4 * 512 + 128);
         RPNN_CUDA_TRY(cudaMemcpy(tlh.data(), trace_buf + 1024 * 12, tlh.size() * 8, cudaMemcpyDeviceToHost));
+        for (int inst = 0; inst < 2; ++inst) {
+            const long long* c = &tlh[4 * 512 + inst * 64];
+            for (int k = 0; k < 14 && c[4 * k]; ++k)
+                fprintf(stderr, "[rpnn tc chunks] inst %d chunk %2d  wait %6lld  issue %6lld  since-start %7lld\n", 23 + inst, k,
+                        c[4 * k + 1] - c[4 * k], c[4 * k + 2] - c[4 * k + 1], c[4 * k] - c[0]);
+        }
         // block 0, second tile: per layer, issue span, issue->acc ready, epilogue span, gap
         for (int n = 22; n < 44 && tlh[4 * n + 3]; ++n) {
             const long long* q = &tlh[4 * n];

@@ -421,6 +421,23 @@ __global__ void __launch_bounds__(128) k_mma_with_copies(int nmma, int mode, con
         uint4* p = reinterpret_cast<uint4*>(sm + 163840 + (tid - 64) * 16);
         long long k = 0;
         while (!done) { p[0] = make_uint4((uint32_t)k, 1, 2, 3); p[64] = p[0]; ++k; }
+    } else if ((mode & 2) && warp >= 2) {
+        // tensor-memory reads of columns 208..255 (not written by the MMAs) in a loop
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 208u;
+        float acc = 0.0f;
+        while (!done) {
+            float v[32];
+            tmem_ld32(ta, v);
+            for (int i = 0; i < 32; ++i) acc += v[i];
+        }
+        if (acc == 12345.0f) atomicOr(err, 64);
+    } else if ((mode & 4) && warp >= 2) {
+        // generic stores of zeros over the A operand the MMAs read, then proxy fences
+        uint4* p = reinterpret_cast<uint4*>(sm + (tid - 64) * 16);
+        while (!done) {
+            for (int k = 0; k < 8; ++k) p[k * 64] = make_uint4(0, 0, 0, 0);
+            fence_proxy_async_smem();
+        }
     }
     __syncwarp();
     tc_fence_before();

@@ -148,7 +148,8 @@ def test_mma_rate_with_concurrent_copies(probe, capsys):
     src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
     cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for mode, name in [(0, "bulk copies"), (1, "bulk copies + smem stores")]:
+    for mode, name in [(0, "bulk copies"), (1, "bulk copies + smem stores"), (2, "bulk copies + tmem loads"),
+                       (4, "bulk copies + A rewrites")]:
         assert probe.tc_mma_with_copies(4096, mode, src.data_ptr(), cyc.data_ptr(), err.data_ptr()) == 0
         assert err.item() == 0
         copies, c = cyc.cpu().tolist()
