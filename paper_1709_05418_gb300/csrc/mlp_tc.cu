@@ -7,13 +7,19 @@
 //   output:   g = relu(T3 . o12 + bT3)  (CUDA cores, in the last epilogue)
 // Widths are padded to N = 208 (zero rows) and the descriptor level to K = 240.
 //
-// Roles (320 threads): warp 0 streams weights (1-D bulk copies of a pre-arranged BF16
-// image through a 5-stage ring; a stage of a block's first layer also carries the matching
-// descriptor k-groups as 2-D TMA boxes of 8 columns x 128 queries); warp 1 allocates
-// tensor memory and one lane issues tcgen05.mma into two alternating FP32 accumulators
-// (so the z-part of a block's first layer overlaps the previous epilogue); warps 2-9
-// are the epilogue: tensor memory -> registers, bias / residual / ReLU, BF16 operands
-// written back to shared memory for the next layer.
+// Roles (320 threads): warp 0 streams operands through two rings -- weights (64 K-columns
+// of the pre-arranged BF16 image per stage, one bulk copy) and, for a block's first layer,
+// descriptor tiles (64 columns x 128 queries per stage, two 2-D TMA boxes); warp 1
+// allocates tensor memory and one lane issues tcgen05.mma, four K = 16 steps per stage,
+// into two alternating FP32 accumulators (so the descriptor part of a block's first layer
+// overlaps the previous epilogue); warps 2-9 are the epilogue: tensor memory -> registers,
+// bias / ReLU, BF16 activations written back to shared memory for the next layer.
+//
+// One activation buffer X serves every layer: a layer's epilogue starts only after all
+// of that layer's MMAs (the readers of X) have completed.  The residual o^{k-1} of a
+// block's second layer therefore cannot stay in X; the previous second layer's epilogue
+// writes o^{k-1} (FP32) back into its accumulator instead, and the next second layer
+// accumulates onto it.
 //
 // Operand layout in shared memory (K-major, 64-byte swizzle): blocks of 32 columns; in a
 // block, row r occupies 64 bytes at r * 64 and its 16-byte unit j (columns 8j..8j+7)
@@ -36,34 +42,36 @@ namespace {
 constexpr int TM = 128;                 // query rows per tile
 constexpr int NP = 208;                 // padded layer width
 constexpr int NLAYERS = 22;             // tensor-core layers
-constexpr int KG_Z = 30;                // 240 / 8 descriptor k-groups per level
-constexpr int KG_H = 26;                // 208 / 8 hidden k-groups
-constexpr int CHUNK_KG = 4;             // k-groups per weight stage
-constexpr int STAGES = 5;
-constexpr uint32_t BLK_A = TM * 64;               // 8192: 32 columns of 128 rows
-constexpr uint32_t BLK_B = NP * 64;               // 13312: 32 columns of 208 rows
-constexpr int NBLK_H = 7;                         // 32-column blocks of a 208-wide operand
-// a ring stage holds up to 4 weight k-groups and, for the descriptor part of a block's
-// first layer, the matching 4 k-groups of the 128-query descriptor tile
-constexpr uint32_t STAGE_W = BLK_B;                            // 13312
-constexpr uint32_t STAGE_BYTES = STAGE_W + BLK_A;              // 21504 (multiple of 512)
-constexpr uint32_t OFF_O = 0;
-constexpr uint32_t OFF_F = OFF_O + NBLK_H * BLK_A;             // 57344
-constexpr uint32_t OFF_RING = OFF_F + NBLK_H * BLK_A;          // 114688
-constexpr uint32_t OFF_BAR = OFF_RING + STAGES * STAGE_BYTES;  // 222208
-// every mbarrier gets its own 128-byte line: barriers the MMA issuer waits on must not
-// share a line with barriers other warps poll or arrive on (those operations serialise)
-constexpr uint32_t BAR_STRIDE = 128;
+constexpr int KZ = 240;                 // padded descriptor level (226 used)
+constexpr int SK = 64;                  // K columns per ring stage: four K = 16 MMAs
+constexpr uint32_t BLK_A = TM * 64;     // 8192: 32 columns of 128 rows
+constexpr uint32_t BLK_B = NP * 64;     // 13312: 32 columns of 208 rows
+constexpr int NBLK = 7;                 // 32-column blocks of a 208-wide activation
+constexpr int W_STAGES = 4, Z_STAGES = 3;
+constexpr uint32_t W_STAGE = 2 * BLK_B;                        // 26624
+constexpr uint32_t Z_STAGE = 2 * BLK_A;                        // 16384
+constexpr uint32_t OFF_X = 0;
+constexpr uint32_t OFF_W = OFF_X + NBLK * BLK_A;               // 57344
+constexpr uint32_t OFF_Z = OFF_W + W_STAGES * W_STAGE;         // 163840
+constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 212992
+constexpr uint32_t BAR_STRIDE = 16;
 constexpr int EPI_THREADS = 256;         // 8 epilogue warps
 constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int NTHREADS = 64 + EPI_THREADS;
 
-// barrier slots from OFF_BAR, BAR_STRIDE bytes apart
-enum { B_WFULL = 0, B_WEMPTY = STAGES, B_ACC = 2 * STAGES, B_BLK, B_PART = B_BLK + NBLK_H, B_COUNT };
+// barrier slots from OFF_BAR, BAR_STRIDE bytes apart; B_DONE completes its phase 0 at
+// setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
+enum {
+    B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES, B_ZEMPTY = B_ZFULL + Z_STAGES,
+    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NBLK, B_DONE, B_COUNT
+};
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
 constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 128 floats
 constexpr uint32_t SMEM_BYTES = OFF_PART + 128 * 4 + 64;
+static_assert(OFF_W % 1024 == 0 && OFF_Z % 1024 == 0 && W_STAGE % 1024 == 0 && Z_STAGE % 1024 == 0,
+              "swizzled operand blocks must stay 1024-byte aligned");
+static_assert(SMEM_BYTES <= 232448, "shared memory over the per-block limit");
 
 struct TcArgs {
     const __nv_bfloat16* img;   // weight image
@@ -77,9 +85,19 @@ struct TcArgs {
     unsigned long long* trace;  // optional per-block cycle counters (diagnostics), or null
 };
 
-__host__ __device__ constexpr int layer_kg(int l) {
-    return l == 0 ? KG_Z : (l < 20 ? ((l & 1) ? KG_H : KG_Z + KG_H) : KG_H);
+// K extent of layer l: a block's first layer reads [z | o] (240 + 208 columns; block 0
+// has no o), every other layer reads the 208-wide activation.
+__host__ __device__ constexpr int layer_k(int l) {
+    return l == 0 ? KZ : ((l < 20 && !(l & 1)) ? KZ + NP : NP);
 }
+// leading K columns of layer l that come from the descriptor tile
+__host__ __device__ constexpr int layer_zk(int l) { return (l < 20 && !(l & 1)) ? KZ : 0; }
+// 32-column blocks of layer l's weight image
+__host__ __device__ constexpr int layer_blocks(int l) { return (layer_k(l) + 31) / 32; }
+// second layers k >= 1 of a block add the residual o^{k-1}: their accumulator starts
+// from it (written back by the epilogue of second layer k-1)
+__host__ __device__ constexpr bool layer_resid(int l) { return (l & 1) && l >= 3 && l < 20; }
+__host__ __device__ constexpr bool layer_keeps_o(int l) { return (l & 1) && l < 18; }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
@@ -104,11 +122,14 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
 
     if (tid == 0) {
         *abort_flag = (base & 1023u) ? 1 : 0;
-        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
+        for (int s = 0; s < W_STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
+        for (int s = 0; s < Z_STAGES; ++s) { tc::mbar_init(bar(B_ZFULL + s), 1); tc::mbar_init(bar(B_ZEMPTY + s), 1); }
         tc::mbar_init(bar(B_ACC), 1);
-        for (int b = 0; b < NBLK_H; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
+        for (int b = 0; b < NBLK; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
+        tc::mbar_init(bar(B_DONE), 1);
         tc::fence_mbar_init();
+        tc::mbar_arrive(bar(B_DONE));
     }
     if (warp == 1) {
         tc::tmem_alloc(base + OFF_TMEM_SLOT, 512);
@@ -121,23 +142,30 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
+        // Stages are filled in the order the issuer consumes them; ring positions and
+        // phases live in registers.
         if (lane == 0 && !*abort_flag) {
-            uint32_t fills[STAGES] = {};
-            int s = 0;
+            uint32_t sw = 0, pw = 0, sz = 0, pz = 0;
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS && !*abort_flag; ++l) {
-                    const bool l1 = l < 20 && !(l & 1);      // reads descriptor level l/2
-                    const int kg = layer_kg(l);
-                    for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
-                        const bool hz = l1 && g0 < KG_Z;        // stage carries descriptor columns
-                        if (!twait(bar(B_WEMPTY + s), (fills[s] & 1u) ^ 1u, cyc_wait)) break;
-                        const uint32_t st = base + OFF_RING + s * STAGE_BYTES;
-                        tc::mbar_expect_tx(bar(B_WFULL + s), BLK_B + (hz ? BLK_A : 0u));
-                        tc::bulk_g2s(st, a.img + a.img_off[l] + (int64_t)(g0 / CHUNK_KG) * (BLK_B / 2), BLK_B,
-                                     bar(B_WFULL + s));
-                        if (hz) tc::tma_load_2d(st + STAGE_W, &zmap, (l / 2) * 240 + 8 * g0, t * TM, bar(B_WFULL + s));
-                        ++fills[s];
-                        s = (s + 1) % STAGES;
+                    const int K = layer_k(l), zk = layer_zk(l), nb = layer_blocks(l);
+                    for (int k0 = 0; k0 < K; k0 += SK) {
+                        if (k0 < zk) {
+                            if (!twait(bar(B_ZEMPTY + sz), pz ^ 1u, cyc_wait)) break;
+                            const uint32_t st = base + OFF_Z + sz * Z_STAGE;
+                            const int x = (l / 2) * KZ + k0;    // level l/2, columns k0 .. k0+63
+                            tc::mbar_expect_tx(bar(B_ZFULL + sz), Z_STAGE);
+                            tc::tma_load_2d(st, &zmap, x, t * TM, bar(B_ZFULL + sz));
+                            tc::tma_load_2d(st + BLK_A, &zmap, x + 32, t * TM, bar(B_ZFULL + sz));
+                            if (++sz == Z_STAGES) { sz = 0; pz ^= 1u; }
+                        }
+                        const int b0 = k0 / 32;
+                        const uint32_t bytes = (nb - b0 >= 2 ? 2u : 1u) * BLK_B;
+                        if (!twait(bar(B_WEMPTY + sw), pw ^ 1u, cyc_wait)) break;
+                        tc::mbar_expect_tx(bar(B_WFULL + sw), bytes);
+                        tc::bulk_g2s(base + OFF_W + sw * W_STAGE, a.img + a.img_off[l] + (int64_t)b0 * (BLK_B / 2),
+                                     bytes, bar(B_WFULL + sw));
+                        if (++sw == W_STAGES) { sw = 0; pw ^= 1u; }
                     }
                 }
             }
@@ -146,74 +174,74 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // ------------------------------------------------------------ MMA issuer
         // No shared-memory load and no wait result may sit between MMAs in this thread
         // (each would stall behind the MMAs in flight): waits are output-free asm loops,
-        // the ring position lives in registers, and the abort flag is read once per tile.
+        // one per stage of four MMAs, covering the weight stage, the descriptor stage and
+        // the activation block the stage needs; the abort flag is read once per tile.
         if (lane == 0 && !*abort_flag) {
             const uint32_t idesc = tc::idesc_bf16(TM, NP);
             const uint32_t abort_addr = base + OFF_ABORT;
+            const uint32_t none = bar(B_DONE);
             const bool trace = a.trace != nullptr;
             // 64-bit operand descriptors are built once; an MMA only adds constants to them
             // (the start-address field counts 16-byte units: +2 = +32 bytes = 16 columns)
-            const uint64_t d_ring = tc::smem_desc_sw64(base + OFF_RING);
-            const uint64_t d_O = tc::smem_desc_sw64(base + OFF_O);
-            const uint64_t d_F = tc::smem_desc_sw64(base + OFF_F);
-            constexpr uint64_t kStageStep = STAGE_BYTES >> 4, kZOff = STAGE_W >> 4, kBlkStep = BLK_A >> 4;
-            uint32_t n = 0;         // layer instance
-            uint32_t s = 0, ph = 0; // ring stage and its phase parity
+            const uint64_t d_W = tc::smem_desc_sw64(base + OFF_W);
+            const uint64_t d_Z = tc::smem_desc_sw64(base + OFF_Z);
+            const uint64_t d_X = tc::smem_desc_sw64(base + OFF_X);
+            uint32_t n = 0;                          // layer instance
+            uint32_t sw = 0, pw = 0, sz = 0, pz = 0; // ring positions and phases
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS; ++l, ++n) {
                     const uint32_t acc = tmem + (n & 1u) * 256u;
                     if (tl && n < 512) tl[4 * n] = clock64();
-                    // One tcgen05 fence per layer orders this layer's MMAs (which overwrite
-                    // accumulator n % 2) after the waits that saw epilogue n-2 finish reading
-                    // it.  Data written by TMA or by the epilogue (fence.proxy.async + mbarrier)
-                    // needs no tcgen05 fence, and a fence after every wait costs the issuing
-                    // thread ~200 cycles each time.
+                    // One tcgen05 fence per layer orders this layer's MMAs after the waits
+                    // (in the previous layer) that saw epilogue n-2 finish with accumulator
+                    // n % 2.  Operands written by TMA or by the epilogue (fence.proxy.async +
+                    // mbarrier) need no tcgen05 fence.
                     tc::tc_fence_after();
-                    const bool l1 = l < 20 && !(l & 1);
-                    const int kg = layer_kg(l);
-                    const uint64_t d_buf = (l1 || l == 20) ? d_O : d_F;
-                    const int zk = l1 ? KG_Z : 0;          // k-groups read from the descriptor tile
-                    // Operands written by the previous epilogue (O or F) become ready one
-                    // 32-column block at a time; wait for block b (phase n-1) right before
-                    // the first k-step that reads it.  Every block phase is waited once per
-                    // layer, so the issuer never runs two phases ahead of the epilogue.
-                    int blk_ready = n > 0 ? -1 : NBLK_H - 1;
-                    long long* cs = (tl && (n == 23 || n == 24)) ? tl + 4 * 512 + (n - 23) * 64 : nullptr;
-                    for (int g0 = 0; g0 < kg; g0 += CHUNK_KG) {
+                    const int K = layer_k(l), zk = layer_zk(l);
+                    const uint32_t first_acc = layer_resid(l) ? 1u : 0u;
+                    // Activation block b of epilogue n-1 is published on B_BLK + b; the
+                    // epilogue warps publish blocks in order, so a completed block also
+                    // covers every block before it.
+                    const uint32_t pb = (n - 1) & 1u;
+                    int blk_ready = n > 0 ? -1 : NBLK - 1;
+                    for (int k0 = 0; k0 < K; k0 += SK) {
+                        const int k1 = min(K, k0 + SK);
+                        const bool hz = k0 < zk;
+                        const int need = k1 > zk ? (k1 - zk - 1) >> 5 : -1;
+                        uint32_t b2 = none, p2 = 0;
+                        if (need > blk_ready) { b2 = bar(B_BLK + need); p2 = pb; blk_ready = need; }
                         const long long tw = trace ? clock64() : 0;
-                        tc::mbar_wait_issuer(bar(B_WFULL + s), ph, tc::kSpinLimit, abort_addr);
+                        tc::mbar_wait_issuer3(bar(B_WFULL + sw), pw, hz ? bar(B_ZFULL + sz) : none, hz ? pz : 0u, b2, p2,
+                                              tc::kSpinLimit, abort_addr);
                         if (trace) cyc_wait += (unsigned long long)(clock64() - tw);
-                        if (cs) { cs[(g0 / 4) * 4] = tw; cs[(g0 / 4) * 4 + 1] = clock64(); }
-                        const uint64_t d_st = d_ring + s * kStageStep;
+                        const uint64_t d_w = d_W + sw * (uint64_t)(W_STAGE >> 4);
+                        const uint64_t d_z = d_Z + sz * (uint64_t)(Z_STAGE >> 4);
 #pragma unroll
-                        for (int j = 0; j < CHUNK_KG; j += 2) {
-                            const int g = g0 + j;
-                            if (g >= kg) break;
+                        for (int j = 0; j < SK / 16; ++j) {
+                            const int k = k0 + 16 * j;
+                            if (k >= k1) break;
+                            const uint64_t d_b = d_w + (uint64_t)(j >> 1) * (BLK_B >> 4) + (uint64_t)(j & 1) * 2u;
                             uint64_t d_a;
-                            if (g < zk) d_a = d_st + kZOff + (uint64_t)(j >> 1) * 2u;
+                            if (k < zk) d_a = d_z + (uint64_t)(j >> 1) * (BLK_A >> 4) + (uint64_t)(j & 1) * 2u;
                             else {
-                                const int gg = g - zk;             // k-group inside O or F
-                                const int blk = gg >> 2;
-                                if (blk_ready < blk) {
-                                    const long long tb = trace ? clock64() : 0;
-                                    while (blk_ready < blk) {
-                                        ++blk_ready;
-                                        tc::mbar_wait_issuer(bar(B_BLK + blk_ready), (n - 1) & 1u, tc::kSpinLimit,
-                                                             abort_addr);
-                                    }
-                                    if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
-                                }
-                                d_a = d_buf + (uint64_t)blk * kBlkStep + (uint64_t)((gg >> 1) & 1) * 2u;
+                                const int c = k - zk;              // column of the activation
+                                d_a = d_X + (uint64_t)(c >> 5) * (BLK_A >> 4) + (uint64_t)((c >> 4) & 1) * 2u;
                             }
-                            tc::mma_bf16(acc, d_a, d_st + (uint64_t)(j >> 1) * 2u, idesc, g > 0 ? 1u : 0u);
+                            tc::mma_bf16(acc, d_a, d_b, idesc, k > 0 ? 1u : first_acc);
                         }
-                        tc::mma_commit(bar(B_WEMPTY + s));
-                        if (cs) cs[(g0 / 4) * 4 + 2] = clock64();
-                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                        tc::mma_commit(bar(B_WEMPTY + sw));
+                        if (++sw == W_STAGES) { sw = 0; pw ^= 1u; }
+                        if (hz) {
+                            tc::mma_commit(bar(B_ZEMPTY + sz));
+                            if (++sz == Z_STAGES) { sz = 0; pz ^= 1u; }
+                        }
                     }
-                    while (blk_ready < NBLK_H - 1) {
-                        ++blk_ready;
-                        tc::mbar_wait_issuer(bar(B_BLK + blk_ready), (n - 1) & 1u, tc::kSpinLimit, abort_addr);
+                    // a layer that reads no activation (a tile's first) still waits for the
+                    // previous epilogue, so the issuer never runs two phases ahead of it
+                    if (blk_ready < NBLK - 1) {
+                        const long long tb = trace ? clock64() : 0;
+                        tc::mbar_wait_issuer(bar(B_BLK + NBLK - 1), pb, tc::kSpinLimit, abort_addr);
+                        if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
                     }
                     tc::mma_commit(bar(B_ACC));
                     if (tl && n < 512) tl[4 * n + 1] = clock64();
@@ -233,8 +261,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         const int row = quarter * 32 + lane;
         const int sw = (row >> 1) & 3;
         uint32_t n = 0;
-        unsigned char* Osm = sm + OFF_O;
-        unsigned char* Fsm = sm + OFF_F;
+        unsigned char* Xsm = sm + OFF_X;
         float* part = reinterpret_cast<float*>(sm + OFF_PART);     // [TM] partial dots
         uint32_t tile_iter = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -248,14 +275,12 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
-                float v[NBLK_H * 16];
+                float v[NBLK * 16];
                 tc::tmem_ld16x7(taddr, v);
-                const bool l1 = l < 20 && !(l & 1);
-                const bool resid = l < 20 && (l & 1) && l > 1;
-                unsigned char* dst = (l1 || l == 20) ? Fsm : Osm;
+                const bool keep = layer_keeps_o(l);
                 const float* bias = a.bias + l * NP;
 #pragma unroll
-                for (int b = 0; b < NBLK_H; ++b) {
+                for (int b = 0; b < NBLK; ++b) {
                     const int c0 = 32 * b + 16 * half;
                     float* w = v + 16 * b;
                     if (c0 < NP) {
@@ -265,23 +290,10 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                             const float4 bb = __ldg(b4 + q);
                             w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
                         }
-                        // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
-                        unsigned char* rb = dst + b * BLK_A + row * 64;
-                        uint4* d0 = reinterpret_cast<uint4*>(rb + (((2 * half) ^ sw) << 4));
-                        uint4* d1 = reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ sw) << 4));
-                        if (resid) {
-                            const uint4 r0 = *d0, r1 = *d1;
-                            const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&r0);
-                            const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&r1);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float2 f0 = __bfloat1622float2(h0[q]), f1 = __bfloat1622float2(h1[q]);
-                                w[2 * q] += f0.x; w[2 * q + 1] += f0.y;
-                                w[8 + 2 * q] += f1.x; w[8 + 2 * q + 1] += f1.y;
-                            }
-                        }
 #pragma unroll
                         for (int i = 0; i < 16; ++i) w[i] = (c0 + i < RPNN_H) ? fmaxf(w[i], 0.0f) : 0.0f;
+                        // o^k stays in the accumulator as the next second layer's start value
+                        if (keep) tc::tmem_st16(taddr + 32u * b, w);
                         if (l == 21) {
                             const float4* w4 = reinterpret_cast<const float4*>(a.w3 + c0);
 #pragma unroll
@@ -291,6 +303,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                                 dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
                             }
                         } else {
+                            // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
+                            unsigned char* rb = Xsm + b * BLK_A + row * 64;
                             uint4 p0, p1;
                             __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
                             __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
@@ -299,11 +313,14 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                                 q0[q] = __floats2bfloat162_rn(w[2 * q], w[2 * q + 1]);
                                 q1[q] = __floats2bfloat162_rn(w[8 + 2 * q], w[8 + 2 * q + 1]);
                             }
-                            *d0 = p0;
-                            *d1 = p1;
+                            *reinterpret_cast<uint4*>(rb + (((2 * half) ^ sw) << 4)) = p0;
+                            *reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ sw) << 4)) = p1;
                             tc::fence_proxy_async_smem();
                         }
                     }
+                    // the accumulator write-back must be complete before the last block is
+                    // published: the MMAs that start from it wait for that block
+                    if (b == NBLK - 1 && keep) tc::tmem_wait_st();
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bar(B_BLK + b));
@@ -393,7 +410,7 @@ ImageLayout image_layout() {
     int64_t o = 0;
     for (int l = 0; l < NLAYERS; ++l) {
         I.off[l] = o;
-        o += (int64_t)((layer_kg(l) + CHUNK_KG - 1) / CHUNK_KG) * (BLK_B / 2);
+        o += (int64_t)layer_blocks(l) * (BLK_B / 2);
     }
     I.img_elems = o;
     I.bias_bytes_off = ((size_t)o * 2 + 255) & ~(size_t)255;
@@ -488,17 +505,11 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
         for (int b = 0; b < grid; ++b)
             for (int i = 0; i < 12; ++i) acc[i] += (double)h[(size_t)b * 12 + i] / grid;
         fprintf(stderr,
-                "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: wait_full %.0f "
-                "wait_act %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
+                "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: stage polls %.0f "
+                "end-of-layer waits %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
                 grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
         std::vector<long long> tlh(4 * 512 + 128);
         RPNN_CUDA_TRY(cudaMemcpy(tlh.data(), trace_buf + 1024 * 12, tlh.size() * 8, cudaMemcpyDeviceToHost));
-        for (int inst = 0; inst < 2; ++inst) {
-            const long long* c = &tlh[4 * 512 + inst * 64];
-            for (int k = 0; k < 14 && c[4 * k]; ++k)
-                fprintf(stderr, "[rpnn tc chunks] inst %d chunk %2d  wait %6lld  issue %6lld  since-start %7lld\n", 23 + inst, k,
-                        c[4 * k + 1] - c[4 * k], c[4 * k + 2] - c[4 * k + 1], c[4 * k] - c[0]);
-        }
         // block 0, second tile: per layer, issue span, issue->acc ready, epilogue span, gap
         for (int n = 22; n < 44 && tlh[4 * n + 3]; ++n) {
             const long long* q = &tlh[4 * n];

@@ -85,6 +85,34 @@ __device__ __forceinline__ void mbar_wait_issuer(uint32_t bar, uint32_t parity, 
         "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr) : "memory");
 }
 
+// As mbar_wait_issuer, for three barriers at once (each with its own parity): the poll
+// succeeds when all three phases have completed.  A caller that needs fewer passes a
+// barrier whose phase 0 completed at setup, with parity 0, in the unused slots.
+__device__ __forceinline__ void mbar_wait_issuer3(uint32_t b0, uint32_t p0, uint32_t b1, uint32_t p1, uint32_t b2,
+                                                  uint32_t p2, uint32_t limit, uint32_t abort_addr) {
+    asm volatile(
+        "{\n"
+        " .reg .pred P1, P2;\n"
+        " .reg .u32 c, f;\n"
+        " mov.u32 c, %6;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%2], %3;\n"
+        " and.pred P1, P1, P2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%4], %5;\n"
+        " and.pred P1, P1, P2;\n"
+        " @P1 bra DONE_%=;\n"
+        " ld.volatile.shared.u32 f, [%7];\n"
+        " setp.ne.u32 P1, f, 0;\n"
+        " @P1 bra DONE_%=;\n"
+        " sub.u32 c, c, 1;\n"
+        " setp.ne.u32 P1, c, 0;\n"
+        " @P1 bra WAIT_%=;\n"
+        " st.volatile.shared.u32 [%7], 1;\n"
+        "DONE_%=:\n"
+        "}\n" ::"r"(b0), "r"(p0), "r"(b1), "r"(p1), "r"(b2), "r"(p2), "r"(limit), "r"(abort_addr) : "memory");
+}
+
 // Bounded wait for the phase with the given parity.  Gives up (returns false) after
 // about kSpinLimit polls, or soon after *abort is set by another role of the block.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
@@ -186,6 +214,24 @@ __device__ __forceinline__ void tmem_ld16x7(uint32_t taddr, float v[112]) {
         : "memory");
 #pragma unroll
     for (int i = 0; i < 112; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store 32 lanes x 16 consecutive 32-bit columns (thread t of the warp writes lane
+// taddr.lane + t).  The store is asynchronous: tmem_wait_st() waits for this thread's
+// earlier stores to complete.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+          "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ---- descriptors -----------------------------------------------------------------

@@ -516,3 +516,159 @@ extern "C" int tc_probe(const void* A, const void* Bimg, const void* T2d, int t_
     if (cudaDeviceSynchronize() != cudaSuccess) return -14;
     return 0;
 }
+
+namespace {
+
+// ---- MMA rate through a 5-stage ring like the network kernel's ---------------------
+// Warp 0 lane 0 (producer) fills stage s after the MMAs that read it have completed:
+// an mbarrier arrive (copy == 0) or a 13,312-byte bulk copy (copy == 1).  Warp 1 lane
+// 0 (issuer) waits for each stage, issues CH MMAs on it and commits them to the stage's
+// "empty" barrier.  CH == 0: no ring, plain MMAs.  Wait forms (WF): 0 the bounded poll
+// whose satisfied path takes a branch; 1 a bounded poll whose satisfied path falls
+// through; 2 as 1, but one poll covers two consecutive stages; 3 as 0 with one commit per
+// two stages (4 stages; the producer refills a pair of stages after that commit).
+// copy & 2: the producer polls with a 200 ns sleep between tries.  Every block of the grid
+// does the same; cycles[b] is block b's issuer time.
+
+// bounded poll of one or two barriers; the satisfied path falls through
+__device__ __forceinline__ void wait_ft(uint32_t bar, uint32_t parity, uint32_t limit, uint32_t abort_addr) {
+    asm volatile(
+        "{\n"
+        " .reg .pred P1, P2;\n"
+        " .reg .u32 c, f;\n"
+        " mov.u32 c, %2;\n"
+        " mov.u32 f, 0;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+        " @!P1 ld.volatile.shared.u32 f, [%3];\n"
+        " @!P1 sub.u32 c, c, 1;\n"
+        " setp.ne.and.u32 P2, c, 0, !P1;\n"
+        " setp.eq.and.u32 P2, f, 0, P2;\n"
+        " @P2 bra WAIT_%=;\n"
+        " setp.eq.and.u32 P2, c, 0, !P1;\n"
+        " @P2 st.volatile.shared.u32 [%3], 1;\n"
+        "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr) : "memory");
+}
+__device__ __forceinline__ void wait_ft2(uint32_t bar0, uint32_t par0, uint32_t bar1, uint32_t par1, uint32_t limit,
+                                         uint32_t abort_addr) {
+    asm volatile(
+        "{\n"
+        " .reg .pred P1, P2, P3;\n"
+        " .reg .u32 c, f;\n"
+        " mov.u32 c, %4;\n"
+        " mov.u32 f, 0;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P3, [%2], %3;\n"
+        " and.pred P1, P1, P3;\n"
+        " @!P1 ld.volatile.shared.u32 f, [%5];\n"
+        " @!P1 sub.u32 c, c, 1;\n"
+        " setp.ne.and.u32 P2, c, 0, !P1;\n"
+        " setp.eq.and.u32 P2, f, 0, P2;\n"
+        " @P2 bra WAIT_%=;\n"
+        " setp.eq.and.u32 P2, c, 0, !P1;\n"
+        " @P2 st.volatile.shared.u32 [%5], 1;\n"
+        "}\n" ::"r"(bar0), "r"(par0), "r"(bar1), "r"(par1), "r"(limit), "r"(abort_addr) : "memory");
+}
+
+template <int CH, int WF>
+__global__ void __launch_bounds__(128) k_mma_ring(int nmma, int copy, const unsigned char* __restrict__ src,
+                                                   long long* cycles, int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    constexpr int S = WF == 3 ? 4 : 5;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bars = base + 180224;   // full[s] at +8s, empty[s] at +64+8s, done at +128
+    for (int i = tid; i < 98304 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < S; ++s) { mbar_init(bars + 8 * s, 1); mbar_init(bars + 64 + 8 * s, 1); }
+        mbar_init(bars + 128, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) { tmem_alloc(base + 180400, 256); tmem_relinquish(); }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 180400);
+    const uint32_t abort_addr = smem_u32(&abort_flag);
+    const int nchunk = CH > 0 ? nmma / CH : 0;
+    if (warp == 0 && lane == 0 && CH > 0) {
+        for (int c = 0; c < nchunk && !abort_flag; ++c) {
+            const int s = c % S;
+            const uint32_t eb = bars + 64 + 8 * (WF == 3 ? (s | 1) : s), ep = ((c / S) & 1) ^ 1;
+            if (copy & 2) {
+                uint32_t it = 0;
+                while (!mbar_test(eb, ep) && ++it < (1u << 22)) __nanosleep(200);
+                if (it >= (1u << 22)) { abort_flag = 1; break; }
+            } else {
+                mbar_wait_issuer(eb, ep, kSpinLimit, abort_addr);
+            }
+            if (copy & 1) {
+                mbar_expect_tx(bars + 8 * s, 13312);
+                bulk_g2s(base + 16384 + s * 16384, src + (size_t)(c % 64) * 13312, 13312, bars + 8 * s);
+            } else {
+                mbar_expect_tx(bars + 8 * s, 0);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t id = idesc_bf16(128, 208);
+        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
+        const long long t0 = clock64();
+        if (CH == 0) {
+            for (int i = 0; i < nmma; ++i) mma_bf16(tmem, a0 + (uint64_t)((i & 1) * 2), b0 + (uint64_t)((i & 1) * 2), id, i > 0);
+        } else {
+            uint32_t s = 0, ph = 0;
+            for (int c = 0; c < nchunk; ++c) {
+                if (WF == 0 || WF == 3) mbar_wait_issuer(bars + 8 * s, ph, kSpinLimit, abort_addr);
+                if (WF == 1) wait_ft(bars + 8 * s, ph, kSpinLimit, abort_addr);
+                if (WF == 2 && !(c & 1)) {
+                    const uint32_t s1 = s + 1 == S ? 0 : s + 1, ph1 = s + 1 == S ? ph ^ 1u : ph;
+                    wait_ft2(bars + 8 * s, ph, bars + 8 * s1, ph1, kSpinLimit, abort_addr);
+                }
+                const uint64_t bs = b0 + (uint64_t)s * (16384 >> 4);
+#pragma unroll
+                for (int j = 0; j < (CH > 0 ? CH : 1); ++j)
+                    mma_bf16(tmem, a0 + (uint64_t)((j & 1) * 2), bs + (uint64_t)((j & 1) * 2), id, (c | j) ? 1u : 0u);
+                if (WF != 3 || (c & 1)) mma_commit(bars + 64 + 8 * s);
+                if (++s == S) { s = 0; ph ^= 1u; }
+            }
+        }
+        mma_commit(bars + 128);
+        if (!mbar_wait(bars + 128, 0, &abort_flag)) atomicOr(err, 1);
+        cycles[blockIdx.x] = clock64() - t0;
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag) atomicOr(err, 2);
+    if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
+template <int CH, int WF>
+int run_ring(int nmma, int copy, int grid, const void* src, long long* cycles, int* err) {
+    if (cudaFuncSetAttribute(k_mma_ring<CH, WF>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess)
+        return -12;
+    k_mma_ring<CH, WF><<<grid, 128, SMEM>>>(nmma, copy, (const unsigned char*)src, cycles, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int tc_mma_ring(int ch, int wf, int nmma, int copy, int grid, const void* src, long long* cycles,
+                           int* err) {
+    switch (ch * 10 + wf) {
+        case 0: return run_ring<0, 0>(nmma, copy, grid, src, cycles, err);
+        case 20: return run_ring<2, 0>(nmma, copy, grid, src, cycles, err);
+        case 21: return run_ring<2, 1>(nmma, copy, grid, src, cycles, err);
+        case 22: return run_ring<2, 2>(nmma, copy, grid, src, cycles, err);
+        case 23: return run_ring<2, 3>(nmma, copy, grid, src, cycles, err);
+        case 40: return run_ring<4, 0>(nmma, copy, grid, src, cycles, err);
+        case 41: return run_ring<4, 1>(nmma, copy, grid, src, cycles, err);
+        case 80: return run_ring<8, 0>(nmma, copy, grid, src, cycles, err);
+        default: return -1;
+    }
+}

@@ -156,3 +156,29 @@ def test_mma_rate_with_concurrent_copies(probe, capsys):
         with capsys.disabled():
             print(f"\n[mma + traffic] {name:26s} {c / 4096:7.1f} cyc/mma, {copies} copies of 13 KB "
                   f"({copies * 13312 / c:5.1f} B/clk)")
+
+
+def test_mma_rate_through_ring(probe, capsys):
+    """MMA rate when every CH MMAs wait for a ring stage and commit it back, on one SM and
+    on every SM at once (the network kernel's pipeline without its epilogue), for three
+    forms of the issuing thread's wait."""
+    probe.tc_mma_ring.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 3
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
+    cyc = torch.zeros(nsm, dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    forms = ["branch on success", "fall-through", "fall-through, 2 stages", "commit every 2 stages"]
+    out = []
+    for ch, wf in [(0, 0), (2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1), (8, 0)]:
+        for copy in ((0,) if ch == 0 else (0, 1, 2, 3)):
+            for grid in (1, nsm) if copy < 2 else (nsm,):
+                cyc.zero_()
+                assert probe.tc_mma_ring(ch, wf, 4096, copy, grid, src.data_ptr(), cyc.data_ptr(),
+                                         err.data_ptr()) == 0
+                assert err.item() == 0
+                c = cyc[:grid].double().cpu()
+                out.append((ch, forms[wf], copy, grid, c.mean().item() / 4096, c.max().item() / 4096))
+    with capsys.disabled():
+        for ch, form, copy, grid, mean, mx in out:
+            print(f"\n[mma ring] {ch} MMAs/stage, {form:22s} copy={copy & 1} sleep={copy >> 1} grid={grid:3d}  {mean:7.1f} cyc/mma "
+                  f"(max {mx:7.1f})")
