@@ -13,7 +13,11 @@
 // allocates tensor memory and one lane issues tcgen05.mma, four K = 16 steps per stage,
 // into two alternating FP32 accumulators (so the descriptor part of a block's first layer
 // overlaps the previous epilogue); warps 2-9 are the epilogue: tensor memory -> registers,
-// bias / ReLU, BF16 activations written back to shared memory for the next layer.
+// ReLU, BF16 activations written back to shared memory for the next layer.
+//
+// Biases ride in the MMAs: activation column 200 (first padding column) holds 1.0 and the
+// weight image carries each layer's bias in that column.  Only block 1's first layer,
+// which reads no activation, adds its bias in the epilogue.
 //
 // One activation buffer X serves every layer: a layer's epilogue starts only after all
 // of that layer's MMAs (the readers of X) have completed.  The residual o^{k-1} of a
@@ -47,6 +51,7 @@ constexpr int SK = 64;                  // K columns per ring stage: four K = 16
 constexpr uint32_t BLK_A = TM * 64;     // 8192: 32 columns of 128 rows
 constexpr uint32_t BLK_B = NP * 64;     // 13312: 32 columns of 208 rows
 constexpr int NBLK = 7;                 // 32-column blocks of a 208-wide activation
+constexpr int NPUB = 4;                 // epilogue publication points: blocks {0,1} {2,3} {4,5} {6}
 constexpr int W_STAGES = 4, Z_STAGES = 3;
 constexpr uint32_t W_STAGE = 2 * BLK_B;                        // 26624
 constexpr uint32_t Z_STAGE = 2 * BLK_A;                        // 16384
@@ -63,7 +68,7 @@ constexpr int NTHREADS = 64 + EPI_THREADS;
 // setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
 enum {
     B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES, B_ZEMPTY = B_ZFULL + Z_STAGES,
-    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NBLK, B_DONE, B_COUNT
+    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB, B_DONE, B_COUNT
 };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
@@ -99,6 +104,19 @@ __host__ __device__ constexpr int layer_blocks(int l) { return (layer_k(l) + 31)
 __host__ __device__ constexpr bool layer_resid(int l) { return (l & 1) && l >= 3 && l < 20; }
 __host__ __device__ constexpr bool layer_keeps_o(int l) { return (l & 1) && l < 18; }
 
+// two floats -> packed BF16 pair (lo in the low half), round to nearest even; the
+// second form also clamps negatives to zero (ReLU)
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -125,7 +143,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         for (int s = 0; s < W_STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
         for (int s = 0; s < Z_STAGES; ++s) { tc::mbar_init(bar(B_ZFULL + s), 1); tc::mbar_init(bar(B_ZEMPTY + s), 1); }
         tc::mbar_init(bar(B_ACC), 1);
-        for (int b = 0; b < NBLK; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
+        for (int b = 0; b < NPUB; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
         tc::mbar_init(bar(B_DONE), 1);
         tc::fence_mbar_init();
@@ -199,15 +217,15 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     tc::tc_fence_after();
                     const int K = layer_k(l), zk = layer_zk(l);
                     const uint32_t first_acc = layer_resid(l) ? 1u : 0u;
-                    // Activation block b of epilogue n-1 is published on B_BLK + b; the
-                    // epilogue warps publish blocks in order, so a completed block also
+                    // Activation blocks 2p, 2p+1 of epilogue n-1 are published on B_BLK + p;
+                    // the epilogue warps publish in order, so a completed publication also
                     // covers every block before it.
                     const uint32_t pb = (n - 1) & 1u;
-                    int blk_ready = n > 0 ? -1 : NBLK - 1;
+                    int blk_ready = n > 0 ? -1 : NPUB - 1;
                     for (int k0 = 0; k0 < K; k0 += SK) {
                         const int k1 = min(K, k0 + SK);
                         const bool hz = k0 < zk;
-                        const int need = k1 > zk ? (k1 - zk - 1) >> 5 : -1;
+                        const int need = k1 > zk ? (k1 - zk - 1) >> 6 : -1;    // publication
                         uint32_t b2 = none, p2 = 0;
                         if (need > blk_ready) { b2 = bar(B_BLK + need); p2 = pb; blk_ready = need; }
                         const long long tw = trace ? clock64() : 0;
@@ -238,9 +256,9 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     }
                     // a layer that reads no activation (a tile's first) still waits for the
                     // previous epilogue, so the issuer never runs two phases ahead of it
-                    if (blk_ready < NBLK - 1) {
+                    if (blk_ready < NPUB - 1) {
                         const long long tb = trace ? clock64() : 0;
-                        tc::mbar_wait_issuer(bar(B_BLK + NBLK - 1), pb, tc::kSpinLimit, abort_addr);
+                        tc::mbar_wait_issuer(bar(B_BLK + NPUB - 1), pb, tc::kSpinLimit, abort_addr);
                         if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
                     }
                     tc::mma_commit(bar(B_ACC));
@@ -278,20 +296,25 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 float v[NBLK * 16];
                 tc::tmem_ld16x7(taddr, v);
                 const bool keep = layer_keeps_o(l);
-                const float* bias = a.bias + l * NP;
 #pragma unroll
                 for (int b = 0; b < NBLK; ++b) {
                     const int c0 = 32 * b + 16 * half;
                     float* w = v + 16 * b;
+                    // accumulator columns 200..207 are exactly zero (zero weight rows and
+                    // zero start values), so ReLU needs no column mask
                     if (c0 < NP) {
-                        const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+                        if (l == 0) {
+                            const float4* b4 = reinterpret_cast<const float4*>(a.bias + c0);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 bb = __ldg(b4 + q);
-                            w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 bb = __ldg(b4 + q);
+                                w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
+                            }
                         }
+                        if (keep || l == 21) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) w[i] = (c0 + i < RPNN_H) ? fmaxf(w[i], 0.0f) : 0.0f;
+                            for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
+                        }
                         // o^k stays in the accumulator as the next second layer's start value
                         if (keep) tc::tmem_st16(taddr + 32u * b, w);
                         if (l == 21) {
@@ -303,27 +326,34 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                                 dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
                             }
                         } else {
-                            // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
-                            unsigned char* rb = Xsm + b * BLK_A + row * 64;
+                            // BF16 pairs (ReLU folded into the conversion unless already applied)
                             uint4 p0, p1;
-                            __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
-                            __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
+                            uint32_t* u0 = reinterpret_cast<uint32_t*>(&p0);
+                            uint32_t* u1 = reinterpret_cast<uint32_t*>(&p1);
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
-                                q0[q] = __floats2bfloat162_rn(w[2 * q], w[2 * q + 1]);
-                                q1[q] = __floats2bfloat162_rn(w[8 + 2 * q], w[8 + 2 * q + 1]);
+                                u0[q] = keep ? pack_bf16x2(w[2 * q], w[2 * q + 1]) : pack_relu_bf16x2(w[2 * q], w[2 * q + 1]);
+                                u1[q] = keep ? pack_bf16x2(w[8 + 2 * q], w[9 + 2 * q])
+                                             : pack_relu_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
                             }
+                            // column 200 carries the constant 1 that multiplies the next layer's bias
+                            if (b == NBLK - 1) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
+                            // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
+                            unsigned char* rb = Xsm + b * BLK_A + row * 64;
                             *reinterpret_cast<uint4*>(rb + (((2 * half) ^ sw) << 4)) = p0;
                             *reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ sw) << 4)) = p1;
-                            tc::fence_proxy_async_smem();
                         }
                     }
-                    // the accumulator write-back must be complete before the last block is
-                    // published: the MMAs that start from it wait for that block
-                    if (b == NBLK - 1 && keep) tc::tmem_wait_st();
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(bar(B_BLK + b));
+                    if ((b & 1) || b == NBLK - 1) {
+                        // publish blocks b-1, b: make the stores visible to the tensor core,
+                        // and (last block) complete the accumulator write-back first, since
+                        // the MMAs that start from it wait for the last publication
+                        tc::fence_proxy_async_smem();
+                        if (b == NBLK - 1 && keep) tc::tmem_wait_st();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(bar(B_BLK + (b >> 1)));
+                    }
                 }
                 if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
@@ -372,15 +402,20 @@ __global__ void k_build_image(const float* __restrict__ P, ParamLayout L, TcArgs
         const int rem = (int)(r % (BLK_B / 2));
         const int n = rem / 32, pos = rem % 32;
         const int c = chunk * 32 + (((pos / 8) ^ ((n >> 1) & 3)) * 8) + pos % 8;
+        // layers l >= 1 read the activation, whose column 200 is the constant 1: the
+        // image holds the layer's bias in that column
         float v = 0.0f;
         if (n < RPNN_H) {
             if (l < 20 && !(l & 1)) {
                 const int k = l / 2;
                 if (c < RPNN_DIN) v = P[L.V[k] + (int64_t)n * RPNN_DIN + c];
-                else if (c >= 240 && c < 240 + RPNN_H) v = P[L.W1[k] + (int64_t)n * RPNN_H + (c - 240)];
+                else if (c >= KZ && c < KZ + RPNN_H) v = P[L.W1[k] + (int64_t)n * RPNN_H + (c - KZ)];
+                else if (c == KZ + RPNN_H && l > 0) v = P[L.b1[k] + n];
             } else if (c < RPNN_H) {
                 const int64_t off = l < 20 ? L.W2[l / 2] : L.T[l - 20];
                 v = P[off + (int64_t)n * RPNN_H + c];
+            } else if (c == RPNN_H) {
+                v = P[(l < 20 ? L.b2[l / 2] : L.bT[l - 20]) + n];
             }
         }
         img[e] = __float2bfloat16_rn(v);
