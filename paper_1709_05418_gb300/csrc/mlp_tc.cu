@@ -68,7 +68,7 @@ constexpr int NTHREADS = 64 + EPI_THREADS;
 // setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
 enum {
     B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES, B_ZEMPTY = B_ZFULL + Z_STAGES,
-    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB, B_DONE, B_COUNT
+    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB, B_DONE, B_DRAIN, B_COUNT
 };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
@@ -104,6 +104,90 @@ __host__ __device__ constexpr int layer_blocks(int l) { return (layer_k(l) + 31)
 __host__ __device__ constexpr bool layer_resid(int l) { return (l & 1) && l >= 3 && l < 20; }
 __host__ __device__ constexpr bool layer_keeps_o(int l) { return (l & 1) && l < 18; }
 
+// Issue state of the MMA thread: the low 32 bits of the current weight / descriptor stage
+// operand descriptors (start address in 16-byte units) and of the activation buffer, the
+// common high word, the current ring barriers, positions and phases.
+struct IssueState {
+    uint32_t idesc, abort_addr, none, hi;
+    uint32_t w0, z0, x0, w, z;
+    uint32_t wbar0, zbar0, wbar, zbar, blk0;
+    uint32_t sw, pw, sz, pz;
+    long long* tr;       // timeline base (block 0, diagnostics) or null
+    long long* stamp;    // per-stage stamps of this layer instance, or null
+    unsigned long long cyc;
+};
+
+// D[acc] (+)= A * B^T with operand descriptors given as low words and a common high word;
+// `accumulate` is a constant at every call site (the two forms differ only in the flag).
+__device__ __forceinline__ void mma_lohi(uint32_t acc, uint32_t a_lo, uint32_t b_lo, uint32_t hi, uint32_t idesc,
+                                         bool accumulate) {
+    if (accumulate)
+        asm volatile(
+            "{\n .reg .b64 da, db;\n .reg .pred p;\n"
+            " mov.b64 da, {%1, %3};\n mov.b64 db, {%2, %3};\n setp.eq.u32 p, 0, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n"
+            ::"r"(acc), "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc) : "memory");
+    else
+        asm volatile(
+            "{\n .reg .b64 da, db;\n .reg .pred p;\n"
+            " mov.b64 da, {%1, %3};\n mov.b64 db, {%2, %3};\n setp.ne.u32 p, 0, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n"
+            ::"r"(acc), "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc) : "memory");
+}
+
+// One layer of K columns, the first ZK of them from the descriptor ring, in stages of 64
+// columns (four K = 16 MMAs).  RESID: the accumulator already holds o^{k-1}.  Activation
+// column c sits in 32-column block c / 32 at half (c / 16) % 2; a stage reading columns
+// up to c waits for publication c / 64 of the previous epilogue (phase parity pb).
+template <bool TRACE, int K, int ZK, bool RESID>
+__device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_t pb) {
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += SK) {
+        const int k1 = k0 + SK < K ? k0 + SK : K;
+        const bool hz = k0 < ZK;
+        const int need = k1 > ZK ? (k1 - ZK - 1) >> 6 : -1;
+        const uint32_t pub = S.blk0 + BAR_STRIDE * (uint32_t)(need < 0 ? 0 : need);
+        long long t0 = 0;
+        if (TRACE) {
+            t0 = clock64();
+            if (S.stamp) S.stamp[(k0 / SK) * 3] = t0;
+        }
+        if (hz && need >= 0)
+            tc::mbar_wait_issuer3(S.wbar, S.pw, S.zbar, S.pz, pub, pb, tc::kSpinLimit, S.abort_addr);
+        else if (hz)
+            tc::mbar_wait_issuer3(S.wbar, S.pw, S.zbar, S.pz, S.none, 0u, tc::kSpinLimit, S.abort_addr);
+        else if (need >= 0)
+            tc::mbar_wait_issuer3(S.wbar, S.pw, pub, pb, S.none, 0u, tc::kSpinLimit, S.abort_addr);
+        else
+            tc::mbar_wait_issuer(S.wbar, S.pw, tc::kSpinLimit, S.abort_addr);
+        if (TRACE) {
+            const long long t1 = clock64();
+            S.cyc += (unsigned long long)(t1 - t0);
+            if (S.stamp) S.stamp[(k0 / SK) * 3 + 1] = t1;
+        }
+#pragma unroll
+        for (int j = 0; j < SK / 16; ++j) {
+            const int k = k0 + 16 * j;
+            if (k < k1) {
+                const uint32_t b = S.w + (uint32_t)((j >> 1) * (BLK_B >> 4) + (j & 1) * 2);
+                const int c = k - ZK;
+                const uint32_t a = k < ZK ? S.z + (uint32_t)((j >> 1) * (BLK_A >> 4) + (j & 1) * 2)
+                                          : S.x0 + (uint32_t)((c >> 5) * (BLK_A >> 4) + ((c >> 4) & 1) * 2);
+                mma_lohi(acc, a, b, S.hi, S.idesc, k > 0 || RESID);
+            }
+        }
+        tc::mma_commit(S.wbar + BAR_STRIDE * W_STAGES);          // this stage's "empty" barrier
+        if (TRACE && S.stamp) S.stamp[(k0 / SK) * 3 + 2] = clock64();
+        if (++S.sw == W_STAGES) { S.sw = 0; S.pw ^= 1u; S.w = S.w0; S.wbar = S.wbar0; }
+        else { S.w += W_STAGE >> 4; S.wbar += BAR_STRIDE; }
+        if (hz) {
+            tc::mma_commit(S.zbar + BAR_STRIDE * Z_STAGES);
+            if (++S.sz == Z_STAGES) { S.sz = 0; S.pz ^= 1u; S.z = S.z0; S.zbar = S.zbar0; }
+            else { S.z += Z_STAGE >> 4; S.zbar += BAR_STRIDE; }
+        }
+    }
+}
+
 // two floats -> packed BF16 pair (lo in the low half), round to nearest even; the
 // second form also clamps negatives to zero (ReLU)
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -117,6 +201,7 @@ __device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
     return d;
 }
 
+template <bool TRACE>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -126,13 +211,13 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     auto bar = [&](int i) { return base + OFF_BAR + BAR_STRIDE * (uint32_t)i; };
     // diagnostics: cycles spent in each role's waits, when a.trace is set, and for block
     // 0 a timeline of 4 stamps per layer instance (MMA issue start/end, epilogue start/end)
-    long long* tl = (a.trace && blockIdx.x == 0) ? reinterpret_cast<long long*>(a.trace + 1024 * 12) : nullptr;
+    long long* tl = (TRACE && blockIdx.x == 0) ? reinterpret_cast<long long*>(a.trace + 1024 * 12) : nullptr;
     unsigned long long cyc_wait = 0, cyc_wait2 = 0;
     const long long cyc_start = clock64();
     auto twait = [&](uint32_t b, uint32_t parity, unsigned long long& acc) {
-        const long long t0 = a.trace ? clock64() : 0;
+        const long long t0 = TRACE ? clock64() : 0;
         const bool r = tc::mbar_wait(b, parity, abort_flag);
-        if (a.trace) acc += (unsigned long long)(clock64() - t0);
+        if (TRACE) acc += (unsigned long long)(clock64() - t0);
         return r;
     };
     const int64_t Q = a.q_dev ? (int64_t)*a.q_dev : a.q_host;
@@ -146,6 +231,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         for (int b = 0; b < NPUB; ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
         tc::mbar_init(bar(B_DONE), 1);
+        tc::mbar_init(bar(B_DRAIN), 1);
         tc::fence_mbar_init();
         tc::mbar_arrive(bar(B_DONE));
     }
@@ -194,77 +280,60 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // (each would stall behind the MMAs in flight): waits are output-free asm loops,
         // one per stage of four MMAs, covering the weight stage, the descriptor stage and
         // the activation block the stage needs; the abort flag is read once per tile.
+        // Each layer kind is issued by a fully unrolled routine, so every descriptor
+        // offset, accumulate flag and wait shape is a compile-time constant: the thread
+        // spends its time in waits and MMAs, not in address arithmetic.
         if (lane == 0 && !*abort_flag) {
-            const uint32_t idesc = tc::idesc_bf16(TM, NP);
-            const uint32_t abort_addr = base + OFF_ABORT;
-            const uint32_t none = bar(B_DONE);
-            const bool trace = a.trace != nullptr;
-            // 64-bit operand descriptors are built once; an MMA only adds constants to them
-            // (the start-address field counts 16-byte units: +2 = +32 bytes = 16 columns)
-            const uint64_t d_W = tc::smem_desc_sw64(base + OFF_W);
-            const uint64_t d_Z = tc::smem_desc_sw64(base + OFF_Z);
-            const uint64_t d_X = tc::smem_desc_sw64(base + OFF_X);
+            IssueState S;
+            S.idesc = tc::idesc_bf16(TM, NP);
+            S.abort_addr = base + OFF_ABORT;
+            S.none = bar(B_DONE);
+            S.hi = (uint32_t)(tc::smem_desc_sw64(base) >> 32);
+            S.w0 = (uint32_t)tc::smem_desc_sw64(base + OFF_W);
+            S.z0 = (uint32_t)tc::smem_desc_sw64(base + OFF_Z);
+            S.x0 = (uint32_t)tc::smem_desc_sw64(base + OFF_X);
+            S.wbar0 = bar(B_WFULL);
+            S.zbar0 = bar(B_ZFULL);
+            S.blk0 = bar(B_BLK);
+            S.w = S.w0; S.z = S.z0; S.wbar = S.wbar0; S.zbar = S.zbar0;
+            S.sw = 0; S.pw = 0; S.sz = 0; S.pz = 0;
+            S.tr = tl;
+            S.cyc = 0;
             uint32_t n = 0;                          // layer instance
-            uint32_t sw = 0, pw = 0, sz = 0, pz = 0; // ring positions and phases
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS; ++l, ++n) {
-                    const uint32_t acc = tmem + (n & 1u) * 256u;
-                    if (tl && n < 512) tl[4 * n] = clock64();
+                    const uint32_t acc = tmem + (uint32_t)(l & 1) * 256u;   // n and l share parity
+                    if (TRACE && tl && n < 512) tl[4 * n] = clock64();
+                    S.stamp = (TRACE && tl && (n == 24 || n == 25)) ? tl + 2048 + (n - 24) * 24 : nullptr;
                     // One tcgen05 fence per layer orders this layer's MMAs after the waits
                     // (in the previous layer) that saw epilogue n-2 finish with accumulator
                     // n % 2.  Operands written by TMA or by the epilogue (fence.proxy.async +
                     // mbarrier) need no tcgen05 fence.
                     tc::tc_fence_after();
-                    const int K = layer_k(l), zk = layer_zk(l);
-                    const uint32_t first_acc = layer_resid(l) ? 1u : 0u;
-                    // Activation blocks 2p, 2p+1 of epilogue n-1 are published on B_BLK + p;
-                    // the epilogue warps publish in order, so a completed publication also
-                    // covers every block before it.
-                    const uint32_t pb = (n - 1) & 1u;
-                    int blk_ready = n > 0 ? -1 : NPUB - 1;
-                    for (int k0 = 0; k0 < K; k0 += SK) {
-                        const int k1 = min(K, k0 + SK);
-                        const bool hz = k0 < zk;
-                        const int need = k1 > zk ? (k1 - zk - 1) >> 6 : -1;    // publication
-                        uint32_t b2 = none, p2 = 0;
-                        if (need > blk_ready) { b2 = bar(B_BLK + need); p2 = pb; blk_ready = need; }
-                        const long long tw = trace ? clock64() : 0;
-                        tc::mbar_wait_issuer3(bar(B_WFULL + sw), pw, hz ? bar(B_ZFULL + sz) : none, hz ? pz : 0u, b2, p2,
-                                              tc::kSpinLimit, abort_addr);
-                        if (trace) cyc_wait += (unsigned long long)(clock64() - tw);
-                        const uint64_t d_w = d_W + sw * (uint64_t)(W_STAGE >> 4);
-                        const uint64_t d_z = d_Z + sz * (uint64_t)(Z_STAGE >> 4);
-#pragma unroll
-                        for (int j = 0; j < SK / 16; ++j) {
-                            const int k = k0 + 16 * j;
-                            if (k >= k1) break;
-                            const uint64_t d_b = d_w + (uint64_t)(j >> 1) * (BLK_B >> 4) + (uint64_t)(j & 1) * 2u;
-                            uint64_t d_a;
-                            if (k < zk) d_a = d_z + (uint64_t)(j >> 1) * (BLK_A >> 4) + (uint64_t)(j & 1) * 2u;
-                            else {
-                                const int c = k - zk;              // column of the activation
-                                d_a = d_X + (uint64_t)(c >> 5) * (BLK_A >> 4) + (uint64_t)((c >> 4) & 1) * 2u;
-                            }
-                            tc::mma_bf16(acc, d_a, d_b, idesc, k > 0 ? 1u : first_acc);
-                        }
-                        tc::mma_commit(bar(B_WEMPTY + sw));
-                        if (++sw == W_STAGES) { sw = 0; pw ^= 1u; }
-                        if (hz) {
-                            tc::mma_commit(bar(B_ZEMPTY + sz));
-                            if (++sz == Z_STAGES) { sz = 0; pz ^= 1u; }
-                        }
-                    }
-                    // a layer that reads no activation (a tile's first) still waits for the
-                    // previous epilogue, so the issuer never runs two phases ahead of it
-                    if (blk_ready < NPUB - 1) {
-                        const long long tb = trace ? clock64() : 0;
-                        tc::mbar_wait_issuer(bar(B_BLK + NPUB - 1), pb, tc::kSpinLimit, abort_addr);
-                        if (trace) cyc_wait2 += (unsigned long long)(clock64() - tb);
+                    // publication parity of epilogue n-1: n and l share parity
+                    const uint32_t pb = (uint32_t)(l & 1) ^ 1u;
+                    if (l == 0) {
+                        issue_layer<TRACE, KZ, KZ, false>(S, acc, pb);
+                        // a tile's first layer reads no activation; it still waits for the
+                        // previous epilogue, so the issuer never runs two phases ahead of it
+                        if (n > 0) tc::mbar_wait_issuer(S.blk0 + BAR_STRIDE * (NPUB - 1), pb, tc::kSpinLimit, S.abort_addr);
+                    } else if (l < 20 && !(l & 1)) {
+                        issue_layer<TRACE, KZ + NP, KZ, false>(S, acc, pb);
+                    } else if (layer_resid(l)) {
+                        issue_layer<TRACE, NP, 0, true>(S, acc, pb);
+                    } else {
+                        issue_layer<TRACE, NP, 0, false>(S, acc, pb);
                     }
                     tc::mma_commit(bar(B_ACC));
-                    if (tl && n < 512) tl[4 * n + 1] = clock64();
+                    if (TRACE && tl && n < 512) tl[4 * n + 1] = clock64();
                 }
                 if (*abort_flag) break;
+            }
+            cyc_wait = S.cyc;
+            if (*abort_flag) {
+                // drain: wait (bounded) for the MMAs in flight before tensor memory is freed
+                tc::mma_commit(bar(B_DRAIN));
+                tc::mbar_poll(bar(B_DRAIN), 0u, tc::kSpinLimit);
             }
         }
     } else {
@@ -289,7 +358,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 // one poller per warp: lane 0 waits, the warp follows
                 if (lane == 0) ok = twait(bar(B_ACC), n & 1u, cyc_wait);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 2] = clock64();
+                if (TRACE && tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 2] = clock64();
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
@@ -353,9 +422,11 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         tc::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(bar(B_BLK + (b >> 1)));
+                        if (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
+                            tl[2048 + 48 + (n - 23) * 8 + (b >> 1)] = clock64();
                     }
                 }
-                if (tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
+                if (TRACE && tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
             if (!ok) break;
             // combine the two column halves of the output layer's dot product: the
@@ -372,7 +443,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             ++tile_iter;
         }
     }
-    if (a.trace && lane == 0 && warp <= 2) {
+    if (TRACE && lane == 0 && warp <= 2) {
         unsigned long long* tr = a.trace + (size_t)blockIdx.x * 12 + warp * 3;
         tr[0] = cyc_wait;
         tr[1] = cyc_wait2;
@@ -524,13 +595,15 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;
     if (!attr) {
-        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
         attr = true;
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
     if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long), s));
-    k_rpnn_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
+    if (tracing) k_rpnn_tc<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
+    else k_rpnn_tc<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
     if (tracing) {
         std::vector<unsigned long long> h((size_t)grid * 12);
@@ -545,6 +618,19 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
                 grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
         std::vector<long long> tlh(4 * 512 + 128);
         RPNN_CUDA_TRY(cudaMemcpy(tlh.data(), trace_buf + 1024 * 12, tlh.size() * 8, cudaMemcpyDeviceToHost));
+        // block 0, layer instances 24 and 25 (second tile, layers 2 and 3): per stage the
+        // poll start / poll end / commit, and the publications of the epilogue feeding it,
+        // relative to the layer's issue start
+        for (int inst = 0; inst < 2; ++inst) {
+            const long long t0 = tlh[4 * (24 + inst)];
+            const long long* st = &tlh[2048 + inst * 24];
+            const long long* pub = &tlh[2048 + 48 + inst * 8];
+            fprintf(stderr, "[rpnn tc stages] inst %d: epilogue %d acc-ready %lld pubs %lld %lld %lld %lld\n", 24 + inst,
+                    23 + inst, tlh[4 * (23 + inst) + 2] - t0, pub[0] - t0, pub[1] - t0, pub[2] - t0, pub[3] - t0);
+            for (int j = 0; j < 8 && st[3 * j]; ++j)
+                fprintf(stderr, "[rpnn tc stages] inst %d stage %d  poll %6lld .. %6lld  commit %6lld\n", 24 + inst, j,
+                        st[3 * j] - t0, st[3 * j + 1] - t0, st[3 * j + 2] - t0);
+        }
         // block 0, second tile: per layer, issue span, issue->acc ready, epilogue span, gap
         for (int n = 22; n < 44 && tlh[4 * n + 3]; ++n) {
             const long long* q = &tlh[4 * n];

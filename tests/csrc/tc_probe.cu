@@ -526,7 +526,13 @@ namespace {
 // "empty" barrier.  CH == 0: no ring, plain MMAs.  Wait forms (WF): 0 the bounded poll
 // whose satisfied path takes a branch; 1 a bounded poll whose satisfied path falls
 // through; 2 as 1, but one poll covers two consecutive stages; 3 as 0 with one commit per
-// two stages (4 stages; the producer refills a pair of stages after that commit).
+// two stages (4 stages; the producer refills a pair of stages after that commit); 4 as 0
+// but the poll covers the stage and two barriers completed at setup (three try_waits);
+// 5 as 0 with a second commit per stage (to a barrier nobody waits on); 6 as 0 with four
+// distinct A and B operands per stage (stages of two 32-column weight blocks, 32 KB apart,
+// and two 32-column A blocks), as in the network kernel; 7 as 6 with 8 more warps that,
+// like the network kernel's epilogue, wait (lane 0 polling) for an accumulator barrier
+// the issuer commits every 7 stages, then arrive on 4 barriers nobody waits on.
 // copy & 2: the producer polls with a 200 ns sleep between tries.  Every block of the grid
 // does the same; cycles[b] is block b's issuer time.
 
@@ -572,7 +578,7 @@ __device__ __forceinline__ void wait_ft2(uint32_t bar0, uint32_t par0, uint32_t 
 }
 
 template <int CH, int WF>
-__global__ void __launch_bounds__(128) k_mma_ring(int nmma, int copy, const unsigned char* __restrict__ src,
+__global__ void __launch_bounds__(WF == 7 ? 320 : 128) k_mma_ring(int nmma, int copy, const unsigned char* __restrict__ src,
                                                    long long* cycles, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ int abort_flag;
@@ -580,13 +586,18 @@ __global__ void __launch_bounds__(128) k_mma_ring(int nmma, int copy, const unsi
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t base = smem_u32(sm);
     const uint32_t bars = base + 180224;   // full[s] at +8s, empty[s] at +64+8s, done at +128
-    for (int i = tid; i < 98304 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (WF >= 6 ? 180224 : 98304) / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
     fence_proxy_async_smem();
     if (tid == 0) {
         abort_flag = 0;
         for (int s = 0; s < S; ++s) { mbar_init(bars + 8 * s, 1); mbar_init(bars + 64 + 8 * s, 1); }
         mbar_init(bars + 128, 1);
+        mbar_init(bars + 136, 1);
+        mbar_init(bars + 144, 1);
+        mbar_init(bars + 152, 1);                       // accumulator barrier (WF 7)
+        for (int p = 0; p < 4; ++p) mbar_init(bars + 160 + 8 * p, 8);
         fence_mbar_init();
+        mbar_arrive(bars + 144);   // phase 0 complete: always satisfied with parity 0
     }
     if (warp == 1) { tmem_alloc(base + 180400, 256); tmem_relinquish(); }
     __syncthreads();
@@ -605,7 +616,10 @@ __global__ void __launch_bounds__(128) k_mma_ring(int nmma, int copy, const unsi
             } else {
                 mbar_wait_issuer(eb, ep, kSpinLimit, abort_addr);
             }
-            if (copy & 1) {
+            if ((copy & 1) && WF >= 6) {
+                mbar_expect_tx(bars + 8 * s, 26624);
+                bulk_g2s(base + 16384 + s * 32768, src + (size_t)(c % 32) * 26624, 26624, bars + 8 * s);
+            } else if (copy & 1) {
                 mbar_expect_tx(bars + 8 * s, 13312);
                 bulk_g2s(base + 16384 + s * 16384, src + (size_t)(c % 64) * 13312, 13312, bars + 8 * s);
             } else {
@@ -620,24 +634,51 @@ __global__ void __launch_bounds__(128) k_mma_ring(int nmma, int copy, const unsi
             for (int i = 0; i < nmma; ++i) mma_bf16(tmem, a0 + (uint64_t)((i & 1) * 2), b0 + (uint64_t)((i & 1) * 2), id, i > 0);
         } else {
             uint32_t s = 0, ph = 0;
+            // block 0, WF 6: stamps of stages 100..107 (poll start, poll end, commit) after
+            // the per-block cycle counts
+            long long* st_tr = (WF >= 6 && blockIdx.x == 0) ? cycles + gridDim.x : nullptr;
             for (int c = 0; c < nchunk; ++c) {
-                if (WF == 0 || WF == 3) mbar_wait_issuer(bars + 8 * s, ph, kSpinLimit, abort_addr);
+                const bool stamp = st_tr && c >= 100 && c < 108;
+                if (stamp) st_tr[(c - 100) * 3] = clock64();
+                if (WF == 0 || WF == 3 || WF == 5 || WF >= 6) mbar_wait_issuer(bars + 8 * s, ph, kSpinLimit, abort_addr);
+                if (stamp) st_tr[(c - 100) * 3 + 1] = clock64();
+                if (WF == 4) mbar_wait_issuer3(bars + 8 * s, ph, bars + 144, 0, bars + 144, 0, kSpinLimit, abort_addr);
                 if (WF == 1) wait_ft(bars + 8 * s, ph, kSpinLimit, abort_addr);
                 if (WF == 2 && !(c & 1)) {
                     const uint32_t s1 = s + 1 == S ? 0 : s + 1, ph1 = s + 1 == S ? ph ^ 1u : ph;
                     wait_ft2(bars + 8 * s, ph, bars + 8 * s1, ph1, kSpinLimit, abort_addr);
                 }
-                const uint64_t bs = b0 + (uint64_t)s * (16384 >> 4);
+                const uint64_t bs = b0 + (uint64_t)s * ((WF >= 6 ? 32768 : 16384) >> 4);
 #pragma unroll
-                for (int j = 0; j < (CH > 0 ? CH : 1); ++j)
-                    mma_bf16(tmem, a0 + (uint64_t)((j & 1) * 2), bs + (uint64_t)((j & 1) * 2), id, (c | j) ? 1u : 0u);
+                for (int j = 0; j < (CH > 0 ? CH : 1); ++j) {
+                    const uint64_t ja = WF >= 6 ? (uint64_t)(j >> 1) * (8192 >> 4) : 0;
+                    const uint64_t jb = WF >= 6 ? (uint64_t)(j >> 1) * (13312 >> 4) : 0;
+                    mma_bf16(tmem, a0 + ja + (uint64_t)((j & 1) * 2), bs + jb + (uint64_t)((j & 1) * 2), id,
+                             (c | j) ? 1u : 0u);
+                }
                 if (WF != 3 || (c & 1)) mma_commit(bars + 64 + 8 * s);
+                if (WF == 5) mma_commit(bars + 136);
+                if (WF == 7 && c % 7 == 6) mma_commit(bars + 152);
+                if (stamp) st_tr[(c - 100) * 3 + 2] = clock64();
                 if (++s == S) { s = 0; ph ^= 1u; }
             }
         }
         mma_commit(bars + 128);
         if (!mbar_wait(bars + 128, 0, &abort_flag)) atomicOr(err, 1);
         cycles[blockIdx.x] = clock64() - t0;
+    } else if (WF == 7 && warp >= 2) {
+        // epilogue stand-in: one wait per 7-stage "layer", then four arrivals
+        const int nlayer = nchunk / 7;
+        for (int l = 0; l < nlayer; ++l) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(bars + 152, l & 1, &abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            for (int p = 0; p < 4; ++p) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bars + 160 + 8 * p);
+            }
+        }
     }
     __syncwarp();
     tc_fence_before();
@@ -650,7 +691,7 @@ template <int CH, int WF>
 int run_ring(int nmma, int copy, int grid, const void* src, long long* cycles, int* err) {
     if (cudaFuncSetAttribute(k_mma_ring<CH, WF>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess)
         return -12;
-    k_mma_ring<CH, WF><<<grid, 128, SMEM>>>(nmma, copy, (const unsigned char*)src, cycles, err);
+    k_mma_ring<CH, WF><<<grid, WF == 7 ? 320 : 128, SMEM>>>(nmma, copy, (const unsigned char*)src, cycles, err);
     if (cudaGetLastError() != cudaSuccess) return -13;
     if (cudaDeviceSynchronize() != cudaSuccess) return -14;
     return 0;
@@ -668,6 +709,10 @@ extern "C" int tc_mma_ring(int ch, int wf, int nmma, int copy, int grid, const v
         case 23: return run_ring<2, 3>(nmma, copy, grid, src, cycles, err);
         case 40: return run_ring<4, 0>(nmma, copy, grid, src, cycles, err);
         case 41: return run_ring<4, 1>(nmma, copy, grid, src, cycles, err);
+        case 44: return run_ring<4, 4>(nmma, copy, grid, src, cycles, err);
+        case 45: return run_ring<4, 5>(nmma, copy, grid, src, cycles, err);
+        case 46: return run_ring<4, 6>(nmma, copy, grid, src, cycles, err);
+        case 47: return run_ring<4, 7>(nmma, copy, grid, src, cycles, err);
         case 80: return run_ring<8, 0>(nmma, copy, grid, src, cycles, err);
         default: return -1;
     }

@@ -165,20 +165,30 @@ def test_mma_rate_through_ring(probe, capsys):
     probe.tc_mma_ring.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 3
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
-    cyc = torch.zeros(nsm, dtype=torch.int64, device="cuda")
+    cyc = torch.zeros(nsm + 24, dtype=torch.int64, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    forms = ["branch on success", "fall-through", "fall-through, 2 stages", "commit every 2 stages"]
+    stamps = {}
+    forms = ["branch on success", "fall-through", "fall-through, 2 stages", "commit every 2 stages",
+             "three-barrier poll", "two commits per stage", "4 distinct operands",
+             "4 distinct, + 8 polling warps"]
     out = []
-    for ch, wf in [(0, 0), (2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1), (8, 0)]:
+    for ch, wf in [(0, 0), (2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1), (4, 4), (4, 5), (4, 6), (4, 7), (8, 0)]:
         for copy in ((0,) if ch == 0 else (0, 1, 2, 3)):
             for grid in (1, nsm) if copy < 2 else (nsm,):
                 cyc.zero_()
+                err.zero_()
                 assert probe.tc_mma_ring(ch, wf, 4096, copy, grid, src.data_ptr(), cyc.data_ptr(),
                                          err.data_ptr()) == 0
-                assert err.item() == 0
                 c = cyc[:grid].double().cpu()
-                out.append((ch, forms[wf], copy, grid, c.mean().item() / 4096, c.max().item() / 4096))
+                if wf >= 6:
+                    stamps[(wf, copy, grid)] = cyc[grid:grid + 24].cpu().tolist()
+                out.append((ch, forms[wf], copy, grid, c.mean().item() / 4096, c.max().item() / 4096, err.item()))
     with capsys.disabled():
-        for ch, form, copy, grid, mean, mx in out:
+        for ch, form, copy, grid, mean, mx, e in out:
             print(f"\n[mma ring] {ch} MMAs/stage, {form:22s} copy={copy & 1} sleep={copy >> 1} grid={grid:3d}  {mean:7.1f} cyc/mma "
-                  f"(max {mx:7.1f})")
+                  f"(max {mx:7.1f}) err={e}")
+        for (wf, copy, grid), st in stamps.items():
+            t0 = st[0]
+            print(f"\n[mma ring stages] wf={wf} copy={copy & 1} sleep={copy >> 1} grid={grid}: " +
+                  "  ".join(f"{st[3 * i] - t0}/{st[3 * i + 1] - t0}/{st[3 * i + 2] - t0}" for i in range(8)))
+    assert all(o[-1] == 0 for o in out)
