@@ -66,51 +66,47 @@ __device__ __forceinline__ Frame make_frame(const float d[3], const float wl[3])
     return F;
 }
 
-// Level geometry in the form one lookup needs: record index of cell (0,0,0) and the
-// record strides (records cover cells -1 .. n-1 on each axis).
-struct LevelGeom {
+// Per-level constants of one volume, staged in shared memory once per block: the
+// coordinate scale s = inv_h0 * 2^-m and gk = (inv_mean * 2^(k-1)) * s of level k (mip m),
+// the level dims, and the record index of cell (0,0,0) with the record strides (records
+// cover cells -1 .. n-1 on each axis).
+struct LevelK {
+    float s, gk;
     uint32_t ax, ay, az;
-    int64_t r000;
-    int32_t sy, sz;
+    uint32_t r000, sy, sz;
 };
 
-__device__ __forceinline__ LevelGeom level_geom(const VolumeView& v, int m) {
-    const LevelDesc L = v.lvl[m];
-    LevelGeom g;
-    g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
-    g.sy = L.ax + 1;
-    g.sz = (L.ax + 1) * (L.ay + 1);
-    g.r000 = L.rec_offset + g.sz + g.sy + 1;
-    return g;
-}
-
-// Trilinear lookup from one 32-byte corner record.  floor(u) by a saturating
-// round-down conversion: a cell index outside [-1, n-1] (including |u| huge) reads 0,
-// exactly as the reference clamps |u| to 1e6 first; the fraction is u - floor(u).
-__device__ __forceinline__ float lookup(const float* __restrict__ packed, const LevelGeom& g, const float u[3]) {
-    const int i0 = __float2int_rd(u[0]), i1 = __float2int_rd(u[1]), i2 = __float2int_rd(u[2]);
+// Trilinear lookup from one 32-byte corner record (c0, c1-c0, c2, c3-c2, c4, c5-c4, c6,
+// c7-c6).  floor(u) by a saturating round-down conversion: a cell index outside
+// [-1, n-1] (including |u| huge) reads 0, exactly as the reference clamps |u| to 1e6
+// first; the fraction is u - floor(u).  The x-lerps use the stored differences, which
+// round exactly as lerp_rn's own subtraction.
+__device__ __forceinline__ float lookup(const float4* __restrict__ packed, const LevelK& g, float u0, float u1,
+                                        float u2) {
+    const int i0 = __float2int_rd(u0), i1 = __float2int_rd(u1), i2 = __float2int_rd(u2);
     if ((uint32_t)(i0 + 1) > g.ax || (uint32_t)(i1 + 1) > g.ay || (uint32_t)(i2 + 1) > g.az) return 0.0f;
-    const float f0 = __fsub_rn(u[0], (float)i0);
-    const float f1 = __fsub_rn(u[1], (float)i1);
-    const float f2 = __fsub_rn(u[2], (float)i2);
-    const int64_t r = g.r000 + (int64_t)i2 * g.sz + (int64_t)i1 * g.sy + i0;
+    const float f0 = __fsub_rn(u0, (float)i0);
+    const float f1 = __fsub_rn(u1, (float)i1);
+    const float f2 = __fsub_rn(u2, (float)i2);
+    const uint32_t r = g.r000 + (uint32_t)i2 * g.sz + (uint32_t)i1 * g.sy + (uint32_t)i0;
     float c[8];
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
-        : "l"(packed + 8 * r));
-    const float c00 = lerp_rn(c[0], c[1], f0);
-    const float c10 = lerp_rn(c[2], c[3], f0);
-    const float c01 = lerp_rn(c[4], c[5], f0);
-    const float c11 = lerp_rn(c[6], c[7], f0);
+        : "l"(packed + 2 * (size_t)r));
+    const float c00 = __fmaf_rn(f0, c[1], c[0]);
+    const float c10 = __fmaf_rn(f0, c[3], c[2]);
+    const float c01 = __fmaf_rn(f0, c[5], c[4]);
+    const float c11 = __fmaf_rn(f0, c[7], c[6]);
     const float c0 = lerp_rn(c00, c10, f1);
     const float c1 = lerp_rn(c01, c11, f1);
     return lerp_rn(c0, c1, f2);
 }
 
-// One warp per shading point (8 per block, grid-stride over points, no block-wide
-// barrier).  The 250 column tasks (level k, stencil column (ix, iy)) are dealt to the
-// lanes in order; a task computes its level's set-up and the (ox, oy) part of the
-// coordinate once and walks the 9 points along z.  BF16 rows are assembled in a
+// One warp per shading point (8 per block, grid-stride over points, one block-wide
+// barrier at the start).  The 250 column tasks (level k, stencil column (ix, iy)) are
+// dealt to the lanes in order; a task reads its level's constants from shared memory,
+// computes the (ox, oy) part of the coordinate once and walks the 9 points along z
+// (fully unrolled: oz = -1 + 0.5 iz are constants).  BF16 rows are assembled in a
 // per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
 // directly (25 consecutive values per level and z-slice).
 template <class OutT>
@@ -121,9 +117,24 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
     constexpr int ROW = RPNN_K * RPNN_DESC_STRIDE;
     constexpr bool STAGE = sizeof(OutT) == 2;
     __shared__ __align__(16) OutT rowbuf[STAGE ? 8 : 1][STAGE ? ROW : 8];
+    __shared__ LevelK lk[RPNN_K];
+    if (threadIdx.x < RPNN_K) {
+        const int k = threadIdx.x;
+        const int m = v.mip_of_level[k];
+        const LevelDesc L = v.lvl[m];
+        LevelK g;
+        g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
+        g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
+        g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
+        g.sy = (uint32_t)(L.ax + 1);
+        g.sz = (uint32_t)((L.ax + 1) * (L.ay + 1));
+        g.r000 = (uint32_t)L.rec_offset + g.sz + g.sy + 1u;
+        lk[k] = g;
+    }
+    __syncthreads();
     const int64_t q = q_dev ? (int64_t)*q_dev : q_host;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float* packed = reinterpret_cast<const float*>(v.packed);
+    const float4* packed = v.packed;
     for (int64_t qi = (int64_t)blockIdx.x * 8 + warp; qi < q; qi += (int64_t)gridDim.x * 8) {
         const float x[3] = {__ldg(xs + 3 * qi), __ldg(xs + 3 * qi + 1), __ldg(xs + 3 * qi + 2)};
         const float d[3] = {__ldg(ds + 3 * qi), __ldg(ds + 3 * qi + 1), __ldg(ds + 3 * qi + 2)};
@@ -133,29 +144,25 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
         OutT* grow = out + qi * (int64_t)ROW;
         OutT* row = STAGE ? rowbuf[warp] : grow;
         for (int task = lane; task < RPNN_K * 25; task += 32) {
-            const int k = task / 25, col = task % 25;
-            const int ix = col % 5, iy = col / 5;
+            const int k = task / 25, col = task - 25 * k;
+            const int iy = col / 5, ix = col - 5 * iy;
             const float ox = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)ix));
             const float oy = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iy));
-            const int m = v.mip_of_level[k];
-            const float s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-            const float gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), s);
-            const LevelGeom geom = level_geom(v, m);
+            const LevelK g = lk[k];
             float P[3], C[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const float A = __fmul_rn(gk, F.ex[a]), B = __fmul_rn(gk, F.ey[a]);
-                C[a] = __fmul_rn(gk, F.ez[a]);
-                const float U0 = __fsub_rn(__fmul_rn(x[a], s), 0.5f);
+                const float A = __fmul_rn(g.gk, F.ex[a]), B = __fmul_rn(g.gk, F.ey[a]);
+                C[a] = __fmul_rn(g.gk, F.ez[a]);
+                const float U0 = __fsub_rn(__fmul_rn(x[a], g.s), 0.5f);
                 P[a] = __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0));
             }
             OutT* dst = row + k * RPNN_DESC_STRIDE + col;
-#pragma unroll 3
+#pragma unroll
             for (int iz = 0; iz < 9; ++iz) {
-                const float oz = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iz));
-                const float u[3] = {__fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
-                                    __fmaf_rn(oz, C[2], P[2])};
-                dst[iz * 25] = cvt_out<OutT>(lookup(packed, geom, u));
+                const float oz = -1.0f + 0.5f * (float)iz;      // exact: -1, -0.5, ..., 3
+                dst[iz * 25] = cvt_out<OutT>(lookup(packed, g, __fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
+                                                    __fmaf_rn(oz, C[2], P[2])));
             }
         }
         for (int e = lane; e < RPNN_K * (RPNN_DESC_STRIDE - RPNN_S); e += 32) {

@@ -110,7 +110,9 @@ __global__ void k_mip_pass(const float* __restrict__ in, float* __restrict__ out
 }
 
 // Corner packing: record (rx, ry, rz) of a level with dims (ax, ay, az) describes cell
-// (rx-1, ry-1, rz-1) and holds its 8 corner values (index dx + 2 dy + 4 dz, zero outside).
+// (rx-1, ry-1, rz-1).  With c[dx + 2 dy + 4 dz] its 8 corner values (zero outside), the
+// record holds c0, c1 - c0, c2, c3 - c2, c4, c5 - c4, c6, c7 - c6: the x-differences the
+// four x-lerps need, rounded exactly as a lerp rounds them.
 __global__ void k_pack(const float* __restrict__ lv, float4* __restrict__ rec, int ax, int ay, int az) {
     const int rx_n = ax + 1, ry_n = ay + 1, rz_n = az + 1;
     const int64_t total = (int64_t)rx_n * ry_n * rz_n;
@@ -126,8 +128,8 @@ __global__ void k_pack(const float* __restrict__ lv, float4* __restrict__ rec, i
             const bool in = x >= 0 && y >= 0 && z >= 0 && x < ax && y < ay && z < az;
             c[k] = in ? lv[((int64_t)z * ay + y) * ax + x] : 0.0f;
         }
-        rec[2 * r] = make_float4(c[0], c[1], c[2], c[3]);
-        rec[2 * r + 1] = make_float4(c[4], c[5], c[6], c[7]);
+        rec[2 * r] = make_float4(c[0], __fsub_rn(c[1], c[0]), c[2], __fsub_rn(c[3], c[2]));
+        rec[2 * r + 1] = make_float4(c[4], __fsub_rn(c[5], c[4]), c[6], __fsub_rn(c[7], c[6]));
     }
 }
 
