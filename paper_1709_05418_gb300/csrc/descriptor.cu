@@ -110,7 +110,7 @@ __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const
 // per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
 // directly (25 consecutive values per level and z-slice).
 template <class OutT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(OutT) == 2 ? 5 : 4)
 k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __restrict__ ds,
              const float* __restrict__ wls, int wl_stride, int64_t q_host,
              const int* __restrict__ q_dev, OutT* __restrict__ out) {
