@@ -250,6 +250,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // phases live in registers.
         if (lane == 0 && !*abort_flag) {
             uint32_t sw = 0, pw = 0, sz = 0, pz = 0;
+            uint32_t wfills = 0, zfills = 0;
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS && !*abort_flag; ++l) {
                     const int K = layer_k(l), zk = layer_zk(l), nb = layer_blocks(l);
@@ -261,6 +262,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                             tc::mbar_expect_tx(bar(B_ZFULL + sz), Z_STAGE);
                             tc::tma_load_2d(st, &zmap, x, t * TM, bar(B_ZFULL + sz));
                             tc::tma_load_2d(st + BLK_A, &zmap, x + 32, t * TM, bar(B_ZFULL + sz));
+                            ++zfills;
                             if (++sz == Z_STAGES) { sz = 0; pz ^= 1u; }
                         }
                         const int b0 = k0 / 32;
@@ -269,9 +271,18 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         tc::mbar_expect_tx(bar(B_WFULL + sw), bytes);
                         tc::bulk_g2s(base + OFF_W + sw * W_STAGE, a.img + a.img_off[l] + (int64_t)b0 * (BLK_B / 2),
                                      bytes, bar(B_WFULL + sw));
+                        ++wfills;
                         if (++sw == W_STAGES) { sw = 0; pw ^= 1u; }
                     }
                 }
+            }
+            if (*abort_flag) {
+                // drain: wait (bounded) for this thread's copies still in flight, i.e. for
+                // the latest fill of every ring slot to have landed
+                for (uint32_t s2 = 0; s2 < W_STAGES && s2 < wfills; ++s2)
+                    tc::mbar_poll(bar(B_WFULL + s2), ((wfills - 1 - s2) / W_STAGES) & 1u, tc::kSpinLimit);
+                for (uint32_t s2 = 0; s2 < Z_STAGES && s2 < zfills; ++s2)
+                    tc::mbar_poll(bar(B_ZFULL + s2), ((zfills - 1 - s2) / Z_STAGES) & 1u, tc::kSpinLimit);
             }
         }
     } else if (warp == 1) {
