@@ -34,6 +34,32 @@ FLOP_PER_QUERY = 2 * (10 * 226 * 200 + 9 * 200 * 200 + 10 * 200 * 200 + 2 * 200 
 L2_FLUSH_BYTES = 256 << 20
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per shading query of the
+# dominant kernels, from one ncu capture of the benchmark workload (178,847 queries; the
+# summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
+# captured build was compiled from.  A kernel whose sources changed since reports null.
+NCU_TRAFFIC = {
+    "descriptor": {"bytes_per_query": (797.670912e6 + 5.609472e6) / 178847,
+                   "sources": {"descriptor.cu": "82d6dfbb246bc4c6", "volume.cu": "019a6dcf787202e9"}},
+    "network": {"bytes_per_query": (889.980160e6 + 3.837440e6) / 178847,
+                "sources": {"mlp_tc.cu": "057df54b897d9822", "tc_ptx.cuh": "421861e4e92c024f"}},
+}
+
+
+def traffic_per_launch(kernel, nq):
+    """ncu-measured DRAM bytes for one launch over nq queries, or None if stale/unknown."""
+    import hashlib
+    t = NCU_TRAFFIC.get(kernel)
+    if t is None:
+        return None
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1709_05418_gb300", "csrc")
+    for name, digest in t["sources"].items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
+                return None
+    return t["bytes_per_query"] * nq
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -313,7 +339,8 @@ def main():
         ach = desc_bytes / (stage_ms[st] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = traffic_per_launch(dom, nq) if prec == api.BF16 else None
+    roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["kernel"] = dom
     roof["peak_src"] = pk["src"]
 
