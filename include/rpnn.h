@@ -185,6 +185,27 @@ enum { RPNN_MODE_RPNN = 0, RPNN_MODE_SINGLE = 1, RPNN_MODE_PATH = 2 };
  * it synchronises `stream`. */
 rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc,
                         float* dev_image, int64_t* out_num_queries, void* stream);
+/* Batched serving (no counterpart in the paper: many clouds, uneven query counts, one
+ * frame).  Item i renders volume items[i].vol with items[i].desc into items[i].dev_image
+ * (FP32, caller-owned, width*height) exactly as rpnn_render would, bit for bit.  The
+ * shading points of all items are compacted into one descriptor launch and one network
+ * launch; the whole sequence (per-item primary stages, a prefix sum of the per-item query
+ * counts, descriptor, network, per-item composites) is captured once as a CUDA graph on a
+ * library-owned stream and replayed on `stream` while the item list (volumes,
+ * descriptions, image pointers) is unchanged; loading a volume, building mips or setting
+ * weights invalidates the captured graph.  Requirements: 1 <= n_items <= RPNN_MAX_BATCH,
+ * every item in RPNN_MODE_RPNN with the same precision.  out_num_queries (host, may be
+ * NULL): n_items per-item shading-point counts; passing it synchronises `stream`.
+ * Errors: RPNN_ERR_ARG (empty, oversized or mixed batch, bad descriptions, null image),
+ * RPNN_ERR_HANDLE, RPNN_ERR_STATE (no weights), RPNN_ERR_OOM, RPNN_ERR_CUDA. */
+enum { RPNN_MAX_BATCH = 32 };
+typedef struct {
+    int32_t vol;
+    rpnn_render_desc desc;
+    float* dev_image;
+} rpnn_batch_item;
+rpnn_status rpnn_render_batch(rpnn_ctx* ctx, const rpnn_batch_item* items, int32_t n_items,
+                              int64_t* out_num_queries, void* stream);
 /* Stage timing (no counterpart in the paper; used to attribute render time).  When on,
  * rpnn_render records CUDA events on its stream at the boundaries of its four stages:
  * primary (tracking + NEE), descriptor, network, composite.  rpnn_read_profile waits for

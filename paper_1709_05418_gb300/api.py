@@ -39,6 +39,10 @@ class RenderDesc(C.Structure):
                 ("light_E", C.c_float), ("precision", C.c_int32), ("mode", C.c_int32)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("vol", C.c_int32), ("desc", RenderDesc), ("dev_image", C.c_void_p)]
+
+
 class VolumeInfo(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("levels", C.c_int32), ("dims", (C.c_int32 * 3) * 16),
                 ("mip_of_level", C.c_int32 * K), ("mean", C.c_double),
@@ -84,6 +88,7 @@ def load():
             "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
             "rpnn_render": [_vp, i32, C.POINTER(RenderDesc), _vp, C.POINTER(i64), _vp],
+            "rpnn_render_batch": [_vp, C.POINTER(BatchItem), i32, C.POINTER(i64), _vp],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
                                  _vp, _vp],
@@ -253,6 +258,26 @@ class Context:
         self._check(self.L.rpnn_render(self.h, vol, C.byref(rd), _ptr(image),
                                        C.byref(nq) if want_count else None, _stream()))
         return (image, nq.value) if want_count else image
+
+    def render_batch(self, jobs, images=None, want_counts=False):
+        """Renders several clouds in one batched launch sequence (BF16 network): `jobs` is a
+        list of (volume, camera dict); `images` (optional) the output tensors, which should
+        be reused across calls so the captured graph is replayed.  Returns the images (and
+        the per-item shading-point counts)."""
+        n = len(jobs)
+        arr = (BatchItem * n)()
+        out = []
+        for i, (vol, cam) in enumerate(jobs):
+            rd = self.render_desc(cam, BF16, MODE_RPNN)
+            img = images[i] if images is not None else torch.empty((rd.height, rd.width), dtype=torch.float32,
+                                                                      device="cuda")
+            arr[i].vol = vol
+            arr[i].desc = rd
+            arr[i].dev_image = _ptr(img)
+            out.append(img)
+        counts = (C.c_int64 * n)() if want_counts else None
+        self._check(self.L.rpnn_render_batch(self.h, arr, n, counts, _stream()))
+        return (out, list(counts)) if want_counts else out
 
     def trace_primary(self, vol, cam: dict):
         rd = self.render_desc(cam)

@@ -89,6 +89,8 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light};
     for (DevBuf* b : bufs) b->release();
+    batch_release(*c);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     delete c;
     return RPNN_OK;
@@ -107,6 +109,7 @@ rpnn_status rpnn_sync_status(rpnn_ctx* ctx, void* stream) {
     if (h & kStatIterLimit) { set_error("a device loop reached its iteration cap"); return RPNN_ERR_ITER_LIMIT; }
     if (h & kStatNonFinite) { set_error("non-finite value met on the device"); return RPNN_ERR_NONFINITE; }
     if (h & kStatTimeout) { set_error("a tensor-core pipeline wait timed out; its results are invalid"); return RPNN_ERR_TIMEOUT; }
+    if (h & kStatCapacity) { set_error("batched render: more shading points than its captured capacity"); return RPNN_ERR_STATE; }
     return RPNN_OK;
 }
 
@@ -134,6 +137,7 @@ rpnn_status rpnn_load_volume(rpnn_ctx* ctx, const void* dev_density, int32_t dty
     if (st) { v->raw.release(); delete v; return st; }
     c->vols.push_back(v);
     *out_vol = (int32_t)c->vols.size() - 1;
+    ++c->epoch;
     return RPNN_OK;
 }
 
@@ -143,6 +147,7 @@ rpnn_status rpnn_build_mips(rpnn_ctx* ctx, int32_t vol, void* stream) {
     Volume* v = get_vol(c, vol, false);
     if (!v) return RPNN_ERR_HANDLE;
     cudaStream_t s = (cudaStream_t)stream;
+    ++c->epoch;
     rpnn_status st = volume_stats(*c, *v, s);
     if (st) return st;
     return volume_pack_levels(*c, *v, s);
@@ -183,6 +188,7 @@ rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_p
     st = mlp_build_bf16_image(*c, s);
     if (st) return st;
     c->weights_set = true;
+    ++c->epoch;
     return RPNN_OK;
 }
 

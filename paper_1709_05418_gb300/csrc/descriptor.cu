@@ -109,38 +109,72 @@ __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const
 // (fully unrolled: oz = -1 + 0.5 iz are constants).  BF16 rows are assembled in a
 // per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
 // directly (25 consecutive values per level and z-slice).
-template <class OutT>
-__global__ void __launch_bounds__(256, sizeof(OutT) == 2 ? 5 : 4)
+//
+// level k's constants of volume v
+__device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
+    const int m = v.mip_of_level[k];
+    const LevelDesc L = v.lvl[m];
+    LevelK g;
+    g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
+    g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
+    g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
+    g.sy = (uint32_t)(L.ax + 1);
+    g.sz = (uint32_t)((L.ax + 1) * (L.ay + 1));
+    g.r000 = (uint32_t)L.rec_offset + g.sz + g.sy + 1u;
+    return g;
+}
+
+// BATCH: the shading points of up to RPNN_MAX_BATCH renders, compacted: point j belongs
+// to the item i with off[i] <= j < off[i+1], reads its position and direction at
+// region_i + j - off[i], and uses item i's volume and light; row j of `out` is written.
+template <class OutT, bool BATCH>
+__global__ void __launch_bounds__(256, sizeof(OutT) == 2 ? (BATCH ? 4 : 5) : 4)
 k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __restrict__ ds,
              const float* __restrict__ wls, int wl_stride, int64_t q_host,
-             const int* __restrict__ q_dev, OutT* __restrict__ out) {
+             const int* __restrict__ q_dev, OutT* __restrict__ out, const BatchItemDev* __restrict__ items,
+             int n_items, const int* __restrict__ off) {
     constexpr int ROW = RPNN_K * RPNN_DESC_STRIDE;
     constexpr bool STAGE = sizeof(OutT) == 2;
+    constexpr int NI = BATCH ? RPNN_MAX_BATCH : 1;
     __shared__ __align__(16) OutT rowbuf[STAGE ? 8 : 1][STAGE ? ROW : 8];
-    __shared__ LevelK lk[RPNN_K];
-    if (threadIdx.x < RPNN_K) {
-        const int k = threadIdx.x;
-        const int m = v.mip_of_level[k];
-        const LevelDesc L = v.lvl[m];
-        LevelK g;
-        g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-        g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
-        g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
-        g.sy = (uint32_t)(L.ax + 1);
-        g.sz = (uint32_t)((L.ax + 1) * (L.ay + 1));
-        g.r000 = (uint32_t)L.rec_offset + g.sz + g.sy + 1u;
-        lk[k] = g;
+    __shared__ LevelK lk[NI][RPNN_K];
+    __shared__ int s_off[NI + 1];
+    __shared__ int64_t s_region[NI];
+    __shared__ float s_light[NI][3];
+    __shared__ const float4* s_packed[NI];
+    if (BATCH) {
+        for (int e = threadIdx.x; e < n_items * RPNN_K; e += blockDim.x)
+            lk[e / RPNN_K][e % RPNN_K] = make_level(items[e / RPNN_K].v, e % RPNN_K);
+        for (int i = threadIdx.x; i <= n_items; i += blockDim.x) s_off[i] = off[i];
+        for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
+            s_region[i] = items[i].region;
+            s_packed[i] = items[i].v.packed;
+            for (int a = 0; a < 3; ++a) s_light[i][a] = items[i].light[a];
+        }
+    } else if (threadIdx.x < RPNN_K) {
+        lk[0][threadIdx.x] = make_level(v, threadIdx.x);
     }
     __syncthreads();
-    const int64_t q = q_dev ? (int64_t)*q_dev : q_host;
+    const int64_t q = BATCH ? (int64_t)s_off[n_items] : (q_dev ? (int64_t)*q_dev : q_host);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float4* packed = v.packed;
     for (int64_t qi = (int64_t)blockIdx.x * 8 + warp; qi < q; qi += (int64_t)gridDim.x * 8) {
-        const float x[3] = {__ldg(xs + 3 * qi), __ldg(xs + 3 * qi + 1), __ldg(xs + 3 * qi + 2)};
-        const float d[3] = {__ldg(ds + 3 * qi), __ldg(ds + 3 * qi + 1), __ldg(ds + 3 * qi + 2)};
-        const float* wp = wls + (int64_t)wl_stride * qi;
-        const float wl[3] = {__ldg(wp), __ldg(wp + 1), __ldg(wp + 2)};
+        int it = 0;
+        int64_t src = qi;
+        const float4* packed = v.packed;
+        float wl[3];
+        if (BATCH) {
+            while (it + 1 < n_items && s_off[it + 1] <= qi) ++it;
+            src = s_region[it] + (qi - s_off[it]);
+            packed = s_packed[it];
+            for (int a = 0; a < 3; ++a) wl[a] = s_light[it][a];
+        } else {
+            const float* wp = wls + (int64_t)wl_stride * qi;
+            for (int a = 0; a < 3; ++a) wl[a] = __ldg(wp + a);
+        }
+        const float x[3] = {__ldg(xs + 3 * src), __ldg(xs + 3 * src + 1), __ldg(xs + 3 * src + 2)};
+        const float d[3] = {__ldg(ds + 3 * src), __ldg(ds + 3 * src + 1), __ldg(ds + 3 * src + 2)};
         const Frame F = make_frame(d, wl);
+        const LevelK* lki = lk[it];
         OutT* grow = out + qi * (int64_t)ROW;
         OutT* row = STAGE ? rowbuf[warp] : grow;
         for (int task = lane; task < RPNN_K * 25; task += 32) {
@@ -148,7 +182,7 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
             const int iy = col / 5, ix = col - 5 * iy;
             const float ox = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)ix));
             const float oy = __fadd_rn(-1.0f, __fmul_rn(0.5f, (float)iy));
-            const LevelK g = lk[k];
+            const LevelK g = lki[k];
             float P[3], C[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -179,6 +213,17 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
     }
 }
 
+template <class OutT, bool BATCH>
+int blocks_per_sm() {
+    static int nb = 0;
+    if (!nb) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<OutT, BATCH>, 256, 0) != cudaSuccess ||
+            nb <= 0)
+            nb = 1;
+    }
+    return nb;
+}
+
 }  // namespace
 
 rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, const float* d,
@@ -186,22 +231,30 @@ rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, cons
                               void* out, int dtype, cudaStream_t s) {
     if (q <= 0 && !q_dev) return RPNN_OK;
     // one resident wave of blocks (8 shading points each), grid-stride beyond that
-    static int per_sm[2] = {0, 0};
-    const int ti = dtype == RPNN_F32 ? 0 : 1;
-    if (!per_sm[ti]) {
-        int nb = 0;
-        if (ti == 0) RPNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<float>, 256, 0));
-        else RPNN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<__nv_bfloat16>, 256, 0));
-        per_sm[ti] = nb > 0 ? nb : 1;
-    }
-    const int64_t wave = (int64_t)c.num_sms * per_sm[ti];
+    const int per_sm = dtype == RPNN_F32 ? blocks_per_sm<float, false>() : blocks_per_sm<__nv_bfloat16, false>();
+    const int64_t wave = (int64_t)c.num_sms * per_sm;
     int64_t g = q_dev ? wave : (q + 7) / 8;
     if (g > wave) g = wave;
     if (dtype == RPNN_F32)
-        k_descriptor<float><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (float*)out);
+        k_descriptor<float, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (float*)out, nullptr, 0,
+                                                          nullptr);
     else
-        k_descriptor<__nv_bfloat16><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
-                                                           (__nv_bfloat16*)out);
+        k_descriptor<__nv_bfloat16, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
+                                                                  (__nv_bfloat16*)out, nullptr, 0, nullptr);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_descriptor_batch(Ctx& c, const BatchItemDev* items, int n, const float* x, const float* d,
+                                    const int* off, int64_t cap, void* out, cudaStream_t s) {
+    if (n < 1 || n > RPNN_MAX_BATCH) { set_error("batch of %d items", n); return RPNN_ERR_ARG; }
+    const int64_t wave = (int64_t)c.num_sms * blocks_per_sm<__nv_bfloat16, true>();
+    int64_t g = (cap + 7) / 8;
+    if (g > wave) g = wave;
+    if (g < 1) g = 1;
+    VolumeView none{};
+    k_descriptor<__nv_bfloat16, true><<<(int)g, 256, 0, s>>>(none, x, d, nullptr, 0, cap, nullptr,
+                                                             (__nv_bfloat16*)out, items, n, off);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }

@@ -13,7 +13,8 @@ namespace rpnn {
 constexpr int kMaxLevels = 16;
 
 // status bits written by kernels into the context's device status word
-enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u, kStatTimeout = 8u };
+enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u, kStatTimeout = 8u,
+                  kStatCapacity = 16u };
 
 void set_error(const char* fmt, ...);
 
@@ -74,6 +75,25 @@ struct Volume {
     VolumeView view() const;
 };
 
+// One item of a batched render as the batched descriptor kernel reads it: the item's
+// volume, the offset of its region in the per-pixel-sample query buffers, its light.
+struct BatchItemDev {
+    VolumeView v;
+    int64_t region;
+    float light[4];
+};
+
+// A captured batched render: the item list it was captured for (the cache key), the
+// context epoch at capture, the graph, and the buffers it owns (stable while it lives).
+struct BatchGraph {
+    std::vector<rpnn_batch_item> items;
+    uint64_t epoch = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t cap = 0;                 // capacity of the compacted query arrays
+    DevBuf x, d, ps, sample, count, off, desc, g, table;
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 0;
@@ -86,6 +106,11 @@ struct Ctx {
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
+    // batched render: a captured graph, the stream it is captured on, and an epoch that
+    // volume loads, mip builds and weight updates advance (invalidating the graph)
+    BatchGraph batch;
+    cudaStream_t capture_stream = nullptr;
+    uint64_t epoch = 1;
     // stage timing: one set of 5 events per profiled render
     bool profiling = false;
     std::vector<cudaEvent_t> prof_events;
@@ -96,6 +121,7 @@ struct Ctx {
 };
 
 // ---- launchers implemented in the .cu files -------------------------------------------
+void batch_release(Ctx& c);           // frees the captured batch graph and its buffers
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s);
 rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s);
@@ -104,16 +130,23 @@ rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStre
 rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, const float* d,
                               const float* wl, int wl_stride, int64_t q, const int* q_dev,
                               void* out, int dtype, cudaStream_t s);
+// Batched form: compacted query j of item i (off[i] <= j < off[i+1], j < off[n]) reads
+// x, d at region_i + j - off[i] and writes descriptor row j.  BF16 output.
+rpnn_status launch_descriptor_batch(Ctx& c, const BatchItemDev* items, int n, const float* x, const float* d,
+                                    const int* off, int64_t cap, void* out, cudaStream_t s);
 
 // Primary stage.  Query outputs (qx, qd, qps, qcount) and inspection outputs (hit, xo,
 // dout, Ld; per pixel sample) are each optional.
 rpnn_status launch_primary(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd,
                            float* sample_val, float* qx, float* qd, uint32_t* qps, int* qcount,
                            int* hit, float* xo, float* dout, float* Ld, cudaStream_t s);
+// g_off / g_total (device, optional): this render's predictions start at g[*g_off] and
+// stop before g[*g_total] (batched renders)
 rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float alpha,
                                      const float* g, const uint32_t* qps, const int* qcount,
                                      float* sample_val, float* image, bool with_g,
-                                     cudaStream_t s);
+                                     cudaStream_t s, const int* g_off = nullptr,
+                                     const int* g_total = nullptr);
 rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n,
                            uint64_t seed, float rel_ci, int n_min, int n_max, float* x,
                            float* d, float* wl, float* label, int* npaths, cudaStream_t s);

@@ -601,7 +601,10 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
     // RPNN_TC_TRACE=1: per-role wait cycles of every block, summarised on stderr
     // (synchronises the stream; diagnostics only)
     static unsigned long long* trace_buf = nullptr;
-    const bool tracing = getenv("RPNN_TC_TRACE") != nullptr;
+    // (never while the stream is being captured into a graph: tracing synchronises)
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &capturing));
+    const bool tracing = getenv("RPNN_TC_TRACE") != nullptr && capturing == cudaStreamCaptureStatusNone;
     if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long)));
     a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;

@@ -85,10 +85,15 @@ k_primary(const VolumeView v, const RenderArgs a, int64_t P, float* __restrict__
 
 // sample_val[ps_i] += alpha * E * g_i for every shading query i
 __global__ void k_scatter(const float* __restrict__ g, const uint32_t* __restrict__ qps,
-                          const int* __restrict__ qcount, float scale, float* __restrict__ sample_val) {
-    const int n = *qcount;
+                          const int* __restrict__ qcount, const int* __restrict__ g_off,
+                          const int* __restrict__ g_total, float scale, float* __restrict__ sample_val) {
+    // predictions of this render's queries start at g[*g_off] (batched renders) and no
+    // index reaches *g_total
+    const int o = g_off ? *g_off : 0;
+    int n = *qcount;
+    if (g_total && *g_total - o < n) n = *g_total - o;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        sample_val[qps[i]] += scale * g[i];
+        sample_val[qps[i]] += scale * g[o + i];
 }
 
 // pixel = mean over its spp samples, summed in sample order
@@ -199,10 +204,11 @@ rpnn_status launch_primary(Ctx& c, const VolumeView& vv, const rpnn_render_desc&
 
 rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float alpha,
                                      const float* g, const uint32_t* qps, const int* qcount,
-                                     float* sample_val, float* image, bool with_g, cudaStream_t s) {
+                                     float* sample_val, float* image, bool with_g, cudaStream_t s,
+                                     const int* g_off, const int* g_total) {
     const int64_t npix = (int64_t)rd.width * rd.height;
     if (with_g) {
-        k_scatter<<<c.num_sms * 8, 256, 0, s>>>(g, qps, qcount, alpha * rd.light_E, sample_val);
+        k_scatter<<<c.num_sms * 8, 256, 0, s>>>(g, qps, qcount, g_off, g_total, alpha * rd.light_E, sample_val);
         RPNN_CHECK_LAUNCH();
     }
     int64_t b = (npix + 255) / 256;

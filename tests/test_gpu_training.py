@@ -51,3 +51,51 @@ def test_training_reduces_loss_and_beats_single_scattering(env):
     rmse_rpnn = float(torch.sqrt(((rp - ref)[mask] ** 2).mean()))
     rmse_ss = float(torch.sqrt(((ss - ref)[mask] ** 2).mean()))
     assert rmse_rpnn < 0.7 * rmse_ss, (rmse_rpnn, rmse_ss)
+
+
+def test_autograd_function_matches_oracle_gradient(env):
+    """rpnn() under torch.autograd gives the FP64 oracle's parameter gradient (the oracle's
+    backward is pinned against finite differences in the CPU tests)."""
+    import oracle
+    from paper_1709_05418_gb300.autograd import rpnn
+    api, train, ctx = env
+    rng = np.random.default_rng(31)
+    z = np.zeros((300, 10, 240), np.float32)
+    z[:, :, :226] = rng.uniform(0, 2, size=(300, 10, 226))
+    p = W.he_init(seed=32, bias=0.02, positive_head=True)
+    w = rng.normal(size=300)
+    pt = torch.from_numpy(p).cuda().requires_grad_(True)
+    g = rpnn(pt, torch.from_numpy(z).cuda(), ctx)
+    (g.double() * torch.from_numpy(w).cuda()).sum().backward()
+    ref_g = oracle.mlp_forward(p.astype(np.float64), z[:, :, :226].astype(np.float64))
+    ref = oracle.mlp_backward(p.astype(np.float64), z[:, :, :226].astype(np.float64), w)
+    ctx.sync_status()
+    assert np.abs(g.detach().cpu().numpy() - ref_g).max() <= 1e-4 * np.abs(ref_g).max()
+    got = pt.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_autograd_function_trains_with_torch_adam(env):
+    """The log-MSE loss of Sec. 5.2 through rpnn() and torch.optim.Adam decreases."""
+    from paper_1709_05418_gb300.autograd import rpnn
+    api, train, ctx = env
+    clouds = train.blob_clouds(2, size=40, seed0=400)
+    desc, label = train.records(ctx, clouds, 2000, seed=21, rel_ci=0.2, n_min=16, n_max=128)
+    p = torch.from_numpy(W.he_init(seed=7)).cuda().mul_(0.5).requires_grad_(True)
+    opt = torch.optim.Adam([p], lr=1e-3)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+
+    def loss_of(idx):
+        g = rpnn(p, desc[idx], ctx)
+        return ((torch.log1p(g) - torch.log1p(label[idx])) ** 2).mean()
+
+    with torch.no_grad():
+        l0 = loss_of(torch.arange(desc.shape[0], device="cuda")).item()
+    for _ in range(150):
+        idx = torch.randint(0, desc.shape[0], (512,), device="cuda", generator=gen)
+        opt.zero_grad()
+        loss_of(idx).backward()
+        opt.step()
+    with torch.no_grad():
+        l1 = loss_of(torch.arange(desc.shape[0], device="cuda")).item()
+    assert l1 < 0.5 * l0, (l0, l1)
