@@ -52,13 +52,13 @@ constexpr uint32_t BLK_A = TM * 64;     // 8192: 32 columns of 128 rows
 constexpr uint32_t BLK_B = NP * 64;     // 13312: 32 columns of 208 rows
 constexpr int NBLK = 7;                 // 32-column blocks of a 208-wide activation
 constexpr int NPUB = 4;                 // epilogue publication points: blocks {0,1} {2,3} {4,5} {6}
-constexpr int W_STAGES = 4, Z_STAGES = 3;
+constexpr int W_STAGES = 4, Z_STAGES = 4;
 constexpr uint32_t W_STAGE = 2 * BLK_B;                        // 26624
 constexpr uint32_t Z_STAGE = 2 * BLK_A;                        // 16384
 constexpr uint32_t OFF_X = 0;
 constexpr uint32_t OFF_W = OFF_X + NBLK * BLK_A;               // 57344
 constexpr uint32_t OFF_Z = OFF_W + W_STAGES * W_STAGE;         // 163840
-constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 212992
+constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 229376
 constexpr uint32_t BAR_STRIDE = 16;
 constexpr int EPI_THREADS = 256;         // 8 epilogue warps
 constexpr int EPI_WARPS = EPI_THREADS / 32;
@@ -199,6 +199,92 @@ __device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
+}
+
+// Epilogue of one layer for one warp: 16 columns of each 32-column block for the warp's
+// 32 rows (already loaded from tensor memory into v), published in block pairs.
+enum { EPI_PLAIN = 0, EPI_KEEP = 1, EPI_FIRST = 2, EPI_LAST = 3 };
+struct EpiArgs {
+    unsigned char* X;
+    int row, sw, half, lane;
+    uint32_t blk_bar;             // publication barrier 0 (the others follow at BAR_STRIDE)
+    const float* bias;            // FP32 bias table (block 1's first layer)
+    const float* w3;              // output layer weights
+    uint32_t taddr;               // the warp's accumulator columns
+    long long *et, *wt, *pt;      // diagnostics stamps or null
+};
+
+// KIND: EPI_PLAIN ReLU + BF16; EPI_KEEP also writes o^k back into the accumulator (the next
+// second layer's start value); EPI_FIRST adds the FP32 bias (block 1's first layer, whose
+// MMAs read no activation column); EPI_LAST is the output layer's ReLU and dot product.
+template <int KIND>
+__device__ __forceinline__ void epi_layer(const EpiArgs& e, float (&v)[NBLK * 16], float& dot) {
+#pragma unroll
+    for (int b = 0; b < NBLK; ++b) {
+        const int c0 = 32 * b + 16 * e.half;
+        float* w = v + 16 * b;
+        // accumulator columns 200..207 are exactly zero (zero weight rows and zero start
+        // values), so ReLU needs no column mask
+        if (c0 < NP) {
+            if (KIND == EPI_FIRST) {
+                const float4* b4 = reinterpret_cast<const float4*>(e.bias + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 bb = __ldg(b4 + q);
+                    w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
+                }
+            }
+            if (KIND == EPI_KEEP || KIND == EPI_LAST) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
+            }
+            if (KIND == EPI_KEEP) tc::tmem_st16(e.taddr + 32u * b, w);
+            if (KIND == EPI_LAST) {
+                const float4* w4 = reinterpret_cast<const float4*>(e.w3 + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 ww = __ldg(w4 + q);
+                    dot = fmaf(w[4 * q], ww.x, dot); dot = fmaf(w[4 * q + 1], ww.y, dot);
+                    dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
+                }
+            } else {
+                // BF16 pairs (ReLU folded into the conversion unless already applied)
+                uint4 p0, p1;
+                uint32_t* u0 = reinterpret_cast<uint32_t*>(&p0);
+                uint32_t* u1 = reinterpret_cast<uint32_t*>(&p1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (KIND == EPI_KEEP) {
+                        u0[q] = pack_bf16x2(w[2 * q], w[2 * q + 1]);
+                        u1[q] = pack_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
+                    } else {
+                        u0[q] = pack_relu_bf16x2(w[2 * q], w[2 * q + 1]);
+                        u1[q] = pack_relu_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
+                    }
+                }
+                // column 200 carries the constant 1 that multiplies the next layer's bias
+                if (b == NBLK - 1) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
+                // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
+                unsigned char* rb = e.X + b * BLK_A + e.row * 64;
+                *reinterpret_cast<uint4*>(rb + (((2 * e.half) ^ e.sw) << 4)) = p0;
+                *reinterpret_cast<uint4*>(rb + (((2 * e.half + 1) ^ e.sw) << 4)) = p1;
+            }
+        }
+        if ((b & 1) || b == NBLK - 1) {
+            // publish blocks b-1, b: make the stores visible to the tensor core, and (last
+            // block) complete the accumulator write-back first, since the MMAs that start
+            // from it wait for the last publication
+            if (e.et) e.et[1 + (b >> 1)] = clock64();
+            tc::fence_proxy_async_smem();
+            if (b == NBLK - 1 && KIND == EPI_KEEP) tc::tmem_wait_st();
+            tc::tc_fence_before();
+            __syncwarp();
+            if (e.et) e.et[5 + (b >> 1)] = clock64();
+            if (e.lane == 0) tc::mbar_arrive(e.blk_bar + BAR_STRIDE * (uint32_t)(b >> 1));
+            if (e.wt) e.wt[b >> 1] = clock64();
+            if (e.pt) e.pt[b >> 1] = clock64();
+        }
+    }
 }
 
 template <bool TRACE>
@@ -375,68 +461,20 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
                 float v[NBLK * 16];
                 tc::tmem_ld16x7(taddr, v);
-                const bool keep = layer_keeps_o(l);
-#pragma unroll
-                for (int b = 0; b < NBLK; ++b) {
-                    const int c0 = 32 * b + 16 * half;
-                    float* w = v + 16 * b;
-                    // accumulator columns 200..207 are exactly zero (zero weight rows and
-                    // zero start values), so ReLU needs no column mask
-                    if (c0 < NP) {
-                        if (l == 0) {
-                            const float4* b4 = reinterpret_cast<const float4*>(a.bias + c0);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 bb = __ldg(b4 + q);
-                                w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
-                            }
-                        }
-                        if (keep || l == 21) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
-                        }
-                        // o^k stays in the accumulator as the next second layer's start value
-                        if (keep) tc::tmem_st16(taddr + 32u * b, w);
-                        if (l == 21) {
-                            const float4* w4 = reinterpret_cast<const float4*>(a.w3 + c0);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 ww = __ldg(w4 + q);
-                                dot = fmaf(w[4 * q], ww.x, dot); dot = fmaf(w[4 * q + 1], ww.y, dot);
-                                dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
-                            }
-                        } else {
-                            // BF16 pairs (ReLU folded into the conversion unless already applied)
-                            uint4 p0, p1;
-                            uint32_t* u0 = reinterpret_cast<uint32_t*>(&p0);
-                            uint32_t* u1 = reinterpret_cast<uint32_t*>(&p1);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                u0[q] = keep ? pack_bf16x2(w[2 * q], w[2 * q + 1]) : pack_relu_bf16x2(w[2 * q], w[2 * q + 1]);
-                                u1[q] = keep ? pack_bf16x2(w[8 + 2 * q], w[9 + 2 * q])
-                                             : pack_relu_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
-                            }
-                            // column 200 carries the constant 1 that multiplies the next layer's bias
-                            if (b == NBLK - 1) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
-                            // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
-                            unsigned char* rb = Xsm + b * BLK_A + row * 64;
-                            *reinterpret_cast<uint4*>(rb + (((2 * half) ^ sw) << 4)) = p0;
-                            *reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ sw) << 4)) = p1;
-                        }
-                    }
-                    if ((b & 1) || b == NBLK - 1) {
-                        // publish blocks b-1, b: make the stores visible to the tensor core,
-                        // and (last block) complete the accumulator write-back first, since
-                        // the MMAs that start from it wait for the last publication
-                        tc::fence_proxy_async_smem();
-                        if (b == NBLK - 1 && keep) tc::tmem_wait_st();
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(bar(B_BLK + (b >> 1)));
-                        if (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
-                            tl[2048 + 48 + (n - 23) * 8 + (b >> 1)] = clock64();
-                    }
-                }
+                // diagnostics (block 0, warp 2, instances 23 and 24): after the load, before
+                // and after each publication's fences
+                long long* et = (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
+                                    ? tl + 2048 + 64 + (n - 23) * 16 : nullptr;
+                if (et) et[0] = clock64();
+                long long* wt = (TRACE && tl && lane == 0 && n == 24) ? tl + 2048 + 96 + (warp - 2) * 4 : nullptr;
+                long long* pt = (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
+                                    ? tl + 2048 + 48 + (n - 23) * 8 : nullptr;
+                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, taddr, et, wt, pt};
+                // one straight-line routine per layer kind
+                if (l == 0) epi_layer<EPI_FIRST>(ea, v, dot);
+                else if (l == 21) epi_layer<EPI_LAST>(ea, v, dot);
+                else if (layer_keeps_o(l)) epi_layer<EPI_KEEP>(ea, v, dot);
+                else epi_layer<EPI_PLAIN>(ea, v, dot);
                 if (TRACE && tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
             if (!ok) break;
@@ -641,6 +679,17 @@ rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int
             const long long* pub = &tlh[2048 + 48 + inst * 8];
             fprintf(stderr, "[rpnn tc stages] inst %d: epilogue %d acc-ready %lld pubs %lld %lld %lld %lld\n", 24 + inst,
                     23 + inst, tlh[4 * (23 + inst) + 2] - t0, pub[0] - t0, pub[1] - t0, pub[2] - t0, pub[3] - t0);
+            const long long* et = &tlh[2048 + 64 + inst * 16];
+            const long long ea = tlh[4 * (23 + inst) + 2];
+            fprintf(stderr, "[rpnn tc epilogue] inst %d (from acc-ready): tmem-ld %lld | pubs: stores %lld %lld %lld %lld"
+                            " / fenced %lld %lld %lld %lld\n", 23 + inst, et[0] - ea, et[1] - ea, et[2] - ea, et[3] - ea,
+                    et[4] - ea, et[5] - ea, et[6] - ea, et[7] - ea, et[8] - ea);
+            if (inst == 1) {
+                for (int w = 0; w < 8; ++w)
+                    fprintf(stderr, "[rpnn tc epilogue] inst 24 warp %d (scheduler %d): pubs %lld %lld %lld %lld\n", w + 2,
+                            (w + 2) & 3, tlh[2048 + 96 + w * 4] - ea, tlh[2048 + 96 + w * 4 + 1] - ea,
+                            tlh[2048 + 96 + w * 4 + 2] - ea, tlh[2048 + 96 + w * 4 + 3] - ea);
+            }
             for (int j = 0; j < 8 && st[3 * j]; ++j)
                 fprintf(stderr, "[rpnn tc stages] inst %d stage %d  poll %6lld .. %6lld  commit %6lld\n", 24 + inst, j,
                         st[3 * j] - t0, st[3 * j + 1] - t0, st[3 * j + 2] - t0);

@@ -11,6 +11,10 @@ namespace tc {
 // upper bound on polls of one mbarrier phase before a wait gives up (each poll of
 // try_wait may itself suspend for a short, hardware-defined time)
 constexpr uint32_t kSpinLimit = 1u << 24;
+// Suspend-time hint of the issuing thread's polls: a poll whose phase is not complete
+// suspends the thread (up to this many ns, or until the phase completes) instead of
+// spinning, leaving the scheduler's issue slots to the warps that share it.
+constexpr uint32_t kPollHintNs = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -46,14 +50,14 @@ __device__ __forceinline__ uint32_t mbar_poll(uint32_t bar, uint32_t parity, uin
         " .reg .pred P1;\n"
         " mov.u32 %0, %3;\n"
         "WAIT_%=:\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %4;\n"
         " @P1 bra DONE_%=;\n"
         " sub.u32 %0, %0, 1;\n"
         " setp.ne.u32 P1, %0, 0;\n"
         " @P1 bra WAIT_%=;\n"
         "DONE_%=:\n"
         "}\n"
-        : "=r"(left) : "r"(bar), "r"(parity), "r"(limit) : "memory");
+        : "=r"(left) : "r"(bar), "r"(parity), "r"(limit), "r"(kPollHintNs) : "memory");
     return left;
 }
 
@@ -72,7 +76,7 @@ __device__ __forceinline__ void mbar_wait_issuer(uint32_t bar, uint32_t parity, 
         " .reg .u32 c, f;\n"
         " mov.u32 c, %2;\n"
         "WAIT_%=:\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1, %4;\n"
         " @P1 bra DONE_%=;\n"
         " ld.volatile.shared.u32 f, [%3];\n"
         " setp.ne.u32 P1, f, 0;\n"
@@ -82,7 +86,7 @@ __device__ __forceinline__ void mbar_wait_issuer(uint32_t bar, uint32_t parity, 
         " @P1 bra WAIT_%=;\n"
         " st.volatile.shared.u32 [%3], 1;\n"
         "DONE_%=:\n"
-        "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr) : "memory");
+        "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr), "r"(kPollHintNs) : "memory");
 }
 
 // As mbar_wait_issuer, for three barriers at once (each with its own parity): the poll
@@ -96,10 +100,10 @@ __device__ __forceinline__ void mbar_wait_issuer3(uint32_t b0, uint32_t p0, uint
         " .reg .u32 c, f;\n"
         " mov.u32 c, %6;\n"
         "WAIT_%=:\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%2], %3;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1, %8;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%2], %3, %8;\n"
         " and.pred P1, P1, P2;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%4], %5;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%4], %5, %8;\n"
         " and.pred P1, P1, P2;\n"
         " @P1 bra DONE_%=;\n"
         " ld.volatile.shared.u32 f, [%7];\n"
@@ -110,7 +114,8 @@ __device__ __forceinline__ void mbar_wait_issuer3(uint32_t b0, uint32_t p0, uint
         " @P1 bra WAIT_%=;\n"
         " st.volatile.shared.u32 [%7], 1;\n"
         "DONE_%=:\n"
-        "}\n" ::"r"(b0), "r"(p0), "r"(b1), "r"(p1), "r"(b2), "r"(p2), "r"(limit), "r"(abort_addr) : "memory");
+        "}\n" ::"r"(b0), "r"(p0), "r"(b1), "r"(p1), "r"(b2), "r"(p2), "r"(limit), "r"(abort_addr),
+          "r"(kPollHintNs) : "memory");
 }
 
 // Bounded wait for the phase with the given parity.  Gives up (returns false) after
