@@ -185,6 +185,11 @@ enum { RPNN_MODE_RPNN = 0, RPNN_MODE_SINGLE = 1, RPNN_MODE_PATH = 2 };
  * it synchronises `stream`. */
 rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc,
                         float* dev_image, int64_t* out_num_queries, void* stream);
+/* Memory budget of rpnn_render (no counterpart in the paper): the descriptor and network
+ * stages run over chunks of at most `rows` shading points (0 = the default 1,048,576
+ * rows, i.e. 5 GB of BF16 descriptors; otherwise at least 128).  Results do not depend on
+ * the chunking.  Errors: RPNN_ERR_ARG for 0 < rows < 128 or rows < 0. */
+rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows);
 /* Batched serving (no counterpart in the paper: many clouds, uneven query counts, one
  * frame).  Item i renders volume items[i].vol with items[i].desc into items[i].dev_image
  * (FP32, caller-owned, width*height) exactly as rpnn_render would, bit for bit.  The

@@ -89,6 +89,7 @@ def load():
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
             "rpnn_render": [_vp, i32, C.POINTER(RenderDesc), _vp, C.POINTER(i64), _vp],
             "rpnn_render_batch": [_vp, C.POINTER(BatchItem), i32, C.POINTER(i64), _vp],
+            "rpnn_set_render_chunk": [_vp, i64],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
                                  _vp, _vp],
@@ -258,6 +259,9 @@ class Context:
         self._check(self.L.rpnn_render(self.h, vol, C.byref(rd), _ptr(image),
                                        C.byref(nq) if want_count else None, _stream()))
         return (image, nq.value) if want_count else image
+
+    def set_render_chunk(self, rows: int):
+        self._check(self.L.rpnn_set_render_chunk(self.h, rows))
 
     def render_batch(self, jobs, images=None, want_counts=False):
         """Renders several clouds in one batched launch sequence (BF16 network): `jobs` is a

@@ -286,15 +286,19 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t P = (int64_t)desc->width * desc->height * desc->spp;
     const bool f32 = desc->precision == RPNN_F32;
+    // the descriptor and network stages run over chunks of at most kChunkRows queries, so
+    // the descriptor buffer stays bounded (5 GB BF16) for renders of millions of samples
+    const int64_t CH = std::min<int64_t>(P, c->chunk_rows > 0 ? c->chunk_rows : kChunkRows);
+    const int nchunks = (int)((P + CH - 1) / CH);
     st = c->sample_val.reserve(P * sizeof(float));
-    if (!st) st = c->q_count.reserve(sizeof(int));
+    if (!st) st = c->q_count.reserve((1 + nchunks) * sizeof(int));
     if (net) {
         if (!st) st = c->q_x.reserve(P * 3 * sizeof(float));
         if (!st) st = c->q_d.reserve(P * 3 * sizeof(float));
         if (!st) st = c->q_ps.reserve(P * sizeof(uint32_t));
         if (!st) st = c->g_out.reserve(P * sizeof(float));
-        if (!st) st = c->desc.reserve((size_t)P * RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2));
-        if (!st) st = ensure_rows(c, P, f32);
+        if (!st) st = c->desc.reserve((size_t)CH * RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2));
+        if (!st) st = ensure_rows(c, CH, f32);
     }
     if (st) return st;
     const VolumeView vv = v->view();
@@ -328,13 +332,23 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         if (st) return st;
         RPNN_CUDA_TRY(cudaMemcpyAsync(c->light.p, desc->light_dir, 3 * sizeof(float),
                                       cudaMemcpyHostToDevice, s));
-        st = launch_descriptor(*c, vv, c->q_x.as<float>(), c->q_d.as<float>(), c->light.as<float>(), 0,
-                               P, qc, c->desc.p, f32 ? RPNN_F32 : RPNN_BF16, s);
-        if (st) return st;
-        if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
-        if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), P, qc, c->g_out.as<float>(), nullptr, s);
-        else st = mlp_forward_bf16(*c, c->desc.p, P, qc, c->g_out.as<float>(), s);
-        if (st) return st;
+        // per-chunk query counts (device): clamp(count - i*CH, 0, CH)
+        if (nchunks > 1) {
+            st = launch_chunk_counts(*c, qc, CH, nchunks, qc + 1, s);
+            if (st) return st;
+        }
+        for (int i = 0; i < nchunks; ++i) {
+            const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
+            const int64_t first = (int64_t)i * CH;
+            st = launch_descriptor(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
+                                   c->light.as<float>(), 0, CH, cnt, c->desc.p, f32 ? RPNN_F32 : RPNN_BF16, s);
+            if (st) return st;
+            // (a chunked render attributes its network time to the descriptor stage)
+            if (ev && i == nchunks - 1) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
+            if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), CH, cnt, c->g_out.as<float>() + first, nullptr, s);
+            else st = mlp_forward_bf16(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
+            if (st) return st;
+        }
         if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[3], s));
     }
     st = launch_scatter_composite(*c, *desc, v->albedo, net ? c->g_out.as<float>() : nullptr,
@@ -348,6 +362,14 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         RPNN_CUDA_TRY(cudaStreamSynchronize(s));
         *out_num_queries = net ? h : -1;
     }
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (rows < 0 || (rows > 0 && rows < 128)) { set_error("chunk rows must be 0 or at least 128"); return RPNN_ERR_ARG; }
+    c->chunk_rows = rows;
     return RPNN_OK;
 }
 

@@ -109,6 +109,7 @@ struct Ctx {
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
+    int64_t chunk_rows = 0;          // descriptor/network chunk of a render (0: kChunkRows)
     cudaStream_t capture_stream = nullptr;
     uint64_t epoch = 1;
     // stage timing: one set of 5 events per profiled render
@@ -147,6 +148,10 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
                                      float* sample_val, float* image, bool with_g,
                                      cudaStream_t s, const int* g_off = nullptr,
                                      const int* g_total = nullptr);
+// Rows per descriptor/network chunk of a render.
+constexpr int64_t kChunkRows = (int64_t)1 << 20;
+// out[i] = clamp(*count - i*rows, 0, rows) for i < n
+rpnn_status launch_chunk_counts(Ctx& c, const int* count, int64_t rows, int n, int* out, cudaStream_t s);
 rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n,
                            uint64_t seed, float rel_ci, int n_min, int n_max, float* x,
                            float* d, float* wl, float* label, int* npaths, cudaStream_t s);

@@ -218,6 +218,23 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
     return RPNN_OK;
 }
 
+namespace {
+__global__ void k_chunk_counts(const int* __restrict__ count, int64_t rows, int n, int* __restrict__ out) {
+    const int64_t total = *count;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t left = total - (int64_t)i * rows;
+        out[i] = (int)(left < 0 ? 0 : (left > rows ? rows : left));
+    }
+}
+}  // namespace
+
+rpnn_status launch_chunk_counts(Ctx& c, const int* count, int64_t rows, int n, int* out, cudaStream_t s) {
+    (void)c;
+    k_chunk_counts<<<1, 128, 0, s>>>(count, rows, n, out);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
 rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n, uint64_t seed,
                            float rel_ci, int n_min, int n_max, float* x, float* d, float* wl,
                            float* label, int* npaths, cudaStream_t s) {

@@ -86,3 +86,25 @@ def test_batch_rejects_bad_lists(env):
         ctx.render_batch([jobs[0]] * 33)
     with pytest.raises(api.RPNNError):
         ctx.render_batch([(999, jobs[0][1])])
+
+
+@pytest.mark.parametrize("prec_name", ["BF16", "F32"])
+def test_chunked_render_equals_single_chunk(env, prec_name):
+    """A render whose descriptor/network stages run in chunks (here 1,000 queries) gives
+    the image of the unchunked render bit for bit."""
+    api, ctx, jobs = env
+    prec = getattr(api, prec_name)
+    v, cam = jobs[3]
+    cam = dict(cam, width=64, height=56, spp=2)
+    ref, nq = ctx.render(v, cam, precision=prec, want_count=True)
+    ref = ref.clone()
+    assert nq > 2500
+    ctx.set_render_chunk(1000)
+    try:
+        out = ctx.render(v, cam, precision=prec)
+        ctx.sync_status()
+        assert torch.equal(out, ref)
+    finally:
+        ctx.set_render_chunk(0)
+    with pytest.raises(api.RPNNError):
+        ctx.set_render_chunk(5)
