@@ -772,3 +772,116 @@ extern "C" int tc_pack_rate(int mode, int iters, long long* cycles, unsigned* si
     if (cudaDeviceSynchronize() != cudaSuccess) return -14;
     return 0;
 }
+
+namespace {
+
+// ---- FP8 (E4M3) operands: the same byte geometry as the BF16 probe ------------------
+// A (128 x 128 E4M3) written by threads in two 64-byte-wide blocks (64 elements per row),
+// B (208 x 128) by two bulk copies of a pre-swizzled image, four K = 32 MMAs of
+// kind::f8f6f4 (E4M3 x E4M3 -> FP32); a 2-D TMA box {64 bytes, 128 rows} of a uint8
+// tensor with the 64-byte swizzle is written out raw.
+__device__ __forceinline__ uint32_t idesc_e4m3(int M_, int N_) {
+    return (1u << 4)                       // D format: F32
+         | (0u << 7)                       // A format: E4M3
+         | (0u << 10)                      // B format: E4M3
+         | ((uint32_t)(N_ >> 3) << 17)
+         | ((uint32_t)(M_ >> 4) << 24);
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_probe_fp8(const unsigned char* __restrict__ A,
+                                                   const unsigned char* __restrict__ Bimg,
+                                                   const __grid_constant__ CUtensorMap tmap,
+                                                   float* __restrict__ D, uint4* __restrict__ tma_out,
+                                                   int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ int abort_flag;
+    constexpr uint32_t SA = 0, SB = 16384, ST = 45056, SBAR = 65536, SSLOT = 65600;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t base = smem_u32(sm);
+    if ((base & 1023u) != 0) { if (tid == 0) atomicOr(err, 8); return; }
+    const uint32_t bar = base + SBAR, bar_mma = base + SBAR + 8;
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        mbar_init(bar_mma, 1);
+        fence_mbar_init();
+    }
+    // element (r, c), c < 128: block c / 64, row r at r * 64, 16-byte unit (c % 64) / 16
+    // at unit ^ ((r >> 1) & 3), byte c % 16 within it
+    for (int i = tid; i < 128 * 128; i += 128) {
+        const int r = i / 128, c = i % 128;
+        sm[SA + (c / 64) * 8192 + r * 64 + ((((c & 63) >> 4) ^ ((r >> 1) & 3)) << 4) + (c & 15)] = A[i];
+    }
+    fence_proxy_async_smem();
+    if (warp == 0) tmem_alloc(base + SSLOT, 256);
+    if (warp == 0) tmem_relinquish();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + SSLOT);
+    if (tid == 0) {
+        mbar_expect_tx(bar, 2 * 13312 + 8192);
+        bulk_g2s(base + SB, Bimg, 13312, bar);
+        bulk_g2s(base + SB + 13312, Bimg + 13312, 13312, bar);
+        tma_load_2d(base + ST, &tmap, 64, 0, bar);
+        if (!mbar_wait(bar, 0, &abort_flag)) { atomicOr(err, 1); }
+        else {
+            tc_fence_after();
+            const uint32_t id = idesc_e4m3(128, 208);
+            for (int j = 0; j < 4; ++j) {        // K = 128: blocks of 64 bytes, two K=32 steps each
+                const uint64_t a = smem_desc_sw64(base + SA + (j / 2) * 8192 + (j % 2) * 32);
+                const uint64_t b = smem_desc_sw64(base + SB + (j / 2) * 13312 + (j % 2) * 32);
+                mma_e4m3(tmem, a, b, id, j > 0);
+            }
+            mma_commit(bar_mma);
+        }
+    }
+    __syncwarp();
+    if (!mbar_wait(bar_mma, 0, &abort_flag)) atomicOr(err, 2);
+    tc_fence_after();
+    if (!abort_flag) {
+        const uint32_t lane_base = (uint32_t)(32 * (warp % 4)) << 16;
+        for (int c = 0; c < 208; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + c, v);
+            const int row = 32 * (warp % 4) + lane;
+            for (int i = 0; i < 16; ++i) D[row * 208 + c + i] = v[i];
+        }
+        for (int i = tid; i < 512; i += 128) tma_out[i] = reinterpret_cast<const uint4*>(sm + ST)[i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+extern "C" int tc_probe_fp8(const void* A, const void* Bimg, const void* T2d, int t_rows, int t_cols, float* D,
+                            void* tma_out, int* err) {
+    typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess || !fn)
+        return -10;
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)t_cols, (cuuint64_t)t_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)t_cols};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = ((EncodeFn)fn)(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(T2d), dims, strides, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -11;
+    if (cudaFuncSetAttribute(k_probe_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
+    k_probe_fp8<<<1, 128, SMEM>>>((const unsigned char*)A, (const unsigned char*)Bimg, tmap, D, (uint4*)tma_out, err);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
+    return 0;
+}

@@ -204,3 +204,50 @@ def test_epilogue_pack_rate(probe, capsys):
         assert probe.tc_pack_rate(mode, 4096, cyc.data_ptr(), sink.data_ptr()) == 0
         with capsys.disabled():
             print(f"\n[pack rate] {name:22s} {cyc.item() / 4096:7.1f} cycles per 8 pairs per warp")
+
+
+def sw64_image_bytes(B):
+    """[rows][128] bytes -> two 64-byte-wide blocks, row-major 64-byte rows, 16-byte unit j
+    of row n at unit j ^ ((n >> 1) & 3)."""
+    rows = B.shape[0]
+    img = np.zeros((2, rows, 4, 16), np.uint8)
+    for blk in range(2):
+        for n in range(rows):
+            for j in range(4):
+                img[blk, n, j ^ ((n >> 1) & 3)] = B[n, 64 * blk + 16 * j:64 * blk + 16 * j + 16]
+    return img
+
+
+def test_mma_fp8_e4m3_layouts(probe):
+    """kind::f8f6f4 with E4M3 A and B in the 64-byte-swizzled K-major layout (64 elements
+    per row of a block, K = 32 per MMA) and a uint8 TMA box: D = A B^T exactly as the FP32
+    sum of the E4M3 products."""
+    f8 = getattr(torch, "float8_e4m3fn", None)
+    if f8 is None:
+        pytest.skip("no float8_e4m3fn in this torch")
+    probe.tc_probe_fp8.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3
+    rng = np.random.default_rng(7)
+    A8 = torch.from_numpy(rng.normal(size=(128, 128)).astype(np.float32)).to(f8)
+    B8 = torch.from_numpy(rng.normal(size=(208, 128)).astype(np.float32)).to(f8)
+    Ab = A8.view(torch.uint8).numpy()
+    Bb = B8.view(torch.uint8).numpy()
+    Bimg = torch.from_numpy(sw64_image_bytes(Bb).reshape(-1).copy()).cuda()
+    T = torch.from_numpy(rng.integers(0, 256, size=(100, 256), dtype=np.uint8)).cuda()
+    D = torch.zeros((128, 208), dtype=torch.float32, device="cuda")
+    tma = torch.zeros(8192, dtype=torch.uint8, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Ad = torch.from_numpy(Ab.copy()).cuda()
+    rc = probe.tc_probe_fp8(Ad.data_ptr(), Bimg.data_ptr(), T.data_ptr(), 100, 256, D.data_ptr(),
+                            tma.data_ptr(), err.data_ptr())
+    assert rc == 0 and err.item() == 0, (rc, err.item())
+    ref = A8.double().numpy() @ B8.double().numpy().T
+    got = D.cpu().double().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    raw = tma.cpu().numpy().reshape(128, 4, 16)
+    box = np.zeros((128, 64), np.uint8)
+    for r in range(128):
+        for j in range(4):
+            box[r, 16 * j:16 * j + 16] = raw[r, j ^ ((r >> 1) & 3)]
+    exp = np.zeros((128, 64), np.uint8)
+    exp[:100] = T.cpu().numpy()[:, 64:128]
+    assert np.array_equal(box, exp)
