@@ -53,13 +53,14 @@ enum {
     RPNN_ERR_TIMEOUT = -9       /* a bounded device-side wait gave up (results invalid) */
 };
 
-enum { RPNN_F32 = 0, RPNN_F16 = 1, RPNN_BF16 = 2 };
+enum { RPNN_F32 = 0, RPNN_F16 = 1, RPNN_BF16 = 2, RPNN_FP8E4M3 = 3 };
 
 enum {
     RPNN_K = 10,            /* stencil levels (Sec. 4.2) */
     RPNN_S = 225,           /* points per level: 5 x 5 x 9 (Sec. 4.2) */
     RPNN_DIN = 226,         /* network input per block: Sigma^k and gamma (Sec. 4.3) */
     RPNN_DESC_STRIDE = 240, /* stored width of one level of a descriptor row */
+    RPNN_DESC_STRIDE_FP8 = 256, /* the same for E4M3 rows (whole 32-byte tensor-core K-steps) */
     RPNN_H = 200,           /* hidden width (Sec. 7: every layer has 200 nodes) */
     RPNN_NPARAMS = 1296601  /* flat parameter count, layout below */
 };
@@ -124,8 +125,10 @@ rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_p
  * directions d (dev_d, q*3 FP32, unit length) and light directions (dev_wl: 3 floats
  * shared by all queries when wl_stride = 0, or q*3 floats when wl_stride = 3; unit
  * length) writes the descriptor rows [q][10][RPNN_DESC_STRIDE] of dtype RPNN_F32 or
- * RPNN_BF16 into dev_desc: per level k the 225 densities rho at the stencil points in
- * (iz*5+iy)*5+ix order, then gamma = acos(omega . light) in radians, then zeros.
+ * RPNN_BF16 (or [q][10][RPNN_DESC_STRIDE_FP8] of RPNN_FP8E4M3: the FP32 value rounded to
+ * E4M3, nearest even, saturating at 448, unscaled) into dev_desc: per level k the 225
+ * densities rho at the stencil points in (iz*5+iy)*5+ix order, then gamma =
+ * acos(omega . light) in radians, then zeros.
  * Frame: z = light, x = normalize(z cross omega), y = z cross x (x = first vector of
  * the Duff et al. 2017 basis of z when omega is parallel to z).  The FP32 arithmetic
  * follows one fixed rounding sequence, bit-identical to the FP32 CPU restatement. */
@@ -134,11 +137,21 @@ rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* de
                                      int64_t q, void* dev_desc, int32_t desc_dtype, void* stream);
 
 /* ---- network forward (Sec. 4.3) -------------------------------------------------------- */
-/* g = RPNN(z) for q descriptor rows (layout of rpnn_extract_descriptors; dtype RPNN_F32
- * or RPNN_BF16).  precision RPNN_F32: FP32 CUDA-core form; RPNN_BF16: tcgen05 tensor
- * cores, BF16 operands, FP32 accumulation (needs desc_dtype RPNN_BF16).  dev_out: q FP32. */
+/* g = RPNN(z) for q descriptor rows (layout of rpnn_extract_descriptors; dtype RPNN_F32,
+ * RPNN_BF16 or RPNN_FP8E4M3).  precision RPNN_F32: FP32 CUDA-core form; RPNN_BF16: tcgen05
+ * tensor cores, BF16 operands, FP32 accumulation (needs desc_dtype RPNN_BF16);
+ * RPNN_FP8E4M3: tcgen05, E4M3 operands with per-tensor scales, FP32 accumulation (needs
+ * desc_dtype RPNN_FP8E4M3 and rpnn_calibrate_fp8 since the last rpnn_set_weights, else
+ * RPNN_ERR_STATE).  dev_out: q FP32. */
 rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
                              int32_t precision, float* dev_out, void* stream);
+/* FP8 calibration (the paper trains and runs in FP32; low precision is this library's):
+ * runs the FP32 network on q FP32 descriptor rows [q][10][RPNN_DESC_STRIDE] (dev_desc,
+ * borrowed for the call), takes each layer's largest activation as its E4M3 range (scale =
+ * max / 448), chooses per-layer weight scales, and builds the E4M3 weight image that
+ * RPNN_FP8E4M3 renders and forwards use until the next rpnn_set_weights.  Synchronises
+ * `stream`.  Errors: RPNN_ERR_STATE (no weights), RPNN_ERR_ARG (q < 1, null), CUDA/OOM. */
+rpnn_status rpnn_calibrate_fp8(rpnn_ctx* ctx, const float* dev_desc, int64_t q, void* stream);
 
 /* ---- FP32 network forward without device allocation ----------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers that must not
@@ -172,7 +185,7 @@ typedef struct {
     uint64_t seed;                /* Philox4x32-10 key */
     float light_dir[3];           /* unit, towards the light */
     float light_E;                /* irradiance of the directional light */
-    int32_t precision;            /* RPNN_F32 or RPNN_BF16 network arithmetic */
+    int32_t precision;            /* RPNN_F32, RPNN_BF16 or RPNN_FP8E4M3 network arithmetic */
     int32_t mode;                 /* RPNN_MODE_* */
 } rpnn_render_desc;
 enum { RPNN_MODE_RPNN = 0, RPNN_MODE_SINGLE = 1, RPNN_MODE_PATH = 2 };

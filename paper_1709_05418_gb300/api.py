@@ -18,7 +18,8 @@ import torch
 from . import build as _build
 
 K, S, DIN, DESC_STRIDE, H, NPARAMS = 10, 225, 226, 240, 200, 1296601
-F32, F16, BF16 = 0, 1, 2
+DESC_STRIDE_FP8 = 256
+F32, F16, BF16, FP8 = 0, 1, 2, 3
 MODE_RPNN, MODE_SINGLE, MODE_PATH = 0, 1, 2
 ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_HANDLE", -3: "ERR_CUDA", -4: "ERR_OOM",
              -5: "ERR_ITER_LIMIT", -6: "ERR_NONFINITE", -7: "ERR_STATE", -8: "ERR_UNSUPPORTED",
@@ -90,6 +91,7 @@ def load():
             "rpnn_render": [_vp, i32, C.POINTER(RenderDesc), _vp, C.POINTER(i64), _vp],
             "rpnn_render_batch": [_vp, C.POINTER(BatchItem), i32, C.POINTER(i64), _vp],
             "rpnn_set_render_chunk": [_vp, i64],
+            "rpnn_calibrate_fp8": [_vp, _vp, i64, _vp],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
                                  _vp, _vp],
@@ -124,6 +126,8 @@ def _stream():
 
 
 def _dtype_code(t):
+    if t.dtype == torch.uint8:
+        return FP8                          # E4M3 bytes
     return {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[t.dtype]
 
 
@@ -201,10 +205,12 @@ class Context:
         self._check(self.L.rpnn_set_weights(self.h, _ptr(params), params.numel(), _stream()))
 
     def extract_descriptors(self, vol, x, d, wl, dtype=torch.float32, out=None):
+        """dtype torch.uint8 selects E4M3 rows [q][10][256] (bytes)."""
         q = x.shape[0]
         stride = 3 if wl.dim() == 2 else 0
         if out is None:
-            out = torch.empty((q, K, DESC_STRIDE), dtype=dtype, device="cuda")
+            width = DESC_STRIDE_FP8 if dtype == torch.uint8 else DESC_STRIDE
+            out = torch.empty((q, K, width), dtype=dtype, device="cuda")
         self._check(self.L.rpnn_extract_descriptors(self.h, vol, _ptr(x), _ptr(d), _ptr(wl),
                                                     stride, q, _ptr(out), _dtype_code(out),
                                                     _stream()))
@@ -217,6 +223,11 @@ class Context:
         self._check(self.L.rpnn_mlp_forward(self.h, _ptr(desc), _dtype_code(desc), q, precision,
                                             _ptr(out), _stream()))
         return out
+
+    def calibrate_fp8(self, desc):
+        """Per-tensor FP8 scales from the FP32 network on these FP32 descriptors."""
+        assert desc.dtype == torch.float32
+        self._check(self.L.rpnn_calibrate_fp8(self.h, _ptr(desc), desc.shape[0], _stream()))
 
     def mlp_backward(self, desc, dout, out=None):
         q = desc.shape[0]

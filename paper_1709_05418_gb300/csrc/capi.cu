@@ -85,7 +85,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
         v->raw.release(); v->packed.release(); v->stats.release();
         delete v;
     }
-    DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->q_x, &c->q_d, &c->q_ps,
+    DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light};
     for (DevBuf* b : bufs) b->release();
@@ -188,6 +188,7 @@ rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_p
     st = mlp_build_bf16_image(*c, s);
     if (st) return st;
     c->weights_set = true;
+    c->fp8_ready = false;
     ++c->epoch;
     return RPNN_OK;
 }
@@ -203,7 +204,10 @@ rpnn_status rpnn_extract_descriptors(rpnn_ctx* ctx, int32_t vol, const float* de
     if (q == 0) return RPNN_OK;
     if (!dev_x || !dev_d || !dev_wl || !dev_desc) { set_error("null pointer"); return RPNN_ERR_ARG; }
     if (wl_stride != 0 && wl_stride != 3) { set_error("wl_stride must be 0 or 3"); return RPNN_ERR_ARG; }
-    if (desc_dtype != RPNN_F32 && desc_dtype != RPNN_BF16) { set_error("desc dtype must be F32 or BF16"); return RPNN_ERR_ARG; }
+    if (desc_dtype != RPNN_F32 && desc_dtype != RPNN_BF16 && desc_dtype != RPNN_FP8E4M3) {
+        set_error("desc dtype must be F32, BF16 or FP8E4M3");
+        return RPNN_ERR_ARG;
+    }
     if ((reinterpret_cast<uintptr_t>(dev_desc) & 15u) != 0) { set_error("dev_desc must be 16-byte aligned"); return RPNN_ERR_ARG; }
     return launch_descriptor(*c, v->view(), dev_x, dev_d, dev_wl, wl_stride, q, nullptr, dev_desc,
                              desc_dtype, (cudaStream_t)stream);
@@ -240,8 +244,23 @@ rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_d
         if (desc_dtype != RPNN_BF16) { set_error("the BF16 network reads BF16 descriptors"); return RPNN_ERR_ARG; }
         return mlp_forward_bf16(*c, dev_desc, q, nullptr, dev_out, s);
     }
-    set_error("precision must be RPNN_F32 or RPNN_BF16");
+    if (precision == RPNN_FP8E4M3) {
+        if (desc_dtype != RPNN_FP8E4M3) { set_error("the FP8 network reads E4M3 descriptors"); return RPNN_ERR_ARG; }
+        return mlp_forward_fp8(*c, dev_desc, q, nullptr, dev_out, s);
+    }
+    set_error("precision must be RPNN_F32, RPNN_BF16 or RPNN_FP8E4M3");
     return RPNN_ERR_ARG;
+}
+
+rpnn_status rpnn_calibrate_fp8(rpnn_ctx* ctx, const float* dev_desc, int64_t q, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    if (!dev_desc || q < 1) { set_error("calibration needs q >= 1 descriptor rows"); return RPNN_ERR_ARG; }
+    if (q > (int64_t)1 << 24) { set_error("q too large"); return RPNN_ERR_ARG; }
+    rpnn_status st = ensure_rows(c, q, true);
+    if (st) return st;
+    return mlp_calibrate_fp8(*c, dev_desc, q, (cudaStream_t)stream);
 }
 
 static rpnn_status check_desc(const rpnn_render_desc* d) {
@@ -252,7 +271,10 @@ static rpnn_status check_desc(const rpnn_render_desc* d) {
         return RPNN_ERR_ARG;
     }
     if (d->mode < RPNN_MODE_RPNN || d->mode > RPNN_MODE_PATH) { set_error("bad mode"); return RPNN_ERR_ARG; }
-    if (d->precision != RPNN_F32 && d->precision != RPNN_BF16) { set_error("bad precision"); return RPNN_ERR_ARG; }
+    if (d->precision != RPNN_F32 && d->precision != RPNN_BF16 && d->precision != RPNN_FP8E4M3) {
+        set_error("bad precision");
+        return RPNN_ERR_ARG;
+    }
     const float l2 = d->light_dir[0] * d->light_dir[0] + d->light_dir[1] * d->light_dir[1] +
                      d->light_dir[2] * d->light_dir[2];
     if (!(fabsf(l2 - 1.0f) < 1e-4f)) { set_error("light_dir must be unit length"); return RPNN_ERR_ARG; }
@@ -283,9 +305,15 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
     if (!dev_image) { set_error("dev_image is null"); return RPNN_ERR_ARG; }
     const bool net = desc->mode == RPNN_MODE_RPNN;
     if (net && !c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
+    if (net && desc->precision == RPNN_FP8E4M3 && !c->fp8_ready) {
+        set_error("FP8 render: rpnn_calibrate_fp8 has not run since the weights were set");
+        return RPNN_ERR_STATE;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t P = (int64_t)desc->width * desc->height * desc->spp;
     const bool f32 = desc->precision == RPNN_F32;
+    const bool fp8 = desc->precision == RPNN_FP8E4M3;
+    const size_t desc_row_bytes = fp8 ? (size_t)RPNN_K * RPNN_DESC_STRIDE_FP8 : (size_t)RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2);
     // the descriptor and network stages run over chunks of at most kChunkRows queries, so
     // the descriptor buffer stays bounded (5 GB BF16) for renders of millions of samples
     const int64_t CH = std::min<int64_t>(P, c->chunk_rows > 0 ? c->chunk_rows : kChunkRows);
@@ -297,7 +325,7 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         if (!st) st = c->q_d.reserve(P * 3 * sizeof(float));
         if (!st) st = c->q_ps.reserve(P * sizeof(uint32_t));
         if (!st) st = c->g_out.reserve(P * sizeof(float));
-        if (!st) st = c->desc.reserve((size_t)CH * RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2));
+        if (!st) st = c->desc.reserve((size_t)CH * desc_row_bytes);
         if (!st) st = ensure_rows(c, CH, f32);
     }
     if (st) return st;
@@ -341,11 +369,13 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
             const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
             const int64_t first = (int64_t)i * CH;
             st = launch_descriptor(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
-                                   c->light.as<float>(), 0, CH, cnt, c->desc.p, f32 ? RPNN_F32 : RPNN_BF16, s);
+                                   c->light.as<float>(), 0, CH, cnt, c->desc.p,
+                                   f32 ? RPNN_F32 : (fp8 ? RPNN_FP8E4M3 : RPNN_BF16), s);
             if (st) return st;
             // (a chunked render attributes its network time to the descriptor stage)
             if (ev && i == nchunks - 1) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
             if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), CH, cnt, c->g_out.as<float>() + first, nullptr, s);
+            else if (fp8) st = mlp_forward_fp8(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
             else st = mlp_forward_bf16(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
             if (st) return st;
         }

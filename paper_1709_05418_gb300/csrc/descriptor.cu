@@ -12,6 +12,7 @@
 // Layout: one warp per shading point; each lookup reads one 32-byte corner record with a
 // single 256-bit load.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -21,6 +22,8 @@ namespace {
 
 template <class T> __device__ __forceinline__ T cvt_out(float v);
 template <> __device__ __forceinline__ float cvt_out<float>(float v) { return v; }
+// E4M3: round to nearest even, saturating at +-448 (the descriptor is stored unscaled)
+template <> __device__ __forceinline__ __nv_fp8_e4m3 cvt_out<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
@@ -133,8 +136,10 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
              const float* __restrict__ wls, int wl_stride, int64_t q_host,
              const int* __restrict__ q_dev, OutT* __restrict__ out, const BatchItemDev* __restrict__ items,
              int n_items, const int* __restrict__ off) {
-    constexpr int ROW = RPNN_K * RPNN_DESC_STRIDE;
-    constexpr bool STAGE = sizeof(OutT) == 2;
+    // row stride per level: 240 values (FP32, BF16) or 256 (E4M3: whole 32-byte K-steps)
+    constexpr int DS = sizeof(OutT) == 1 ? 256 : RPNN_DESC_STRIDE;
+    constexpr int ROW = RPNN_K * DS;
+    constexpr bool STAGE = sizeof(OutT) <= 2;
     constexpr int NI = BATCH ? RPNN_MAX_BATCH : 1;
     __shared__ __align__(16) OutT rowbuf[STAGE ? 8 : 1][STAGE ? ROW : 8];
     __shared__ LevelK lk[NI][RPNN_K];
@@ -191,7 +196,7 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
                 const float U0 = __fsub_rn(__fmul_rn(x[a], g.s), 0.5f);
                 P[a] = __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0));
             }
-            OutT* dst = row + k * RPNN_DESC_STRIDE + col;
+            OutT* dst = row + k * DS + col;
 #pragma unroll
             for (int iz = 0; iz < 9; ++iz) {
                 const float oz = -1.0f + 0.5f * (float)iz;      // exact: -1, -0.5, ..., 3
@@ -199,9 +204,9 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
                                                     __fmaf_rn(oz, C[2], P[2])));
             }
         }
-        for (int e = lane; e < RPNN_K * (RPNN_DESC_STRIDE - RPNN_S); e += 32) {
-            const int kk = e / (RPNN_DESC_STRIDE - RPNN_S), j = e % (RPNN_DESC_STRIDE - RPNN_S);
-            row[kk * RPNN_DESC_STRIDE + RPNN_S + j] = cvt_out<OutT>(j == 0 ? F.gamma : 0.0f);
+        for (int e = lane; e < RPNN_K * (DS - RPNN_S); e += 32) {
+            const int kk = e / (DS - RPNN_S), j = e % (DS - RPNN_S);
+            row[kk * DS + RPNN_S + j] = cvt_out<OutT>(j == 0 ? F.gamma : 0.0f);
         }
         if (STAGE) {
             __syncwarp();
@@ -231,13 +236,18 @@ rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, cons
                               void* out, int dtype, cudaStream_t s) {
     if (q <= 0 && !q_dev) return RPNN_OK;
     // one resident wave of blocks (8 shading points each), grid-stride beyond that
-    const int per_sm = dtype == RPNN_F32 ? blocks_per_sm<float, false>() : blocks_per_sm<__nv_bfloat16, false>();
+    const int per_sm = dtype == RPNN_F32       ? blocks_per_sm<float, false>()
+                       : dtype == RPNN_FP8E4M3 ? blocks_per_sm<__nv_fp8_e4m3, false>()
+                                               : blocks_per_sm<__nv_bfloat16, false>();
     const int64_t wave = (int64_t)c.num_sms * per_sm;
     int64_t g = q_dev ? wave : (q + 7) / 8;
     if (g > wave) g = wave;
     if (dtype == RPNN_F32)
         k_descriptor<float, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (float*)out, nullptr, 0,
                                                           nullptr);
+    else if (dtype == RPNN_FP8E4M3)
+        k_descriptor<__nv_fp8_e4m3, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
+                                                                  (__nv_fp8_e4m3*)out, nullptr, 0, nullptr);
     else
         k_descriptor<__nv_bfloat16, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
                                                                   (__nv_bfloat16*)out, nullptr, 0, nullptr);

@@ -101,7 +101,9 @@ struct Ctx {
     DevBuf status;           // uint32 status bits
     DevBuf params32;         // FP32 parameters (flat, the documented layout)
     DevBuf wimg_bf16;        // tensor-core weight image
+    DevBuf wimg_fp8;         // E4M3 weight image with its scales (after rpnn_calibrate_fp8)
     bool weights_set = false;
+    bool fp8_ready = false;  // FP8 image built for the current weights
     // render scratch
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
@@ -174,6 +176,12 @@ rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);
 rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev,
                              float* out, cudaStream_t s);
+// FP8 (E4M3) tensor-core network on [q][10][256] E4M3 descriptors; needs mlp_calibrate_fp8
+rpnn_status mlp_forward_fp8(Ctx& c, const void* desc_fp8, int64_t q, const int* q_dev, float* out,
+                            cudaStream_t s);
+// Per-tensor scales from the FP32 network on q FP32 descriptors [q][10][240]; builds the
+// E4M3 weight image (synchronises s)
+rpnn_status mlp_calibrate_fp8(Ctx& c, const float* desc, int64_t q, cudaStream_t s);
 
 // parameter layout offsets (floats) of the flat vector
 struct ParamLayout {

@@ -265,6 +265,15 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
+// Instruction descriptor of kind::f8f6f4: E4M3 A and B (K-major), FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4)                       // D format: F32
+         | (0u << 7)                       // A format: E4M3
+         | (0u << 10)                      // B format: E4M3
+         | ((uint32_t)(N >> 3) << 17)      // N / 8
+         | ((uint32_t)(M >> 4) << 24);     // M / 16
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 accumulator.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4)                       // D format: F32
