@@ -155,6 +155,14 @@ def barrier(ws):
         dist.barrier()
 
 
+def calibration_sample(hit, n):
+    """Indices of at most n shading points spread evenly over the image (every k-th hit in
+    pixel order), so the FP8 scales see the whole range of the render's activations."""
+    import torch
+    idx = torch.nonzero(hit).squeeze(1)
+    return idx[::max(1, idx.numel() // n)][:n]
+
+
 def make_workload(rank, device=None):
     from paper_1709_05418_gb300 import workloads as W
     dens = W.fbm_cloud(256, seed=7, device=device)
@@ -266,10 +274,13 @@ def run_batch(args, ws, rank, local):
 
 LARGE_WORKLOAD = ("large render: 1024^3 FP16 fBm density (seed 300, 6 octaves, 30% non-zero, peak sigma_t "
                   "50/unit), 1920x1080 at 4 spp, random light dir, descriptor/network stages in chunks of "
-                  "1,048,576 queries, BF16 RPNN, He-init weights")
+                  "1,048,576 queries, FP8 (E4M3, per-tensor scales) RPNN, He-init weights")
 
 
 def run_large(args, ws, rank, local):
+    """The large configuration: BF16 and FP8 renders of a 1024^3 FP16 cloud at 1920x1080x4,
+    the FP8 one (the configuration's precision) as the line's value; error of both against
+    the FP64 oracle on a seeded sample of pixels."""
     import torch
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -277,46 +288,79 @@ def run_large(args, ws, rank, local):
     from paper_1709_05418_gb300 import workloads as W
     dens = torch.from_numpy(W.fbm_cloud(1024, seed=300, device=dev)).to(device=dev, dtype=torch.float16)
     cam = W.camera(tuple(dens.shape), 1920, 1080, spp=4, seed=301 + rank, light_seed=302 + rank)
+    params = W.he_init(seed=2)
     ctx = api.Context()
     vol = ctx.load_volume(dens)
+    dens_host = dens.float().cpu().numpy() if (rank == 0 and not args.no_cpu) else None
     del dens
     ctx.build_mips(vol)
-    ctx.set_weights(torch.from_numpy(W.he_init(seed=2)).to(dev))
-    rd = ctx.render_desc(cam, api.BF16, api.MODE_RPNN)
-    img = torch.empty((1080, 1920), dtype=torch.float32, device=dev)
-    _, nq = ctx.render(vol, cam, desc=rd, image=img, want_count=True)
-    for _ in range(args.warmup):
-        ctx.render(vol, cam, desc=rd, image=img)
-    ctx.sync_status()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.set_weights(torch.from_numpy(params).to(dev))
+    # FP8 scales from the FP32 network on 65,536 of this render's shading points
+    hit, qx, qd, _ = ctx.trace_primary(vol, cam)
+    sel = calibration_sample(hit, 65536)
+    wl = torch.as_tensor(np.asarray(cam["light_dir"], np.float32), device=dev)
+    ctx.calibrate_fp8(ctx.extract_descriptors(vol, qx[sel].contiguous(), qd[sel].contiguous(), wl))
+    del hit, qx, qd, sel
+
+    def timed(prec):
+        rd = ctx.render_desc(cam, prec, api.MODE_RPNN)
+        img = torch.empty((1080, 1920), dtype=torch.float32, device=dev)
+        _, nq = ctx.render(vol, cam, desc=rd, image=img, want_count=True)
+        for _ in range(args.warmup):
+            ctx.render(vol, cam, desc=rd, image=img)
+        ctx.sync_status()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        barrier(ws)
+        ctx.set_profiling(True)
+        for e0, e1 in evs:
+            e0.record()
+            ctx.render(vol, cam, desc=rd, image=img)
+            e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ctx.set_profiling(False)
+        prof = ctx.read_profile()
+        ctx.sync_status()
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
+        n = max(1, prof["renders"])
+        return nq, ms, {k: prof[k] / n for k in ("primary", "descriptor", "network", "composite")}, img
+
     clocks = Clocks(local)
     clocks.start()
-    torch.cuda.synchronize()
-    barrier(ws)
-    ctx.set_profiling(True)
-    for e0, e1 in evs:
-        e0.record()
-        ctx.render(vol, cam, desc=rd, image=img)
-        e1.record()
-    torch.cuda.synchronize()
-    barrier(ws)
-    ctx.set_profiling(False)
-    prof = ctx.read_profile()
+    nq, ms8, st8, img8 = timed(api.FP8)
+    _, ms16, st16, img16 = timed(api.BF16)
     clk = clocks.stop()
-    ctx.sync_status()
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
     q_total = sum_over_ranks(float(nq) * args.steps, ws, dev)
-    n = max(1, prof["renders"])
     line = {
-        "metric": METRIC, "value": q_total / (ms / 1e3), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "metric": METRIC, "value": q_total / (ms8 / 1e3), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms8 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp8e4m3", "data": "synthetic",
         "config": {"workload": LARGE_WORKLOAD, "queries_per_step": int(nq), "pixel_samples": 1920 * 1080 * 4,
-                   "l2": "inputs larger than L2 (4.3 GB grid, 5 GB descriptor chunk)"},
-        "stages_ms_per_step": {k: prof[k] / n for k in ("primary", "descriptor", "network", "composite")},
+                   "l2": "inputs larger than L2 (4.3 GB grid, descriptor chunks of 1,048,576 rows)",
+                   "fp8_calibration": "per-tensor E4M3 scales from the FP32 network on 65,536 of the render's "
+                                      "shading points, spread evenly over the image"},
+        "stages_ms_per_step": st8,
         "stage_note": "chunked render: the descriptor stage includes the network chunks",
+        "bf16_form": {"value": q_total / (ms16 / 1e3), "unit": "queries/s", "ms_per_step": ms16 / args.steps,
+                      "stages_ms_per_step": st16},
         "clocks": clk,
     }
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        v = oracle.Volume(dens_host)
+        npix = args.large_oracle_pixels
+        pix = np.sort(np.random.default_rng(7).choice(1920 * 1080, npix, replace=False))
+        t0 = time.perf_counter()
+        vals = v.render_pixels(cam, pix, params=params.astype(np.float64), nthreads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+
+        def rel(img):
+            g = img.double().cpu().numpy().ravel()[pix]
+            return float(np.sqrt(np.mean((g - vals) ** 2)) / max(np.sqrt(np.mean(vals ** 2)), 1e-30))
+
+        line["error_vs_fp64_oracle"] = {"pixels": int(npix), "fp8_rel_rmse": rel(img8), "bf16_rel_rmse": rel(img16),
+                                        "oracle_seconds": dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -367,6 +411,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--cpu-pixels", type=int, default=2048)
     ap.add_argument("--ref-pixels", type=int, default=512)
+    ap.add_argument("--large-oracle-pixels", type=int, default=10000,
+                    help="pixels the FP64 oracle renders for the large workload's error")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "large"],
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
@@ -456,6 +502,23 @@ def main():
                     "network_ms_per_step": prof32["network"] / max(1, prof32["renders"])}
         f32_form["ratio"] = value / ws / f32_form["value"]
 
+    # FP8 (E4M3) form of the same render: per-tensor scales calibrated on this render's own
+    # shading points (FP32 descriptors of up to 65,536 of them), outside the timed region
+    fp8_form, img8 = None, None
+    if prec == api.BF16:
+        hit, qx, qd, _ = ctx.trace_primary(vol, cam)
+        sel = calibration_sample(hit, 65536)
+        wl = torch.as_tensor(np.asarray(cam["light_dir"], np.float32), device=dev)
+        ctx.calibrate_fp8(ctx.extract_descriptors(vol, qx[sel].contiguous(), qd[sel].contiguous(), wl))
+        nq8, ms8, prof8, img8 = timed(api.FP8, args.steps, 3)
+        fp8_form = {"value": nq8 * args.steps / (ms8 / 1e3),
+                    "unit": "queries/s", "ms_per_step": ms8 / args.steps,
+                    "network_ms_per_step": prof8["network"] / max(1, prof8["renders"]),
+                    "descriptor_ms_per_step": prof8["descriptor"] / max(1, prof8["renders"]),
+                    "calibration": "per-tensor E4M3 scales from the FP32 network on <= 65,536 of the render's "
+                                   "own shading points, spread evenly over the image"}
+        img8 = img8.clone()
+
     # end to end through the public API: host-visible result every step
     host_img = torch.empty((512, 512), dtype=torch.float32, pin_memory=True)
     rd = ctx.render_desc(cam, prec, api.MODE_RPNN)
@@ -511,6 +574,8 @@ def main():
     }
     if f32_form:
         line["fp32_form"] = f32_form
+    if fp8_form:
+        line["fp8_form"] = fp8_form
     if rank == 0 and not args.no_cpu:
         pix, vals, hits, dt, nth = cpu_sample(dens, cam, params, args.cpu_pixels)
         line["cpu_baseline"] = {"value": hits / dt, "unit": "queries/s", "cores": nth, "kind": "oracle",
@@ -519,6 +584,11 @@ def main():
         got = img.double().cpu().numpy().ravel()[pix]
         err = float(np.sqrt(np.mean((got - vals) ** 2)) / max(np.sqrt(np.mean(vals ** 2)), 1e-30))
         line["error_vs_fp64_oracle"] = {"pixels": int(pix.size), "rel_rmse": err}
+        if fp8_form:
+            g8 = img8.double().cpu().numpy().ravel()[pix]
+            fp8_form["error_vs_fp64_oracle"] = {
+                "pixels": int(pix.size),
+                "rel_rmse": float(np.sqrt(np.mean((g8 - vals) ** 2)) / max(np.sqrt(np.mean(vals ** 2)), 1e-30))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
