@@ -718,60 +718,6 @@ extern "C" int tc_mma_ring(int ch, int wf, int nmma, int copy, int grid, const v
     }
 }
 
-namespace {
-
-// ---- epilogue arithmetic throughput --------------------------------------------------
-// 8 warps (2 per scheduler, as the network kernel's epilogue) repeat a block of
-// independent work on 16 values per thread: mode 0 cvt.rn.relu.bf16x2.f32 (8 per block),
-// mode 1 the same rounding by integer arithmetic (ReLU by fmaxf, round-to-nearest-even by
-// adding 0x7FFF plus the kept LSB, PRMT to pack), mode 2 cvt.rn.satfinite.relu.e4m3x2.f32,
-// mode 3 cvt.rn.f16x2.f32, mode 4 two fmaxf only (the loop's own cost).  Eight independent
-// accumulators keep the conversions independent of each other.
-// cycles[0] = clock cycles of warp 0 for `iters` blocks; the checksum keeps the work alive.
-__global__ void __launch_bounds__(256) k_pack_rate(int mode, int iters, long long* cycles, unsigned* sink) {
-    float v[16];
-    for (int i = 0; i < 16; ++i) v[i] = (float)(threadIdx.x * 16 + i) * 0.37f - 20.0f;
-    unsigned acc8[8] = {};
-    __syncthreads();
-    const long long t0 = clock64();
-    for (int it = 0; it < iters; ++it) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float lo = v[2 * q] + (float)it, hi = v[2 * q + 1] - (float)it;
-            uint32_t d;
-            if (mode == 3) {
-                asm volatile("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-            } else if (mode == 4) {
-                d = __float_as_uint(fmaxf(lo, 0.0f)) ^ __float_as_uint(fmaxf(hi, 0.0f));
-            } else if (mode == 0) {
-                asm volatile("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-            } else if (mode == 1) {
-                const uint32_t a = __float_as_uint(fmaxf(lo, 0.0f)), b = __float_as_uint(fmaxf(hi, 0.0f));
-                const uint32_t ra = a + 0x7FFFu + ((a >> 16) & 1u), rb = b + 0x7FFFu + ((b >> 16) & 1u);
-                d = __byte_perm(ra, rb, 0x7632);
-            } else {
-                uint16_t h;
-                asm volatile("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(h) : "f"(hi), "f"(lo));
-                d = h;
-            }
-            acc8[q] ^= d;
-        }
-    }
-    const long long t1 = clock64();
-    unsigned acc = 0;
-    for (int q = 0; q < 8; ++q) acc += acc8[q];
-    if (threadIdx.x == 0) cycles[0] = t1 - t0;
-    if (acc == 0x12345678u) atomicAdd(sink, 1u);
-}
-
-}  // namespace
-
-extern "C" int tc_pack_rate(int mode, int iters, long long* cycles, unsigned* sink) {
-    k_pack_rate<<<1, 256>>>(mode, iters, cycles, sink);
-    if (cudaGetLastError() != cudaSuccess) return -13;
-    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
-    return 0;
-}
 
 namespace {
 

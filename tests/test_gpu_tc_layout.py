@@ -194,17 +194,6 @@ def test_mma_rate_through_ring(probe, capsys):
     assert all(o[-1] == 0 for o in out)
 
 
-def test_epilogue_pack_rate(probe, capsys):
-    """Cycles per warp for 8 packed conversions of 16 values (2 warps per scheduler)."""
-    probe.tc_pack_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
-    cyc = torch.zeros(1, dtype=torch.int64, device="cuda")
-    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for mode, name in [(0, "cvt.rn.relu.bf16x2"), (1, "integer RNE + fmaxf"), (2, "cvt e4m3x2 relu"),
-                       (3, "cvt.rn.f16x2"), (4, "fmaxf only")]:
-        assert probe.tc_pack_rate(mode, 4096, cyc.data_ptr(), sink.data_ptr()) == 0
-        with capsys.disabled():
-            print(f"\n[pack rate] {name:22s} {cyc.item() / 4096:7.1f} cycles per 8 pairs per warp")
-
 
 def sw64_image_bytes(B):
     """[rows][128] bytes -> two 64-byte-wide blocks, row-major 64-byte rows, 16-byte unit j
