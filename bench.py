@@ -39,10 +39,12 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (797.670912e6 + 5.609472e6) / 178847,
-                   "sources": {"descriptor.cu": "82d6dfbb246bc4c6", "volume.cu": "019a6dcf787202e9"}},
-    "network": {"bytes_per_query": (889.980160e6 + 3.837440e6) / 178847,
-                "sources": {"mlp_tc.cu": "057df54b897d9822", "tc_ptx.cuh": "421861e4e92c024f"}},
+    "descriptor": {"bytes_per_query": (797.830400e6 + 5.624320e6) / 178847,
+                   "sources": {"descriptor.cu": "b520e610f8058d2b", "volume.cu": "019a6dcf787202e9"}},
+    "network": {"bytes_per_query": (886.093568e6 + 3.916800e6) / 178847,
+                "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
+    "network_fp8": {"bytes_per_query": (459.987200e6 + 5.108224e6) / 178847,
+                    "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
 }
 
 
@@ -418,7 +420,7 @@ def main():
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
                          "call; large: 1024^3 FP16 cloud at 1920x1080x4")
     ap.add_argument("--profile-only", action="store_true",
-                    help="one BF16 and one FP32 render of the workload, no timing (for ncu captures)")
+                    help="one BF16, one FP32 and one FP8 render of the workload, no timing (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -446,6 +448,11 @@ def main():
     if args.profile_only:
         for p in (api.BF16, api.F32):
             ctx.render(vol, cam, precision=p)
+        hit, qx, qd, _ = ctx.trace_primary(vol, cam)
+        sel = calibration_sample(hit, 65536)
+        wl = torch.as_tensor(np.asarray(cam["light_dir"], np.float32), device=dev)
+        ctx.calibrate_fp8(ctx.extract_descriptors(vol, qx[sel].contiguous(), qd[sel].contiguous(), wl))
+        ctx.render(vol, cam, precision=api.FP8)
         ctx.sync_status()
         torch.cuda.synchronize()
         ctx.close()
@@ -559,6 +566,22 @@ def main():
     roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["kernel"] = dom
     roof["peak_src"] = pk["src"]
+    # the tensor-core network beside it (BF16 here, E4M3 in fp8_form): dense FLOPs per launch over
+    # the CUDA-event time of the launch, against the measured BF16 burst peak (x2 for E4M3, the
+    # nominal FP8:BF16 tensor ratio)
+    if prec == api.BF16:
+        ach = nq * FLOP_PER_QUERY / (stage_ms["network"] / 1e3) / 1e12
+        line_net = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops"], "traffic": traffic_per_launch("network", nq),
+                    "algorithmic_bytes": nq * (10 * 240 * 2), "kernel": "network", "peak_src": pk["src"]}
+        if fp8_form:
+            ms_net8 = fp8_form["network_ms_per_step"]
+            ach8 = nq8 * FLOP_PER_QUERY / (ms_net8 / 1e3) / 1e12
+            fp8_form["network_roofline"] = {
+                "bound": "tensor", "achieved": ach8, "peak": 2 * pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach8 / (2 * pk["bf16_tflops"]), "traffic": traffic_per_launch("network_fp8", nq8),
+                "algorithmic_bytes": nq8 * (10 * 256), "kernel": "network",
+                "peak_src": pk["src"] + " bf16 x 2 (nominal E4M3:BF16 ratio)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -572,6 +595,8 @@ def main():
         "gpu_launches": (5 if prec == api.BF16 else 27) * args.steps,
         "e2e": e2e, "roofline": roof, "clocks": clk,
     }
+    if prec == api.BF16:
+        line["network_roofline"] = line_net
     if f32_form:
         line["fp32_form"] = f32_form
     if fp8_form:
