@@ -274,6 +274,147 @@ def run_batch(args, ws, rank, local):
     ctx.close()
 
 
+# kernels of one FP32 training step: 23 forward GEMMs, the loss, 78 backward launches (GEMMs,
+# bias-gradient sums, one mask), Adam, and the BF16 weight image for rendering
+TRAIN_LAUNCHES = 23 + 1 + 78 + 1 + 1
+TRAIN_WORKLOAD = ("training: fBm clouds (seeds 100-103, edges drawn from {128, 160, 192, 224, 256}, FP32 "
+                  "density), labelled records (uniform direction, origin on the bounding-sphere disk, "
+                  "uniform light; path-traced L_i until +-2% at 95% confidence, 64 paths at least, capped "
+                  "as `records.rule` states), FP32 "
+                  "descriptors; one step = forward with saved activations, log-MSE loss, backward, Adam "
+                  "(lr 1e-3) on a minibatch of 4,096 records")
+
+
+def run_train(args, ws, rank, local):
+    """Label generation (records/s) and the training step (samples/s) of the network."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_05418_gb300 import api
+    from paper_1709_05418_gb300 import workloads as W
+    rng = np.random.default_rng(100 + rank)
+    ctx = api.Context()
+    per_cloud = max(1, args.train_records // 4)
+    gen_ms, pool_z, pool_t, npaths = 0.0, [], [], []
+    for i in range(4):
+        edge = int(rng.choice([128, 160, 192, 224, 256]))
+        vol = ctx.load_volume(torch.from_numpy(W.fbm_cloud(edge, seed=100 + 4 * rank + i)).to(dev))
+        ctx.build_mips(vol)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        x, d, wl, lab, npa = ctx.gen_records(vol, 0, per_cloud, 1000 + i, rel_ci=0.02, n_min=64,
+                                             n_max=args.train_max_paths)
+        e1.record()
+        torch.cuda.synchronize()
+        gen_ms += e0.elapsed_time(e1)
+        print(f"cloud {i}: edge {edge}, {per_cloud} records in {e0.elapsed_time(e1):.0f} ms", file=sys.stderr, flush=True)
+        pool_z.append(ctx.extract_descriptors(vol, x, d, wl))
+        pool_t.append(lab)
+        npaths.append(npa)
+    ctx.sync_status()
+    z = torch.cat(pool_z)
+    t = torch.cat(pool_t)
+    npa = torch.cat(npaths)
+    nrec = z.shape[0]
+    B = 4096
+    nb = max(1, nrec // B)
+    params = torch.from_numpy(W.he_init(seed=2)).to(dev)
+    ctx.set_weights(params)
+    ctx.set_autotune(not args.no_autotune)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    batches = [(z[i * B:(i + 1) * B].contiguous(), t[i * B:(i + 1) * B].contiguous()) for i in range(nb)]
+    step = 0
+    for i in range(args.warmup):
+        step += 1
+        ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
+    ctx.sync_status()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier(ws)
+    for i, (e0, e1) in enumerate(evs):
+        flush.zero_()
+        step += 1
+        e0.record()
+        ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
+        e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ctx.sync_status()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
+    total = sum_over_ranks(float(B) * args.steps, ws, dev)
+    # end to end: each step's minibatch copied from pinned host memory, the loss read back
+    hz = [bz.cpu().pin_memory() for bz, _ in batches]
+    ht = [bt.cpu().pin_memory() for _, bt in batches]
+    dz = torch.empty_like(batches[0][0])
+    dt_ = torch.empty_like(batches[0][1])
+    hl = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step += 1
+        dz.copy_(hz[i % nb], non_blocking=True)
+        dt_.copy_(ht[i % nb], non_blocking=True)
+        ctx.train_step(dz, dt_, params, m, v, step, loss=loss)
+        hl.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    pk = peaks()
+    flop = 3 * FLOP_PER_QUERY * B
+    ach = flop / (ms / args.steps / 1e3) / 1e12
+    alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    line = {
+        "metric": "RPNN training samples/s on 1 GB300 (log-MSE + Adam, minibatch 4096)",
+        "value": total / (ms / 1e3), "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": TRAIN_WORKLOAD, "batch": B, "records": int(nrec),
+                   "minibatches": f"{nb} distinct minibatches of the record pool, in turn",
+                   "l2": "flushed: 256 MB write between timed steps"},
+        "records": {"value": nrec / (gen_ms / 1e3), "unit": "records/s", "records": int(nrec),
+                    "rule": f"+-2% at 95% confidence, 64..{args.train_max_paths} paths",
+                    "mean_paths_per_record": float(npa.double().mean()),
+                    "capped_at_max_paths": int((npa >= args.train_max_paths).sum())},
+        "gpu_launches": None,
+        "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(dz.numel() * 4 + dt_.numel() * 4),
+                "d2h_bytes_per_step": 8},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                     "traffic": None, "kernel": "whole training step (FP32 CUDA-core GEMMs, 3 x 2.5844 MFLOP per sample)",
+                     "peak_src": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"},
+        "clocks": clk,
+    }
+    tab = ctx.autotune_table()
+    line["gpu_launches"] = (TRAIN_LAUNCHES + sum(1 for e in tab if e["splits"] > 1)) * args.steps
+    line["autotune"] = {"on": not args.no_autotune, "shapes": len(tab),
+                        "tuned_us_sum": sum(e["us"] for e in tab),
+                        "default_tile_us_sum": sum(e["default_us"] for e in tab),
+                        "choices": [f'{e["M"]}x{e["N"]}x{e["K0"]}+{e["K1"]}: {e["tile_m"]}x{e["tile_n"]}x{e["tile_k"]}'
+                                    f' split {e["splits"]} ({e["us"]:.1f} vs {e["default_us"]:.1f} us)' for e in tab]}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        zn = z[:args.cpu_rows].reshape(-1, 10, api.DESC_STRIDE)[:, :, :226].double().cpu().numpy()
+        tn = t[:args.cpu_rows].double().cpu().numpy()
+        pc = params.double().cpu().numpy().copy()
+        mc = np.zeros_like(pc); vc = np.zeros_like(pc)
+        t0 = time.perf_counter()
+        g = oracle.mlp_forward(pc, zn)
+        _, dg = oracle.logmse_loss(g, tn)
+        grad = oracle.mlp_backward(pc, zn, dg)
+        oracle.adam(pc, mc, vc, grad, 1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": zn.shape[0] / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 training step on {zn.shape[0]} records of the pool"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 LARGE_WORKLOAD = ("large render: 1024^3 FP16 fBm density (seed 300, 6 octaves, 30% non-zero, peak sigma_t "
                   "50/unit), 1920x1080 at 4 spp, random light dir, descriptor/network stages in chunks of "
                   "1,048,576 queries, FP8 (E4M3, per-tensor scales) RPNN, He-init weights")
@@ -416,7 +557,15 @@ def main():
     ap.add_argument("--large-oracle-pixels", type=int, default=10000,
                     help="pixels the FP64 oracle renders for the large workload's error")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "large"],
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default 64x64 tile for every FP32 CUDA-core GEMM (no tuning)")
+    ap.add_argument("--train-records", type=int, default=8192,
+                    help="labelled records generated (and timed) for the training workload")
+    ap.add_argument("--train-max-paths", type=int, default=4096,
+                    help="path cap of the records' stopping rule in the training workload")
+    ap.add_argument("--cpu-rows", type=int, default=256,
+                    help="records in the FP64 oracle's training step (training workload)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train"],
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
                          "call; large: 1024^3 FP16 cloud at 1920x1080x4")
     ap.add_argument("--profile-only", action="store_true",
@@ -434,6 +583,9 @@ def main():
     if args.workload == "large":
         run_large(args, ws, rank, local)
         return
+    if args.workload == "train":
+        run_train(args, ws, rank, local)
+        return
 
     import torch
     torch.cuda.set_device(local)
@@ -444,6 +596,7 @@ def main():
     vol = ctx.load_volume(torch.from_numpy(dens).to(dev))
     ctx.build_mips(vol)
     ctx.set_weights(torch.from_numpy(params).to(dev))
+    ctx.set_autotune(not args.no_autotune)
     info = ctx.get_volume_info(vol)
     if args.profile_only:
         for p in (api.BF16, api.F32):

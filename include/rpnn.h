@@ -265,6 +265,29 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
                             int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
                             float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
                             void* stream);
+/* GEMM-tile autotuner of the FP32 CUDA-core network (forward, backward, the FP32 render
+ * form; no counterpart in the paper).  With `on` != 0 (the default), the first call of
+ * each GEMM shape (rows, columns, inner sizes, operand layouts, epilogue kind) times every
+ * admissible tile shape and split-K factor on the call's own operands (writing into
+ * library scratch, so the call's output is unaffected), synchronising the stream once, and
+ * later calls of that shape use the fastest.  Calls made during CUDA-graph capture use a
+ * choice already made, else the default tile.  Tile shapes change no result bit (every
+ * output sums its products in increasing k); K is split only for inner sizes of at least
+ * 1,024 (the weight gradients, which sum over the batch), whose runs' partial sums are
+ * added in run order, so those results differ from the default tile by rounding only and
+ * are the same from run to run once the choice is made.  Forward results (rpnn_mlp_forward,
+ * the FP32 render form) are therefore bit for bit those of the default tile.  With on == 0 every GEMM uses the default
+ * 64 x 64 tile without a split and the table is kept. */
+rpnn_status rpnn_set_autotune(rpnn_ctx* ctx, int32_t on);
+typedef struct {
+    int32_t M, N, K0, K1;          /* rows, columns, inner sizes of the two operand segments */
+    int32_t flags;                 /* operand layouts and epilogue kind (library-defined bits) */
+    int32_t tile_m, tile_n, tile_k, splits;   /* the choice */
+    float us, default_us;          /* its measured time and that of the default tile (us) */
+} rpnn_tune_entry;
+/* Copies up to `cap` entries of the tuning table into out (host) and the table's size to
+ * *n (host).  Errors: RPNN_ERR_ARG for cap < 0, n NULL, or out NULL with cap > 0. */
+rpnn_status rpnn_get_autotune(rpnn_ctx* ctx, rpnn_tune_entry* out, int32_t cap, int32_t* n);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,13 @@ class VolumeInfo(C.Structure):
                 ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("K0", C.c_int32), ("K1", C.c_int32),
+                ("flags", C.c_int32), ("tile_m", C.c_int32), ("tile_n", C.c_int32),
+                ("tile_k", C.c_int32), ("splits", C.c_int32), ("us", C.c_float),
+                ("default_us", C.c_float)]
+
+
 class AdamCfg(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
@@ -99,6 +106,8 @@ def load():
             "rpnn_train_step": [_vp, _vp, _vp, i32, C.POINTER(AdamCfg), i64, _vp, _vp, _vp,
                                 _vp, _vp],
             "rpnn_set_profiling": [_vp, i32],
+            "rpnn_set_autotune": [_vp, i32],
+            "rpnn_get_autotune": [_vp, C.POINTER(TuneEntry), i32, C.POINTER(i32)],
             "rpnn_read_profile": [_vp, C.POINTER(C.c_double), C.POINTER(i64)],
         }
         for name, args in sig.items():
@@ -190,6 +199,17 @@ class Context:
 
     def set_profiling(self, on: bool):
         self._check(self.L.rpnn_set_profiling(self.h, 1 if on else 0))
+
+    def set_autotune(self, on: bool):
+        self._check(self.L.rpnn_set_autotune(self.h, 1 if on else 0))
+
+    def autotune_table(self) -> list:
+        """The GEMM-tile choices made so far, one dict per shape."""
+        n = C.c_int32()
+        self._check(self.L.rpnn_get_autotune(self.h, None, 0, C.byref(n)))
+        buf = (TuneEntry * max(1, n.value))()
+        self._check(self.L.rpnn_get_autotune(self.h, buf, n.value, C.byref(n)))
+        return [{f: getattr(buf[i], f) for f, _ in TuneEntry._fields_} for i in range(n.value)]
 
     def read_profile(self) -> dict:
         ms = (C.c_double * 4)()

@@ -87,8 +87,11 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     }
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
-                      &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light};
+                      &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
+                      &c->tuner.scratch, &c->tuner.ws};
     for (DevBuf* b : bufs) b->release();
+    if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
+    if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
     batch_release(*c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -400,6 +403,28 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (rows < 0 || (rows > 0 && rows < 128)) { set_error("chunk rows must be 0 or at least 128"); return RPNN_ERR_ARG; }
     c->chunk_rows = rows;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_set_autotune(rpnn_ctx* ctx, int32_t on) {
+    CHECK_CTX(ctx);
+    reinterpret_cast<Ctx*>(ctx)->tuner.enabled = on != 0;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_get_autotune(rpnn_ctx* ctx, rpnn_tune_entry* out, int32_t cap, int32_t* n) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (cap < 0 || !n || (!out && cap > 0)) { set_error("bad output buffer"); return RPNN_ERR_ARG; }
+    const auto& t = c->tuner.table;
+    *n = (int32_t)t.size();
+    for (int32_t i = 0; i < cap && i < (int32_t)t.size(); ++i) {
+        const GemmKey& k = t[i].first;
+        const GemmChoice& ch = t[i].second;
+        int tm, tn, tk;
+        gemm_tile_shape(ch.tile, &tm, &tn, &tk);
+        out[i] = rpnn_tune_entry{k.M, k.N, k.K0, k.K1, k.flags, tm, tn, tk, ch.splits, ch.us, ch.default_us};
+    }
     return RPNN_OK;
 }
 

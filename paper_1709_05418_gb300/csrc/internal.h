@@ -75,6 +75,31 @@ struct Volume {
     VolumeView view() const;
 };
 
+// Autotuned SIMT GEMM launches: a shape (rows, columns, the K of each operand segment,
+// operand layouts and epilogue kind) maps to the tile shape and split-K factor that ran
+// fastest when the shape was first met.
+struct GemmKey {
+    int M, N, K0, K1, flags;
+    bool operator==(const GemmKey& o) const {
+        return M == o.M && N == o.N && K0 == o.K0 && K1 == o.K1 && flags == o.flags;
+    }
+};
+struct GemmChoice {
+    int tile, splits;     // index into the tile table; K split into this many runs
+    float us, default_us; // measured time of the choice and of the default tile
+};
+struct GemmTuner {
+    bool enabled = true;
+    std::vector<std::pair<GemmKey, GemmChoice>> table;
+    DevBuf scratch, ws;   // tuning output, split-K partial sums
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const GemmChoice* find(const GemmKey& k) const {
+        for (const auto& e : table)
+            if (e.first == k) return &e.second;
+        return nullptr;
+    }
+};
+
 // One item of a batched render as the batched descriptor kernel reads it: the item's
 // volume, the offset of its region in the per-pixel-sample query buffers, its light.
 struct BatchItemDev {
@@ -108,6 +133,7 @@ struct Ctx {
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
+    GemmTuner tuner;
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
@@ -164,6 +190,8 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
 rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
                              const float* dout, float* dparams, cudaStream_t s);
 size_t mlp_saved_floats_per_row();
+// block tile (rows, columns, K step) of entry `tile` of the SIMT GEMM tile table
+void gemm_tile_shape(int tile, int* bm, int* bn, int* bk);
 // FP32 forward with caller-provided parameters P and three q x 200 scratch buffers
 rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
                                  float* s1, float* s2, cudaStream_t s);

@@ -7,14 +7,13 @@
 // serves the forward layers, the data gradients (dY W) and the weight gradients
 // (dY^T X).  The block's first layer is two segments: [z^k | o^{k-1}] [V^k | W1^k]^T.
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
 namespace rpnn {
 
 namespace {
-
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 struct Seg {
     const float* A;
@@ -35,6 +34,15 @@ struct Epi {
     int64_t ldc;
 };
 
+__device__ __forceinline__ float epilogue(const Epi& e, int m, int n, float v) {
+    if (e.bias) v += e.bias[n];
+    if (e.res) v += e.res[(int64_t)m * e.ldr + n];
+    if (e.relu) v = fmaxf(v, 0.0f);
+    if (e.mask && !(e.mask[(int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
+    return v;
+}
+
+template <int BM, int BN, int BK, int NT>
 __device__ __forceinline__ void load_tiles(const Seg& s, int m0, int n0, int k0, int M, int N,
                                            float (*As)[BM + 4], float (*Bs)[BN + 4]) {
     const int tid = threadIdx.x;
@@ -56,50 +64,74 @@ __device__ __forceinline__ void load_tiles(const Seg& s, int m0, int n0, int k0,
     }
 }
 
-__global__ void __launch_bounds__(NT)
-k_gemm(int M_host, const int* __restrict__ M_dev, int N, Seg s0, Seg s1, int nseg, Epi e) {
+// C tile [BM x BN] per block, [TM x TN] per thread (rows ty + i*BM/TM, columns
+// tx + j*BN/TN).  Every output sums its products in increasing k (segment 0, then
+// segment 1) with one FMA each, whatever the tile shape, so all tiles give the same bits.
+// With splits > 1, block z takes the z-th contiguous run of the K tiles and writes its
+// partial sums to ws[z][m][n]; k_splitk_epi adds them in z order and applies the epilogue.
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(int M_host, const int* __restrict__ M_dev, int N, Seg s0, Seg s1, int nseg, Epi e, int splits,
+       float* __restrict__ ws) {
+    constexpr int NT = (BM / TM) * (BN / TN), CX = BN / TN, RY = BM / TM;
+    static_assert((BM * BK) % NT == 0 && (BN * BK) % NT == 0, "tile loads must divide evenly");
     const int M = M_dev ? *M_dev : M_host;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (m0 >= M) return;
     __shared__ float As[BK][BM + 4];
     __shared__ float Bs[BK][BN + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[4][4] = {};
-    for (int si = 0; si < nseg; ++si) {
-        const Seg& s = si == 0 ? s0 : s1;
-        for (int k0 = 0; k0 < s.K; k0 += BK) {
-            load_tiles(s, m0, n0, k0, M, N, As, Bs);
-            __syncthreads();
+    const int tx = threadIdx.x % CX, ty = threadIdx.x / CX;
+    float acc[TM][TN] = {};
+    const int T0 = (s0.K + BK - 1) / BK;
+    const int T = T0 + (nseg > 1 ? (s1.K + BK - 1) / BK : 0);
+    const int per = (T + splits - 1) / splits;
+    const int tb = (int)blockIdx.z * per, te = min(T, tb + per);
+    for (int t = tb; t < te; ++t) {
+        const bool first = t < T0;
+        const Seg& s = first ? s0 : s1;
+        const int k0 = (first ? t : t - T0) * BK;
+        load_tiles<BM, BN, BK, NT>(s, m0, n0, k0, M, N, As, Bs);
+        __syncthreads();
 #pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                float a[4], b[4];
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[TM], b[TN];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + RY * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + CX * j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
-            __syncthreads();
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
+        __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty + 16 * i;
+    for (int i = 0; i < TM; ++i) {
+        const int m = m0 + ty + RY * i;
         if (m >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx + 16 * j;
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx + CX * j;
             if (n >= N) continue;
-            float v = acc[i][j];
-            if (e.bias) v += e.bias[n];
-            if (e.res) v += e.res[(int64_t)m * e.ldr + n];
-            if (e.relu) v = fmaxf(v, 0.0f);
-            if (e.mask && !(e.mask[(int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
-            e.C[(int64_t)m * e.ldc + n] = v;
+            if (splits > 1)
+                ws[((int64_t)blockIdx.z * M_host + m) * N + n] = acc[i][j];
+            else
+                e.C[(int64_t)m * e.ldc + n] = epilogue(e, m, n, acc[i][j]);
         }
+    }
+}
+
+__global__ void k_splitk_epi(const float* __restrict__ ws, int splits, int M_host, const int* __restrict__ M_dev,
+                             int N, Epi e) {
+    const int M = M_dev ? *M_dev : M_host;
+    const int64_t total = (int64_t)M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / N), n = (int)(i % N);
+        float v = 0.0f;
+        for (int z = 0; z < splits; ++z) v += ws[((int64_t)z * M_host + m) * N + n];
+        e.C[(int64_t)m * e.ldc + n] = epilogue(e, m, n, v);
     }
 }
 
@@ -110,13 +142,23 @@ __global__ void k_mask(const float* __restrict__ x, const float* __restrict__ m,
     if (i < n) out[i] = m[i] > 0.0f ? x[i] : 0.0f;
 }
 
-// column sums: out[n] = sum_m X[m][n] (bias gradients), fixed order per column
-__global__ void k_colsum(const float* __restrict__ X, int M, int N, int64_t ld, float* __restrict__ out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// column sums: out[n] = sum_m X[m][n] (bias gradients).  Block of 32 x 32 threads per 32
+// columns: thread (x, y) sums rows y, y + 32, ... of column x in increasing order, then
+// the 32 partial sums are added in y order (a fixed order for given M).
+__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ X, int M, int N, int64_t ld,
+                                                 float* __restrict__ out) {
+    __shared__ float part[32][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
-    for (int m = 0; m < M; ++m) s += X[(int64_t)m * ld + n];
-    out[n] = s;
+    if (n < N)
+        for (int m = threadIdx.y; m < M; m += 32) s += X[(int64_t)m * ld + n];
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.0f;
+        for (int y = 0; y < 32; ++y) t += part[y][threadIdx.x];
+        out[n] = t;
+    }
 }
 
 Seg seg(const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk, int64_t sbn, int K) {
@@ -133,14 +175,147 @@ Epi epi(float* C, int64_t ldc, const float* bias = nullptr, int relu = 0,
     return e;
 }
 
-rpnn_status gemm(int M, const int* M_dev, int N, const Seg& s0, const Seg* s1, const Epi& e,
+// ---- tile shapes and the autotuner ----------------------------------------------------
+struct TileShape { int bm, bn, bk, tm, tn; };
+constexpr TileShape kTiles[] = {
+    {64, 64, 16, 4, 4},    // the default (no tuning)
+    {128, 64, 16, 8, 4},
+    {64, 128, 16, 4, 8},
+    {128, 128, 8, 8, 8},
+    {32, 64, 16, 2, 4},
+    {128, 32, 16, 8, 2},
+};
+constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+constexpr int kSplits[] = {1, 2, 4, 8, 16, 32};
+constexpr int kMinSplitK = 1024;
+
+template <int BM, int BN, int BK, int TM, int TN>
+void launch_tile(int M, const int* M_dev, int N, const Seg& s0, const Seg& s1, int nseg, const Epi& e,
+                 int splits, float* ws, cudaStream_t s) {
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    k_gemm<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(M, M_dev, N, s0, s1, nseg, e, splits, ws);
+}
+
+rpnn_status launch_gemm(int tile, int splits, int M, const int* M_dev, int N, const Seg& s0, const Seg& s1,
+                        int nseg, const Epi& e, float* ws, cudaStream_t s) {
+    const TileShape& t = kTiles[tile];
+    if ((M + t.bm - 1) / t.bm > 65535) { set_error("GEMM with %d rows exceeds the grid limit", M); return RPNN_ERR_ARG; }
+    switch (tile) {
+        case 0: launch_tile<64, 64, 16, 4, 4>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+        case 1: launch_tile<128, 64, 16, 8, 4>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+        case 2: launch_tile<64, 128, 16, 4, 8>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+        case 3: launch_tile<128, 128, 8, 8, 8>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+        case 4: launch_tile<32, 64, 16, 2, 4>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+        default: launch_tile<128, 32, 16, 8, 2>(M, M_dev, N, s0, s1, nseg, e, splits, ws, s); break;
+    }
+    RPNN_CHECK_LAUNCH();
+    if (splits > 1) {
+        const int64_t total = (int64_t)M * N;
+        int64_t b = (total + 255) / 256;
+        if (b > 152 * 8) b = 152 * 8;
+        k_splitk_epi<<<(unsigned)b, 256, 0, s>>>(ws, splits, M, M_dev, N, e);
+        RPNN_CHECK_LAUNCH();
+    }
+    return RPNN_OK;
+}
+
+GemmKey make_key(int M, int N, const Seg& s0, const Seg* s1, const Epi& e, bool dyn) {
+    GemmKey k{};
+    k.M = M; k.N = N; k.K0 = s0.K; k.K1 = s1 ? s1->K : 0;
+    k.flags = (s0.sak == 1) | (s0.sbn == 1) << 1 | (s1 && s1->sak == 1) << 2 | (s1 && s1->sbn == 1) << 3 |
+              (e.bias != nullptr) << 4 | (e.res != nullptr) << 5 | (e.mask != nullptr) << 6 | (int)dyn << 7;
+    return k;
+}
+
+// Times every admissible (tile, split) on the call's own operands, writing into scratch
+// (the caller's output is untouched, so in-place residuals stay valid), and returns the
+// fastest.  Synchronises the stream.
+rpnn_status tune(Ctx& c, const GemmKey& key, int M, const int* M_dev, int N, const Seg& s0, const Seg& s1,
+                 int nseg, const Epi& e, cudaStream_t s, GemmChoice* out) {
+    GemmTuner& tu = c.tuner;
+    // admissible (tile, split) pairs: tiles no taller than twice the rows; a split only
+    // for inner sizes of at least kMinSplitK (the weight gradients, which sum over the
+    // batch; forward GEMMs therefore never split and give the default tile's bits), where
+    // the tiles alone fill fewer than one wave, keeping >= 4 K tiles per run and at most
+    // 8 blocks per SM
+    struct Cand { int t, sp; };
+    std::vector<Cand> cands;
+    int maxsplit = 1;
+    const int ksteps16 = (s0.K + 15) / 16 + (nseg > 1 ? (s1.K + 15) / 16 : 0);
+    for (int t = 0; t < kNumTiles; ++t) {
+        const TileShape& ts = kTiles[t];
+        if (t > 0 && ts.bm > 2 * M) continue;
+        const int64_t blocks = (int64_t)((N + ts.bn - 1) / ts.bn) * ((M + ts.bm - 1) / ts.bm);
+        for (int sp : kSplits) {
+            if (sp > 1 && (ksteps16 * 16 < kMinSplitK || blocks >= c.num_sms || blocks * sp > (int64_t)c.num_sms * 8 ||
+                           (ksteps16 * 16 / ts.bk) / sp < 4))
+                continue;
+            cands.push_back({t, sp});
+            if (sp > maxsplit) maxsplit = sp;
+        }
+    }
+    rpnn_status st = tu.scratch.reserve((size_t)M * N * sizeof(float));
+    if (!st && maxsplit > 1) st = tu.ws.reserve((size_t)maxsplit * M * N * sizeof(float));
+    if (st) return st;
+    Epi es = e;
+    es.C = tu.scratch.as<float>();
+    es.ldc = N;
+    if (!tu.ev0) {
+        RPNN_CUDA_TRY(cudaEventCreate(&tu.ev0));
+        RPNN_CUDA_TRY(cudaEventCreate(&tu.ev1));
+    }
+    GemmChoice best{0, 1, 1e30f, 0.0f};
+    for (const Cand& cd : cands) {
+        st = launch_gemm(cd.t, cd.sp, M, M_dev, N, s0, s1, nseg, es, tu.ws.as<float>(), s);   // warm
+        if (st) return st;
+        RPNN_CUDA_TRY(cudaEventRecord(tu.ev0, s));
+        for (int r = 0; r < 3; ++r) {
+            st = launch_gemm(cd.t, cd.sp, M, M_dev, N, s0, s1, nseg, es, tu.ws.as<float>(), s);
+            if (st) return st;
+        }
+        RPNN_CUDA_TRY(cudaEventRecord(tu.ev1, s));
+        RPNN_CUDA_TRY(cudaEventSynchronize(tu.ev1));
+        float ms = 0.0f;
+        RPNN_CUDA_TRY(cudaEventElapsedTime(&ms, tu.ev0, tu.ev1));
+        const float us = ms * 1000.0f / 3.0f;
+        if (cd.t == 0 && cd.sp == 1) best.default_us = us;
+        if (us < best.us) { best.us = us; best.tile = cd.t; best.splits = cd.sp; }
+    }
+    tu.table.emplace_back(key, best);
+    *out = best;
+    return RPNN_OK;
+}
+
+// C = epilogue(sum_seg A_seg B_seg).  With a context whose autotuner is on, the tile shape
+// and split-K factor are the fastest measured for this shape (timed at its first use,
+// outside stream capture); otherwise the default 64 x 64 tile without a split.
+rpnn_status gemm(Ctx* c, int M, const int* M_dev, int N, const Seg& s0, const Seg* s1, const Epi& e,
                  cudaStream_t s) {
     if (M <= 0 || N <= 0) return RPNN_OK;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    if (grid.y > 65535u) { set_error("GEMM with %d rows exceeds the grid limit", M); return RPNN_ERR_ARG; }
-    k_gemm<<<grid, NT, 0, s>>>(M, M_dev, N, s0, s1 ? *s1 : s0, s1 ? 2 : 1, e);
-    RPNN_CHECK_LAUNCH();
-    return RPNN_OK;
+    GemmChoice ch{0, 1, 0.0f, 0.0f};
+    const Seg& s1r = s1 ? *s1 : s0;
+    const int nseg = s1 ? 2 : 1;
+    if (c && c->tuner.enabled) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            const GemmKey key = make_key(M, N, s0, s1, e, M_dev != nullptr);
+            const GemmChoice* hit = c->tuner.find(key);
+            if (hit) {
+                ch = *hit;
+            } else {
+                rpnn_status st = tune(*c, key, M, M_dev, N, s0, s1r, nseg, e, s, &ch);
+                if (st) return st;
+            }
+        }
+    }
+    float* ws = nullptr;
+    if (ch.splits > 1) {
+        rpnn_status st = c->tuner.ws.reserve((size_t)ch.splits * M * N * sizeof(float));
+        if (st) return st;
+        ws = c->tuner.ws.as<float>();
+    }
+    return launch_gemm(ch.tile, ch.splits, M, M_dev, N, s0, s1r, nseg, e, ws, s);
 }
 
 // Deterministic log-MSE loss (Sec. 5.2): one block; FP64 tree reduction.
@@ -177,6 +352,11 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 }
 
 }  // namespace
+
+void gemm_tile_shape(int tile, int* bm, int* bn, int* bk) {
+    const TileShape& t = kTiles[(tile >= 0 && tile < kNumTiles) ? tile : 0];
+    *bm = t.bm; *bn = t.bn; *bk = t.bk;
+}
 
 const ParamLayout& param_layout() {
     static ParamLayout L = [] {
@@ -219,27 +399,27 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
         Seg z = seg(desc + k * RPNN_DESC_STRIDE, ZS, 1, P + L.V[k], 1, RPNN_DIN, RPNN_DIN);
         if (k > 0) {
             Seg o = seg(o_prev, H, 1, P + L.W1[k], 1, H, RPNN_H);
-            st = gemm(M, q_dev, RPNN_H, z, &o, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(&c, M, q_dev, RPNN_H, z, &o, epi(f1, H, P + L.b1[k], 1), s);
         } else {
-            st = gemm(M, q_dev, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(&c, M, q_dev, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
         }
         if (st) return st;
         // o^k = relu(W2 F1 + b2 + o^{k-1})  (in place when not saving)
         Seg w2 = seg(f1, H, 1, P + L.W2[k], 1, H, RPNN_H);
-        st = gemm(M, q_dev, RPNN_H, w2, nullptr, epi(o_cur, H, P + L.b2[k], 1, k > 0 ? o_prev : nullptr, H), s);
+        st = gemm(&c, M, q_dev, RPNN_H, w2, nullptr, epi(o_cur, H, P + L.b2[k], 1, k > 0 ? o_prev : nullptr, H), s);
         if (st) return st;
         o_prev = o_cur;
     }
     // standard layers
     float* t0 = saved ? slot(20) : c.act1.as<float>();
     float* t1 = saved ? slot(21) : c.act2.as<float>();
-    st = gemm(M, q_dev, RPNN_H, seg(o_prev, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr,
+    st = gemm(&c, M, q_dev, RPNN_H, seg(o_prev, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr,
               epi(t0, H, P + L.bT[0], 1), s);
     if (st) return st;
-    st = gemm(M, q_dev, RPNN_H, seg(t0, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr,
+    st = gemm(&c, M, q_dev, RPNN_H, seg(t0, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr,
               epi(t1, H, P + L.bT[1], 1), s);
     if (st) return st;
-    st = gemm(M, q_dev, 1, seg(t1, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
+    st = gemm(&c, M, q_dev, 1, seg(t1, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
     if (st) return st;
     if (saved) RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float),
                                              cudaMemcpyDeviceToDevice, s));
@@ -258,20 +438,20 @@ rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, f
         Seg z = seg(desc + k * RPNN_DESC_STRIDE, ZS, 1, P + L.V[k], 1, RPNN_DIN, RPNN_DIN);
         if (k > 0) {
             Seg oo = seg(o, H, 1, P + L.W1[k], 1, H, RPNN_H);
-            st = gemm(M, nullptr, RPNN_H, z, &oo, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(nullptr, M, nullptr, RPNN_H, z, &oo, epi(f1, H, P + L.b1[k], 1), s);
         } else {
-            st = gemm(M, nullptr, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(nullptr, M, nullptr, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
         }
         if (st) return st;
         Seg w2 = seg(f1, H, 1, P + L.W2[k], 1, H, RPNN_H);
-        st = gemm(M, nullptr, RPNN_H, w2, nullptr, epi(o, H, P + L.b2[k], 1, k > 0 ? o : nullptr, H), s);
+        st = gemm(nullptr, M, nullptr, RPNN_H, w2, nullptr, epi(o, H, P + L.b2[k], 1, k > 0 ? o : nullptr, H), s);
         if (st) return st;
     }
-    st = gemm(M, nullptr, RPNN_H, seg(o, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr, epi(s1, H, P + L.bT[0], 1), s);
+    st = gemm(nullptr, M, nullptr, RPNN_H, seg(o, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr, epi(s1, H, P + L.bT[0], 1), s);
     if (st) return st;
-    st = gemm(M, nullptr, RPNN_H, seg(s1, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr, epi(s2, H, P + L.bT[1], 1), s);
+    st = gemm(nullptr, M, nullptr, RPNN_H, seg(s1, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr, epi(s2, H, P + L.bT[1], 1), s);
     if (st) return st;
-    return gemm(M, nullptr, 1, seg(s2, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
+    return gemm(nullptr, M, nullptr, 1, seg(s2, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
 }
 
 rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
@@ -291,29 +471,29 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
     float* bufB = c.act1.as<float>();
     float* da = c.act2.as<float>();
     float* da3 = c.t_dg.as<float>();
-    const dim3 cs_grid((RPNN_H + 255) / 256);
+    const dim3 cs_grid((RPNN_H + 31) / 32), cs_block(32, 32);
     // last layer: g = relu(T3 o12 + bT3): da3 = dout * (g > 0)
     k_mask<<<(M + 255) / 256, 256, 0, s>>>(dout, g, M, da3);
     RPNN_CHECK_LAUNCH();
     // dT3[0][j] = sum_m da3[m] o12[m][j]; dbT3 = sum_m da3
-    st = gemm(1, nullptr, RPNN_H, seg(da3, 0, 1, slot(21), H, 1, M), nullptr, epi(dP + L.T[2], H), s);
+    st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, slot(21), H, 1, M), nullptr, epi(dP + L.T[2], H), s);
     if (st) return st;
-    k_colsum<<<1, 32, 0, s>>>(da3, M, 1, 1, dP + L.bT[2]);
+    k_colsum<<<1, cs_block, 0, s>>>(da3, M, 1, 1, dP + L.bT[2]);
     RPNN_CHECK_LAUNCH();
     // da2 = (da3 T3) * (o12 > 0)
-    st = gemm(M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
+    st = gemm(&c, M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
               epi(bufA, H, nullptr, 0, nullptr, 0, slot(21), H), s);
     if (st) return st;
     // standard layer 2: input o11 (slot 20); layer 1: input o10 (slot 9)
     const float* tin[2] = {slot(9), slot(20)};
     for (int t = 1; t >= 0; --t) {
         // dT = da^T x_in; db = colsum(da)
-        st = gemm(RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, tin[t], H, 1, M), nullptr, epi(dP + L.T[t], H), s);
+        st = gemm(&c, RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, tin[t], H, 1, M), nullptr, epi(dP + L.T[t], H), s);
         if (st) return st;
-        k_colsum<<<cs_grid, 256, 0, s>>>(bufA, M, RPNN_H, H, dP + L.bT[t]);
+        k_colsum<<<cs_grid, cs_block, 0, s>>>(bufA, M, RPNN_H, H, dP + L.bT[t]);
         RPNN_CHECK_LAUNCH();
         // d x_in = da T, masked by (x_in > 0) (x_in is a ReLU output)
-        st = gemm(M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.T[t], H, 1, RPNN_H), nullptr,
+        st = gemm(&c, M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.T[t], H, 1, RPNN_H), nullptr,
                   epi(bufB, H, nullptr, 0, nullptr, 0, tin[t], H), s);
         if (st) return st;
         float* tmp = bufA; bufA = bufB; bufB = tmp;
@@ -322,26 +502,26 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
     for (int k = RPNN_K - 1; k >= 0; --k) {
         const float* f1 = slot(10 + k);
         // dW2 = dpre^T F1; db2 = colsum(dpre)
-        st = gemm(RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, f1, H, 1, M), nullptr, epi(dP + L.W2[k], H), s);
+        st = gemm(&c, RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, f1, H, 1, M), nullptr, epi(dP + L.W2[k], H), s);
         if (st) return st;
-        k_colsum<<<cs_grid, 256, 0, s>>>(bufA, M, RPNN_H, H, dP + L.b2[k]);
+        k_colsum<<<cs_grid, cs_block, 0, s>>>(bufA, M, RPNN_H, H, dP + L.b2[k]);
         RPNN_CHECK_LAUNCH();
         // da1 = (dpre W2) * (F1 > 0)
-        st = gemm(M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.W2[k], H, 1, RPNN_H), nullptr,
+        st = gemm(&c, M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.W2[k], H, 1, RPNN_H), nullptr,
                   epi(da, H, nullptr, 0, nullptr, 0, f1, H), s);
         if (st) return st;
         // dV = da1^T z^k; db1 = colsum(da1)
-        st = gemm(RPNN_H, nullptr, RPNN_DIN, seg(da, 1, H, desc + k * RPNN_DESC_STRIDE, ZS, 1, M), nullptr,
+        st = gemm(&c, RPNN_H, nullptr, RPNN_DIN, seg(da, 1, H, desc + k * RPNN_DESC_STRIDE, ZS, 1, M), nullptr,
                   epi(dP + L.V[k], RPNN_DIN), s);
         if (st) return st;
-        k_colsum<<<cs_grid, 256, 0, s>>>(da, M, RPNN_H, H, dP + L.b1[k]);
+        k_colsum<<<cs_grid, cs_block, 0, s>>>(da, M, RPNN_H, H, dP + L.b1[k]);
         RPNN_CHECK_LAUNCH();
         if (k > 0) {
             const float* oprev = slot(k - 1);
-            st = gemm(RPNN_H, nullptr, RPNN_H, seg(da, 1, H, oprev, H, 1, M), nullptr, epi(dP + L.W1[k], H), s);
+            st = gemm(&c, RPNN_H, nullptr, RPNN_H, seg(da, 1, H, oprev, H, 1, M), nullptr, epi(dP + L.W1[k], H), s);
             if (st) return st;
             // dpre_{k-1} = (dpre_k + da1 W1) * (o^{k-1} > 0)
-            st = gemm(M, nullptr, RPNN_H, seg(da, H, 1, P + L.W1[k], H, 1, RPNN_H), nullptr,
+            st = gemm(&c, M, nullptr, RPNN_H, seg(da, H, 1, P + L.W1[k], H, 1, RPNN_H), nullptr,
                       epi(bufB, H, nullptr, 0, bufA, H, oprev, H), s);
             if (st) return st;
             float* tmp = bufA; bufA = bufB; bufB = tmp;
