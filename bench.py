@@ -274,9 +274,25 @@ def run_batch(args, ws, rank, local):
     ctx.close()
 
 
-# kernels of one FP32 training step: 23 forward GEMMs, the loss, 78 backward launches (GEMMs,
-# bias-gradient sums, one mask), Adam, and the BF16 weight image for rendering
-TRAIN_LAUNCHES = 23 + 1 + 78 + 1 + 1
+def train_launches(tab, bf16, batch):
+    """Kernels of one training step.  FP32: 23 forward GEMMs, the loss, 78 backward launches
+    (GEMMs, bias-gradient sums, one mask), Adam and the BF16 render image.  BF16: the training
+    weight image and descriptor conversion, 22 tensor-core and 1 CUDA-core forward GEMMs, the
+    loss, 4 output-layer backward launches, 1 conversion, 74 backward GEMMs and sums, Adam and
+    the render image.  Plus one reduction per split-K weight-gradient GEMM: the 200 x 200 shape
+    runs 21 times a step (T1, T2, W2 x 10, W1 x 9), the 200 x 226 one 10 times, the 1 x 200 once."""
+    n = 107 if bf16 else 104
+    for e in tab:
+        if e["splits"] <= 1 or e["K0"] != batch:
+            continue
+        tc = bool(e["flags"] & 256)
+        if e["M"] == 1:
+            n += 1
+        elif tc == bf16:
+            n += 21 if e["N"] == 200 else 10
+    return n
+
+
 TRAIN_WORKLOAD = ("training: fBm clouds (seeds 100-103, edges drawn from {128, 160, 192, 224, 256}, FP32 "
                   "density), labelled records (uniform direction, origin on the bounding-sphere disk, "
                   "uniform light; path-traced L_i until +-2% at 95% confidence, 64 paths at least, capped "
@@ -328,26 +344,36 @@ def run_train(args, ws, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     batches = [(z[i * B:(i + 1) * B].contiguous(), t[i * B:(i + 1) * B].contiguous()) for i in range(nb)]
     step = 0
-    for i in range(args.warmup):
-        step += 1
-        ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
-    ctx.sync_status()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def timed_steps(prec, steps):
+        nonlocal step
+        ctx.set_train_precision(prec)
+        ctx.set_weights(params)
+        for i in range(args.warmup):
+            step += 1
+            ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
+        ctx.sync_status()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        barrier(ws)
+        for i, (e0, e1) in enumerate(evs):
+            flush.zero_()
+            step += 1
+            e0.record()
+            ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
+            e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ctx.sync_status()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
+
+    main_prec = api.BF16 if args.train_precision == "bf16" else api.F32
+    other_prec = api.F32 if main_prec == api.BF16 else api.BF16
+    ms_other = timed_steps(other_prec, max(3, args.steps // 2))
     clocks = Clocks(local)
     clocks.start()
-    torch.cuda.synchronize()
-    barrier(ws)
-    for i, (e0, e1) in enumerate(evs):
-        flush.zero_()
-        step += 1
-        e0.record()
-        ctx.train_step(*batches[i % nb], params, m, v, step, loss=loss)
-        e1.record()
-    torch.cuda.synchronize()
-    barrier(ws)
+    ms = timed_steps(main_prec, args.steps)
     clk = clocks.stop()
-    ctx.sync_status()
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
     total = sum_over_ranks(float(B) * args.steps, ws, dev)
     # end to end: each step's minibatch copied from pinned host memory, the loss read back
     hz = [bz.cpu().pin_memory() for bz, _ in batches]
@@ -373,7 +399,7 @@ def run_train(args, ws, rank, local):
         "metric": "RPNN training samples/s on 1 GB300 (log-MSE + Adam, minibatch 4096)",
         "value": total / (ms / 1e3), "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.train_precision, "data": "synthetic",
         "config": {"workload": TRAIN_WORKLOAD, "batch": B, "records": int(nrec),
                    "minibatches": f"{nb} distinct minibatches of the record pool, in turn",
                    "l2": "flushed: 256 MB write between timed steps"},
@@ -384,13 +410,23 @@ def run_train(args, ws, rank, local):
         "gpu_launches": None,
         "e2e": {"value": total / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(dz.numel() * 4 + dt_.numel() * 4),
                 "d2h_bytes_per_step": 8},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                     "traffic": None, "kernel": "whole training step (FP32 CUDA-core GEMMs, 3 x 2.5844 MFLOP per sample)",
-                     "peak_src": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"},
+        "roofline": ({"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"] or pk["bf16_tflops"],
+                      "unit": "TFLOP/s", "frac": ach / (pk["bf16_tflops_sustained"] or pk["bf16_tflops"]),
+                      "traffic": None,
+                      "kernel": "whole training step (BF16 tcgen05 GEMMs + FP32 epilogues, 3 x 2.5844 MFLOP per sample)",
+                      "peak_src": pk["src"] + " BF16 sustained"}
+                     if main_prec == api.BF16 else
+                     {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                      "traffic": None,
+                      "kernel": "whole training step (FP32 CUDA-core GEMMs, 3 x 2.5844 MFLOP per sample)",
+                      "peak_src": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}),
+        "other_precision": {"dtype": "f32" if main_prec == api.BF16 else "bf16",
+                            "value": float(B) * max(3, args.steps // 2) / (ms_other / 1e3), "unit": "samples/s",
+                            "ms_per_step": ms_other / max(3, args.steps // 2)},
         "clocks": clk,
     }
     tab = ctx.autotune_table()
-    line["gpu_launches"] = (TRAIN_LAUNCHES + sum(1 for e in tab if e["splits"] > 1)) * args.steps
+    line["gpu_launches"] = train_launches(tab, main_prec == api.BF16, B) * args.steps
     line["autotune"] = {"on": not args.no_autotune, "shapes": len(tab),
                         "tuned_us_sum": sum(e["us"] for e in tab),
                         "default_tile_us_sum": sum(e["default_us"] for e in tab),
@@ -559,6 +595,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default 64x64 tile for every FP32 CUDA-core GEMM (no tuning)")
+    ap.add_argument("--train-precision", default="bf16", choices=["bf16", "f32"],
+                    help="arithmetic of the training workload's timed steps (the other is timed beside)")
     ap.add_argument("--train-records", type=int, default=8192,
                     help="labelled records generated (and timed) for the training workload")
     ap.add_argument("--train-max-paths", type=int, default=4096,
@@ -598,6 +636,19 @@ def main():
     ctx.set_weights(torch.from_numpy(params).to(dev))
     ctx.set_autotune(not args.no_autotune)
     info = ctx.get_volume_info(vol)
+    # statistics + Gaussian pyramid + corner packing of the volume (per-volume preprocessing,
+    # outside the render), rebuilt a few times with the L2 flushed in between
+    fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pyr_ms = []
+    for _ in range(4):
+        fl.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        ctx.build_mips(vol)
+        a1.record()
+        torch.cuda.synchronize()
+        pyr_ms.append(a0.elapsed_time(a1))
+    del fl
     if args.profile_only:
         for p in (api.BF16, api.F32):
             ctx.render(vol, cam, precision=p)
@@ -719,6 +770,15 @@ def main():
     roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     roof["kernel"] = dom
     roof["peak_src"] = pk["src"]
+    # a1/a2: the FP32 grid read once and the packed pyramid levels written once
+    nvox = int(np.prod(info["n"]))
+    pyr_ms_med = float(np.median(pyr_ms[1:]))
+    pyr_alg = nvox * 4 + pyr_bytes
+    pyramid = {"ms": pyr_ms_med, "algorithmic_bytes": pyr_alg,
+               "roofline": {"bound": "hbm", "achieved": pyr_alg / (pyr_ms_med / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                            "unit": "GB/s", "frac": pyr_alg / (pyr_ms_med / 1e3) / 1e9 / pk["hbm_gbs"],
+                            "peak_src": pk["src"]},
+               "note": "statistics, separable Gaussian levels and corner-record packing; median of 3 rebuilds"}
     # the tensor-core network beside it (BF16 here, E4M3 in fp8_form): dense FLOPs per launch over
     # the CUDA-event time of the launch, against the measured BF16 burst peak (x2 for E4M3, the
     # nominal FP8:BF16 tensor ratio)
@@ -745,6 +805,8 @@ def main():
                    "l2": "flushed: 256 MB write between timed steps",
                    "mip_of_level": info["mip_of_level"]},
         "stages_ms_per_step": stage_ms,
+        "primary_rays_per_s": 512 * 512 / (stage_ms["primary"] / 1e3),
+        "pyramid_build": pyramid,
         "gpu_launches": (5 if prec == api.BF16 else 27) * args.steps,
         "e2e": e2e, "roofline": roof, "clocks": clk,
     }

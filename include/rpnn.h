@@ -265,8 +265,16 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
                             int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
                             float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
                             void* stream);
+/* Arithmetic of rpnn_train_step and rpnn_mlp_backward: RPNN_F32 (the default; FP32 CUDA-core
+ * GEMMs) or RPNN_BF16 (mixed precision: every 200-wide layer and weight gradient is a BF16
+ * tcgen05 GEMM with FP32 accumulation; FP32 master weights, biases, residual sums, ReLU
+ * masks, loss, gradients and Adam; the 1-wide output layer stays FP32).  No counterpart in
+ * the paper, which does not state its training arithmetic.  Errors: RPNN_ERR_ARG for any
+ * other value. */
+rpnn_status rpnn_set_train_precision(rpnn_ctx* ctx, int32_t precision);
 /* GEMM-tile autotuner of the FP32 CUDA-core network (forward, backward, the FP32 render
- * form; no counterpart in the paper).  With `on` != 0 (the default), the first call of
+ * form) and of the BF16 tensor-core training GEMMs (tile width 64/128/256 and split-K; no
+ * counterpart in the paper).  With `on` != 0 (the default), the first call of
  * each GEMM shape (rows, columns, inner sizes, operand layouts, epilogue kind) times every
  * admissible tile shape and split-K factor on the call's own operands (writing into
  * library scratch, so the call's output is unaffected), synchronising the stream once, and

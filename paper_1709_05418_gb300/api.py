@@ -107,6 +107,7 @@ def load():
                                 _vp, _vp],
             "rpnn_set_profiling": [_vp, i32],
             "rpnn_set_autotune": [_vp, i32],
+            "rpnn_set_train_precision": [_vp, i32],
             "rpnn_get_autotune": [_vp, C.POINTER(TuneEntry), i32, C.POINTER(i32)],
             "rpnn_read_profile": [_vp, C.POINTER(C.c_double), C.POINTER(i64)],
         }
@@ -199,6 +200,10 @@ class Context:
 
     def set_profiling(self, on: bool):
         self._check(self.L.rpnn_set_profiling(self.h, 1 if on else 0))
+
+    def set_train_precision(self, precision):
+        """F32 (default) or BF16 arithmetic for train_step and mlp_backward."""
+        self._check(self.L.rpnn_set_train_precision(self.h, precision))
 
     def set_autotune(self, on: bool):
         self._check(self.L.rpnn_set_autotune(self.h, 1 if on else 0))

@@ -46,6 +46,29 @@ void DevBuf::release() {
 
 using namespace rpnn;
 
+namespace {
+// Forward with saved activations in the context's training precision (FP32 CUDA cores,
+// or BF16 tensor-core GEMMs with FP32 master weights); the prediction goes to t_out.
+rpnn_status train_forward(Ctx& c, const float* desc, int64_t q, cudaStream_t s) {
+    rpnn_status st = c.t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
+    if (!st) st = c.t_out.reserve(q * sizeof(float));
+    if (st) return st;
+    if (c.train_precision == RPNN_BF16) {
+        st = c.t_saved16.reserve(train_bf16_saved_elems(q) * 2);
+        if (st) return st;
+        return mlp_forward_bf16_train(c, desc, q, c.t_out.as<float>(), c.t_saved.as<float>(),
+                                      c.t_saved16.as<uint16_t>(), s);
+    }
+    return mlp_forward_f32(c, desc, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
+}
+
+rpnn_status train_backward(Ctx& c, const float* desc, int64_t q, const float* dout, float* dP, cudaStream_t s) {
+    if (c.train_precision == RPNN_BF16)
+        return mlp_backward_bf16_train(c, q, c.t_saved.as<float>(), c.t_saved16.as<uint16_t>(), dout, dP, s);
+    return mlp_backward_f32(c, desc, q, c.t_saved.as<float>(), dout, dP, s);
+}
+}  // namespace
+
 #define CHECK_CTX(ctx)                                                        \
     do {                                                                      \
         if (!(ctx)) { set_error("null context"); return RPNN_ERR_HANDLE; }    \
@@ -88,7 +111,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
-                      &c->tuner.scratch, &c->tuner.ws};
+                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
@@ -406,6 +429,16 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {
     return RPNN_OK;
 }
 
+rpnn_status rpnn_set_train_precision(rpnn_ctx* ctx, int32_t precision) {
+    CHECK_CTX(ctx);
+    if (precision != RPNN_F32 && precision != RPNN_BF16) {
+        set_error("training precision must be RPNN_F32 or RPNN_BF16");
+        return RPNN_ERR_ARG;
+    }
+    reinterpret_cast<Ctx*>(ctx)->train_precision = precision;
+    return RPNN_OK;
+}
+
 rpnn_status rpnn_set_autotune(rpnn_ctx* ctx, int32_t on) {
     CHECK_CTX(ctx);
     reinterpret_cast<Ctx*>(ctx)->tuner.enabled = on != 0;
@@ -421,8 +454,8 @@ rpnn_status rpnn_get_autotune(rpnn_ctx* ctx, rpnn_tune_entry* out, int32_t cap, 
     for (int32_t i = 0; i < cap && i < (int32_t)t.size(); ++i) {
         const GemmKey& k = t[i].first;
         const GemmChoice& ch = t[i].second;
-        int tm, tn, tk;
-        gemm_tile_shape(ch.tile, &tm, &tn, &tk);
+        int tm = 128, tn = ch.tile, tk = 64;           // tensor-core entries store the tile width
+        if (!(k.flags & (1 << 8))) gemm_tile_shape(ch.tile, &tm, &tn, &tk);
         out[i] = rpnn_tune_entry{k.M, k.N, k.K0, k.K1, k.flags, tm, tn, tk, ch.splits, ch.us, ch.default_us};
     }
     return RPNN_OK;
@@ -477,12 +510,9 @@ rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q, c
     if (q <= 0 || q > 65535 * 64) { set_error("q must be in [1, %d]", 65535 * 64); return RPNN_ERR_ARG; }
     if (!dev_desc || !dev_dout || !dev_dparams) { set_error("null pointer"); return RPNN_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
-    rpnn_status st = c->t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
-    if (!st) st = c->t_out.reserve(q * sizeof(float));
+    rpnn_status st = train_forward(*c, dev_desc, q, s);
     if (st) return st;
-    st = mlp_forward_f32(*c, dev_desc, q, nullptr, c->t_out.as<float>(), c->t_saved.as<float>(), s);
-    if (st) return st;
-    return mlp_backward_f32(*c, dev_desc, q, c->t_saved.as<float>(), dev_dout, dev_dparams, s);
+    return train_backward(*c, dev_desc, q, dev_dout, dev_dparams, s);
 }
 
 rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* dev_target, int32_t batch,
@@ -499,17 +529,15 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t q = batch;
-    rpnn_status st = c->t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
-    if (!st) st = c->t_out.reserve(q * sizeof(float));
-    if (!st) st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
+    rpnn_status st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
     if (!st) st = c->sample_val.reserve(q * sizeof(float));
     if (st) return st;
-    st = mlp_forward_f32(*c, dev_desc, q, nullptr, c->t_out.as<float>(), c->t_saved.as<float>(), s);
+    st = train_forward(*c, dev_desc, q, s);
     if (st) return st;
     float* dg = c->sample_val.as<float>();
     st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
     if (st) return st;
-    st = mlp_backward_f32(*c, dev_desc, q, c->t_saved.as<float>(), dg, c->t_grad.as<float>(), s);
+    st = train_backward(*c, dev_desc, q, dg, c->t_grad.as<float>(), s);
     if (st) return st;
     st = launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), RPNN_NPARAMS, step, *adam, s);
     if (st) return st;

@@ -1,0 +1,352 @@
+// gemm_tc.cu -- BF16 tensor-core GEMM of the mixed-precision training step (Sec. 5.2 with
+// BF16 operands, FP32 accumulation and FP32 master weights):
+//
+//   D = epilogue( A0 B0^T + A1 B1^T )      A_s: [M][K_s] BF16, B_s: [N][K_s] BF16 (K contiguous)
+//
+// One CTA of four warps per 128 x BN output tile (BN = 64, 128 or 256): thread 0 streams
+// both operands through a ring of shared-memory stages with 2-D TMA copies (64-byte
+// swizzled K-major boxes of 32 elements, two per operand and stage), thread 32 issues
+// four 128 x BN x 16 tcgen05 MMAs per stage into one FP32 accumulator in tensor memory,
+// and after the last stage all four warps read their 32 accumulator lanes back and apply
+// the epilogue: bias, residual, ReLU, mask, then FP32, BF16 and transposed-BF16 stores.
+// With splits > 1, CTA z takes the z-th run of the K stages and writes raw partial sums
+// to a workspace; k_tg_splitk adds them in run order and applies the epilogue.  Out-of-
+// range rows and columns of a tile are zero-filled by the copies and not stored.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+#include "tmap.h"
+
+namespace rpnn {
+
+namespace {
+
+constexpr int TGM = 128;                  // output rows per tile (one M = 128 MMA)
+constexpr int KST = 64;                   // K elements per stage: two 32-element boxes
+constexpr uint32_t ABOX = TGM * 64;       // bytes of one A box (128 rows x 64 bytes)
+constexpr int NTH = 128;
+
+struct TgEpiDev {
+    const float* bias;                    // [N] or null
+    const float* res;                     // [M][ldr] or null
+    int64_t ldr;
+    const float* mask;                    // multiply by (mask > 0): [M][ldm] or null
+    int64_t ldm;
+    int relu;
+    float* C;                             // FP32 [M][ldc] or null
+    int64_t ldc;
+    __nv_bfloat16* Cb;                    // BF16 [M][ldb] or null
+    int64_t ldb;
+    __nv_bfloat16* Ct;                    // BF16 transposed [N][ldt] or null
+    int64_t ldt;
+};
+
+struct TgArgs {
+    int M, N, K0, K1;                     // K1 = 0: one segment
+    int splits;
+    float* ws;                            // [splits][M][N] partial sums when splits > 1
+    TgEpiDev e;
+    uint32_t* status;
+};
+
+template <int BN>
+struct TgCfg {
+    static constexpr uint32_t BBOX = BN * 64;
+    static constexpr uint32_t STAGE = 2 * ABOX + 2 * BBOX;
+    static constexpr int STAGES = BN == 256 ? 3 : 4;
+    static constexpr uint32_t OFF_BAR = STAGES * STAGE;
+    static constexpr uint32_t SMEM = OFF_BAR + 256 + 1024;   // barriers, TMEM slot, alignment slack
+};
+
+__device__ __forceinline__ void tg_store(const TgEpiDev& e, int m, int n, float v) {
+    if (e.bias) v += e.bias[n];
+    if (e.res) v += e.res[(int64_t)m * e.ldr + n];
+    if (e.relu) v = fmaxf(v, 0.0f);
+    if (e.mask && !(e.mask[(int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
+    if (e.C) e.C[(int64_t)m * e.ldc + n] = v;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    if (e.Cb) e.Cb[(int64_t)m * e.ldb + n] = b;
+    if (e.Ct) e.Ct[(int64_t)n * e.ldt + m] = b;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTH, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap b0,
+          const __grid_constant__ CUtensorMap a1, const __grid_constant__ CUtensorMap b1, const TgArgs g) {
+    using C = TgCfg<BN>;
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;          // swizzle atoms want 512-byte alignment
+    unsigned char* sbase = smem_raw + (base - raw);
+    const uint32_t bar = base + C::OFF_BAR;                 // full[S], empty[S], done
+    const uint32_t done = bar + 8u * (2 * C::STAGES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + C::OFF_BAR + 8 * (2 * C::STAGES + 1));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TGM, n0 = blockIdx.x * BN;
+    const int T0 = (g.K0 + KST - 1) / KST, T = T0 + (g.K1 + KST - 1) / KST;
+    const int per = (T + g.splits - 1) / g.splits;
+    const int tb = (int)blockIdx.z * per;
+    const int nst = max(0, min(T, tb + per) - tb);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            tc::mbar_init(bar + 8u * s, 1);
+            tc::mbar_init(bar + 8u * (C::STAGES + s), 1);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tmem_slot), BN);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (nst > 0) {
+        if (threadIdx.x == 0) {                              // producer
+            for (int it = 0; it < nst; ++it) {
+                const int s = it % C::STAGES;
+                if (it >= C::STAGES &&
+                    !tc::mbar_wait(bar + 8u * (C::STAGES + s), ((it / C::STAGES) - 1) & 1, abort_flag))
+                    break;
+                const int t = tb + it;
+                const bool first = t < T0;
+                const void* am = first ? static_cast<const void*>(&a0) : static_cast<const void*>(&a1);
+                const void* bm = first ? static_cast<const void*>(&b0) : static_cast<const void*>(&b1);
+                const int k0 = (first ? t : t - T0) * KST;
+                const uint32_t st = base + (uint32_t)s * C::STAGE;
+                const uint32_t fb = bar + 8u * s;
+                tc::mbar_expect_tx(fb, C::STAGE);
+                tc::tma_load_2d(st, am, k0, m0, fb);
+                tc::tma_load_2d(st + ABOX, am, k0 + 32, m0, fb);
+                tc::tma_load_2d(st + 2 * ABOX, bm, k0, n0, fb);
+                tc::tma_load_2d(st + 2 * ABOX + C::BBOX, bm, k0 + 32, n0, fb);
+            }
+        } else if (threadIdx.x == 32) {                      // MMA issuer
+            const uint32_t idesc = tc::idesc_bf16(TGM, BN);
+            for (int it = 0; it < nst; ++it) {
+                const int s = it % C::STAGES;
+                if (!tc::mbar_wait(bar + 8u * s, (it / C::STAGES) & 1, abort_flag)) break;
+                tc::tc_fence_after();
+                const uint32_t st = base + (uint32_t)s * C::STAGE;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t ao = st + (kk >> 1) * ABOX + (kk & 1) * 32;
+                    const uint32_t bo = st + 2 * ABOX + (kk >> 1) * C::BBOX + (kk & 1) * 32;
+                    tc::mma_bf16(tmem, tc::smem_desc_sw64(ao), tc::smem_desc_sw64(bo), idesc, (it | kk) != 0);
+                }
+                tc::mma_commit(bar + 8u * (C::STAGES + s));
+            }
+            tc::mma_commit(done);
+        }
+        __syncwarp();
+        tc::mbar_wait(done, 0, abort_flag);
+        tc::tc_fence_after();
+    }
+
+    // epilogue: warp w owns accumulator lanes (tile rows) 32 w .. 32 w + 31
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN && n0 + c0 < g.N; c0 += 16) {
+        float v[16];
+        if (nst > 0) {
+            tc::tmem_ld16(trow + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+        }
+        if (row < g.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c0 + j;
+                if (n >= g.N) break;
+                if (g.splits > 1)
+                    g.ws[((int64_t)blockIdx.z * g.M + row) * g.N + n] = v[j];
+                else
+                    tg_store(g.e, row, n, v[j]);
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, BN);
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(g.status, kStatTimeout);
+}
+
+__global__ void k_tg_splitk(const float* __restrict__ ws, int splits, int M, int N, TgEpiDev e) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / N), n = (int)(i % N);
+        float v = 0.0f;
+        for (int z = 0; z < splits; ++z) v += ws[((int64_t)z * M + m) * N + n];
+        tg_store(e, m, n, v);
+    }
+}
+
+constexpr int kTgTiles[] = {64, 128, 256};
+constexpr int kTgSplits[] = {1, 2, 4, 8, 16, 32};
+constexpr int kTgMinSplitK = 1024;
+constexpr int kTgFlag = 1 << 8;             // distinguishes tensor-core shapes in the tuning table
+
+rpnn_status make_map(CUtensorMap* m, const void* p, int64_t ld, int K, int rows, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) { set_error("cuTensorMapEncodeTiled is unavailable"); return RPNN_ERR_UNSUPPORTED; }
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) != 0 || (ld * 2) % 16 != 0 || ld < K) {
+        set_error("BF16 GEMM operand must be 16-byte aligned with a row pitch of 8k elements >= K");
+        return RPNN_ERR_ARG;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(p), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return RPNN_ERR_CUDA; }
+    return RPNN_OK;
+}
+
+TgEpiDev to_dev(const TgOut& o) {
+    TgEpiDev e;
+    e.bias = o.bias; e.res = o.res; e.ldr = o.ldr; e.mask = o.mask; e.ldm = o.ldm; e.relu = o.relu;
+    e.C = o.C; e.ldc = o.ldc;
+    e.Cb = reinterpret_cast<__nv_bfloat16*>(o.Cb); e.ldb = o.ldb;
+    e.Ct = reinterpret_cast<__nv_bfloat16*>(o.Ct); e.ldt = o.ldt;
+    return e;
+}
+
+template <int BN>
+rpnn_status launch_bn(const CUtensorMap* maps, const TgArgs& a, cudaStream_t s) {
+    using C = TgCfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        attr = true;
+    }
+    dim3 grid((a.N + BN - 1) / BN, (a.M + TGM - 1) / TGM, a.splits);
+    k_tc_gemm<BN><<<grid, NTH, C::SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+// One launch (plus the split-K reduction) with tile width bn and `splits` K runs.
+rpnn_status launch_tg(Ctx& c, int bn, int splits, int M, int N, const TgSeg& s0, const TgSeg* s1,
+                      const TgEpiDev& e, float* ws, cudaStream_t s) {
+    if ((M + TGM - 1) / TGM > 65535) { set_error("BF16 GEMM with %d rows exceeds the grid limit", M); return RPNN_ERR_ARG; }
+    CUtensorMap maps[4];
+    rpnn_status st = make_map(&maps[0], s0.A, s0.lda, s0.K, M, TGM);
+    if (!st) st = make_map(&maps[1], s0.B, s0.ldb, s0.K, N, bn);
+    if (!st && s1) st = make_map(&maps[2], s1->A, s1->lda, s1->K, M, TGM);
+    if (!st && s1) st = make_map(&maps[3], s1->B, s1->ldb, s1->K, N, bn);
+    if (st) return st;
+    if (!s1) { maps[2] = maps[0]; maps[3] = maps[1]; }
+    TgArgs a;
+    a.M = M; a.N = N; a.K0 = s0.K; a.K1 = s1 ? s1->K : 0;
+    a.splits = splits; a.ws = ws; a.e = e; a.status = c.status.as<uint32_t>();
+    switch (bn) {
+        case 64: st = launch_bn<64>(maps, a, s); break;
+        case 128: st = launch_bn<128>(maps, a, s); break;
+        default: st = launch_bn<256>(maps, a, s); break;
+    }
+    if (st) return st;
+    if (splits > 1) {
+        const int64_t total = (int64_t)M * N;
+        int64_t b = (total + 255) / 256;
+        if (b > (int64_t)c.num_sms * 8) b = (int64_t)c.num_sms * 8;
+        k_tg_splitk<<<(unsigned)b, 256, 0, s>>>(ws, splits, M, N, e);
+        RPNN_CHECK_LAUNCH();
+    }
+    return RPNN_OK;
+}
+
+}  // namespace
+
+rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return RPNN_OK;
+    const TgEpiDev e = to_dev(o);
+    const int Ktot = s0.K + (s1 ? s1->K : 0);
+    int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256), splits = 1;
+    GemmTuner& tu = c.tuner;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (tu.enabled && cs == cudaStreamCaptureStatusNone) {
+        GemmKey key{M, N, s0.K, s1 ? s1->K : 0,
+                    kTgFlag | (o.bias != nullptr) << 4 | (o.res != nullptr) << 5 | (o.mask != nullptr) << 6 |
+                        (o.Cb != nullptr) << 9 | (o.Ct != nullptr) << 10};
+        const GemmChoice* hit = tu.find(key);
+        if (hit) {
+            bn = hit->tile;
+            splits = hit->splits;
+        } else {
+            // time every admissible (tile width, split) on the call's operands, writing the
+            // FP32 result into scratch only
+            struct Cand { int bn, sp; };
+            std::vector<Cand> cands;
+            int maxsplit = 1;
+            for (int t : kTgTiles) {
+                if (t > 64 && t / 2 >= N) continue;
+                const int64_t tiles = (int64_t)((N + t - 1) / t) * ((M + TGM - 1) / TGM);
+                const int stages = (s0.K + KST - 1) / KST + (s1 ? (s1->K + KST - 1) / KST : 0);
+                for (int sp : kTgSplits) {
+                    if (sp > 1 && (Ktot < kTgMinSplitK || tiles >= c.num_sms || stages / sp < 2 ||
+                                   tiles * sp > (int64_t)c.num_sms * 4))
+                        continue;
+                    cands.push_back({t, sp});
+                    maxsplit = std::max(maxsplit, sp);
+                }
+            }
+            rpnn_status st = tu.scratch.reserve((size_t)M * N * sizeof(float));
+            if (!st && maxsplit > 1) st = tu.ws.reserve((size_t)maxsplit * M * N * sizeof(float));
+            if (st) return st;
+            if (!tu.ev0) {
+                RPNN_CUDA_TRY(cudaEventCreate(&tu.ev0));
+                RPNN_CUDA_TRY(cudaEventCreate(&tu.ev1));
+            }
+            TgEpiDev es = e;
+            es.C = tu.scratch.as<float>();
+            es.ldc = N;
+            es.Cb = nullptr;
+            es.Ct = nullptr;
+            GemmChoice best{bn, 1, 1e30f, 0.0f};
+            for (const Cand& cd : cands) {
+                st = launch_tg(c, cd.bn, cd.sp, M, N, s0, s1, es, tu.ws.as<float>(), s);
+                if (st) return st;
+                RPNN_CUDA_TRY(cudaEventRecord(tu.ev0, s));
+                for (int r = 0; r < 3; ++r) {
+                    st = launch_tg(c, cd.bn, cd.sp, M, N, s0, s1, es, tu.ws.as<float>(), s);
+                    if (st) return st;
+                }
+                RPNN_CUDA_TRY(cudaEventRecord(tu.ev1, s));
+                RPNN_CUDA_TRY(cudaEventSynchronize(tu.ev1));
+                float ms = 0.0f;
+                RPNN_CUDA_TRY(cudaEventElapsedTime(&ms, tu.ev0, tu.ev1));
+                const float us = ms * 1000.0f / 3.0f;
+                if (cd.bn == bn && cd.sp == 1) best.default_us = us;
+                if (us < best.us) { best.us = us; best.tile = cd.bn; best.splits = cd.sp; }
+            }
+            tu.table.emplace_back(key, best);
+            bn = best.tile;
+            splits = best.splits;
+        }
+    }
+    float* ws = nullptr;
+    if (splits > 1) {
+        rpnn_status st = tu.ws.reserve((size_t)splits * M * N * sizeof(float));
+        if (st) return st;
+        ws = tu.ws.as<float>();
+    }
+    return launch_tg(c, bn, splits, M, N, s0, s1, e, ws, s);
+}
+
+}  // namespace rpnn

@@ -133,6 +133,8 @@ struct Ctx {
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
+    DevBuf t_w16, t_saved16, t_scr16;   // BF16 training: weight image, activation copies, gradient scratch
+    int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
@@ -199,6 +201,50 @@ rpnn_status launch_loss(const float* g, const float* target, int batch, double* 
                         float* dg, cudaStream_t s);
 rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,
                         int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s);
+
+// BF16 tensor-core GEMM (training): D = epilogue(A0 B0^T + A1 B1^T), A_s [M][K_s] and
+// B_s [N][K_s] BF16 with K contiguous (row pitches lda/ldb in elements, multiples of 8;
+// 16-byte aligned bases).  The epilogue adds bias [N] and residual, applies ReLU and the
+// mask (x * (mask > 0)), and stores any of FP32 C, BF16 Cb and transposed BF16 Ct
+// (Ct[n * ldt + m]).  Tile width and split-K are autotuned per shape like the SIMT GEMM.
+struct TgSeg {
+    const uint16_t* A;
+    int64_t lda;
+    const uint16_t* B;
+    int64_t ldb;
+    int K;
+};
+struct TgOut {
+    float* C = nullptr;
+    int64_t ldc = 0;
+    uint16_t* Cb = nullptr;
+    int64_t ldb = 0;
+    uint16_t* Ct = nullptr;
+    int64_t ldt = 0;
+    const float* bias = nullptr;
+    const float* res = nullptr;
+    int64_t ldr = 0;
+    const float* mask = nullptr;
+    int64_t ldm = 0;
+    int relu = 0;
+};
+rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s);
+
+// FP32 output layer g = relu(T3 t1 + bT3) and its backward (da3 = dout * (g > 0); dT3, dbT3
+// into dP; da2 = (da3 T3) * (t1 > 0)); bias-gradient column sums
+rpnn_status mlp_output_layer_f32(Ctx& c, const float* t1, int64_t q, float* out, cudaStream_t s);
+rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* g, const float* dout, int64_t q,
+                                          float* dP, float* da2, cudaStream_t s);
+rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s);
+
+// Mixed-precision training form (BF16 tensor-core GEMMs, FP32 master weights and
+// activations): saved FP32 slots as mlp_forward_f32, BF16 copies in s16
+// (train_bf16_saved_elems(q) elements)
+size_t train_bf16_saved_elems(int64_t q);
+rpnn_status mlp_forward_bf16_train(Ctx& c, const float* desc, int64_t q, float* out, float* saved, uint16_t* s16,
+                                   cudaStream_t s);
+rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
+                                    float* dP, cudaStream_t s);
 
 // BF16 tensor-core network
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);

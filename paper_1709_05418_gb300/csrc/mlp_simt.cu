@@ -530,6 +530,40 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
     return RPNN_OK;
 }
 
+rpnn_status mlp_output_layer_f32(Ctx& c, const float* t1, int64_t q, float* out, cudaStream_t s) {
+    const ParamLayout& L = param_layout();
+    const float* P = c.params32.as<float>();
+    const int64_t H = RPNN_H;
+    return gemm(&c, (int)q, nullptr, 1, seg(t1, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr,
+                epi(out, 1, P + L.bT[2], 1), s);
+}
+
+rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* g, const float* dout, int64_t q,
+                                          float* dP, float* da2, cudaStream_t s) {
+    const ParamLayout& L = param_layout();
+    const float* P = c.params32.as<float>();
+    const int M = (int)q;
+    const int64_t H = RPNN_H;
+    rpnn_status st = c.t_dg.reserve((size_t)q * sizeof(float));
+    if (st) return st;
+    float* da3 = c.t_dg.as<float>();
+    k_mask<<<(M + 255) / 256, 256, 0, s>>>(dout, g, M, da3);
+    RPNN_CHECK_LAUNCH();
+    st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, t1, H, 1, M), nullptr, epi(dP + L.T[2], H), s);
+    if (st) return st;
+    k_colsum<<<1, dim3(32, 32), 0, s>>>(da3, M, 1, 1, dP + L.bT[2]);
+    RPNN_CHECK_LAUNCH();
+    return gemm(&c, M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
+                epi(da2, H, nullptr, 0, nullptr, 0, t1, H), s);
+}
+
+rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s) {
+    (void)c;
+    k_colsum<<<(N + 31) / 32, dim3(32, 32), 0, s>>>(X, M, N, N, out);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
 rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss, float* dg,
                         cudaStream_t s) {
     k_loss<<<1, 1024, 0, s>>>(g, target, batch, loss, dg);

@@ -50,6 +50,7 @@
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
+#include "tmap.h"
 
 namespace rpnn {
 
@@ -709,22 +710,6 @@ ImageLayout image_layout() {
     I.scale_bytes_off = (I.w3_bytes_off + NP * 4 + 255) & ~(size_t)255;
     I.total_bytes = I.scale_bytes_off + NLAYERS * 16 + 256;
     return I;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess)
-            return (EncodeTiledFn) nullptr;
-        return (EncodeTiledFn)p;
-    }();
-    return fn;
 }
 
 // Launch of the network kernel in format F on q descriptor rows (q_dev: device count, or

@@ -1,0 +1,301 @@
+// train_bf16.cu -- mixed-precision training form of the network (Sec. 4.3 forward, Sec. 5.2
+// chain rule): every 200-wide layer and every weight gradient is a BF16 tensor-core GEMM
+// (gemm_tc.cu) with FP32 accumulation; biases, residual sums, ReLU masks, saved
+// activations, the loss, the gradients and the Adam step stay FP32 (FP32 master weights).
+// The 1-wide output layer and its gradients, which have a K or N of 1, run on the FP32
+// CUDA-core GEMM.
+//
+// Each 200-wide activation is stored three times by the epilogue of the GEMM that makes
+// it: FP32 [q][200] (residual input, ReLU mask), BF16 [q][200] (A operand of the next
+// layer and of the data gradients) and BF16 transposed [200][ldq] (operand of the weight
+// gradients, which sum over the q rows); ldq = q rounded up to 8 elements.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace rpnn {
+
+namespace {
+
+constexpr int H = RPNN_H;
+constexpr int VLD = 232;                  // row pitch of V^k in BF16 (226 rounded up to 8)
+constexpr int kMaxMats = 64;
+
+// BF16 weight image: V^k [200][232] (K-major for the forward), W1^k and W2^k [200][200]
+// and their transposes (K-major for the data gradients), T1, T2 and their transposes.
+struct TrainImage {
+    int64_t V[RPNN_K], W1[RPNN_K], W2[RPNN_K], W1T[RPNN_K], W2T[RPNN_K], T[2], TT[2];
+    int64_t total;
+};
+
+const TrainImage& train_image() {
+    static TrainImage I = [] {
+        TrainImage t{};
+        int64_t o = 0;
+        for (int k = 0; k < RPNN_K; ++k) {
+            t.V[k] = o; o += (int64_t)H * VLD;
+            t.W2[k] = o; o += (int64_t)H * H;
+            t.W2T[k] = o; o += (int64_t)H * H;
+            if (k > 0) {
+                t.W1[k] = o; o += (int64_t)H * H;
+                t.W1T[k] = o; o += (int64_t)H * H;
+            } else {
+                t.W1[k] = t.W1T[k] = -1;
+            }
+        }
+        for (int i = 0; i < 2; ++i) {
+            t.T[i] = o; o += (int64_t)H * H;
+            t.TT[i] = o; o += (int64_t)H * H;
+        }
+        t.total = o;
+        return t;
+    }();
+    return I;
+}
+
+struct MatJob {
+    int64_t src, dst;                     // offsets (floats / BF16 elements)
+    int rows, cols, ld, transpose;        // source [rows][cols]; destination pitch ld
+};
+struct MatJobs {
+    MatJob j[kMaxMats];
+    int n;
+};
+
+// blockIdx.y = matrix; destination element (r, c) of a [rows][ld] (or transposed
+// [cols][ld]) matrix, padding columns written as zero
+__global__ void k_train_image(const float* __restrict__ P, const MatJobs jobs, __nv_bfloat16* __restrict__ img) {
+    const MatJob& J = jobs.j[blockIdx.y];
+    const int drows = J.transpose ? J.cols : J.rows;
+    const int dcols = J.transpose ? J.rows : J.cols;
+    const int64_t total = (int64_t)drows * J.ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / J.ld), c = (int)(i % J.ld);
+        float v = 0.0f;
+        if (c < dcols) v = J.transpose ? P[J.src + (int64_t)c * J.cols + r] : P[J.src + (int64_t)r * J.cols + c];
+        img[J.dst + i] = __float2bfloat16_rn(v);
+    }
+}
+
+// z [q][10][240] FP32 -> zb [q][10][240] BF16 and zt [10][226][ldq] BF16 (per level, transposed)
+__global__ void k_train_desc(const float* __restrict__ z, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ zb,
+                             __nv_bfloat16* __restrict__ zt) {
+    const int64_t row = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
+    const int64_t total = q * row;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        zb[i] = __float2bfloat16_rn(z[i]);
+    // transposed copy: consecutive threads take consecutive rows m of one (level, column)
+    const int64_t ttotal = (int64_t)RPNN_K * RPNN_DIN * q;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ttotal; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i % q, lc = i / q;
+        const int k = (int)(lc / RPNN_DIN), c = (int)(lc % RPNN_DIN);
+        zt[((int64_t)k * RPNN_DIN + c) * ldq + m] = __float2bfloat16_rn(z[m * row + (int64_t)k * RPNN_DESC_STRIDE + c]);
+    }
+}
+
+// x [q][200] FP32 -> BF16 [q][200] and transposed BF16 [200][ldq]
+__global__ void k_train_act(const float* __restrict__ x, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ xb,
+                            __nv_bfloat16* __restrict__ xt) {
+    const int64_t total = q * H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i % q, n = i / q;
+        const __nv_bfloat16 b = __float2bfloat16_rn(x[m * H + n]);
+        xb[m * H + n] = b;
+        xt[n * ldq + m] = b;
+    }
+}
+
+int grid_for(int64_t n, int sms) {
+    int64_t b = (n + 255) / 256;
+    if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;
+    return (int)std::max<int64_t>(b, 1);
+}
+
+}  // namespace
+
+int64_t train_ldq(int64_t q) { return (q + 7) & ~(int64_t)7; }
+
+size_t train_bf16_saved_elems(int64_t q) {
+    // 22 activations as BF16 [q][200] and BF16 [200][ldq]; descriptors as BF16 [q][2400]
+    // and [10][226][ldq]
+    return (size_t)22 * q * H + (size_t)22 * H * train_ldq(q) + (size_t)q * RPNN_K * RPNN_DESC_STRIDE +
+           (size_t)RPNN_K * RPNN_DIN * train_ldq(q);
+}
+
+rpnn_status train_build_image(Ctx& c, cudaStream_t s) {
+    const TrainImage& I = train_image();
+    const ParamLayout& L = param_layout();
+    rpnn_status st = c.t_w16.reserve((size_t)I.total * 2);
+    if (st) return st;
+    MatJobs jobs{};
+    auto add = [&](int64_t src, int64_t dst, int rows, int cols, int ld, int tr) {
+        jobs.j[jobs.n++] = MatJob{src, dst, rows, cols, ld, tr};
+    };
+    for (int k = 0; k < RPNN_K; ++k) {
+        add(L.V[k], I.V[k], H, RPNN_DIN, VLD, 0);
+        add(L.W2[k], I.W2[k], H, H, H, 0);
+        add(L.W2[k], I.W2T[k], H, H, H, 1);
+        if (k > 0) {
+            add(L.W1[k], I.W1[k], H, H, H, 0);
+            add(L.W1[k], I.W1T[k], H, H, H, 1);
+        }
+    }
+    for (int i = 0; i < 2; ++i) {
+        add(L.T[i], I.T[i], H, H, H, 0);
+        add(L.T[i], I.TT[i], H, H, H, 1);
+    }
+    k_train_image<<<dim3(32, jobs.n), 256, 0, s>>>(c.params32.as<float>(), jobs, c.t_w16.as<__nv_bfloat16>());
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+// Forward with saved activations: FP32 slots as the FP32 form (o^1..o^10, F1^1..F1^10,
+// o^11, o^12, then g) in `saved`, BF16 copies in `s16` (train_bf16_saved_elems(q)).
+rpnn_status mlp_forward_bf16_train(Ctx& c, const float* desc, int64_t q, float* out, float* saved, uint16_t* s16,
+                                   cudaStream_t s) {
+    const ParamLayout& L = param_layout();
+    const TrainImage& I = train_image();
+    const float* P = c.params32.as<float>();
+    const int M = (int)q;
+    const int64_t ldq = train_ldq(q);
+    rpnn_status st = train_build_image(c, s);
+    if (st) return st;
+    const uint16_t* W = c.t_w16.as<uint16_t>();
+    auto slot = [&](int i) { return saved + (size_t)i * q * H; };
+    auto slotb = [&](int i) { return s16 + (size_t)i * q * H; };
+    auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
+    uint16_t* zb = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq;
+    uint16_t* zt = zb + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
+    k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
+        desc, q, ldq, reinterpret_cast<__nv_bfloat16*>(zb), reinterpret_cast<__nv_bfloat16*>(zt));
+    RPNN_CHECK_LAUNCH();
+    for (int k = 0; k < RPNN_K; ++k) {
+        // F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)
+        const TgSeg sz{zb + (size_t)k * RPNN_DESC_STRIDE, (int64_t)RPNN_K * RPNN_DESC_STRIDE, W + I.V[k], VLD, RPNN_DIN};
+        TgOut o1;
+        o1.C = slot(10 + k); o1.ldc = H;
+        o1.Cb = slotb(10 + k); o1.ldb = H;
+        o1.Ct = slott(10 + k); o1.ldt = ldq;
+        o1.bias = P + L.b1[k]; o1.relu = 1;
+        if (k > 0) {
+            const TgSeg so{slotb(k - 1), H, W + I.W1[k], H, H};
+            st = tc_gemm(c, M, H, sz, &so, o1, s);
+        } else {
+            st = tc_gemm(c, M, H, sz, nullptr, o1, s);
+        }
+        if (st) return st;
+        // o^k = relu(W2 F1 + b2 + o^{k-1})
+        const TgSeg sf{slotb(10 + k), H, W + I.W2[k], H, H};
+        TgOut o2;
+        o2.C = slot(k); o2.ldc = H;
+        o2.Cb = slotb(k); o2.ldb = H;
+        o2.Ct = slott(k); o2.ldt = ldq;
+        o2.bias = P + L.b2[k]; o2.relu = 1;
+        if (k > 0) { o2.res = slot(k - 1); o2.ldr = H; }
+        st = tc_gemm(c, M, H, sf, nullptr, o2, s);
+        if (st) return st;
+    }
+    // standard layers o^11 (slot 20), o^12 (slot 21), then the 1-wide output on CUDA cores
+    for (int t = 0; t < 2; ++t) {
+        const int in = t == 0 ? 9 : 20, outs = 20 + t;
+        const TgSeg sx{slotb(in), H, W + I.T[t], H, H};
+        TgOut o;
+        o.C = slot(outs); o.ldc = H;
+        o.Cb = slotb(outs); o.ldb = H;
+        o.Ct = slott(outs); o.ldt = ldq;
+        o.bias = P + L.bT[t]; o.relu = 1;
+        st = tc_gemm(c, M, H, sx, nullptr, o, s);
+        if (st) return st;
+    }
+    st = mlp_output_layer_f32(c, slot(21), q, out, s);
+    if (st) return st;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return RPNN_OK;
+}
+
+rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
+                                    float* dP, cudaStream_t s) {
+    const ParamLayout& L = param_layout();
+    const TrainImage& I = train_image();
+    const int M = (int)q;
+    const int64_t ldq = train_ldq(q);
+    const uint16_t* W = c.t_w16.as<uint16_t>();
+    auto slot = [&](int i) { return saved + (size_t)i * q * H; };
+    auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
+    const uint16_t* zt = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
+    rpnn_status st = c.act0.reserve((size_t)q * H * sizeof(float));
+    if (!st) st = c.act1.reserve((size_t)q * H * sizeof(float));
+    if (!st) st = c.act2.reserve((size_t)q * H * sizeof(float));
+    if (!st) st = c.t_scr16.reserve((size_t)3 * ((size_t)q * H + (size_t)H * ldq) * 2);
+    if (st) return st;
+    // three gradient buffers, each FP32 [q][200] + BF16 [q][200] + BF16 transposed [200][ldq]
+    struct Buf { float* f; uint16_t* b; uint16_t* t; };
+    uint16_t* sc = c.t_scr16.as<uint16_t>();
+    const size_t per16 = (size_t)q * H + (size_t)H * ldq;
+    Buf A{c.act0.as<float>(), sc, sc + (size_t)q * H};
+    Buf B{c.act1.as<float>(), sc + per16, sc + per16 + (size_t)q * H};
+    Buf D{c.act2.as<float>(), sc + 2 * per16, sc + 2 * per16 + (size_t)q * H};
+    auto out_to = [&](const Buf& b) {
+        TgOut o;
+        o.C = b.f; o.ldc = H;
+        o.Cb = b.b; o.ldb = H;
+        o.Ct = b.t; o.ldt = ldq;
+        return o;
+    };
+    auto wgrad = [&](const uint16_t* at, const uint16_t* bt, int N, float* dst) {
+        // dW[j][i] = sum_m a[m][j] x[m][i]: A = a^T [200][ldq], B = x^T [N][ldq], K = q
+        const TgSeg sg{at, ldq, bt, ldq, M};
+        TgOut o;
+        o.C = dst; o.ldc = N;
+        return tc_gemm(c, H, N, sg, nullptr, o, s);
+    };
+    // output layer (CUDA cores): A.f = dl/d(pre-activation of o^12 ... ) masked, dT3, dbT3
+    st = mlp_output_layer_backward_f32(c, slot(21), saved + (size_t)22 * q * H, dout, q, dP, A.f, s);
+    if (st) return st;
+    k_train_act<<<grid_for(q * H, c.num_sms), 256, 0, s>>>(A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b),
+                                                        reinterpret_cast<__nv_bfloat16*>(A.t));
+    RPNN_CHECK_LAUNCH();
+    // standard layers 2 (input o^11, slot 20) and 1 (input o^10, slot 9)
+    for (int t = 1; t >= 0; --t) {
+        const int in = t == 1 ? 20 : 9;
+        st = wgrad(A.t, slott(in), H, dP + L.T[t]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.bT[t], s);
+        if (st) return st;
+        TgOut o = out_to(B);
+        o.mask = slot(in); o.ldm = H;
+        const TgSeg sd{A.b, H, W + I.TT[t], H, H};
+        st = tc_gemm(c, M, H, sd, nullptr, o, s);
+        if (st) return st;
+        std::swap(A, B);
+    }
+    // blocks k = 10 .. 1; A = dl/d(pre-activation of o^k)
+    for (int k = RPNN_K - 1; k >= 0; --k) {
+        st = wgrad(A.t, slott(10 + k), H, dP + L.W2[k]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.b2[k], s);
+        if (st) return st;
+        // da1 = (dpre W2) * (F1 > 0)
+        TgOut o = out_to(D);
+        o.mask = slot(10 + k); o.ldm = H;
+        const TgSeg sd{A.b, H, W + I.W2T[k], H, H};
+        st = tc_gemm(c, M, H, sd, nullptr, o, s);
+        if (st) return st;
+        st = wgrad(D.t, zt + (size_t)k * RPNN_DIN * ldq, RPNN_DIN, dP + L.V[k]);
+        if (!st) st = colsum_f32(c, D.f, M, H, dP + L.b1[k], s);
+        if (st) return st;
+        if (k > 0) {
+            st = wgrad(D.t, slott(k - 1), H, dP + L.W1[k]);
+            if (st) return st;
+            // dpre_{k-1} = (dpre_k + da1 W1) * (o^{k-1} > 0)
+            TgOut o2 = out_to(B);
+            o2.res = A.f; o2.ldr = H;
+            o2.mask = slot(k - 1); o2.ldm = H;
+            const TgSeg s1{D.b, H, W + I.W1T[k], H, H};
+            st = tc_gemm(c, M, H, s1, nullptr, o2, s);
+            if (st) return st;
+            std::swap(A, B);
+        }
+    }
+    return RPNN_OK;
+}
+
+}  // namespace rpnn

@@ -1,0 +1,154 @@
+"""Mixed-precision training form (Sec. 5.2 with BF16 tensor-core GEMMs, FP32 master weights).
+
+Its parameter gradient is compared with the CPU reference of the same arithmetic
+(tests/mixed_precision_ref.py: the FP64 chain rule with each GEMM operand rounded to BF16
+where the kernels round it, pinned to the oracle in the CPU tests), at a ragged batch and at
+a batch long enough for the weight gradients to split K; its distance from the FP64
+oracle's gradient is reported.  A fit lowers the validation loss as the FP32 form's does."""
+import numpy as np
+import pytest
+
+from paper_1709_05418_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# Against the same-arithmetic reference the kernels differ in FP32 (not FP64) accumulation
+# and sums, which can move the BF16 rounding of an activation by one unit.  Where no ReLU
+# input is near zero that stays a rounding-level difference (TOL_LINEAR); at He
+# initialisation many are, and a unit moved across zero re-routes that row's gradient, so
+# two BF16 evaluations differ by a few percent (TOL_FLIPS) -- as BF16 and FP64 differ by
+# about 15 %.  Bounds are per parameter tensor, relative L2.
+TOL_LINEAR = 5e-3
+TOL_FLIPS = 5e-2
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_05418_gb300 import api
+    ctx = api.Context()
+    ctx.set_train_precision(api.BF16)
+    params = torch.from_numpy(W.he_init(seed=2)).cuda()
+    ctx.set_weights(params)
+    yield api, ctx, params
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def cloud_desc():
+    """FP32 descriptors of 333 shading points in the 64^3 blob cloud, from the oracle."""
+    import oracle
+    vol = oracle.Volume(W.blob_cloud(64, seed=1))
+    x, d = W.random_queries((64, 64, 64), 333, seed=11, margin=0.2)
+    wl = np.array([0.3, 0.5, -0.8])
+    wl /= np.linalg.norm(wl)
+    z = vol.descriptor(x.astype(np.float32), d.astype(np.float32), wl.astype(np.float32), f32=True)
+    vol.close()
+    zp = np.zeros((z.shape[0], 10, 240), np.float32)
+    zp[:, :, :226] = z
+    return zp
+
+
+def per_tensor_errors(g, ref):
+    out = {}
+    pg, pr = W.split_params(g), W.split_params(ref)
+    for name, rr in pr.items():
+        nr = np.linalg.norm(rr)
+        out[name] = float(np.linalg.norm(pg[name] - rr) / nr) if nr > 0 else float(np.linalg.norm(pg[name]))
+    return out
+
+
+def gradients(ctx, params, zz, dout):
+    import oracle
+    from mixed_precision_ref import forward_backward
+    ctx.set_weights(params)
+    g = ctx.mlp_backward(torch.from_numpy(zz).cuda(), torch.from_numpy(dout).cuda()).double().cpu().numpy()
+    ctx.sync_status()
+    assert np.isfinite(g).all()
+    p64 = params.double().cpu().numpy()
+    _, ref16 = forward_backward(p64, zz[:, :, :226], dout, bf16=True)
+    ref64 = oracle.mlp_backward(p64, zz[:, :, :226].astype(np.float64), dout.astype(np.float64))
+    return per_tensor_errors(g, ref16), per_tensor_errors(g, ref64)
+
+
+def rows_of(cloud_desc, rows):
+    reps = -(-rows // cloud_desc.shape[0])
+    return np.concatenate([cloud_desc] * reps)[:rows]
+
+
+@pytest.mark.parametrize("rows", [333, 2048])
+def test_bf16_gradient_without_relu_flips(env, cloud_desc, rows):
+    """Non-negative weights and positive biases keep every ReLU input positive, so the BF16
+    kernels and the reference take the same branches: any wrong operand, transpose, scale or
+    missing term shows above rounding level."""
+    api, ctx, params = env
+    p = params.abs() * 0.05
+    L = W.split_params(np.zeros(W.param_count()))
+    names = list(L)
+    flat = p.cpu().numpy().copy()
+    off = 0
+    for n in names:
+        size = L[n].size
+        if n.startswith("b"):
+            flat[off:off + size] = 0.01
+        off += size
+    p = torch.from_numpy(flat).cuda()
+    zz = rows_of(cloud_desc, rows)
+    dout = np.random.default_rng(3).normal(size=rows).astype(np.float32)
+    err, e64 = gradients(ctx, p, zz, dout)
+    worst = max(err, key=err.get)
+    print(f"BF16 gradient, all ReLUs active, {rows} rows: vs same-arithmetic reference worst {worst} "
+          f"{err[worst]:.2e}; vs FP64 oracle worst {max(e64.values()):.2e}")
+    assert err[worst] <= TOL_LINEAR, err
+    ctx.set_weights(params)
+
+
+@pytest.mark.parametrize("rows", [333, 2048])
+def test_bf16_gradient_at_he_init(env, cloud_desc, rows):
+    api, ctx, params = env
+    zz = rows_of(cloud_desc, rows)
+    dout = np.random.default_rng(3).normal(size=rows).astype(np.float32)
+    err, e64 = gradients(ctx, params, zz, dout)
+    worst = max(err, key=err.get)
+    print(f"BF16 gradient, He init, {rows} rows: vs same-arithmetic reference worst {worst} {err[worst]:.2e}, "
+          f"median {np.median(list(err.values())):.2e}; vs FP64 oracle median "
+          f"{np.median(list(e64.values())):.2e}, worst {max(e64.values()):.2e}")
+    assert err[worst] <= TOL_FLIPS, err
+
+
+def test_bf16_train_step_loss_matches_reference(env, cloud_desc):
+    import oracle
+    api, ctx, params = env
+    z = torch.from_numpy(cloud_desc).cuda()
+    target = torch.linspace(0.01, 0.5, z.shape[0], device="cuda")
+    p = params.clone()
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    loss = ctx.train_step(z, target, p, m, v, step=1, lr=1e-3)
+    ctx.sync_status()
+    from mixed_precision_ref import forward_backward
+    p64 = params.double().cpu().numpy()
+    g16, _ = forward_backward(p64, cloud_desc[:, :, :226], np.zeros(z.shape[0]), bf16=True)
+    ref16 = oracle.logmse_loss(g16, target.double().cpu().numpy(), want_grad=False)
+    g64 = oracle.mlp_forward(p64, cloud_desc[:, :, :226].astype(np.float64))
+    ref64 = oracle.logmse_loss(g64, target.double().cpu().numpy(), want_grad=False)
+    print(f"BF16 training loss {float(loss):.6f}; same-arithmetic reference {ref16:.6f}; FP64 oracle {ref64:.6f}")
+    assert abs(float(loss) - ref16) <= 2e-3 * ref16, (float(loss), ref16)
+    assert torch.isfinite(p).all() and not torch.equal(p, params)
+    ctx.set_weights(params)
+
+
+def test_bf16_fit_lowers_validation_loss(env):
+    from paper_1709_05418_gb300 import train
+    api, ctx, _ = env
+    clouds = train.blob_clouds(3, size=48, seed0=320)
+    desc, label = train.records(ctx, clouds, 4000, seed=21, rel_ci=0.1, n_min=32, n_max=512)
+    tr, va = train.split(desc, label)
+    params = torch.from_numpy(W.he_init(seed=5)).cuda()
+    params.mul_(0.5)
+    ctx.set_weights(params)
+    v0 = train.val_loss(ctx, *va)
+    hist = train.fit(ctx, tr, va, params, steps=300, batch=1024, lr=1e-3, eval_every=100)
+    v1 = hist[-1][2]
+    assert v1 < 0.3 * v0, (v0, hist)

@@ -150,3 +150,21 @@ def test_adam_hand_values(orc):
     mh, vh = m2 / (1 - 0.81), v2 / (1 - 0.999 ** 2)
     p_exp = np.array([1.0 - 0.1 * 0.5 / (0.5 + 1e-8), -2.0 + 0.1 / (1.0 + 1e-8), 0.5]) - 0.1 * mh / (np.sqrt(vh) + 1e-8)
     np.testing.assert_allclose(p, p_exp, rtol=1e-14)
+
+
+def test_mixed_precision_reference_without_rounding_is_the_oracle(orc):
+    """The BF16-arithmetic reference the BF16 training kernels are checked against is, with
+    its rounding switched off, the oracle's network and chain rule (so a dropped term or a
+    transposed product in it would show here); with rounding on it moves the gradient."""
+    from mixed_precision_ref import forward_backward
+    rng = np.random.default_rng(8)
+    params = W.he_init(seed=4)
+    params[W.param_count() - 1] = 0.3              # keep the output ReLU active
+    z = rng.uniform(0.0, 1.5, size=(7, 10, 226))
+    dout = rng.normal(size=7)
+    g, dp = forward_backward(params, z, dout, bf16=False)
+    assert np.allclose(g, orc.mlp_forward(params.astype(np.float64), z), rtol=1e-12, atol=1e-12)
+    ref = orc.mlp_backward(params.astype(np.float64), z, dout)
+    assert np.allclose(dp, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    _, dp16 = forward_backward(params, z, dout, bf16=True)
+    assert 1e-5 < np.linalg.norm(dp16 - ref) / np.linalg.norm(ref) < 0.5
