@@ -75,23 +75,32 @@ __device__ __forceinline__ Frame make_frame(const float d[3], const float wl[3])
 // cover cells -1 .. n-1 on each axis).
 struct LevelK {
     float s, gk;
-    uint32_t ax, ay, az;
-    uint32_t r000, sy, sz;
+    float hx, hy, hz;          // 1.5*2^23 + n - 1 per axis: the largest valid t (see lookup)
+    uint32_t rbias, sy, sz;    // record index = rbias + bits(t2) sz + bits(t1) sy + bits(t0)
 };
 
 // Trilinear lookup from one 32-byte corner record (c0, c1-c0, c2, c3-c2, c4, c5-c4, c6,
-// c7-c6).  floor(u) by a saturating round-down conversion: a cell index outside
-// [-1, n-1] (including |u| huge) reads 0, exactly as the reference clamps |u| to 1e6
-// first; the fraction is u - floor(u).  The x-lerps use the stored differences, which
+// c7-c6).  floor(u) without conversions: t = u + 1.5*2^23 rounded down is floor(u) +
+// 1.5*2^23 exactly for |u| < 2^22, and its bit pattern minus that of 1.5*2^23 is the cell
+// index; the fraction u - (t - 1.5*2^23) is u - floor(u) exactly.  The cell is inside
+// [-1, n-1] iff t lies in [1.5*2^23 - 1, 1.5*2^23 + n - 1], a test that also rejects any
+// |u| >= 2^22 (t then falls outside), so out-of-range points read 0 exactly as the
+// reference, which clamps |u| to 1e6 first.  The record index folds the bit-pattern
+// offsets into r000 (uint32 wrap-around).  The x-lerps use the stored differences, which
 // round exactly as lerp_rn's own subtraction.
+constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
+
 __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const LevelK& g, float u0, float u1,
                                         float u2) {
-    const int i0 = __float2int_rd(u0), i1 = __float2int_rd(u1), i2 = __float2int_rd(u2);
-    if ((uint32_t)(i0 + 1) > g.ax || (uint32_t)(i1 + 1) > g.ay || (uint32_t)(i2 + 1) > g.az) return 0.0f;
-    const float f0 = __fsub_rn(u0, (float)i0);
-    const float f1 = __fsub_rn(u1, (float)i1);
-    const float f2 = __fsub_rn(u2, (float)i2);
-    const uint32_t r = g.r000 + (uint32_t)i2 * g.sz + (uint32_t)i1 * g.sy + (uint32_t)i0;
+    const float t0 = __fadd_rd(u0, kFloorMagic), t1 = __fadd_rd(u1, kFloorMagic), t2 = __fadd_rd(u2, kFloorMagic);
+    if (!(t0 >= kFloorMagic - 1.0f && t0 <= g.hx && t1 >= kFloorMagic - 1.0f && t1 <= g.hy &&
+          t2 >= kFloorMagic - 1.0f && t2 <= g.hz))
+        return 0.0f;
+    const float f0 = __fsub_rn(u0, __fsub_rn(t0, kFloorMagic));
+    const float f1 = __fsub_rn(u1, __fsub_rn(t1, kFloorMagic));
+    const float f2 = __fsub_rn(u2, __fsub_rn(t2, kFloorMagic));
+    const uint32_t r = g.rbias + (uint32_t)__float_as_int(t2) * g.sz + (uint32_t)__float_as_int(t1) * g.sy +
+                       (uint32_t)__float_as_int(t0);
     float c[8];
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
@@ -120,10 +129,15 @@ __device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
     LevelK g;
     g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
     g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
-    g.ax = (uint32_t)L.ax; g.ay = (uint32_t)L.ay; g.az = (uint32_t)L.az;
+    g.hx = kFloorMagic + (float)(L.ax - 1);
+    g.hy = kFloorMagic + (float)(L.ay - 1);
+    g.hz = kFloorMagic + (float)(L.az - 1);
     g.sy = (uint32_t)(L.ax + 1);
     g.sz = (uint32_t)((L.ax + 1) * (L.ay + 1));
-    g.r000 = (uint32_t)L.rec_offset + g.sz + g.sy + 1u;
+    // cell (i0, i1, i2) is record rec_offset + (i2+1) sz + (i1+1) sy + (i0+1), and
+    // i = bits(t) - bits(1.5*2^23)
+    const uint32_t mb = (uint32_t)__float_as_int(kFloorMagic);
+    g.rbias = (uint32_t)L.rec_offset + g.sz + g.sy + 1u - mb * (g.sz + g.sy + 1u);
     return g;
 }
 

@@ -23,7 +23,9 @@ struct RenderArgs {
     int mode;   // RPNN_MODE_*
 };
 
-__global__ void __launch_bounds__(128)
+// 6 blocks of 128 threads per SM (80 registers, no spills): more rays in flight to hide the
+// latency of the density gathers
+__global__ void __launch_bounds__(128, 6)
 k_primary(const VolumeView v, const RenderArgs a, int64_t P, float* __restrict__ sample_val,
           float* __restrict__ qx, float* __restrict__ qd, uint32_t* __restrict__ qps,
           int* __restrict__ qcount, int* __restrict__ hit_out, float* __restrict__ x_out,
