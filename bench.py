@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (797.830400e6 + 5.624320e6) / 178847,
-                   "sources": {"descriptor.cu": "b520e610f8058d2b", "volume.cu": "019a6dcf787202e9"}},
+    "descriptor": {"bytes_per_query": (797.787648e6 + 5.636096e6) / 178847,
+                   "sources": {"descriptor.cu": "ff94a607ab93cba5", "volume.cu": "019a6dcf787202e9"}},
     "network": {"bytes_per_query": (886.093568e6 + 3.916800e6) / 178847,
                 "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
     "network_fp8": {"bytes_per_query": (459.987200e6 + 5.108224e6) / 178847,
@@ -451,6 +451,74 @@ def run_train(args, ws, rank, local):
     ctx.close()
 
 
+ENV_WORKLOAD = ("environment lighting: the single-cloud render (256^3 fBm, 512x512, 1 spp) under a sun and "
+                "8 sky directions (seeded, upper hemisphere) standing in for a sun-sky model; every shading "
+                "point gets one next-event estimate and one BF16 network prediction per direction")
+
+
+def run_env(args, ws, rank, local):
+    """Environment-lit render: shading queries x directions per second."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_05418_gb300 import api
+    from paper_1709_05418_gb300 import workloads as W
+    dens, cam, params = make_workload(rank, device=dev)
+    ctx = api.Context()
+    vol = ctx.load_volume(torch.from_numpy(dens).to(dev))
+    ctx.build_mips(vol)
+    ctx.set_weights(torch.from_numpy(params).to(dev))
+    sky = [W.unit_sphere_dir(500 + i) for i in range(8)]
+    dirs = np.array([cam["light_dir"]] + [s if s[1] > 0 else -s for s in sky], np.float32)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    irr = np.array([1.0] + [0.1] * 8, np.float32)
+    img, nq = ctx.render_env(vol, cam, dirs, irr, precision=api.BF16, want_count=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.render_env(vol, cam, dirs, irr, precision=api.BF16, image=img)
+    ctx.sync_status()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    barrier(ws)
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record()
+        ctx.render_env(vol, cam, dirs, irr, precision=api.BF16, image=img)
+        e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ctx.sync_status()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
+    nl = dirs.shape[0]
+    total = sum_over_ranks(float(nq) * nl * args.steps, ws, dev)
+    host = torch.empty(img.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.render_env(vol, cam, dirs, irr, precision=api.BF16, image=img)
+        host.copy_(img, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    line = {
+        "metric": "RPNN shading queries x light directions per second on 1 GB300 (environment lighting)",
+        "value": total / (ms / 1e3), "unit": "queries*directions/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": ENV_WORKLOAD, "queries_per_step": int(nq), "directions": int(nl),
+                   "l2": "flushed: 256 MB write between timed steps"},
+        "gpu_launches": (1 + 1 + 2 * nl + nl + 1) * args.steps,   # primary, env NEE, descriptor+network per light, scatters, composite
+        "e2e": {"value": total / e2e_s, "unit": "queries*directions/s", "h2d_bytes_per_step": int(dirs.nbytes + irr.nbytes),
+                "d2h_bytes_per_step": int(img.numel() * 4)},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 LARGE_WORKLOAD = ("large render: 1024^3 FP16 fBm density (seed 300, 6 octaves, 30% non-zero, peak sigma_t "
                   "50/unit), 1920x1080 at 4 spp, random light dir, descriptor/network stages in chunks of "
                   "1,048,576 queries, FP8 (E4M3, per-tensor scales) RPNN, He-init weights")
@@ -603,7 +671,7 @@ def main():
                     help="path cap of the records' stopping rule in the training workload")
     ap.add_argument("--cpu-rows", type=int, default=256,
                     help="records in the FP64 oracle's training step (training workload)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train", "env"],
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
                          "call; large: 1024^3 FP16 cloud at 1920x1080x4")
     ap.add_argument("--profile-only", action="store_true",
@@ -623,6 +691,9 @@ def main():
         return
     if args.workload == "train":
         run_train(args, ws, rank, local)
+        return
+    if args.workload == "env":
+        run_env(args, ws, rank, local)
         return
 
     import torch

@@ -198,6 +198,21 @@ enum { RPNN_MODE_RPNN = 0, RPNN_MODE_SINGLE = 1, RPNN_MODE_PATH = 2 };
  * it synchronises `stream`. */
 rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc,
                         float* dev_image, int64_t* out_num_queries, void* stream);
+/* Environment lighting (Sec. 4.4: a distant emitter such as a sun-sky model is approximated
+ * by directional samples whose predictions are summed): renders as rpnn_render with the n
+ * directional lights dirs[j] (host, [n][3], unit, towards the light) of irradiance
+ * irradiance[j] (host, [n], >= 0) in place of desc->light_dir / light_E:
+ * pixel = (1/spp) sum_s alpha sum_j E_j (p_HG(d.w_j) T_j + g(z_j)), z_j the descriptor in
+ * light j's frame.  The visible point of a sample does not depend on the lights and each
+ * light's shadow ray uses the stream a single-light render with that light uses, so the
+ * result is the sum of the n single-light renders (up to FP32 summation order).
+ * desc->mode: RPNN_MODE_RPNN or RPNN_MODE_SINGLE.  The descriptor and network stages run
+ * once per light.  Errors: RPNN_ERR_ARG for n outside 1..RPNN_MAX_ENV_LIGHTS, a non-unit
+ * direction, a negative or non-finite irradiance, or path mode; otherwise as rpnn_render. */
+#define RPNN_MAX_ENV_LIGHTS 1024
+rpnn_status rpnn_render_env(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, const float* dirs,
+                            const float* irradiance, int32_t n, float* dev_image, int64_t* out_num_queries,
+                            void* stream);
 /* Memory budget of rpnn_render (no counterpart in the paper): the descriptor and network
  * stages run over chunks of at most `rows` shading points (0 = the default 1,048,576
  * rows, i.e. 5 GB of BF16 descriptors; otherwise at least 128).  Results do not depend on

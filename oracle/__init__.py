@@ -331,6 +331,19 @@ class Volume:
             raise RuntimeError(f"oracle render failed ({r})")
         return out
 
+    def render_pixels_env(self, cam: dict, pixels, dirs, irradiance, params=None, mode=0, nthreads=None):
+        """Environment lighting (Sec. 4.4): the distant emitter is a set of directional
+        lights (dirs[j] towards the light, irradiance E_j), and a pixel sums each light's
+        direct in-scattering and predicted indirect in-scattering over the lights.  The
+        visible point does not depend on the light and each light's shadow ray draws the
+        same stream, so the sum is taken over single-light renders, in light order."""
+        out = None
+        for w, e in zip(np.asarray(dirs, np.float64), np.asarray(irradiance, np.float64)):
+            cj = dict(cam, light_dir=tuple(float(v) for v in w), light_E=float(e))
+            r = self.render_pixels(cj, pixels, params=params, mode=mode, nthreads=nthreads)
+            out = r if out is None else out + r
+        return out
+
     def gen_record(self, seed, rec, rel_ci=0.02, n_min=64, n_max=65536):
         x = np.zeros(3); d = np.zeros(3); wl = np.zeros(3); lab = np.zeros(1); hw = np.zeros(1)
         n = C.c_int64(0)

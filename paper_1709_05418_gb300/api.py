@@ -97,6 +97,8 @@ def load():
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
             "rpnn_render": [_vp, i32, C.POINTER(RenderDesc), _vp, C.POINTER(i64), _vp],
             "rpnn_render_batch": [_vp, C.POINTER(BatchItem), i32, C.POINTER(i64), _vp],
+            "rpnn_render_env": [_vp, i32, C.POINTER(RenderDesc), C.POINTER(f32), C.POINTER(f32), i32, _vp,
+                                C.POINTER(i64), _vp],
             "rpnn_set_render_chunk": [_vp, i64],
             "rpnn_calibrate_fp8": [_vp, _vp, i64, _vp],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
@@ -294,6 +296,24 @@ class Context:
         nq = C.c_int64(-1)
         self._check(self.L.rpnn_render(self.h, vol, C.byref(rd), _ptr(image),
                                        C.byref(nq) if want_count else None, _stream()))
+        return (image, nq.value) if want_count else image
+
+    def render_env(self, vol, cam: dict, dirs, irradiance, precision=F32, mode=MODE_RPNN, image=None,
+                   want_count=False):
+        """Render under n directional lights (dirs [n][3] unit, towards the light; irradiance
+        [n]) approximating an environment emitter."""
+        import numpy as np
+        dirs = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 3)
+        irr = np.ascontiguousarray(irradiance, dtype=np.float32).reshape(-1)
+        assert dirs.shape[0] == irr.shape[0]
+        rd = self.render_desc(cam, precision, mode)
+        if image is None:
+            image = torch.empty((cam["height"], cam["width"]), dtype=torch.float32, device="cuda")
+        nq = C.c_int64(-1)
+        fp = C.POINTER(C.c_float)
+        self._check(self.L.rpnn_render_env(self.h, vol, C.byref(rd), dirs.ctypes.data_as(fp),
+                                           irr.ctypes.data_as(fp), dirs.shape[0], _ptr(image),
+                                           C.byref(nq) if want_count else None, _stream()))
         return (image, nq.value) if want_count else image
 
     def set_render_chunk(self, rows: int):

@@ -320,10 +320,11 @@ rpnn_status rpnn_trace_primary(rpnn_ctx* ctx, int32_t vol, const rpnn_render_des
                           dev_x, dev_d, dev_Ld, (cudaStream_t)stream);
 }
 
-rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, float* dev_image,
-                        int64_t* out_num_queries, void* stream) {
-    CHECK_CTX(ctx);
-    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+// One render: the camera and light of `desc`, or (n_env > 0) the n_env directional lights
+// env_dir [n][3] / env_E [n] (host) in place of desc's light (environment lighting).
+static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc, const float* env_dir,
+                               const float* env_E, int n_env, float* dev_image, int64_t* out_num_queries,
+                               cudaStream_t s) {
     Volume* v = get_vol(c, vol, true);
     if (!v) return RPNN_ERR_HANDLE;
     rpnn_status st = check_desc(desc);
@@ -335,7 +336,16 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         set_error("FP8 render: rpnn_calibrate_fp8 has not run since the weights were set");
         return RPNN_ERR_STATE;
     }
-    cudaStream_t s = (cudaStream_t)stream;
+    // the lights: desc's one, or the environment's directions
+    const int nl = n_env > 0 ? n_env : 1;
+    std::vector<float> lights(4 * (size_t)nl);
+    for (int j = 0; j < nl; ++j)
+        for (int a = 0; a < 3; ++a) lights[3 * j + a] = n_env > 0 ? env_dir[3 * j + a] : desc->light_dir[a];
+    for (int j = 0; j < nl; ++j) lights[3 * nl + j] = n_env > 0 ? env_E[j] : desc->light_E;
+    rpnn_render_desc rd0 = *desc;                   // the primary pass carries light 0
+    for (int a = 0; a < 3; ++a) rd0.light_dir[a] = lights[a];
+    rd0.light_E = lights[3 * nl];
+    const bool queries = net || nl > 1;             // shading points are listed for the network or extra lights
     const int64_t P = (int64_t)desc->width * desc->height * desc->spp;
     const bool f32 = desc->precision == RPNN_F32;
     const bool fp8 = desc->precision == RPNN_FP8E4M3;
@@ -346,10 +356,13 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
     const int nchunks = (int)((P + CH - 1) / CH);
     st = c->sample_val.reserve(P * sizeof(float));
     if (!st) st = c->q_count.reserve((1 + nchunks) * sizeof(int));
-    if (net) {
+    if (!st) st = c->light.reserve(lights.size() * sizeof(float));
+    if (queries) {
         if (!st) st = c->q_x.reserve(P * 3 * sizeof(float));
         if (!st) st = c->q_d.reserve(P * 3 * sizeof(float));
         if (!st) st = c->q_ps.reserve(P * sizeof(uint32_t));
+    }
+    if (net) {
         if (!st) st = c->g_out.reserve(P * sizeof(float));
         if (!st) st = c->desc.reserve((size_t)CH * desc_row_bytes);
         if (!st) st = ensure_rows(c, CH, f32);
@@ -370,44 +383,59 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         ++c->prof_used;
         RPNN_CUDA_TRY(cudaEventRecord(ev[0], s));
     }
+    // light directions (device, [nl][3]) then irradiances ([nl]), read by the descriptor
+    // and environment next-event kernels
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c->light.p, lights.data(), lights.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    const float* ldir = c->light.as<float>();
     RPNN_CUDA_TRY(cudaMemsetAsync(qc, 0, sizeof(int), s));
-    st = launch_primary(*c, vv, *desc, c->sample_val.as<float>(), net ? c->q_x.as<float>() : nullptr,
-                        net ? c->q_d.as<float>() : nullptr, net ? c->q_ps.as<uint32_t>() : nullptr,
-                        net ? qc : nullptr, nullptr, nullptr, nullptr, nullptr, s);
+    st = launch_primary(*c, vv, rd0, c->sample_val.as<float>(), queries ? c->q_x.as<float>() : nullptr,
+                        queries ? c->q_d.as<float>() : nullptr, queries ? c->q_ps.as<uint32_t>() : nullptr,
+                        queries ? qc : nullptr, nullptr, nullptr, nullptr, nullptr, s);
     if (st) return st;
+    if (nl > 1) {
+        st = launch_nee_env(*c, vv, rd0, c->q_x.as<float>(), c->q_d.as<float>(), c->q_ps.as<uint32_t>(), qc, P, ldir,
+                            ldir + 3 * nl, 1, nl, c->sample_val.as<float>(), s);
+        if (st) return st;
+    }
     if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[1], s));
     if (!net && ev) {
         RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
         RPNN_CUDA_TRY(cudaEventRecord(ev[3], s));
     }
     if (net) {
-        // one light direction for the whole render, read by the descriptor kernel
-        st = c->light.reserve(4 * sizeof(float));
-        if (st) return st;
-        RPNN_CUDA_TRY(cudaMemcpyAsync(c->light.p, desc->light_dir, 3 * sizeof(float),
-                                      cudaMemcpyHostToDevice, s));
         // per-chunk query counts (device): clamp(count - i*CH, 0, CH)
         if (nchunks > 1) {
             st = launch_chunk_counts(*c, qc, CH, nchunks, qc + 1, s);
             if (st) return st;
         }
-        for (int i = 0; i < nchunks; ++i) {
-            const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
-            const int64_t first = (int64_t)i * CH;
-            st = launch_descriptor(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
-                                   c->light.as<float>(), 0, CH, cnt, c->desc.p,
-                                   f32 ? RPNN_F32 : (fp8 ? RPNN_FP8E4M3 : RPNN_BF16), s);
-            if (st) return st;
-            // (a chunked render attributes its network time to the descriptor stage)
-            if (ev && i == nchunks - 1) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
-            if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), CH, cnt, c->g_out.as<float>() + first, nullptr, s);
-            else if (fp8) st = mlp_forward_fp8(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
-            else st = mlp_forward_bf16(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
-            if (st) return st;
+        for (int j = 0; j < nl; ++j) {
+            for (int i = 0; i < nchunks; ++i) {
+                const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
+                const int64_t first = (int64_t)i * CH;
+                st = launch_descriptor(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
+                                       ldir + 3 * j, 0, CH, cnt, c->desc.p,
+                                       f32 ? RPNN_F32 : (fp8 ? RPNN_FP8E4M3 : RPNN_BF16), s);
+                if (st) return st;
+                // (a chunked render attributes its network time to the descriptor stage)
+                if (ev && j == nl - 1 && i == nchunks - 1) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
+                if (f32) st = mlp_forward_f32(*c, c->desc.as<float>(), CH, cnt, c->g_out.as<float>() + first, nullptr, s);
+                else if (fp8) st = mlp_forward_fp8(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
+                else st = mlp_forward_bf16(*c, c->desc.p, CH, cnt, c->g_out.as<float>() + first, s);
+                if (st) return st;
+            }
+            // light j's predictions, weighted by albedo * E_j (the last light's scatter runs
+            // with the composite below)
+            if (j < nl - 1) {
+                st = launch_scatter(*c, v->albedo * lights[3 * nl + j], c->g_out.as<float>(), c->q_ps.as<uint32_t>(),
+                                    qc, c->sample_val.as<float>(), s);
+                if (st) return st;
+            }
         }
         if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[3], s));
     }
-    st = launch_scatter_composite(*c, *desc, v->albedo, net ? c->g_out.as<float>() : nullptr,
+    rpnn_render_desc rdl = *desc;                   // the composite's scatter carries the last light
+    rdl.light_E = lights[3 * nl + nl - 1];
+    st = launch_scatter_composite(*c, rdl, v->albedo, net ? c->g_out.as<float>() : nullptr,
                                   net ? c->q_ps.as<uint32_t>() : nullptr, qc, c->sample_val.as<float>(),
                                   dev_image, net, s);
     if (st) return st;
@@ -419,6 +447,32 @@ rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc
         *out_num_queries = net ? h : -1;
     }
     return RPNN_OK;
+}
+
+rpnn_status rpnn_render(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, float* dev_image,
+                        int64_t* out_num_queries, void* stream) {
+    CHECK_CTX(ctx);
+    return render_impl(reinterpret_cast<Ctx*>(ctx), vol, desc, nullptr, nullptr, 0, dev_image, out_num_queries,
+                       (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_render_env(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* desc, const float* dirs,
+                            const float* irradiance, int32_t n, float* dev_image, int64_t* out_num_queries,
+                            void* stream) {
+    CHECK_CTX(ctx);
+    if (n < 1 || n > RPNN_MAX_ENV_LIGHTS || !dirs || !irradiance) {
+        set_error("environment needs 1..%d directions and irradiances", RPNN_MAX_ENV_LIGHTS);
+        return RPNN_ERR_ARG;
+    }
+    if (desc && desc->mode == RPNN_MODE_PATH) { set_error("environment lighting renders RPNN or SINGLE mode"); return RPNN_ERR_ARG; }
+    for (int j = 0; j < n; ++j) {
+        const float* w = dirs + 3 * j;
+        const float l2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        if (!(fabsf(l2 - 1.0f) < 1e-4f)) { set_error("direction %d is not unit length", j); return RPNN_ERR_ARG; }
+        if (!(irradiance[j] >= 0.0f) || !std::isfinite(irradiance[j])) { set_error("irradiance %d is negative or not finite", j); return RPNN_ERR_ARG; }
+    }
+    return render_impl(reinterpret_cast<Ctx*>(ctx), vol, desc, dirs, irradiance, n, dev_image, out_num_queries,
+                       (cudaStream_t)stream);
 }
 
 rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {

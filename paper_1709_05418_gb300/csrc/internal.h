@@ -178,6 +178,14 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
                                      float* sample_val, float* image, bool with_g,
                                      cudaStream_t s, const int* g_off = nullptr,
                                      const int* g_total = nullptr);
+// Environment lighting: next-event estimates towards lights j0..n-1 (device dirs [n][3],
+// irradiances E [n]) of the *qcount (<= max_q) shading points, added to their samples.
+rpnn_status launch_nee_env(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd, const float* qx,
+                           const float* qd, const uint32_t* qps, const int* qcount, int64_t max_q, const float* dirs,
+                           const float* E, int j0, int n, float* sample_val, cudaStream_t s);
+// sample_val[qps[i]] += scale * g[i] for i < *qcount
+rpnn_status launch_scatter(Ctx& c, float scale, const float* g, const uint32_t* qps, const int* qcount,
+                           float* sample_val, cudaStream_t s);
 // Rows per descriptor/network chunk of a render.
 constexpr int64_t kChunkRows = (int64_t)1 << 20;
 // out[i] = clamp(*count - i*rows, 0, rows) for i < n

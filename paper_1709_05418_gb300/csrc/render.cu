@@ -98,6 +98,32 @@ __global__ void k_scatter(const float* __restrict__ g, const uint32_t* __restric
         sample_val[qps[i]] += scale * g[o + i];
 }
 
+// Environment lighting (Sec. 4.4: a distant emitter approximated by directional samples):
+// for every shading point i and every light j >= j0, the next-event estimate towards
+// direction j with irradiance E_j, added to the point's sample value times the albedo.
+// Each direction restarts the point's shadow stream (pixel, sample, shadow domain) at draw
+// 0, so direction j's estimate is the one a single-light render with light j makes.
+__global__ void __launch_bounds__(128)
+k_nee_env(const VolumeView v, const RenderArgs a, const float* __restrict__ qx, const float* __restrict__ qd,
+          const uint32_t* __restrict__ qps, const int* __restrict__ qcount, const float* __restrict__ dirs,
+          const float* __restrict__ E, int j0, int n, float* __restrict__ sample_val, uint32_t* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *qcount) return;
+    const uint32_t ps = qps[i];
+    const uint32_t pixel = ps / (uint32_t)a.spp, s = ps % (uint32_t)a.spp;
+    const float3 x = f3(qx[3 * i], qx[3 * i + 1], qx[3 * i + 2]);
+    const float3 d = f3(qd[3 * i], qd[3 * i + 1], qd[3 * i + 2]);
+    const Rng rng = make_rng(a.seed, pixel, s, kDomShadow);
+    bool capped = false;
+    float Ld = 0.0f;
+    for (int j = j0; j < n; ++j) {
+        uint32_t ctr = 0;
+        Ld += nee(v, x, d, f3(dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]), E[j], rng, ctr, capped);
+    }
+    if (capped) raise_status(status, kStatIterLimit);
+    sample_val[ps] += v.albedo * Ld;
+}
+
 // pixel = mean over its spp samples, summed in sample order
 __global__ void k_composite(const float* __restrict__ sample_val, int64_t npix, int spp,
                             float* __restrict__ image) {
@@ -216,6 +242,23 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
     int64_t b = (npix + 255) / 256;
     if (b > c.num_sms * 16) b = c.num_sms * 16;
     k_composite<<<(unsigned)b, 256, 0, s>>>(sample_val, npix, rd.spp, image);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_nee_env(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd, const float* qx,
+                           const float* qd, const uint32_t* qps, const int* qcount, int64_t max_q, const float* dirs,
+                           const float* E, int j0, int n, float* sample_val, cudaStream_t s) {
+    if (max_q <= 0 || j0 >= n) return RPNN_OK;
+    k_nee_env<<<(unsigned)((max_q + 127) / 128), 128, 0, s>>>(vv, make_args(rd), qx, qd, qps, qcount, dirs, E, j0, n,
+                                                                sample_val, c.status.as<uint32_t>());
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_scatter(Ctx& c, float scale, const float* g, const uint32_t* qps, const int* qcount,
+                           float* sample_val, cudaStream_t s) {
+    k_scatter<<<c.num_sms * 8, 256, 0, s>>>(g, qps, qcount, nullptr, nullptr, scale, sample_val);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }

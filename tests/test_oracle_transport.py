@@ -120,3 +120,30 @@ def test_primary_sample_is_consistent(orc):
             assert 0 <= Ld <= 2.0 * orc.hg(0.85, float(np.dot(d, cam["light_dir"]))) + 1e-15
         else:
             assert pix[p] == 0.0
+
+
+def test_environment_render_is_the_superposition_of_its_lights(orc):
+    """Sec. 4.4's environment emitter as directional samples: one light reproduces the
+    single-light render, a light split into two halves of its irradiance gives the same
+    image, and the image is linear in the irradiances (single scattering and a network
+    prediction alike scale with E)."""
+    from paper_1709_05418_gb300 import workloads as W
+    vol = orc.Volume(W.blob_cloud(24, nblobs=4, seed=3))
+    cam = W.camera((24, 24, 24), 12, 10, spp=2, seed=8, light_seed=9)
+    params = W.he_init(seed=2, K_=10).astype(np.float64)
+    pix = np.arange(120)
+    w0 = np.asarray(cam["light_dir"], np.float64)
+    w1 = np.array([0.0, 0.6, 0.8])
+    single = vol.render_pixels(cam, pix, params=params)
+    assert np.count_nonzero(single) > 20
+    one = vol.render_pixels_env(cam, pix, [w0], [1.0], params=params)
+    assert np.array_equal(one, single)
+    halves = vol.render_pixels_env(cam, pix, [w0, w0], [0.5, 0.5], params=params)
+    assert np.allclose(halves, single, rtol=1e-12, atol=1e-15)
+    a = vol.render_pixels_env(cam, pix, [w0, w1], [1.0, 2.0], params=params)
+    b = vol.render_pixels_env(cam, pix, [w0, w1], [3.0, 6.0], params=params)
+    assert np.allclose(b, 3.0 * a, rtol=1e-12, atol=1e-15)
+    second = vol.render_pixels(dict(cam, light_dir=tuple(w1), light_E=2.0), pix, params=params)
+    assert np.allclose(a, single + second, rtol=1e-12, atol=1e-15)
+    assert not np.allclose(a, single)
+    vol.close()
