@@ -3,7 +3,7 @@
 //
 //   D = epilogue( A0 B0^T + A1 B1^T )      A_s: [M][K_s] BF16, B_s: [N][K_s] BF16 (K contiguous)
 //
-// One CTA of four warps per 128 x BN output tile (BN = 64, 128 or 256): thread 0 streams
+// One CTA of four warps per 128 x BN output tile (BN = 32, 64, 128 or 256): thread 0 streams
 // both operands through a ring of shared-memory stages with 2-D TMA copies (64-byte
 // swizzled K-major boxes of 32 elements, two per operand and stage), thread 32 issues
 // four 128 x BN x 16 tcgen05 MMAs per stage into one FP32 accumulator in tensor memory,
@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -59,6 +60,7 @@ struct TgCfg {
     static constexpr uint32_t BBOX = BN * 64;
     static constexpr uint32_t STAGE = 2 * ABOX + 2 * BBOX;
     static constexpr int STAGES = BN == 256 ? 3 : 4;
+    static_assert(4 * 32 * 17 * 4 <= STAGES * STAGE, "epilogue tiles reuse the stage ring");
     static constexpr uint32_t OFF_BAR = STAGES * STAGE;
     static constexpr uint32_t SMEM = OFF_BAR + 256 + 1024;   // barriers, TMEM slot, alignment slack
 };
@@ -154,8 +156,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtens
         tc::tc_fence_after();
     }
 
-    // epilogue: warp w owns accumulator lanes (tile rows) 32 w .. 32 w + 31
-    const int row = m0 + warp * 32 + lane;
+    // epilogue: warp w owns accumulator lanes (tile rows) 32 w .. 32 w + 31.  Each 32 x 16
+    // chunk goes through a per-warp shared tile (the stage ring is idle once the MMAs are
+    // done): a row-major pass (half a warp per row, 16 consecutive columns) applies bias,
+    // residual, ReLU and mask and makes the FP32 / BF16 / split-K stores coalesced; a
+    // column pass (one lane per row) makes the transposed BF16 store coalesced.
+    float* stile = reinterpret_cast<float*>(sbase) + warp * (32 * 17);
+    const int row0 = m0 + warp * 32, row = row0 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < BN && n0 + c0 < g.N; c0 += 16) {
         float v[16];
@@ -165,17 +172,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtens
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = 0.0f;
         }
-        if (row < g.M) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c0 + j;
-                if (n >= g.N) break;
-                if (g.splits > 1)
-                    g.ws[((int64_t)blockIdx.z * g.M + row) * g.N + n] = v[j];
-                else
-                    tg_store(g.e, row, n, v[j]);
+        for (int j = 0; j < 16; ++j) stile[lane * 17 + j] = v[j];
+        __syncwarp();
+        const int j = lane & 15, n = n0 + c0 + j;
+        const bool ncol = n < g.N;
+        if (g.splits > 1) {
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+                const int rr = 2 * it + (lane >> 4), m = row0 + rr;
+                if (m < g.M && ncol) g.ws[((int64_t)blockIdx.z * g.M + m) * g.N + n] = stile[rr * 17 + j];
+            }
+        } else {
+            // all of the chunk's residual and mask loads first (independent, in flight together)
+            float rv[16], mv[16];
+            const float bias = (g.e.bias && ncol) ? g.e.bias[n] : 0.0f;
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+                const int m = row0 + 2 * it + (lane >> 4);
+                const bool in = m < g.M && ncol;
+                rv[it] = (g.e.res && in) ? g.e.res[(int64_t)m * g.e.ldr + n] : 0.0f;
+                mv[it] = (g.e.mask && in) ? g.e.mask[(int64_t)m * g.e.ldm + n] : 1.0f;
+            }
+#pragma unroll
+            for (int it = 0; it < 16; ++it) {
+                const int rr = 2 * it + (lane >> 4), m = row0 + rr;
+                if (m < g.M && ncol) {
+                    float x = stile[rr * 17 + j];
+                    if (g.e.bias) x += bias;
+                    if (g.e.res) x += rv[it];
+                    if (g.e.relu) x = fmaxf(x, 0.0f);
+                    if (g.e.mask && !(mv[it] > 0.0f)) x = 0.0f;
+                    if (g.e.C) g.e.C[(int64_t)m * g.e.ldc + n] = x;
+                    if (g.e.Cb) g.e.Cb[(int64_t)m * g.e.ldb + n] = __float2bfloat16_rn(x);
+                    stile[rr * 17 + j] = x;
+                }
             }
         }
+        if (g.splits == 1 && g.e.Ct) {
+            __syncwarp();
+            if (row < g.M) {
+                for (int jj = 0; jj < 16 && n0 + c0 + jj < g.N; ++jj)
+                    g.e.Ct[(int64_t)(n0 + c0 + jj) * g.e.ldt + row] = __float2bfloat16_rn(stile[lane * 17 + jj]);
+            }
+        }
+        __syncwarp();
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -194,12 +235,19 @@ __global__ void k_tg_splitk(const float* __restrict__ ws, int splits, int M, int
     }
 }
 
-constexpr int kTgTiles[] = {64, 128, 256};
+constexpr int kTgTiles[] = {32, 64, 128, 256};
 constexpr int kTgSplits[] = {1, 2, 4, 8, 16, 32};
 constexpr int kTgMinSplitK = 1024;
 constexpr int kTgFlag = 1 << 8;             // distinguishes tensor-core shapes in the tuning table
 
-rpnn_status make_map(CUtensorMap* m, const void* p, int64_t ld, int K, int rows, int box_rows) {
+rpnn_status make_map(Ctx& c, CUtensorMap* m, const void* p, int64_t ld, int K, int rows, int box_rows) {
+    static_assert(sizeof(CUtensorMap) == sizeof(TmapBytes), "tensor map size");
+    const TmapKey key{p, ld, K, rows, box_rows};
+    const auto it = c.tmaps.find(key);
+    if (it != c.tmaps.end()) {
+        memcpy(m, it->second.b, sizeof(CUtensorMap));
+        return RPNN_OK;
+    }
     EncodeTiledFn enc = encode_fn();
     if (!enc) { set_error("cuTensorMapEncodeTiled is unavailable"); return RPNN_ERR_UNSUPPORTED; }
     if ((reinterpret_cast<uintptr_t>(p) & 15u) != 0 || (ld * 2) % 16 != 0 || ld < K) {
@@ -214,6 +262,10 @@ rpnn_status make_map(CUtensorMap* m, const void* p, int64_t ld, int K, int rows,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return RPNN_ERR_CUDA; }
+    if (c.tmaps.size() > 4096) c.tmaps.clear();
+    TmapBytes tb;
+    memcpy(tb.b, m, sizeof(CUtensorMap));
+    c.tmaps.emplace(key, tb);
     return RPNN_OK;
 }
 
@@ -245,16 +297,17 @@ rpnn_status launch_tg(Ctx& c, int bn, int splits, int M, int N, const TgSeg& s0,
                       const TgEpiDev& e, float* ws, cudaStream_t s) {
     if ((M + TGM - 1) / TGM > 65535) { set_error("BF16 GEMM with %d rows exceeds the grid limit", M); return RPNN_ERR_ARG; }
     CUtensorMap maps[4];
-    rpnn_status st = make_map(&maps[0], s0.A, s0.lda, s0.K, M, TGM);
-    if (!st) st = make_map(&maps[1], s0.B, s0.ldb, s0.K, N, bn);
-    if (!st && s1) st = make_map(&maps[2], s1->A, s1->lda, s1->K, M, TGM);
-    if (!st && s1) st = make_map(&maps[3], s1->B, s1->ldb, s1->K, N, bn);
+    rpnn_status st = make_map(c, &maps[0], s0.A, s0.lda, s0.K, M, TGM);
+    if (!st) st = make_map(c, &maps[1], s0.B, s0.ldb, s0.K, N, bn);
+    if (!st && s1) st = make_map(c, &maps[2], s1->A, s1->lda, s1->K, M, TGM);
+    if (!st && s1) st = make_map(c, &maps[3], s1->B, s1->ldb, s1->K, N, bn);
     if (st) return st;
     if (!s1) { maps[2] = maps[0]; maps[3] = maps[1]; }
     TgArgs a;
     a.M = M; a.N = N; a.K0 = s0.K; a.K1 = s1 ? s1->K : 0;
     a.splits = splits; a.ws = ws; a.e = e; a.status = c.status.as<uint32_t>();
     switch (bn) {
+        case 32: st = launch_bn<32>(maps, a, s); break;
         case 64: st = launch_bn<64>(maps, a, s); break;
         case 128: st = launch_bn<128>(maps, a, s); break;
         default: st = launch_bn<256>(maps, a, s); break;
@@ -295,7 +348,7 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
             std::vector<Cand> cands;
             int maxsplit = 1;
             for (int t : kTgTiles) {
-                if (t > 64 && t / 2 >= N) continue;
+                if (t > 32 && t / 2 >= N) continue;
                 const int64_t tiles = (int64_t)((N + t - 1) / t) * ((M + TGM - 1) / TGM);
                 const int stages = (s0.K + KST - 1) / KST + (s1 ? (s1->K + KST - 1) / KST : 0);
                 for (int sp : kTgSplits) {

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rpnn.h"
@@ -100,6 +101,29 @@ struct GemmTuner {
     }
 };
 
+// Encoded 2-D tensor maps of BF16 GEMM operands, by what they encode (base address, row
+// pitch, inner size, rows, box rows): a pure function of the key, so entries never go stale.
+struct TmapKey {
+    const void* p;
+    int64_t ld;
+    int K, rows, box;
+    bool operator==(const TmapKey& o) const {
+        return p == o.p && ld == o.ld && K == o.K && rows == o.rows && box == o.box;
+    }
+};
+struct TmapKeyHash {
+    size_t operator()(const TmapKey& k) const {
+        size_t h = std::hash<const void*>()(k.p);
+        h = h * 1000003u ^ (size_t)k.ld;
+        h = h * 1000003u ^ (size_t)k.K;
+        h = h * 1000003u ^ (size_t)k.rows;
+        return h * 1000003u ^ (size_t)k.box;
+    }
+};
+struct alignas(64) TmapBytes {
+    unsigned char b[128];
+};
+
 // One item of a batched render as the batched descriptor kernel reads it: the item's
 // volume, the offset of its region in the per-pixel-sample query buffers, its light.
 struct BatchItemDev {
@@ -136,6 +160,7 @@ struct Ctx {
     DevBuf t_w16, t_saved16, t_scr16;   // BF16 training: weight image, activation copies, gradient scratch
     int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
+    std::unordered_map<TmapKey, TmapBytes, TmapKeyHash> tmaps;   // BF16 GEMM operand maps
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
