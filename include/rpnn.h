@@ -266,7 +266,8 @@ rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t 
                              float* dev_d, float* dev_wl, float* dev_label,
                              int32_t* dev_npaths, void* stream);
 /* Gradient of sum_i dout_i * g(z_i) w.r.t. the parameters currently set by
- * rpnn_set_weights (FP32 CUDA-core chain rule), written (not accumulated) to
+ * rpnn_set_weights (the chain rule in the training precision, rpnn_set_train_precision:
+ * FP32 CUDA cores by default, or BF16 tensor-core GEMMs), written (not accumulated) to
  * dev_dparams (RPNN_NPARAMS floats).  dev_desc: q rows, FP32. */
 rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q,
                               const float* dev_dout, float* dev_dparams, void* stream);

@@ -47,3 +47,19 @@ def test_library_loads_and_resolves(libpath):
     # argument checks that need no device
     L.rpnn_create.argtypes = [ctypes.c_void_p]
     assert L.rpnn_create(None) == -1
+
+
+def test_argument_checks_without_a_device(libpath):
+    """Entry points reject a null context before touching the device."""
+    import torch  # noqa: F401
+    L = ctypes.CDLL(libpath)
+    L.rpnn_set_train_precision.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.rpnn_set_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.rpnn_get_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    L.rpnn_render_env.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+    for rc in (L.rpnn_set_train_precision(None, 2), L.rpnn_set_autotune(None, 1),
+               L.rpnn_get_autotune(None, None, 0, None),
+               L.rpnn_render_env(None, 0, None, None, None, 1, None, None, None)):
+        assert rc == -2    # RPNN_ERR_HANDLE
