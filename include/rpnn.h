@@ -100,6 +100,7 @@ typedef struct {
     float inv_mean_f;          /* (float)(1/mean) = one mean free path in world units */
     float majorant;            /* max voxel value */
     int64_t nonzero;           /* voxels > 0 */
+    int32_t bricks[3];         /* tracking majorant bricks per axis: ceil(n / 8) */
 } rpnn_volume_info;
 /* Host copy of the statistics (valid after rpnn_build_mips). */
 rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* out);
@@ -107,6 +108,11 @@ rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* o
  * if the stencil does not use it). */
 rpnn_status rpnn_copy_mip_level(rpnn_ctx* ctx, int32_t vol, int32_t level, float* dev_out,
                                 void* stream);
+/* Writes the tracking majorant grid as FP32 [bricks[2]][bricks[1]][bricks[0]] into dev_out:
+ * delta and ratio tracking (Sec. 4.4) bound the density piecewise by bricks of 8^3 voxels,
+ * brick b by the largest of the voxels its trilinear density interpolates (8b - 1 .. 8b + 8
+ * per axis, zero outside the grid), and cross empty bricks without drawing. */
+rpnn_status rpnn_copy_brick_majorants(rpnn_ctx* ctx, int32_t vol, float* dev_out, void* stream);
 
 /* ---- network parameters (Sec. 4.3) --------------------------------------------------- */
 /* Flat FP32 parameter vector, row-major [out][in] matrices, in this order:

@@ -99,6 +99,12 @@ def lib():
             L.orc_ratio_track.argtypes = [C.c_void_p, _dp, _dp, C.c_uint64, C.c_uint32,
                                           C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
                                           C.POINTER(C.c_int)]
+            for name in ("orc_delta_track_global",):
+                getattr(L, name).argtypes = L.orc_delta_track.argtypes
+            L.orc_ratio_track_global.restype = C.c_double
+            L.orc_ratio_track_global.argtypes = L.orc_ratio_track.argtypes
+            L.orc_brick_majorant.restype = C.c_float
+            L.orc_brick_majorant.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
             L.orc_hg.restype = C.c_double
             L.orc_hg.argtypes = [C.c_double, C.c_double]
             L.orc_primary.argtypes = [C.c_void_p, C.POINTER(Camera), C.c_int64, C.c_int,
@@ -296,21 +302,34 @@ class Volume:
         assert r == 0
         return out
 
-    def delta_track(self, o, d, seed, id0, id1, domain=2):
+    def delta_track(self, o, d, seed, id0, id1, domain=2, global_majorant=False):
+        """Delta tracking over the brick majorants (global_majorant: against the single
+        global majorant, the estimator the brick form must agree with in distribution)."""
         o = _c64(o, (3,)); d = _c64(d, (3,))
         x = np.zeros(3); t = np.zeros(1)
         ctr = C.c_uint32(0)
-        r = lib().orc_delta_track(self.h, _d(o), _d(d), seed, id0, id1, domain,
-                                  C.byref(ctr), _d(x), _d(t))
+        fn = lib().orc_delta_track_global if global_majorant else lib().orc_delta_track
+        r = fn(self.h, _d(o), _d(d), seed, id0, id1, domain, C.byref(ctr), _d(x), _d(t))
         return r, x, float(t[0])
 
-    def ratio_track(self, o, d, seed, id0, id1, domain=3):
+    def ratio_track(self, o, d, seed, id0, id1, domain=3, global_majorant=False):
         o = _c64(o, (3,)); d = _c64(d, (3,))
         ctr = C.c_uint32(0)
         capped = C.c_int(0)
-        T = lib().orc_ratio_track(self.h, _d(o), _d(d), seed, id0, id1, domain,
-                                  C.byref(ctr), C.byref(capped))
+        fn = lib().orc_ratio_track_global if global_majorant else lib().orc_ratio_track
+        T = fn(self.h, _d(o), _d(d), seed, id0, id1, domain, C.byref(ctr), C.byref(capped))
         return T
+
+    def brick_majorants(self):
+        """Per-brick majorant grid [nbz][nby][nbx] (bricks of 8^3 voxels)."""
+        nz, ny, nx = self.shape
+        nb = [(n + 7) // 8 for n in (nx, ny, nz)]
+        out = np.zeros((nb[2], nb[1], nb[0]), np.float32)
+        for z in range(nb[2]):
+            for y in range(nb[1]):
+                for x in range(nb[0]):
+                    out[z, y, x] = lib().orc_brick_majorant(self.h, x, y, z)
+        return out
 
     def primary(self, cam: dict, pixel: int, sample: int):
         c = make_camera(cam)

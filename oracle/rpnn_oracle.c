@@ -77,6 +77,8 @@ struct orc_ctx {
     float* dens;
     double albedo, g;
     orc_stats st;
+    int nb[3];          /* bricks of ORC_BRICK^3 voxels per axis */
+    float* bmaj;        /* per-brick majorant [nb2][nb1][nb0] */
     double* mip64[ORC_MAX_LEVELS];
     float* mip32[ORC_MAX_LEVELS];
 };
@@ -135,6 +137,34 @@ static void compute_stats(orc_ctx* c) {
     }
 }
 
+/* Majorant of each brick of ORC_BRICK^3 voxels for tracking (Sec. 7 names spatial
+ * acceleration of the Monte Carlo part; per-brick majorants are the standard piecewise-
+ * constant bound): brick b covers fine voxel-centre coordinates [8b - 1/2, 8b + 8 - 1/2]
+ * per axis, where the trilinear density interpolates voxels 8b - 1 .. 8b + 8, so the
+ * largest of those voxels (zero outside the grid) bounds the density in the brick. */
+static void compute_brick_majorants(orc_ctx* c) {
+    for (int a = 0; a < 3; ++a) c->nb[a] = (c->n[a] + ORC_BRICK - 1) / ORC_BRICK;
+    c->bmaj = (float*)calloc((size_t)c->nb[0] * c->nb[1] * c->nb[2], sizeof(float));
+    for (int bz = 0; bz < c->nb[2]; ++bz)
+        for (int by = 0; by < c->nb[1]; ++by)
+            for (int bx = 0; bx < c->nb[0]; ++bx) {
+                float m = 0.0f;
+                for (int z = bz * ORC_BRICK - 1; z <= bz * ORC_BRICK + ORC_BRICK; ++z)
+                    for (int y = by * ORC_BRICK - 1; y <= by * ORC_BRICK + ORC_BRICK; ++y)
+                        for (int x = bx * ORC_BRICK - 1; x <= bx * ORC_BRICK + ORC_BRICK; ++x) {
+                            if (x < 0 || y < 0 || z < 0 || x >= c->n[0] || y >= c->n[1] || z >= c->n[2]) continue;
+                            const float v = c->dens[((size_t)z * c->n[1] + y) * c->n[0] + x];
+                            if (v > m) m = v;
+                        }
+                c->bmaj[((size_t)bz * c->nb[1] + by) * c->nb[0] + bx] = m;
+            }
+}
+
+float orc_brick_majorant(const orc_ctx* c, int bx, int by, int bz) {
+    if (bx < 0 || by < 0 || bz < 0 || bx >= c->nb[0] || by >= c->nb[1] || bz >= c->nb[2]) return -1.0f;
+    return c->bmaj[((size_t)bz * c->nb[1] + by) * c->nb[0] + bx];
+}
+
 orc_ctx* orc_create(const float* density, int nx, int ny, int nz, double albedo, double hg_g) {
     if (!density || nx <= 0 || ny <= 0 || nz <= 0) return NULL;
     const int64_t nv = (int64_t)nx * ny * nz;
@@ -148,6 +178,7 @@ orc_ctx* orc_create(const float* density, int nx, int ny, int nz, double albedo,
     c->g = hg_g;
     compute_stats(c);
     if (c->st.nonzero == 0) { orc_destroy(c); return NULL; }
+    compute_brick_majorants(c);
     return c;
 }
 
@@ -155,6 +186,7 @@ void orc_destroy(orc_ctx* c) {
     if (!c) return;
     for (int i = 0; i < ORC_MAX_LEVELS; ++i) { free(c->mip64[i]); free(c->mip32[i]); }
     free(c->dens);
+    free(c->bmaj);
     free(c);
 }
 
@@ -579,10 +611,12 @@ static int box_clip(const double ext[3], const double o[3], const double d[3], d
     return tmin < tmax;
 }
 
-/* Delta (Woodcock) tracking against the global majorant (Sec. 4.4).  Each tentative
+/* Delta (Woodcock) tracking against the global majorant (Sec. 4.4): the path tracer's
+ * bounces (which start inside the medium) use it, and it is the estimator the brick
+ * tracking below must agree with in distribution.  Each tentative
  * collision draws one Philox block: xi0 for the exponential step, xi1 for the
  * real/null decision (xi1 * majorant < mu_t). */
-int orc_delta_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
                     uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, double x[3],
                     double* t_out) {
     double t0, t1;
@@ -607,7 +641,7 @@ int orc_delta_track(const orc_ctx* c, const double o[3], const double d[3], uint
 
 /* Ratio tracking (Novak et al. 2014, cited in Sec. 2) for the shadow-ray
  * transmittance; one Philox block per tentative collision (xi0). */
-double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+double orc_ratio_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
                        uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped) {
     double t0, t1;
     const double maj = (double)c->st.majorant;
@@ -621,6 +655,146 @@ double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], u
         if (t >= t1) return T;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         T *= 1.0 - orc_density(c, p) / maj;
+    }
+    if (capped) *capped = 1;
+    return T;
+}
+
+/* Walk over the bricks a ray crosses (3-D DDA): brick b[], the ray parameter at which it
+ * leaves the current brick along each axis (tnext) and the parameter span of one brick
+ * (tdelta).  Brick size bs = ORC_BRICK fine voxels in world units. */
+typedef struct {
+    int b[3], step[3];
+    double tnext[3], tdelta[3];
+} brick_walk;
+
+static void walk_init(const orc_ctx* c, const double o[3], const double d[3], double t0, brick_walk* w) {
+    const double bs = (double)ORC_BRICK * c->st.h0;
+    for (int a = 0; a < 3; ++a) {
+        const double p = o[a] + t0 * d[a];
+        int b = (int)floor(p / bs);
+        if (b < 0) b = 0;
+        if (b > c->nb[a] - 1) b = c->nb[a] - 1;
+        w->b[a] = b;
+        if (d[a] > 0.0) {
+            w->step[a] = 1;
+            w->tnext[a] = ((double)(b + 1) * bs - o[a]) / d[a];
+            w->tdelta[a] = bs / d[a];
+        } else if (d[a] < 0.0) {
+            w->step[a] = -1;
+            w->tnext[a] = ((double)b * bs - o[a]) / d[a];
+            w->tdelta[a] = -bs / d[a];
+        } else {
+            w->step[a] = 0;
+            w->tnext[a] = INFINITY;
+            w->tdelta[a] = INFINITY;
+        }
+    }
+}
+
+/* end of the current brick's segment (capped at t1) */
+static double walk_exit(const brick_walk* w, double t1) {
+    double t = w->tnext[0];
+    if (w->tnext[1] < t) t = w->tnext[1];
+    if (w->tnext[2] < t) t = w->tnext[2];
+    return t < t1 ? t : t1;
+}
+
+/* steps into the next brick along the first axis whose boundary comes first; 0 when the
+ * ray leaves the grid of bricks */
+static int walk_step(const orc_ctx* c, brick_walk* w) {
+    int a = 0;
+    if (w->tnext[1] < w->tnext[a]) a = 1;
+    if (w->tnext[2] < w->tnext[a]) a = 2;
+    w->b[a] += w->step[a];
+    w->tnext[a] += w->tdelta[a];
+    return w->b[a] >= 0 && w->b[a] < c->nb[a];
+}
+
+static double walk_majorant(const orc_ctx* c, const brick_walk* w) {
+    return (double)c->bmaj[((size_t)w->b[2] * c->nb[1] + w->b[1]) * c->nb[0] + w->b[0]];
+}
+
+/* Delta (Woodcock) tracking (Sec. 4.4) with a piecewise-constant majorant.  Each tentative
+ * collision draws one Philox block: xi0 gives the optical depth tau = -log(1 - xi0) of
+ * the majorant to travel, xi1 the real/null decision (xi1 * mu_b < mu_t).  The ray walks
+ * the bricks spending tau at each brick's rate mu_b (mu_b = 0: nothing spent), so the
+ * tentative collision falls where the majorant's optical depth from the previous one
+ * reaches tau -- the exponential free flight of the piecewise-constant majorant. */
+int orc_delta_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                    uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, double x[3],
+                    double* t_out) {
+    double t0, t1;
+    if (c->st.majorant <= 0.0f || !box_clip(c->st.ext, o, d, &t0, &t1)) return 0;
+    brick_walk w;
+    walk_init(c, o, d, t0, &w);
+    double t = t0, tau = 0.0, xi[4] = {0, 0, 0, 0};
+    int fresh = 1;                     /* a new block is needed for the next collision */
+    for (uint32_t n = 0; n < TRACK_CAP; ++n) {
+        const double te = walk_exit(&w, t1);
+        const double mu_b = walk_majorant(c, &w);
+        if (mu_b > 0.0) {
+            if (fresh) {
+                draw(seed, id0, id1, (*ctr)++, domain, xi);
+                tau = -log(1.0 - xi[0]);
+                fresh = 0;
+            }
+            const double seg = mu_b * (te - t);
+            if (tau < seg) {
+                t += tau / mu_b;
+                fresh = 1;
+                double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                if (xi[1] * mu_b < orc_density(c, p)) {
+                    x[0] = p[0]; x[1] = p[1]; x[2] = p[2];
+                    if (t_out) *t_out = t;
+                    return 1;
+                }
+                continue;
+            }
+            tau -= seg;
+        }
+        if (te >= t1) return 0;
+        t = te;
+        if (!walk_step(c, &w)) return 0;
+    }
+    return -1;
+}
+
+/* Ratio tracking (Novak et al. 2014, cited in Sec. 2) for the shadow-ray transmittance,
+ * over the same walk: one Philox block (xi0 -> optical depth) per tentative collision,
+ * T *= 1 - mu_t / mu_b there. */
+double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                       uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped) {
+    double t0, t1;
+    if (capped) *capped = 0;
+    if (c->st.majorant <= 0.0f || !box_clip(c->st.ext, o, d, &t0, &t1)) return 1.0;
+    brick_walk w;
+    walk_init(c, o, d, t0, &w);
+    double t = t0, T = 1.0, tau = 0.0;
+    int fresh = 1;
+    for (uint32_t n = 0; n < TRACK_CAP; ++n) {
+        const double te = walk_exit(&w, t1);
+        const double mu_b = walk_majorant(c, &w);
+        if (mu_b > 0.0) {
+            if (fresh) {
+                double xi[4];
+                draw(seed, id0, id1, (*ctr)++, domain, xi);
+                tau = -log(1.0 - xi[0]);
+                fresh = 0;
+            }
+            const double seg = mu_b * (te - t);
+            if (tau < seg) {
+                t += tau / mu_b;
+                fresh = 1;
+                double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                T *= 1.0 - orc_density(c, p) / mu_b;
+                continue;
+            }
+            tau -= seg;
+        }
+        if (te >= t1) return T;
+        t = te;
+        if (!walk_step(c, &w)) return T;
     }
     if (capped) *capped = 1;
     return T;
@@ -678,7 +852,9 @@ static double path_Li(const orc_ctx* c, const double x0[3], const double d0[3],
         double nd[3];
         orc_sample_hg(c->g, d, xi[0], xi[1], nd);
         double nx[3];
-        int hit = orc_delta_track(c, x, nd, seed, id0, id1, dom, &ctr, nx, NULL);
+        /* a bounce starts inside the medium, where bricks hold nearly the global majorant:
+         * track it against the global one (crossing bricks there only costs) */
+        int hit = orc_delta_track_global(c, x, nd, seed, id0, id1, dom, &ctr, nx, NULL);
         if (hit < 0) { if (capped) *capped = 1; return L; }
         if (hit == 0) return L;
         draw(seed, id0, id1, ctr++, dom, xi);

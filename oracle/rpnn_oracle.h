@@ -87,6 +87,17 @@ typedef struct {
     double light_E;        /* irradiance of the directional light */
 } orc_camera;
 
+/* Tracking reads a per-brick majorant: bricks of ORC_BRICK^3 fine voxels, each bounded by
+ * the largest voxel its trilinear density interpolates (voxels 8b-1 .. 8b+8 per axis). */
+#define ORC_BRICK 8
+float orc_brick_majorant(const orc_ctx* c, int bx, int by, int bz);   /* -1 outside */
+/* The same estimators against the global majorant (the path tracer's bounces; pins). */
+int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                           uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr,
+                           double x[3], double* t_out);
+double orc_ratio_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                              uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped);
+
 /* Free flight by delta tracking from o along unit d inside the unit-box grid.
  * RNG counter (id0, id1, step, domain).  Returns 1 on collision (x written, t), 0
  * on escape, -1 if the step cap was reached. */

@@ -47,7 +47,8 @@ class BatchItem(C.Structure):
 class VolumeInfo(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("levels", C.c_int32), ("dims", (C.c_int32 * 3) * 16),
                 ("mip_of_level", C.c_int32 * K), ("mean", C.c_double),
-                ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64)]
+                ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64),
+                ("bricks", C.c_int32 * 3)]
 
 
 class TuneEntry(C.Structure):
@@ -92,6 +93,7 @@ def load():
             "rpnn_build_mips": [_vp, i32, _vp],
             "rpnn_get_volume_info": [_vp, i32, C.POINTER(VolumeInfo)],
             "rpnn_copy_mip_level": [_vp, i32, i32, _vp, _vp],
+            "rpnn_copy_brick_majorants": [_vp, i32, _vp, _vp],
             "rpnn_set_weights": [_vp, _vp, i64, _vp],
             "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
@@ -186,13 +188,20 @@ class Context:
         return {"n": tuple(i.n), "levels": i.levels,
                 "dims": [tuple(i.dims[k]) for k in range(i.levels)],
                 "mip_of_level": list(i.mip_of_level), "mean": i.mean,
-                "inv_mean_f": i.inv_mean_f, "majorant": i.majorant, "nonzero": i.nonzero}
+                "inv_mean_f": i.inv_mean_f, "majorant": i.majorant, "nonzero": i.nonzero,
+                "bricks": tuple(i.bricks)}
 
     def copy_mip_level(self, vol: int, level: int) -> torch.Tensor:
         info = self.get_volume_info(vol)
         ax, ay, az = info["dims"][level]
         out = torch.empty((az, ay, ax), dtype=torch.float32, device="cuda")
         self._check(self.L.rpnn_copy_mip_level(self.h, vol, level, _ptr(out), _stream()))
+        return out
+
+    def copy_brick_majorants(self, vol: int) -> torch.Tensor:
+        nb = self.get_volume_info(vol)["bricks"]
+        out = torch.empty((nb[2], nb[1], nb[0]), dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_copy_brick_majorants(self.h, vol, _ptr(out), _stream()))
         return out
 
     def sync_status(self):

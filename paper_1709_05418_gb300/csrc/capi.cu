@@ -105,7 +105,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     cudaDeviceSynchronize();
     for (Volume* v : c->vols) {
         if (!v) continue;
-        v->raw.release(); v->packed.release(); v->stats.release();
+        v->raw.release(); v->packed.release(); v->stats.release(); v->bmaj.release();
         delete v;
     }
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
@@ -175,6 +175,7 @@ rpnn_status rpnn_build_mips(rpnn_ctx* ctx, int32_t vol, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     ++c->epoch;
     rpnn_status st = volume_stats(*c, *v, s);
+    if (!st) st = volume_brick_majorants(*c, *v, s);
     if (st) return st;
     return volume_pack_levels(*c, *v, s);
 }
@@ -186,6 +187,17 @@ rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* o
     if (!v) return RPNN_ERR_HANDLE;
     if (!out) { set_error("out is null"); return RPNN_ERR_ARG; }
     *out = v->info;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_copy_brick_majorants(rpnn_ctx* ctx, int32_t vol, float* dev_out, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (!dev_out) { set_error("dev_out is null"); return RPNN_ERR_ARG; }
+    RPNN_CUDA_TRY(cudaMemcpyAsync(dev_out, v->bmaj.p, (size_t)v->nb[0] * v->nb[1] * v->nb[2] * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return RPNN_OK;
 }
 

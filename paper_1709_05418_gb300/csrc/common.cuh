@@ -133,19 +133,98 @@ __device__ __forceinline__ float raw_density(const VolumeView& v, float3 p) {
     return fmaf(f[2], c1 - c0, c0);
 }
 
-// Delta (Woodcock) tracking against the global majorant.  Each tentative collision
-// draws one Philox block at step *ctr: x for the exponential step, y for the
-// real/null decision (y * majorant < mu_t).  1 = collision at x, 0 = escape,
-// -1 = cap reached.
+// Walk over the tracking bricks a ray crosses (3-D DDA): current brick (bx, by, bz), the
+// ray parameter at which it is left across each axis (tn*), the parameter span of one
+// brick along each axis (td*) and the step direction (s*).
+struct BrickWalk {
+    int bx, by, bz, sx, sy, sz;
+    float tnx, tny, tnz, tdx, tdy, tdz;
+};
+
+__device__ __forceinline__ void walk_axis(float o, float d, float t0, float bs, int nb, int& b, int& s, float& tn,
+                                          float& td) {
+    b = (int)floorf((o + t0 * d) / bs);
+    b = min(max(b, 0), nb - 1);
+    if (d > 0.0f) { s = 1; tn = ((float)(b + 1) * bs - o) / d; td = bs / d; }
+    else if (d < 0.0f) { s = -1; tn = ((float)b * bs - o) / d; td = -bs / d; }
+    else { s = 0; tn = INFINITY; td = INFINITY; }
+}
+
+__device__ __forceinline__ void walk_init(const VolumeView& v, float3 o, float3 d, float t0, BrickWalk& w) {
+    walk_axis(o.x, d.x, t0, v.bs, v.nb[0], w.bx, w.sx, w.tnx, w.tdx);
+    walk_axis(o.y, d.y, t0, v.bs, v.nb[1], w.by, w.sy, w.tny, w.tdy);
+    walk_axis(o.z, d.z, t0, v.bs, v.nb[2], w.bz, w.sz, w.tnz, w.tdz);
+}
+
+// end of the current brick's segment, capped at t1
+__device__ __forceinline__ float walk_exit(const BrickWalk& w, float t1) {
+    return fminf(fminf(fminf(w.tnx, w.tny), w.tnz), t1);
+}
+
+// into the next brick across the first boundary (x before y before z on ties); false
+// once the ray leaves the grid of bricks
+__device__ __forceinline__ bool walk_step(const VolumeView& v, BrickWalk& w) {
+    if (w.tny < w.tnx && w.tny <= w.tnz) { w.by += w.sy; w.tny += w.tdy; return (unsigned)w.by < (unsigned)v.nb[1]; }
+    if (w.tnz < w.tnx) { w.bz += w.sz; w.tnz += w.tdz; return (unsigned)w.bz < (unsigned)v.nb[2]; }
+    w.bx += w.sx; w.tnx += w.tdx; return (unsigned)w.bx < (unsigned)v.nb[0];
+}
+
+__device__ __forceinline__ float walk_majorant(const VolumeView& v, const BrickWalk& w) {
+    return __ldg(v.bmaj + ((size_t)w.bz * v.nb[1] + w.by) * v.nb[0] + w.bx);
+}
+
+// Delta (Woodcock) tracking with a piecewise-constant majorant.  Each tentative collision
+// draws one Philox block at step *ctr: x gives the majorant optical depth to travel,
+// tau = -log(1 - x), y the real/null decision (y * mu_b < mu_t).  The ray walks the
+// bricks spending tau at each brick's rate mu_b (empty bricks spend nothing), so the
+// tentative collision falls where the majorant's optical depth reaches tau.
+// 1 = collision at x, 0 = escape, -1 = cap reached.
 __device__ __forceinline__ int delta_track(const VolumeView& v, float3 o, float3 d, const Rng& rng,
                                            uint32_t& ctr, float3& x) {
     float t0, t1;
     if (v.majorant <= 0.0f || !box_clip(v.ext, o, d, t0, t1)) return 0;
+    BrickWalk w;
+    walk_init(v, o, d, t0, w);
+    float t = t0, tau = 0.0f, xy = 0.0f;
+    bool fresh = true;                  // a new block is needed for the next collision
+    for (uint32_t n = 0; n < kTrackCap; ++n) {
+        const float te = walk_exit(w, t1);
+        const float mu_b = walk_majorant(v, w);
+        if (mu_b > 0.0f) {
+            if (fresh) {
+                const float4 xi = rng.draw(ctr++);
+                tau = -logf(1.0f - xi.x);
+                xy = xi.y;
+                fresh = false;
+            }
+            const float seg = mu_b * (te - t);
+            if (tau < seg) {
+                t += tau / mu_b;
+                fresh = true;
+                const float3 p = o + t * d;
+                if (xy * mu_b < raw_density(v, p)) { x = p; return 1; }
+                continue;
+            }
+            tau -= seg;
+        }
+        if (te >= t1) return 0;
+        t = te;
+        if (!walk_step(v, w)) return 0;
+    }
+    return -1;
+}
+
+// Delta tracking against the global majorant (one block per tentative collision: x for
+// the exponential step, y for the real/null decision), for the path tracer's bounces,
+// which start inside the medium where the bricks hold nearly the global majorant anyway.
+__device__ __forceinline__ int delta_track_global(const VolumeView& v, float3 o, float3 d, const Rng& rng,
+                                                  uint32_t& ctr, float3& x) {
+    float t0, t1;
+    if (v.majorant <= 0.0f || !box_clip(v.ext, o, d, t0, t1)) return 0;
     float t = t0;
-    const float inv_maj = 1.0f / v.majorant;
     for (uint32_t n = 0; n < kTrackCap; ++n) {
         const float4 xi = rng.draw(ctr++);
-        t -= logf(1.0f - xi.x) * inv_maj;
+        t -= logf(1.0f - xi.x) / v.majorant;
         if (t >= t1) return 0;
         const float3 p = o + t * d;
         if (xi.y * v.majorant < raw_density(v, p)) { x = p; return 1; }
@@ -153,18 +232,36 @@ __device__ __forceinline__ int delta_track(const VolumeView& v, float3 o, float3
     return -1;
 }
 
-// Ratio-tracking transmittance from o along d to the grid boundary (one block / step).
+// Ratio-tracking transmittance from o along d to the grid boundary over the same walk:
+// one block (x -> optical depth) per tentative collision, T *= 1 - mu_t / mu_b there.
 __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, float3 d, const Rng& rng,
                                              uint32_t& ctr, bool& capped) {
     float t0, t1;
     if (v.majorant <= 0.0f || !box_clip(v.ext, o, d, t0, t1)) return 1.0f;
-    float t = t0, T = 1.0f;
-    const float inv_maj = 1.0f / v.majorant;
+    BrickWalk w;
+    walk_init(v, o, d, t0, w);
+    float t = t0, T = 1.0f, tau = 0.0f;
+    bool fresh = true;
     for (uint32_t n = 0; n < kTrackCap; ++n) {
-        const float4 xi = rng.draw(ctr++);
-        t -= logf(1.0f - xi.x) * inv_maj;
-        if (t >= t1) return T;
-        T *= 1.0f - raw_density(v, o + t * d) * inv_maj;
+        const float te = walk_exit(w, t1);
+        const float mu_b = walk_majorant(v, w);
+        if (mu_b > 0.0f) {
+            if (fresh) {
+                tau = -logf(1.0f - rng.draw(ctr++).x);
+                fresh = false;
+            }
+            const float seg = mu_b * (te - t);
+            if (tau < seg) {
+                t += tau / mu_b;
+                fresh = true;
+                T *= 1.0f - raw_density(v, o + t * d) / mu_b;
+                continue;
+            }
+            tau -= seg;
+        }
+        if (te >= t1) return T;
+        t = te;
+        if (!walk_step(v, w)) return T;
     }
     capped = true;
     return T;
@@ -190,7 +287,7 @@ __device__ __forceinline__ float path_Li(const VolumeView& v, float3 x, float3 d
         float4 xi = rng.draw(ctr++);
         const float3 nd = hg_sample(v.g, d, xi.x, xi.y);
         float3 nx;
-        const int hit = delta_track(v, x, nd, rng, ctr, nx);
+        const int hit = delta_track_global(v, x, nd, rng, ctr, nx);
         if (hit < 0) { capped = true; return L; }
         if (hit == 0) return L;
         xi = rng.draw(ctr++);

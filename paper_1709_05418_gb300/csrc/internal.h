@@ -12,6 +12,7 @@
 namespace rpnn {
 
 constexpr int kMaxLevels = 16;
+constexpr int kBrick = 8;    // tracking majorant bricks: kBrick^3 voxels
 
 // status bits written by kernels into the context's device status word
 enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u, kStatTimeout = 8u,
@@ -59,6 +60,9 @@ struct VolumeView {
     int mip_of_level[RPNN_K];
     const float4* packed;    // corner records (2 float4 per record)
     LevelDesc lvl[kMaxLevels];
+    const float* bmaj;       // per-brick majorant [nb2][nb1][nb0] (bricks of kBrick^3 voxels)
+    int nb[3];
+    float bs;                // brick edge in world units (kBrick / max(n))
 };
 
 struct Volume {
@@ -67,6 +71,8 @@ struct Volume {
     DevBuf raw;              // FP32 copy
     DevBuf packed;           // corner records for the levels the stencil reads
     DevBuf stats;            // device-side statistics scratch
+    DevBuf bmaj;             // per-brick tracking majorants
+    int nb[3] = {0, 0, 0};
     bool built = false;
     int levels = 0;
     int dims[kMaxLevels][3] = {};
@@ -179,6 +185,7 @@ struct Ctx {
 // ---- launchers implemented in the .cu files -------------------------------------------
 void batch_release(Ctx& c);           // frees the captured batch graph and its buffers
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
+rpnn_status volume_brick_majorants(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s);
 rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStream_t s);

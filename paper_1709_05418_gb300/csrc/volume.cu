@@ -180,6 +180,36 @@ rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStre
     return RPNN_OK;
 }
 
+// Per-brick majorant for tracking: brick b (kBrick^3 voxels) bounds the trilinear density
+// over its region by the largest of the voxels it interpolates, 8b - 1 .. 8b + 8 per axis
+// (zero outside the grid).  One thread per brick; max is exact, so the order is free.
+__global__ void k_brick_majorant(const float* __restrict__ raw, int nx, int ny, int nz, int bx, int by, int bz,
+                                 float* __restrict__ out) {
+    const int64_t nb = (int64_t)bx * by * bz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x0 = (int)(i % bx) * kBrick - 1, y0 = (int)((i / bx) % by) * kBrick - 1,
+                  z0 = (int)(i / ((int64_t)bx * by)) * kBrick - 1;
+        float m = 0.0f;
+        for (int z = max(z0, 0); z <= min(z0 + kBrick + 1, nz - 1); ++z)
+            for (int y = max(y0, 0); y <= min(y0 + kBrick + 1, ny - 1); ++y) {
+                const float* r = raw + ((int64_t)z * ny + y) * nx;
+                for (int x = max(x0, 0); x <= min(x0 + kBrick + 1, nx - 1); ++x) m = fmaxf(m, __ldg(r + x));
+            }
+        out[i] = m;
+    }
+}
+
+rpnn_status volume_brick_majorants(Ctx& c, Volume& v, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a) v.info.bricks[a] = v.nb[a] = (v.n[a] + kBrick - 1) / kBrick;
+    const int64_t nb = (int64_t)v.nb[0] * v.nb[1] * v.nb[2];
+    rpnn_status st = v.bmaj.reserve((size_t)nb * sizeof(float));
+    if (st) return st;
+    k_brick_majorant<<<grid_for(nb, 128, c.num_sms), 128, 0, s>>>(v.raw.as<float>(), v.n[0], v.n[1], v.n[2], v.nb[0],
+                                                                  v.nb[1], v.nb[2], v.bmaj.as<float>());
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
     const int64_t n = (int64_t)v.n[0] * v.n[1] * v.n[2];
     rpnn_status st = v.stats.reserve(sizeof(DevStats));
@@ -299,6 +329,9 @@ VolumeView Volume::view() const {
     for (int k = 0; k < RPNN_K; ++k) w.mip_of_level[k] = info.mip_of_level[k];
     w.packed = packed.as<float4>();
     for (int i = 0; i < kMaxLevels; ++i) w.lvl[i] = lvl[i];
+    w.bmaj = bmaj.as<float>();
+    for (int a = 0; a < 3; ++a) w.nb[a] = nb[a];
+    w.bs = (float)((double)kBrick / (double)nmax);
     return w;
 }
 

@@ -58,6 +58,17 @@ def params():
 
 # ---------------------------------------------------------------- volume
 @pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9)])
+def test_brick_majorants_bit_exact(ctx, shape, seed):
+    dens = W.fbm_cloud(shape=shape, seed=seed, coverage=0.35) if seed != 1 else W.blob_cloud(64, seed=1)
+    v = ctx.load_volume(cuda(dens))
+    ctx.build_mips(v)
+    got = ctx.copy_brick_majorants(v).cpu().numpy()
+    ref = oracle.Volume(dens).brick_majorants()
+    assert got.shape == ref.shape and np.array_equal(got, ref)
+    assert (ref == 0).any() or seed == 1
+
+
+@pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9)])
 def test_stats_and_mips_bit_exact(ctx, shape, seed):
     dens = W.fbm_cloud(shape=shape, seed=seed, coverage=0.35) if seed != 1 else W.blob_cloud(64, seed=1)
     v = ctx.load_volume(cuda(dens))

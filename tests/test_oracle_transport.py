@@ -147,3 +147,59 @@ def test_environment_render_is_the_superposition_of_its_lights(orc):
     assert np.allclose(a, single + second, rtol=1e-12, atol=1e-15)
     assert not np.allclose(a, single)
     vol.close()
+
+
+def _sparse_grid(n=20, seed=5):
+    """Heterogeneous grid with empty bricks: random values in two blobs, zero elsewhere."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros((n, n, n), np.float32)
+    g[2:9, 3:12, 1:10] = rng.uniform(5.0, 40.0, size=(7, 9, 9))
+    g[12:19, 10:18, 11:19] = rng.uniform(0.0, 8.0, size=(7, 8, 8))
+    return g
+
+
+def test_brick_majorants_are_the_max_of_the_interpolated_voxels(orc):
+    g = _sparse_grid()
+    vol = orc.Volume(g)
+    bm = vol.brick_majorants()
+    n = g.shape[0]
+    pad = np.zeros((n + 2, n + 2, n + 2), np.float32)
+    pad[1:-1, 1:-1, 1:-1] = g                       # voxel i at pad index i + 1
+    for bz in range(bm.shape[0]):
+        for by in range(bm.shape[1]):
+            for bx in range(bm.shape[2]):
+                sl = pad[8 * bz:8 * bz + 10, 8 * by:8 * by + 10, 8 * bx:8 * bx + 10]
+                assert bm[bz, by, bx] == sl.max()
+    assert (bm == 0).any() and (bm > 0).any()
+    # every point's trilinear density stays below its brick's majorant
+    rng = np.random.default_rng(1)
+    ext = n / n
+    for p in rng.uniform(0.0, ext, size=(3000, 3)):
+        b = np.minimum((p * n / 8).astype(int), np.array(bm.shape[::-1]) - 1)
+        assert vol.density(p) <= bm[b[2], b[1], b[0]] + 1e-12
+    vol.close()
+
+
+def test_brick_tracking_matches_global_majorant_in_distribution(orc):
+    """On a grid with empty and dense bricks, free-flight distances of the brick-majorant
+    delta tracking and of the global-majorant one follow the same law (two-sample KS), and
+    ratio tracking's mean transmittance matches exp(-optical depth) by fine ray marching."""
+    g = _sparse_grid()
+    vol = orc.Volume(g)
+    o = np.array([-0.2, 0.25, 0.22])
+    d = np.array([1.0, 0.12, 0.2]); d /= np.linalg.norm(d)
+    def dists(glob):
+        out = []
+        for s in range(3000):
+            r, x, t = vol.delta_track(o, d, 1234, s, 0, global_majorant=glob)
+            out.append(t if r == 1 else 10.0)
+        return np.array(out)
+    a, b = dists(False), dists(True)
+    assert (a < 10).mean() > 0.3
+    assert stats.ks_2samp(a, b).pvalue > 1e-3
+    ts = np.linspace(0.0, 2.0, 200001)
+    mus = np.array([vol.density(o + t * d) for t in ts[::20]])
+    tau = np.trapezoid(mus, ts[::20])
+    T = np.array([vol.ratio_track(o, d, 99, s, 0) for s in range(4000)])
+    assert abs(T.mean() - math.exp(-tau)) <= 4 * T.std() / math.sqrt(T.size) + 1e-4
+    vol.close()
