@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (797.787648e6 + 5.636096e6) / 178847,
-                   "sources": {"descriptor.cu": "ff94a607ab93cba5", "volume.cu": "019a6dcf787202e9"}},
+    "descriptor": {"bytes_per_query": (796.725760e6 + 5.659136e6) / 178847,
+                   "sources": {"descriptor.cu": "ff94a607ab93cba5", "volume.cu": "e2b4bb206a1f917d"}},
     "network": {"bytes_per_query": (886.093568e6 + 3.916800e6) / 178847,
                 "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
     "network_fp8": {"bytes_per_query": (459.987200e6 + 5.108224e6) / 178847,
