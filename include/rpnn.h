@@ -101,6 +101,7 @@ typedef struct {
     float majorant;            /* max voxel value */
     int64_t nonzero;           /* voxels > 0 */
     int32_t bricks[3];         /* tracking majorant bricks per axis: ceil(n / 8) */
+    float mip_weight[RPNN_K];  /* blended descriptor: weight of level mip_of_level[k] + 1 */
 } rpnn_volume_info;
 /* Host copy of the statistics (valid after rpnn_build_mips). */
 rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* out);
@@ -108,6 +109,15 @@ rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* o
  * if the stencil does not use it). */
 rpnn_status rpnn_copy_mip_level(rpnn_ctx* ctx, int32_t vol, int32_t level, float* dev_out,
                                 void* stream);
+/* Blended (fractional) mip selection for the descriptor of volume `vol` (Sec. 6 fixes a
+ * Gaussian pyramid but not how a stencil level picks from it; blending is the fractional
+ * choice): with on != 0, stencil level k reads (1 - w_k) rho_{m_k} + w_k rho_{m_k + 1},
+ * w_k = the fraction of log2(stencil spacing in fine voxels) above m_k (0 where the spacing is
+ * outside the pyramid), as lerp(a, b, w) = fma(w, b - a, a) in FP32.  The descriptor then
+ * varies continuously with the mean free path instead of jumping where m_k switches (e.g.
+ * over an animation), at twice the lookups.  Off by default; applies to later descriptor
+ * extractions and renders of the volume. */
+rpnn_status rpnn_set_mip_blend(rpnn_ctx* ctx, int32_t vol, int32_t on);
 /* Writes the tracking majorant grid as FP32 [bricks[2]][bricks[1]][bricks[0]] into dev_out:
  * delta and ratio tracking (Sec. 4.4) bound the density piecewise by bricks of 8^3 voxels,
  * brick b by the largest of the voxels its trilinear density interpolates (8b - 1 .. 8b + 8

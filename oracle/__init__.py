@@ -52,7 +52,7 @@ class Stats(C.Structure):
         ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64),
         ("levels", C.c_int), ("mip_of_level", C.c_int * K),
         ("dims", (C.c_int * 3) * MAX_LEVELS), ("h0", C.c_double), ("inv_h0", C.c_double),
-        ("ext", C.c_double * 3),
+        ("ext", C.c_double * 3), ("mip_weight", C.c_double * K), ("mip_weight_f", C.c_float * K),
     ]
 
 
@@ -103,6 +103,8 @@ def lib():
                 getattr(L, name).argtypes = L.orc_delta_track.argtypes
             L.orc_ratio_track_global.restype = C.c_double
             L.orc_ratio_track_global.argtypes = L.orc_ratio_track.argtypes
+            L.orc_set_mip_blend.argtypes = [C.c_void_p, C.c_int]
+            L.orc_set_mip_blend.restype = None
             L.orc_brick_majorant.restype = C.c_float
             L.orc_brick_majorant.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
             L.orc_hg.restype = C.c_double
@@ -270,7 +272,12 @@ class Volume:
             "levels": s.levels, "mip_of_level": list(s.mip_of_level),
             "dims": [tuple(s.dims[i]) for i in range(s.levels)],
             "h0": s.h0, "inv_h0": s.inv_h0, "ext": tuple(s.ext),
+            "mip_weight": list(s.mip_weight), "mip_weight_f": list(s.mip_weight_f),
         }
+
+    def set_mip_blend(self, on: bool):
+        """Blended (fractional) mip selection for descriptors (off by default)."""
+        lib().orc_set_mip_blend(self.h, 1 if on else 0)
 
     def mip_level(self, level: int, f32: bool = False):
         st = self.stats()

@@ -78,6 +78,7 @@ struct orc_ctx {
     double albedo, g;
     orc_stats st;
     int nb[3];          /* bricks of ORC_BRICK^3 voxels per axis */
+    int mip_blend;      /* descriptor blends levels m_k and m_k + 1 (orc_set_mip_blend) */
     float* bmaj;        /* per-brick majorant [nb2][nb1][nb0] */
     double* mip64[ORC_MAX_LEVELS];
     float* mip32[ORC_MAX_LEVELS];
@@ -134,8 +135,20 @@ static void compute_stats(orc_ctx* c) {
         if (m < 0) m = 0;
         if (m > L - 1) m = L - 1;
         s->mip_of_level[k] = m;
+        /* fractional level for the blended descriptor: log2 of the spacing; the weight of
+         * level m + 1 is its fraction above m (0 where the spacing falls outside the
+         * pyramid's range, which keeps the clamped level alone) */
+        double w = 0.0;
+        if (sk > 0.0) {
+            const double mr = log2(sk);
+            if (mr > 0.0 && mr < (double)(L - 1)) w = mr - floor(mr);
+        }
+        s->mip_weight[k] = w;
+        s->mip_weight_f[k] = (float)w;
     }
 }
+
+void orc_set_mip_blend(orc_ctx* c, int on) { c->mip_blend = on != 0; }
 
 /* Majorant of each brick of ORC_BRICK^3 voxels for tracking (Sec. 7 names spatial
  * acceleration of the Monte Carlo part; per-brick majorants are the standard piecewise-
@@ -485,7 +498,11 @@ int orc_descriptor_f64(orc_ctx* c, const double* x, const double* d, const doubl
                        int64_t q, double* out) {
     if (!c) return -1;
     const double* lv[ORC_K];
-    for (int k = 0; k < ORC_K; ++k) lv[k] = get_mip64(c, c->st.mip_of_level[k]);
+    const double* lv1[ORC_K];
+    for (int k = 0; k < ORC_K; ++k) {
+        lv[k] = get_mip64(c, c->st.mip_of_level[k]);
+        lv1[k] = (c->mip_blend && c->st.mip_weight[k] > 0.0) ? get_mip64(c, c->st.mip_of_level[k] + 1) : NULL;
+    }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < q; ++i) {
         double ex[3], ey[3], ez[3], gamma;
@@ -495,16 +512,22 @@ int orc_descriptor_f64(orc_ctx* c, const double* x, const double* d, const doubl
             const int m = c->st.mip_of_level[k];
             const double scale = ldexp(c->st.inv_mean, k);      /* 2^(k-1) mfp, k 1-based */
             const double s_m = ldexp(c->st.inv_h0, -m);          /* level-m voxels per unit */
+            const double w = c->st.mip_weight[k];
             for (int iz = 0; iz < 9; ++iz)
                 for (int iy = 0; iy < 5; ++iy)
                     for (int ix = 0; ix < 5; ++ix) {
                         double ox = -1.0 + 0.5 * ix, oy = -1.0 + 0.5 * iy, oz = -1.0 + 0.5 * iz;
-                        double u[3];
+                        double p[3], u[3];
                         for (int a = 0; a < 3; ++a) {
-                            double p = x[3 * i + a] + scale * (ox * ex[a] + oy * ey[a] + oz * ez[a]);
-                            u[a] = p * s_m - 0.5;
+                            p[a] = x[3 * i + a] + scale * (ox * ex[a] + oy * ey[a] + oz * ez[a]);
+                            u[a] = p[a] * s_m - 0.5;
                         }
-                        o[k * ORC_DIN + (iz * 5 + iy) * 5 + ix] = trilinear64(lv[k], c->st.dims[m], u);
+                        double r = trilinear64(lv[k], c->st.dims[m], u);
+                        if (lv1[k]) {   /* blended: (1 - w) rho_m + w rho_{m+1} */
+                            for (int a = 0; a < 3; ++a) u[a] = p[a] * (0.5 * s_m) - 0.5;
+                            r = (1.0 - w) * r + w * trilinear64(lv1[k], c->st.dims[m + 1], u);
+                        }
+                        o[k * ORC_DIN + (iz * 5 + iy) * 5 + ix] = r;
                     }
             o[k * ORC_DIN + ORC_S] = gamma;
         }
@@ -524,7 +547,11 @@ int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float w
                        int64_t q, float* out) {
     if (!c) return -1;
     const float* lv[ORC_K];
-    for (int k = 0; k < ORC_K; ++k) lv[k] = get_mip32(c, c->st.mip_of_level[k]);
+    const float* lv1[ORC_K];
+    for (int k = 0; k < ORC_K; ++k) {
+        lv[k] = get_mip32(c, c->st.mip_of_level[k]);
+        lv1[k] = (c->mip_blend && c->st.mip_weight[k] > 0.0) ? get_mip32(c, c->st.mip_of_level[k] + 1) : NULL;
+    }
     const float inv_h0 = (float)c->st.inv_h0;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < q; ++i) {
@@ -568,6 +595,15 @@ int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float w
                 float xs = xi[a] * s;
                 U0[a] = xs - 0.5f;
             }
+            /* level m + 1: the same formulas with s1 = inv_h0 * 2^-(m+1) */
+            const float s1 = ldexpf(inv_h0, -(m + 1));
+            const float g1 = ldexpf(c->st.inv_mean_f, k) * s1;
+            float A1[3], B1[3], C1[3], U01[3];
+            for (int a = 0; a < 3; ++a) {
+                A1[a] = g1 * ex[a]; B1[a] = g1 * ey[a]; C1[a] = g1 * ez[a];
+                float xs = xi[a] * s1;
+                U01[a] = xs - 0.5f;
+            }
             for (int iz = 0; iz < 9; ++iz)
                 for (int iy = 0; iy < 5; ++iy)
                     for (int ix = 0; ix < 5; ++ix) {
@@ -577,7 +613,13 @@ int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float w
                         float u[3];
                         for (int a = 0; a < 3; ++a)
                             u[a] = fmaf(oz, C[a], fmaf(oy, B[a], fmaf(ox, A[a], U0[a])));
-                        o[k * ORC_DIN + (iz * 5 + iy) * 5 + ix] = trilinear32(lv[k], c->st.dims[m], u);
+                        float r = trilinear32(lv[k], c->st.dims[m], u);
+                        if (lv1[k]) {   /* blended: lerp(rho_m, rho_{m+1}, w) at level m + 1's coordinates */
+                            for (int a = 0; a < 3; ++a)
+                                u[a] = fmaf(oz, C1[a], fmaf(oy, B1[a], fmaf(ox, A1[a], U01[a])));
+                            r = lerp32(r, trilinear32(lv1[k], c->st.dims[m + 1], u), c->st.mip_weight_f[k]);
+                        }
+                        o[k * ORC_DIN + (iz * 5 + iy) * 5 + ix] = r;
                     }
             o[k * ORC_DIN + ORC_S] = gamma;
         }

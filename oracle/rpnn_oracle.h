@@ -53,8 +53,14 @@ typedef struct {
     int dims[ORC_MAX_LEVELS][3];
     double h0, inv_h0;
     double ext[3];
+    double mip_weight[ORC_K];   /* blended descriptor: weight of level m_k + 1 (FP64) */
+    float mip_weight_f[ORC_K];  /* the same, rounded to FP32 */
 } orc_stats;
 int orc_get_stats(const orc_ctx* c, orc_stats* out);
+/* Blended (fractional) mip selection for the descriptor: stencil level k reads
+ * (1 - w_k) rho_{m_k} + w_k rho_{m_k + 1}, w_k the fraction of log2(spacing in fine voxels)
+ * above m_k (0 where the spacing is outside the pyramid).  Off by default. */
+void orc_set_mip_blend(orc_ctx* c, int on);
 
 /* ---- Gaussian mip pyramid (Sec. 6 "Implementation": sigma_i = 2^i) ---------- */
 int orc_gauss_taps(int level, double* w, int cap, int* off); /* -> tap count */

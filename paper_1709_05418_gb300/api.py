@@ -48,7 +48,7 @@ class VolumeInfo(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("levels", C.c_int32), ("dims", (C.c_int32 * 3) * 16),
                 ("mip_of_level", C.c_int32 * K), ("mean", C.c_double),
                 ("inv_mean_f", C.c_float), ("majorant", C.c_float), ("nonzero", C.c_int64),
-                ("bricks", C.c_int32 * 3)]
+                ("bricks", C.c_int32 * 3), ("mip_weight", C.c_float * K)]
 
 
 class TuneEntry(C.Structure):
@@ -94,6 +94,7 @@ def load():
             "rpnn_get_volume_info": [_vp, i32, C.POINTER(VolumeInfo)],
             "rpnn_copy_mip_level": [_vp, i32, i32, _vp, _vp],
             "rpnn_copy_brick_majorants": [_vp, i32, _vp, _vp],
+            "rpnn_set_mip_blend": [_vp, i32, i32],
             "rpnn_set_weights": [_vp, _vp, i64, _vp],
             "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
@@ -189,7 +190,7 @@ class Context:
                 "dims": [tuple(i.dims[k]) for k in range(i.levels)],
                 "mip_of_level": list(i.mip_of_level), "mean": i.mean,
                 "inv_mean_f": i.inv_mean_f, "majorant": i.majorant, "nonzero": i.nonzero,
-                "bricks": tuple(i.bricks)}
+                "bricks": tuple(i.bricks), "mip_weight": list(i.mip_weight)}
 
     def copy_mip_level(self, vol: int, level: int) -> torch.Tensor:
         info = self.get_volume_info(vol)
@@ -197,6 +198,10 @@ class Context:
         out = torch.empty((az, ay, ax), dtype=torch.float32, device="cuda")
         self._check(self.L.rpnn_copy_mip_level(self.h, vol, level, _ptr(out), _stream()))
         return out
+
+    def set_mip_blend(self, vol: int, on: bool):
+        """Blended (fractional) mip selection for the volume's descriptors."""
+        self._check(self.L.rpnn_set_mip_blend(self.h, vol, 1 if on else 0))
 
     def copy_brick_majorants(self, vol: int) -> torch.Tensor:
         nb = self.get_volume_info(vol)["bricks"]

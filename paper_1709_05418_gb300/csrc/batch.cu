@@ -76,8 +76,10 @@ rpnn_status enqueue_batch(Ctx& c, const rpnn_batch_item* items, int n, const std
     }
     k_batch_offsets<<<1, 32, 0, s>>>(count, n, B.cap, off, c.status.as<uint32_t>());
     RPNN_CHECK_LAUNCH();
+    bool blend = false;
+    for (int i = 0; i < n; ++i) blend |= c.vol(items[i].vol)->mip_blend;
     rpnn_status st = launch_descriptor_batch(c, B.table.as<BatchItemDev>(), n, B.x.as<float>(), B.d.as<float>(),
-                                             off, B.cap, B.desc.p, s);
+                                             off, B.cap, B.desc.p, blend, s);
     if (st) return st;
     st = mlp_forward_bf16(c, B.desc.p, B.cap, off + n, B.g.as<float>(), s);
     if (st) return st;

@@ -190,6 +190,16 @@ rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* o
     return RPNN_OK;
 }
 
+rpnn_status rpnn_set_mip_blend(rpnn_ctx* ctx, int32_t vol, int32_t on) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, false);
+    if (!v) return RPNN_ERR_HANDLE;
+    v->mip_blend = on != 0;
+    ++c->epoch;                      // captured batch renders hold the volume's view
+    return RPNN_OK;
+}
+
 rpnn_status rpnn_copy_brick_majorants(rpnn_ctx* ctx, int32_t vol, float* dev_out, void* stream) {
     CHECK_CTX(ctx);
     Ctx* c = reinterpret_cast<Ctx*>(ctx);

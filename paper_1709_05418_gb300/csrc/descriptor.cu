@@ -73,10 +73,21 @@ __device__ __forceinline__ Frame make_frame(const float d[3], const float wl[3])
 // coordinate scale s = inv_h0 * 2^-m and gk = (inv_mean * 2^(k-1)) * s of level k (mip m),
 // the level dims, and the record index of cell (0,0,0) with the record strides (records
 // cover cells -1 .. n-1 on each axis).
-struct LevelK {
-    float s, gk;
+struct LevelGeo {
     float hx, hy, hz;          // 1.5*2^23 + n - 1 per axis: the largest valid t (see lookup)
     uint32_t rbias, sy, sz;    // record index = rbias + bits(t2) sz + bits(t1) sy + bits(t0)
+};
+// Level k's constants (32 bytes, two 16-byte shared loads) ...
+struct __align__(16) LevelK {
+    float s, gk;
+    LevelGeo g0;
+};
+// ... and, for a blended descriptor, those of mip level m + 1 with its weight w (w = 0:
+// level k reads level m alone)
+struct __align__(16) LevelB {
+    float s1, gk1, w, pad;
+    LevelGeo g1;
+    uint32_t pad2[2];
 };
 
 // Trilinear lookup from one 32-byte corner record (c0, c1-c0, c2, c3-c2, c4, c5-c4, c6,
@@ -90,7 +101,7 @@ struct LevelK {
 // round exactly as lerp_rn's own subtraction.
 constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
 
-__device__ __forceinline__ float lookup(const float4* __restrict__ packed, const LevelK& g, float u0, float u1,
+__device__ __forceinline__ float lookup(const float4* __restrict__ packed, const LevelGeo& g, float u0, float u1,
                                         float u2) {
     const float t0 = __fadd_rd(u0, kFloorMagic), t1 = __fadd_rd(u1, kFloorMagic), t2 = __fadd_rd(u2, kFloorMagic);
     if (!(t0 >= kFloorMagic - 1.0f && t0 <= g.hx && t1 >= kFloorMagic - 1.0f && t1 <= g.hy &&
@@ -123,12 +134,9 @@ __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const
 // directly (25 consecutive values per level and z-slice).
 //
 // level k's constants of volume v
-__device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
-    const int m = v.mip_of_level[k];
+__device__ __forceinline__ LevelGeo make_geo(const VolumeView& v, int m) {
     const LevelDesc L = v.lvl[m];
-    LevelK g;
-    g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-    g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
+    LevelGeo g;
     g.hx = kFloorMagic + (float)(L.ax - 1);
     g.hy = kFloorMagic + (float)(L.ay - 1);
     g.hz = kFloorMagic + (float)(L.az - 1);
@@ -141,10 +149,34 @@ __device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
     return g;
 }
 
+// level k's constants of volume v
+__device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
+    const int m = v.mip_of_level[k];
+    LevelK g;
+    g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
+    g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
+    g.g0 = make_geo(v, m);
+    return g;
+}
+
+__device__ __forceinline__ LevelB make_blend(const VolumeView& v, int k) {
+    const int m = v.mip_of_level[k];
+    LevelB b{};
+    b.w = v.mip_w[k];
+    if (b.w > 0.0f) {
+        b.s1 = __fmul_rn(v.inv_h0, __int_as_float((126 - m) << 23));   // * 2^-(m+1)
+        b.gk1 = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), b.s1);
+        b.g1 = make_geo(v, m + 1);
+    }
+    return b;
+}
+
 // BATCH: the shading points of up to RPNN_MAX_BATCH renders, compacted: point j belongs
 // to the item i with off[i] <= j < off[i+1], reads its position and direction at
 // region_i + j - off[i], and uses item i's volume and light; row j of `out` is written.
-template <class OutT, bool BATCH>
+// BLEND: some stencil level blends two mip levels (a separate instance, so the plain
+// kernel keeps its registers).
+template <class OutT, bool BATCH, bool BLEND>
 __global__ void __launch_bounds__(256, sizeof(OutT) == 2 ? (BATCH ? 4 : 5) : 4)
 k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __restrict__ ds,
              const float* __restrict__ wls, int wl_stride, int64_t q_host,
@@ -157,13 +189,16 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
     constexpr int NI = BATCH ? RPNN_MAX_BATCH : 1;
     __shared__ __align__(16) OutT rowbuf[STAGE ? 8 : 1][STAGE ? ROW : 8];
     __shared__ LevelK lk[NI][RPNN_K];
+    __shared__ LevelB lb[BLEND ? NI : 1][RPNN_K];
     __shared__ int s_off[NI + 1];
     __shared__ int64_t s_region[NI];
     __shared__ float s_light[NI][3];
     __shared__ const float4* s_packed[NI];
     if (BATCH) {
-        for (int e = threadIdx.x; e < n_items * RPNN_K; e += blockDim.x)
+        for (int e = threadIdx.x; e < n_items * RPNN_K; e += blockDim.x) {
             lk[e / RPNN_K][e % RPNN_K] = make_level(items[e / RPNN_K].v, e % RPNN_K);
+            if (BLEND) lb[e / RPNN_K][e % RPNN_K] = make_blend(items[e / RPNN_K].v, e % RPNN_K);
+        }
         for (int i = threadIdx.x; i <= n_items; i += blockDim.x) s_off[i] = off[i];
         for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
             s_region[i] = items[i].region;
@@ -172,6 +207,7 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
         }
     } else if (threadIdx.x < RPNN_K) {
         lk[0][threadIdx.x] = make_level(v, threadIdx.x);
+        if (BLEND) lb[0][threadIdx.x] = make_blend(v, threadIdx.x);
     }
     __syncthreads();
     const int64_t q = BATCH ? (int64_t)s_off[n_items] : (q_dev ? (int64_t)*q_dev : q_host);
@@ -194,6 +230,7 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
         const float d[3] = {__ldg(ds + 3 * src), __ldg(ds + 3 * src + 1), __ldg(ds + 3 * src + 2)};
         const Frame F = make_frame(d, wl);
         const LevelK* lki = lk[it];
+        const LevelB* lbi = lb[BLEND ? it : 0];
         OutT* grow = out + qi * (int64_t)ROW;
         OutT* row = STAGE ? rowbuf[warp] : grow;
         for (int task = lane; task < RPNN_K * 25; task += 32) {
@@ -211,11 +248,34 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
                 P[a] = __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0));
             }
             OutT* dst = row + k * DS + col;
+            const float bw = BLEND ? lbi[k].w : 0.0f;
+            if (BLEND && bw > 0.0f) {
+                // blended: lerp(rho_m, rho_{m+1}, w), level m + 1 read at its own coordinates
+                const LevelB b = lbi[k];
+                float P1[3], C1[3];
 #pragma unroll
-            for (int iz = 0; iz < 9; ++iz) {
-                const float oz = -1.0f + 0.5f * (float)iz;      // exact: -1, -0.5, ..., 3
-                dst[iz * 25] = cvt_out<OutT>(lookup(packed, g, __fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
-                                                    __fmaf_rn(oz, C[2], P[2])));
+                for (int a = 0; a < 3; ++a) {
+                    const float A = __fmul_rn(b.gk1, F.ex[a]), B = __fmul_rn(b.gk1, F.ey[a]);
+                    C1[a] = __fmul_rn(b.gk1, F.ez[a]);
+                    const float U0 = __fsub_rn(__fmul_rn(x[a], b.s1), 0.5f);
+                    P1[a] = __fmaf_rn(oy, B, __fmaf_rn(ox, A, U0));
+                }
+#pragma unroll 3
+                for (int iz = 0; iz < 9; ++iz) {
+                    const float oz = -1.0f + 0.5f * (float)iz;
+                    const float r0 = lookup(packed, g.g0, __fmaf_rn(oz, C[0], P[0]), __fmaf_rn(oz, C[1], P[1]),
+                                            __fmaf_rn(oz, C[2], P[2]));
+                    const float r1 = lookup(packed, b.g1, __fmaf_rn(oz, C1[0], P1[0]), __fmaf_rn(oz, C1[1], P1[1]),
+                                            __fmaf_rn(oz, C1[2], P1[2]));
+                    dst[iz * 25] = cvt_out<OutT>(lerp_rn(r0, r1, b.w));
+                }
+            } else {
+#pragma unroll
+                for (int iz = 0; iz < 9; ++iz) {
+                    const float oz = -1.0f + 0.5f * (float)iz;      // exact: -1, -0.5, ..., 3
+                    dst[iz * 25] = cvt_out<OutT>(lookup(packed, g.g0, __fmaf_rn(oz, C[0], P[0]),
+                                                        __fmaf_rn(oz, C[1], P[1]), __fmaf_rn(oz, C[2], P[2])));
+                }
             }
         }
         for (int e = lane; e < RPNN_K * (DS - RPNN_S); e += 32) {
@@ -232,15 +292,37 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
     }
 }
 
-template <class OutT, bool BATCH>
+template <class OutT, bool BATCH, bool BLEND>
 int blocks_per_sm() {
     static int nb = 0;
     if (!nb) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<OutT, BATCH>, 256, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_descriptor<OutT, BATCH, BLEND>, 256, 0) != cudaSuccess ||
             nb <= 0)
             nb = 1;
     }
     return nb;
+}
+
+template <class OutT, bool BLEND>
+rpnn_status launch_one(Ctx& c, const VolumeView& vv, const float* x, const float* d, const float* wl,
+                       int wl_stride, int64_t q, const int* q_dev, void* out, cudaStream_t s) {
+    // one resident wave of blocks (8 shading points each), grid-stride beyond that
+    const int64_t wave = (int64_t)c.num_sms * blocks_per_sm<OutT, false, BLEND>();
+    int64_t g = q_dev ? wave : (q + 7) / 8;
+    if (g > wave) g = wave;
+    k_descriptor<OutT, false, BLEND><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (OutT*)out, nullptr, 0,
+                                                            nullptr);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+template <class OutT>
+rpnn_status launch_typed(Ctx& c, const VolumeView& vv, const float* x, const float* d, const float* wl,
+                         int wl_stride, int64_t q, const int* q_dev, void* out, cudaStream_t s) {
+    bool blend = false;
+    for (int k = 0; k < RPNN_K; ++k) blend |= vv.mip_w[k] > 0.0f;
+    return blend ? launch_one<OutT, true>(c, vv, x, d, wl, wl_stride, q, q_dev, out, s)
+                 : launch_one<OutT, false>(c, vv, x, d, wl, wl_stride, q, q_dev, out, s);
 }
 
 }  // namespace
@@ -249,36 +331,26 @@ rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, cons
                               const float* wl, int wl_stride, int64_t q, const int* q_dev,
                               void* out, int dtype, cudaStream_t s) {
     if (q <= 0 && !q_dev) return RPNN_OK;
-    // one resident wave of blocks (8 shading points each), grid-stride beyond that
-    const int per_sm = dtype == RPNN_F32       ? blocks_per_sm<float, false>()
-                       : dtype == RPNN_FP8E4M3 ? blocks_per_sm<__nv_fp8_e4m3, false>()
-                                               : blocks_per_sm<__nv_bfloat16, false>();
-    const int64_t wave = (int64_t)c.num_sms * per_sm;
-    int64_t g = q_dev ? wave : (q + 7) / 8;
-    if (g > wave) g = wave;
-    if (dtype == RPNN_F32)
-        k_descriptor<float, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev, (float*)out, nullptr, 0,
-                                                          nullptr);
-    else if (dtype == RPNN_FP8E4M3)
-        k_descriptor<__nv_fp8_e4m3, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
-                                                                  (__nv_fp8_e4m3*)out, nullptr, 0, nullptr);
-    else
-        k_descriptor<__nv_bfloat16, false><<<(int)g, 256, 0, s>>>(vv, x, d, wl, wl_stride, q, q_dev,
-                                                                  (__nv_bfloat16*)out, nullptr, 0, nullptr);
-    RPNN_CHECK_LAUNCH();
-    return RPNN_OK;
+    if (dtype == RPNN_F32) return launch_typed<float>(c, vv, x, d, wl, wl_stride, q, q_dev, out, s);
+    if (dtype == RPNN_FP8E4M3) return launch_typed<__nv_fp8_e4m3>(c, vv, x, d, wl, wl_stride, q, q_dev, out, s);
+    return launch_typed<__nv_bfloat16>(c, vv, x, d, wl, wl_stride, q, q_dev, out, s);
 }
 
 rpnn_status launch_descriptor_batch(Ctx& c, const BatchItemDev* items, int n, const float* x, const float* d,
-                                    const int* off, int64_t cap, void* out, cudaStream_t s) {
+                                    const int* off, int64_t cap, void* out, bool blend, cudaStream_t s) {
     if (n < 1 || n > RPNN_MAX_BATCH) { set_error("batch of %d items", n); return RPNN_ERR_ARG; }
-    const int64_t wave = (int64_t)c.num_sms * blocks_per_sm<__nv_bfloat16, true>();
+    const int64_t wave = (int64_t)c.num_sms * (blend ? blocks_per_sm<__nv_bfloat16, true, true>()
+                                                     : blocks_per_sm<__nv_bfloat16, true, false>());
     int64_t g = (cap + 7) / 8;
     if (g > wave) g = wave;
     if (g < 1) g = 1;
     VolumeView none{};
-    k_descriptor<__nv_bfloat16, true><<<(int)g, 256, 0, s>>>(none, x, d, nullptr, 0, cap, nullptr,
-                                                             (__nv_bfloat16*)out, items, n, off);
+    if (blend)
+        k_descriptor<__nv_bfloat16, true, true><<<(int)g, 256, 0, s>>>(none, x, d, nullptr, 0, cap, nullptr,
+                                                                       (__nv_bfloat16*)out, items, n, off);
+    else
+        k_descriptor<__nv_bfloat16, true, false><<<(int)g, 256, 0, s>>>(none, x, d, nullptr, 0, cap, nullptr,
+                                                                        (__nv_bfloat16*)out, items, n, off);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }

@@ -63,6 +63,7 @@ struct VolumeView {
     const float* bmaj;       // per-brick majorant [nb2][nb1][nb0] (bricks of kBrick^3 voxels)
     int nb[3];
     float bs;                // brick edge in world units (kBrick / max(n))
+    float mip_w[RPNN_K];     // blended descriptor: weight of level mip_of_level[k] + 1 (0: off)
 };
 
 struct Volume {
@@ -73,6 +74,7 @@ struct Volume {
     DevBuf stats;            // device-side statistics scratch
     DevBuf bmaj;             // per-brick tracking majorants
     int nb[3] = {0, 0, 0};
+    bool mip_blend = false;  // descriptor blends levels m_k and m_k + 1
     bool built = false;
     int levels = 0;
     int dims[kMaxLevels][3] = {};
@@ -195,8 +197,9 @@ rpnn_status launch_descriptor(Ctx& c, const VolumeView& vv, const float* x, cons
                               void* out, int dtype, cudaStream_t s);
 // Batched form: compacted query j of item i (off[i] <= j < off[i+1], j < off[n]) reads
 // x, d at region_i + j - off[i] and writes descriptor row j.  BF16 output.
+// blend: some item's volume blends mip levels (rpnn_set_mip_blend).
 rpnn_status launch_descriptor_batch(Ctx& c, const BatchItemDev* items, int n, const float* x, const float* d,
-                                    const int* off, int64_t cap, void* out, cudaStream_t s);
+                                    const int* off, int64_t cap, void* out, bool blend, cudaStream_t s);
 
 // Primary stage.  Query outputs (qx, qd, qps, qcount) and inspection outputs (hit, xo,
 // dout, Ld; per pixel sample) are each optional.

@@ -248,6 +248,14 @@ rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
         if (sk > 0.0) { int ex; std::frexp(sk, &ex); m = ex - 1; }
         m = std::max(0, std::min(m, L - 1));
         I.mip_of_level[k] = m;
+        // blended descriptor: weight of level m + 1 = fraction of log2(spacing) above m
+        // (0 where the spacing is outside the pyramid's range)
+        double w = 0.0;
+        if (sk > 0.0) {
+            const double mr = std::log2(sk);
+            if (mr > 0.0 && mr < (double)(L - 1)) w = mr - std::floor(mr);
+        }
+        I.mip_weight[k] = (float)w;
     }
     return RPNN_OK;
 }
@@ -281,7 +289,10 @@ rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStr
 rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s) {
     int64_t total = 0;
     bool need[kMaxLevels] = {};
-    for (int k = 0; k < RPNN_K; ++k) need[v.info.mip_of_level[k]] = true;
+    for (int k = 0; k < RPNN_K; ++k) {
+        need[v.info.mip_of_level[k]] = true;
+        if (v.info.mip_weight[k] > 0.0f) need[v.info.mip_of_level[k] + 1] = true;   // blended descriptor
+    }
     for (int i = 0; i < v.levels; ++i) {
         v.level_packed[i] = need[i];
         v.lvl[i].ax = v.dims[i][0]; v.lvl[i].ay = v.dims[i][1]; v.lvl[i].az = v.dims[i][2];
@@ -332,6 +343,7 @@ VolumeView Volume::view() const {
     w.bmaj = bmaj.as<float>();
     for (int a = 0; a < 3; ++a) w.nb[a] = nb[a];
     w.bs = (float)((double)kBrick / (double)nmax);
+    for (int k = 0; k < RPNN_K; ++k) w.mip_w[k] = mip_blend ? info.mip_weight[k] : 0.0f;
     return w;
 }
 

@@ -141,6 +141,38 @@ def test_descriptor_shared_light_and_degenerate_frame(ctx, blob_vol, blob_orc):
     assert np.array_equal(g[:, :, :225].view(np.uint32), ref[:, :, :225].view(np.uint32))
 
 
+@pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9)])
+def test_blended_mip_descriptor_bit_exact(ctx, api, shape, seed):
+    """rpnn_set_mip_blend: each entry lerps levels m_k and m_k + 1 with the volume's weights;
+    FP32 bit-exact against the oracle's FP32 restatement with blending, BF16 its rounding,
+    and switching it off gives the plain descriptor back."""
+    dens = W.fbm_cloud(shape=shape, seed=seed, coverage=0.35) if seed != 1 else W.blob_cloud(64, seed=1)
+    v = ctx.load_volume(cuda(dens))
+    ctx.build_mips(v)
+    orc = oracle.Volume(dens)
+    orc.set_mip_blend(True)
+    gi, oi = ctx.get_volume_info(v), orc.stats()
+    assert [np.float32(w) for w in gi["mip_weight"]] == [np.float32(w) for w in oi["mip_weight_f"]]
+    assert any(w > 0 for w in gi["mip_weight"])
+    q = 97
+    x, d = W.random_queries(shape, q, seed=31)
+    x32, d32 = x.astype(np.float32), d.astype(np.float32)
+    wl = np.array([0.36, -0.48, 0.8], np.float32)
+    ctx.set_mip_blend(v, True)
+    g = ctx.extract_descriptors(v, cuda(x32), cuda(d32), cuda(wl)).cpu().numpy()
+    ref = orc.descriptor(x32, d32, wl, f32=True)
+    assert np.array_equal(g[:, :, :225].view(np.uint32), ref[:, :, :225].view(np.uint32))
+    gb = ctx.extract_descriptors(v, cuda(x32), cuda(d32), cuda(wl), dtype=torch.bfloat16)
+    assert torch.equal(gb[:, :, :225].cpu(), torch.from_numpy(ref[:, :, :225].copy()).to(torch.bfloat16))
+    ctx.set_mip_blend(v, False)
+    orc.set_mip_blend(False)
+    g0 = ctx.extract_descriptors(v, cuda(x32), cuda(d32), cuda(wl)).cpu().numpy()
+    ref0 = orc.descriptor(x32, d32, wl, f32=True)
+    assert np.array_equal(g0[:, :, :225].view(np.uint32), ref0[:, :, :225].view(np.uint32))
+    assert not np.array_equal(g0, g)
+    orc.close()
+
+
 # ---------------------------------------------------------------- network
 def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))

@@ -142,3 +142,62 @@ def test_level_extent_ratio(orc):
     e10 = np.ptp(pts10 @ np.eye(3), axis=0)
     assert np.allclose(e10, 512 * e1)
     assert abs(np.prod(e10) / np.prod(e1) - 512 ** 3) < 1e-3 * 512 ** 3
+
+
+def test_blended_mips_reproduce_a_linear_field(orc):
+    """With blending on, each entry is (1 - w) rho_m + w rho_{m+1} read at the same world
+    point; both levels of a linear field are that field away from the boundary, so the
+    blend reproduces it too -- a wrong level, scale or coordinate for level m + 1 would not."""
+    n = 96
+    i = np.arange(n, dtype=np.float64)
+    Z, Y, X = np.meshgrid(i, i, i, indexing="ij")
+    a, b, c, e = 30.0, 0.25, -0.125, 0.0625
+    dens = (a + b * X + c * Y + e * Z).astype(np.float32)
+    v = orc.Volume(dens)
+    v.set_mip_blend(True)
+    st = v.stats()
+    assert any(0.05 < w < 0.95 for w in st["mip_weight"])
+    rng = np.random.default_rng(4)
+    checked = 0
+    for _ in range(6):
+        x = rng.uniform(0.4, 0.6, size=3)
+        d = unit(rng.normal(size=3))
+        wl = unit(rng.normal(size=3))
+        z = v.descriptor(x[None], d[None], wl)[0]
+        for k in range(1, 11):
+            m = st["mip_of_level"][k - 1] + 1
+            pts = _stencil_world(x, d, wl, st["inv_mean"], k)
+            u = pts * n - 0.5
+            reach = 3 * 2 ** m + 2 ** m + 1
+            ok = np.all((u > reach) & (u < n - 1 - reach), axis=1)
+            exp = (a + b * u[:, 0] + c * u[:, 1] + e * u[:, 2]) / st["mean"]
+            assert np.allclose(z[k - 1, :225][ok], exp[ok], rtol=1e-11, atol=0)
+            checked += int(ok.sum())
+    assert checked > 500
+
+
+def test_blended_mips_are_continuous_across_a_level_switch(orc):
+    """Scaling the extinction by c moves the stencil spacing (in voxels) as 1/c; where it
+    crosses a power of two the selected level switches.  Without blending the descriptor
+    jumps there, with blending it moves by O(dc)."""
+    base = W.blob_cloud(48, nblobs=6, seed=21)
+    v0 = orc.Volume(base)
+    st = v0.stats()
+    k = 2                                         # stencil level 3 (0-based 2)
+    sk = 0.5 * math.ldexp(st["inv_mean_f"], k) * st["inv_h0"]
+    j = math.floor(math.log2(sk))
+    c_switch = sk / 2.0 ** j                      # spacing / c crosses 2^j at c = c_switch
+    x, d = W.random_queries(base.shape, 16, seed=3, margin=0.25)
+    wl = unit([0.2, 0.9, -0.3])
+    out = {}
+    for blend in (False, True):
+        zs = []
+        for f in (1.0 - 1e-4, 1.0 + 1e-4):
+            v = orc.Volume(base * np.float32(c_switch * f))
+            v.set_mip_blend(blend)
+            zs.append(v.descriptor(x, d, wl)[:, k, :225])
+            assert v.stats()["mip_of_level"][k] == (j - 1 if f > 1 else j) or not (0 < j < st["levels"])
+            v.close()
+        out[blend] = np.abs(zs[1] - zs[0]).max() / np.abs(zs[0]).max()
+    assert out[False] > 1e-2, out
+    assert out[True] < 2e-3, out
