@@ -39,12 +39,12 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (796.725760e6 + 5.659136e6) / 178847,
-                   "sources": {"descriptor.cu": "ff94a607ab93cba5", "volume.cu": "e2b4bb206a1f917d"}},
-    "network": {"bytes_per_query": (886.093568e6 + 3.916800e6) / 178847,
-                "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
-    "network_fp8": {"bytes_per_query": (459.987200e6 + 5.108224e6) / 178847,
-                    "sources": {"mlp_tc.cu": "3fed0f7dd901fa62", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
+    "descriptor": {"bytes_per_query": (797.218816e6 + 5.808640e6) / 178847,
+                   "sources": {"descriptor.cu": "9285b6ec0284c9d8", "volume.cu": "1b325d3f3fb105a7"}},
+    "network": {"bytes_per_query": (882.251776e6 + 3.977472e6) / 178847,
+                "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
+    "network_fp8": {"bytes_per_query": (459.278080e6 + 5.133824e6) / 178847,
+                    "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
 }
 
 
@@ -801,6 +801,60 @@ def main():
                                    "own shading points, spread evenly over the image"}
         img8 = img8.clone()
 
+    # the network kernel alone at steady state: 1,048,576 rows (a chunk of the large render),
+    # the render's own BF16 descriptors repeated, so the last partial wave of 128-row tiles
+    # (9.19 tiles per SM on the render above) costs little
+    net_1m, net8_1m = None, None
+    if prec == api.BF16:
+        hit, qx, qd, _ = ctx.trace_primary(vol, cam)
+        idx = torch.nonzero(hit).squeeze(1)
+        wl = torch.as_tensor(np.asarray(cam["light_dir"], np.float32), device=dev)
+        zb = ctx.extract_descriptors(vol, qx[idx].contiguous(), qd[idx].contiguous(), wl, dtype=torch.bfloat16)
+        rows = 1 << 20
+        reps = -(-rows // zb.shape[0])
+        z1m = zb.repeat(reps, 1, 1)[:rows].contiguous()
+        del zb
+        g1m = torch.empty(rows, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            ctx.mlp_forward(z1m, precision=api.BF16, out=g1m)
+        ctx.sync_status()
+        evn = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        flush1 = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for e0, e1 in evn:
+            flush1.zero_()
+            e0.record()
+            ctx.mlp_forward(z1m, precision=api.BF16, out=g1m)
+            e1.record()
+        torch.cuda.synchronize()
+        ms1 = sum(a.elapsed_time(b) for a, b in evn) / len(evn)
+        ach1 = rows * FLOP_PER_QUERY / (ms1 / 1e3) / 1e12
+        pk1 = peaks()
+        net_1m = {"rows": rows, "ms_per_launch": ms1, "bound": "tensor", "achieved": ach1,
+                  "peak": pk1["bf16_tflops"], "unit": "TFLOP/s", "frac": ach1 / pk1["bf16_tflops"],
+                  "peak_src": pk1["src"], "tiles_per_sm": rows / 128 / 152}
+        del z1m
+        if fp8_form:
+            z8 = ctx.extract_descriptors(vol, qx[idx].contiguous(), qd[idx].contiguous(), wl, dtype=torch.uint8)
+            z8m = z8.repeat(reps, 1, 1)[:rows].contiguous()
+            del z8
+            for _ in range(3):
+                ctx.mlp_forward(z8m, precision=api.FP8, out=g1m)
+            ctx.sync_status()
+            for e0, e1 in evn:
+                flush1.zero_()
+                e0.record()
+                ctx.mlp_forward(z8m, precision=api.FP8, out=g1m)
+                e1.record()
+            torch.cuda.synchronize()
+            ms8 = sum(a.elapsed_time(b) for a, b in evn) / len(evn)
+            ach8 = rows * FLOP_PER_QUERY / (ms8 / 1e3) / 1e12
+            net8_1m = {
+                "rows": rows, "ms_per_launch": ms8, "bound": "tensor", "achieved": ach8,
+                "peak": 2 * pk1["bf16_tflops"], "unit": "TFLOP/s", "frac": ach8 / (2 * pk1["bf16_tflops"]),
+                "peak_src": pk1["src"] + " bf16 x 2 (nominal E4M3:BF16 ratio)"}
+            del z8m
+        del g1m, flush1
+
     # end to end through the public API: host-visible result every step
     host_img = torch.empty((512, 512), dtype=torch.float32, pin_memory=True)
     rd = ctx.render_desc(cam, prec, api.MODE_RPNN)
@@ -866,6 +920,8 @@ def main():
                 "frac": ach8 / (2 * pk["bf16_tflops"]), "traffic": traffic_per_launch("network_fp8", nq8),
                 "algorithmic_bytes": nq8 * (10 * 256), "kernel": "network",
                 "peak_src": pk["src"] + " bf16 x 2 (nominal E4M3:BF16 ratio)"}
+            if net8_1m:
+                fp8_form["network_roofline"]["steady_state_1m_rows"] = net8_1m
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -883,6 +939,8 @@ def main():
     }
     if prec == api.BF16:
         line["network_roofline"] = line_net
+        if net_1m:
+            line["network_roofline"]["steady_state_1m_rows"] = net_1m
     if f32_form:
         line["fp32_form"] = f32_form
     if fp8_form:
