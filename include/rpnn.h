@@ -118,6 +118,12 @@ rpnn_status rpnn_copy_mip_level(rpnn_ctx* ctx, int32_t vol, int32_t level, float
  * over an animation), at twice the lookups.  Off by default; applies to later descriptor
  * extractions and renders of the volume. */
 rpnn_status rpnn_set_mip_blend(rpnn_ctx* ctx, int32_t vol, int32_t on);
+/* Cap on the tentative collisions (and brick steps) of one tracking call through volume
+ * `vol` (0 = the default 1,000,000).  A call that reaches it stops, its result is truncated
+ * and the device status raises RPNN_ERR_ITER_LIMIT at the next status read (rpnn_sync_status,
+ * or a call that reads the count); the context stays usable.  For fault injection in tests
+ * and for bounding the time of a render. */
+rpnn_status rpnn_set_iteration_cap(rpnn_ctx* ctx, int32_t vol, int64_t cap);
 /* Writes the tracking majorant grid as FP32 [bricks[2]][bricks[1]][bricks[0]] into dev_out:
  * delta and ratio tracking (Sec. 4.4) bound the density piecewise by bricks of 8^3 voxels,
  * brick b by the largest of the voxels its trilinear density interpolates (8b - 1 .. 8b + 8
@@ -132,7 +138,9 @@ rpnn_status rpnn_copy_brick_majorants(rpnn_ctx* ctx, int32_t vol, float* dev_out
  * 1,296,601 values.  Block: F1 = relu(V z^k + W1 o^{k-1} + b1), F2 = W2 F1 + b2,
  * o^k = relu(F2 + o^{k-1}); standard layer o' = relu(W o + b); g = last output.
  * The library keeps its own FP32 copy and a BF16 tensor-core image; the caller's
- * buffer may be freed after the call returns (the copy is enqueued on `stream`). */
+ * buffer may be freed after the call returns (the copy is enqueued on `stream`).
+ * Parameters are checked first (the call synchronises `stream` for it): a NaN or Inf
+ * returns RPNN_ERR_NONFINITE and leaves the previous weights in place. */
 rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_params,
                              void* stream);
 
@@ -328,6 +336,12 @@ typedef struct {
 /* Copies up to `cap` entries of the tuning table into out (host) and the table's size to
  * *n (host).  Errors: RPNN_ERR_ARG for cap < 0, n NULL, or out NULL with cap > 0. */
 rpnn_status rpnn_get_autotune(rpnn_ctx* ctx, rpnn_tune_entry* out, int32_t cap, int32_t* n);
+/* Restores n tuning decisions (as rpnn_get_autotune wrote them, e.g. from a checkpoint):
+ * later calls of those shapes use them without timing, so a resumed training run repeats
+ * the arithmetic of the run that wrote them bit for bit.  Entries for shapes already in the
+ * table replace them.  Errors: RPNN_ERR_ARG for n < 0, entries NULL with n > 0, or a tile
+ * shape or split the library does not have. */
+rpnn_status rpnn_set_autotune_table(rpnn_ctx* ctx, const rpnn_tune_entry* entries, int32_t n);
 
 #ifdef __cplusplus
 }

@@ -95,6 +95,8 @@ def load():
             "rpnn_copy_mip_level": [_vp, i32, i32, _vp, _vp],
             "rpnn_copy_brick_majorants": [_vp, i32, _vp, _vp],
             "rpnn_set_mip_blend": [_vp, i32, i32],
+            "rpnn_set_iteration_cap": [_vp, i32, i64],
+            "rpnn_set_autotune_table": [_vp, C.POINTER(TuneEntry), i32],
             "rpnn_set_weights": [_vp, _vp, i64, _vp],
             "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
@@ -223,6 +225,18 @@ class Context:
 
     def set_autotune(self, on: bool):
         self._check(self.L.rpnn_set_autotune(self.h, 1 if on else 0))
+
+    def set_autotune_table(self, table: list):
+        """Restores tuning decisions written by autotune_table() (e.g. from a checkpoint)."""
+        buf = (TuneEntry * max(1, len(table)))()
+        for i, e in enumerate(table):
+            for f, _ in TuneEntry._fields_:
+                setattr(buf[i], f, e[f])
+        self._check(self.L.rpnn_set_autotune_table(self.h, buf, len(table)))
+
+    def set_iteration_cap(self, vol: int, cap: int):
+        """Tentative collisions per tracking call through the volume (0: the default)."""
+        self._check(self.L.rpnn_set_iteration_cap(self.h, vol, int(cap)))
 
     def autotune_table(self) -> list:
         """The GEMM-tile choices made so far, one dict per shape."""

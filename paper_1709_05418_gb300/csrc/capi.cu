@@ -169,6 +169,7 @@ rpnn_status rpnn_load_volume(rpnn_ctx* ctx, const void* dev_density, int32_t dty
 
 rpnn_status rpnn_build_mips(rpnn_ctx* ctx, int32_t vol, void* stream) {
     CHECK_CTX(ctx);
+    NvtxRange range("rpnn_build_mips");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     Volume* v = get_vol(c, vol, false);
     if (!v) return RPNN_ERR_HANDLE;
@@ -187,6 +188,17 @@ rpnn_status rpnn_get_volume_info(rpnn_ctx* ctx, int32_t vol, rpnn_volume_info* o
     if (!v) return RPNN_ERR_HANDLE;
     if (!out) { set_error("out is null"); return RPNN_ERR_ARG; }
     *out = v->info;
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_set_iteration_cap(rpnn_ctx* ctx, int32_t vol, int64_t cap) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, false);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (cap < 0 || cap > 0xFFFFFFFFll) { set_error("cap must be in [0, 2^32)"); return RPNN_ERR_ARG; }
+    v->track_cap = (uint32_t)cap;
+    ++c->epoch;
     return RPNN_OK;
 }
 
@@ -230,6 +242,9 @@ rpnn_status rpnn_set_weights(rpnn_ctx* ctx, const float* dev_params, int64_t n_p
     }
     cudaStream_t s = (cudaStream_t)stream;
     rpnn_status st = c->params32.reserve(n_params * sizeof(float));
+    if (st) return st;
+    // a NaN or Inf parameter is rejected before it reaches any weight copy (synchronises s)
+    st = check_finite(*c, dev_params, n_params, s);
     if (st) return st;
     RPNN_CUDA_TRY(cudaMemcpyAsync(c->params32.p, dev_params, n_params * sizeof(float),
                                   cudaMemcpyDeviceToDevice, s));
@@ -347,6 +362,7 @@ rpnn_status rpnn_trace_primary(rpnn_ctx* ctx, int32_t vol, const rpnn_render_des
 static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc, const float* env_dir,
                                const float* env_E, int n_env, float* dev_image, int64_t* out_num_queries,
                                cudaStream_t s) {
+    NvtxRange range(n_env > 0 ? "rpnn_render_env" : "rpnn_render");
     Volume* v = get_vol(c, vol, true);
     if (!v) return RPNN_ERR_HANDLE;
     rpnn_status st = check_desc(desc);
@@ -410,14 +426,17 @@ static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc
     RPNN_CUDA_TRY(cudaMemcpyAsync(c->light.p, lights.data(), lights.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     const float* ldir = c->light.as<float>();
     RPNN_CUDA_TRY(cudaMemsetAsync(qc, 0, sizeof(int), s));
-    st = launch_primary(*c, vv, rd0, c->sample_val.as<float>(), queries ? c->q_x.as<float>() : nullptr,
-                        queries ? c->q_d.as<float>() : nullptr, queries ? c->q_ps.as<uint32_t>() : nullptr,
-                        queries ? qc : nullptr, nullptr, nullptr, nullptr, nullptr, s);
-    if (st) return st;
-    if (nl > 1) {
-        st = launch_nee_env(*c, vv, rd0, c->q_x.as<float>(), c->q_d.as<float>(), c->q_ps.as<uint32_t>(), qc, P, ldir,
-                            ldir + 3 * nl, 1, nl, c->sample_val.as<float>(), s);
+    {
+        NvtxRange stage("primary");
+        st = launch_primary(*c, vv, rd0, c->sample_val.as<float>(), queries ? c->q_x.as<float>() : nullptr,
+                            queries ? c->q_d.as<float>() : nullptr, queries ? c->q_ps.as<uint32_t>() : nullptr,
+                            queries ? qc : nullptr, nullptr, nullptr, nullptr, nullptr, s);
         if (st) return st;
+        if (nl > 1) {
+            st = launch_nee_env(*c, vv, rd0, c->q_x.as<float>(), c->q_d.as<float>(), c->q_ps.as<uint32_t>(), qc, P,
+                                ldir, ldir + 3 * nl, 1, nl, c->sample_val.as<float>(), s);
+            if (st) return st;
+        }
     }
     if (ev) RPNN_CUDA_TRY(cudaEventRecord(ev[1], s));
     if (!net && ev) {
@@ -430,6 +449,7 @@ static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc
             st = launch_chunk_counts(*c, qc, CH, nchunks, qc + 1, s);
             if (st) return st;
         }
+        NvtxRange stage("descriptor+network");
         for (int j = 0; j < nl; ++j) {
             for (int i = 0; i < nchunks; ++i) {
                 const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
@@ -505,6 +525,45 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {
     return RPNN_OK;
 }
 
+rpnn_status rpnn_set_autotune_table(rpnn_ctx* ctx, const rpnn_tune_entry* entries, int32_t n) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (n < 0 || (!entries && n > 0)) { set_error("bad entries"); return RPNN_ERR_ARG; }
+    std::vector<std::pair<GemmKey, GemmChoice>> add;
+    for (int32_t i = 0; i < n; ++i) {
+        const rpnn_tune_entry& e = entries[i];
+        GemmKey k{e.M, e.N, e.K0, e.K1, e.flags};
+        GemmChoice ch{0, e.splits, e.us, e.default_us};
+        const bool tc = (e.flags & (1 << 8)) != 0;
+        if (tc) {
+            if (e.tile_m != 128 || e.tile_k != 64 ||
+                (e.tile_n != 32 && e.tile_n != 64 && e.tile_n != 128 && e.tile_n != 256)) {
+                set_error("entry %d: no tensor-core tile %d x %d x %d", i, e.tile_m, e.tile_n, e.tile_k);
+                return RPNN_ERR_ARG;
+            }
+            ch.tile = e.tile_n;
+        } else {
+            ch.tile = gemm_tile_index(e.tile_m, e.tile_n, e.tile_k);
+            if (ch.tile < 0) {
+                set_error("entry %d: no tile %d x %d x %d", i, e.tile_m, e.tile_n, e.tile_k);
+                return RPNN_ERR_ARG;
+            }
+        }
+        if (e.splits < 1 || e.splits > 32 || (e.splits & (e.splits - 1))) {
+            set_error("entry %d: split %d", i, e.splits);
+            return RPNN_ERR_ARG;
+        }
+        add.emplace_back(k, ch);
+    }
+    for (const auto& kc : add) {
+        bool found = false;
+        for (auto& e : c->tuner.table)
+            if (e.first == kc.first) { e.second = kc.second; found = true; }
+        if (!found) c->tuner.table.push_back(kc);
+    }
+    return RPNN_OK;
+}
+
 rpnn_status rpnn_set_train_precision(rpnn_ctx* ctx, int32_t precision) {
     CHECK_CTX(ctx);
     if (precision != RPNN_F32 && precision != RPNN_BF16) {
@@ -567,6 +626,7 @@ rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t 
                              float rel_ci, int32_t n_min, int32_t n_max, float* dev_x, float* dev_d,
                              float* dev_wl, float* dev_label, int32_t* dev_npaths, void* stream) {
     CHECK_CTX(ctx);
+    NvtxRange range("rpnn_gen_records");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     Volume* v = get_vol(c, vol, true);
     if (!v) return RPNN_ERR_HANDLE;
@@ -595,6 +655,7 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
                             const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
                             float* dev_v, double* dev_loss, void* stream) {
     CHECK_CTX(ctx);
+    NvtxRange range("rpnn_train_step");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
     if (batch <= 0 || batch > 65535 * 64) { set_error("bad batch %d", batch); return RPNN_ERR_ARG; }

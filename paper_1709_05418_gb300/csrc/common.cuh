@@ -12,7 +12,6 @@ enum : uint32_t {
     kDomCamera = 1, kDomPrimary = 2, kDomShadow = 3, kDomPath = 4,
     kDomRecord = 5, kDomRecTrack = 6, kDomLight = 7, kDomLabel = 8
 };
-constexpr uint32_t kTrackCap = 1000000u;   // tentative collisions per tracking call
 constexpr int kBounceCap = 100000;         // collisions per path
 constexpr int kRecordAttempts = 4096;
 constexpr float kPi = 3.14159265358979323846f;
@@ -187,7 +186,7 @@ __device__ __forceinline__ int delta_track(const VolumeView& v, float3 o, float3
     walk_init(v, o, d, t0, w);
     float t = t0, tau = 0.0f, xy = 0.0f;
     bool fresh = true;                  // a new block is needed for the next collision
-    for (uint32_t n = 0; n < kTrackCap; ++n) {
+    for (uint32_t n = 0; n < v.track_cap; ++n) {
         const float te = walk_exit(w, t1);
         const float mu_b = walk_majorant(v, w);
         if (mu_b > 0.0f) {
@@ -222,7 +221,7 @@ __device__ __forceinline__ int delta_track_global(const VolumeView& v, float3 o,
     float t0, t1;
     if (v.majorant <= 0.0f || !box_clip(v.ext, o, d, t0, t1)) return 0;
     float t = t0;
-    for (uint32_t n = 0; n < kTrackCap; ++n) {
+    for (uint32_t n = 0; n < v.track_cap; ++n) {
         const float4 xi = rng.draw(ctr++);
         t -= logf(1.0f - xi.x) / v.majorant;
         if (t >= t1) return 0;
@@ -242,7 +241,7 @@ __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, floa
     walk_init(v, o, d, t0, w);
     float t = t0, T = 1.0f, tau = 0.0f;
     bool fresh = true;
-    for (uint32_t n = 0; n < kTrackCap; ++n) {
+    for (uint32_t n = 0; n < v.track_cap; ++n) {
         const float te = walk_exit(w, t1);
         const float mu_b = walk_majorant(v, w);
         if (mu_b > 0.0f) {

@@ -7,18 +7,30 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rpnn.h"
 
 namespace rpnn {
 
 constexpr int kMaxLevels = 16;
 constexpr int kBrick = 8;    // tracking majorant bricks: kBrick^3 voxels
+constexpr uint32_t kTrackCapDefault = 1000000u;   // tentative collisions per tracking call
 
 // status bits written by kernels into the context's device status word
 enum : uint32_t { kStatIterLimit = 1u, kStatNonFinite = 2u, kStatNegative = 4u, kStatTimeout = 8u,
                   kStatCapacity = 16u };
 
 void set_error(const char* fmt, ...);
+
+// NVTX range for the life of a scope (names a library call or a render stage in profiler
+// timelines; costs nothing measurable when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define RPNN_CUDA_TRY(call)                                                              \
     do {                                                                                 \
@@ -64,6 +76,7 @@ struct VolumeView {
     int nb[3];
     float bs;                // brick edge in world units (kBrick / max(n))
     float mip_w[RPNN_K];     // blended descriptor: weight of level mip_of_level[k] + 1 (0: off)
+    uint32_t track_cap;      // tentative collisions (and brick steps) per tracking call
 };
 
 struct Volume {
@@ -75,6 +88,7 @@ struct Volume {
     DevBuf bmaj;             // per-brick tracking majorants
     int nb[3] = {0, 0, 0};
     bool mip_blend = false;  // descriptor blends levels m_k and m_k + 1
+    uint32_t track_cap = 0;  // 0: the default cap (rpnn_set_iteration_cap)
     bool built = false;
     int levels = 0;
     int dims[kMaxLevels][3] = {};
@@ -218,6 +232,8 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
 rpnn_status launch_nee_env(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd, const float* qx,
                            const float* qd, const uint32_t* qps, const int* qcount, int64_t max_q, const float* dirs,
                            const float* E, int j0, int n, float* sample_val, cudaStream_t s);
+// RPNN_ERR_NONFINITE if any of the n values is NaN or Inf (synchronises s)
+rpnn_status check_finite(Ctx& c, const float* p, int64_t n, cudaStream_t s);
 // sample_val[qps[i]] += scale * g[i] for i < *qcount
 rpnn_status launch_scatter(Ctx& c, float scale, const float* g, const uint32_t* qps, const int* qcount,
                            float* sample_val, cudaStream_t s);
@@ -237,6 +253,8 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
 size_t mlp_saved_floats_per_row();
 // block tile (rows, columns, K step) of entry `tile` of the SIMT GEMM tile table
 void gemm_tile_shape(int tile, int* bm, int* bn, int* bk);
+// index of the tile (bm, bn, bk) in that table, or -1
+int gemm_tile_index(int bm, int bn, int bk);
 // FP32 forward with caller-provided parameters P and three q x 200 scratch buffers
 rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
                                  float* s1, float* s2, cudaStream_t s);

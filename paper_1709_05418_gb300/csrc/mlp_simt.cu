@@ -353,6 +353,12 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 
 }  // namespace
 
+int gemm_tile_index(int bm, int bn, int bk) {
+    for (int t = 0; t < kNumTiles; ++t)
+        if (kTiles[t].bm == bm && kTiles[t].bn == bn && kTiles[t].bk == bk) return t;
+    return -1;
+}
+
 void gemm_tile_shape(int tile, int* bm, int* bn, int* bk) {
     const TileShape& t = kTiles[(tile >= 0 && tile < kNumTiles) ? tile : 0];
     *bm = t.bm; *bn = t.bn; *bk = t.bk;

@@ -264,6 +264,29 @@ rpnn_status launch_scatter(Ctx& c, float scale, const float* g, const uint32_t* 
 }
 
 namespace {
+__global__ void k_count_nonfinite(const float* __restrict__ p, int64_t n, unsigned int* bad) {
+    unsigned int b = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b |= !isfinite(p[i]);
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+}  // namespace
+
+rpnn_status check_finite(Ctx& c, const float* p, int64_t n, cudaStream_t s) {
+    rpnn_status st = c.t_loss.reserve(sizeof(unsigned int));
+    if (st) return st;
+    unsigned int* bad = c.t_loss.as<unsigned int>();
+    RPNN_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned int), s));
+    k_count_nonfinite<<<c.num_sms * 4, 256, 0, s>>>(p, n, bad);
+    RPNN_CHECK_LAUNCH();
+    unsigned int h = 0;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) { set_error("parameters contain NaN or Inf"); return RPNN_ERR_NONFINITE; }
+    return RPNN_OK;
+}
+
+namespace {
 __global__ void k_chunk_counts(const int* __restrict__ count, int64_t rows, int n, int* __restrict__ out) {
     const int64_t total = *count;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {

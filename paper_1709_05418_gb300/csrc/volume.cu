@@ -344,6 +344,7 @@ VolumeView Volume::view() const {
     for (int a = 0; a < 3; ++a) w.nb[a] = nb[a];
     w.bs = (float)((double)kBrick / (double)nmax);
     for (int k = 0; k < RPNN_K; ++k) w.mip_w[k] = mip_blend ? info.mip_weight[k] : 0.0f;
+    w.track_cap = track_cap ? track_cap : kTrackCapDefault;
     return w;
 }
 

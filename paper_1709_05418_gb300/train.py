@@ -5,6 +5,9 @@ records():  path-traced (descriptor, L_i) records (Sec. 5.1) from seeded clouds,
 split():    75 % / 25 % non-overlapping train / validation split (Sec. 5.1).
 fit():      minibatch Adam on the log-MSE loss (Sec. 5.2) with the library's own
             forward / backward kernels (rpnn_train_step); returns the loss history.
+save_checkpoint() / load_checkpoint(): the FP32 master parameters, Adam moments, step,
+            training precision and the GEMM autotuner's decisions, so a resumed run repeats
+            the next step bit for bit.
 Every step of the arithmetic runs in the CUDA library; this module only sequences
 calls and holds tensors.
 """
@@ -82,3 +85,25 @@ def fit(ctx: api.Context, train, val, params: torch.Tensor, steps: int, batch: i
 
 def blob_clouds(n: int, size: int = 64, seed0: int = 100):
     return [W.blob_cloud(size, nblobs=8, seed=seed0 + i) for i in range(n)]
+
+
+def save_checkpoint(path, ctx: api.Context, params: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+                    step: int, precision=api.F32):
+    """Writes the training state: parameters, Adam moments, the last step taken, the
+    training precision and the autotuner's table (its split-K choices fix the order of the
+    weight-gradient sums)."""
+    torch.save({"params": params.detach().cpu(), "m": m.detach().cpu(), "v": v.detach().cpu(),
+                "step": int(step), "precision": int(precision), "autotune": ctx.autotune_table()}, path)
+
+
+def load_checkpoint(path, ctx: api.Context, device="cuda"):
+    """Restores a checkpoint into ctx (weights, training precision, tuning decisions);
+    returns (params, m, v, step) on the device -- the next step is step + 1."""
+    st = torch.load(path, map_location="cpu")
+    params = st["params"].to(device)
+    m = st["m"].to(device)
+    v = st["v"].to(device)
+    ctx.set_autotune_table(st["autotune"])
+    ctx.set_train_precision(st["precision"])
+    ctx.set_weights(params)
+    return params, m, v, st["step"]

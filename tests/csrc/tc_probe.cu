@@ -343,6 +343,35 @@ int run_variant(int nmma, long long* cycles, int* err) {
 
 }  // namespace
 
+// Failure path of the bounded waits, without a fault: a barrier phase nobody completes.
+// The poll helper gives up after `limit` polls (err[0] = 1), and the issuer's wait gives up
+// and raises the block's abort flag (err[1] = 1), as the network kernel's roles do before
+// they free tensor memory and return an error status.
+__global__ void k_wait_timeout(uint32_t limit, int* err, long long* cycles) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ uint32_t abort_word;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+        abort_word = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        const uint32_t left = mbar_poll(smem_u32(&bar), 0, limit);
+        mbar_wait_issuer(smem_u32(&bar), 0, limit, smem_u32(&abort_word));
+        cycles[0] = clock64() - t0;
+        err[0] = left == 0 ? 1 : 0;
+        err[1] = (int)*(volatile uint32_t*)&abort_word;
+    }
+}
+
+extern "C" int tc_wait_timeout(int limit, int* err, long long* cycles) {
+    k_wait_timeout<<<1, 32>>>((uint32_t)limit, err, cycles);
+    if (cudaGetLastError() != cudaSuccess) return -13;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : -14;
+}
+
 extern "C" int tc_mma_variant(int v, int nmma, long long* cycles, int* err) {
     switch (v) {
         case 0: return run_variant<0>(nmma, cycles, err);

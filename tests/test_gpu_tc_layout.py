@@ -240,3 +240,16 @@ def test_mma_fp8_e4m3_layouts(probe):
     exp = np.zeros((128, 64), np.uint8)
     exp[:100] = T.cpu().numpy()[:, 64:128]
     assert np.array_equal(box, exp)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(probe):
+    """A wait on a barrier phase nobody completes returns after its poll budget with the
+    error set (no hang, no trap), and the device keeps working afterwards."""
+    probe.tc_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    err = torch.zeros(2, dtype=torch.int32, device="cuda")
+    cyc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert probe.tc_wait_timeout(2000, err.data_ptr(), cyc.data_ptr()) == 0
+    assert err.tolist() == [1, 1]
+    assert int(cyc) > 0
+    x = torch.arange(1000, device="cuda", dtype=torch.float32)
+    assert float(x.sum()) == 499500.0
