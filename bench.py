@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
     "descriptor": {"bytes_per_query": (797.218816e6 + 5.808640e6) / 178847,
-                   "sources": {"descriptor.cu": "9285b6ec0284c9d8", "volume.cu": "1b325d3f3fb105a7"}},
+                   "sources": {"descriptor.cu": "9285b6ec0284c9d8", "volume.cu:k_pack": "f1b80b6358e59e22"}},
     "network": {"bytes_per_query": (882.251776e6 + 3.977472e6) / 178847,
                 "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
     "network_fp8": {"bytes_per_query": (459.278080e6 + 5.133824e6) / 178847,
@@ -48,17 +48,31 @@ NCU_TRAFFIC = {
 }
 
 
-def traffic_per_launch(kernel, nq):
-    """ncu-measured DRAM bytes for one launch over nq queries, or None if stale/unknown."""
+def _source_digest(csrc, name):
+    """SHA-256 prefix of a source file, or of one function in it ("file.cu:k_name": the text
+    from that __global__ function's line up to the first line that is a lone closing brace)."""
     import hashlib
+    fname, _, fn = name.partition(":")
+    with open(os.path.join(csrc, fname), "rb") as f:
+        data = f.read()
+    if fn:
+        text = data.decode()
+        i = text.index("__global__ void " + fn + "(")
+        j = text.index("\n}\n", i) + 3
+        data = text[i:j].encode()
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def traffic_per_launch(kernel, nq):
+    """ncu-measured DRAM bytes for one launch over nq queries, or None once a source that
+    determines the kernel's traffic has changed since the capture."""
     t = NCU_TRAFFIC.get(kernel)
     if t is None:
         return None
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1709_05418_gb300", "csrc")
     for name, digest in t["sources"].items():
-        with open(os.path.join(csrc, name), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
-                return None
+        if _source_digest(csrc, name) != digest:
+            return None
     return t["bytes_per_query"] * nq
 
 
