@@ -305,6 +305,29 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
                             int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
                             float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
                             void* stream);
+/* ---- plain MLP of the architecture comparison (Sec. 7, Fig. 10) -------------------------
+ * The paper compares its progressive network with "all-at-once" MLPs that take the whole
+ * descriptor in the first layer: shallow-wide (hidden widths 400, 400, 200, 200, 200) and
+ * deep-narrow (22 hidden layers of 200).  Here: n_hidden hidden layers of widths[i] (host
+ * array), ReLU after every layer including the 1-wide output; input rows of din FP32
+ * values (e.g. descriptor rows [10][240], din = 2400, whose zero padding leaves the matching
+ * weights inert).  Parameters (FP32, caller-owned, flat): per hidden layer W [w_i][w_{i-1}]
+ * row-major then b [w_i], then w_o [1][w_last], b_o.  FP32 CUDA-core GEMMs (autotuned). */
+int64_t rpnn_dense_param_count(const int32_t* widths, int32_t n_hidden, int32_t din);   /* -1: bad args */
+rpnn_status rpnn_dense_forward(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                               const float* dev_params, const float* dev_in, int64_t q, float* dev_out,
+                               void* stream);
+/* Gradient of sum_i dout_i g(x_i) w.r.t. the parameters, written to dev_dparams. */
+rpnn_status rpnn_dense_backward(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                                const float* dev_params, const float* dev_in, int64_t q, const float* dev_dout,
+                                float* dev_dparams, void* stream);
+/* One Adam step on the log-MSE loss (as rpnn_train_step), parameters and moments updated in
+ * place, loss (FP64) to *dev_loss. */
+rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                                  const float* dev_in, const float* dev_target, int32_t batch,
+                                  const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
+                                  float* dev_v, double* dev_loss, void* stream);
+
 /* Arithmetic of rpnn_train_step and rpnn_mlp_backward: RPNN_F32 (the default; FP32 CUDA-core
  * GEMMs) or RPNN_BF16 (mixed precision: every 200-wide layer and weight gradient is a BF16
  * tcgen05 GEMM with FP32 accumulation; FP32 master weights, biases, residual sums, ReLU

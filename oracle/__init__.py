@@ -225,6 +225,50 @@ def adam(p, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     lib().orc_adam(_d(p), _d(m), _d(v), _d(grad), p.size, t, lr, b1, b2, eps)
 
 
+def dense_forward(params, widths, x):
+    """Plain ("all-at-once") MLP of the architecture comparison (Sec. 7, Fig. 10) in FP64:
+    h_i = relu(W_i h_{i-1} + b_i) with h_{-1} = x (rows), g = relu(w_o h_last + b_o).
+    Parameters flat: per hidden layer W_i [w_i][w_{i-1}] row-major then b_i, then w_o, b_o.
+    Returns (g [q], [h_0, ..., h_{n-1}])."""
+    p = np.asarray(params, np.float64)
+    h = np.asarray(x, np.float64).reshape(len(x), -1)
+    acts, o = [], 0
+    for w in widths:
+        W = p[o:o + w * h.shape[1]].reshape(w, h.shape[1]); o += w * h.shape[1]
+        b = p[o:o + w]; o += w
+        h = np.maximum(h @ W.T + b, 0.0)
+        acts.append(h)
+    wo = p[o:o + h.shape[1]]; o += h.shape[1]
+    g = np.maximum(h @ wo + p[o], 0.0)
+    assert o + 1 == p.size
+    return g, acts
+
+
+def dense_backward(params, widths, x, dout):
+    """Gradient of sum_i dout_i g_i with respect to the flat parameters (chain rule, FP64)."""
+    p = np.asarray(params, np.float64)
+    xin = np.asarray(x, np.float64).reshape(len(x), -1)
+    g, acts = dense_forward(p, widths, xin)
+    grad = np.zeros_like(p)
+    offs, o, prev = [], 0, xin.shape[1]
+    for w in widths:
+        offs.append((o, prev, w)); o += w * prev + w; prev = w
+    da = np.asarray(dout, np.float64) * (g > 0)
+    hl = acts[-1] if acts else xin
+    grad[o:o + prev] = da @ hl
+    grad[o + prev] = da.sum()
+    dh = np.outer(da, p[o:o + prev]) * (hl > 0)
+    for i in range(len(widths) - 1, -1, -1):
+        oi, pw, w = offs[i]
+        xi = acts[i - 1] if i else xin
+        grad[oi:oi + w * pw] = (dh.T @ xi).ravel()
+        grad[oi + w * pw:oi + w * pw + w] = dh.sum(axis=0)
+        if i:
+            W = p[oi:oi + w * pw].reshape(w, pw)
+            dh = (dh @ W) * (acts[i - 1] > 0)
+    return grad
+
+
 def make_camera(cam: dict) -> Camera:
     c = Camera()
     for k in ("cam_pos", "cam_fwd", "cam_right", "cam_up", "light_dir"):

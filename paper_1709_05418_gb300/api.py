@@ -97,6 +97,10 @@ def load():
             "rpnn_set_mip_blend": [_vp, i32, i32],
             "rpnn_set_iteration_cap": [_vp, i32, i64],
             "rpnn_set_autotune_table": [_vp, C.POINTER(TuneEntry), i32],
+            "rpnn_dense_forward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp],
+            "rpnn_dense_backward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp, _vp],
+            "rpnn_dense_train_step": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i32, C.POINTER(AdamCfg),
+                                      i64, _vp, _vp, _vp, _vp, _vp],
             "rpnn_set_weights": [_vp, _vp, i64, _vp],
             "rpnn_extract_descriptors": [_vp, i32, _vp, _vp, _vp, i32, i64, _vp, i32, _vp],
             "rpnn_mlp_forward": [_vp, _vp, i32, i64, i32, _vp, _vp],
@@ -122,6 +126,8 @@ def load():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int32
+        L.rpnn_dense_param_count.restype = C.c_int64
+        L.rpnn_dense_param_count.argtypes = [C.POINTER(C.c_int32), C.c_int32, C.c_int32]
         L.rpnn_last_error.restype = C.c_char_p
         L.rpnn_last_error.argtypes = []
         _lib = L
@@ -218,6 +224,44 @@ class Context:
 
     def set_profiling(self, on: bool):
         self._check(self.L.rpnn_set_profiling(self.h, 1 if on else 0))
+
+    # -- plain ("all-at-once") MLP of the architecture comparison (Sec. 7) -----------
+    @staticmethod
+    def _widths(widths):
+        w = (C.c_int32 * max(1, len(widths)))(*[int(x) for x in widths])
+        return w, len(widths)
+
+    def dense_param_count(self, widths, din):
+        w, n = self._widths(widths)
+        return int(self.L.rpnn_dense_param_count(w, n, din))
+
+    def dense_forward(self, widths, params, x, out=None):
+        w, n = self._widths(widths)
+        q, din = x.shape[0], x[0].numel()
+        if out is None:
+            out = torch.empty(q, dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_dense_forward(self.h, w, n, din, _ptr(params), _ptr(x), q, _ptr(out), _stream()))
+        return out
+
+    def dense_backward(self, widths, params, x, dout, out=None):
+        w, n = self._widths(widths)
+        q, din = x.shape[0], x[0].numel()
+        if out is None:
+            out = torch.empty(params.numel(), dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_dense_backward(self.h, w, n, din, _ptr(params), _ptr(x), q, _ptr(dout), _ptr(out),
+                                               _stream()))
+        return out
+
+    def dense_train_step(self, widths, x, target, params, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999,
+                         eps=1e-8, loss=None):
+        w, n = self._widths(widths)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        cfg = AdamCfg(lr, beta1, beta2, eps)
+        self._check(self.L.rpnn_dense_train_step(self.h, w, n, x[0].numel(), _ptr(x), _ptr(target), x.shape[0],
+                                                 C.byref(cfg), step, _ptr(params), _ptr(m), _ptr(v), _ptr(loss),
+                                                 _stream()))
+        return loss
 
     def set_train_precision(self, precision):
         """F32 (default) or BF16 arithmetic for train_step and mlp_backward."""

@@ -525,6 +525,82 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {
     return RPNN_OK;
 }
 
+static bool dense_args_ok(const int32_t* widths, int32_t n, int32_t din) {
+    if (n < 0 || n > 64 || din <= 0 || (n > 0 && !widths)) return false;
+    for (int i = 0; i < n; ++i)
+        if (widths[i] <= 0 || widths[i] > 16384) return false;
+    return true;
+}
+
+int64_t rpnn_dense_param_count(const int32_t* widths, int32_t n_hidden, int32_t din) {
+    if (!dense_args_ok(widths, n_hidden, din)) return -1;
+    return dense_param_count(widths, n_hidden, din);
+}
+
+rpnn_status rpnn_dense_forward(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                               const float* dev_params, const float* dev_in, int64_t q, float* dev_out,
+                               void* stream) {
+    CHECK_CTX(ctx);
+    if (!dense_args_ok(widths, n_hidden, din)) { set_error("bad layer widths"); return RPNN_ERR_ARG; }
+    if (q <= 0 || q > 65535 * 64 || !dev_params || !dev_in || !dev_out) { set_error("bad rows or pointer"); return RPNN_ERR_ARG; }
+    return dense_forward(*reinterpret_cast<Ctx*>(ctx), widths, n_hidden, din, dev_params, dev_in, q, dev_out, nullptr,
+                         (cudaStream_t)stream);
+}
+
+static rpnn_status dense_fwd_saved(Ctx& c, const int32_t* widths, int32_t n, int32_t din, const float* P,
+                                   const float* in, int64_t q, cudaStream_t s) {
+    int64_t per_row = 1;
+    for (int i = 0; i < n; ++i) per_row += widths[i];
+    rpnn_status st = c.t_saved.reserve((size_t)per_row * q * sizeof(float));
+    if (!st) st = c.t_out.reserve((size_t)q * sizeof(float));
+    if (st) return st;
+    return dense_forward(c, widths, n, din, P, in, q, c.t_out.as<float>(), c.t_saved.as<float>(), s);
+}
+
+rpnn_status rpnn_dense_backward(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                                const float* dev_params, const float* dev_in, int64_t q, const float* dev_dout,
+                                float* dev_dparams, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!dense_args_ok(widths, n_hidden, din)) { set_error("bad layer widths"); return RPNN_ERR_ARG; }
+    if (q <= 0 || q > 65535 * 64 || !dev_params || !dev_in || !dev_dout || !dev_dparams) {
+        set_error("bad rows or pointer");
+        return RPNN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = dense_fwd_saved(*c, widths, n_hidden, din, dev_params, dev_in, q, s);
+    if (st) return st;
+    return dense_backward(*c, widths, n_hidden, din, dev_params, dev_in, q, c->t_saved.as<float>(), dev_dout,
+                          dev_dparams, s);
+}
+
+rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t n_hidden, int32_t din,
+                                  const float* dev_in, const float* dev_target, int32_t batch,
+                                  const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
+                                  float* dev_v, double* dev_loss, void* stream) {
+    CHECK_CTX(ctx);
+    NvtxRange range("rpnn_dense_train_step");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!dense_args_ok(widths, n_hidden, din)) { set_error("bad layer widths"); return RPNN_ERR_ARG; }
+    if (batch <= 0 || batch > 65535 * 64 || !adam || step < 1 || !dev_in || !dev_target || !dev_params || !dev_m ||
+        !dev_v || !dev_loss) {
+        set_error("bad batch, step or pointer");
+        return RPNN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t np = dense_param_count(widths, n_hidden, din);
+    rpnn_status st = c->t_grad.reserve((size_t)np * sizeof(float));
+    if (!st) st = c->sample_val.reserve((size_t)batch * sizeof(float));
+    if (!st) st = dense_fwd_saved(*c, widths, n_hidden, din, dev_params, dev_in, batch, s);
+    if (st) return st;
+    float* dg = c->sample_val.as<float>();
+    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
+    if (!st) st = dense_backward(*c, widths, n_hidden, din, dev_params, dev_in, batch, c->t_saved.as<float>(), dg,
+                                 c->t_grad.as<float>(), s);
+    if (st) return st;
+    return launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), np, step, *adam, s);
+}
+
 rpnn_status rpnn_set_autotune_table(rpnn_ctx* ctx, const rpnn_tune_entry* entries, int32_t n) {
     CHECK_CTX(ctx);
     Ctx* c = reinterpret_cast<Ctx*>(ctx);

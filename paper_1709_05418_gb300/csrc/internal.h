@@ -298,6 +298,14 @@ rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* 
                                           float* dP, float* da2, cudaStream_t s);
 rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s);
 
+// Plain ("all-at-once") MLP of the architecture comparison (Sec. 7): n hidden layers of
+// widths[i], ReLU everywhere, one ReLU output; FP32 CUDA-core GEMMs
+int64_t dense_param_count(const int* widths, int n, int din);
+rpnn_status dense_forward(Ctx& c, const int* widths, int n, int din, const float* P, const float* in, int64_t q,
+                          float* out, float* saved, cudaStream_t s);
+rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const float* P, const float* in, int64_t q,
+                           const float* saved, const float* dout, float* dP, cudaStream_t s);
+
 // Mixed-precision training form (BF16 tensor-core GEMMs, FP32 master weights and
 // activations): saved FP32 slots as mlp_forward_f32, BF16 copies in s16
 // (train_bf16_saved_elems(q) elements)

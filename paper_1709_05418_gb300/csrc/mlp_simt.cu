@@ -6,6 +6,7 @@
 // where each operand is addressed through (row, col) strides, so the same kernel
 // serves the forward layers, the data gradients (dY W) and the weight gradients
 // (dY^T X).  The block's first layer is two segments: [z^k | o^{k-1}] [V^k | W1^k]^T.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -567,6 +568,106 @@ rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStr
     (void)c;
     k_colsum<<<(N + 31) / 32, dim3(32, 32), 0, s>>>(X, M, N, N, out);
     RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+// ---- plain ("all-at-once") MLP of the architecture comparison (Sec. 7, Fig. 10) -------
+// hidden layers h_i = relu(W_i h_{i-1} + b_i) (h_{-1} = the input row), output
+// g = relu(w_o h_last + b_o); parameters per layer W_i [w_i][w_{i-1}] row-major, then b_i,
+// then w_o [1][w_last], b_o.
+
+int64_t dense_param_count(const int* widths, int n, int din) {
+    int64_t c = 0, prev = din;
+    for (int i = 0; i < n; ++i) {
+        c += prev * widths[i] + widths[i];
+        prev = widths[i];
+    }
+    return c + prev + 1;
+}
+
+// forward; saved (optional) receives h_0 .. h_{n-1} ([q][w_i] each, consecutive) then g
+rpnn_status dense_forward(Ctx& c, const int* widths, int n, int din, const float* P, const float* in, int64_t q,
+                          float* out, float* saved, cudaStream_t s) {
+    const int M = (int)q;
+    const float* x = in;
+    int64_t prev = din, off = 0, soff = 0, wmax = 1;
+    for (int i = 0; i < n; ++i) wmax = std::max<int64_t>(wmax, widths[i]);
+    rpnn_status st = RPNN_OK;
+    if (!saved) {
+        st = c.act0.reserve((size_t)q * wmax * sizeof(float));
+        if (!st) st = c.act1.reserve((size_t)q * wmax * sizeof(float));
+        if (st) return st;
+    }
+    float* bufs[2] = {c.act0.as<float>(), c.act1.as<float>()};
+    for (int i = 0; i < n; ++i) {
+        const int w = widths[i];
+        float* h = saved ? saved + soff : bufs[i & 1];
+        st = gemm(&c, M, nullptr, w, seg(x, prev, 1, P + off, 1, prev, (int)prev), nullptr,
+                  epi(h, w, P + off + (int64_t)w * prev, 1), s);
+        if (st) return st;
+        off += (int64_t)w * prev + w;
+        soff += (int64_t)q * w;
+        x = h;
+        prev = w;
+    }
+    st = gemm(&c, M, nullptr, 1, seg(x, prev, 1, P + off, 1, prev, (int)prev), nullptr, epi(out, 1, P + off + prev, 1), s);
+    if (st) return st;
+    if (saved) RPNN_CUDA_TRY(cudaMemcpyAsync(saved + soff, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return RPNN_OK;
+}
+
+// gradient of sum_i dout_i g_i into dP (written), from the saved activations
+rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const float* P, const float* in, int64_t q,
+                           const float* saved, const float* dout, float* dP, cudaStream_t s) {
+    const int M = (int)q;
+    int64_t wmax = 1;
+    for (int i = 0; i < n; ++i) wmax = std::max<int64_t>(wmax, widths[i]);
+    rpnn_status st = c.act0.reserve((size_t)q * wmax * sizeof(float));
+    if (!st) st = c.act1.reserve((size_t)q * wmax * sizeof(float));
+    if (!st) st = c.t_dg.reserve((size_t)q * sizeof(float));
+    if (st) return st;
+    std::vector<int64_t> poff(n + 1), soff(n + 1);
+    int64_t o = 0, so = 0, prev = din;
+    for (int i = 0; i < n; ++i) {
+        poff[i] = o; soff[i] = so;
+        o += (int64_t)widths[i] * prev + widths[i];
+        so += (int64_t)q * widths[i];
+        prev = widths[i];
+    }
+    poff[n] = o; soff[n] = so;
+    const float* g = saved + so;
+    float* da = c.t_dg.as<float>();
+    k_mask<<<(M + 255) / 256, 256, 0, s>>>(dout, g, M, da);
+    RPNN_CHECK_LAUNCH();
+    const int64_t wl = n ? widths[n - 1] : din;
+    const float* hl = n ? saved + soff[n - 1] : in;
+    // output layer: dw_o = da^T h_last, db_o = sum da, dh_last = (da w_o) * (h_last > 0)
+    st = gemm(&c, 1, nullptr, (int)wl, seg(da, 0, 1, hl, wl, 1, M), nullptr, epi(dP + poff[n], wl), s);
+    if (st) return st;
+    k_colsum<<<1, dim3(32, 32), 0, s>>>(da, M, 1, 1, dP + poff[n] + wl);
+    RPNN_CHECK_LAUNCH();
+    if (n == 0) return RPNN_OK;
+    float* cur = c.act0.as<float>();
+    float* nxt = c.act1.as<float>();
+    st = gemm(&c, M, nullptr, (int)wl, seg(da, 1, 1, P + poff[n], wl, 1, 1), nullptr,
+              epi(cur, wl, nullptr, 0, nullptr, 0, hl, wl), s);
+    if (st) return st;
+    for (int i = n - 1; i >= 0; --i) {
+        const int64_t w = widths[i], pw = i ? widths[i - 1] : din;
+        const float* xin = i ? saved + soff[i - 1] : in;
+        // dW_i = dh_i^T x_{i-1}; db_i = colsum(dh_i)
+        st = gemm(&c, (int)w, nullptr, (int)pw, seg(cur, 1, w, xin, pw, 1, M), nullptr, epi(dP + poff[i], pw), s);
+        if (st) return st;
+        k_colsum<<<(unsigned)((w + 31) / 32), dim3(32, 32), 0, s>>>(cur, M, (int)w, w, dP + poff[i] + w * pw);
+        RPNN_CHECK_LAUNCH();
+        if (i > 0) {
+            // dh_{i-1} = (dh_i W_i) * (h_{i-1} > 0)
+            st = gemm(&c, M, nullptr, (int)pw, seg(cur, w, 1, P + poff[i], pw, 1, (int)w), nullptr,
+                      epi(nxt, pw, nullptr, 0, nullptr, 0, xin, pw), s);
+            if (st) return st;
+            std::swap(cur, nxt);
+        }
+    }
     return RPNN_OK;
 }
 

@@ -254,3 +254,23 @@ def split_params(flat, **kw) -> dict:
 def join_params(parts: dict, **kw) -> np.ndarray:
     return np.concatenate([np.asarray(parts[name], np.float64).ravel()
                            for name, _, _ in param_shapes(**kw)])
+
+
+# architectures of the comparison in Sec. 7 (Fig. 10): hidden widths of the plain MLPs
+SHALLOW_WIDE = (400, 400, 200, 200, 200)
+DEEP_NARROW = (200,) * 22
+
+
+def dense_he_init(widths, din: int, seed: int = 2, bias: float = 0.0, positive_head: bool = True) -> np.ndarray:
+    """He-normal weights for a plain MLP with hidden widths `widths` on din inputs (flat
+    layout: W_i [w_i][w_{i-1}], b_i per layer, then the output row and bias), float32."""
+    rng = np.random.default_rng(seed)
+    parts, prev = [], din
+    for w in widths:
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / prev), size=w * prev))
+        parts.append(np.full(w, bias))
+        prev = w
+    wo = rng.normal(0.0, math.sqrt(2.0 / prev), size=prev)
+    parts.append(np.abs(wo) if positive_head else wo)
+    parts.append(np.full(1, bias))
+    return np.concatenate(parts).astype(np.float32)

@@ -168,3 +168,35 @@ def test_mixed_precision_reference_without_rounding_is_the_oracle(orc):
     assert np.allclose(dp, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
     _, dp16 = forward_backward(params, z, dout, bf16=True)
     assert 1e-5 < np.linalg.norm(dp16 - ref) / np.linalg.norm(ref) < 0.5
+
+
+def test_dense_mlp_reduces_to_hand_computation(orc):
+    """One hidden unit: g = relu(wo * relu(w . x + b) + bo), by hand."""
+    x = np.array([[0.5, -1.0, 2.0], [1.0, 1.0, 1.0]])
+    w, b, wo, bo = np.array([0.3, 0.2, -0.1]), 0.05, 1.5, -0.01
+    params = np.concatenate([w, [b], [wo], [bo]])
+    g, _ = orc.dense_forward(params, [1], x)
+    h = np.maximum(x @ w + b, 0.0)
+    assert np.allclose(g, np.maximum(wo * h + bo, 0.0), rtol=0, atol=1e-15)
+    # no hidden layer: a single ReLU unit on the input
+    g0, _ = orc.dense_forward(np.array([0.1, -0.2, 0.3, 0.4]), [], x)
+    assert np.allclose(g0, np.maximum(x @ [0.1, -0.2, 0.3] + 0.4, 0.0))
+
+
+def test_dense_mlp_backward_matches_finite_differences(orc):
+    rng = np.random.default_rng(12)
+    widths, din = [6, 5, 4], 7
+    n = din * 6 + 6 + 6 * 5 + 5 + 5 * 4 + 4 + 4 + 1
+    params = rng.normal(scale=0.6, size=n)
+    params[-1] = 0.5
+    x = rng.uniform(-1.0, 1.0, size=(9, din))
+    dout = rng.normal(size=9)
+    grad = orc.dense_backward(params, widths, x, dout)
+    h = 1e-6
+    fd = np.zeros(n)
+    for i in range(n):
+        e = np.zeros(n); e[i] = h
+        fp = orc.dense_forward(params + e, widths, x)[0] @ dout
+        fm = orc.dense_forward(params - e, widths, x)[0] @ dout
+        fd[i] = (fp - fm) / (2 * h)
+    assert np.allclose(grad, fd, rtol=1e-6, atol=1e-7)
