@@ -2,7 +2,9 @@
 
 A plain C implementation (``rpnn_oracle.c``) of what the GPU library computes,
 written from Kallweit et al., "Deep Scattering" (Sec. 3.2 Eq. 1, Sec. 4.2-4.4,
-Sec. 5, Sec. 6), wrapped here with ctypes + numpy.  Only ``tests/``, the smoke
+Sec. 5, Sec. 6), wrapped here with ctypes + numpy; the plain MLPs of the architecture
+comparison (Sec. 7) and the environment superposition (Sec. 4.4) are written here in
+numpy / Python directly.  Only ``tests/``, the smoke
 check and the benchmark's ``cpu_baseline`` / reference leg may import this
 package; the CUDA library never calls it and shares no code with it.
 
