@@ -86,6 +86,7 @@ struct Volume {
     DevBuf packed;           // corner records for the levels the stencil reads
     DevBuf stats;            // device-side statistics scratch
     DevBuf bmaj;             // per-brick tracking majorants
+    DevBuf mip_a, mip_b, mip_w;   // separable-pass scratch and taps of the pyramid build
     int nb[3] = {0, 0, 0};
     bool mip_blend = false;  // descriptor blends levels m_k and m_k + 1
     uint32_t track_cap = 0;  // 0: the default cap (rpnn_set_iteration_cap)

@@ -101,10 +101,11 @@ __global__ void k_mip_pass(const float* __restrict__ in, float* __restrict__ out
         else { j = z; n = iz; base = (int64_t)y * ix + x; stride = (int64_t)ix * iy; }
         float acc = 0.0f;
         const int t0 = j * st + off;
-        for (int m = 0; m < T; ++m) {
-            const int t = t0 + m;
-            if (t >= 0 && t < n) acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), __ldg(in + base + t * stride)));
-        }
+        // only the taps that land inside the grid contribute (zero outside): the same terms
+        // in the same ascending order, without visiting the rest
+        const int mlo = max(0, -t0), mhi = min(T, n - t0);
+        for (int m = mlo; m < mhi; ++m)
+            acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), __ldg(in + base + (int64_t)(t0 + m) * stride)));
         out[o] = apply_scale ? __fmul_rn(acc, scale) : acc;
     }
 }
@@ -267,10 +268,14 @@ rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStr
     const int T = (int)w.size();
     const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
     const int ax = v.dims[level][0], ay = v.dims[level][1], az = v.dims[level][2];
-    float *dw = nullptr, *A = nullptr, *B = nullptr;
-    RPNN_CUDA_TRY(cudaMalloc(&dw, T * sizeof(float)));
-    RPNN_CUDA_TRY(cudaMalloc(&A, (size_t)ax * ny * nz * sizeof(float)));
-    RPNN_CUDA_TRY(cudaMalloc(&B, (size_t)ax * ay * nz * sizeof(float)));
+    // volume-owned scratch (grows, never shrinks): no allocation or synchronisation per level
+    rpnn_status rs = v.mip_w.reserve(T * sizeof(float));
+    if (!rs) rs = v.mip_a.reserve((size_t)ax * ny * nz * sizeof(float));
+    if (!rs) rs = v.mip_b.reserve((size_t)ax * ay * nz * sizeof(float));
+    if (rs) return rs;
+    float* dw = v.mip_w.as<float>();
+    float* A = v.mip_a.as<float>();
+    float* B = v.mip_b.as<float>();
     RPNN_CUDA_TRY(cudaMemcpyAsync(dw, w.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
     const int st = 1 << level;
     const float scale = v.info.inv_mean_f;
@@ -281,8 +286,6 @@ rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStr
     k_mip_pass<<<grid_for((int64_t)ax * ay * az, 256, c.num_sms), 256, 0, s>>>(
         B, dst, ax, ay, nz, ax, ay, az, 2, st, off, dw, T, scale, 1);
     RPNN_CHECK_LAUNCH();
-    RPNN_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaFree(dw); cudaFree(A); cudaFree(B);
     return RPNN_OK;
 }
 
