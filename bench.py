@@ -35,15 +35,15 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per shading query of the
-# dominant kernels, from one ncu capture of the benchmark workload (178,847 queries; the
+# dominant kernels, from one ncu capture of the benchmark workload (178,675 queries; the
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (797.218816e6 + 5.808640e6) / 178847,
+    "descriptor": {"bytes_per_query": (797.218816e6 + 5.808640e6) / 178675,
                    "sources": {"descriptor.cu": "9285b6ec0284c9d8", "volume.cu:k_pack": "f1b80b6358e59e22"}},
-    "network": {"bytes_per_query": (882.251776e6 + 3.977472e6) / 178847,
+    "network": {"bytes_per_query": (882.251776e6 + 3.977472e6) / 178675,
                 "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
-    "network_fp8": {"bytes_per_query": (459.278080e6 + 5.133824e6) / 178847,
+    "network_fp8": {"bytes_per_query": (459.278080e6 + 5.133824e6) / 178675,
                     "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
 }
 
