@@ -250,8 +250,9 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows);
  * counts, descriptor, network, per-item composites) is captured once as a CUDA graph on a
  * library-owned stream and replayed on `stream` while the item list (volumes,
  * descriptions, image pointers) is unchanged; loading a volume, building mips or setting
- * weights invalidates the captured graph.  Requirements: 1 <= n_items <= RPNN_MAX_BATCH,
- * every item in RPNN_MODE_RPNN with the same precision.  out_num_queries (host, may be
+ * weights invalidates the captured graph, and so do rpnn_set_mip_blend and
+ * rpnn_set_iteration_cap.  Requirements: 1 <= n_items <= RPNN_MAX_BATCH, every item in
+ * RPNN_MODE_RPNN with RPNN_BF16 precision.  out_num_queries (host, may be
  * NULL): n_items per-item shading-point counts; passing it synchronises `stream`.
  * Errors: RPNN_ERR_ARG (empty, oversized or mixed batch, bad descriptions, null image),
  * RPNN_ERR_HANDLE, RPNN_ERR_STATE (no weights), RPNN_ERR_OOM, RPNN_ERR_CUDA. */
