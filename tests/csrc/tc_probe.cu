@@ -1,9 +1,10 @@
 // tc_probe.cu -- test-only check of the tensor-core operand layouts used by the BF16
 // network kernel: one 128 x 208 x 32 tcgen05 MMA from shared memory (A written by
 // threads, B by a bulk copy), tensor-memory loads, and a 2-D TMA box load with
-// out-of-bounds zero fill.  Every shared-memory access stays inside a 192 KiB
-// allocation even if a descriptor field were read with another meaning, and every wait
-// is bounded.
+// out-of-bounds zero fill; MMA issue-rate measurements; and the give-up path of the
+// bounded barrier waits (a phase nobody completes).  Every shared-memory access stays
+// inside a 192 KiB allocation even if a descriptor field were read with another meaning,
+// and every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
