@@ -533,6 +533,77 @@ def run_env(args, ws, rank, local):
     ctx.close()
 
 
+TTUV_WORKLOAD = ("time to unit variance (Sec. 6, Table 1): the 256^3 fBm cloud at 256x256, 1 spp, rendered "
+                 "with 16 camera seeds by the RPNN (BF16, weights trained here on path-traced records of 4 "
+                 "small fBm clouds) and by the library's plain path tracer; TTUV = seconds per render x mean "
+                 "per-pixel variance over the seeds")
+
+
+def run_ttuv(args, ws, rank, local):
+    """TTUV of the RPNN render and of plain path tracing, and their ratio (the speedup
+    measure of Table 1), with a network trained here briefly on synthetic records."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_05418_gb300 import api
+    from paper_1709_05418_gb300 import workloads as W
+    dens, cam, params = make_workload(rank, device=dev)
+    cam = W.camera(dens.shape, 256, 256, spp=1, seed=3 + rank, light_seed=4 + rank)
+    ctx = api.Context()
+    # a network trained here first (untrained weights predict values far off the path
+    # tracer's scale, which would make the variance comparison meaningless): path-traced
+    # records from four small fBm clouds, BF16 training steps
+    from paper_1709_05418_gb300 import train as T
+    clouds = [W.fbm_cloud(64, seed=900 + i) for i in range(4)]
+    desc, label = T.records(ctx, clouds, 4000, seed=77, rel_ci=0.05, n_min=32, n_max=1024)
+    tr, va = T.split(desc, label)
+    p = torch.from_numpy(W.he_init(seed=5)).to(dev)
+    p.mul_(0.5)
+    ctx.set_train_precision(api.BF16)
+    ctx.set_weights(p)
+    v0 = T.val_loss(ctx, *va)
+    hist = T.fit(ctx, tr, va, p, steps=args.ttuv_train_steps, batch=1024, lr=1e-3,
+                 eval_every=args.ttuv_train_steps)
+    ctx.set_weights(p)
+    vol = ctx.load_volume(torch.from_numpy(dens).to(dev))
+    ctx.build_mips(vol)
+    out = {}
+    for name, prec, mode in (("rpnn", api.BF16, api.MODE_RPNN), ("path_tracing", api.F32, api.MODE_PATH)):
+        imgs = []
+        for s in range(args.warmup):
+            ctx.render(vol, dict(cam, seed=10_000 + s), precision=prec, mode=mode)
+        ctx.sync_status()
+        ms = 0.0
+        for s in range(16):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            img = ctx.render(vol, dict(cam, seed=20_000 + 7919 * s), precision=prec, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            imgs.append(img.double())
+        ctx.sync_status()
+        stack = torch.stack(imgs)
+        var = float(stack.var(dim=0, unbiased=True).mean())
+        sec = ms / 16 / 1e3
+        out[name] = {"ms_per_render": sec * 1e3, "mean_pixel_variance": var, "ttuv": sec * var,
+                     "mean_pixel_value": float(stack.mean())}
+    line = {
+        "metric": "time-to-unit-variance speedup of the RPNN render over plain path tracing on 1 GB300",
+        "value": out["path_tracing"]["ttuv"] / out["rpnn"]["ttuv"], "unit": "x", "n_gpus": ws, "steps": 16,
+        "warmup": args.warmup, "ms_per_step": out["rpnn"]["ms_per_render"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": TTUV_WORKLOAD}, "rpnn": out["rpnn"], "path_tracing": out["path_tracing"],
+        "training": {"records": int(desc.shape[0]), "steps": args.ttuv_train_steps, "val_loss_start": v0,
+                     "val_loss_end": hist[-1][2]},
+        "note": "variance and time on one view; the network is trained briefly on 4 small synthetic clouds, "
+                "so its bias (which Table 1 reports beside the speedup) is not representative",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 LARGE_WORKLOAD = ("large render: 1024^3 FP16 fBm density (seed 300, 6 octaves, 30% non-zero, peak sigma_t "
                   "50/unit), 1920x1080 at 4 spp, random light dir, descriptor/network stages in chunks of "
                   "1,048,576 queries, FP8 (E4M3, per-tensor scales) RPNN, He-init weights")
@@ -677,6 +748,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default 64x64 tile for every FP32 CUDA-core GEMM (no tuning)")
+    ap.add_argument("--ttuv-train-steps", type=int, default=600,
+                    help="training steps of the network the TTUV workload renders with")
     ap.add_argument("--train-precision", default="bf16", choices=["bf16", "f32"],
                     help="arithmetic of the training workload's timed steps (the other is timed beside)")
     ap.add_argument("--train-records", type=int, default=8192,
@@ -685,7 +758,7 @@ def main():
                     help="path cap of the records' stopping rule in the training workload")
     ap.add_argument("--cpu-rows", type=int, default=256,
                     help="records in the FP64 oracle's training step (training workload)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train", "env"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train", "env", "ttuv"],
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
                          "call; large: 1024^3 FP16 cloud at 1920x1080x4")
     ap.add_argument("--profile-only", action="store_true",
@@ -708,6 +781,9 @@ def main():
         return
     if args.workload == "env":
         run_env(args, ws, rank, local)
+        return
+    if args.workload == "ttuv":
+        run_ttuv(args, ws, rank, local)
         return
 
     import torch
