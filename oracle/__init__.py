@@ -105,6 +105,11 @@ def lib():
                 getattr(L, name).argtypes = L.orc_delta_track.argtypes
             L.orc_ratio_track_global.restype = C.c_double
             L.orc_ratio_track_global.argtypes = L.orc_ratio_track.argtypes
+            L.orc_mie_single.argtypes = [C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.orc_lm_table.argtypes = [_dp, _dp, _dp, C.c_int]
+            L.orc_set_phase_lm.argtypes = [C.c_void_p, C.c_int]
+            L.orc_set_phase_lm.restype = None
             L.orc_set_mip_blend.argtypes = [C.c_void_p, C.c_int]
             L.orc_set_mip_blend.restype = None
             L.orc_brick_majorant.restype = C.c_float
@@ -271,6 +276,26 @@ def dense_backward(params, widths, x, dout):
     return grad
 
 
+LM_BINS = 1800
+
+
+def mie_single(x, m_re, m_im, mu):
+    """Lorenz-Mie of one sphere: (s11 at cosines mu, Q_ext, Q_sca)."""
+    mu = _c64(mu)
+    out = np.zeros(mu.size)
+    qe, qs = C.c_double(), C.c_double()
+    assert lib().orc_mie_single(float(x), float(m_re), float(m_im), _d(mu), mu.size, _d(out),
+                                C.byref(qe), C.byref(qs)) == 0
+    return out, qe.value, qs.value
+
+
+def lm_table():
+    """The tabulated cloud phase function: (bin means p, cumulative cdf, bin-edge cosines)."""
+    p, cdf, ce = np.zeros(LM_BINS), np.zeros(LM_BINS + 1), np.zeros(LM_BINS + 1)
+    assert lib().orc_lm_table(_d(p), _d(cdf), _d(ce), LM_BINS) == 0
+    return p, cdf, ce
+
+
 def make_camera(cam: dict) -> Camera:
     c = Camera()
     for k in ("cam_pos", "cam_fwd", "cam_right", "cam_up", "light_dir"):
@@ -320,6 +345,10 @@ class Volume:
             "h0": s.h0, "inv_h0": s.inv_h0, "ext": tuple(s.ext),
             "mip_weight": list(s.mip_weight), "mip_weight_f": list(s.mip_weight_f),
         }
+
+    def set_phase_lm(self, on: bool):
+        """Tabulated Lorenz-Mie phase function instead of Henyey-Greenstein."""
+        lib().orc_set_phase_lm(self.h, 1 if on else 0)
 
     def set_mip_blend(self, on: bool):
         """Blended (fractional) mip selection for descriptors (off by default)."""

@@ -15,6 +15,7 @@
  */
 #include "rpnn_oracle.h"
 
+#include <complex.h>
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
@@ -79,6 +80,7 @@ struct orc_ctx {
     orc_stats st;
     int nb[3];          /* bricks of ORC_BRICK^3 voxels per axis */
     int mip_blend;      /* descriptor blends levels m_k and m_k + 1 (orc_set_mip_blend) */
+    int phase_lm;       /* phase function: 0 Henyey-Greenstein (g), 1 tabulated Lorenz-Mie */
     float* bmaj;        /* per-brick majorant [nb2][nb1][nb0] */
     double* mip64[ORC_MAX_LEVELS];
     float* mip32[ORC_MAX_LEVELS];
@@ -867,6 +869,151 @@ void orc_sample_hg(double g, const double d[3], double xi0, double xi1, double o
     normalize3(out);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Lorenz-Mie phase function of cloud droplets (Sec. 3.1).                      */
+/* The paper's tables and chopping live in its supplement, which is not        */
+/* available; here the phase function is computed from the series of Bohren &  */
+/* Huffman (1983, App. A) for water droplets (m = 1.333, no absorption) at      */
+/* 0.55 um, averaged over Deirmendjian's cumulus C.1 size distribution          */
+/* n(r) ~ r^6 exp(-1.5 r) (r in um, mode 4 um), and tabulated as its mean over  */
+/* ORC_LM_BINS bins of 0.1 degree of scattering angle (by solid angle): the     */
+/* phase function used is that piecewise-constant one, which is sampled        */
+/* exactly (bin by its cumulative probability, then cos theta uniform in it).   */
+/* ------------------------------------------------------------------------- */
+int orc_mie_single(double x, double m_re, double m_im, const double* mu, int nmu, double* s11, double* qext,
+                   double* qsca) {
+    if (!(x > 0.0) || nmu < 0) return -1;
+    const double complex m = m_re + I * m_im, y = m * x;
+    const int nstop = (int)(x + 4.0 * cbrt(x) + 2.0);
+    const int nmx = (int)fmax((double)nstop, cabs(y)) + 16;
+    double complex* D = (double complex*)calloc((size_t)nmx + 1, sizeof(double complex));
+    double complex* S1 = (double complex*)calloc((size_t)(nmu > 0 ? nmu : 1), sizeof(double complex));
+    double complex* S2 = (double complex*)calloc((size_t)(nmu > 0 ? nmu : 1), sizeof(double complex));
+    double* pim1 = (double*)calloc((size_t)(nmu > 0 ? nmu : 1), sizeof(double));   /* pi_{n-1} */
+    double* pin = (double*)malloc(sizeof(double) * (size_t)(nmu > 0 ? nmu : 1));    /* pi_n */
+    for (int k = 0; k < nmu; ++k) pin[k] = 1.0;
+    /* logarithmic derivative D_n(y) by downward recurrence from D_nmx = 0 */
+    for (int n = nmx; n > 0; --n) D[n - 1] = (double)n / y - 1.0 / (D[n] + (double)n / y);
+    /* Riccati-Bessel functions psi_n, chi_n by upward recurrence, xi_n = psi_n - i chi_n */
+    double psi0 = cos(x), psi1 = sin(x), chi0 = -sin(x), chi1 = cos(x);
+    double complex xi1 = psi1 - I * chi1;
+    double qe = 0.0, qs = 0.0;
+    for (int n = 1; n <= nstop; ++n) {
+        const double dn = (double)n;
+        const double psi = (2.0 * dn - 1.0) / x * psi1 - psi0;
+        const double chi = (2.0 * dn - 1.0) / x * chi1 - chi0;
+        const double complex xi = psi - I * chi;
+        const double complex da = D[n] / m + dn / x, db = m * D[n] + dn / x;
+        const double complex an = (da * psi - psi1) / (da * xi - xi1);
+        const double complex bn = (db * psi - psi1) / (db * xi - xi1);
+        qs += (2.0 * dn + 1.0) * (creal(an) * creal(an) + cimag(an) * cimag(an) + creal(bn) * creal(bn) +
+                                  cimag(bn) * cimag(bn));
+        qe += (2.0 * dn + 1.0) * creal(an + bn);
+        const double fn = (2.0 * dn + 1.0) / (dn * (dn + 1.0));
+        for (int k = 0; k < nmu; ++k) {
+            const double pi = pin[k], tau = dn * mu[k] * pi - (dn + 1.0) * pim1[k];
+            S1[k] += fn * (an * pi + bn * tau);
+            S2[k] += fn * (an * tau + bn * pi);
+            /* pi_{n+1} = ((2n+1)/n) mu pi_n - ((n+1)/n) pi_{n-1} */
+            const double next = (2.0 * dn + 1.0) / dn * mu[k] * pi - (dn + 1.0) / dn * pim1[k];
+            pim1[k] = pi;
+            pin[k] = next;
+        }
+        psi0 = psi1; psi1 = psi;
+        chi0 = chi1; chi1 = chi;
+        xi1 = psi1 - I * chi1;
+    }
+    for (int k = 0; k < nmu; ++k) {
+        const double a1 = cabs(S1[k]), a2 = cabs(S2[k]);
+        s11[k] = 0.5 * (a1 * a1 + a2 * a2);
+    }
+    if (qext) *qext = 2.0 / (x * x) * qe;
+    if (qsca) *qsca = 2.0 / (x * x) * qs;
+    free(D); free(S1); free(S2); free(pim1); free(pin);
+    return 0;
+}
+
+static double lm_p[ORC_LM_BINS], lm_cdf[ORC_LM_BINS + 1], lm_cos[ORC_LM_BINS + 1];
+static int lm_ready = 0;
+
+static void lm_build(void) {
+    const double dth = ORC_PI / ORC_LM_BINS;
+    const int nf = 2 * ORC_LM_BINS + 1;                  /* bin edges and midpoints */
+    double* mu = (double*)malloc(sizeof(double) * nf);
+    double* acc = (double*)calloc((size_t)nf, sizeof(double));
+    double* s11 = (double*)malloc(sizeof(double) * nf);
+    for (int f = 0; f < nf; ++f) mu[f] = cos(0.5 * dth * f);
+    const double lambda = 0.55, k = 2.0 * ORC_PI / lambda;
+    for (int ir = 1; ir <= 160; ++ir) {                 /* r = 0.1 .. 16 um */
+        const double r = 0.1 * ir, w = pow(r, 6.0) * exp(-1.5 * r);
+        orc_mie_single(k * r, 1.333, 0.0, mu, nf, s11, NULL, NULL);
+        for (int f = 0; f < nf; ++f) acc[f] += w * s11[f];
+    }
+    double total = 0.0;
+    for (int j = 0; j < ORC_LM_BINS; ++j) {
+        const double t0 = dth * j, tm = t0 + 0.5 * dth, t1 = t0 + dth;
+        /* Simpson over the bin of i(theta) sin(theta) d theta, per unit solid angle */
+        const double integ = (acc[2 * j] * sin(t0) + 4.0 * acc[2 * j + 1] * sin(tm) + acc[2 * j + 2] * sin(t1)) *
+                             dth / 6.0;
+        const double dcos = cos(t0) - cos(t1);
+        lm_p[j] = integ / dcos;
+        total += 2.0 * ORC_PI * integ;
+    }
+    lm_cdf[0] = 0.0;
+    for (int j = 0; j < ORC_LM_BINS; ++j) {
+        lm_p[j] /= total;
+        lm_cos[j] = cos(dth * j);
+        lm_cdf[j + 1] = lm_cdf[j] + lm_p[j] * 2.0 * ORC_PI * (cos(dth * j) - cos(dth * (j + 1)));
+    }
+    lm_cos[ORC_LM_BINS] = -1.0;
+    lm_cdf[ORC_LM_BINS] = 1.0;
+    free(mu); free(acc); free(s11);
+    lm_ready = 1;
+}
+
+int orc_lm_table(double* p, double* cdf, double* cos_edges, int n) {
+    if (n != ORC_LM_BINS) return -1;
+    if (!lm_ready) lm_build();
+    for (int j = 0; j < n; ++j) { if (p) p[j] = lm_p[j]; }
+    for (int j = 0; j <= n; ++j) { if (cdf) cdf[j] = lm_cdf[j]; if (cos_edges) cos_edges[j] = lm_cos[j]; }
+    return 0;
+}
+
+void orc_set_phase_lm(orc_ctx* c, int on) {
+    if (on && !lm_ready) lm_build();
+    c->phase_lm = on != 0;
+}
+
+/* phase function of the volume at cos theta between propagation directions */
+static double phase_eval(const orc_ctx* c, double ct) {
+    if (!c->phase_lm) return orc_hg(c->g, ct);
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    int j = (int)(acos(ct) / (ORC_PI / ORC_LM_BINS));
+    if (j > ORC_LM_BINS - 1) j = ORC_LM_BINS - 1;
+    return lm_p[j];
+}
+
+/* new tracing direction: HG, or the tabulated Lorenz-Mie function (bin by its cumulative
+ * probability xi0, cos theta uniform inside the bin, azimuth 2 pi xi1) */
+static void phase_sample(const orc_ctx* c, const double d[3], double xi0, double xi1, double out[3]) {
+    if (!c->phase_lm) { orc_sample_hg(c->g, d, xi0, xi1, out); return; }
+    int lo = 0, hi = ORC_LM_BINS;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (lm_cdf[mid] <= xi0) lo = mid; else hi = mid;
+    }
+    const double f = (xi0 - lm_cdf[lo]) / (lm_cdf[lo + 1] - lm_cdf[lo]);
+    double ct = lm_cos[lo] - f * (lm_cos[lo] - lm_cos[lo + 1]);
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    const double st = sqrt(fmax(0.0, 1.0 - ct * ct)), phi = 2.0 * ORC_PI * xi1;
+    double b1[3], b2[3];
+    duff_basis(d, b1, b2);
+    for (int a = 0; a < 3; ++a) out[a] = st * cos(phi) * b1[a] + st * sin(phi) * b2[a] + ct * d[a];
+    normalize3(out);
+}
+
 /* Direct in-scattering by next-event estimation towards the directional light
  * (Sec. 4.4; MIS with phase sampling adds nothing for a delta light). */
 static double nee(const orc_ctx* c, const double x[3], const double d[3], const double wl[3],
@@ -874,7 +1021,7 @@ static double nee(const orc_ctx* c, const double x[3], const double d[3], const 
                   uint32_t* ctr) {
     double ct = d[0] * wl[0] + d[1] * wl[1] + d[2] * wl[2];
     double T = orc_ratio_track(c, x, wl, seed, id0, id1, dom, ctr, NULL);
-    return E * orc_hg(c->g, ct) * T;
+    return E * phase_eval(c, ct) * T;
 }
 
 /* One path estimate of the indirect in-scattered radiance L_i at vertex x reached with
@@ -892,7 +1039,7 @@ static double path_Li(const orc_ctx* c, const double x0[3], const double d0[3],
         double xi[4];
         draw(seed, id0, id1, ctr++, dom, xi);
         double nd[3];
-        orc_sample_hg(c->g, d, xi[0], xi[1], nd);
+        phase_sample(c, d, xi[0], xi[1], nd);
         double nx[3];
         /* a bounce starts inside the medium, where bricks hold nearly the global majorant:
          * track it against the global one (crossing bricks there only costs) */

@@ -113,6 +113,18 @@ int orc_delta_track(const orc_ctx* c, const double o[3], const double d[3], uint
 /* Ratio-tracking transmittance from o along d to the grid boundary. */
 double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
                        uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped);
+/* Lorenz-Mie scattering of one sphere (Bohren & Huffman 1983, App. A): size parameter x,
+ * relative refractive index m_re + i m_im; s11[k] = (|S1|^2 + |S2|^2) / 2 at cosines mu[k];
+ * extinction and scattering efficiencies. */
+int orc_mie_single(double x, double m_re, double m_im, const double* mu, int nmu, double* s11, double* qext,
+                   double* qsca);
+/* The tabulated cloud phase function (water, 0.55 um, Deirmendjian C.1 droplets): bin means
+ * p[ORC_LM_BINS] over 0.1-degree bins of scattering angle, cumulative probabilities
+ * cdf[ORC_LM_BINS + 1] and bin-edge cosines cos_edges[ORC_LM_BINS + 1]. */
+#define ORC_LM_BINS 1800
+int orc_lm_table(double* p, double* cdf, double* cos_edges, int n);
+/* Volume phase function: 0 Henyey-Greenstein with the volume's g, 1 the Lorenz-Mie table. */
+void orc_set_phase_lm(orc_ctx* c, int on);
 /* Henyey-Greenstein phase function of the cosine between propagation directions. */
 double orc_hg(double g, double cos_theta);
 /* New tracing direction scattered from tracing direction d, cosine ~ HG(g). */
