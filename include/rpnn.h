@@ -124,6 +124,22 @@ rpnn_status rpnn_set_mip_blend(rpnn_ctx* ctx, int32_t vol, int32_t on);
  * or a call that reads the count); the context stays usable.  For fault injection in tests
  * and for bounding the time of a render. */
 rpnn_status rpnn_set_iteration_cap(rpnn_ctx* ctx, int32_t vol, int64_t cap);
+/* Phase function of volume `vol` (Sec. 3.1): RPNN_PHASE_HG (the default; Henyey-Greenstein
+ * with the g given at rpnn_load_volume) or RPNN_PHASE_LORENZ_MIE, the cloud droplets'
+ * Lorenz-Mie function: the Mie series (Bohren & Huffman 1983) for water spheres (index
+ * 1.333) at 0.55 um over Deirmendjian's cumulus C.1 size distribution, averaged over
+ * RPNN_LM_BINS bins of 0.1 degree per unit solid angle.  It applies to next-event
+ * estimation and to the path tracer's direction sampling (label records, path mode), which
+ * samples a bin by its cumulative probability and cos(theta) uniformly inside it.  (The
+ * paper's own tables and its chopped variant are in its unavailable supplement.)
+ * Errors: RPNN_ERR_ARG for another kind. */
+enum { RPNN_PHASE_HG = 0, RPNN_PHASE_LORENZ_MIE = 1 };
+#define RPNN_LM_BINS 1800
+rpnn_status rpnn_set_phase_function(rpnn_ctx* ctx, int32_t vol, int32_t kind);
+/* Host copy of that table (no device work): bin values p[RPNN_LM_BINS] (per steradian),
+ * cumulative probabilities cdf[RPNN_LM_BINS + 1] and bin-edge cosines cos_edges[...];
+ * any pointer may be NULL.  Errors: RPNN_ERR_ARG unless n == RPNN_LM_BINS. */
+rpnn_status rpnn_lorenz_mie_table(double* p, double* cdf, double* cos_edges, int32_t n);
 /* Writes the tracking majorant grid as FP32 [bricks[2]][bricks[1]][bricks[0]] into dev_out:
  * delta and ratio tracking (Sec. 4.4) bound the density piecewise by bricks of 8^3 voxels,
  * brick b by the largest of the voxels its trilinear density interpolates (8b - 1 .. 8b + 8

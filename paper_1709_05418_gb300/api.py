@@ -26,6 +26,10 @@ ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_HANDLE", -3: "ERR_CUDA", -4: "ERR_
              -9: "ERR_TIMEOUT"}
 
 
+PHASE_HG, PHASE_LORENZ_MIE = 0, 1
+LM_BINS = 1800
+
+
 class RPNNError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -96,6 +100,7 @@ def load():
             "rpnn_copy_brick_majorants": [_vp, i32, _vp, _vp],
             "rpnn_set_mip_blend": [_vp, i32, i32],
             "rpnn_set_iteration_cap": [_vp, i32, i64],
+            "rpnn_set_phase_function": [_vp, i32, i32],
             "rpnn_set_autotune_table": [_vp, C.POINTER(TuneEntry), i32],
             "rpnn_dense_forward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp],
             "rpnn_dense_backward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp, _vp],
@@ -277,6 +282,10 @@ class Context:
             for f, _ in TuneEntry._fields_:
                 setattr(buf[i], f, e[f])
         self._check(self.L.rpnn_set_autotune_table(self.h, buf, len(table)))
+
+    def set_phase_function(self, vol: int, kind: int):
+        """PHASE_HG (default) or PHASE_LORENZ_MIE, the tabulated cloud-droplet function."""
+        self._check(self.L.rpnn_set_phase_function(self.h, vol, int(kind)))
 
     def set_iteration_cap(self, vol: int, cap: int):
         """Tentative collisions per tracking call through the volume (0: the default)."""

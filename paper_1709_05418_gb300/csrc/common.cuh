@@ -87,6 +87,38 @@ __device__ __forceinline__ float3 hg_sample(float g, float3 d, float xi0, float 
     return normalize3((st * cp) * b1 + (st * sp) * b2 + ct * d);
 }
 
+// The volume's phase function at cos theta between propagation directions: HG, or the
+// Lorenz-Mie table's value in the 0.1-degree bin of theta.
+__device__ __forceinline__ float phase_eval(const VolumeView& v, float ct) {
+    if (!v.lm) return hg_eval(v.g, ct);
+    const float th = acosf(fminf(fmaxf(ct, -1.0f), 1.0f));
+    const int j = min((int)(th * ((float)RPNN_LM_BINS / kPi)), RPNN_LM_BINS - 1);
+    return __ldg(v.lm + j);
+}
+
+// New tracing direction from the volume's phase function: HG, or a Lorenz-Mie bin chosen by
+// its cumulative probability xi0 with cos theta uniform inside it (azimuth 2 pi xi1).
+__device__ __forceinline__ float3 phase_sample(const VolumeView& v, float3 d, float xi0, float xi1) {
+    if (!v.lm) return hg_sample(v.g, d, xi0, xi1);
+    const float* cdf = v.lm + RPNN_LM_BINS;
+    const float* cb = v.lm + 2 * RPNN_LM_BINS + 1;
+    int lo = 0, hi = RPNN_LM_BINS;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(cdf + mid) <= xi0) lo = mid; else hi = mid;
+    }
+    const float c0 = __ldg(cdf + lo), c1 = __ldg(cdf + lo + 1);
+    const float f = c1 > c0 ? (xi0 - c0) / (c1 - c0) : 0.0f;
+    const float e0 = __ldg(cb + lo), e1 = __ldg(cb + lo + 1);
+    const float ct = fminf(fmaxf(e0 - f * (e0 - e1), -1.0f), 1.0f);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float sp, cp;
+    sincosf(2.0f * kPi * xi1, &sp, &cp);
+    float3 b1, b2;
+    duff_basis(d, b1, b2);
+    return normalize3((st * cp) * b1 + (st * sp) * b2 + ct * d);
+}
+
 // Ray / grid-box clip: [t0, t1] inside [0, ext].
 __device__ __forceinline__ bool box_clip(const float ext[3], float3 o, float3 d, float& t0, float& t1) {
     float tmin = 0.0f, tmax = INFINITY;
@@ -271,7 +303,7 @@ __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, floa
 __device__ __forceinline__ float nee(const VolumeView& v, float3 x, float3 d, float3 wl, float E,
                                      const Rng& rng, uint32_t& ctr, bool& capped) {
     const float T = ratio_track(v, x, wl, rng, ctr, capped);
-    return E * hg_eval(v.g, dot3(d, wl)) * T;
+    return E * phase_eval(v, dot3(d, wl)) * T;
 }
 
 // One path estimate of L_i at vertex x reached along tracing direction d: phase
@@ -284,7 +316,7 @@ __device__ __forceinline__ float path_Li(const VolumeView& v, float3 x, float3 d
     float L = 0.0f;
     for (int b = 0; b < kBounceCap; ++b) {
         float4 xi = rng.draw(ctr++);
-        const float3 nd = hg_sample(v.g, d, xi.x, xi.y);
+        const float3 nd = phase_sample(v, d, xi.x, xi.y);
         float3 nx;
         const int hit = delta_track_global(v, x, nd, rng, ctr, nx);
         if (hit < 0) { capped = true; return L; }

@@ -348,6 +348,7 @@ VolumeView Volume::view() const {
     w.bs = (float)((double)kBrick / (double)nmax);
     for (int k = 0; k < RPNN_K; ++k) w.mip_w[k] = mip_blend ? info.mip_weight[k] : 0.0f;
     w.track_cap = track_cap ? track_cap : kTrackCapDefault;
+    w.lm = lm;
     return w;
 }
 
