@@ -130,16 +130,25 @@ rpnn_status rpnn_set_iteration_cap(rpnn_ctx* ctx, int32_t vol, int64_t cap);
  * 1.333) at 0.55 um over Deirmendjian's cumulus C.1 size distribution, averaged over
  * RPNN_LM_BINS bins of 0.1 degree per unit solid angle.  It applies to next-event
  * estimation and to the path tracer's direction sampling (label records, path mode), which
- * samples a bin by its cumulative probability and cos(theta) uniformly inside it.  (The
- * paper's own tables and its chopped variant are in its unavailable supplement.)
- * Errors: RPNN_ERR_ARG for another kind. */
-enum { RPNN_PHASE_HG = 0, RPNN_PHASE_LORENZ_MIE = 1 };
+ * samples a bin by its cumulative probability and cos(theta) uniformly inside it.
+ * RPNN_PHASE_LORENZ_MIE_CHOPPED (Sec. 3.1, Sec. 5.1): the full function at a path's first
+ * bounce (the camera's or a training record's vertex); after it, the function without its
+ * diffraction peak (the RPNN_LM_CHOP_BINS bins below 5 degrees, holding the fraction f of
+ * the scattered light) renormalised, in a medium of extinction (1 - f albedo) mu_t and
+ * albedo (1 - f) albedo / (1 - f albedo); light reaches every vertex (next-event shadow
+ * rays) through that thinner medium, camera rays and record sampling see the full one.
+ * (The paper's own tables and chop angle are in its unavailable supplement.)
+ * Errors: RPNN_ERR_ARG for another kind, RPNN_ERR_HANDLE for an unknown volume. */
+enum { RPNN_PHASE_HG = 0, RPNN_PHASE_LORENZ_MIE = 1, RPNN_PHASE_LORENZ_MIE_CHOPPED = 2 };
 #define RPNN_LM_BINS 1800
+#define RPNN_LM_CHOP_BINS 50
 rpnn_status rpnn_set_phase_function(rpnn_ctx* ctx, int32_t vol, int32_t kind);
-/* Host copy of that table (no device work): bin values p[RPNN_LM_BINS] (per steradian),
- * cumulative probabilities cdf[RPNN_LM_BINS + 1] and bin-edge cosines cos_edges[...];
- * any pointer may be NULL.  Errors: RPNN_ERR_ARG unless n == RPNN_LM_BINS. */
-rpnn_status rpnn_lorenz_mie_table(double* p, double* cdf, double* cos_edges, int32_t n);
+/* Host copy of the full (chopped = 0) or chopped table (no device work): bin values
+ * p[RPNN_LM_BINS] (per steradian), cumulative probabilities cdf[RPNN_LM_BINS + 1], bin-edge
+ * cosines cos_edges[...] and the peak's fraction f; any pointer may be NULL.
+ * Errors: RPNN_ERR_ARG unless n == RPNN_LM_BINS. */
+rpnn_status rpnn_lorenz_mie_table(int32_t chopped, double* p, double* cdf, double* cos_edges, int32_t n,
+                                  double* peak_fraction);
 /* Writes the tracking majorant grid as FP32 [bricks[2]][bricks[1]][bricks[0]] into dev_out:
  * delta and ratio tracking (Sec. 4.4) bound the density piecewise by bricks of 8^3 voxels,
  * brick b by the largest of the voxels its trilinear density interpolates (8b - 1 .. 8b + 8

@@ -110,6 +110,16 @@ def lib():
             L.orc_lm_table.argtypes = [_dp, _dp, _dp, C.c_int]
             L.orc_set_phase_lm.argtypes = [C.c_void_p, C.c_int]
             L.orc_set_phase_lm.restype = None
+            L.orc_set_phase.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_chop_params.argtypes = [C.c_void_p, _dp, _dp, _dp]
+            L.orc_lm_chopped_table.argtypes = [C.c_void_p, _dp, _dp, C.c_int]
+            L.orc_delta_track_global_scaled.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_uint64,
+                                                        C.c_uint32, C.c_uint32, C.c_uint32,
+                                                        C.POINTER(C.c_uint32), _dp, _dp]
+            L.orc_ratio_track_scaled.restype = C.c_double
+            L.orc_ratio_track_scaled.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_uint64, C.c_uint32,
+                                                 C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
+                                                 C.POINTER(C.c_int)]
             L.orc_set_mip_blend.argtypes = [C.c_void_p, C.c_int]
             L.orc_set_mip_blend.restype = None
             L.orc_brick_majorant.restype = C.c_float
@@ -277,6 +287,7 @@ def dense_backward(params, widths, x, dout):
 
 
 LM_BINS = 1800
+LM_CHOP_BINS = 50       # the chopped diffraction peak: scattering angles below 5 degrees
 
 
 def mie_single(x, m_re, m_im, mu):
@@ -350,6 +361,22 @@ class Volume:
         """Tabulated Lorenz-Mie phase function instead of Henyey-Greenstein."""
         lib().orc_set_phase_lm(self.h, 1 if on else 0)
 
+    def set_phase(self, kind: int, chop_bins: int = LM_CHOP_BINS):
+        """0 HG, 1 Lorenz-Mie, 2 Lorenz-Mie at the first bounce and chopped (first chop_bins
+        bins removed) in the thinner medium after it."""
+        assert lib().orc_set_phase(self.h, int(kind), int(chop_bins)) == 0
+
+    def chop_params(self):
+        """(peak fraction f, extinction scale, albedo) after the first bounce."""
+        f, s, a = C.c_double(), C.c_double(), C.c_double()
+        assert lib().orc_chop_params(self.h, C.byref(f), C.byref(s), C.byref(a)) == 0
+        return f.value, s.value, a.value
+
+    def lm_chopped_table(self):
+        p, cdf = np.zeros(LM_BINS), np.zeros(LM_BINS + 1)
+        assert lib().orc_lm_chopped_table(self.h, _d(p), _d(cdf), LM_BINS) == 0
+        return p, cdf
+
     def set_mip_blend(self, on: bool):
         """Blended (fractional) mip selection for descriptors (off by default)."""
         lib().orc_set_mip_blend(self.h, 1 if on else 0)
@@ -384,20 +411,28 @@ class Volume:
         assert r == 0
         return out
 
-    def delta_track(self, o, d, seed, id0, id1, domain=2, global_majorant=False):
+    def delta_track(self, o, d, seed, id0, id1, domain=2, global_majorant=False, scale=None):
         """Delta tracking over the brick majorants (global_majorant: against the single
-        global majorant, the estimator the brick form must agree with in distribution)."""
+        global majorant, the estimator the brick form must agree with in distribution;
+        scale: against the global majorant in a medium of extinction scale * mu_t)."""
         o = _c64(o, (3,)); d = _c64(d, (3,))
         x = np.zeros(3); t = np.zeros(1)
         ctr = C.c_uint32(0)
+        if scale is not None:
+            r = lib().orc_delta_track_global_scaled(self.h, _d(o), _d(d), float(scale), seed, id0, id1,
+                                                    domain, C.byref(ctr), _d(x), _d(t))
+            return r, x, float(t[0])
         fn = lib().orc_delta_track_global if global_majorant else lib().orc_delta_track
         r = fn(self.h, _d(o), _d(d), seed, id0, id1, domain, C.byref(ctr), _d(x), _d(t))
         return r, x, float(t[0])
 
-    def ratio_track(self, o, d, seed, id0, id1, domain=3, global_majorant=False):
+    def ratio_track(self, o, d, seed, id0, id1, domain=3, global_majorant=False, scale=None):
         o = _c64(o, (3,)); d = _c64(d, (3,))
         ctr = C.c_uint32(0)
         capped = C.c_int(0)
+        if scale is not None:
+            return lib().orc_ratio_track_scaled(self.h, _d(o), _d(d), float(scale), seed, id0, id1, domain,
+                                                C.byref(ctr), C.byref(capped))
         fn = lib().orc_ratio_track_global if global_majorant else lib().orc_ratio_track
         T = fn(self.h, _d(o), _d(d), seed, id0, id1, domain, C.byref(ctr), C.byref(capped))
         return T

@@ -80,7 +80,13 @@ struct orc_ctx {
     orc_stats st;
     int nb[3];          /* bricks of ORC_BRICK^3 voxels per axis */
     int mip_blend;      /* descriptor blends levels m_k and m_k + 1 (orc_set_mip_blend) */
-    int phase_lm;       /* phase function: 0 Henyey-Greenstein (g), 1 tabulated Lorenz-Mie */
+    int phase_lm;       /* phase function: 0 Henyey-Greenstein (g), 1 tabulated Lorenz-Mie,
+                         * 2 Lorenz-Mie at the first bounce, chopped afterwards (orc_set_phase) */
+    double chop_f;      /* fraction of scattered light in the chopped forward peak */
+    double dscale;      /* extinction scale after the first bounce: 1 - f albedo (1 unchopped) */
+    double albedo_c;    /* albedo after the first bounce: albedo (1 - f) / (1 - f albedo) */
+    double* lmc_p;      /* chopped table: bin values, cumulative probabilities */
+    double* lmc_cdf;
     float* bmaj;        /* per-brick majorant [nb2][nb1][nb0] */
     double* mip64[ORC_MAX_LEVELS];
     float* mip32[ORC_MAX_LEVELS];
@@ -190,6 +196,8 @@ orc_ctx* orc_create(const float* density, int nx, int ny, int nz, double albedo,
     c->dens = (float*)malloc(sizeof(float) * nv);
     memcpy(c->dens, density, sizeof(float) * nv);
     c->albedo = albedo;
+    c->albedo_c = albedo;
+    c->dscale = 1.0;
     c->g = hg_g;
     compute_stats(c);
     if (c->st.nonzero == 0) { orc_destroy(c); return NULL; }
@@ -202,6 +210,8 @@ void orc_destroy(orc_ctx* c) {
     for (int i = 0; i < ORC_MAX_LEVELS; ++i) { free(c->mip64[i]); free(c->mip32[i]); }
     free(c->dens);
     free(c->bmaj);
+    free(c->lmc_p);
+    free(c->lmc_cdf);
     free(c);
 }
 
@@ -659,18 +669,21 @@ static int box_clip(const double ext[3], const double o[3], const double d[3], d
  * bounces (which start inside the medium) use it, and it is the estimator the brick
  * tracking below must agree with in distribution.  Each tentative
  * collision draws one Philox block: xi0 for the exponential step, xi1 for the
- * real/null decision (xi1 * majorant < mu_t). */
-int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
-                    uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, double x[3],
-                    double* t_out) {
+ * real/null decision (xi1 * majorant < mu_t).  The extinction is the grid's times s (the
+ * chopped medium's optically thinner volume, Sec. 3.1): the majorant s mu_max sets the
+ * step, and the real/null ratio s mu_t / (s mu_max) is the unscaled one. */
+int orc_delta_track_global_scaled(const orc_ctx* c, const double o[3], const double d[3], double s,
+                                  uint64_t seed, uint32_t id0, uint32_t id1, uint32_t domain,
+                                  uint32_t* ctr, double x[3], double* t_out) {
     double t0, t1;
     const double maj = (double)c->st.majorant;
     if (maj <= 0.0 || !box_clip(c->st.ext, o, d, &t0, &t1)) return 0;
+    const double maj_s = s * maj;
     double t = t0;
     for (uint32_t n = 0; n < TRACK_CAP; ++n) {
         double xi[4];
         draw(seed, id0, id1, (*ctr)++, domain, xi);
-        t -= log(1.0 - xi[0]) / maj;
+        t -= log(1.0 - xi[0]) / maj_s;
         if (t >= t1) return 0;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         double mu = orc_density(c, p);
@@ -681,6 +694,12 @@ int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3
         }
     }
     return -1;
+}
+
+int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                           uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, double x[3],
+                           double* t_out) {
+    return orc_delta_track_global_scaled(c, o, d, 1.0, seed, id0, id1, domain, ctr, x, t_out);
 }
 
 /* Ratio tracking (Novak et al. 2014, cited in Sec. 2) for the shadow-ray
@@ -806,9 +825,11 @@ int orc_delta_track(const orc_ctx* c, const double o[3], const double d[3], uint
 
 /* Ratio tracking (Novak et al. 2014, cited in Sec. 2) for the shadow-ray transmittance,
  * over the same walk: one Philox block (xi0 -> optical depth) per tentative collision,
- * T *= 1 - mu_t / mu_b there. */
-double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
-                       uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped) {
+ * T *= 1 - mu_t / mu_b there.  The extinction is the grid's times s (the chopped medium's
+ * thinner volume, Sec. 3.1): each brick's majorant rate is s mu_b, the ratio unchanged. */
+double orc_ratio_track_scaled(const orc_ctx* c, const double o[3], const double d[3], double s,
+                              uint64_t seed, uint32_t id0, uint32_t id1, uint32_t domain,
+                              uint32_t* ctr, int* capped) {
     double t0, t1;
     if (capped) *capped = 0;
     if (c->st.majorant <= 0.0f || !box_clip(c->st.ext, o, d, &t0, &t1)) return 1.0;
@@ -826,9 +847,10 @@ double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], u
                 tau = -log(1.0 - xi[0]);
                 fresh = 0;
             }
-            const double seg = mu_b * (te - t);
+            const double mu_s = s * mu_b;
+            const double seg = mu_s * (te - t);
             if (tau < seg) {
-                t += tau / mu_b;
+                t += tau / mu_s;
                 fresh = 1;
                 double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
                 T *= 1.0 - orc_density(c, p) / mu_b;
@@ -842,6 +864,11 @@ double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], u
     }
     if (capped) *capped = 1;
     return T;
+}
+
+double orc_ratio_track(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
+                       uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped) {
+    return orc_ratio_track_scaled(c, o, d, 1.0, seed, id0, id1, domain, ctr, capped);
 }
 
 static void normalize3(double v[3]) {
@@ -979,31 +1006,82 @@ int orc_lm_table(double* p, double* cdf, double* cos_edges, int n) {
     return 0;
 }
 
-void orc_set_phase_lm(orc_ctx* c, int on) {
-    if (on && !lm_ready) lm_build();
-    c->phase_lm = on != 0;
+/* The chopped table (Sec. 3.1, after Bouthors et al. 2008): the first `chop_bins` bins (the
+ * diffraction peak) hold the fraction f of the scattered light; they are removed and the
+ * rest renormalised by 1 / (1 - f).  Light scattered into the peak is treated as not
+ * scattered at all, so the scattering coefficient drops to (1 - f) mu_s while absorption
+ * stays: extinction (1 - f albedo) mu_t, albedo (1 - f) albedo / (1 - f albedo). */
+static void chop_build(orc_ctx* c, int chop_bins) {
+    const double dth = ORC_PI / ORC_LM_BINS;
+    if (!c->lmc_p) c->lmc_p = (double*)malloc(sizeof(double) * ORC_LM_BINS);
+    if (!c->lmc_cdf) c->lmc_cdf = (double*)malloc(sizeof(double) * (ORC_LM_BINS + 1));
+    double f = 0.0;
+    for (int j = 0; j < chop_bins; ++j) f += lm_p[j] * 2.0 * ORC_PI * (cos(dth * j) - cos(dth * (j + 1)));
+    c->lmc_cdf[0] = 0.0;
+    for (int j = 0; j < ORC_LM_BINS; ++j) {
+        c->lmc_p[j] = j < chop_bins ? 0.0 : lm_p[j] / (1.0 - f);
+        c->lmc_cdf[j + 1] = c->lmc_cdf[j] + c->lmc_p[j] * 2.0 * ORC_PI * (cos(dth * j) - cos(dth * (j + 1)));
+    }
+    c->lmc_cdf[ORC_LM_BINS] = 1.0;
+    c->chop_f = f;
+    c->dscale = 1.0 - f * c->albedo;
+    c->albedo_c = c->albedo * (1.0 - f) / (1.0 - f * c->albedo);
 }
 
-/* phase function of the volume at cos theta between propagation directions */
-static double phase_eval(const orc_ctx* c, double ct) {
+int orc_set_phase(orc_ctx* c, int kind, int chop_bins) {
+    if (!c || kind < 0 || kind > 2 || chop_bins < 0 || chop_bins >= ORC_LM_BINS) return -1;
+    if (kind > 0 && !lm_ready) lm_build();
+    c->phase_lm = kind;
+    c->chop_f = 0.0;
+    c->dscale = 1.0;
+    c->albedo_c = c->albedo;
+    if (kind == 2) chop_build(c, chop_bins);
+    return 0;
+}
+
+void orc_set_phase_lm(orc_ctx* c, int on) {
+    orc_set_phase(c, on ? 1 : 0, 0);
+}
+
+int orc_chop_params(const orc_ctx* c, double* f, double* dscale, double* albedo_c) {
+    if (!c) return -1;
+    if (f) *f = c->chop_f;
+    if (dscale) *dscale = c->dscale;
+    if (albedo_c) *albedo_c = c->albedo_c;
+    return 0;
+}
+
+int orc_lm_chopped_table(const orc_ctx* c, double* p, double* cdf, int n) {
+    if (!c || c->phase_lm != 2 || n != ORC_LM_BINS) return -1;
+    for (int j = 0; j < n; ++j) { if (p) p[j] = c->lmc_p[j]; }
+    for (int j = 0; j <= n; ++j) { if (cdf) cdf[j] = c->lmc_cdf[j]; }
+    return 0;
+}
+
+/* phase function of the volume at cos theta between propagation directions, at the first
+ * bounce of a path (the camera's or a record's vertex) or after it */
+static double phase_eval(const orc_ctx* c, int first, double ct) {
     if (!c->phase_lm) return orc_hg(c->g, ct);
+    const double* tp = (c->phase_lm == 2 && !first) ? c->lmc_p : lm_p;
     if (ct > 1.0) ct = 1.0;
     if (ct < -1.0) ct = -1.0;
     int j = (int)(acos(ct) / (ORC_PI / ORC_LM_BINS));
     if (j > ORC_LM_BINS - 1) j = ORC_LM_BINS - 1;
-    return lm_p[j];
+    return tp[j];
 }
 
 /* new tracing direction: HG, or the tabulated Lorenz-Mie function (bin by its cumulative
  * probability xi0, cos theta uniform inside the bin, azimuth 2 pi xi1) */
-static void phase_sample(const orc_ctx* c, const double d[3], double xi0, double xi1, double out[3]) {
+static void phase_sample(const orc_ctx* c, int first, const double d[3], double xi0, double xi1,
+                         double out[3]) {
     if (!c->phase_lm) { orc_sample_hg(c->g, d, xi0, xi1, out); return; }
+    const double* cdf = (c->phase_lm == 2 && !first) ? c->lmc_cdf : lm_cdf;
     int lo = 0, hi = ORC_LM_BINS;
     while (hi - lo > 1) {
         const int mid = (lo + hi) / 2;
-        if (lm_cdf[mid] <= xi0) lo = mid; else hi = mid;
+        if (cdf[mid] <= xi0) lo = mid; else hi = mid;
     }
-    const double f = (xi0 - lm_cdf[lo]) / (lm_cdf[lo + 1] - lm_cdf[lo]);
+    const double f = (xi0 - cdf[lo]) / (cdf[lo + 1] - cdf[lo]);
     double ct = lm_cos[lo] - f * (lm_cos[lo] - lm_cos[lo + 1]);
     if (ct > 1.0) ct = 1.0;
     if (ct < -1.0) ct = -1.0;
@@ -1015,13 +1093,15 @@ static void phase_sample(const orc_ctx* c, const double d[3], double xi0, double
 }
 
 /* Direct in-scattering by next-event estimation towards the directional light
- * (Sec. 4.4; MIS with phase sampling adds nothing for a delta light). */
-static double nee(const orc_ctx* c, const double x[3], const double d[3], const double wl[3],
+ * (Sec. 4.4; MIS with phase sampling adds nothing for a delta light).  `first`: the vertex
+ * is a path's first bounce, which scatters with the full phase function; the light reaches
+ * every vertex through the (chopped medium's) extinction dscale mu_t. */
+static double nee(const orc_ctx* c, int first, const double x[3], const double d[3], const double wl[3],
                   double E, uint64_t seed, uint32_t id0, uint32_t id1, uint32_t dom,
                   uint32_t* ctr) {
     double ct = d[0] * wl[0] + d[1] * wl[1] + d[2] * wl[2];
-    double T = orc_ratio_track(c, x, wl, seed, id0, id1, dom, ctr, NULL);
-    return E * phase_eval(c, ct) * T;
+    double T = orc_ratio_track_scaled(c, x, wl, c->dscale, seed, id0, id1, dom, ctr, NULL);
+    return E * phase_eval(c, first, ct) * T;
 }
 
 /* One path estimate of the indirect in-scattered radiance L_i at vertex x reached with
@@ -1039,16 +1119,18 @@ static double path_Li(const orc_ctx* c, const double x0[3], const double d0[3],
         double xi[4];
         draw(seed, id0, id1, ctr++, dom, xi);
         double nd[3];
-        phase_sample(c, d, xi[0], xi[1], nd);
+        /* x0 is the path's first bounce (full phase function); later vertices scatter
+         * with the chopped one where the volume is set so (Sec. 3.1) */
+        phase_sample(c, b == 0, d, xi[0], xi[1], nd);
         double nx[3];
         /* a bounce starts inside the medium, where bricks hold nearly the global majorant:
          * track it against the global one (crossing bricks there only costs) */
-        int hit = orc_delta_track_global(c, x, nd, seed, id0, id1, dom, &ctr, nx, NULL);
+        int hit = orc_delta_track_global_scaled(c, x, nd, c->dscale, seed, id0, id1, dom, &ctr, nx, NULL);
         if (hit < 0) { if (capped) *capped = 1; return L; }
         if (hit == 0) return L;
         draw(seed, id0, id1, ctr++, dom, xi);
-        if (!(xi[0] < c->albedo)) return L;    /* absorbed */
-        L += nee(c, nx, nd, wl, E, seed, id0, id1, dom, &ctr);
+        if (!(xi[0] < c->albedo_c)) return L;    /* absorbed */
+        L += nee(c, 0, nx, nd, wl, E, seed, id0, id1, dom, &ctr);
         x[0] = nx[0]; x[1] = nx[1]; x[2] = nx[2];
         d[0] = nd[0]; d[1] = nd[1]; d[2] = nd[2];
     }
@@ -1072,7 +1154,7 @@ int orc_primary(const orc_ctx* c, const orc_camera* cam, int64_t pixel, int samp
                               DOM_PRIMARY, &ctr, x, NULL);
     if (hit != 1) { *Ld = 0.0; return hit; }
     uint32_t sc = 0;
-    *Ld = nee(c, x, d, cam->light_dir, cam->light_E, cam->seed, (uint32_t)pixel,
+    *Ld = nee(c, 1, x, d, cam->light_dir, cam->light_E, cam->seed, (uint32_t)pixel,
               (uint32_t)sample, DOM_SHADOW, &sc);
     return 1;
 }

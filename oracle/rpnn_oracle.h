@@ -103,6 +103,14 @@ int orc_delta_track_global(const orc_ctx* c, const double o[3], const double d[3
                            double x[3], double* t_out);
 double orc_ratio_track_global(const orc_ctx* c, const double o[3], const double d[3], uint64_t seed,
                               uint32_t id0, uint32_t id1, uint32_t domain, uint32_t* ctr, int* capped);
+/* The same estimators in a medium of extinction s mu_t (the chopped medium after the first
+ * bounce, Sec. 3.1); s = 1 gives the functions above exactly. */
+int orc_delta_track_global_scaled(const orc_ctx* c, const double o[3], const double d[3], double s,
+                                  uint64_t seed, uint32_t id0, uint32_t id1, uint32_t domain,
+                                  uint32_t* ctr, double x[3], double* t_out);
+double orc_ratio_track_scaled(const orc_ctx* c, const double o[3], const double d[3], double s,
+                              uint64_t seed, uint32_t id0, uint32_t id1, uint32_t domain,
+                              uint32_t* ctr, int* capped);
 
 /* Free flight by delta tracking from o along unit d inside the unit-box grid.
  * RNG counter (id0, id1, step, domain).  Returns 1 on collision (x written, t), 0
@@ -123,8 +131,17 @@ int orc_mie_single(double x, double m_re, double m_im, const double* mu, int nmu
  * cdf[ORC_LM_BINS + 1] and bin-edge cosines cos_edges[ORC_LM_BINS + 1]. */
 #define ORC_LM_BINS 1800
 int orc_lm_table(double* p, double* cdf, double* cos_edges, int n);
-/* Volume phase function: 0 Henyey-Greenstein with the volume's g, 1 the Lorenz-Mie table. */
-void orc_set_phase_lm(orc_ctx* c, int on);
+/* Volume phase function: 0 Henyey-Greenstein with the volume's g, 1 the Lorenz-Mie table,
+ * 2 the Lorenz-Mie table at a path's first bounce and, after it, the table with its first
+ * chop_bins bins (the diffraction peak, fraction f of the scattered light) removed and
+ * renormalised, in a medium of extinction (1 - f albedo) mu_t and albedo
+ * (1 - f) albedo / (1 - f albedo) (Sec. 3.1).  -1 on a bad kind or bin count. */
+int orc_set_phase(orc_ctx* c, int kind, int chop_bins);
+void orc_set_phase_lm(orc_ctx* c, int on);     /* orc_set_phase(c, on ? 1 : 0, 0) */
+/* f, the extinction scale and the albedo after the first bounce (0, 1, albedo unchopped) */
+int orc_chop_params(const orc_ctx* c, double* f, double* dscale, double* albedo_c);
+/* the chopped table (kind 2 only): bin values p[n], cumulative probabilities cdf[n + 1] */
+int orc_lm_chopped_table(const orc_ctx* c, double* p, double* cdf, int n);
 /* Henyey-Greenstein phase function of the cosine between propagation directions. */
 double orc_hg(double g, double cos_theta);
 /* New tracing direction scattered from tracing direction d, cosine ~ HG(g). */

@@ -26,8 +26,8 @@ ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_HANDLE", -3: "ERR_CUDA", -4: "ERR_
              -9: "ERR_TIMEOUT"}
 
 
-PHASE_HG, PHASE_LORENZ_MIE = 0, 1
-LM_BINS = 1800
+PHASE_HG, PHASE_LORENZ_MIE, PHASE_LORENZ_MIE_CHOPPED = 0, 1, 2
+LM_BINS, LM_CHOP_BINS = 1800, 50
 
 
 class RPNNError(RuntimeError):
@@ -284,7 +284,9 @@ class Context:
         self._check(self.L.rpnn_set_autotune_table(self.h, buf, len(table)))
 
     def set_phase_function(self, vol: int, kind: int):
-        """PHASE_HG (default) or PHASE_LORENZ_MIE, the tabulated cloud-droplet function."""
+        """PHASE_HG (default), PHASE_LORENZ_MIE (the tabulated cloud-droplet function) or
+        PHASE_LORENZ_MIE_CHOPPED (full at a path's first bounce, chopped after it in the
+        correspondingly thinner medium)."""
         self._check(self.L.rpnn_set_phase_function(self.h, vol, int(kind)))
 
     def set_iteration_cap(self, vol: int, cap: int):

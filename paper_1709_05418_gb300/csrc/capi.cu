@@ -112,7 +112,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
-                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16, &c->lm_table};
+                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16, &c->lm_table, &c->lmc_table};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
@@ -197,13 +197,24 @@ rpnn_status rpnn_set_phase_function(rpnn_ctx* ctx, int32_t vol, int32_t kind) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     Volume* v = get_vol(c, vol, false);
     if (!v) return RPNN_ERR_HANDLE;
-    if (kind != RPNN_PHASE_HG && kind != RPNN_PHASE_LORENZ_MIE) { set_error("unknown phase function %d", kind); return RPNN_ERR_ARG; }
-    if (kind == RPNN_PHASE_LORENZ_MIE) {
+    if (kind != RPNN_PHASE_HG && kind != RPNN_PHASE_LORENZ_MIE && kind != RPNN_PHASE_LORENZ_MIE_CHOPPED) {
+        set_error("unknown phase function %d", kind);
+        return RPNN_ERR_ARG;
+    }
+    v->lm = v->lmc = nullptr;
+    v->dscale = 1.0f;
+    v->albedo_c = 0.0f;
+    if (kind != RPNN_PHASE_HG) {
         rpnn_status st = phase_lm_upload(*c, nullptr);
         if (st) return st;
         v->lm = c->lm_table.as<float>();
-    } else {
-        v->lm = nullptr;
+        v->lmc = v->lm;
+    }
+    if (kind == RPNN_PHASE_LORENZ_MIE_CHOPPED) {
+        const double f = phase_lm_chop_fraction(), a = (double)v->albedo;
+        v->lmc = c->lmc_table.as<float>();
+        v->dscale = (float)(1.0 - f * a);
+        v->albedo_c = (float)(a * (1.0 - f) / (1.0 - f * a));
     }
     ++c->epoch;
     return RPNN_OK;

@@ -87,21 +87,23 @@ __device__ __forceinline__ float3 hg_sample(float g, float3 d, float xi0, float 
     return normalize3((st * cp) * b1 + (st * sp) * b2 + ct * d);
 }
 
-// The volume's phase function at cos theta between propagation directions: HG, or the
-// Lorenz-Mie table's value in the 0.1-degree bin of theta.
-__device__ __forceinline__ float phase_eval(const VolumeView& v, float ct) {
-    if (!v.lm) return hg_eval(v.g, ct);
+// The volume's phase function at cos theta between propagation directions: HG (tab null),
+// or the table's value in the 0.1-degree bin of theta.  tab is the volume's first-bounce
+// table (v.lm) or the one after the first bounce (v.lmc, chopped or the same).
+__device__ __forceinline__ float phase_eval(const VolumeView& v, const float* tab, float ct) {
+    if (!tab) return hg_eval(v.g, ct);
     const float th = acosf(fminf(fmaxf(ct, -1.0f), 1.0f));
     const int j = min((int)(th * ((float)RPNN_LM_BINS / kPi)), RPNN_LM_BINS - 1);
-    return __ldg(v.lm + j);
+    return __ldg(tab + j);
 }
 
-// New tracing direction from the volume's phase function: HG, or a Lorenz-Mie bin chosen by
+// New tracing direction from the phase function: HG (tab null), or a table bin chosen by
 // its cumulative probability xi0 with cos theta uniform inside it (azimuth 2 pi xi1).
-__device__ __forceinline__ float3 phase_sample(const VolumeView& v, float3 d, float xi0, float xi1) {
-    if (!v.lm) return hg_sample(v.g, d, xi0, xi1);
-    const float* cdf = v.lm + RPNN_LM_BINS;
-    const float* cb = v.lm + 2 * RPNN_LM_BINS + 1;
+__device__ __forceinline__ float3 phase_sample(const VolumeView& v, const float* tab, float3 d, float xi0,
+                                               float xi1) {
+    if (!tab) return hg_sample(v.g, d, xi0, xi1);
+    const float* cdf = tab + RPNN_LM_BINS;
+    const float* cb = tab + 2 * RPNN_LM_BINS + 1;
     int lo = 0, hi = RPNN_LM_BINS;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -248,14 +250,17 @@ __device__ __forceinline__ int delta_track(const VolumeView& v, float3 o, float3
 // Delta tracking against the global majorant (one block per tentative collision: x for
 // the exponential step, y for the real/null decision), for the path tracer's bounces,
 // which start inside the medium where the bricks hold nearly the global majorant anyway.
+// The medium behind a first bounce has extinction v.dscale * mu_t (the chopped
+// Lorenz-Mie medium; 1 otherwise): the majorant's rate scales, the real/null ratio not.
 __device__ __forceinline__ int delta_track_global(const VolumeView& v, float3 o, float3 d, const Rng& rng,
                                                   uint32_t& ctr, float3& x) {
     float t0, t1;
     if (v.majorant <= 0.0f || !box_clip(v.ext, o, d, t0, t1)) return 0;
+    const float maj_s = v.majorant * v.dscale;
     float t = t0;
     for (uint32_t n = 0; n < v.track_cap; ++n) {
         const float4 xi = rng.draw(ctr++);
-        t -= logf(1.0f - xi.x) / v.majorant;
+        t -= logf(1.0f - xi.x) / maj_s;
         if (t >= t1) return 0;
         const float3 p = o + t * d;
         if (xi.y * v.majorant < raw_density(v, p)) { x = p; return 1; }
@@ -265,6 +270,8 @@ __device__ __forceinline__ int delta_track_global(const VolumeView& v, float3 o,
 
 // Ratio-tracking transmittance from o along d to the grid boundary over the same walk:
 // one block (x -> optical depth) per tentative collision, T *= 1 - mu_t / mu_b there.
+// Light travels through the medium of extinction v.dscale * mu_t (see delta_track_global):
+// each brick's rate is v.dscale * mu_b, the ratio unchanged.
 __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, float3 d, const Rng& rng,
                                              uint32_t& ctr, bool& capped) {
     float t0, t1;
@@ -281,9 +288,10 @@ __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, floa
                 tau = -logf(1.0f - rng.draw(ctr++).x);
                 fresh = false;
             }
-            const float seg = mu_b * (te - t);
+            const float mu_s = mu_b * v.dscale;
+            const float seg = mu_s * (te - t);
             if (tau < seg) {
-                t += tau / mu_b;
+                t += tau / mu_s;
                 fresh = true;
                 T *= 1.0f - raw_density(v, o + t * d) / mu_b;
                 continue;
@@ -299,31 +307,35 @@ __device__ __forceinline__ float ratio_track(const VolumeView& v, float3 o, floa
 }
 
 // Next-event estimate towards the directional light (the phase argument is the
-// cosine between tracing direction d and the light direction).
-__device__ __forceinline__ float nee(const VolumeView& v, float3 x, float3 d, float3 wl, float E,
+// cosine between tracing direction d and the light direction).  `first`: x is a path's
+// first bounce (the camera's or a record's vertex), which scatters with the full phase
+// function; later vertices use the one after the first bounce.
+__device__ __forceinline__ float nee(const VolumeView& v, bool first, float3 x, float3 d, float3 wl, float E,
                                      const Rng& rng, uint32_t& ctr, bool& capped) {
     const float T = ratio_track(v, x, wl, rng, ctr, capped);
-    return E * phase_eval(v, dot3(d, wl)) * T;
+    return E * phase_eval(v, first ? v.lm : v.lmc, dot3(d, wl)) * T;
 }
 
 // One path estimate of L_i at vertex x reached along tracing direction d: phase
 // sampling, delta tracking to the next collision, survival with probability albedo,
 // NEE there, repeat.  Draw order per bounce: direction block, tracking blocks,
-// survival block, shadow blocks.
+// survival block, shadow blocks.  x is the path's first bounce (full phase function);
+// everything after it uses the medium behind the first bounce (v.lmc, v.dscale,
+// v.albedo_c), which is the volume's own unless its Lorenz-Mie function is chopped.
 __device__ __forceinline__ float path_Li(const VolumeView& v, float3 x, float3 d, float3 wl, float E,
                                          const Rng& rng, bool& capped) {
     uint32_t ctr = 0;
     float L = 0.0f;
     for (int b = 0; b < kBounceCap; ++b) {
         float4 xi = rng.draw(ctr++);
-        const float3 nd = phase_sample(v, d, xi.x, xi.y);
+        const float3 nd = phase_sample(v, b == 0 ? v.lm : v.lmc, d, xi.x, xi.y);
         float3 nx;
         const int hit = delta_track_global(v, x, nd, rng, ctr, nx);
         if (hit < 0) { capped = true; return L; }
         if (hit == 0) return L;
         xi = rng.draw(ctr++);
-        if (!(xi.x < v.albedo)) return L;
-        L += nee(v, nx, nd, wl, E, rng, ctr, capped);
+        if (!(xi.x < v.albedo_c)) return L;
+        L += nee(v, false, nx, nd, wl, E, rng, ctr, capped);
         x = nx;
         d = nd;
     }

@@ -77,7 +77,10 @@ struct VolumeView {
     float bs;                // brick edge in world units (kBrick / max(n))
     float mip_w[RPNN_K];     // blended descriptor: weight of level mip_of_level[k] + 1 (0: off)
     uint32_t track_cap;      // tentative collisions (and brick steps) per tracking call
-    const float* lm;         // Lorenz-Mie table (p[N], cdf[N+1], cos[N+1]) or null: HG with g
+    const float* lm;         // first-bounce Lorenz-Mie table (p[N], cdf[N+1], cos[N+1]) or null: HG
+    const float* lmc;        // the table after the first bounce (chopped or = lm; null: HG)
+    float dscale;            // extinction scale after the first bounce (1 unless chopped)
+    float albedo_c;          // albedo after the first bounce (= albedo unless chopped)
 };
 
 struct Volume {
@@ -91,7 +94,9 @@ struct Volume {
     int nb[3] = {0, 0, 0};
     bool mip_blend = false;  // descriptor blends levels m_k and m_k + 1
     uint32_t track_cap = 0;  // 0: the default cap (rpnn_set_iteration_cap)
-    const float* lm = nullptr;  // the context's Lorenz-Mie table when selected
+    const float* lm = nullptr;   // the context's Lorenz-Mie table when selected
+    const float* lmc = nullptr;  // the table after the first bounce (chopped or = lm)
+    float dscale = 1.0f, albedo_c = 0.0f;  // chopped medium (albedo_c 0: = albedo)
     bool built = false;
     int levels = 0;
     int dims[kMaxLevels][3] = {};
@@ -186,6 +191,7 @@ struct Ctx {
     int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
     DevBuf lm_table;         // Lorenz-Mie phase table, uploaded on first use
+    DevBuf lmc_table;        // its chopped form, same layout
     std::unordered_map<TmapKey, TmapBytes, TmapKeyHash> tmaps;   // BF16 GEMM operand maps
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
@@ -238,6 +244,8 @@ rpnn_status launch_nee_env(Ctx& c, const VolumeView& vv, const rpnn_render_desc&
                            const float* E, int j0, int n, float* sample_val, cudaStream_t s);
 // uploads the Lorenz-Mie phase table to c.lm_table once (synchronises s)
 rpnn_status phase_lm_upload(Ctx& c, cudaStream_t s);
+// fraction of the scattered light in the chopped peak (RPNN_LM_CHOP_BINS bins)
+double phase_lm_chop_fraction();
 // RPNN_ERR_NONFINITE if any of the n values is NaN or Inf (synchronises s)
 rpnn_status check_finite(Ctx& c, const float* p, int64_t n, cudaStream_t s);
 // sample_val[qps[i]] += scale * g[i] for i < *qcount

@@ -9,6 +9,12 @@
 // edges and midpoint).  The tracking kernels use that piecewise-constant function: they
 // read a bin's value for next-event estimation and sample a bin by its cumulative
 // probability, then cos(theta) uniformly inside it.
+//
+// The chopped form (after Bouthors et al. 2008, as Sec. 3.1 takes it) removes the
+// diffraction peak, the bins below 5 degrees holding the fraction f of the scattered light,
+// and renormalises the rest by 1 / (1 - f); the light scattered into the peak counts as
+// not scattered, so the medium behind a path's first bounce has extinction (1 - f albedo)
+// mu_t and albedo (1 - f) albedo / (1 - f albedo).
 #include <cmath>
 #include <complex>
 #include <mutex>
@@ -64,6 +70,8 @@ void sphere_intensity(double x, cplx m, const std::vector<double>& cs, std::vect
 
 struct LmTable {
     std::vector<double> p, cdf, cosb;
+    std::vector<double> pc, cdfc;   // chopped
+    double f = 0.0;                 // fraction in the chopped peak
 };
 
 const LmTable& lm_table() {
@@ -99,25 +107,46 @@ const LmTable& lm_table() {
         }
         T.cosb[N] = -1.0;
         T.cdf[N] = 1.0;
+        const int K = RPNN_LM_CHOP_BINS;
+        T.f = T.cdf[K];
+        T.pc.assign(N, 0.0);
+        T.cdfc.assign(N + 1, 0.0);
+        for (int j = K; j < N; ++j) {
+            T.pc[j] = T.p[j] / (1.0 - T.f);
+            T.cdfc[j + 1] = (T.cdf[j + 1] - T.f) / (1.0 - T.f);
+        }
+        T.cdfc[N] = 1.0;
     });
     return T;
 }
 
-}  // namespace
-
-rpnn_status phase_lm_upload(Ctx& c, cudaStream_t s) {
-    if (c.lm_table.p) return RPNN_OK;
-    const LmTable& T = lm_table();
+// one table as floats [p (N) | cdf (N + 1) | cos edges (N + 1)]
+std::vector<float> pack(const std::vector<double>& p, const std::vector<double>& cdf,
+                        const std::vector<double>& cosb) {
     const int N = RPNN_LM_BINS;
     std::vector<float> h(3 * (size_t)N + 2);
-    for (int j = 0; j < N; ++j) h[j] = (float)T.p[j];
+    for (int j = 0; j < N; ++j) h[j] = (float)p[j];
     for (int j = 0; j <= N; ++j) {
-        h[N + j] = (float)T.cdf[j];
-        h[2 * N + 1 + j] = (float)T.cosb[j];
+        h[N + j] = (float)cdf[j];
+        h[2 * N + 1 + j] = (float)cosb[j];
     }
-    rpnn_status st = c.lm_table.reserve(h.size() * sizeof(float));
+    return h;
+}
+
+}  // namespace
+
+double phase_lm_chop_fraction() { return lm_table().f; }
+
+rpnn_status phase_lm_upload(Ctx& c, cudaStream_t s) {
+    if (c.lm_table.p && c.lmc_table.p) return RPNN_OK;
+    const LmTable& T = lm_table();
+    const std::vector<float> full = pack(T.p, T.cdf, T.cosb), chopped = pack(T.pc, T.cdfc, T.cosb);
+    const size_t bytes = full.size() * sizeof(float);
+    rpnn_status st = c.lm_table.reserve(bytes);
+    if (!st) st = c.lmc_table.reserve(bytes);
     if (st) return st;
-    RPNN_CUDA_TRY(cudaMemcpyAsync(c.lm_table.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c.lm_table.p, full.data(), bytes, cudaMemcpyHostToDevice, s));
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c.lmc_table.p, chopped.data(), bytes, cudaMemcpyHostToDevice, s));
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
     return RPNN_OK;
 }
@@ -126,17 +155,21 @@ rpnn_status phase_lm_upload(Ctx& c, cudaStream_t s) {
 
 using namespace rpnn;
 
-extern "C" rpnn_status rpnn_lorenz_mie_table(double* p, double* cdf, double* cos_edges, int32_t n) {
+extern "C" rpnn_status rpnn_lorenz_mie_table(int32_t chopped, double* p, double* cdf, double* cos_edges,
+                                              int32_t n, double* peak_fraction) {
     if (n != RPNN_LM_BINS) {
         set_error("the table has %d bins", RPNN_LM_BINS);
         return RPNN_ERR_ARG;
     }
     const LmTable& T = lm_table();
+    const std::vector<double>& tp = chopped ? T.pc : T.p;
+    const std::vector<double>& tc = chopped ? T.cdfc : T.cdf;
     for (int j = 0; j < n; ++j)
-        if (p) p[j] = T.p[j];
+        if (p) p[j] = tp[j];
     for (int j = 0; j <= n; ++j) {
-        if (cdf) cdf[j] = T.cdf[j];
+        if (cdf) cdf[j] = tc[j];
         if (cos_edges) cos_edges[j] = T.cosb[j];
     }
+    if (peak_fraction) *peak_fraction = T.f;
     return RPNN_OK;
 }

@@ -54,7 +54,7 @@ k_primary(const VolumeView v, const RenderArgs a, int64_t P, float* __restrict__
         if (hit) {
             const float3 wl = f3(a.wl[0], a.wl[1], a.wl[2]);
             uint32_t c2 = 0;
-            Ld = nee(v, x, d, wl, a.E, make_rng(a.seed, pixel, s, kDomShadow), c2, capped);
+            Ld = nee(v, true, x, d, wl, a.E, make_rng(a.seed, pixel, s, kDomShadow), c2, capped);
             float Li = 0.0f;
             if (a.mode == RPNN_MODE_PATH)
                 Li = path_Li(v, x, d, wl, a.E, make_rng(a.seed, pixel, s, kDomPath), capped);
@@ -118,7 +118,7 @@ k_nee_env(const VolumeView v, const RenderArgs a, const float* __restrict__ qx, 
     float Ld = 0.0f;
     for (int j = j0; j < n; ++j) {
         uint32_t ctr = 0;
-        Ld += nee(v, x, d, f3(dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]), E[j], rng, ctr, capped);
+        Ld += nee(v, true, x, d, f3(dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]), E[j], rng, ctr, capped);
     }
     if (capped) raise_status(status, kStatIterLimit);
     sample_val[ps] += v.albedo * Ld;

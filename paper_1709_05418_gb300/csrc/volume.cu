@@ -349,6 +349,9 @@ VolumeView Volume::view() const {
     for (int k = 0; k < RPNN_K; ++k) w.mip_w[k] = mip_blend ? info.mip_weight[k] : 0.0f;
     w.track_cap = track_cap ? track_cap : kTrackCapDefault;
     w.lm = lm;
+    w.lmc = lmc;
+    w.dscale = dscale;
+    w.albedo_c = albedo_c > 0.0f ? albedo_c : albedo;
     return w;
 }
 

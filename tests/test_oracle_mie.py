@@ -45,16 +45,149 @@ def test_cloud_phase_table(orc):
     assert p[-1] > p[1400]              # the glory / back-scattering rise
 
 
-def test_lorenz_mie_single_scattering_matches_quadrature(orc):
-    """With the table as the phase function, a front-lit slab pixel's single scattering
-    follows the same 1-D quadrature as with HG (the phase value enters as p(cos theta))."""
+def test_chopped_table(orc):
+    """The chopped table (Sec. 3.1): the peak below 5 degrees removed, the rest renormalised;
+    the removed fraction is about half the scattered light, as the extinction paradox gives
+    for droplets much larger than the wavelength (diffraction carries half the extinction)."""
     from paper_1709_05418_gb300 import workloads as W
-    n = 8
-    vol = orc.Volume(np.full((n, n, n), 1.5, np.float32), 0.9, 0.85)
-    vol.set_phase_lm(True)
-    cam = W.camera((n, n, n), 4, 4, spp=1, seed=3, light_seed=4)
-    a = vol.render_pixels(cam, np.arange(16), params=None)
-    vol.set_phase_lm(False)
-    b = vol.render_pixels(cam, np.arange(16), params=None)
-    assert np.isfinite(a).all() and not np.allclose(a, b)
+    p, cdf, ce = orc.lm_table()
+    vol = orc.Volume(W.blob_cloud(16, seed=1), 0.9, 0.85)
+    vol.set_phase(2)
+    f, scale, alb_c = vol.chop_params()
+    pc, cdfc = vol.lm_chopped_table()
+    k = orc.LM_CHOP_BINS
+    assert abs(math.degrees(math.acos(ce[k])) - 5.0) < 1e-9
+    dom = 2.0 * math.pi * (ce[:-1] - ce[1:])
+    assert abs(f - (p[:k] * dom[:k]).sum()) < 1e-12
+    assert 0.35 < f < 0.55, f
+    assert np.all(pc[:k] == 0) and np.allclose(pc[k:], p[k:] / (1.0 - f), rtol=1e-12)
+    assert abs((pc * dom).sum() - 1.0) < 1e-12 and cdfc[-1] == 1.0
+    assert np.all(cdfc[:k + 1] == 0) and np.allclose(np.diff(cdfc), pc * dom, rtol=1e-12, atol=1e-13)
+    # the asymmetry splits into the peak's and the chopped function's
+    mid = 0.5 * (ce[:-1] + ce[1:])
+    g, g_c = (p * dom * mid).sum(), (pc * dom * mid).sum()
+    g_peak = (p[:k] * dom[:k] * mid[:k]).sum() / f
+    assert abs(g - (f * g_peak + (1.0 - f) * g_c)) < 1e-12 and g_peak > math.cos(math.radians(5.0))
+    # chopping moves light from scattering to "not scattered": the absorption coefficient
+    # (1 - albedo) mu_t is kept and the scattering coefficient drops by the factor 1 - f
+    assert abs((1.0 - alb_c) * scale - (1.0 - 0.9)) < 1e-14
+    assert abs(alb_c * scale - (1.0 - f) * 0.9) < 1e-14
+    # without absorption the chopped medium does not absorb either
+    vol1 = orc.Volume(W.blob_cloud(16, seed=1), 1.0, 0.85)
+    vol1.set_phase(2)
+    assert vol1.chop_params()[2] == 1.0
     vol.close()
+    vol1.close()
+
+
+def test_scaled_tracking_is_beer_lambert_of_the_thinner_medium(orc):
+    """The chopped medium's transport (extinction s mu_t) against closed forms on the
+    constant cube: ratio-tracking mean exp(-s tau), delta-tracking free paths 1 - exp(-s tau)."""
+    from scipy import integrate, stats
+    n, mu0, s = 8, 1.5, 0.55
+    ramp = lambda u: np.clip(np.minimum(u + 1.0, n - u), 0.0, 1.0)
+    tau = lambda x0, x1: integrate.quad(lambda x: mu0 * ramp(x * n - 0.5), x0, x1,
+                                        points=[0.5 / n, 1 - 0.5 / n], limit=200)[0]
+    v = orc.Volume(np.full((n, n, n), mu0, np.float32), 0.9, 0.85)
+    o = np.array([-0.5, 3.5 / n, 3.5 / n])
+    d = np.array([1.0, 0.0, 0.0])
+    T = np.array([v.ratio_track(o, d, 77, i, 0, scale=s) for i in range(4000)])
+    exact = math.exp(-s * tau(0.0, 1.0))
+    assert abs(T.mean() - exact) < 4 * T.std() / math.sqrt(T.size)
+    # s = 1 is the unscaled estimator, draw for draw
+    assert all(v.ratio_track(o, d, 77, i, 0, scale=1.0) == v.ratio_track(o, d, 77, i, 0) for i in range(50))
+    o = np.array([-0.25, 4.5 / n, 4.5 / n])
+    hits, xs, m = 0, [], 4000
+    for i in range(m):
+        r, x, _ = v.delta_track(o, d, 99, i, 0, scale=s)
+        if r == 1:
+            hits += 1
+            xs.append(x[0])
+    p = 1 - math.exp(-s * tau(0.0, 1.0))
+    assert abs(hits / m - p) < 4 * math.sqrt(p * (1 - p) / m)
+    grid = np.linspace(0, 1, 401)
+    taus = np.array([tau(0.0, x) if x > 0 else 0.0 for x in grid])
+    F = lambda x: np.interp(x, grid, (1 - np.exp(-s * taus)) / p)
+    assert stats.kstest(xs, F).pvalue > 1e-3
+    v.close()
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_lorenz_mie_single_scattering_matches_quadrature(orc, kind):
+    """Single scattering of a slab pixel with the table: the camera's vertex scatters with the
+    full Lorenz-Mie function (the first bounce) in both modes; in the chopped mode the light
+    reaches it through the thinner medium (extinction s mu_t)."""
+    from scipy import integrate
+    n, mu0, alb = 8, 1.5, 0.8
+    ramp = lambda u: float(np.clip(min(u + 1.0, n - u), 0.0, 1.0))
+    v = orc.Volume(np.full((n, n, n), mu0, np.float32), alb, 0.85)
+    v.set_phase(kind)
+    s = v.chop_params()[1]
+    assert (s == 1.0) == (kind == 1)
+    y0, z0 = 3.5 / n, 4.5 / n
+    a = math.radians(23.456)                    # scattering angle 113.456 degrees: inside a bin
+    wl = np.array([-math.sin(a), math.cos(a), 0.0])
+    cam = {"cam_pos": [-1.0, y0, z0], "cam_fwd": [1.0, 0, 0], "cam_right": [0, 0, -1.0],
+           "cam_up": [0, 1.0, 0], "tan_half_fov_y": 1e-9, "width": 64, "height": 64,
+           "spp": 8, "seed": 4242, "light_dir": wl, "light_E": 1.0}
+    px = v.render_pixels(cam, np.arange(64 * 64), params=None, mode=0)
+    p_tab = orc.lm_table()[0]
+    theta = math.acos(float(np.dot([1.0, 0.0, 0.0], wl)))
+    ph = p_tab[int(math.degrees(theta) / 0.1)]
+
+    def tau_light(x):
+        s_end = min(x / math.sin(a), (1.0 - y0) / math.cos(a))      # leaves the unit box
+        fx = lambda u: mu0 * ramp((x - u * math.sin(a)) * n - 0.5) * ramp((y0 + u * math.cos(a)) * n - 0.5)
+        return integrate.quad(fx, 0.0, s_end, limit=200)[0]
+
+    def tau_cam(x):
+        return integrate.quad(lambda u: mu0 * ramp(u * n - 0.5), 0.0, x, points=[0.5 / n], limit=200)[0]
+
+    def f(x):
+        return mu0 * ramp(x * n - 0.5) * math.exp(-tau_cam(x)) * ph * math.exp(-s * tau_light(x))
+
+    exp = alb * integrate.quad(f, 0, 1, points=[0.5 / n, 1 - 0.5 / n], limit=100)[0]
+    se = px.std() / math.sqrt(px.size)
+    assert abs(px.mean() - exp) < 4 * se + 1e-9, (px.mean(), exp, se)
+    v.close()
+
+
+def test_chopping_nothing_is_the_full_function(orc):
+    """Chopped mode with no bins removed follows the full Lorenz-Mie paths exactly."""
+    from paper_1709_05418_gb300 import workloads as W
+    dens = W.blob_cloud(32, seed=1)
+    a, b = orc.Volume(dens), orc.Volume(dens)
+    a.set_phase(1)
+    b.set_phase(2, chop_bins=0)
+    assert b.chop_params() == (0.0, 1.0, a.chop_params()[2])
+    cam = W.camera(dens.shape, 16, 12, spp=1, seed=3, light_seed=4)
+    pix = np.arange(16 * 12)
+    assert np.array_equal(a.render_pixels(cam, pix, mode=1), b.render_pixels(cam, pix, mode=1))
+    for r in range(4):
+        ra, rb = a.gen_record(7, r, 0.1, 32, 256), b.gen_record(7, r, 0.1, 32, 256)
+        assert ra["label"] == rb["label"] and ra["npaths"] == rb["npaths"]
+    a.close()
+    b.close()
+
+
+def test_chopped_lorenz_mie_approximates_the_full_function(orc):
+    """Sec. 3.1: the chopped function (after the first bounce, in the thinner medium) gives
+    nearly the full function's in-scattered radiance at far lower estimator variance."""
+    from paper_1709_05418_gb300 import workloads as W
+    v = orc.Volume(W.blob_cloud(64, seed=1))
+    full, chop = [], []
+    for rec in range(6):
+        r = v.gen_record(5, rec, rel_ci=0.1, n_min=32, n_max=256)
+        for kind, out in ((1, full), (2, chop)):
+            v.set_phase(kind)
+            st, mean, var = v.estimate_Li(9, rec, r["x"], r["d"], r["wl"], 20000)
+            assert st == 0
+            out.append((mean, var))
+        v.set_phase(0)
+    mf, vf = np.array(full).T
+    mc, vc = np.array(chop).T
+    se = np.sqrt((vf + vc) / 20000)
+    print("full", mf, "chopped", mc, "se", se)
+    assert abs(mc.sum() - mf.sum()) <= 4 * np.sqrt((se ** 2).sum()) + 0.05 * mf.sum()
+    assert vc.sum() < 0.2 * vf.sum()
+    v.close()
