@@ -354,6 +354,33 @@ rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t 
                                   const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
                                   float* dev_v, double* dev_loss, void* stream);
 
+/* ---- stencil-size comparison (Sec. 7, Fig. 10 right) -------------------------------------
+ * The progressive network fed by stencils of other resolutions over the standard extent:
+ * n_xy x n_xy x (2 n_xy - 1) points at (-1 + h ix, -1 + h iy, -1 + h iz) * 2^(k-1) mean free
+ * paths, h = 2 / (n_xy - 1), n_xy in [2, 9] (5: the standard 5 x 5 x 9 stencil).  Level k
+ * reads the mip whose voxel is the largest power of two (fine voxels) not above the spacing
+ * h 2^(k-1) mean free paths.  Rows are FP32 [q][RPNN_K][din], din = n_xy^2 (2 n_xy - 1) + 1
+ * (points in (iz n_xy + iy) n_xy + ix order, then gamma), unpadded.  The network is the
+ * standard one (Sec. 4.3) with V^k of width din: parameters (FP32, caller-owned, flat) in
+ * the order of rpnn_set_weights.  FP32 CUDA-core GEMMs; at most 2^20 rows per call.
+ * Errors: RPNN_ERR_ARG for n_xy outside [2, 9], a bad row count or a null pointer;
+ * RPNN_ERR_HANDLE / RPNN_ERR_STATE for an unknown volume or one without rpnn_build_mips. */
+int64_t rpnn_stencil_param_count(int32_t n_xy);   /* -1 for n_xy outside [2, 9] */
+/* Descriptors of q shading points (dev_x, dev_d [q][3]; light directions dev_wl [3] per
+ * point at stride wl_stride floats, 0 for one shared direction) to dev_desc. */
+rpnn_status rpnn_stencil_descriptors(rpnn_ctx* ctx, int32_t vol, int32_t n_xy, const float* dev_x,
+                                     const float* dev_d, const float* dev_wl, int32_t wl_stride, int64_t q,
+                                     float* dev_desc, void* stream);
+rpnn_status rpnn_stencil_forward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_params, const float* dev_desc,
+                                 int64_t q, float* dev_out, void* stream);
+/* Gradient of sum_i dout_i g(z_i) w.r.t. the parameters, written to dev_dparams. */
+rpnn_status rpnn_stencil_backward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_params, const float* dev_desc,
+                                  int64_t q, const float* dev_dout, float* dev_dparams, void* stream);
+/* One Adam step on the log-MSE loss (as rpnn_train_step), loss (FP64) to *dev_loss. */
+rpnn_status rpnn_stencil_train_step(rpnn_ctx* ctx, int32_t n_xy, const float* dev_desc, const float* dev_target,
+                                    int32_t batch, const rpnn_adam_cfg* adam, int64_t step, float* dev_params,
+                                    float* dev_m, float* dev_v, double* dev_loss, void* stream);
+
 /* Arithmetic of rpnn_train_step and rpnn_mlp_backward: RPNN_F32 (the default; FP32 CUDA-core
  * GEMMs) or RPNN_BF16 (mixed precision: every 200-wide layer and weight gradient is a BF16
  * tcgen05 GEMM with FP32 accumulation; FP32 master weights, biases, residual sums, ReLU

@@ -91,6 +91,9 @@ def lib():
             L.orc_mip_level_f32.argtypes = [C.c_void_p, C.c_int, _fp]
             L.orc_descriptor_f64.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int64, _dp]
             L.orc_descriptor_f32.argtypes = [C.c_void_p, _fp, _fp, _fp, C.c_int64, _fp]
+            L.orc_stencil_din.argtypes = [C.c_int]
+            L.orc_descriptor_stencil_f64.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_int64, _dp]
+            L.orc_descriptor_stencil_f32.argtypes = [C.c_void_p, C.c_int, _fp, _fp, _fp, C.c_int64, _fp]
             L.orc_frame_f64.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
             L.orc_density.restype = C.c_double
             L.orc_density.argtypes = [C.c_void_p, _dp]
@@ -203,6 +206,14 @@ def frame(d, wl):
 def net_param_count(K=10, din=226, H=200, ntail=3) -> int:
     n = Net(K, din, H, ntail)
     return int(lib().orc_net_param_count(C.byref(n)))
+
+
+def stencil_din(n: int) -> int:
+    """Block input width of the n x n x (2n - 1) stencil: n^2 (2n - 1) points and gamma."""
+    din = int(lib().orc_stencil_din(int(n)))
+    if din < 0:
+        raise ValueError(f"stencil resolution {n} outside [2, 9]")
+    return din
 
 
 def mlp_forward(params, z, K=10, din=226, H=200, ntail=3):
@@ -408,6 +419,22 @@ class Volume:
             q = x.shape[0]
             out = np.zeros((q, K, DIN), np.float64)
             r = lib().orc_descriptor_f64(self.h, _d(x), _d(d), _d(wl), q, _d(out))
+        assert r == 0
+        return out
+
+    def descriptor_stencil(self, n, x, d, wl, f32: bool = False):
+        """Descriptor of the n x n x (2n - 1) stencil (stencil-size comparison): [q][K][din]."""
+        din = stencil_din(n)
+        if f32:
+            x = _c32(x, (-1, 3)); d = _c32(d, (-1, 3)); wl = _c32(wl, (3,))
+            q = x.shape[0]
+            out = np.zeros((q, K, din), np.float32)
+            r = lib().orc_descriptor_stencil_f32(self.h, n, _f(x), _f(d), _f(wl), q, _f(out))
+        else:
+            x = _c64(x, (-1, 3)); d = _c64(d, (-1, 3)); wl = _c64(wl, (3,))
+            q = x.shape[0]
+            out = np.zeros((q, K, din), np.float64)
+            r = lib().orc_descriptor_stencil_f64(self.h, n, _d(x), _d(d), _d(wl), q, _d(out))
         assert r == 0
         return out
 

@@ -640,6 +640,130 @@ int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float w
 }
 
 /* ------------------------------------------------------------------------- */
+/* Other stencil resolutions (the stencil-size comparison of Sec. 7, Fig. 10):   */
+/* n x n x (2n - 1) points over the standard stencil's extent [-1,1]^2 x [-1,3],   */
+/* spacing h = 2 / (n - 1) (n = 5: the standard 5 x 5 x 9 stencil), index          */
+/* (iz*n + iy)*n + ix, then gamma; level k reads the mip whose voxel is the largest */
+/* power of two (fine voxels) not above the spacing h 2^(k-1) mean free paths.      */
+/* ------------------------------------------------------------------------- */
+int orc_stencil_din(int n) {
+    if (n < 2 || n > 9) return -1;
+    return n * n * (2 * n - 1) + 1;
+}
+
+static int stencil_mip(const orc_ctx* c, int n, int k) {
+    const double h = 2.0 / (double)(n - 1);
+    const double sk = h * ldexp((double)c->st.inv_mean_f, k) * c->st.inv_h0;   /* fine voxels */
+    int m = 0;
+    if (sk > 0.0) { int ex; frexp(sk, &ex); m = ex - 1; }
+    if (m < 0) m = 0;
+    if (m > c->st.levels - 1) m = c->st.levels - 1;
+    return m;
+}
+
+int orc_descriptor_stencil_f64(orc_ctx* c, int n, const double* x, const double* d, const double wl[3],
+                               int64_t q, double* out) {
+    const int din = orc_stencil_din(n);
+    if (!c || din < 0) return -1;
+    const int nz = 2 * n - 1, S = din - 1;
+    const double h = 2.0 / (double)(n - 1);
+    int mk[ORC_K];
+    const double* lv[ORC_K];
+    for (int k = 0; k < ORC_K; ++k) { mk[k] = stencil_mip(c, n, k); lv[k] = get_mip64(c, mk[k]); }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < q; ++i) {
+        double ex[3], ey[3], ez[3], gamma;
+        orc_frame_f64(d + 3 * i, wl, ex, ey, ez, &gamma);
+        double* o = out + i * (int64_t)ORC_K * din;
+        for (int k = 0; k < ORC_K; ++k) {
+            const double scale = ldexp(c->st.inv_mean, k);
+            const double s_m = ldexp(c->st.inv_h0, -mk[k]);
+            for (int iz = 0; iz < nz; ++iz)
+                for (int iy = 0; iy < n; ++iy)
+                    for (int ix = 0; ix < n; ++ix) {
+                        const double ox = -1.0 + h * ix, oy = -1.0 + h * iy, oz = -1.0 + h * iz;
+                        double u[3];
+                        for (int a = 0; a < 3; ++a)
+                            u[a] = (x[3 * i + a] + scale * (ox * ex[a] + oy * ey[a] + oz * ez[a])) * s_m - 0.5;
+                        o[k * din + (iz * n + iy) * n + ix] = trilinear64(lv[k], c->st.dims[mk[k]], u);
+                    }
+            o[k * din + S] = gamma;
+        }
+    }
+    return 0;
+}
+
+/* FP32 restatement with the standard descriptor's rounding sequence (orc_descriptor_f32)
+ * and the offsets -1 + h_f i, h_f = (float)(2 / (n - 1)), each product and sum rounded. */
+int orc_descriptor_stencil_f32(orc_ctx* c, int n, const float* x, const float* d, const float wl[3],
+                               int64_t q, float* out) {
+    const int din = orc_stencil_din(n);
+    if (!c || din < 0) return -1;
+    const int nz = 2 * n - 1, S = din - 1;
+    const float hf = (float)(2.0 / (double)(n - 1));
+    int mk[ORC_K];
+    const float* lv[ORC_K];
+    for (int k = 0; k < ORC_K; ++k) { mk[k] = stencil_mip(c, n, k); lv[k] = get_mip32(c, mk[k]); }
+    const float inv_h0 = (float)c->st.inv_h0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < q; ++i) {
+        const float* xi = x + 3 * i;
+        const float* di = d + 3 * i;
+        float w[3] = {-di[0], -di[1], -di[2]};
+        const float* ez = wl;
+        float cr[3];
+        { float p, r;
+          p = ez[1] * w[2]; r = ez[2] * w[1]; cr[0] = p - r;
+          p = ez[2] * w[0]; r = ez[0] * w[2]; cr[1] = p - r;
+          p = ez[0] * w[1]; r = ez[1] * w[0]; cr[2] = p - r; }
+        float len2;
+        { float a = cr[0] * cr[0], b = cr[1] * cr[1], e = cr[2] * cr[2]; len2 = (a + b) + e; }
+        float ex[3];
+        if (len2 < 1e-12f) {
+            double nn[3] = {ez[0], ez[1], ez[2]}, b1[3], b2[3];
+            duff_basis(nn, b1, b2);
+            for (int a = 0; a < 3; ++a) ex[a] = (float)b1[a];
+        } else {
+            float len = sqrtf(len2);
+            for (int a = 0; a < 3; ++a) ex[a] = cr[a] / len;
+        }
+        float ey[3];
+        { float p, r;
+          p = ez[1] * ex[2]; r = ez[2] * ex[1]; ey[0] = p - r;
+          p = ez[2] * ex[0]; r = ez[0] * ex[2]; ey[1] = p - r;
+          p = ez[0] * ex[1]; r = ez[1] * ex[0]; ey[2] = p - r; }
+        float cg;
+        { float a = w[0] * wl[0], b = w[1] * wl[1], e = w[2] * wl[2]; cg = (a + b) + e; }
+        cg = fminf(fmaxf(cg, -1.0f), 1.0f);
+        const float gamma = acosf(cg);
+        float* o = out + i * (int64_t)ORC_K * din;
+        for (int k = 0; k < ORC_K; ++k) {
+            const int m = mk[k];
+            const float s = ldexpf(inv_h0, -m);
+            const float g = ldexpf(c->st.inv_mean_f, k) * s;
+            float A[3], B[3], C[3], U0[3];
+            for (int a = 0; a < 3; ++a) {
+                A[a] = g * ex[a]; B[a] = g * ey[a]; C[a] = g * ez[a];
+                float xs = xi[a] * s;
+                U0[a] = xs - 0.5f;
+            }
+            for (int iz = 0; iz < nz; ++iz)
+                for (int iy = 0; iy < n; ++iy)
+                    for (int ix = 0; ix < n; ++ix) {
+                        float px = hf * (float)ix, py = hf * (float)iy, pz = hf * (float)iz;
+                        const float ox = -1.0f + px, oy = -1.0f + py, oz = -1.0f + pz;
+                        float u[3];
+                        for (int a = 0; a < 3; ++a)
+                            u[a] = fmaf(oz, C[a], fmaf(oy, B[a], fmaf(ox, A[a], U0[a])));
+                        o[k * din + (iz * n + iy) * n + ix] = trilinear32(lv[k], c->st.dims[m], u);
+                    }
+            o[k * din + S] = gamma;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Transport                                                                    */
 /* ------------------------------------------------------------------------- */
 double orc_hg(double g, double ct) {

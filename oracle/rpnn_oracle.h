@@ -77,6 +77,15 @@ int orc_descriptor_f64(orc_ctx* c, const double* x, const double* d, const doubl
                        int64_t q, double* out);
 int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float wl[3],
                        int64_t q, float* out);
+/* The same descriptor for an n x n x (2n - 1) stencil over the standard extent (spacing
+ * 2 / (n - 1); the stencil-size comparison of Sec. 7): rows [q][ORC_K][din], din =
+ * orc_stencil_din(n) = n^2 (2n - 1) + 1 (-1 for n outside [2, 9]); n = 5 is the standard
+ * descriptor without its padding.  Level k reads the mip matching the spacing. */
+int orc_stencil_din(int n);
+int orc_descriptor_stencil_f64(orc_ctx* c, int n, const double* x, const double* d, const double wl[3],
+                               int64_t q, double* out);
+int orc_descriptor_stencil_f32(orc_ctx* c, int n, const float* x, const float* d, const float wl[3],
+                               int64_t q, float* out);
 /* local frame, for pinning: ex, ey, ez, gamma */
 void orc_frame_f64(const double d[3], const double wl[3], double ex[3], double ey[3],
                    double ez[3], double* gamma);

@@ -101,6 +101,11 @@ def load():
             "rpnn_set_mip_blend": [_vp, i32, i32],
             "rpnn_set_iteration_cap": [_vp, i32, i64],
             "rpnn_set_phase_function": [_vp, i32, i32],
+            "rpnn_stencil_descriptors": [_vp, i32, i32, _vp, _vp, _vp, i32, i64, _vp, _vp],
+            "rpnn_stencil_forward": [_vp, i32, _vp, _vp, i64, _vp, _vp],
+            "rpnn_stencil_backward": [_vp, i32, _vp, _vp, i64, _vp, _vp, _vp],
+            "rpnn_stencil_train_step": [_vp, i32, _vp, _vp, i32, C.POINTER(AdamCfg), i64, _vp, _vp, _vp, _vp,
+                                        _vp],
             "rpnn_set_autotune_table": [_vp, C.POINTER(TuneEntry), i32],
             "rpnn_dense_forward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp],
             "rpnn_dense_backward": [_vp, C.POINTER(i32), i32, i32, _vp, _vp, i64, _vp, _vp, _vp],
@@ -131,6 +136,8 @@ def load():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int32
+        L.rpnn_stencil_param_count.restype = C.c_int64
+        L.rpnn_stencil_param_count.argtypes = [C.c_int32]
         L.rpnn_dense_param_count.restype = C.c_int64
         L.rpnn_dense_param_count.argtypes = [C.POINTER(C.c_int32), C.c_int32, C.c_int32]
         L.rpnn_last_error.restype = C.c_char_p
@@ -266,6 +273,44 @@ class Context:
         self._check(self.L.rpnn_dense_train_step(self.h, w, n, x[0].numel(), _ptr(x), _ptr(target), x.shape[0],
                                                  C.byref(cfg), step, _ptr(params), _ptr(m), _ptr(v), _ptr(loss),
                                                  _stream()))
+        return loss
+
+    # ---- stencil-size comparison (Sec. 7, Fig. 10 right)
+    def stencil_param_count(self, n_xy: int) -> int:
+        return int(self.L.rpnn_stencil_param_count(n_xy))
+
+    def stencil_descriptors(self, vol, n_xy, x, d, wl, out=None):
+        """FP32 rows [q][10][n_xy^2 (2 n_xy - 1) + 1] of the n_xy x n_xy x (2 n_xy - 1) stencil."""
+        q = x.shape[0]
+        stride = 3 if wl.dim() == 2 else 0
+        if out is None:
+            out = torch.empty((q, K, n_xy * n_xy * (2 * n_xy - 1) + 1), dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_stencil_descriptors(self.h, vol, n_xy, _ptr(x), _ptr(d), _ptr(wl), stride, q,
+                                                    _ptr(out), _stream()))
+        return out
+
+    def stencil_forward(self, n_xy, params, desc, out=None):
+        q = desc.shape[0]
+        if out is None:
+            out = torch.empty(q, dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_stencil_forward(self.h, n_xy, _ptr(params), _ptr(desc), q, _ptr(out), _stream()))
+        return out
+
+    def stencil_backward(self, n_xy, params, desc, dout, out=None):
+        if out is None:
+            out = torch.empty(params.numel(), dtype=torch.float32, device="cuda")
+        self._check(self.L.rpnn_stencil_backward(self.h, n_xy, _ptr(params), _ptr(desc), desc.shape[0], _ptr(dout),
+                                                 _ptr(out), _stream()))
+        return out
+
+    def stencil_train_step(self, n_xy, desc, target, params, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999,
+                           eps=1e-8, loss=None):
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        cfg = AdamCfg(lr, beta1, beta2, eps)
+        self._check(self.L.rpnn_stencil_train_step(self.h, n_xy, _ptr(desc), _ptr(target), desc.shape[0],
+                                                   C.byref(cfg), step, _ptr(params), _ptr(m), _ptr(v), _ptr(loss),
+                                                   _stream()))
         return loss
 
     def set_train_precision(self, precision):

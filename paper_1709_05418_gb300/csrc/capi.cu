@@ -106,7 +106,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     for (Volume* v : c->vols) {
         if (!v) continue;
         v->raw.release(); v->packed.release(); v->stats.release(); v->bmaj.release();
-        v->mip_a.release(); v->mip_b.release(); v->mip_w.release();
+        v->mip_a.release(); v->mip_b.release(); v->mip_w.release(); v->stencil_mips.release();
         delete v;
     }
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
@@ -628,6 +628,101 @@ rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t 
                                  c->t_grad.as<float>(), s);
     if (st) return st;
     return launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), np, step, *adam, s);
+}
+
+// ---------------------------------------------------------------- stencil-size comparison
+int64_t rpnn_stencil_param_count(int32_t n_xy) {
+    const int din = stencil_din(n_xy);
+    return din < 0 ? -1 : param_layout_for(din).total;
+}
+
+static bool stencil_shape(int32_t n_xy, ParamLayout* L, NetDims* nd) {
+    const int din = stencil_din(n_xy);
+    if (din < 0) {
+        set_error("stencil resolution %d outside [2, 9]", n_xy);
+        return false;
+    }
+    *L = param_layout_for(din);
+    *nd = NetDims{L, din, din};
+    return true;
+}
+
+rpnn_status rpnn_stencil_descriptors(rpnn_ctx* ctx, int32_t vol, int32_t n_xy, const float* dev_x,
+                                     const float* dev_d, const float* dev_wl, int32_t wl_stride, int64_t q,
+                                     float* dev_desc, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    Volume* v = get_vol(c, vol, true);
+    if (!v) return RPNN_ERR_HANDLE;
+    if (q < 0 || q > kChunkRows) { set_error("q must be in [0, %lld]", (long long)kChunkRows); return RPNN_ERR_ARG; }
+    if (wl_stride < 0) { set_error("wl_stride < 0"); return RPNN_ERR_ARG; }
+    if (q > 0 && (!dev_x || !dev_d || !dev_wl || !dev_desc)) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    return stencil_descriptors(*c, *v, n_xy, dev_x, dev_d, dev_wl, wl_stride, q, dev_desc, (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_stencil_forward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_params, const float* dev_desc,
+                                 int64_t q, float* dev_out, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    ParamLayout L;
+    NetDims nd;
+    if (!stencil_shape(n_xy, &L, &nd)) return RPNN_ERR_ARG;
+    if (q <= 0 || q > kChunkRows) { set_error("q must be in [1, %lld]", (long long)kChunkRows); return RPNN_ERR_ARG; }
+    if (!dev_params || !dev_desc || !dev_out) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    rpnn_status st = ensure_rows(c, q, true);
+    if (st) return st;
+    return rpnn_forward_f32(*c, nd, dev_params, dev_desc, q, nullptr, dev_out, nullptr, (cudaStream_t)stream);
+}
+
+// forward with saved activations (t_saved), prediction to t_out
+static rpnn_status stencil_fwd_saved(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                                     cudaStream_t s) {
+    rpnn_status st = c.t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
+    if (!st) st = c.t_out.reserve(q * sizeof(float));
+    if (st) return st;
+    return rpnn_forward_f32(c, nd, P, desc, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
+}
+
+rpnn_status rpnn_stencil_backward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_params, const float* dev_desc,
+                                  int64_t q, const float* dev_dout, float* dev_dparams, void* stream) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    ParamLayout L;
+    NetDims nd;
+    if (!stencil_shape(n_xy, &L, &nd)) return RPNN_ERR_ARG;
+    if (q <= 0 || q > kChunkRows) { set_error("q must be in [1, %lld]", (long long)kChunkRows); return RPNN_ERR_ARG; }
+    if (!dev_params || !dev_desc || !dev_dout || !dev_dparams) { set_error("null pointer"); return RPNN_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = stencil_fwd_saved(*c, nd, dev_params, dev_desc, q, s);
+    if (st) return st;
+    return rpnn_backward_f32(*c, nd, dev_params, dev_desc, q, c->t_saved.as<float>(), dev_dout, dev_dparams, s);
+}
+
+rpnn_status rpnn_stencil_train_step(rpnn_ctx* ctx, int32_t n_xy, const float* dev_desc, const float* dev_target,
+                                    int32_t batch, const rpnn_adam_cfg* adam, int64_t step, float* dev_params,
+                                    float* dev_m, float* dev_v, double* dev_loss, void* stream) {
+    CHECK_CTX(ctx);
+    NvtxRange range("rpnn_stencil_train_step");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    ParamLayout L;
+    NetDims nd;
+    if (!stencil_shape(n_xy, &L, &nd)) return RPNN_ERR_ARG;
+    if (batch <= 0 || batch > kChunkRows || !adam || step < 1 || !dev_desc || !dev_target || !dev_params ||
+        !dev_m || !dev_v || !dev_loss) {
+        set_error("bad batch, step or pointer");
+        return RPNN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rpnn_status st = c->t_grad.reserve((size_t)L.total * sizeof(float));
+    if (!st) st = c->sample_val.reserve((size_t)batch * sizeof(float));
+    if (!st) st = stencil_fwd_saved(*c, nd, dev_params, dev_desc, batch, s);
+    if (st) return st;
+    float* dg = c->sample_val.as<float>();
+    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
+    if (!st) st = rpnn_backward_f32(*c, nd, dev_params, dev_desc, batch, c->t_saved.as<float>(), dg,
+                                    c->t_grad.as<float>(), s);
+    if (st) return st;
+    return launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), L.total, step, *adam, s);
 }
 
 rpnn_status rpnn_set_autotune_table(rpnn_ctx* ctx, const rpnn_tune_entry* entries, int32_t n) {

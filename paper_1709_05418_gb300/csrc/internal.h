@@ -97,6 +97,9 @@ struct Volume {
     const float* lm = nullptr;   // the context's Lorenz-Mie table when selected
     const float* lmc = nullptr;  // the table after the first bounce (chopped or = lm)
     float dscale = 1.0f, albedo_c = 0.0f;  // chopped medium (albedo_c 0: = albedo)
+    DevBuf stencil_mips;     // every pyramid level as plain FP32, for the stencil-size sweep
+    int64_t smip_off[kMaxLevels] = {};   // element offset of each level in stencil_mips
+    bool stencil_ready = false;
     bool built = false;
     int levels = 0;
     int dims[kMaxLevels][3] = {};
@@ -242,6 +245,13 @@ rpnn_status launch_scatter_composite(Ctx& c, const rpnn_render_desc& rd, float a
 rpnn_status launch_nee_env(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd, const float* qx,
                            const float* qd, const uint32_t* qps, const int* qcount, int64_t max_q, const float* dirs,
                            const float* E, int j0, int n, float* sample_val, cudaStream_t s);
+// Descriptors of an n_xy x n_xy x (2 n_xy - 1) stencil (the stencil-size comparison of
+// Sec. 7): FP32 rows [q][RPNN_K][stencil_din(n_xy)], level k's points
+// (-1 + h ix, -1 + h iy, -1 + h iz) * 2^(k-1) mean free paths, h = 2 / (n_xy - 1), read from
+// the mip level matching that spacing; n_xy = 5 is the standard descriptor.
+int stencil_din(int n_xy);
+rpnn_status stencil_descriptors(Ctx& c, Volume& v, int n_xy, const float* x, const float* d, const float* wl,
+                                int wl_stride, int64_t q, float* out, cudaStream_t s);
 // uploads the Lorenz-Mie phase table to c.lm_table once (synchronises s)
 rpnn_status phase_lm_upload(Ctx& c, cudaStream_t s);
 // fraction of the scattered light in the chopped peak (RPNN_LM_CHOP_BINS bins)
@@ -347,5 +357,20 @@ struct ParamLayout {
     int64_t total;
 };
 const ParamLayout& param_layout();
+ParamLayout param_layout_for(int din);   // the same network with block input width din
+
+// A progressive network's shape: parameter layout, block input width (Sigma^k and gamma)
+// and the stored width of one level of a descriptor row.
+struct NetDims {
+    const ParamLayout* L;
+    int din;
+    int64_t stride;
+};
+// The FP32 forward and backward of mlp_forward_f32 / mlp_backward_f32 for any NetDims and
+// parameter vector P (the two call these with the standard shape and the context's weights).
+rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                             const int* q_dev, float* out, float* saved, cudaStream_t s);
+rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                              const float* saved, const float* dout, float* dP, cudaStream_t s);
 
 }  // namespace rpnn

@@ -365,37 +365,39 @@ void gemm_tile_shape(int tile, int* bm, int* bn, int* bk) {
     *bm = t.bm; *bn = t.bn; *bk = t.bk;
 }
 
+ParamLayout param_layout_for(int din) {
+    ParamLayout l{};
+    int64_t o = 0;
+    for (int k = 0; k < RPNN_K; ++k) {
+        l.V[k] = o; o += (int64_t)RPNN_H * din;
+        if (k > 0) { l.W1[k] = o; o += (int64_t)RPNN_H * RPNN_H; } else l.W1[k] = -1;
+        l.b1[k] = o; o += RPNN_H;
+        l.W2[k] = o; o += (int64_t)RPNN_H * RPNN_H;
+        l.b2[k] = o; o += RPNN_H;
+    }
+    for (int t = 0; t < 3; ++t) {
+        const int out = t == 2 ? 1 : RPNN_H;
+        l.T[t] = o; o += (int64_t)out * RPNN_H;
+        l.bT[t] = o; o += out;
+    }
+    l.total = o;
+    return l;
+}
+
 const ParamLayout& param_layout() {
-    static ParamLayout L = [] {
-        ParamLayout l{};
-        int64_t o = 0;
-        for (int k = 0; k < RPNN_K; ++k) {
-            l.V[k] = o; o += (int64_t)RPNN_H * RPNN_DIN;
-            if (k > 0) { l.W1[k] = o; o += (int64_t)RPNN_H * RPNN_H; } else l.W1[k] = -1;
-            l.b1[k] = o; o += RPNN_H;
-            l.W2[k] = o; o += (int64_t)RPNN_H * RPNN_H;
-            l.b2[k] = o; o += RPNN_H;
-        }
-        for (int t = 0; t < 3; ++t) {
-            const int out = t == 2 ? 1 : RPNN_H;
-            l.T[t] = o; o += (int64_t)out * RPNN_H;
-            l.bT[t] = o; o += out;
-        }
-        l.total = o;
-        return l;
-    }();
+    static ParamLayout L = param_layout_for(RPNN_DIN);
     return L;
 }
+
 
 // saved activations per row: o^1..o^10, F1^1..F1^10, o^11, o^12 (each 200), g
 size_t mlp_saved_floats_per_row() { return 22 * (size_t)RPNN_H + 1; }
 
-rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_dev, float* out,
-                            float* saved, cudaStream_t s) {
-    const ParamLayout& L = param_layout();
-    const float* P = c.params32.as<float>();
+rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                             const int* q_dev, float* out, float* saved, cudaStream_t s) {
+    const ParamLayout& L = *nd.L;
     const int M = (int)q;
-    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
+    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * nd.stride;
     float *o_prev = nullptr, *o_cur, *f1;
     auto slot = [&](int i) { return saved + (size_t)i * q * H; };
     rpnn_status st;
@@ -403,7 +405,7 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
         if (saved) { o_cur = slot(k); f1 = slot(10 + k); }
         else { o_cur = c.act0.as<float>(); f1 = c.act1.as<float>(); }
         // F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)
-        Seg z = seg(desc + k * RPNN_DESC_STRIDE, ZS, 1, P + L.V[k], 1, RPNN_DIN, RPNN_DIN);
+        Seg z = seg(desc + k * nd.stride, ZS, 1, P + L.V[k], 1, nd.din, nd.din);
         if (k > 0) {
             Seg o = seg(o_prev, H, 1, P + L.W1[k], 1, H, RPNN_H);
             st = gemm(&c, M, q_dev, RPNN_H, z, &o, epi(f1, H, P + L.b1[k], 1), s);
@@ -431,6 +433,12 @@ rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_d
     if (saved) RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float),
                                              cudaMemcpyDeviceToDevice, s));
     return RPNN_OK;
+}
+
+rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_dev, float* out,
+                            float* saved, cudaStream_t s) {
+    const NetDims nd{&param_layout(), RPNN_DIN, RPNN_DESC_STRIDE};
+    return rpnn_forward_f32(c, nd, c.params32.as<float>(), desc, q, q_dev, out, saved, s);
 }
 
 rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
@@ -461,12 +469,11 @@ rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, f
     return gemm(nullptr, M, nullptr, 1, seg(s2, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
 }
 
-rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
-                             const float* dout, float* dP, cudaStream_t s) {
-    const ParamLayout& L = param_layout();
-    const float* P = c.params32.as<float>();
+rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                              const float* saved, const float* dout, float* dP, cudaStream_t s) {
+    const ParamLayout& L = *nd.L;
     const int M = (int)q;
-    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
+    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * nd.stride;
     auto slot = [&](int i) { return saved + (size_t)i * q * H; };
     const float* g = saved + (size_t)22 * q * H;
     rpnn_status st = c.act0.reserve((size_t)q * H * sizeof(float));
@@ -518,8 +525,8 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
                   epi(da, H, nullptr, 0, nullptr, 0, f1, H), s);
         if (st) return st;
         // dV = da1^T z^k; db1 = colsum(da1)
-        st = gemm(&c, RPNN_H, nullptr, RPNN_DIN, seg(da, 1, H, desc + k * RPNN_DESC_STRIDE, ZS, 1, M), nullptr,
-                  epi(dP + L.V[k], RPNN_DIN), s);
+        st = gemm(&c, RPNN_H, nullptr, nd.din, seg(da, 1, H, desc + k * nd.stride, ZS, 1, M), nullptr,
+                  epi(dP + L.V[k], nd.din), s);
         if (st) return st;
         k_colsum<<<cs_grid, cs_block, 0, s>>>(da, M, RPNN_H, H, dP + L.b1[k]);
         RPNN_CHECK_LAUNCH();
@@ -535,6 +542,12 @@ rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* 
         }
     }
     return RPNN_OK;
+}
+
+rpnn_status mlp_backward_f32(Ctx& c, const float* desc, int64_t q, const float* saved,
+                             const float* dout, float* dP, cudaStream_t s) {
+    const NetDims nd{&param_layout(), RPNN_DIN, RPNN_DESC_STRIDE};
+    return rpnn_backward_f32(c, nd, c.params32.as<float>(), desc, q, saved, dout, dP, s);
 }
 
 rpnn_status mlp_output_layer_f32(Ctx& c, const float* t1, int64_t q, float* out, cudaStream_t s) {

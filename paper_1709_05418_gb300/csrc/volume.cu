@@ -324,6 +324,7 @@ rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s) {
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
     if (tmp) cudaFree(tmp);
     v.built = true;
+    v.stencil_ready = false;
     return RPNN_OK;
 }
 

@@ -1,0 +1,133 @@
+"""GPU parity for the stencil-size comparison (Sec. 7, Fig. 10 right): descriptors of other
+stencil resolutions bit-exact against the oracle's FP32 restatement (gamma to 2 ulp, CUDA
+acosf against libm), the n = 5 stencil against the standard descriptor kernel, and the
+progressive network of any input width (forward, gradient, Adam step) against the FP64
+oracle; a short sweep trains every resolution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_05418_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_05418_gb300 import api
+    ctx = api.Context()
+    dens = W.blob_cloud(64, seed=1)
+    vol = ctx.load_volume(torch.from_numpy(dens).cuda())
+    ctx.build_mips(vol)
+    orc = oracle.Volume(dens)
+    yield api, ctx, vol, orc
+    ctx.close()
+
+
+def _queries(q, seed=11):
+    x, d = W.random_queries((64, 64, 64), q, seed=seed, margin=0.2)
+    wl = np.array([0.3, 0.5, -0.8])
+    wl /= np.linalg.norm(wl)
+    return x.astype(np.float32), d.astype(np.float32), wl.astype(np.float32)
+
+
+def _gamma_ulps(a, b):
+    return np.abs(a.view(np.int32).astype(np.int64) - b.view(np.int32).astype(np.int64))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 7, 9])
+@pytest.mark.parametrize("q", [1, 37, 1031])
+def test_stencil_descriptor_bit_exact(env, n, q):
+    api, ctx, vol, orc = env
+    x, d, wl = _queries(q)
+    got = ctx.stencil_descriptors(vol, n, torch.from_numpy(x).cuda(), torch.from_numpy(d).cuda(),
+                                  torch.from_numpy(wl).cuda()).cpu().numpy()
+    ctx.sync_status()
+    ref = orc.descriptor_stencil(n, x, d, wl, f32=True)
+    assert got.shape == ref.shape == (q, 10, n * n * (2 * n - 1) + 1)
+    assert np.array_equal(got[:, :, :-1], ref[:, :, :-1])
+    assert _gamma_ulps(got[:, :, -1], ref[:, :, -1]).max() <= 2
+    assert np.count_nonzero(got[:, :, :-1]) > 0
+
+
+def test_stencil_five_matches_the_standard_kernel(env):
+    api, ctx, vol, _ = env
+    x, d, wl = [torch.from_numpy(a).cuda() for a in _queries(517, seed=5)]
+    per_point_wl = wl.expand(x.shape[0], 3).contiguous()
+    std = ctx.extract_descriptors(vol, x, d, per_point_wl)[:, :, :226]
+    gen = ctx.stencil_descriptors(vol, 5, x, d, per_point_wl)
+    ctx.sync_status()
+    assert torch.equal(std, gen)
+
+
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_stencil_network_forward_and_gradient(env, n):
+    api, ctx, vol, orc = env
+    x, d, wl = _queries(333, seed=13)
+    z = orc.descriptor_stencil(n, x, d, wl, f32=True)
+    din = z.shape[2]
+    p = W.he_init(seed=3, din=din)
+    assert p.size == ctx.stencil_param_count(n)
+    pc, zc = torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda()
+    g = ctx.stencil_forward(n, pc, zc).double().cpu().numpy()
+    ref = oracle.mlp_forward(p.astype(np.float64), z.astype(np.float64), din=din)
+    assert np.linalg.norm(g - ref) <= F32_REL * np.linalg.norm(ref)
+    dout = np.random.default_rng(7).normal(size=z.shape[0])
+    dp = ctx.stencil_backward(n, pc, zc, torch.from_numpy(dout.astype(np.float32)).cuda()).double().cpu().numpy()
+    ctx.sync_status()
+    dref = oracle.mlp_backward(p.astype(np.float64), z.astype(np.float64), dout, din=din)
+    assert np.linalg.norm(dp - dref) <= 1e-4 * np.linalg.norm(dref)
+
+
+def test_stencil_train_step_matches_oracle(env):
+    api, ctx, vol, orc = env
+    n = 3
+    x, d, wl = _queries(256, seed=17)
+    z = orc.descriptor_stencil(n, x, d, wl, f32=True)
+    din = z.shape[2]
+    p = W.he_init(seed=3, din=din)
+    t = np.linspace(0.01, 0.5, z.shape[0]).astype(np.float32)
+    pc = torch.from_numpy(p).cuda()
+    m, v = torch.zeros_like(pc), torch.zeros_like(pc)
+    loss = ctx.stencil_train_step(n, torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda(), pc, m, v, 1, lr=1e-3)
+    ctx.sync_status()
+    p64, z64 = p.astype(np.float64), z.astype(np.float64)
+    g = oracle.mlp_forward(p64, z64, din=din)
+    ref_loss, dg = oracle.logmse_loss(g, t.astype(np.float64))
+    assert abs(float(loss) - ref_loss) <= 1e-5 * ref_loss
+    grad = oracle.mlp_backward(p64, z64, dg, din=din)
+    pr, mr, vr = p64.copy(), np.zeros_like(p64), np.zeros_like(p64)
+    oracle.adam(pr, mr, vr, grad, 1, lr=1e-3)
+    got = pc.double().cpu().numpy()
+    moved = np.abs(pr - p64) > 1e-4          # entries the step clearly moved
+    assert moved.mean() > 0.1
+    assert np.abs((got - p64)[moved] - (pr - p64)[moved]).max() <= 1e-4
+
+
+def test_stencil_errors(env):
+    api, ctx, vol, _ = env
+    x, d, wl = [torch.from_numpy(a).cuda() for a in _queries(4)]
+    assert ctx.stencil_param_count(1) == -1 and ctx.stencil_param_count(10) == -1
+    for n in (1, 10):
+        with pytest.raises(api.RPNNError):
+            ctx.stencil_descriptors(vol, n, x, d, wl, out=torch.empty(4, 10, 8, device="cuda"))
+    with pytest.raises(api.RPNNError):
+        ctx.stencil_descriptors(12345, 3, x, d, wl)
+
+
+def test_stencil_sweep_trains_every_resolution(env):
+    from paper_1709_05418_gb300 import ablation, train
+    api, ctx, _, _ = env
+    clouds = train.blob_clouds(2, size=48, seed0=330)
+    descs, label = ablation.stencil_records(ctx, clouds, 1500, (3, 5), seed=41)
+    curves, counts = ablation.compare_stencils(ctx, descs, label, steps=150, batch=512, eval_every=50)
+    print({n: [round(v, 4) for _, v in c] for n, c in curves.items()}, counts)
+    for n, c in curves.items():
+        vals = [v for _, v in c]
+        assert np.all(np.isfinite(vals)) and vals[-1] < vals[0], (n, vals)
+    assert counts[5] == 1296601 and counts[3] < counts[5]
