@@ -65,23 +65,43 @@ def test_stencil_five_matches_the_standard_kernel(env):
     assert torch.equal(std, gen)
 
 
+def _all_active(p, din):
+    """Non-negative weights and positive biases: with non-negative descriptors every ReLU
+    input is positive, so FP32 and FP64 take the same branches everywhere."""
+    flat = np.abs(p) * 0.05
+    off = 0
+    for name, shp, _ in W.param_shapes(din=din):
+        size = int(np.prod(shp))
+        if name.startswith("b"):
+            flat[off:off + size] = 0.01
+        off += size
+    return flat.astype(np.float32)
+
+
 @pytest.mark.parametrize("n", [3, 5, 7])
 def test_stencil_network_forward_and_gradient(env, n):
     api, ctx, vol, orc = env
     x, d, wl = _queries(333, seed=13)
     z = orc.descriptor_stencil(n, x, d, wl, f32=True)
     din = z.shape[2]
-    p = W.he_init(seed=3, din=din)
-    assert p.size == ctx.stencil_param_count(n)
-    pc, zc = torch.from_numpy(p).cuda(), torch.from_numpy(z).cuda()
-    g = ctx.stencil_forward(n, pc, zc).double().cpu().numpy()
-    ref = oracle.mlp_forward(p.astype(np.float64), z.astype(np.float64), din=din)
-    assert np.linalg.norm(g - ref) <= F32_REL * np.linalg.norm(ref)
+    zc = torch.from_numpy(z).cuda()
     dout = np.random.default_rng(7).normal(size=z.shape[0])
-    dp = ctx.stencil_backward(n, pc, zc, torch.from_numpy(dout.astype(np.float32)).cuda()).double().cpu().numpy()
-    ctx.sync_status()
-    dref = oracle.mlp_backward(p.astype(np.float64), z.astype(np.float64), dout, din=din)
-    assert np.linalg.norm(dp - dref) <= 1e-4 * np.linalg.norm(dref)
+    dc = torch.from_numpy(dout.astype(np.float32)).cuda()
+    he = W.he_init(seed=3, din=din)
+    assert he.size == ctx.stencil_param_count(n)
+    for p, grad_tol in ((_all_active(he, din), 1e-4), (he, 5e-3)):
+        pc = torch.from_numpy(p).cuda()
+        g = ctx.stencil_forward(n, pc, zc).double().cpu().numpy()
+        ref = oracle.mlp_forward(p.astype(np.float64), z.astype(np.float64), din=din)
+        assert np.linalg.norm(g - ref) <= F32_REL * np.linalg.norm(ref)
+        dp = ctx.stencil_backward(n, pc, zc, dc).double().cpu().numpy()
+        ctx.sync_status()
+        dref = oracle.mlp_backward(p.astype(np.float64), z.astype(np.float64), dout, din=din)
+        # at He initialisation a few ReLU inputs lie within FP32 rounding of zero (the
+        # 46-wide stencil has two at 5e-8 of their layer's scale): FP32 takes the other
+        # branch there and re-routes those rows' gradients, hence the looser bound
+        rel = np.linalg.norm(dp - dref) / np.linalg.norm(dref)
+        assert rel <= grad_tol, (n, rel)
 
 
 def test_stencil_train_step_matches_oracle(env):
