@@ -63,3 +63,30 @@ def test_argument_checks_without_a_device(libpath):
                L.rpnn_get_autotune(None, None, 0, None),
                L.rpnn_render_env(None, 0, None, None, None, 1, None, None, None)):
         assert rc == -2    # RPNN_ERR_HANDLE
+
+
+def test_phase_and_stencil_entry_points_check_arguments_without_a_device(libpath):
+    """The Lorenz-Mie option and the stencil-size entry points reject a null context, and
+    the stencil widths and parameter counts follow their definitions (host-only calls)."""
+    import torch  # noqa: F401
+    L = ctypes.CDLL(libpath)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.rpnn_set_phase_function.argtypes = [vp, i32, i32]
+    L.rpnn_stencil_param_count.argtypes = [i32]
+    L.rpnn_stencil_param_count.restype = i64
+    L.rpnn_stencil_descriptors.argtypes = [vp, i32, i32, vp, vp, vp, i32, i64, vp, vp]
+    L.rpnn_stencil_forward.argtypes = [vp, i32, vp, vp, i64, vp, vp]
+    L.rpnn_stencil_backward.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp]
+    L.rpnn_stencil_train_step.argtypes = [vp, i32, vp, vp, i32, vp, i64, vp, vp, vp, vp, vp]
+    for rc in (L.rpnn_set_phase_function(None, 0, 1),
+               L.rpnn_stencil_descriptors(None, 0, 3, None, None, None, 0, 1, None, None),
+               L.rpnn_stencil_forward(None, 3, None, None, 1, None, None),
+               L.rpnn_stencil_backward(None, 3, None, None, 1, None, None, None),
+               L.rpnn_stencil_train_step(None, 3, None, None, 1, None, 1, None, None, None, None, None)):
+        assert rc == -2    # RPNN_ERR_HANDLE
+    for n in range(2, 10):
+        din = n * n * (2 * n - 1) + 1
+        expect = 10 * (200 * din + 200 + 200 * 200 + 200) + 9 * 200 * 200 + 2 * (200 * 200 + 200) + 201
+        assert L.rpnn_stencil_param_count(n) == expect
+    assert L.rpnn_stencil_param_count(5) == 1296601
+    assert L.rpnn_stencil_param_count(1) == -1 and L.rpnn_stencil_param_count(10) == -1
