@@ -1,8 +1,9 @@
 """CPU oracle for the RPNN hot path (TEST INFRASTRUCTURE ONLY).
 
 A plain C implementation (``rpnn_oracle.c``) of what the GPU library computes,
-written from Kallweit et al., "Deep Scattering" (Sec. 3.2 Eq. 1, Sec. 4.2-4.4,
-Sec. 5, Sec. 6), wrapped here with ctypes + numpy; the plain MLPs of the architecture
+written from Kallweit et al., "Deep Scattering" (Sec. 3.1 Lorenz-Mie phase function and its
+chopped form, Sec. 3.2 Eq. 1, Sec. 4.2-4.4, Sec. 5, Sec. 6, Sec. 7's stencil sizes), wrapped
+here with ctypes + numpy; the plain MLPs of the architecture
 comparison (Sec. 7) and the environment superposition (Sec. 4.4) are written here in
 numpy / Python directly.  Only ``tests/``, the smoke
 check and the benchmark's ``cpu_baseline`` / reference leg may import this

@@ -1,7 +1,8 @@
 /*
  * rpnn_oracle.c -- CPU reference for the RPNN hot path (TEST INFRASTRUCTURE ONLY).
  *
- * Kallweit et al., "Deep Scattering" (Sec. 3.2 Eq. 1, Sec. 4.2-4.4, Sec. 5, Sec. 6).
+ * Kallweit et al., "Deep Scattering" (Sec. 3.1 Lorenz-Mie phase function, full and chopped;
+ * Sec. 3.2 Eq. 1, Sec. 4.2-4.4, Sec. 5, Sec. 6; Sec. 7's stencil sizes).
  * Plain loops, FP64 unless a function name ends in _f32.  No blocking, fusion or
  * reordering beyond what the paper's definitions state; every reading the paper
  * leaves open is fixed in the comments where it is taken.
