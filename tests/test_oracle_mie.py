@@ -30,6 +30,18 @@ def test_no_absorption_conserves_energy_and_large_spheres_extinguish_twice(orc):
     assert qe > qs * 1.05
 
 
+@pytest.mark.parametrize("x,m_im", [(0.5, 0.0), (3.0, 0.0), (25.0, 0.0), (10.0, 0.05)])
+def test_angular_intensity_integrates_to_the_scattering_efficiency(orc, x, m_im):
+    """Q_sca from the coefficient series (sum of (2n+1)(|a_n|^2 + |b_n|^2)) equals the
+    integral of the angular intensity, (2 / x^2) int_{-1}^{1} (|S1|^2 + |S2|^2)/2 dmu, which
+    runs through the angular functions pi_n, tau_n instead (Bohren & Huffman's Eq. 4.61 and
+    the definition of the scattering cross section)."""
+    mu, w = np.polynomial.legendre.leggauss(1500)
+    s11, _, qs = orc.mie_single(x, 1.333, m_im, mu)
+    q_int = 2.0 / (x * x) * float((w * s11).sum())
+    assert abs(q_int - qs) <= 1e-9 * qs, (q_int, qs)
+
+
 def test_cloud_phase_table(orc):
     p, cdf, ce = orc.lm_table()
     assert p.size == orc.LM_BINS and np.all(p > 0)
