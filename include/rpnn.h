@@ -137,8 +137,10 @@ rpnn_status rpnn_set_iteration_cap(rpnn_ctx* ctx, int32_t vol, int64_t cap);
  * the scattered light) renormalised, in a medium of extinction (1 - f albedo) mu_t and
  * albedo (1 - f) albedo / (1 - f albedo); light reaches every vertex (next-event shadow
  * rays) through that thinner medium, camera rays and record sampling see the full one.
- * (The paper's own tables and chop angle are in its unavailable supplement.)
- * Errors: RPNN_ERR_ARG for another kind, RPNN_ERR_HANDLE for an unknown volume. */
+ * (The paper's own tables and chop angle are in its unavailable supplement.)  The first
+ * Lorenz-Mie selection in a context uploads both tables (context-owned, 43 KB) and
+ * synchronises the default stream.  Errors: RPNN_ERR_ARG for another kind, RPNN_ERR_HANDLE
+ * for an unknown volume. */
 enum { RPNN_PHASE_HG = 0, RPNN_PHASE_LORENZ_MIE = 1, RPNN_PHASE_LORENZ_MIE_CHOPPED = 2 };
 #define RPNN_LM_BINS 1800
 #define RPNN_LM_CHOP_BINS 50
@@ -364,7 +366,9 @@ rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t 
  * standard one (Sec. 4.3) with V^k of width din: parameters (FP32, caller-owned, flat) in
  * the order of rpnn_set_weights.  FP32 CUDA-core GEMMs; at most 2^20 rows per call.
  * Errors: RPNN_ERR_ARG for n_xy outside [2, 9], a bad row count or a null pointer;
- * RPNN_ERR_HANDLE / RPNN_ERR_STATE for an unknown volume or one without rpnn_build_mips. */
+ * RPNN_ERR_HANDLE for an unknown volume or one without rpnn_build_mips.  The first
+ * rpnn_stencil_descriptors call on a pyramid builds its levels as plain FP32 (volume-owned,
+ * about 1.14x the grid) on the given stream. */
 int64_t rpnn_stencil_param_count(int32_t n_xy);   /* -1 for n_xy outside [2, 9] */
 /* Descriptors of q shading points (dev_x, dev_d [q][3]; light directions dev_wl [3] per
  * point at stride wl_stride floats, 0 for one shared direction) to dev_desc. */
