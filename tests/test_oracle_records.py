@@ -104,3 +104,32 @@ def test_label_stopping_rule(orc):
     # re-estimating with the same number of paths reproduces the label (same streams)
     rr, m, _ = v.estimate_Li(7, 3, r["x"], r["d"], r["wl"], r["npaths"])
     assert abs(m - r["label"]) < 1e-12 * max(1.0, m)
+
+
+def test_record_positions_in_a_thin_medium_follow_the_density(orc):
+    """Sec. 5.1's sampler in the optically thin limit: rays with directions uniform on the
+    sphere and origins uniform over the bounding sphere's cross-section are a uniform,
+    isotropic flux, so first collisions fall with density proportional to mu(x) -- each
+    coordinate's marginal is the trilinear ramp profile of the constant cube -- and, since the
+    chords through the cube integrate to its volume from every direction, the directions of
+    the rays that collide stay uniform (cos theta uniform on [-1, 1])."""
+    from scipy import integrate, stats
+    mu_thin = 0.01
+    v = orc.Volume(np.full((N, N, N), mu_thin, np.float32), 0.5, 0.0)
+    xs, dz, lz = [], [], []
+    for rec in range(3000):
+        r = v.gen_record(901, rec, rel_ci=1.0, n_min=1, n_max=1)
+        assert r["status"] == 0
+        xs.append(r["x"])
+        dz.append(r["d"][2])
+        lz.append(r["wl"][2])
+    xs = np.array(xs)
+    grid = np.linspace(0.0, 1.0, 801)
+    prof = ramp(grid * N - 0.5)
+    cdf = integrate.cumulative_trapezoid(prof, grid, initial=0.0)
+    cdf /= cdf[-1]
+    for a in range(3):
+        assert stats.kstest(xs[:, a], lambda t: np.interp(t, grid, cdf)).pvalue > 1e-3, a
+    assert stats.kstest(dz, stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    assert stats.kstest(lz, stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    v.close()
