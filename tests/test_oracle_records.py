@@ -102,8 +102,16 @@ def test_label_stopping_rule(orc):
     assert r["half_width"] <= 0.05 * r["label"]
     assert r["npaths"] >= 64
     # re-estimating with the same number of paths reproduces the label (same streams)
-    rr, m, _ = v.estimate_Li(7, 3, r["x"], r["d"], r["wl"], r["npaths"])
+    rr, m, var = v.estimate_Li(7, 3, r["x"], r["d"], r["wl"], r["npaths"])
     assert abs(m - r["label"]) < 1e-12 * max(1.0, m)
+    # the half-width is the normal 95 % quantile times the standard error of the mean
+    from scipy import stats
+    z95 = stats.norm.ppf(0.975)
+    assert abs(r["half_width"] - z95 * math.sqrt(var / r["npaths"])) <= 1e-4 * r["half_width"]
+    # and the rule stopped at the first path count that met it (after n_min)
+    if r["npaths"] > 64:
+        _, m1, var1 = v.estimate_Li(7, 3, r["x"], r["d"], r["wl"], r["npaths"] - 1)
+        assert not (m1 > 0 and z95 * math.sqrt(var1 / (r["npaths"] - 1)) <= 0.05 * m1 * (1 - 1e-4))
 
 
 def test_record_positions_in_a_thin_medium_follow_the_density(orc):
