@@ -203,3 +203,41 @@ def test_brick_tracking_matches_global_majorant_in_distribution(orc):
     T = np.array([vol.ratio_track(o, d, 99, s, 0) for s in range(4000)])
     assert abs(T.mean() - math.exp(-tau)) <= 4 * T.std() / math.sqrt(T.size) + 1e-4
     vol.close()
+
+
+def test_furnace(orc):
+    """Energy conservation of the whole transport (the furnace test): a non-absorbing cube
+    (albedo 1) under a uniform environment of unit radiance -- here 200 directional lights
+    on a Fibonacci sphere, each of irradiance 4 pi / 200 (Sec. 4.4's environment as
+    directional samples) -- has unit radiance everywhere inside, so at every collision the
+    direct plus path-traced in-scattering add up to 1 on average, and a pixel whose ray meets
+    the medium with probability 1 - exp(-tau) sees that fraction of it."""
+    v = cube(orc, 1.0, 0.3)
+    y0, z0 = 3.5 / N, 4.5 / N
+    K = 200
+    i = np.arange(K) + 0.5
+    zc = 1 - 2 * i / K
+    ph = math.pi * (1 + 5 ** 0.5) * i
+    r = np.sqrt(1 - zc * zc)
+    dirs = np.stack([r * np.cos(ph), r * np.sin(ph), zc], 1)
+    W_, H_, spp = 32, 32, 8
+    cam = {"cam_pos": [-1.0, y0, z0], "cam_fwd": [1.0, 0, 0], "cam_right": [0, 0, -1.0],
+           "cam_up": [0, 1.0, 0], "tan_half_fov_y": 1e-9, "width": W_, "height": H_,
+           "spp": spp, "seed": 77, "light_dir": dirs[0], "light_E": 1.0}
+    pix = np.arange(W_ * H_)
+    irr = np.full(K, 4 * math.pi / K)
+    px = v.render_pixels_env(cam, pix, dirs, irr, mode=1)
+    hits = np.array([[v.primary(cam, int(p), s)[0] == 1 for s in range(spp)] for p in pix])
+    # the visible-point fraction is Beer-Lambert's
+    q = 1.0 - math.exp(-tau_axis(0, 1))
+    assert abs(hits.mean() - q) < 4 * math.sqrt(q * (1 - q) / hits.size)
+    # in-scattered radiance at the collisions: unit on average (pixel sums over hits only)
+    per_hit = px * spp
+    n_hit = hits.sum(1)
+    mean = per_hit.sum() / n_hit.sum()
+    # standard error from the per-pixel sums (ratio estimator)
+    se = np.sqrt(((per_hit - mean * n_hit) ** 2).sum()) / n_hit.sum()
+    assert abs(mean - 1.0) < 4 * se + 0.01, (mean, se)
+    # single scattering alone falls well short of it
+    ss = v.render_pixels_env(cam, pix, dirs, irr, mode=0) * spp
+    assert ss.sum() / n_hit.sum() < 0.8
