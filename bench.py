@@ -187,19 +187,62 @@ def make_workload(rank, device=None):
     return dens, cam, params
 
 
-def cpu_sample(dens, cam, params, npix, seed=0):
-    """Oracle render of `npix` sampled pixels; returns (pixels, values, queries, seconds, threads)."""
+def oracle_warm(v, shape):
+    """Builds every FP64 pyramid level the oracle's descriptor reads (it builds them on first
+    use), so no timed oracle step pays for them: one descriptor at the box centre."""
+    centre = np.array(shape[::-1], np.float64) / max(shape) / 2
+    v.descriptor(centre[None], np.array([[0.0, 0.0, 1.0]]), np.array([0.0, 1.0, 0.0]))
+
+
+def oracle_pixels(dens, cam, params, npix, seed=0):
+    """Oracle render of `npix` sampled pixels (untimed; for the image error)."""
     import oracle
     v = oracle.Volume(dens)
     pix = np.sort(np.random.default_rng(seed).choice(cam["width"] * cam["height"], npix, replace=False))
+    vals = v.render_pixels(cam, pix, params=params.astype(np.float64), nthreads=os.cpu_count() or 1)
+    v.close()
+    return pix, vals
+
+
+def oracle_rate(dens, cam, params, npix, steps, warmup, seed=123):
+    """The CPU oracle's render rate on the benchmark workload: `warmup` + `steps` renders of
+    `npix` random pixels each, on all host threads, after every pyramid level was built.
+    Returns (queries per step, seconds per step, threads) of the timed steps."""
+    import oracle
+    v = oracle.Volume(dens)
     nthreads = os.cpu_count() or 1
-    # pyramid levels are built on first use: do it outside the timed region
-    v.render_pixels(cam, pix[:1], params=params.astype(np.float64))
-    hits = sum(1 for p in pix if v.primary(cam, int(p), 0)[0] == 1)
-    t0 = time.perf_counter()
-    vals = v.render_pixels(cam, pix, params=params.astype(np.float64), nthreads=nthreads)
-    dt = time.perf_counter() - t0
-    return pix, vals, hits, dt, nthreads
+    p64 = params.astype(np.float64)
+    oracle_warm(v, dens.shape)
+    rng = np.random.default_rng(seed)
+    times, queries = [], []
+    for i in range(warmup + steps):
+        pix = np.sort(rng.choice(cam["width"] * cam["height"], npix, replace=False))
+        hits = sum(1 for p in pix if v.primary(cam, int(p), 0)[0] == 1)
+        t0 = time.perf_counter()
+        v.render_pixels(cam, pix, params=p64, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+            queries.append(hits)
+    v.close()
+    return queries, times, nthreads
+
+
+def cpu_baseline_subprocess(npix, steps, warmup):
+    """The reference arm's own measurement (the CPU oracle, `bench.py --impl reference`) run
+    in a fresh single-rank process, so the oracle's threads share the host with nothing the
+    GPU run left behind; returns that line's cpu_baseline."""
+    import subprocess
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT",
+                        "GROUP_RANK", "ROLE_RANK", "TORCHELASTIC_RUN_ID")}
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+           "--warmup", str(warmup), "--ref-pixels", str(npix)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("CPU oracle run failed: " + r.stderr[-2000:])
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    return line["cpu_baseline"]
 
 
 BATCH_WORKLOAD = ("batched serving: 16 fBm clouds (seeds 200-215), edges log-uniform in [64, 512], FP16 "
@@ -683,6 +726,7 @@ def run_large(args, ws, rank, local):
         v = oracle.Volume(dens_host)
         npix = args.large_oracle_pixels
         pix = np.sort(np.random.default_rng(7).choice(1920 * 1080, npix, replace=False))
+        oracle_warm(v, dens_host.shape)
         t0 = time.perf_counter()
         vals = v.render_pixels(cam, pix, params=params.astype(np.float64), nthreads=os.cpu_count() or 1)
         dt = time.perf_counter() - t0
@@ -702,25 +746,11 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     dens, cam, params = make_workload(0, device="cpu")
-    import oracle
-    v = oracle.Volume(dens)
-    nthreads = os.cpu_count() or 1
     npix = args.ref_pixels
-    rng = np.random.default_rng(123)
-    p64 = params.astype(np.float64)
-    v.render_pixels(cam, np.arange(1), params=p64)
-    times, queries = [], []
-    for i in range(args.warmup + args.steps):
-        pix = np.sort(rng.choice(cam["width"] * cam["height"], npix, replace=False))
-        hits = sum(1 for p in pix if v.primary(cam, int(p), 0)[0] == 1)
-        t0 = time.perf_counter()
-        v.render_pixels(cam, pix, params=p64, nthreads=nthreads)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-            queries.append(hits)
+    queries, times, nthreads = oracle_rate(dens, cam, params, npix, args.steps, args.warmup)
     T = sum(times)
     val = sum(queries) / T
+    rates = sorted(q / t for q, t in zip(queries, times))
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
@@ -728,7 +758,10 @@ def run_reference(args, ws, rank):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": f"{npix} random pixels of the 512x512 image per step"},
         "cpu_baseline": {"value": val, "unit": "queries/s", "cores": nthreads, "kind": "oracle",
-                         "sample": f"{npix} pixels per step x {args.steps} steps"},
+                         "sample": f"{npix} random pixels per step x {args.steps} timed steps after "
+                                   f"{args.warmup} warm-up steps, every FP64 pyramid level built first",
+                         "per_step_median": rates[len(rates) // 2], "per_step_min": rates[0],
+                         "per_step_max": rates[-1]},
         "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -741,8 +774,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"])
-    ap.add_argument("--cpu-pixels", type=int, default=2048)
-    ap.add_argument("--ref-pixels", type=int, default=512)
+    ap.add_argument("--cpu-pixels", type=int, default=2048,
+                    help="pixels the FP64 oracle renders for the image error")
+    ap.add_argument("--ref-pixels", type=int, default=4096,
+                    help="pixels the CPU oracle renders per timed step (reference arm and cpu_baseline)")
+    ap.add_argument("--cpu-steps", type=int, default=10,
+                    help="timed oracle steps of the cpu_baseline (a fresh reference-arm process)")
     ap.add_argument("--large-oracle-pixels", type=int, default=10000,
                     help="pixels the FP64 oracle renders for the large workload's error")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1036,10 +1073,8 @@ def main():
     if fp8_form:
         line["fp8_form"] = fp8_form
     if rank == 0 and not args.no_cpu:
-        pix, vals, hits, dt, nth = cpu_sample(dens, cam, params, args.cpu_pixels)
-        line["cpu_baseline"] = {"value": hits / dt, "unit": "queries/s", "cores": nth, "kind": "oracle",
-                                "sample": f"{args.cpu_pixels} random pixels of the 512x512 image "
-                                          f"({hits} shading queries), FP64"}
+        line["cpu_baseline"] = cpu_baseline_subprocess(args.ref_pixels, args.cpu_steps, 3)
+        pix, vals = oracle_pixels(dens, cam, params, args.cpu_pixels)
         got = img.double().cpu().numpy().ravel()[pix]
         err = float(np.sqrt(np.mean((got - vals) ** 2)) / max(np.sqrt(np.mean(vals ** 2)), 1e-30))
         line["error_vs_fp64_oracle"] = {"pixels": int(pix.size), "rel_rmse": err}

@@ -205,14 +205,16 @@ rpnn_status rpnn_mlp_forward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_d
 rpnn_status rpnn_calibrate_fp8(rpnn_ctx* ctx, const float* dev_desc, int64_t q, void* stream);
 
 /* ---- FP32 network forward without device allocation ----------------------------------------
- * The paper has no counterpart to this entry point.  It exists for callers that must not
- * allocate device memory at call time: code running while another component captures the
- * stream into a CUDA graph (an allocation there breaks or serialises the capture), hosts
- * whose device memory is owned by a foreign allocator or a fixed budget, and real-time loops
- * that forbid allocation after start-up.  It computes the same g = RPNN(z) as
- * rpnn_mlp_forward with precision RPNN_F32 (same kernels, same order), for at most
- * RPNN_STATIC_MAX_ROWS rows of FP32 descriptors, with the caller's FP32 parameter vector
- * (layout above) and without a context.
+ * The paper has no counterpart to this entry point.  It serves callers that cannot call
+ * cudaMalloc when they run the network: hosts whose device memory is all owned by their own
+ * allocator or reserved up front under a fixed budget (a game engine, a serving runtime),
+ * and real-time loops that allow no allocation after start-up (cudaMalloc and cudaFree may
+ * block and synchronise the device).  It computes g = RPNN(z) for at most
+ * RPNN_STATIC_MAX_ROWS rows of FP32 descriptors (layout of rpnn_extract_descriptors) with
+ * the caller's FP32 parameter vector (layout above), without a context, through the same
+ * routine and the same FP32 CUDA-core GEMM kernel as rpnn_mlp_forward with precision
+ * RPNN_F32, with the GEMM's default tile.  The result equals rpnn_mlp_forward's bit for bit:
+ * tile shapes change no result bit and a forward GEMM is never split along K.
  *  - Scratch: one static device array of 3 * RPNN_STATIC_MAX_ROWS * 200 floats (9.8 MB),
  *    present on every GPU that loads the library until the process exits.  It keeps the
  *    last call's contents; nothing in it needs to start at zero (every layer writes its
@@ -320,16 +322,21 @@ rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t 
 /* Gradient of sum_i dout_i * g(z_i) w.r.t. the parameters currently set by
  * rpnn_set_weights (the chain rule in the training precision, rpnn_set_train_precision:
  * FP32 CUDA cores by default, or BF16 tensor-core GEMMs), written (not accumulated) to
- * dev_dparams (RPNN_NPARAMS floats).  dev_desc: q rows, FP32. */
-rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q,
+ * dev_dparams (RPNN_NPARAMS floats).  dev_desc: q rows [10][RPNN_DESC_STRIDE] of desc_dtype
+ * RPNN_F32 or RPNN_BF16 (BF16 records take half the memory: 4.8 KB instead of 9.6 KB per
+ * row).  The BF16 training form rounds FP32 rows to BF16 itself, so both dtypes give it the
+ * same result for BF16-representable rows; the FP32 form widens BF16 rows exactly (into
+ * context scratch).  Errors: RPNN_ERR_ARG for another dtype, q outside [1, 4194240] or a
+ * null pointer; RPNN_ERR_STATE before rpnn_set_weights. */
+rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
                               const float* dev_dout, float* dev_dparams, void* stream);
 typedef struct { float lr, beta1, beta2, eps; } rpnn_adam_cfg;
-/* One optimiser step (Sec. 5.2): forward on `batch` FP32 descriptor rows, loss
- * mean (log(1+g) - log(1+L))^2 written as FP64 to *dev_loss (device), backward, Adam
- * (step >= 1, bias-corrected) on the caller's FP32 parameters dev_params with moments
- * dev_m, dev_v (RPNN_NPARAMS each, updated in place), then the library's weight copies
- * are refreshed from the updated parameters. */
-rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* dev_target,
+/* One optimiser step (Sec. 5.2): forward on `batch` descriptor rows (desc_dtype RPNN_F32 or
+ * RPNN_BF16, as rpnn_mlp_backward), loss mean (log(1+g) - log(1+L))^2 written as FP64 to
+ * *dev_loss (device), backward, Adam (step >= 1, bias-corrected) on the caller's FP32
+ * parameters dev_params with moments dev_m, dev_v (RPNN_NPARAMS each, updated in place),
+ * then the library's weight copies are refreshed from the updated parameters. */
+rpnn_status rpnn_train_step(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, const float* dev_target,
                             int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
                             float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
                             void* stream);

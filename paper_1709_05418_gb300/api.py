@@ -123,8 +123,8 @@ def load():
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
                                  _vp, _vp],
-            "rpnn_mlp_backward": [_vp, _vp, i64, _vp, _vp, _vp],
-            "rpnn_train_step": [_vp, _vp, _vp, i32, C.POINTER(AdamCfg), i64, _vp, _vp, _vp,
+            "rpnn_mlp_backward": [_vp, _vp, i32, i64, _vp, _vp, _vp],
+            "rpnn_train_step": [_vp, _vp, i32, _vp, i32, C.POINTER(AdamCfg), i64, _vp, _vp, _vp,
                                 _vp, _vp],
             "rpnn_set_profiling": [_vp, i32],
             "rpnn_set_autotune": [_vp, i32],
@@ -168,6 +168,8 @@ def _dtype_code(t):
 
 class Context:
     """One rpnn_ctx bound to the current CUDA device."""
+
+    train_precision = F32
 
     def __init__(self):
         self.L = load()
@@ -316,6 +318,7 @@ class Context:
     def set_train_precision(self, precision):
         """F32 (default) or BF16 arithmetic for train_step and mlp_backward."""
         self._check(self.L.rpnn_set_train_precision(self.h, precision))
+        self.train_precision = precision
 
     def set_autotune(self, on: bool):
         self._check(self.L.rpnn_set_autotune(self.h, 1 if on else 0))
@@ -388,7 +391,8 @@ class Context:
         q = desc.shape[0]
         if out is None:
             out = torch.empty(NPARAMS, dtype=torch.float32, device="cuda")
-        self._check(self.L.rpnn_mlp_backward(self.h, _ptr(desc), q, _ptr(dout), _ptr(out), _stream()))
+        self._check(self.L.rpnn_mlp_backward(self.h, _ptr(desc), _dtype_code(desc), q, _ptr(dout), _ptr(out),
+                                             _stream()))
         return out
 
     def train_step(self, desc, target, params, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999,
@@ -396,7 +400,7 @@ class Context:
         if loss is None:
             loss = torch.empty(1, dtype=torch.float64, device="cuda")
         cfg = AdamCfg(lr, beta1, beta2, eps)
-        self._check(self.L.rpnn_train_step(self.h, _ptr(desc), _ptr(target), desc.shape[0],
+        self._check(self.L.rpnn_train_step(self.h, _ptr(desc), _dtype_code(desc), _ptr(target), desc.shape[0],
                                            C.byref(cfg), step, _ptr(params), _ptr(m), _ptr(v),
                                            _ptr(loss), _stream()))
         return loss

@@ -47,25 +47,47 @@ void DevBuf::release() {
 using namespace rpnn;
 
 namespace {
+// Training descriptors as the training precision reads them: the BF16 form reads FP32 or
+// BF16 rows itself; the FP32 form reads FP32 rows, so BF16 rows are widened (exactly) into
+// context scratch first.  *d32 is the FP32 view (null for the BF16 form).
+rpnn_status train_desc(Ctx& c, const void* desc, int dtype, int64_t q, const float** d32, cudaStream_t s) {
+    *d32 = nullptr;
+    if (c.train_precision == RPNN_BF16) return RPNN_OK;
+    if (dtype == RPNN_F32) { *d32 = static_cast<const float*>(desc); return RPNN_OK; }
+    const int64_t n = q * RPNN_K * RPNN_DESC_STRIDE;
+    rpnn_status st = c.t_desc32.reserve((size_t)n * sizeof(float));
+    if (st) return st;
+    st = launch_bf16_to_f32(desc, c.t_desc32.as<float>(), n, c.num_sms, s);
+    if (st) return st;
+    *d32 = c.t_desc32.as<float>();
+    return RPNN_OK;
+}
+
 // Forward with saved activations in the context's training precision (FP32 CUDA cores,
 // or BF16 tensor-core GEMMs with FP32 master weights); the prediction goes to t_out.
-rpnn_status train_forward(Ctx& c, const float* desc, int64_t q, cudaStream_t s) {
+rpnn_status train_forward(Ctx& c, const void* desc, int dtype, const float* d32, int64_t q, cudaStream_t s) {
     rpnn_status st = c.t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
     if (!st) st = c.t_out.reserve(q * sizeof(float));
     if (st) return st;
     if (c.train_precision == RPNN_BF16) {
         st = c.t_saved16.reserve(train_bf16_saved_elems(q) * 2);
         if (st) return st;
-        return mlp_forward_bf16_train(c, desc, q, c.t_out.as<float>(), c.t_saved.as<float>(),
+        return mlp_forward_bf16_train(c, desc, dtype, q, c.t_out.as<float>(), c.t_saved.as<float>(),
                                       c.t_saved16.as<uint16_t>(), s);
     }
-    return mlp_forward_f32(c, desc, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
+    return mlp_forward_f32(c, d32, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
 }
 
-rpnn_status train_backward(Ctx& c, const float* desc, int64_t q, const float* dout, float* dP, cudaStream_t s) {
+rpnn_status train_backward(Ctx& c, const float* d32, int64_t q, const float* dout, float* dP, cudaStream_t s) {
     if (c.train_precision == RPNN_BF16)
         return mlp_backward_bf16_train(c, q, c.t_saved.as<float>(), c.t_saved16.as<uint16_t>(), dout, dP, s);
-    return mlp_backward_f32(c, desc, q, c.t_saved.as<float>(), dout, dP, s);
+    return mlp_backward_f32(c, d32, q, c.t_saved.as<float>(), dout, dP, s);
+}
+
+rpnn_status check_train_desc(const void* desc, int dtype) {
+    (void)desc;
+    if (dtype != RPNN_F32 && dtype != RPNN_BF16) { set_error("training descriptors must be F32 or BF16"); return RPNN_ERR_ARG; }
+    return RPNN_OK;
 }
 }  // namespace
 
@@ -112,7 +134,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
-                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16, &c->lm_table, &c->lmc_table};
+                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16, &c->t_desc32, &c->lm_table, &c->lmc_table};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
@@ -671,7 +693,8 @@ rpnn_status rpnn_stencil_forward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_p
     if (!dev_params || !dev_desc || !dev_out) { set_error("null pointer"); return RPNN_ERR_ARG; }
     rpnn_status st = ensure_rows(c, q, true);
     if (st) return st;
-    return rpnn_forward_f32(*c, nd, dev_params, dev_desc, q, nullptr, dev_out, nullptr, (cudaStream_t)stream);
+    float* const scr[3] = {c->act0.as<float>(), c->act1.as<float>(), c->act2.as<float>()};
+    return rpnn_forward_f32(c, nd, dev_params, dev_desc, q, nullptr, dev_out, nullptr, scr, (cudaStream_t)stream);
 }
 
 // forward with saved activations (t_saved), prediction to t_out
@@ -680,7 +703,7 @@ static rpnn_status stencil_fwd_saved(Ctx& c, const NetDims& nd, const float* P, 
     rpnn_status st = c.t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
     if (!st) st = c.t_out.reserve(q * sizeof(float));
     if (st) return st;
-    return rpnn_forward_f32(c, nd, P, desc, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
+    return rpnn_forward_f32(&c, nd, P, desc, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), nullptr, s);
 }
 
 rpnn_status rpnn_stencil_backward(rpnn_ctx* ctx, int32_t n_xy, const float* dev_params, const float* dev_desc,
@@ -838,20 +861,24 @@ rpnn_status rpnn_gen_records(rpnn_ctx* ctx, int32_t vol, int64_t first, int64_t 
                           dev_label, dev_npaths, (cudaStream_t)stream);
 }
 
-rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const float* dev_desc, int64_t q, const float* dev_dout,
-                              float* dev_dparams, void* stream) {
+rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, int64_t q,
+                              const float* dev_dout, float* dev_dparams, void* stream) {
     CHECK_CTX(ctx);
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (!c->weights_set) { set_error("rpnn_set_weights has not run"); return RPNN_ERR_STATE; }
     if (q <= 0 || q > 65535 * 64) { set_error("q must be in [1, %d]", 65535 * 64); return RPNN_ERR_ARG; }
     if (!dev_desc || !dev_dout || !dev_dparams) { set_error("null pointer"); return RPNN_ERR_ARG; }
-    cudaStream_t s = (cudaStream_t)stream;
-    rpnn_status st = train_forward(*c, dev_desc, q, s);
+    rpnn_status st = check_train_desc(dev_desc, desc_dtype);
     if (st) return st;
-    return train_backward(*c, dev_desc, q, dev_dout, dev_dparams, s);
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* d32 = nullptr;
+    st = train_desc(*c, dev_desc, desc_dtype, q, &d32, s);
+    if (!st) st = train_forward(*c, dev_desc, desc_dtype, d32, q, s);
+    if (st) return st;
+    return train_backward(*c, d32, q, dev_dout, dev_dparams, s);
 }
 
-rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* dev_target, int32_t batch,
+rpnn_status rpnn_train_step(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, const float* dev_target, int32_t batch,
                             const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
                             float* dev_v, double* dev_loss, void* stream) {
     CHECK_CTX(ctx);
@@ -864,17 +891,21 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const float* dev_desc, const float* d
         set_error("null pointer");
         return RPNN_ERR_ARG;
     }
+    rpnn_status st = check_train_desc(dev_desc, desc_dtype);
+    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t q = batch;
-    rpnn_status st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
+    st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
     if (!st) st = c->sample_val.reserve(q * sizeof(float));
     if (st) return st;
-    st = train_forward(*c, dev_desc, q, s);
+    const float* d32 = nullptr;
+    st = train_desc(*c, dev_desc, desc_dtype, q, &d32, s);
+    if (!st) st = train_forward(*c, dev_desc, desc_dtype, d32, q, s);
     if (st) return st;
     float* dg = c->sample_val.as<float>();
     st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
     if (st) return st;
-    st = train_backward(*c, dev_desc, q, dg, c->t_grad.as<float>(), s);
+    st = train_backward(*c, d32, q, dg, c->t_grad.as<float>(), s);
     if (st) return st;
     st = launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), RPNN_NPARAMS, step, *adam, s);
     if (st) return st;

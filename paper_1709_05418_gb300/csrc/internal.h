@@ -191,6 +191,7 @@ struct Ctx {
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
     DevBuf t_w16, t_saved16, t_scr16;   // BF16 training: weight image, activation copies, gradient scratch
+    DevBuf t_desc32;                    // FP32 widening of BF16 training descriptors (FP32 training form)
     int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
     DevBuf lm_table;         // Lorenz-Mie phase table, uploaded on first use
@@ -279,9 +280,6 @@ size_t mlp_saved_floats_per_row();
 void gemm_tile_shape(int tile, int* bm, int* bn, int* bk);
 // index of the tile (bm, bn, bk) in that table, or -1
 int gemm_tile_index(int bm, int bn, int bk);
-// FP32 forward with caller-provided parameters P and three q x 200 scratch buffers
-rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
-                                 float* s1, float* s2, cudaStream_t s);
 rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss,
                         float* dg, cudaStream_t s);
 rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,
@@ -334,8 +332,11 @@ rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const floa
 // activations): saved FP32 slots as mlp_forward_f32, BF16 copies in s16
 // (train_bf16_saved_elems(q) elements)
 size_t train_bf16_saved_elems(int64_t q);
-rpnn_status mlp_forward_bf16_train(Ctx& c, const float* desc, int64_t q, float* out, float* saved, uint16_t* s16,
-                                   cudaStream_t s);
+// desc: q rows [10][240] of dtype desc_dtype (RPNN_F32 or RPNN_BF16)
+rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int64_t q, float* out, float* saved,
+                                   uint16_t* s16, cudaStream_t s);
+// exact FP32 widening of n BF16 values
+rpnn_status launch_bf16_to_f32(const void* in, float* out, int64_t n, int sms, cudaStream_t s);
 rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
                                     float* dP, cudaStream_t s);
 
@@ -368,8 +369,11 @@ struct NetDims {
 };
 // The FP32 forward and backward of mlp_forward_f32 / mlp_backward_f32 for any NetDims and
 // parameter vector P (the two call these with the standard shape and the context's weights).
-rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
-                             const int* q_dev, float* out, float* saved, cudaStream_t s);
+// The forward's activations go to `saved` (22 slots of [q][200] and g) or, when it is null,
+// to the three [q][200] buffers scr[0..2].  c may be null: every GEMM then runs the default
+// tile without split-K and nothing is allocated (tile shapes change no result bit).
+rpnn_status rpnn_forward_f32(Ctx* c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                             const int* q_dev, float* out, float* saved, float* const scr[3], cudaStream_t s);
 rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
                               const float* saved, const float* dout, float* dP, cudaStream_t s);
 

@@ -393,8 +393,8 @@ const ParamLayout& param_layout() {
 // saved activations per row: o^1..o^10, F1^1..F1^10, o^11, o^12 (each 200), g
 size_t mlp_saved_floats_per_row() { return 22 * (size_t)RPNN_H + 1; }
 
-rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,
-                             const int* q_dev, float* out, float* saved, cudaStream_t s) {
+rpnn_status rpnn_forward_f32(Ctx* c, const NetDims& nd, const float* P, const float* desc, int64_t q,
+                             const int* q_dev, float* out, float* saved, float* const scr[3], cudaStream_t s) {
     const ParamLayout& L = *nd.L;
     const int M = (int)q;
     const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * nd.stride;
@@ -403,32 +403,32 @@ rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const fl
     rpnn_status st;
     for (int k = 0; k < RPNN_K; ++k) {
         if (saved) { o_cur = slot(k); f1 = slot(10 + k); }
-        else { o_cur = c.act0.as<float>(); f1 = c.act1.as<float>(); }
+        else { o_cur = scr[0]; f1 = scr[1]; }
         // F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)
         Seg z = seg(desc + k * nd.stride, ZS, 1, P + L.V[k], 1, nd.din, nd.din);
         if (k > 0) {
             Seg o = seg(o_prev, H, 1, P + L.W1[k], 1, H, RPNN_H);
-            st = gemm(&c, M, q_dev, RPNN_H, z, &o, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(c, M, q_dev, RPNN_H, z, &o, epi(f1, H, P + L.b1[k], 1), s);
         } else {
-            st = gemm(&c, M, q_dev, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
+            st = gemm(c, M, q_dev, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
         }
         if (st) return st;
         // o^k = relu(W2 F1 + b2 + o^{k-1})  (in place when not saving)
         Seg w2 = seg(f1, H, 1, P + L.W2[k], 1, H, RPNN_H);
-        st = gemm(&c, M, q_dev, RPNN_H, w2, nullptr, epi(o_cur, H, P + L.b2[k], 1, k > 0 ? o_prev : nullptr, H), s);
+        st = gemm(c, M, q_dev, RPNN_H, w2, nullptr, epi(o_cur, H, P + L.b2[k], 1, k > 0 ? o_prev : nullptr, H), s);
         if (st) return st;
         o_prev = o_cur;
     }
     // standard layers
-    float* t0 = saved ? slot(20) : c.act1.as<float>();
-    float* t1 = saved ? slot(21) : c.act2.as<float>();
-    st = gemm(&c, M, q_dev, RPNN_H, seg(o_prev, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr,
+    float* t0 = saved ? slot(20) : scr[1];
+    float* t1 = saved ? slot(21) : scr[2];
+    st = gemm(c, M, q_dev, RPNN_H, seg(o_prev, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr,
               epi(t0, H, P + L.bT[0], 1), s);
     if (st) return st;
-    st = gemm(&c, M, q_dev, RPNN_H, seg(t0, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr,
+    st = gemm(c, M, q_dev, RPNN_H, seg(t0, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr,
               epi(t1, H, P + L.bT[1], 1), s);
     if (st) return st;
-    st = gemm(&c, M, q_dev, 1, seg(t1, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
+    st = gemm(c, M, q_dev, 1, seg(t1, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
     if (st) return st;
     if (saved) RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float),
                                              cudaMemcpyDeviceToDevice, s));
@@ -438,35 +438,8 @@ rpnn_status rpnn_forward_f32(Ctx& c, const NetDims& nd, const float* P, const fl
 rpnn_status mlp_forward_f32(Ctx& c, const float* desc, int64_t q, const int* q_dev, float* out,
                             float* saved, cudaStream_t s) {
     const NetDims nd{&param_layout(), RPNN_DIN, RPNN_DESC_STRIDE};
-    return rpnn_forward_f32(c, nd, c.params32.as<float>(), desc, q, q_dev, out, saved, s);
-}
-
-rpnn_status mlp_forward_f32_with(const float* P, const float* desc, int64_t q, float* out, float* s0,
-                                 float* s1, float* s2, cudaStream_t s) {
-    const ParamLayout& L = param_layout();
-    const int M = (int)q;
-    const int64_t H = RPNN_H, ZS = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
-    float* o = s0;
-    float* f1 = s1;
-    rpnn_status st;
-    for (int k = 0; k < RPNN_K; ++k) {
-        Seg z = seg(desc + k * RPNN_DESC_STRIDE, ZS, 1, P + L.V[k], 1, RPNN_DIN, RPNN_DIN);
-        if (k > 0) {
-            Seg oo = seg(o, H, 1, P + L.W1[k], 1, H, RPNN_H);
-            st = gemm(nullptr, M, nullptr, RPNN_H, z, &oo, epi(f1, H, P + L.b1[k], 1), s);
-        } else {
-            st = gemm(nullptr, M, nullptr, RPNN_H, z, nullptr, epi(f1, H, P + L.b1[k], 1), s);
-        }
-        if (st) return st;
-        Seg w2 = seg(f1, H, 1, P + L.W2[k], 1, H, RPNN_H);
-        st = gemm(nullptr, M, nullptr, RPNN_H, w2, nullptr, epi(o, H, P + L.b2[k], 1, k > 0 ? o : nullptr, H), s);
-        if (st) return st;
-    }
-    st = gemm(nullptr, M, nullptr, RPNN_H, seg(o, H, 1, P + L.T[0], 1, H, RPNN_H), nullptr, epi(s1, H, P + L.bT[0], 1), s);
-    if (st) return st;
-    st = gemm(nullptr, M, nullptr, RPNN_H, seg(s1, H, 1, P + L.T[1], 1, H, RPNN_H), nullptr, epi(s2, H, P + L.bT[1], 1), s);
-    if (st) return st;
-    return gemm(nullptr, M, nullptr, 1, seg(s2, H, 1, P + L.T[2], 1, H, RPNN_H), nullptr, epi(out, 1, P + L.bT[2], 1), s);
+    float* const scr[3] = {c.act0.as<float>(), c.act1.as<float>(), c.act2.as<float>()};
+    return rpnn_forward_f32(&c, nd, c.params32.as<float>(), desc, q, q_dev, out, saved, scr, s);
 }
 
 rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const float* desc, int64_t q,

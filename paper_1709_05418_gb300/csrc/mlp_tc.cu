@@ -112,7 +112,6 @@ struct TcArgs {
     const int* q_dev;
     float* out;
     uint32_t* status;
-    unsigned long long* trace;  // optional per-block cycle counters (diagnostics), or null
 };
 
 // K bytes of layer l: a block's first layer reads [z | o] (block 1 has no o), every other
@@ -137,9 +136,6 @@ struct IssueState {
     uint32_t w0, z0, x0, w, z;
     uint32_t wbar0, zbar0, wbar, zbar, blk0;
     uint32_t sw, pw, sz, pz;
-    long long* tr;       // timeline base (block 0, diagnostics) or null
-    long long* stamp;    // per-stage stamps of this layer instance, or null
-    unsigned long long cyc;
 };
 
 // D[acc] (+)= A * B^T with operand descriptors given as low words and a common high word;
@@ -166,7 +162,7 @@ __device__ __forceinline__ void mma_lohi(uint32_t acc, uint32_t a_lo, uint32_t b
 // 128 bytes (four MMAs of 32 bytes).  RESID: the accumulator already holds o^{k-1}.
 // Activation byte c sits in 64-byte block c / 64 at half (c / 32) % 2; a stage reading
 // bytes up to c waits for publication c / 128 of the previous epilogue (parity pb).
-template <bool TRACE, bool FP8, int KB, int ZKB, bool RESID>
+template <bool FP8, int KB, int ZKB, bool RESID>
 __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_t pb) {
 #pragma unroll
     for (int k0 = 0; k0 < KB; k0 += SKB) {
@@ -174,11 +170,6 @@ __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_
         const bool hz = k0 < ZKB;
         const int need = k1 > ZKB ? (k1 - ZKB - 1) >> 7 : -1;
         const uint32_t pub = S.blk0 + BAR_STRIDE * (uint32_t)(need < 0 ? 0 : need);
-        long long t0 = 0;
-        if (TRACE) {
-            t0 = clock64();
-            if (S.stamp) S.stamp[(k0 / SKB) * 3] = t0;
-        }
         if (hz && need >= 0)
             tc::mbar_wait_issuer3(S.wbar, S.pw, S.zbar, S.pz, pub, pb, tc::kSpinLimit, S.abort_addr);
         else if (hz)
@@ -187,11 +178,6 @@ __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_
             tc::mbar_wait_issuer3(S.wbar, S.pw, pub, pb, S.none, 0u, tc::kSpinLimit, S.abort_addr);
         else
             tc::mbar_wait_issuer(S.wbar, S.pw, tc::kSpinLimit, S.abort_addr);
-        if (TRACE) {
-            const long long t1 = clock64();
-            S.cyc += (unsigned long long)(t1 - t0);
-            if (S.stamp) S.stamp[(k0 / SKB) * 3 + 1] = t1;
-        }
 #pragma unroll
         for (int j = 0; j < SKB / 32; ++j) {
             const int k = k0 + 32 * j;
@@ -204,7 +190,6 @@ __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_
             }
         }
         tc::mma_commit(S.wbar + BAR_STRIDE * W_STAGES);          // this stage's "empty" barrier
-        if (TRACE && S.stamp) S.stamp[(k0 / SKB) * 3 + 2] = clock64();
         if (++S.sw == W_STAGES) { S.sw = 0; S.pw ^= 1u; S.w = S.w0; S.wbar = S.wbar0; }
         else { S.w += W_STAGE >> 4; S.wbar += BAR_STRIDE; }
         if (hz) {
@@ -246,7 +231,6 @@ struct EpiArgs {
     const float* w3;              // output layer weights
     const float* scale;           // FP8 per-layer scales, or null
     uint32_t taddr;               // the warp's accumulator columns
-    long long *et, *wt, *pt;      // diagnostics stamps or null
 };
 
 // KIND: EPI_PLAIN ReLU + BF16; EPI_KEEP also writes o^k back into the accumulator (the next
@@ -339,20 +323,16 @@ __device__ __forceinline__ void epi_layer(const EpiArgs& e, float (&v)[NBLK * 16
             // make the stores visible to the tensor core, and (last chunk) complete the
             // accumulator write-back first, since the MMAs that start from it wait for the
             // last publication
-            if (e.et) e.et[1 + p] = clock64();
             tc::fence_proxy_async_smem();
             if (b == NBLK - 1 && KIND == EPI_KEEP) tc::tmem_wait_st();
             tc::tc_fence_before();
             __syncwarp();
-            if (e.et) e.et[5 + p] = clock64();
             if (e.lane == 0) tc::mbar_arrive(e.blk_bar + BAR_STRIDE * (uint32_t)p);
-            if (e.wt) e.wt[p] = clock64();
-            if (e.pt) e.pt[p] = clock64();
         }
     }
 }
 
-template <bool TRACE, class F>
+template <class F>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -360,17 +340,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     const uint32_t base = tc::smem_u32(sm);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_ABORT);
     auto bar = [&](int i) { return base + OFF_BAR + BAR_STRIDE * (uint32_t)i; };
-    // diagnostics: cycles spent in each role's waits, when a.trace is set, and for block
-    // 0 a timeline of 4 stamps per layer instance (MMA issue start/end, epilogue start/end)
-    long long* tl = (TRACE && blockIdx.x == 0) ? reinterpret_cast<long long*>(a.trace + 1024 * 12) : nullptr;
-    unsigned long long cyc_wait = 0, cyc_wait2 = 0;
-    const long long cyc_start = clock64();
-    auto twait = [&](uint32_t b, uint32_t parity, unsigned long long& acc) {
-        const long long t0 = TRACE ? clock64() : 0;
-        const bool r = tc::mbar_wait(b, parity, abort_flag);
-        if (TRACE) acc += (unsigned long long)(clock64() - t0);
-        return r;
-    };
+    auto twait = [&](uint32_t b, uint32_t parity) { return tc::mbar_wait(b, parity, abort_flag); };
     const int64_t Q = a.q_dev ? (int64_t)*a.q_dev : a.q_host;
     const int ntiles = (int)((Q + TM - 1) / TM);
 
@@ -411,7 +381,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     const int KB = layer_kb<F>(l), zkb = layer_zkb<F>(l), nb = layer_blocks<F>(l);
                     for (int k0 = 0; k0 < KB; k0 += SKB) {
                         if (k0 < zkb) {
-                            if (!twait(bar(B_ZEMPTY + sz), pz ^ 1u, cyc_wait)) break;
+                            if (!twait(bar(B_ZEMPTY + sz), pz ^ 1u)) break;
                             const uint32_t st = base + OFF_Z + sz * Z_STAGE;
                             // level l/2, bytes k0 .. k0+127 as two boxes of 64 bytes (x in elements)
                             const int x = ((l / 2) * F::KZB + k0) / F::EB;
@@ -423,7 +393,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                         }
                         const int b0 = k0 / 64;
                         const uint32_t bytes = (nb - b0 >= 2 ? 2u : 1u) * BLK_B;
-                        if (!twait(bar(B_WEMPTY + sw), pw ^ 1u, cyc_wait)) break;
+                        if (!twait(bar(B_WEMPTY + sw), pw ^ 1u)) break;
                         tc::mbar_expect_tx(bar(B_WFULL + sw), bytes);
                         tc::bulk_g2s(base + OFF_W + sw * W_STAGE, a.img + a.img_off[l] + (int64_t)b0 * BLK_B, bytes,
                                      bar(B_WFULL + sw));
@@ -464,14 +434,10 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             S.blk0 = bar(B_BLK);
             S.w = S.w0; S.z = S.z0; S.wbar = S.wbar0; S.zbar = S.zbar0;
             S.sw = 0; S.pw = 0; S.sz = 0; S.pz = 0;
-            S.tr = tl;
-            S.cyc = 0;
             uint32_t n = 0;                          // layer instance
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 for (int l = 0; l < NLAYERS; ++l, ++n) {
                     const uint32_t acc = tmem + (uint32_t)(l & 1) * 256u;   // n and l share parity
-                    if (TRACE && tl && n < 512) tl[4 * n] = clock64();
-                    S.stamp = (TRACE && tl && (n == 24 || n == 25)) ? tl + 2048 + (n - 24) * 24 : nullptr;
                     // One tcgen05 fence per layer orders this layer's MMAs after the waits
                     // (in the previous layer) that saw epilogue n-2 finish with accumulator
                     // n % 2.  Operands written by TMA or by the epilogue (fence.proxy.async +
@@ -480,24 +446,22 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     // publication parity of epilogue n-1: n and l share parity
                     const uint32_t pb = (uint32_t)(l & 1) ^ 1u;
                     if (l == 0) {
-                        issue_layer<TRACE, F::FP8, F::KZB, F::KZB, false>(S, acc, pb);
+                        issue_layer<F::FP8, F::KZB, F::KZB, false>(S, acc, pb);
                         // a tile's first layer reads no activation; it still waits for the
                         // previous epilogue, so the issuer never runs two phases ahead of it
                         if (n > 0)
                             tc::mbar_wait_issuer(S.blk0 + BAR_STRIDE * (npub<F>() - 1), pb, tc::kSpinLimit, S.abort_addr);
                     } else if (l < 20 && !(l & 1)) {
-                        issue_layer<TRACE, F::FP8, F::KZB + F::XB, F::KZB, false>(S, acc, pb);
+                        issue_layer<F::FP8, F::KZB + F::XB, F::KZB, false>(S, acc, pb);
                     } else if (layer_resid(l)) {
-                        issue_layer<TRACE, F::FP8, F::XB, 0, true>(S, acc, pb);
+                        issue_layer<F::FP8, F::XB, 0, true>(S, acc, pb);
                     } else {
-                        issue_layer<TRACE, F::FP8, F::XB, 0, false>(S, acc, pb);
+                        issue_layer<F::FP8, F::XB, 0, false>(S, acc, pb);
                     }
                     tc::mma_commit(bar(B_ACC));
-                    if (TRACE && tl && n < 512) tl[4 * n + 1] = clock64();
                 }
                 if (*abort_flag) break;
             }
-            cyc_wait = S.cyc;
             if (*abort_flag) {
                 // drain: wait (bounded) for the MMAs in flight before tensor memory is freed
                 tc::mma_commit(bar(B_DRAIN));
@@ -524,29 +488,19 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
                 // one poller per warp: lane 0 waits, the warp follows
-                if (lane == 0) ok = twait(bar(B_ACC), n & 1u, cyc_wait);
+                if (lane == 0) ok = twait(bar(B_ACC), n & 1u);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (TRACE && tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 2] = clock64();
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
                 float v[NBLK * 16];
                 tc::tmem_ld16x7(taddr, v);
-                // diagnostics (block 0, warp 2, instances 23 and 24): after the load, before
-                // and after each publication's fences
-                long long* et = (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
-                                    ? tl + 2048 + 64 + (n - 23) * 16 : nullptr;
-                if (et) et[0] = clock64();
-                long long* wt = (TRACE && tl && lane == 0 && n == 24) ? tl + 2048 + 96 + (warp - 2) * 4 : nullptr;
-                long long* pt = (TRACE && tl && warp == 2 && lane == 0 && (n == 23 || n == 24))
-                                    ? tl + 2048 + 48 + (n - 23) * 8 : nullptr;
-                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, a.scale, taddr, et, wt, pt};
+                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, a.scale, taddr};
                 // one straight-line routine per layer kind
                 if (l == 0) epi_layer<F, EPI_FIRST>(ea, v, dot, l);
                 else if (l == 21) epi_layer<F, EPI_LAST>(ea, v, dot, l);
                 else if (layer_keeps_o(l)) epi_layer<F, EPI_KEEP>(ea, v, dot, l);
                 else epi_layer<F, EPI_PLAIN>(ea, v, dot, l);
-                if (TRACE && tl && n < 512 && warp == 2 && lane == 0) tl[4 * n + 3] = clock64();
             }
             if (!ok) break;
             // combine the two column halves of the output layer's dot product: the
@@ -562,12 +516,6 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             }
             ++tile_iter;
         }
-    }
-    if (TRACE && lane == 0 && warp <= 2) {
-        unsigned long long* tr = a.trace + (size_t)blockIdx.x * 12 + warp * 3;
-        tr[0] = cyc_wait;
-        tr[1] = cyc_wait2;
-        tr[2] = (unsigned long long)(clock64() - cyc_start);
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -713,7 +661,7 @@ ImageLayout image_layout() {
 }
 
 // Launch of the network kernel in format F on q descriptor rows (q_dev: device count, or
-// null), with the tracing diagnostics of RPNN_TC_TRACE.
+// null).
 template <class F>
 rpnn_status forward_tc(Ctx& c, const DevBuf& image, const void* desc, int64_t q, const int* q_dev, float* out,
                        cudaStream_t s) {
@@ -746,70 +694,15 @@ rpnn_status forward_tc(Ctx& c, const DevBuf& image, const void* desc, int64_t q,
     a.q_dev = q_dev;
     a.out = out;
     a.status = c.status.as<uint32_t>();
-    // RPNN_TC_TRACE=1: per-role wait cycles of every block, summarised on stderr
-    // (synchronises the stream; diagnostics only; never while the stream is being captured)
-    static unsigned long long* trace_buf = nullptr;
-    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
-    RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &capturing));
-    const bool tracing = getenv("RPNN_TC_TRACE") != nullptr && capturing == cudaStreamCaptureStatusNone;
-    if (tracing && !trace_buf) RPNN_CUDA_TRY(cudaMalloc(&trace_buf, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long)));
-    a.trace = tracing ? trace_buf : nullptr;
     static bool attr = false;
     if (!attr) {
-        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<false, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<true, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
         attr = true;
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
-    if (tracing) RPNN_CUDA_TRY(cudaMemsetAsync(trace_buf, 0, (1024 * 12 + 4 * 512 + 128) * sizeof(unsigned long long), s));
-    if (tracing) k_rpnn_tc<true, F><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
-    else k_rpnn_tc<false, F><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
+    k_rpnn_tc<F><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
-    if (tracing) {
-        std::vector<unsigned long long> h((size_t)grid * 12);
-        RPNN_CUDA_TRY(cudaMemcpyAsync(h.data(), trace_buf, h.size() * 8, cudaMemcpyDeviceToHost, s));
-        RPNN_CUDA_TRY(cudaStreamSynchronize(s));
-        double acc[12] = {};
-        for (int b = 0; b < grid; ++b)
-            for (int i = 0; i < 12; ++i) acc[i] += (double)h[(size_t)b * 12 + i] / grid;
-        fprintf(stderr,
-                "[rpnn tc trace] blocks %d  producer: wait_empty %.0f of %.0f cyc | mma: stage polls %.0f "
-                "end-of-layer waits %.0f of %.0f | epilogue(w2): wait_acc %.0f of %.0f\n",
-                grid, acc[0], acc[2], acc[3], acc[4], acc[5], acc[6], acc[8]);
-        std::vector<long long> tlh(4 * 512 + 128);
-        RPNN_CUDA_TRY(cudaMemcpy(tlh.data(), trace_buf + 1024 * 12, tlh.size() * 8, cudaMemcpyDeviceToHost));
-        // block 0, layer instances 24 and 25 (second tile, layers 2 and 3): per stage the
-        // poll start / poll end / commit, and the publications of the epilogue feeding it,
-        // relative to the layer's issue start
-        for (int inst = 0; inst < 2; ++inst) {
-            const long long t0 = tlh[4 * (24 + inst)];
-            const long long* st = &tlh[2048 + inst * 24];
-            const long long* pub = &tlh[2048 + 48 + inst * 8];
-            fprintf(stderr, "[rpnn tc stages] inst %d: epilogue %d acc-ready %lld pubs %lld %lld %lld %lld\n", 24 + inst,
-                    23 + inst, tlh[4 * (23 + inst) + 2] - t0, pub[0] - t0, pub[1] - t0, pub[2] - t0, pub[3] - t0);
-            const long long* et = &tlh[2048 + 64 + inst * 16];
-            const long long ea = tlh[4 * (23 + inst) + 2];
-            fprintf(stderr, "[rpnn tc epilogue] inst %d (from acc-ready): tmem-ld %lld | pubs: stores %lld %lld %lld %lld"
-                            " / fenced %lld %lld %lld %lld\n", 23 + inst, et[0] - ea, et[1] - ea, et[2] - ea, et[3] - ea,
-                    et[4] - ea, et[5] - ea, et[6] - ea, et[7] - ea, et[8] - ea);
-            if (inst == 1) {
-                for (int w = 0; w < 8; ++w)
-                    fprintf(stderr, "[rpnn tc epilogue] inst 24 warp %d (scheduler %d): pubs %lld %lld %lld %lld\n", w + 2,
-                            (w + 2) & 3, tlh[2048 + 96 + w * 4] - ea, tlh[2048 + 96 + w * 4 + 1] - ea,
-                            tlh[2048 + 96 + w * 4 + 2] - ea, tlh[2048 + 96 + w * 4 + 3] - ea);
-            }
-            for (int j = 0; j < 8 && st[3 * j]; ++j)
-                fprintf(stderr, "[rpnn tc stages] inst %d stage %d  poll %6lld .. %6lld  commit %6lld\n", 24 + inst, j,
-                        st[3 * j] - t0, st[3 * j + 1] - t0, st[3 * j + 2] - t0);
-        }
-        // block 0, second tile: per layer, issue span, issue->acc ready, epilogue span, gap
-        for (int n = 22; n < 44 && tlh[4 * n + 3]; ++n) {
-            const long long* q = &tlh[4 * n];
-            fprintf(stderr, "[rpnn tc timeline] layer %2d issue %6lld  to-acc %6lld  epi %6lld  next-issue-gap %6lld\n",
-                    n - 22, q[1] - q[0], q[2] - q[0], q[3] - q[2], n < 511 ? q[4] - q[1] : 0LL);
-        }
-    }
     return RPNN_OK;
 }
 

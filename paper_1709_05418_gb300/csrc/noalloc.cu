@@ -53,7 +53,10 @@ extern "C" rpnn_status rpnn_mlp_forward_f32_static(const float* dev_params, cons
     float* scratch = nullptr;
     rpnn_status st = scratch_for_current_device(&scratch);
     if (st) return st;
+    // the context path's forward with no context: default GEMM tile, no split-K, no tuning
     const int64_t plane = kStaticRows * RPNN_H;
-    return mlp_forward_f32_with(dev_params, dev_desc, q, dev_out, scratch, scratch + plane, scratch + 2 * plane,
-                                (cudaStream_t)stream);
+    float* const scr[3] = {scratch, scratch + plane, scratch + 2 * plane};
+    const NetDims nd{&param_layout(), RPNN_DIN, RPNN_DESC_STRIDE};
+    return rpnn_forward_f32(nullptr, nd, dev_params, dev_desc, q, nullptr, dev_out, nullptr, scr,
+                            (cudaStream_t)stream);
 }

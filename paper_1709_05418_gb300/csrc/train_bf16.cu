@@ -77,20 +77,30 @@ __global__ void k_train_image(const float* __restrict__ P, const MatJobs jobs, _
     }
 }
 
-// z [q][10][240] FP32 -> zb [q][10][240] BF16 and zt [10][226][ldq] BF16 (per level, transposed)
-__global__ void k_train_desc(const float* __restrict__ z, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ zb,
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 v) { return v; }
+
+// z [q][10][240] FP32 or BF16 -> zb [q][10][240] BF16 and zt [10][226][ldq] BF16 (per level,
+// transposed); FP32 values are rounded to nearest even, BF16 values copied
+template <class T>
+__global__ void k_train_desc(const T* __restrict__ z, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ zb,
                              __nv_bfloat16* __restrict__ zt) {
     const int64_t row = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
     const int64_t total = q * row;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-        zb[i] = __float2bfloat16_rn(z[i]);
+        zb[i] = to_bf16(z[i]);
     // transposed copy: consecutive threads take consecutive rows m of one (level, column)
     const int64_t ttotal = (int64_t)RPNN_K * RPNN_DIN * q;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ttotal; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = i % q, lc = i / q;
         const int k = (int)(lc / RPNN_DIN), c = (int)(lc % RPNN_DIN);
-        zt[((int64_t)k * RPNN_DIN + c) * ldq + m] = __float2bfloat16_rn(z[m * row + (int64_t)k * RPNN_DESC_STRIDE + c]);
+        zt[((int64_t)k * RPNN_DIN + c) * ldq + m] = to_bf16(z[m * row + (int64_t)k * RPNN_DESC_STRIDE + c]);
     }
+}
+
+__global__ void k_bf16_to_f32(const __nv_bfloat16* __restrict__ in, float* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(in[i]);
 }
 
 // x [q][200] FP32 -> BF16 [q][200] and transposed BF16 [200][ldq]
@@ -114,6 +124,13 @@ int grid_for(int64_t n, int sms) {
 }  // namespace
 
 int64_t train_ldq(int64_t q) { return (q + 7) & ~(int64_t)7; }
+
+rpnn_status launch_bf16_to_f32(const void* in, float* out, int64_t n, int sms, cudaStream_t s) {
+    if (n <= 0) return RPNN_OK;
+    k_bf16_to_f32<<<grid_for(n, sms), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(in), out, n);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
 
 size_t train_bf16_saved_elems(int64_t q) {
     // 22 activations as BF16 [q][200] and BF16 [200][ldq]; descriptors as BF16 [q][2400]
@@ -151,8 +168,8 @@ rpnn_status train_build_image(Ctx& c, cudaStream_t s) {
 
 // Forward with saved activations: FP32 slots as the FP32 form (o^1..o^10, F1^1..F1^10,
 // o^11, o^12, then g) in `saved`, BF16 copies in `s16` (train_bf16_saved_elems(q)).
-rpnn_status mlp_forward_bf16_train(Ctx& c, const float* desc, int64_t q, float* out, float* saved, uint16_t* s16,
-                                   cudaStream_t s) {
+rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int64_t q, float* out, float* saved,
+                                   uint16_t* s16, cudaStream_t s) {
     const ParamLayout& L = param_layout();
     const TrainImage& I = train_image();
     const float* P = c.params32.as<float>();
@@ -166,8 +183,14 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const float* desc, int64_t q, float* 
     auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
     uint16_t* zb = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq;
     uint16_t* zt = zb + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
-    k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
-        desc, q, ldq, reinterpret_cast<__nv_bfloat16*>(zb), reinterpret_cast<__nv_bfloat16*>(zt));
+    if (desc_dtype == RPNN_BF16)
+        k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
+            static_cast<const __nv_bfloat16*>(desc), q, ldq, reinterpret_cast<__nv_bfloat16*>(zb),
+            reinterpret_cast<__nv_bfloat16*>(zt));
+    else
+        k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
+            static_cast<const float*>(desc), q, ldq, reinterpret_cast<__nv_bfloat16*>(zb),
+            reinterpret_cast<__nv_bfloat16*>(zt));
     RPNN_CHECK_LAUNCH();
     for (int k = 0; k < RPNN_K; ++k) {
         // F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)

@@ -52,6 +52,19 @@ __global__ void k_stats_max(const float* __restrict__ v, int64_t n, DevStats* st
     }
 }
 
+// x * 2^S truncated to an integer, for finite x > 0 with x * 2^S < 2^32, from the float's
+// bits: x = M * 2^(E - 150) with the 24-bit significand M (hidden bit set unless
+// subnormal) and biased exponent E (1 for subnormals), so the product is M shifted by
+// E - 150 + S, and a right shift truncates exactly as the real value rounds toward zero.
+__device__ __forceinline__ unsigned long long fixed_point(float x, int S) {
+    const uint32_t b = __float_as_uint(x);
+    const int E = (int)(b >> 23);
+    const unsigned long long M = (b & 0x7FFFFFu) | (E ? 0x800000u : 0u);
+    const int sh = (E ? E : 1) - 150 + S;
+    if (sh >= 0) return M << sh;
+    return sh > -24 ? M >> (-sh) : 0ull;
+}
+
 // Fixed-point sum: each v > 0 truncated to an integer with S = 32 - e fraction bits,
 // where the majorant is below 2^e; the integer sum is exact (< 2^62 for 2^30 voxels)
 // and independent of order.
@@ -63,7 +76,7 @@ __global__ void k_stats_sum(const float* __restrict__ v, int64_t n, DevStats* st
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float x = v[i];
-        if (x > 0.0f) s += (unsigned long long)__double2ll_rz(ldexp((double)x, S));
+        if (x > 0.0f) s += fixed_point(x, S);
     }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&st->isum, s);

@@ -21,9 +21,10 @@ from . import workloads as W
 
 
 def records(ctx: api.Context, clouds, n_per_cloud: int, seed: int = 1000, rel_ci: float = 0.02,
-            n_min: int = 64, n_max: int = 4096, chunk: int = 8192, albedo: float = 0.99, hg_g: float = 0.85):
-    """Returns (desc [N,10,240] FP32, label [N]) for `n_per_cloud` records of each cloud
-    (a list of FP32 density grids, numpy [nz][ny][nx])."""
+            n_min: int = 64, n_max: int = 4096, chunk: int = 8192, albedo: float = 0.99, hg_g: float = 0.85,
+            dtype=torch.float32):
+    """Returns (desc [N,10,240] of `dtype` (FP32, or BF16 at half the memory), label [N]) for
+    `n_per_cloud` records of each cloud (a list of FP32 density grids, numpy [nz][ny][nx])."""
     descs, labels = [], []
     for ci, dens in enumerate(clouds):
         vol = ctx.load_volume(torch.from_numpy(np.ascontiguousarray(dens)).cuda(), albedo, hg_g)
@@ -31,7 +32,7 @@ def records(ctx: api.Context, clouds, n_per_cloud: int, seed: int = 1000, rel_ci
         for first in range(0, n_per_cloud, chunk):
             n = min(chunk, n_per_cloud - first)
             x, d, wl, lab, _ = ctx.gen_records(vol, first, n, seed + 7919 * ci, rel_ci, n_min, n_max)
-            z = ctx.extract_descriptors(vol, x, d, wl)
+            z = ctx.extract_descriptors(vol, x, d, wl, dtype=dtype)
             descs.append(z)
             labels.append(lab)
         ctx.sync_status()
@@ -50,7 +51,7 @@ def val_loss(ctx: api.Context, desc, label, batch: int = 8192) -> float:
     tot, n = 0.0, 0
     for i in range(0, desc.shape[0], batch):
         z, t = desc[i:i + batch], label[i:i + batch]
-        g = ctx.mlp_forward(z, precision=api.F32)
+        g = ctx.mlp_forward(z, precision=api.BF16 if z.dtype == torch.bfloat16 else api.F32)
         r = torch.log1p(g.double()) - torch.log1p(t.double())
         tot += float((r * r).sum())
         n += z.shape[0]

@@ -1,8 +1,7 @@
 // tc_probe.cu -- test-only check of the tensor-core operand layouts used by the BF16
 // network kernel: one 128 x 208 x 32 tcgen05 MMA from shared memory (A written by
 // threads, B by a bulk copy), tensor-memory loads, and a 2-D TMA box load with
-// out-of-bounds zero fill; MMA issue-rate measurements; and the give-up path of the
-// bounded barrier waits (a phase nobody completes).  Every shared-memory access stays
+// out-of-bounds zero fill; and the give-up path of the bounded barrier waits (a phase nobody completes).  Every shared-memory access stays
 // inside a 192 KiB allocation even if a descriptor field were read with another meaning,
 // and every wait is bounded.
 #include <cuda.h>
@@ -165,183 +164,6 @@ __global__ void __launch_bounds__(128) k_probe_sw64(const __nv_bfloat16* __restr
 }
 
 
-// ---- issue-rate measurement: `nmma` back-to-back MMAs on resident operands ----------
-// mode bit 0: commit to an mbarrier after every second MMA; bit 1: N = 256 instead of
-// 208; bit 2: 64-byte swizzled descriptors instead of interleaved.  The operands are
-// zeros (only timing matters); clock64 brackets issue and completion.
-__global__ void __launch_bounds__(512) k_mma_rate(int nmma, int mode, long long* cycles, int* err) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid / 32;
-    const uint32_t base = smem_u32(sm);
-    const uint32_t bar = base + 65536, bar2 = base + 65544;
-    // mode bit 5: warps beyond the first four exit at once
-    if ((mode & 32) && warp >= 4) return;
-    const int nthr = (mode & 32) ? min((int)blockDim.x, 128) : (int)blockDim.x;
-    for (int i = tid; i < 65536 / 16; i += nthr) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async_smem();
-    if (tid == 0) {
-        abort_flag = 0;
-        mbar_init(bar, 1);
-        mbar_init(bar2, 1);
-        mbar_init(bar2 + 8, 1);
-        mbar_init(bar2 + 16, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) { tmem_alloc(base + 65600, 256); tmem_relinquish(); }
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 65600);
-    // mode bit 3: warps 1..7 poll an mbarrier that only completes after the timed loop
-    // (warp 4 shares the issuing warp's scheduler)
-    // (the situation of epilogue / producer warps waiting while one thread issues MMAs)
-    if ((mode & 8) && warp > 0) {
-        if (!mbar_wait(bar2 + 8, 0, &abort_flag)) atomicOr(err, 4);
-    }
-    if (tid == 0) {
-        const int n = (mode & 2) ? 256 : 208;
-        const uint32_t id = idesc_bf16(128, n);
-        const bool sw = (mode & 4) != 0;
-        const uint64_t a0 = sw ? smem_desc_sw64(base) : smem_desc(base, 2048, 128);
-        const uint64_t b0 = sw ? smem_desc_sw64(base + 16384) : smem_desc(base + 16384, 4096, 128);
-        uint32_t commits = 0;
-        const long long t0 = clock64();
-        if (mode & 16) mbar_arrive(bar2 + 16);                     // phase 0 of bar3 completes now
-        for (int i = 0; i < nmma; ++i) {
-            if ((mode & 16) && !(i & 1)) {
-                // what the network kernel does per ring stage: a (satisfied) wait and a fence
-                if (!mbar_wait(bar2 + 16, 0, &abort_flag)) atomicOr(err, 8);
-                tc_fence_after();
-            }
-            const uint64_t off = (uint64_t)((i & 1) * 2);          // +32 bytes inside the row
-            const uint64_t blk = (mode & 16) ? (uint64_t)(((i >> 1) % 5) * (512 >> 4)) : 0;
-            mma_bf16(tmem, a0 + off + blk, b0 + off + blk, id, i > 0);
-            if ((mode & 1) && (i & 1)) { mma_commit(bar2); ++commits; }
-        }
-        const long long t1 = clock64();
-        mma_commit(bar);
-        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
-        const long long t2 = clock64();
-        cycles[0] = t1 - t0;
-        cycles[1] = t2 - t0;
-        (void)commits;
-        if (mode & 8) mbar_arrive(bar2 + 8);
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
-}
-
-
-// ---- variants compiled separately: what in an MMA issue loop slows it down ----------
-// V=0 plain; V=1 satisfied mbarrier wait every 2 MMAs; V=2 tcgen05.fence::after_thread_sync
-// every 2 MMAs; V=3 one fence before the loop; V=4 commit every 2 MMAs; V=5 wait + commit
-// every 2 MMAs (no fence).
-template <int V>
-__global__ void __launch_bounds__(128) k_mma_variant(int nmma, long long* cycles, int* err) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ int abort_flag;
-    const int tid = threadIdx.x, warp = tid / 32;
-    const uint32_t base = smem_u32(sm);
-    const uint32_t bar = base + 65536, bar2 = base + 65544, bar3 = base + 65552;
-    for (int i = tid; i < 65536 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async_smem();
-    if (tid == 0) {
-        abort_flag = 0;
-        mbar_init(bar, 1);
-        mbar_init(bar2, 1);
-        mbar_init(bar3, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) { tmem_alloc(base + 65600, 256); tmem_relinquish(); }
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 65600);
-    if (tid == 0) {
-        const uint32_t id = idesc_bf16(128, 208);
-        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
-        mbar_arrive(bar3);                                   // phase 0 of bar3 is complete
-        *reinterpret_cast<volatile uint32_t*>(sm + 65700) = 1u;   // counter already satisfied
-        if (V == 3) tc_fence_after();
-        const long long t0 = clock64();
-        for (int i = 0; i < nmma; ++i) {
-            if (!(i & 1)) {
-                if (V == 1 || V == 5) { if (!mbar_wait(bar3, 0, &abort_flag)) atomicOr(err, 8); }
-                if (V == 2) tc_fence_after();
-                if (V == 6) {   // relaxed try_wait
-                    uint32_t ok = 0;
-                    for (int it = 0; it < (1 << 20) && !ok; ++it)
-                        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n"
-                                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
-                }
-                if (V == 7 || V == 8) {   // test_wait (acquire / relaxed), non-suspending
-                    uint32_t ok = 0;
-                    for (int it = 0; it < (1 << 20) && !ok; ++it) {
-                        if (V == 7)
-                            asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                                         " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
-                        else
-                            asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n"
-                                         " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar3), "r"(0u) : "memory");
-                    }
-                }
-                if (V == 9) {   // try_wait loop inside one asm statement (no C++ loop around it)
-                    asm volatile("{\n .reg .pred P1;\n WAIT_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
-                                 " @!P1 bra WAIT_%=;\n}\n" :: "r"(bar3), "r"(0u) : "memory");
-                }
-            }
-            if (V == 10 && !(i & 3)) { if (!mbar_wait(bar3, 0, &abort_flag)) atomicOr(err, 8); }
-            if ((V == 13 || V == 14) && !(i & 1)) {
-                // poll a shared counter that another thread bumps after its own mbarrier wait
-                uint32_t seen = 0;
-                for (int it = 0; it < (1 << 20); ++it) {
-                    if (V == 13) seen = *reinterpret_cast<volatile uint32_t*>(sm + 65700);
-                    else asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(seen) : "r"(base + 65700) : "memory");
-                    if (seen >= 1u) break;
-                }
-                if (seen < 1u) atomicOr(err, 16);
-            }
-            if (V == 15 && !(i & 3))
-                asm volatile("{\n .reg .pred P1;\n .reg .u32 c;\n mov.u32 c, %2;\n"
-                             "W_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n @P1 bra D_%=;\n"
-                             " sub.u32 c, c, 1;\n setp.ne.u32 P1, c, 0;\n @P1 bra W_%=;\n"
-                             " st.shared.u32 [%3], 1;\n"
-                             "D_%=:\n}\n" :: "r"(bar3), "r"(0u), "r"(1u << 20), "r"(smem_u32(&abort_flag)) : "memory");
-            if ((V == 11 || V == 12) && !(i & 1)) {
-                // bounded poll with no output: on give-up it raises the abort flag itself
-                if (V == 11 || !abort_flag)
-                    asm volatile("{\n .reg .pred P1;\n .reg .u32 c;\n mov.u32 c, %2;\n"
-                                 "W_%=:\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n @P1 bra D_%=;\n"
-                                 " sub.u32 c, c, 1;\n setp.ne.u32 P1, c, 0;\n @P1 bra W_%=;\n"
-                                 " st.shared.u32 [%3], 1;\n"
-                                 "D_%=:\n}\n" :: "r"(bar3), "r"(0u), "r"(1u << 20), "r"(smem_u32(&abort_flag)) : "memory");
-            }
-            const uint64_t off = (uint64_t)((i & 1) * 2);
-            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
-            if ((V == 4 || V == 5) && (i & 1)) mma_commit(bar2);
-        }
-        const long long t1 = clock64();
-        mma_commit(bar);
-        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
-        cycles[0] = t1 - t0;
-        cycles[1] = clock64() - t0;
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
-}
-
-template <int V>
-int run_variant(int nmma, long long* cycles, int* err) {
-    if (cudaFuncSetAttribute(k_mma_variant<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
-    k_mma_variant<V><<<1, 128, SMEM>>>(nmma, cycles, err);
-    if (cudaGetLastError() != cudaSuccess) return -13;
-    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
-    return 0;
-}
-
 }  // namespace
 
 // Failure path of the bounded waits, without a fault: a barrier phase nobody completes.
@@ -372,130 +194,6 @@ extern "C" int tc_wait_timeout(int limit, int* err, long long* cycles) {
     if (cudaGetLastError() != cudaSuccess) return -13;
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : -14;
 }
-
-extern "C" int tc_mma_variant(int v, int nmma, long long* cycles, int* err) {
-    switch (v) {
-        case 0: return run_variant<0>(nmma, cycles, err);
-        case 1: return run_variant<1>(nmma, cycles, err);
-        case 2: return run_variant<2>(nmma, cycles, err);
-        case 3: return run_variant<3>(nmma, cycles, err);
-        case 4: return run_variant<4>(nmma, cycles, err);
-        case 5: return run_variant<5>(nmma, cycles, err);
-        case 6: return run_variant<6>(nmma, cycles, err);
-        case 7: return run_variant<7>(nmma, cycles, err);
-        case 8: return run_variant<8>(nmma, cycles, err);
-        case 9: return run_variant<9>(nmma, cycles, err);
-        case 10: return run_variant<10>(nmma, cycles, err);
-        case 11: return run_variant<11>(nmma, cycles, err);
-        case 12: return run_variant<12>(nmma, cycles, err);
-        case 13: return run_variant<13>(nmma, cycles, err);
-        case 14: return run_variant<14>(nmma, cycles, err);
-        case 15: return run_variant<15>(nmma, cycles, err);
-        default: return -1;
-    }
-}
-
-namespace {
-
-// ---- MMA rate while another warp streams bulk copies into shared memory -------------
-// Warp 0 lane 0 issues nmma MMAs (operands at 0 .. 48 KB); warp 1 lane 0 keeps `inflight`
-// 13,312-byte bulk copies (from an L2-resident global buffer) landing in shared memory
-// at 96 .. 160 KB until the MMAs are done; warps 2-3 optionally (mode & 1) also store to
-// shared memory continuously (epilogue-like traffic).
-__global__ void __launch_bounds__(128) k_mma_with_copies(int nmma, int mode, const unsigned char* __restrict__ src,
-                                                          long long* cycles, int* err) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ int abort_flag;
-    __shared__ volatile int done;
-    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    const uint32_t base = smem_u32(sm);
-    const uint32_t bar = base + 180224, barc = base + 180232;
-    for (int i = tid; i < 49152 / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async_smem();
-    if (tid == 0) {
-        abort_flag = 0;
-        done = 0;
-        mbar_init(bar, 1);
-        mbar_init(barc, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) { tmem_alloc(base + 180300, 256); tmem_relinquish(); }
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 180300);
-    if (tid == 0) {
-        const uint32_t id = idesc_bf16(128, 208);
-        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
-        const long long t0 = clock64();
-        for (int i = 0; i < nmma; ++i) {
-            const uint64_t off = (uint64_t)((i & 1) * 2);
-            mma_bf16(tmem, a0 + off, b0 + off, id, i > 0);
-        }
-        mma_commit(bar);
-        if (!mbar_wait(bar, 0, &abort_flag)) atomicOr(err, 1);
-        cycles[1] = clock64() - t0;
-        done = 1;
-    } else if (warp == 1 && lane == 0) {
-        long long copies = 0;
-        uint32_t ph = 0;
-        while (!done) {
-            mbar_expect_tx(barc, 4 * 13312);
-            for (int k = 0; k < 4; ++k)
-                bulk_g2s(base + 98304 + k * 13312, src + (size_t)(copies % 64) * 13312, 13312, barc);
-            if (!mbar_wait(barc, ph, &abort_flag)) { atomicOr(err, 2); break; }
-            ph ^= 1u;
-            copies += 4;
-        }
-        cycles[0] = copies;
-    } else if ((mode & 1) && warp >= 2) {
-        uint4* p = reinterpret_cast<uint4*>(sm + 163840 + (tid - 64) * 16);
-        long long k = 0;
-        while (!done) { p[0] = make_uint4((uint32_t)k, 1, 2, 3); p[64] = p[0]; ++k; }
-    } else if ((mode & 2) && warp >= 2) {
-        // tensor-memory reads of columns 208..255 (not written by the MMAs) in a loop
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 208u;
-        float acc = 0.0f;
-        while (!done) {
-            float v[32];
-            tmem_ld32(ta, v);
-            for (int i = 0; i < 32; ++i) acc += v[i];
-        }
-        if (acc == 12345.0f) atomicOr(err, 64);
-    } else if ((mode & 4) && warp >= 2) {
-        // generic stores of zeros over the A operand the MMAs read, then proxy fences
-        uint4* p = reinterpret_cast<uint4*>(sm + (tid - 64) * 16);
-        while (!done) {
-            for (int k = 0; k < 8; ++k) p[k * 64] = make_uint4(0, 0, 0, 0);
-            fence_proxy_async_smem();
-        }
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
-}
-
-}  // namespace
-
-extern "C" int tc_mma_with_copies(int nmma, int mode, const void* src, long long* cycles, int* err) {
-    if (cudaFuncSetAttribute(k_mma_with_copies, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
-    k_mma_with_copies<<<1, 128, SMEM>>>(nmma, mode, (const unsigned char*)src, cycles, err);
-    if (cudaGetLastError() != cudaSuccess) return -13;
-    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
-    return 0;
-}
-
-namespace {
-}  // namespace
-
-extern "C" int tc_mma_rate(int nmma, int mode, long long* cycles, int* err, int nthreads) {
-    if (cudaFuncSetAttribute(k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return -12;
-    k_mma_rate<<<1, nthreads, SMEM>>>(nmma, mode, cycles, err);
-    if (cudaGetLastError() != cudaSuccess) return -13;
-    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
-    return 0;
-}
-
 
 extern "C" int tc_probe_sw64(const void* A, const void* Bimg, const void* T2d, int t_rows, int t_cols,
                              float* D, void* tma_out, int* err) {
@@ -546,208 +244,6 @@ extern "C" int tc_probe(const void* A, const void* Bimg, const void* T2d, int t_
     if (cudaDeviceSynchronize() != cudaSuccess) return -14;
     return 0;
 }
-
-namespace {
-
-// ---- MMA rate through a 5-stage ring like the network kernel's ---------------------
-// Warp 0 lane 0 (producer) fills stage s after the MMAs that read it have completed:
-// an mbarrier arrive (copy == 0) or a 13,312-byte bulk copy (copy == 1).  Warp 1 lane
-// 0 (issuer) waits for each stage, issues CH MMAs on it and commits them to the stage's
-// "empty" barrier.  CH == 0: no ring, plain MMAs.  Wait forms (WF): 0 the bounded poll
-// whose satisfied path takes a branch; 1 a bounded poll whose satisfied path falls
-// through; 2 as 1, but one poll covers two consecutive stages; 3 as 0 with one commit per
-// two stages (4 stages; the producer refills a pair of stages after that commit); 4 as 0
-// but the poll covers the stage and two barriers completed at setup (three try_waits);
-// 5 as 0 with a second commit per stage (to a barrier nobody waits on); 6 as 0 with four
-// distinct A and B operands per stage (stages of two 32-column weight blocks, 32 KB apart,
-// and two 32-column A blocks), as in the network kernel; 7 as 6 with 8 more warps that,
-// like the network kernel's epilogue, wait (lane 0 polling) for an accumulator barrier
-// the issuer commits every 7 stages, then arrive on 4 barriers nobody waits on.
-// copy & 2: the producer polls with a 200 ns sleep between tries.  Every block of the grid
-// does the same; cycles[b] is block b's issuer time.
-
-// bounded poll of one or two barriers; the satisfied path falls through
-__device__ __forceinline__ void wait_ft(uint32_t bar, uint32_t parity, uint32_t limit, uint32_t abort_addr) {
-    asm volatile(
-        "{\n"
-        " .reg .pred P1, P2;\n"
-        " .reg .u32 c, f;\n"
-        " mov.u32 c, %2;\n"
-        " mov.u32 f, 0;\n"
-        "WAIT_%=:\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
-        " @!P1 ld.volatile.shared.u32 f, [%3];\n"
-        " @!P1 sub.u32 c, c, 1;\n"
-        " setp.ne.and.u32 P2, c, 0, !P1;\n"
-        " setp.eq.and.u32 P2, f, 0, P2;\n"
-        " @P2 bra WAIT_%=;\n"
-        " setp.eq.and.u32 P2, c, 0, !P1;\n"
-        " @P2 st.volatile.shared.u32 [%3], 1;\n"
-        "}\n" ::"r"(bar), "r"(parity), "r"(limit), "r"(abort_addr) : "memory");
-}
-__device__ __forceinline__ void wait_ft2(uint32_t bar0, uint32_t par0, uint32_t bar1, uint32_t par1, uint32_t limit,
-                                         uint32_t abort_addr) {
-    asm volatile(
-        "{\n"
-        " .reg .pred P1, P2, P3;\n"
-        " .reg .u32 c, f;\n"
-        " mov.u32 c, %4;\n"
-        " mov.u32 f, 0;\n"
-        "WAIT_%=:\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P3, [%2], %3;\n"
-        " and.pred P1, P1, P3;\n"
-        " @!P1 ld.volatile.shared.u32 f, [%5];\n"
-        " @!P1 sub.u32 c, c, 1;\n"
-        " setp.ne.and.u32 P2, c, 0, !P1;\n"
-        " setp.eq.and.u32 P2, f, 0, P2;\n"
-        " @P2 bra WAIT_%=;\n"
-        " setp.eq.and.u32 P2, c, 0, !P1;\n"
-        " @P2 st.volatile.shared.u32 [%5], 1;\n"
-        "}\n" ::"r"(bar0), "r"(par0), "r"(bar1), "r"(par1), "r"(limit), "r"(abort_addr) : "memory");
-}
-
-template <int CH, int WF>
-__global__ void __launch_bounds__(WF == 7 ? 320 : 128) k_mma_ring(int nmma, int copy, const unsigned char* __restrict__ src,
-                                                   long long* cycles, int* err) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ int abort_flag;
-    constexpr int S = WF == 3 ? 4 : 5;
-    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-    const uint32_t base = smem_u32(sm);
-    const uint32_t bars = base + 180224;   // full[s] at +8s, empty[s] at +64+8s, done at +128
-    for (int i = tid; i < (WF >= 6 ? 180224 : 98304) / 16; i += blockDim.x) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async_smem();
-    if (tid == 0) {
-        abort_flag = 0;
-        for (int s = 0; s < S; ++s) { mbar_init(bars + 8 * s, 1); mbar_init(bars + 64 + 8 * s, 1); }
-        mbar_init(bars + 128, 1);
-        mbar_init(bars + 136, 1);
-        mbar_init(bars + 144, 1);
-        mbar_init(bars + 152, 1);                       // accumulator barrier (WF 7)
-        for (int p = 0; p < 4; ++p) mbar_init(bars + 160 + 8 * p, 8);
-        fence_mbar_init();
-        mbar_arrive(bars + 144);   // phase 0 complete: always satisfied with parity 0
-    }
-    if (warp == 1) { tmem_alloc(base + 180400, 256); tmem_relinquish(); }
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + 180400);
-    const uint32_t abort_addr = smem_u32(&abort_flag);
-    const int nchunk = CH > 0 ? nmma / CH : 0;
-    if (warp == 0 && lane == 0 && CH > 0) {
-        for (int c = 0; c < nchunk && !abort_flag; ++c) {
-            const int s = c % S;
-            const uint32_t eb = bars + 64 + 8 * (WF == 3 ? (s | 1) : s), ep = ((c / S) & 1) ^ 1;
-            if (copy & 2) {
-                uint32_t it = 0;
-                while (!mbar_test(eb, ep) && ++it < (1u << 22)) __nanosleep(200);
-                if (it >= (1u << 22)) { abort_flag = 1; break; }
-            } else {
-                mbar_wait_issuer(eb, ep, kSpinLimit, abort_addr);
-            }
-            if ((copy & 1) && WF >= 6) {
-                mbar_expect_tx(bars + 8 * s, 26624);
-                bulk_g2s(base + 16384 + s * 32768, src + (size_t)(c % 32) * 26624, 26624, bars + 8 * s);
-            } else if (copy & 1) {
-                mbar_expect_tx(bars + 8 * s, 13312);
-                bulk_g2s(base + 16384 + s * 16384, src + (size_t)(c % 64) * 13312, 13312, bars + 8 * s);
-            } else {
-                mbar_expect_tx(bars + 8 * s, 0);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        const uint32_t id = idesc_bf16(128, 208);
-        const uint64_t a0 = smem_desc_sw64(base), b0 = smem_desc_sw64(base + 16384);
-        const long long t0 = clock64();
-        if (CH == 0) {
-            for (int i = 0; i < nmma; ++i) mma_bf16(tmem, a0 + (uint64_t)((i & 1) * 2), b0 + (uint64_t)((i & 1) * 2), id, i > 0);
-        } else {
-            uint32_t s = 0, ph = 0;
-            // block 0, WF 6: stamps of stages 100..107 (poll start, poll end, commit) after
-            // the per-block cycle counts
-            long long* st_tr = (WF >= 6 && blockIdx.x == 0) ? cycles + gridDim.x : nullptr;
-            for (int c = 0; c < nchunk; ++c) {
-                const bool stamp = st_tr && c >= 100 && c < 108;
-                if (stamp) st_tr[(c - 100) * 3] = clock64();
-                if (WF == 0 || WF == 3 || WF == 5 || WF >= 6) mbar_wait_issuer(bars + 8 * s, ph, kSpinLimit, abort_addr);
-                if (stamp) st_tr[(c - 100) * 3 + 1] = clock64();
-                if (WF == 4) mbar_wait_issuer3(bars + 8 * s, ph, bars + 144, 0, bars + 144, 0, kSpinLimit, abort_addr);
-                if (WF == 1) wait_ft(bars + 8 * s, ph, kSpinLimit, abort_addr);
-                if (WF == 2 && !(c & 1)) {
-                    const uint32_t s1 = s + 1 == S ? 0 : s + 1, ph1 = s + 1 == S ? ph ^ 1u : ph;
-                    wait_ft2(bars + 8 * s, ph, bars + 8 * s1, ph1, kSpinLimit, abort_addr);
-                }
-                const uint64_t bs = b0 + (uint64_t)s * ((WF >= 6 ? 32768 : 16384) >> 4);
-#pragma unroll
-                for (int j = 0; j < (CH > 0 ? CH : 1); ++j) {
-                    const uint64_t ja = WF >= 6 ? (uint64_t)(j >> 1) * (8192 >> 4) : 0;
-                    const uint64_t jb = WF >= 6 ? (uint64_t)(j >> 1) * (13312 >> 4) : 0;
-                    mma_bf16(tmem, a0 + ja + (uint64_t)((j & 1) * 2), bs + jb + (uint64_t)((j & 1) * 2), id,
-                             (c | j) ? 1u : 0u);
-                }
-                if (WF != 3 || (c & 1)) mma_commit(bars + 64 + 8 * s);
-                if (WF == 5) mma_commit(bars + 136);
-                if (WF == 7 && c % 7 == 6) mma_commit(bars + 152);
-                if (stamp) st_tr[(c - 100) * 3 + 2] = clock64();
-                if (++s == S) { s = 0; ph ^= 1u; }
-            }
-        }
-        mma_commit(bars + 128);
-        if (!mbar_wait(bars + 128, 0, &abort_flag)) atomicOr(err, 1);
-        cycles[blockIdx.x] = clock64() - t0;
-    } else if (WF == 7 && warp >= 2) {
-        // epilogue stand-in: one wait per 7-stage "layer", then four arrivals
-        const int nlayer = nchunk / 7;
-        for (int l = 0; l < nlayer; ++l) {
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(bars + 152, l & 1, &abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) break;
-            for (int p = 0; p < 4; ++p) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bars + 160 + 8 * p);
-            }
-        }
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (abort_flag) atomicOr(err, 2);
-    if (warp == 1) tmem_dealloc(tmem, 256);
-}
-
-template <int CH, int WF>
-int run_ring(int nmma, int copy, int grid, const void* src, long long* cycles, int* err) {
-    if (cudaFuncSetAttribute(k_mma_ring<CH, WF>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess)
-        return -12;
-    k_mma_ring<CH, WF><<<grid, WF == 7 ? 320 : 128, SMEM>>>(nmma, copy, (const unsigned char*)src, cycles, err);
-    if (cudaGetLastError() != cudaSuccess) return -13;
-    if (cudaDeviceSynchronize() != cudaSuccess) return -14;
-    return 0;
-}
-
-}  // namespace
-
-extern "C" int tc_mma_ring(int ch, int wf, int nmma, int copy, int grid, const void* src, long long* cycles,
-                           int* err) {
-    switch (ch * 10 + wf) {
-        case 0: return run_ring<0, 0>(nmma, copy, grid, src, cycles, err);
-        case 20: return run_ring<2, 0>(nmma, copy, grid, src, cycles, err);
-        case 21: return run_ring<2, 1>(nmma, copy, grid, src, cycles, err);
-        case 22: return run_ring<2, 2>(nmma, copy, grid, src, cycles, err);
-        case 23: return run_ring<2, 3>(nmma, copy, grid, src, cycles, err);
-        case 40: return run_ring<4, 0>(nmma, copy, grid, src, cycles, err);
-        case 41: return run_ring<4, 1>(nmma, copy, grid, src, cycles, err);
-        case 44: return run_ring<4, 4>(nmma, copy, grid, src, cycles, err);
-        case 45: return run_ring<4, 5>(nmma, copy, grid, src, cycles, err);
-        case 46: return run_ring<4, 6>(nmma, copy, grid, src, cycles, err);
-        case 47: return run_ring<4, 7>(nmma, copy, grid, src, cycles, err);
-        case 80: return run_ring<8, 0>(nmma, copy, grid, src, cycles, err);
-        default: return -1;
-    }
-}
-
 
 namespace {
 

@@ -20,3 +20,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_is_the_reference_measurement():
+    """The GPU arm's cpu_baseline is the reference arm's own measurement, run in a fresh
+    process after every oracle pyramid level was built (so no timed step builds one)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.cpu_baseline_subprocess(24, 2, 1)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
+    assert cb["per_step_min"] <= cb["per_step_median"] <= cb["per_step_max"]
+    assert "pyramid level built first" in cb["sample"]

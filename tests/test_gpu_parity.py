@@ -92,6 +92,26 @@ def test_stats_and_mips_bit_exact(ctx, shape, seed):
         assert np.abs(g - r64).max() <= 2e-6 * max(1.0, np.abs(r64).max())
 
 
+def test_stats_mean_exact_over_the_exponent_range(ctx):
+    """The fixed-point mean (32 fraction bits below the majorant's exponent, truncated per
+    voxel, summed exactly) over values spread across every float exponent, subnormals
+    included: the GPU's integer form of each truncation equals the oracle's."""
+    rng = np.random.default_rng(77)
+    n = 32 * 32 * 32
+    e = rng.integers(-149, 6, size=n)
+    v = np.ldexp(rng.uniform(1.0, 2.0, size=n), e).astype(np.float32)
+    v[rng.random(n) < 0.3] = 0.0
+    v[0] = np.float32(np.ldexp(1.0, -149))          # smallest subnormal
+    v[1] = np.float32(47.5)                         # the majorant
+    d = v.reshape(32, 32, 32)
+    g = ctx.load_volume(cuda(d))
+    ctx.build_mips(g)
+    gi = ctx.get_volume_info(g)
+    oi = oracle.Volume(d).stats()
+    assert gi["mean"] == oi["mean"] and gi["nonzero"] == oi["nonzero"] and gi["majorant"] == oi["majorant"]
+    assert abs(oi["mean"] - oi["mean_ld"]) <= 2.0 ** -32 * 64 * 2
+
+
 def test_volume_rejects_bad_input(ctx, api):
     d = np.ones((8, 8, 8), np.float32)
     d[3, 3, 3] = -1.0
@@ -332,6 +352,23 @@ def test_render_bf16_matches_oracle(ctx, api, blob_vol, blob_orc, cam64, params)
     assert _rel_l2(got, ref) <= BF16_REL
     scale = np.maximum(np.abs(ref), np.median(np.abs(ref[ref > 0])))
     assert (np.abs(got - ref) <= 3e-2 * scale).mean() >= 0.98
+
+
+def test_path_render_matches_oracle(ctx, api, blob_vol, blob_orc, cam64):
+    """RPNN_MODE_PATH, the plain Monte Carlo path tracer (Henyey-Greenstein phase function)
+    that judges per-pixel error: the same Philox streams make the GPU follow the oracle's
+    paths decision by decision; a path whose decision flips on an FP32 rounding differs."""
+    img = ctx.render(blob_vol, cam64, precision=api.F32, mode=api.MODE_PATH)
+    ctx.sync_status()
+    got = img.cpu().numpy().ravel().astype(np.float64)
+    ref = blob_orc.render_pixels(cam64, np.arange(got.size), mode=1)
+    single = blob_orc.render_pixels(cam64, np.arange(got.size), mode=0)
+    assert ref.mean() > 1.2 * single.mean()            # multiple scattering is present
+    tol = 1e-3 * np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max()) + 1e-7
+    frac = (np.abs(got - ref) <= tol).mean()
+    print(f"HG path render: {frac:.4f} of pixels within 1e-3 of the oracle")
+    assert frac >= 0.9, frac
+    assert abs(got.mean() / ref.mean() - 1) <= 0.02
 
 
 def test_render_multi_spp_and_ragged_image(ctx, api, blob_vol, blob_orc, params):

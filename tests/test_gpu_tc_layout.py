@@ -101,100 +101,6 @@ def test_mma_sw64_layouts(probe):
     assert np.array_equal(box, exp)
 
 
-def test_mma_issue_rate(probe, capsys):
-    """Back-to-back tcgen05.mma throughput on resident operands (reported, loosely checked)."""
-    probe.tc_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
-    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rates = {}
-    cases = [(4, 128, "sw64 N208, 4 warps"), (6, 128, "sw64 N256, 4 warps"), (4, 160, "sw64 N208, 5 warps"),
-             (4, 192, "sw64 N208, 6 warps"), (4, 256, "sw64 N208, 8 warps"), (4, 320, "sw64 N208, 10 warps"),
-             (4 | 32, 256, "8 warps, 4 exit early"), (4 | 16, 128, "4 warps, wait+fence per 2"),
-             (4 | 8, 256, "8 warps, 7 polling")]
-    for mode, nt, name in cases:
-        n = 4096
-        assert probe.tc_mma_rate(n, mode, cyc.data_ptr(), err.data_ptr(), nt) == 0
-        assert err.item() == 0
-        issue, done = cyc.cpu().tolist()
-        macs = 128 * (256 if mode & 2 else 208) * 16
-        rates[name] = (issue / n, done / n, macs / (done / n))
-    with capsys.disabled():
-        for k, (i, d, r) in rates.items():
-            print(f"\n[mma rate] {k:28s} issue {i:7.1f} cyc/mma  complete {d:7.1f} cyc/mma  {r:7.0f} MAC/clk")
-    for _, d, _ in rates.values():
-        assert d > 0
-
-
-def test_mma_issue_loop_variants(probe, capsys):
-    probe.tc_mma_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
-    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    names = ["plain", "wait/2", "fence::after/2", "fence before loop", "commit/2", "wait+commit/2",
-             "relaxed try_wait/2", "test_wait/2", "relaxed test_wait/2", "asm try_wait loop/2", "wait/4",
-             "bounded asm, no output/2", "abort check + bounded/2", "volatile counter poll/2",
-             "acquire counter poll/2", "bounded asm, no output/4"]
-    out = []
-    for v, name in enumerate(names):
-        assert probe.tc_mma_variant(v, 4096, cyc.data_ptr(), err.data_ptr()) == 0
-        assert err.item() == 0
-        out.append((name, cyc.cpu().tolist()[1] / 4096))
-    with capsys.disabled():
-        for name, c in out:
-            print(f"\n[mma loop] {name:20s} {c:7.1f} cyc/mma")
-
-
-def test_mma_rate_with_concurrent_copies(probe, capsys):
-    probe.tc_mma_with_copies.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-    src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
-    cyc = torch.zeros(2, dtype=torch.int64, device="cuda")
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for mode, name in [(0, "bulk copies"), (1, "bulk copies + smem stores"), (2, "bulk copies + tmem loads"),
-                       (4, "bulk copies + A rewrites")]:
-        assert probe.tc_mma_with_copies(4096, mode, src.data_ptr(), cyc.data_ptr(), err.data_ptr()) == 0
-        assert err.item() == 0
-        copies, c = cyc.cpu().tolist()
-        with capsys.disabled():
-            print(f"\n[mma + traffic] {name:26s} {c / 4096:7.1f} cyc/mma, {copies} copies of 13 KB "
-                  f"({copies * 13312 / c:5.1f} B/clk)")
-
-
-def test_mma_rate_through_ring(probe, capsys):
-    """MMA rate when every CH MMAs wait for a ring stage and commit it back, on one SM and
-    on every SM at once (the network kernel's pipeline without its epilogue), for three
-    forms of the issuing thread's wait."""
-    probe.tc_mma_ring.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 3
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    src = torch.zeros(64 * 13312, dtype=torch.uint8, device="cuda")
-    cyc = torch.zeros(nsm + 24, dtype=torch.int64, device="cuda")
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    stamps = {}
-    forms = ["branch on success", "fall-through", "fall-through, 2 stages", "commit every 2 stages",
-             "three-barrier poll", "two commits per stage", "4 distinct operands",
-             "4 distinct, + 8 polling warps"]
-    out = []
-    for ch, wf in [(0, 0), (2, 0), (2, 1), (2, 2), (2, 3), (4, 0), (4, 1), (4, 4), (4, 5), (4, 6), (4, 7), (8, 0)]:
-        for copy in ((0,) if ch == 0 else (0, 1, 2, 3)):
-            for grid in (1, nsm) if copy < 2 else (nsm,):
-                cyc.zero_()
-                err.zero_()
-                assert probe.tc_mma_ring(ch, wf, 4096, copy, grid, src.data_ptr(), cyc.data_ptr(),
-                                         err.data_ptr()) == 0
-                c = cyc[:grid].double().cpu()
-                if wf >= 6:
-                    stamps[(wf, copy, grid)] = cyc[grid:grid + 24].cpu().tolist()
-                out.append((ch, forms[wf], copy, grid, c.mean().item() / 4096, c.max().item() / 4096, err.item()))
-    with capsys.disabled():
-        for ch, form, copy, grid, mean, mx, e in out:
-            print(f"\n[mma ring] {ch} MMAs/stage, {form:22s} copy={copy & 1} sleep={copy >> 1} grid={grid:3d}  {mean:7.1f} cyc/mma "
-                  f"(max {mx:7.1f}) err={e}")
-        for (wf, copy, grid), st in stamps.items():
-            t0 = st[0]
-            print(f"\n[mma ring stages] wf={wf} copy={copy & 1} sleep={copy >> 1} grid={grid}: " +
-                  "  ".join(f"{st[3 * i] - t0}/{st[3 * i + 1] - t0}/{st[3 * i + 2] - t0}" for i in range(8)))
-    assert all(o[-1] == 0 for o in out)
-
-
-
 def sw64_image_bytes(B):
     """[rows][128] bytes -> two 64-byte-wide blocks, row-major 64-byte rows, 16-byte unit j
     of row n at unit j ^ ((n >> 1) & 3)."""

@@ -152,3 +152,55 @@ def test_bf16_fit_lowers_validation_loss(env):
     hist = train.fit(ctx, tr, va, params, steps=300, batch=1024, lr=1e-3, eval_every=100)
     v1 = hist[-1][2]
     assert v1 < 0.3 * v0, (v0, hist)
+
+
+@pytest.mark.parametrize("precision", ["F32", "BF16"])
+def test_bf16_training_records_equal_rounded_fp32_records(env, cloud_desc, precision):
+    """rpnn_train_step and rpnn_mlp_backward take BF16 descriptor rows (half the record
+    memory).  BF16 rows are the FP32 rows' RNE rounding; fed as BF16, or as the same values
+    widened back to FP32, both training forms give the same loss, gradient and update bit
+    for bit."""
+    api, ctx, params = env
+    zb = torch.from_numpy(cloud_desc).cuda().to(torch.bfloat16)
+    zf = zb.float()
+    target = torch.linspace(0.01, 0.5, zb.shape[0], device="cuda")
+    dout = torch.from_numpy(np.random.default_rng(9).normal(size=zb.shape[0]).astype(np.float32)).cuda()
+    ctx.set_train_precision(getattr(api, precision))
+    try:
+        ctx.set_weights(params)
+        assert torch.equal(ctx.mlp_backward(zb, dout), ctx.mlp_backward(zf, dout))
+        res = []
+        for z in (zb, zf):
+            p = params.clone()
+            m, v = torch.zeros_like(p), torch.zeros_like(p)
+            loss = ctx.train_step(z, target, p, m, v, step=1, lr=1e-3)
+            res.append((float(loss), p, m, v))
+            ctx.set_weights(params)
+        assert res[0][0] == res[1][0]
+        for a, b in zip(res[0][1:], res[1][1:]):
+            assert torch.equal(a, b)
+        with pytest.raises(api.RPNNError):
+            ctx.train_step(zb.to(torch.float16), target, params.clone(), torch.zeros_like(params),
+                           torch.zeros_like(params), step=1)
+    finally:
+        ctx.set_train_precision(api.BF16)
+        ctx.set_weights(params)
+
+
+def test_autograd_function_bf16_route(env, cloud_desc):
+    """In BF16 training precision the autograd Function runs the tensor-core forward on BF16
+    descriptors and rpnn_mlp_backward's BF16 gradient; FP32 descriptors are refused."""
+    from paper_1709_05418_gb300.autograd import rpnn
+    api, ctx, params = env
+    zb = torch.from_numpy(cloud_desc).cuda().to(torch.bfloat16)
+    p = params.clone().requires_grad_(True)
+    g = rpnn(p, zb, ctx)
+    ref = ctx.mlp_forward(zb, precision=api.BF16)
+    assert torch.equal(g.detach(), ref)
+    w = torch.from_numpy(np.random.default_rng(10).normal(size=zb.shape[0]).astype(np.float32)).cuda()
+    (g * w).sum().backward()
+    ctx.set_weights(params)
+    assert torch.equal(p.grad, ctx.mlp_backward(zb, w))
+    with pytest.raises(TypeError):
+        rpnn(p, zb.float(), ctx)
+    ctx.set_weights(params)
