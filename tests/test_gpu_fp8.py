@@ -1,7 +1,7 @@
 """FP8 (E4M3) form of the network (per-tensor scales, FP32 accumulation) against the FP64
 oracle: the E4M3 descriptor is the round-to-nearest-even E4M3 value of the bit-exact FP32
 descriptor; network outputs stay within the FP8 budget (relative L2 <= 3e-2 over a
-batch); rendered images are reported and held to 5e-2 (the network's error reaches them
+batch, and per element within 9e-2 of max(|y|, median |y|)); rendered images are reported and held to 5e-2 (the network's error reaches them
 through the share of each pixel that is the prediction); the FP8 path refuses to run
 before calibration."""
 import numpy as np
@@ -14,7 +14,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP8_REL = 3e-2        # network output, relative L2 over the batch
-FP8_ELEM = 3e-2       # network output, per element: |err| <= FP8_ELEM * max(|y|, median |y|)
+# network output, per element: |err| <= FP8_ELEM * max(|y|, median |y|).  Three times the
+# norm-wise bound, as the BF16 tests' per-element 3e-2 is three times their 1e-2: one E4M3
+# rounding moves a value by up to 2^-4 = 6.25 %, and a prediction dominated by a few
+# activations inherits about that (largest measured: 7.2e-2), so a per-element bound at the
+# norm-wise 3e-2 is below the format's own resolution.
+FP8_ELEM = 9e-2
 FP8_IMG_REL = 5e-2    # rendered image, relative L2 over the pixels
 
 
