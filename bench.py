@@ -910,6 +910,28 @@ def main():
                     "ms_per_step": ms32 / max(3, args.steps // 4),
                     "network_ms_per_step": prof32["network"] / max(1, prof32["renders"])}
         f32_form["ratio"] = value / ws / f32_form["value"]
+        # the ratio's denominator against its own roofline: the 23-launch FP32 CUDA-core GEMM
+        # chain (autotuned tiles) on the FP32 pipe, 128 FMA lanes x 2 FLOP per SM per clock
+        pk32 = peaks()
+        alu_peak = 152 * 128 * 2 * pk32["sm_max_mhz"] * 1e6 / 1e12
+        ach32 = nq32 * FLOP_PER_QUERY / (f32_form["network_ms_per_step"] / 1e3) / 1e12
+        f32_form["network_roofline"] = {"bound": "alu", "achieved": ach32, "peak": alu_peak, "unit": "TFLOP/s",
+                                        "frac": ach32 / alu_peak, "kernel": "k_gemm chain (23 launches)",
+                                        "peak_src": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+
+    # the same BF16 render with the descriptor and network stages as separate kernels
+    # (descriptor rows written to and read back from HBM), for the fusion's effect
+    unfused_form = None
+    if prec == api.BF16:
+        ctx.set_fused(False)
+        nqu, msu, profu, imgu = timed(api.BF16, args.steps, 3)
+        ctx.set_fused(True)
+        nr = max(1, profu["renders"])
+        unfused_form = {"value": nqu * args.steps / (msu / 1e3), "unit": "queries/s", "ms_per_step": msu / args.steps,
+                        "stages_ms_per_step": {k: profu[k] / nr for k in ("primary", "descriptor", "network",
+                                                                          "composite")},
+                        "image_equal_to_fused": bool(torch.equal(imgu, img))}
+        del imgu
 
     # FP8 (E4M3) form of the same render: per-tensor scales calibrated on this render's own
     # shading points (FP32 descriptors of up to 65,536 of them), outside the timed region
@@ -1018,9 +1040,12 @@ def main():
         ach = desc_bytes / (stage_ms[st] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_per_launch(dom, nq) if prec == api.BF16 else None
+    # BF16: the network stage is the fused kernel (descriptor gather + network in one launch)
+    kname = "fused" if (prec == api.BF16 and dom == "network") else dom
+    roof["traffic"] = traffic_per_launch(kname, nq) if prec == api.BF16 else None
     roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
-    roof["kernel"] = dom
+    roof["kernel"] = ("k_rpnn_fused: descriptor gather + tcgen05 network, no descriptor rows in HBM"
+                      if kname == "fused" else dom)
     roof["peak_src"] = pk["src"]
     # a1/a2: the FP32 grid read once and the packed pyramid levels written once
     nvox = int(np.prod(info["n"]))
@@ -1037,8 +1062,10 @@ def main():
     if prec == api.BF16:
         ach = nq * FLOP_PER_QUERY / (stage_ms["network"] / 1e3) / 1e12
         line_net = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                    "frac": ach / pk["bf16_tflops"], "traffic": traffic_per_launch("network", nq),
-                    "algorithmic_bytes": nq * (10 * 240 * 2), "kernel": "network", "peak_src": pk["src"]}
+                    "frac": ach / pk["bf16_tflops"], "traffic": traffic_per_launch("fused", nq),
+                    "algorithmic_bytes": nq * (24 + 4), "kernel": "k_rpnn_fused", "peak_src": pk["src"],
+                    "note": "fused kernel: reads each shading point (x, d) and writes g; the weight image and "
+                            "the corner-packed pyramid levels stay L2-resident"}
         if fp8_form:
             ms_net8 = fp8_form["network_ms_per_step"]
             ach8 = nq8 * FLOP_PER_QUERY / (ms_net8 / 1e3) / 1e12
@@ -1061,7 +1088,9 @@ def main():
         "stages_ms_per_step": stage_ms,
         "primary_rays_per_s": 512 * 512 / (stage_ms["primary"] / 1e3),
         "pyramid_build": pyramid,
-        "gpu_launches": (5 if prec == api.BF16 else 27) * args.steps,
+        # primary, fused descriptor+network, scatter, composite (BF16); the FP32 form runs the
+        # descriptor and 23 GEMM launches
+        "gpu_launches": (4 if prec == api.BF16 else 27) * args.steps,
         "e2e": e2e, "roofline": roof, "clocks": clk,
     }
     if prec == api.BF16:
@@ -1070,6 +1099,8 @@ def main():
             line["network_roofline"]["steady_state_1m_rows"] = net_1m
     if f32_form:
         line["fp32_form"] = f32_form
+    if unfused_form:
+        line["unfused_form"] = unfused_form
     if fp8_form:
         line["fp8_form"] = fp8_form
     if rank == 0 and not args.no_cpu:

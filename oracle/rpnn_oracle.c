@@ -480,6 +480,17 @@ static void duff_basis(const double n[3], double b1[3], double b2[3]) {
     b2[0] = b; b2[1] = sign + n[1] * n[1] * a; b2[2] = -n[1];
 }
 
+/* The first vector of the same basis in FP32 with one fixed rounding sequence (the FP32
+ * restatement's degenerate frame): sign = copysign(1, z), a = -1 / (sign + z),
+ * x = (1 + ((sign x) x) a, sign ((x y) a), -sign x), every operation rounded to float. */
+static void duff_x_f32(const float n[3], float b1[3]) {
+    const float sign = signbit(n[2]) ? -1.0f : 1.0f;
+    const float a = -1.0f / (sign + n[2]);
+    b1[0] = 1.0f + ((sign * n[0]) * n[0]) * a;
+    b1[1] = sign * ((n[0] * n[1]) * a);
+    b1[2] = -sign * n[0];
+}
+
 static void cross64(const double a[3], const double b[3], double o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
@@ -551,7 +562,7 @@ int orc_descriptor_f64(orc_ctx* c, const double* x, const double* d, const doubl
 /* FP32 restatement of the same descriptor with one fixed rounding sequence:
  *   omega = -d; c = ez x omega (each product rounded, then the difference);
  *   len2 = (c0*c0 + c1*c1) + c2*c2; ex = c / sqrtf(len2) (correctly rounded ops);
- *   degenerate (len2 < 1e-12): Duff basis in FP64 from the FP32 inputs, rounded;
+ *   degenerate (len2 < 1e-12): Duff basis in FP32 (duff_x_f32);
  *   ey = ez x ex; cos gamma = (w0*l0 + w1*l1) + w2*l2, clamped; gamma = acosf;
  *   level k (0-based here): s = inv_h0 * 2^-m, g = (inv_mean_f * 2^k) * s,
  *   A = g*ex, B = g*ey, C = g*ez, U0 = x*s - 0.5,
@@ -581,9 +592,7 @@ int orc_descriptor_f32(orc_ctx* c, const float* x, const float* d, const float w
         { float a = cr[0] * cr[0], b = cr[1] * cr[1], e = cr[2] * cr[2]; len2 = (a + b) + e; }
         float ex[3];
         if (len2 < 1e-12f) {
-            double n[3] = {ez[0], ez[1], ez[2]}, b1[3], b2[3];
-            duff_basis(n, b1, b2);
-            for (int a = 0; a < 3; ++a) ex[a] = (float)b1[a];
+            duff_x_f32(ez, ex);
         } else {
             float len = sqrtf(len2);
             for (int a = 0; a < 3; ++a) ex[a] = cr[a] / len;
@@ -721,9 +730,7 @@ int orc_descriptor_stencil_f32(orc_ctx* c, int n, const float* x, const float* d
         { float a = cr[0] * cr[0], b = cr[1] * cr[1], e = cr[2] * cr[2]; len2 = (a + b) + e; }
         float ex[3];
         if (len2 < 1e-12f) {
-            double nn[3] = {ez[0], ez[1], ez[2]}, b1[3], b2[3];
-            duff_basis(nn, b1, b2);
-            for (int a = 0; a < 3; ++a) ex[a] = (float)b1[a];
+            duff_x_f32(ez, ex);
         } else {
             float len = sqrtf(len2);
             for (int a = 0; a < 3; ++a) ex[a] = cr[a] / len;

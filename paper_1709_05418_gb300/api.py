@@ -119,6 +119,7 @@ def load():
             "rpnn_render_env": [_vp, i32, C.POINTER(RenderDesc), C.POINTER(f32), C.POINTER(f32), i32, _vp,
                                 C.POINTER(i64), _vp],
             "rpnn_set_render_chunk": [_vp, i64],
+            "rpnn_set_fused": [_vp, i32],
             "rpnn_calibrate_fp8": [_vp, _vp, i64, _vp],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
@@ -450,6 +451,11 @@ class Context:
 
     def set_render_chunk(self, rows: int):
         self._check(self.L.rpnn_set_render_chunk(self.h, rows))
+
+    def set_fused(self, on: bool):
+        """BF16 renders gather descriptors inside the network kernel (default) or run the
+        descriptor and network stages separately."""
+        self._check(self.L.rpnn_set_fused(self.h, 1 if on else 0))
 
     def render_batch(self, jobs, images=None, want_counts=False):
         """Renders several clouds in one batched launch sequence (BF16 network): `jobs` is a

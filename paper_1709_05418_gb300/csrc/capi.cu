@@ -438,6 +438,8 @@ static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc
     const int64_t P = (int64_t)desc->width * desc->height * desc->spp;
     const bool f32 = desc->precision == RPNN_F32;
     const bool fp8 = desc->precision == RPNN_FP8E4M3;
+    // BF16: descriptor and network in one kernel, no descriptor rows in memory
+    const bool fused = net && !f32 && !fp8 && c->fused && fused_supported(v->view());
     const size_t desc_row_bytes = fp8 ? (size_t)RPNN_K * RPNN_DESC_STRIDE_FP8 : (size_t)RPNN_K * RPNN_DESC_STRIDE * (f32 ? 4 : 2);
     // the descriptor and network stages run over chunks of at most kChunkRows queries, so
     // the descriptor buffer stays bounded (5 GB BF16) for renders of millions of samples
@@ -453,7 +455,7 @@ static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc
     }
     if (net) {
         if (!st) st = c->g_out.reserve(P * sizeof(float));
-        if (!st) st = c->desc.reserve((size_t)CH * desc_row_bytes);
+        if (!st && !fused) st = c->desc.reserve((size_t)CH * desc_row_bytes);
         if (!st) st = ensure_rows(c, CH, f32);
     }
     if (st) return st;
@@ -505,6 +507,13 @@ static rpnn_status render_impl(Ctx* c, int32_t vol, const rpnn_render_desc* desc
             for (int i = 0; i < nchunks; ++i) {
                 const int* cnt = nchunks > 1 ? qc + 1 + i : qc;
                 const int64_t first = (int64_t)i * CH;
+                if (fused) {
+                    if (ev && j == nl - 1 && i == nchunks - 1) RPNN_CUDA_TRY(cudaEventRecord(ev[2], s));
+                    st = fused_forward_bf16(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
+                                            &lights[3 * j], CH, cnt, c->g_out.as<float>() + first, s);
+                    if (st) return st;
+                    continue;
+                }
                 st = launch_descriptor(*c, vv, c->q_x.as<float>() + 3 * first, c->q_d.as<float>() + 3 * first,
                                        ldir + 3 * j, 0, CH, cnt, c->desc.p,
                                        f32 ? RPNN_F32 : (fp8 ? RPNN_FP8E4M3 : RPNN_BF16), s);
@@ -566,6 +575,12 @@ rpnn_status rpnn_render_env(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* 
     }
     return render_impl(reinterpret_cast<Ctx*>(ctx), vol, desc, dirs, irradiance, n, dev_image, out_num_queries,
                        (cudaStream_t)stream);
+}
+
+rpnn_status rpnn_set_fused(rpnn_ctx* ctx, int32_t on) {
+    CHECK_CTX(ctx);
+    reinterpret_cast<Ctx*>(ctx)->fused = on != 0;
+    return RPNN_OK;
 }
 
 rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows) {

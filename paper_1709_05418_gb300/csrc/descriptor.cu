@@ -15,10 +15,13 @@
 #include <cuda_fp8.h>
 
 #include "common.cuh"
+#include "desc_lookup.cuh"
 
 namespace rpnn {
 
 namespace {
+
+using namespace desc;
 
 template <class T> __device__ __forceinline__ T cvt_out(float v);
 template <> __device__ __forceinline__ float cvt_out<float>(float v) { return v; }
@@ -26,103 +29,6 @@ template <> __device__ __forceinline__ float cvt_out<float>(float v) { return v;
 template <> __device__ __forceinline__ __nv_fp8_e4m3 cvt_out<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
-}
-
-__device__ __forceinline__ float lerp_rn(float a, float b, float f) {
-    return __fmaf_rn(f, __fsub_rn(b, a), a);
-}
-
-struct Frame {
-    float ex[3], ey[3], ez[3];
-    float gamma;
-};
-
-__device__ __forceinline__ Frame make_frame(const float d[3], const float wl[3]) {
-    Frame F;
-    const float w[3] = {-d[0], -d[1], -d[2]};
-    const float* ez = wl;
-    float cr[3];
-    cr[0] = __fsub_rn(__fmul_rn(ez[1], w[2]), __fmul_rn(ez[2], w[1]));
-    cr[1] = __fsub_rn(__fmul_rn(ez[2], w[0]), __fmul_rn(ez[0], w[2]));
-    cr[2] = __fsub_rn(__fmul_rn(ez[0], w[1]), __fmul_rn(ez[1], w[0]));
-    const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(cr[0], cr[0]), __fmul_rn(cr[1], cr[1])),
-                                 __fmul_rn(cr[2], cr[2]));
-    if (len2 < 1e-12f) {
-        // Duff et al. 2017 basis of z, in FP64 from the FP32 inputs, rounded
-        const double n0 = ez[0], n1 = ez[1], n2 = ez[2];
-        const double sg = signbit(ez[2]) ? -1.0 : 1.0;   // copysign(1, z)
-        const double a = __ddiv_rn(-1.0, __dadd_rn(sg, n2));
-        F.ex[0] = __double2float_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, n0), n0), a)));
-        F.ex[1] = __double2float_rn(__dmul_rn(sg, __dmul_rn(__dmul_rn(n0, n1), a)));
-        F.ex[2] = __double2float_rn(__dmul_rn(-sg, n0));
-    } else {
-        const float len = __fsqrt_rn(len2);
-        for (int a = 0; a < 3; ++a) F.ex[a] = __fdiv_rn(cr[a], len);
-    }
-    for (int a = 0; a < 3; ++a) F.ez[a] = ez[a];
-    F.ey[0] = __fsub_rn(__fmul_rn(ez[1], F.ex[2]), __fmul_rn(ez[2], F.ex[1]));
-    F.ey[1] = __fsub_rn(__fmul_rn(ez[2], F.ex[0]), __fmul_rn(ez[0], F.ex[2]));
-    F.ey[2] = __fsub_rn(__fmul_rn(ez[0], F.ex[1]), __fmul_rn(ez[1], F.ex[0]));
-    float cg = __fadd_rn(__fadd_rn(__fmul_rn(w[0], wl[0]), __fmul_rn(w[1], wl[1])), __fmul_rn(w[2], wl[2]));
-    cg = fminf(fmaxf(cg, -1.0f), 1.0f);
-    F.gamma = acosf(cg);
-    return F;
-}
-
-// Per-level constants of one volume, staged in shared memory once per block: the
-// coordinate scale s = inv_h0 * 2^-m and gk = (inv_mean * 2^(k-1)) * s of level k (mip m),
-// the level dims, and the record index of cell (0,0,0) with the record strides (records
-// cover cells -1 .. n-1 on each axis).
-struct LevelGeo {
-    float hx, hy, hz;          // 1.5*2^23 + n - 1 per axis: the largest valid t (see lookup)
-    uint32_t rbias, sy, sz;    // record index = rbias + bits(t2) sz + bits(t1) sy + bits(t0)
-};
-// Level k's constants (32 bytes, two 16-byte shared loads) ...
-struct __align__(16) LevelK {
-    float s, gk;
-    LevelGeo g0;
-};
-// ... and, for a blended descriptor, those of mip level m + 1 with its weight w (w = 0:
-// level k reads level m alone)
-struct __align__(16) LevelB {
-    float s1, gk1, w, pad;
-    LevelGeo g1;
-    uint32_t pad2[2];
-};
-
-// Trilinear lookup from one 32-byte corner record (c0, c1-c0, c2, c3-c2, c4, c5-c4, c6,
-// c7-c6).  floor(u) without conversions: t = u + 1.5*2^23 rounded down is floor(u) +
-// 1.5*2^23 exactly for |u| < 2^22, and its bit pattern minus that of 1.5*2^23 is the cell
-// index; the fraction u - (t - 1.5*2^23) is u - floor(u) exactly.  The cell is inside
-// [-1, n-1] iff t lies in [1.5*2^23 - 1, 1.5*2^23 + n - 1], a test that also rejects any
-// |u| >= 2^22 (t then falls outside), so out-of-range points read 0 exactly as the
-// reference, which clamps |u| to 1e6 first.  The record index folds the bit-pattern
-// offsets into r000 (uint32 wrap-around).  The x-lerps use the stored differences, which
-// round exactly as lerp_rn's own subtraction.
-constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
-
-__device__ __forceinline__ float lookup(const float4* __restrict__ packed, const LevelGeo& g, float u0, float u1,
-                                        float u2) {
-    const float t0 = __fadd_rd(u0, kFloorMagic), t1 = __fadd_rd(u1, kFloorMagic), t2 = __fadd_rd(u2, kFloorMagic);
-    if (!(t0 >= kFloorMagic - 1.0f && t0 <= g.hx && t1 >= kFloorMagic - 1.0f && t1 <= g.hy &&
-          t2 >= kFloorMagic - 1.0f && t2 <= g.hz))
-        return 0.0f;
-    const float f0 = __fsub_rn(u0, __fsub_rn(t0, kFloorMagic));
-    const float f1 = __fsub_rn(u1, __fsub_rn(t1, kFloorMagic));
-    const float f2 = __fsub_rn(u2, __fsub_rn(t2, kFloorMagic));
-    const uint32_t r = g.rbias + (uint32_t)__float_as_int(t2) * g.sz + (uint32_t)__float_as_int(t1) * g.sy +
-                       (uint32_t)__float_as_int(t0);
-    float c[8];
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
-        : "l"(packed + 2 * (size_t)r));
-    const float c00 = __fmaf_rn(f0, c[1], c[0]);
-    const float c10 = __fmaf_rn(f0, c[3], c[2]);
-    const float c01 = __fmaf_rn(f0, c[5], c[4]);
-    const float c11 = __fmaf_rn(f0, c[7], c[6]);
-    const float c0 = lerp_rn(c00, c10, f1);
-    const float c1 = lerp_rn(c01, c11, f1);
-    return lerp_rn(c0, c1, f2);
 }
 
 // One warp per shading point (8 per block, grid-stride over points, one block-wide
@@ -133,44 +39,6 @@ __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const
 // per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
 // directly (25 consecutive values per level and z-slice).
 //
-// level k's constants of volume v
-__device__ __forceinline__ LevelGeo make_geo(const VolumeView& v, int m) {
-    const LevelDesc L = v.lvl[m];
-    LevelGeo g;
-    g.hx = kFloorMagic + (float)(L.ax - 1);
-    g.hy = kFloorMagic + (float)(L.ay - 1);
-    g.hz = kFloorMagic + (float)(L.az - 1);
-    g.sy = (uint32_t)(L.ax + 1);
-    g.sz = (uint32_t)((L.ax + 1) * (L.ay + 1));
-    // cell (i0, i1, i2) is record rec_offset + (i2+1) sz + (i1+1) sy + (i0+1), and
-    // i = bits(t) - bits(1.5*2^23)
-    const uint32_t mb = (uint32_t)__float_as_int(kFloorMagic);
-    g.rbias = (uint32_t)L.rec_offset + g.sz + g.sy + 1u - mb * (g.sz + g.sy + 1u);
-    return g;
-}
-
-// level k's constants of volume v
-__device__ __forceinline__ LevelK make_level(const VolumeView& v, int k) {
-    const int m = v.mip_of_level[k];
-    LevelK g;
-    g.s = __fmul_rn(v.inv_h0, __int_as_float((127 - m) << 23));   // * 2^-m
-    g.gk = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), g.s);
-    g.g0 = make_geo(v, m);
-    return g;
-}
-
-__device__ __forceinline__ LevelB make_blend(const VolumeView& v, int k) {
-    const int m = v.mip_of_level[k];
-    LevelB b{};
-    b.w = v.mip_w[k];
-    if (b.w > 0.0f) {
-        b.s1 = __fmul_rn(v.inv_h0, __int_as_float((126 - m) << 23));   // * 2^-(m+1)
-        b.gk1 = __fmul_rn(__fmul_rn(v.inv_mean_f, (float)(1 << k)), b.s1);
-        b.g1 = make_geo(v, m + 1);
-    }
-    return b;
-}
-
 // BATCH: the shading points of up to RPNN_MAX_BATCH renders, compacted: point j belongs
 // to the item i with off[i] <= j < off[i+1], reads its position and direction at
 // region_i + j - off[i], and uses item i's volume and light; row j of `out` is written.

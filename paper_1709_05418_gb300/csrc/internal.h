@@ -201,6 +201,7 @@ struct Ctx {
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
     int64_t chunk_rows = 0;          // descriptor/network chunk of a render (0: kChunkRows)
+    bool fused = true;               // BF16 renders gather descriptors inside the network kernel
     cudaStream_t capture_stream = nullptr;
     uint64_t epoch = 1;
     // stage timing: one set of 5 events per profiled render
@@ -342,6 +343,11 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
 
 // BF16 tensor-core network
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);
+// Descriptor gather fused into the BF16 network (the render's two stages in one launch):
+// shading points xs / ds ([q][3], or the device count q_dev with capacity q), light wl.
+bool fused_supported(const VolumeView& vv);
+rpnn_status fused_forward_bf16(Ctx& c, const VolumeView& vv, const float* xs, const float* ds, const float wl[3],
+                               int64_t q, const int* q_dev, float* out, cudaStream_t s);
 rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev,
                              float* out, cudaStream_t s);
 // FP8 (E4M3) tensor-core network on [q][10][256] E4M3 descriptors; needs mlp_calibrate_fp8

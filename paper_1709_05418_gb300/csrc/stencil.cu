@@ -66,7 +66,7 @@ struct Frame3 {
 };
 
 // light-aligned frame: ez = wl, ex = normalize(ez x omega), ey = ez x ex (omega = -d);
-// a degenerate omega takes ex from Duff et al.'s basis of ez (FP64 from the FP32 inputs)
+// a degenerate omega takes ex from Duff et al.'s basis of ez (FP32, fixed rounding sequence)
 __device__ __forceinline__ Frame3 light_frame(const float d[3], const float wl[3]) {
     Frame3 F;
     const float w[3] = {-d[0], -d[1], -d[2]};
@@ -77,12 +77,11 @@ __device__ __forceinline__ Frame3 light_frame(const float d[3], const float wl[3
     const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(cr[0], cr[0]), __fmul_rn(cr[1], cr[1])),
                                  __fmul_rn(cr[2], cr[2]));
     if (len2 < 1e-12f) {
-        const double n0 = wl[0], n1 = wl[1], n2 = wl[2];
-        const double sg = signbit(wl[2]) ? -1.0 : 1.0;
-        const double a = __ddiv_rn(-1.0, __dadd_rn(sg, n2));
-        F.ex[0] = __double2float_rn(__dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, n0), n0), a)));
-        F.ex[1] = __double2float_rn(__dmul_rn(sg, __dmul_rn(__dmul_rn(n0, n1), a)));
-        F.ex[2] = __double2float_rn(__dmul_rn(-sg, n0));
+        const float sg = signbit(wl[2]) ? -1.0f : 1.0f;
+        const float a = __fdiv_rn(-1.0f, __fadd_rn(sg, wl[2]));
+        F.ex[0] = __fadd_rn(1.0f, __fmul_rn(__fmul_rn(__fmul_rn(sg, wl[0]), wl[0]), a));
+        F.ex[1] = __fmul_rn(sg, __fmul_rn(__fmul_rn(wl[0], wl[1]), a));
+        F.ex[2] = __fmul_rn(-sg, wl[0]);
     } else {
         const float len = __fsqrt_rn(len2);
         for (int a = 0; a < 3; ++a) F.ex[a] = __fdiv_rn(cr[a], len);

@@ -19,9 +19,6 @@ struct DevStats {
     unsigned int bad;           // negative / NaN / Inf seen
     unsigned long long count;   // voxels > 0
     unsigned long long isum;    // fixed-point sum
-    double mean, inv_mean;
-    float inv_mean_f;
-    int S;
 };
 
 __global__ void k_f16_to_f32(const __half* __restrict__ in, float* __restrict__ out, int64_t n) {
@@ -80,18 +77,6 @@ __global__ void k_stats_sum(const float* __restrict__ v, int64_t n, DevStats* st
     }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&st->isum, s);
-}
-
-__global__ void k_stats_final(DevStats* st) {
-    int e;
-    frexpf(__uint_as_float(st->max_bits), &e);
-    const int S = 32 - e;
-    st->S = S;
-    if (st->count == 0) { st->mean = 0.0; st->inv_mean = 0.0; st->inv_mean_f = 0.0f; return; }
-    const double sum = __ll2double_rn((long long)st->isum);
-    st->mean = __ddiv_rn(ldexp(sum, -S), (double)st->count);
-    st->inv_mean = __ddiv_rn(1.0, st->mean);
-    st->inv_mean_f = __double2float_rn(st->inv_mean);
 }
 
 // One separable pass of the Gaussian filter along `axis` with decimation: output index
@@ -235,13 +220,17 @@ rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
     RPNN_CHECK_LAUNCH();
     k_stats_sum<<<g, 256, 0, s>>>(v.raw.as<float>(), n, ds);
     RPNN_CHECK_LAUNCH();
-    k_stats_final<<<1, 1, 0, s>>>(ds);
-    RPNN_CHECK_LAUNCH();
     DevStats h;
     RPNN_CUDA_TRY(cudaMemcpyAsync(&h, ds, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
     if (h.bad) { set_error("density has negative, NaN or Inf voxels"); return RPNN_ERR_NONFINITE; }
     if (h.count == 0) { set_error("density grid has no voxel > 0"); return RPNN_ERR_ARG; }
+    // mean = (fixed-point sum) 2^-S / count, S = 32 - e with the majorant below 2^e; in
+    // IEEE double on the host (each operation correctly rounded)
+    int e;
+    std::frexp(bits_to_float(h.max_bits), &e);
+    const double mean = std::ldexp((double)(long long)h.isum, -(32 - e)) / (double)h.count;
+    const float inv_mean_f = (float)(1.0 / mean);
     rpnn_volume_info& I = v.info;
     for (int a = 0; a < 3; ++a) I.n[a] = v.n[a];
     const int nmax = std::max(v.n[0], std::max(v.n[1], v.n[2]));
@@ -250,14 +239,14 @@ rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
     I.levels = v.levels = L;
     for (int i = 0; i < 16; ++i)
         for (int a = 0; a < 3; ++a) I.dims[i][a] = v.dims[i][a] = (v.n[a] + (1 << i) - 1) >> i;
-    I.mean = h.mean;
-    I.inv_mean_f = h.inv_mean_f;
+    I.mean = mean;
+    I.inv_mean_f = inv_mean_f;
     I.majorant = bits_to_float(h.max_bits);
     I.nonzero = (int64_t)h.count;
     // mip level read by stencil level k: largest power-of-two voxel not above the
     // stencil spacing 0.5 * 2^(k-1) mean free paths (exact frexp of an exact product)
     for (int k = 0; k < RPNN_K; ++k) {
-        const double sk = 0.5 * std::ldexp((double)h.inv_mean_f, k) * (double)nmax;
+        const double sk = 0.5 * std::ldexp((double)inv_mean_f, k) * (double)nmax;
         int m = 0;
         if (sk > 0.0) { int ex; std::frexp(sk, &ex); m = ex - 1; }
         m = std::max(0, std::min(m, L - 1));
