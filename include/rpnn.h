@@ -271,14 +271,17 @@ rpnn_status rpnn_render_env(rpnn_ctx* ctx, int32_t vol, const rpnn_render_desc* 
  * rows, i.e. 5 GB of BF16 descriptors; otherwise at least 128).  Results do not depend on
  * the chunking.  Errors: RPNN_ERR_ARG for 0 < rows < 128 or rows < 0. */
 rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows);
-/* Fused descriptor + network stages (on by default; Sec. 4.2 and 4.3 in one kernel, no
+/* Fused descriptor + network stages (off by default; Sec. 4.2 and 4.3 in one kernel, no
  * counterpart in the paper, which names descriptor construction as the bottleneck in
- * Sec. 7): a BF16 render (rpnn_render, rpnn_render_env) gathers each shading point's
- * descriptor inside the tensor-core network kernel, so no descriptor rows are written to
- * or read from device memory.  The image is bit for bit that of the unfused stages (the
- * same FP32 descriptor arithmetic and BF16 rounding, the same MMAs in the same order).
- * Renders with blended mip selection (rpnn_set_mip_blend) run unfused.  on == 0 runs the
- * descriptor and network stages as separate kernels.  Never fails for a valid context. */
+ * Sec. 7): with on != 0 a BF16 render (rpnn_render, rpnn_render_env) gathers each shading
+ * point's descriptor inside the tensor-core network kernel, so no descriptor rows are
+ * written to or read from device memory and no descriptor buffer is allocated.  The image
+ * is bit for bit that of the unfused stages (the same FP32 descriptor arithmetic and BF16
+ * rounding, the same MMAs in the same order).  On a GB300 the fused kernel is slower than
+ * the two separate kernels (its gather warps share the SM's registers and issue slots with
+ * the network's epilogue), so it serves renders whose descriptor buffer would not fit.
+ * Renders with blended mip selection (rpnn_set_mip_blend) run unfused.  Never fails for a
+ * valid context. */
 rpnn_status rpnn_set_fused(rpnn_ctx* ctx, int32_t on);
 /* Batched serving (no counterpart in the paper: many clouds, uneven query counts, one
  * frame).  Item i renders volume items[i].vol with items[i].desc into items[i].dev_image

@@ -453,8 +453,8 @@ class Context:
         self._check(self.L.rpnn_set_render_chunk(self.h, rows))
 
     def set_fused(self, on: bool):
-        """BF16 renders gather descriptors inside the network kernel (default) or run the
-        descriptor and network stages separately."""
+        """BF16 renders gather descriptors inside the network kernel (no descriptor buffer)
+        or run the descriptor and network stages separately (the default)."""
         self._check(self.L.rpnn_set_fused(self.h, 1 if on else 0))
 
     def render_batch(self, jobs, images=None, want_counts=False):

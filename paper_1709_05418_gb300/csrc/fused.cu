@@ -57,8 +57,8 @@ enum {
 };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
-constexpr uint32_t OFF_PART = OFF_ABORT + 8;                   // 128 floats
-constexpr uint32_t OFF_LK = (OFF_PART + 128 * 4 + 15) & ~15u;   // LevelK[10]
+constexpr uint32_t OFF_PART = OFF_ABORT + 8;                   // 3 x 128 floats
+constexpr uint32_t OFF_LK = (OFF_PART + 3 * 128 * 4 + 15) & ~15u;   // LevelK[10]
 constexpr uint32_t OFF_OFS = OFF_LK + RPNN_K * sizeof(LevelK);  // float4[NPTS]: stencil offsets
 constexpr uint32_t SMEM_BYTES = OFF_OFS + NPTS * 16 + 64;
 static_assert(OFF_W % 1024 == 0 && OFF_Z % 1024 == 0, "swizzled operand blocks must stay 1024-byte aligned");
@@ -82,33 +82,40 @@ __device__ __forceinline__ float4 stencil_offset(int p) {
                        -1.0f + 0.5f * (float)iz, 0.0f);
 }
 
-// One gather task: descriptor columns p0 .. p0+7 of the lane's shading point at level (g,
-// frame terms A, B, C, U0), rounded to BF16 and packed as one 16-byte unit.  The lookups
-// are branch-free, so the loads of four of them can be in flight together.
-__device__ __forceinline__ uint4 gather_task(const float4* __restrict__ packed, const LevelK& g, uint32_t safe,
-                                             const float4* ofs, int p0, const float (&A)[3], const float (&B)[3],
-                                             const float (&C)[3], const float (&U0)[3], float gamma, bool valid) {
-    // two halves of four lookups each: four loads in flight, their results packed at once
+// Stencil points p0 .. p0+7 of the lane's shading point at level (g; frame terms A, B, C,
+// U0), as BF16 pairs in one 16-byte unit.  cls (stencil_class) selects lookups without
+// range tests, with them, or none; the values are those of lookup() in every case.
+template <int CLS>
+__device__ __forceinline__ uint4 gather_points(const float4* __restrict__ packed, const LevelGeo& g, const float4* ofs,
+                                               int p0, const float (&A)[3], const float (&B)[3], const float (&C)[3],
+                                               const float (&U0)[3]) {
     uint32_t w[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float val[4];
+    for (int h = 0; h < 4; ++h) {
+        float val[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 o = ofs[p0 + 4 * h + i];
+        for (int i = 0; i < 2; ++i) {
+            const float4 o = ofs[p0 + 2 * h + i];
             float u[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) u[a] = __fmaf_rn(o.z, C[a], __fmaf_rn(o.y, B[a], __fmaf_rn(o.x, A[a], U0[a])));
-            val[i] = lookup_nb(packed, g.g0, safe, valid && o.w == 0.0f, u[0], u[1], u[2]);
-            // the level's tail: gamma (w = 1) after its last point, then zeros (w = 2)
-            if (p0 + 8 > RPNN_S && o.w == 1.0f) val[i] = valid ? gamma : 0.0f;
+            val[i] = CLS == kInside ? lookup_in(packed, g, u[0], u[1], u[2]) : lookup(packed, g, u[0], u[1], u[2]);
         }
-        w[2 * h] = pack_bf16x2(val[0], val[1]);
-        w[2 * h + 1] = pack_bf16x2(val[2], val[3]);
+        w[h] = pack_bf16x2(val[0], val[1]);
     }
-    uint4 q;
-    q.x = w[0]; q.y = w[1]; q.z = w[2]; q.w = w[3];
-    return q;
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// The level's tail task (columns 224..231): its last point, gamma, zeros.
+__device__ __forceinline__ uint4 gather_tail(const float4* __restrict__ packed, const LevelGeo& g, const float4* ofs,
+                                             const float (&A)[3], const float (&B)[3], const float (&C)[3],
+                                             const float (&U0)[3], float gamma, bool live) {
+    const float4 o = ofs[RPNN_S - 1];
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = __fmaf_rn(o.z, C[a], __fmaf_rn(o.y, B[a], __fmaf_rn(o.x, A[a], U0[a])));
+    const float last = live ? lookup(packed, g, u[0], u[1], u[2]) : 0.0f;
+    return make_uint4(pack_bf16x2(last, live ? gamma : 0.0f), 0u, 0u, 0u);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constant__ FusedArgs fa) {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
         float* part = reinterpret_cast<float*>(sm + OFF_PART);
         uint32_t tile_iter = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            float dot = 0.0f;
+            float dot = 0.0f, dot1 = 0.0f;       // output-layer quarters: even / odd blocks
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
                 if (lane == 0) ok = tc::mbar_wait(bar(B_ACC), n & 1u, abort_flag);
@@ -244,14 +251,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                     constexpr int K = decltype(kind)::value;
                     float v[32];
                     tc::tmem_ld16x2(taddr, v);
-                    epi_blocks<F, K, 0, 2>(ea, v, dot, l);
+                    epi_blocks<F, K, 0, 2>(ea, v, dot, dot1, l);
                     tc::tmem_ld16x2(taddr + 64u, v);
-                    epi_blocks<F, K, 2, 2>(ea, v, dot, l);
+                    epi_blocks<F, K, 2, 2>(ea, v, dot, dot1, l);
                     tc::tmem_ld16x2(taddr + 128u, v);
-                    epi_blocks<F, K, 4, 2>(ea, v, dot, l);
+                    epi_blocks<F, K, 4, 2>(ea, v, dot, dot1, l);
                     float v1[16];
                     tc::tmem_ld16(taddr + 192u, v1);
-                    epi_blocks<F, K, 6, 1>(ea, v1, dot, l);
+                    epi_blocks<F, K, 6, 1>(ea, v1, dot, dot1, l);
                 };
                 if (l == 0) rounds(std::integral_constant<int, EPI_FIRST>{});
                 else if (l == 21) rounds(std::integral_constant<int, EPI_LAST>{});
@@ -259,14 +266,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                 else rounds(std::integral_constant<int, EPI_PLAIN>{});
             }
             if (!ok) break;
+            // half 1 holds quarters 1 (even blocks) and 3 (odd), half 0 quarters 0 and 2
             if (half) {
                 part[row] = dot;
+                part[2 * TM + row] = dot1;
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(bar(B_PART));
             } else {
                 if (!tc::mbar_wait(bar(B_PART), tile_iter & 1u, abort_flag)) break;
                 const int64_t r = (int64_t)t * TM + row;
-                if (r < Q) a.out[r] = fmaxf(dot + part[row] + __ldg(a.w3 + NP - 1), 0.0f);
+                if (r < Q) a.out[r] = out_from_quarters(dot, part[row], dot1, part[2 * TM + row], __ldg(a.w3 + NP - 1));
             }
             ++tile_iter;
         }
@@ -291,7 +300,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                 for (int c = 0; c < 3; ++c) { x[c] = __ldg(fa.xs + 3 * qs + c); d[c] = __ldg(fa.ds + 3 * qs + c); }
                 const Frame Fr = make_frame(d, fa.wl);
                 const LevelK g = lk[k];
-                const uint32_t safe = geo_safe_record(g.g0);
                 float A[3], B[3], C[3], U0[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -301,6 +309,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                     U0[c] = __fsub_rn(__fmul_rn(x[c], g.s), 0.5f);
                 }
                 const float gamma = Fr.gamma;
+                const int cls = valid ? stencil_class(g.g0, A, B, C, U0) : kOutside;
                 for (int st = 0; st < 4; ++st) {
                     // the ring slot is free once the MMAs of its previous contents completed
                     if (lane == 0) ok = tc::mbar_wait(bar(B_ZEMPTY + sz), pz ^ 1u, abort_flag);
@@ -309,7 +318,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                     unsigned char* slot = sm + OFF_Z + sz * Z_STAGE + row * 64;
                     const int ntask = st < 3 ? 8 : 6;       // stage 3 holds columns 192..239
                     for (int j = wq; j < ntask; j += 4) {
-                        const uint4 q = gather_task(packed, g, safe, ofs, 64 * st + 8 * j, A, B, C, U0, gamma, valid);
+                        const int p0 = 64 * st + 8 * j;
+                        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                        if (p0 + 8 > RPNN_S) {
+                            if (p0 < RPNN_S) q = gather_tail(packed, g.g0, ofs, A, B, C, U0, gamma, valid);
+                        } else if (cls == kInside) {
+                            q = gather_points<kInside>(packed, g.g0, ofs, p0, A, B, C, U0);
+                        } else if (cls == kMixed) {
+                            q = gather_points<kMixed>(packed, g.g0, ofs, p0, A, B, C, U0);
+                        }
                         // column 8j of the stage: 32-column block j / 4, 16-byte unit j % 4
                         *reinterpret_cast<uint4*>(slot + (j >> 2) * BLK_A + (((j & 3) ^ sw) << 4)) = q;
                     }

@@ -201,7 +201,7 @@ struct Ctx {
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
     int64_t chunk_rows = 0;          // descriptor/network chunk of a render (0: kChunkRows)
-    bool fused = true;               // BF16 renders gather descriptors inside the network kernel
+    bool fused = false;              // BF16 renders gather descriptors inside the network kernel
     cudaStream_t capture_stream = nullptr;
     uint64_t epoch = 1;
     // stage timing: one set of 5 events per profiled render

@@ -64,9 +64,8 @@ constexpr uint32_t OFF_X = 0;
 constexpr uint32_t OFF_W = OFF_X + NBLK * BLK_A;               // 57344
 constexpr uint32_t OFF_Z = OFF_W + W_STAGES * W_STAGE;         // 163840
 constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 229376
-constexpr int EPI_THREADS = 256;         // 8 epilogue warps
-constexpr int EPI_WARPS = EPI_THREADS / 32;
-constexpr int NTHREADS = 64 + EPI_THREADS;
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 
 // barrier slots from OFF_BAR, BAR_STRIDE bytes apart; B_DONE completes its phase 0 at
 // setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
@@ -76,8 +75,8 @@ enum {
 };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
-constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 128 floats
-constexpr uint32_t SMEM_BYTES = OFF_PART + 128 * 4 + 64;
+constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 3 x 128 floats
+constexpr uint32_t SMEM_BYTES = OFF_PART + 3 * 128 * 4 + 64;
 static_assert(OFF_W % 1024 == 0 && OFF_Z % 1024 == 0 && W_STAGE % 1024 == 0 && Z_STAGE % 1024 == 0,
               "swizzled operand blocks must stay 1024-byte aligned");
 static_assert(SMEM_BYTES <= 232448, "shared memory over the per-block limit");
@@ -223,7 +222,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // 8 warps: warp w reads tensor-memory lanes 32*(w%4) .. +31 (its 32 query rows)
         // and, in every 32-column block b, the columns 32b + 16*half .. +15 (half = 0 for
         // warps 2-5, 1 for warps 6-9).  All 7 chunks are loaded in one round trip; each
-        // finished block is published on its own barrier so the next layer's MMAs can
+        // finished block pair is published on its own barrier so the next layer's MMAs can
         // start on it while later blocks are still being written.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
@@ -231,10 +230,10 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         const int sw = (row >> 1) & 3;
         uint32_t n = 0;
         unsigned char* Xsm = sm + OFF_X;
-        float* part = reinterpret_cast<float*>(sm + OFF_PART);     // [TM] partial dots
+        float* part = reinterpret_cast<float*>(sm + OFF_PART);     // [3][TM] partial dots
         uint32_t tile_iter = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            float dot = 0.0f;
+            float dot = 0.0f, dot1 = 0.0f;      // output-layer quarters: even / odd blocks
             bool ok = true;
             for (int l = 0; l < NLAYERS; ++l, ++n) {
                 // one poller per warp: lane 0 waits, the warp follows
@@ -247,22 +246,24 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 tc::tmem_ld16x7(taddr, v);
                 const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, a.scale, taddr};
                 // one straight-line routine per layer kind
-                if (l == 0) epi_layer<F, EPI_FIRST>(ea, v, dot, l);
-                else if (l == 21) epi_layer<F, EPI_LAST>(ea, v, dot, l);
-                else if (layer_keeps_o(l)) epi_layer<F, EPI_KEEP>(ea, v, dot, l);
-                else epi_layer<F, EPI_PLAIN>(ea, v, dot, l);
+                if (l == 0) epi_layer<F, EPI_FIRST>(ea, v, dot, dot1, l);
+                else if (l == 21) epi_layer<F, EPI_LAST>(ea, v, dot, dot1, l);
+                else if (layer_keeps_o(l)) epi_layer<F, EPI_KEEP>(ea, v, dot, dot1, l);
+                else epi_layer<F, EPI_PLAIN>(ea, v, dot, dot1, l);
             }
             if (!ok) break;
-            // combine the two column halves of the output layer's dot product: the
-            // second half publishes its partial sums, the first half adds them (bounded wait)
+            // combine the column quarters' partial dot products of the output layer: half 1
+            // holds quarters 1 (even blocks) and 3 (odd), half 0 quarters 0 and 2 and adds
+            // them in the fixed order (bounded wait)
             if (half) {
                 part[row] = dot;
+                part[2 * TM + row] = dot1;
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(bar(B_PART));
             } else {
                 if (!tc::mbar_wait(bar(B_PART), tile_iter & 1u, abort_flag)) break;
                 const int64_t r = (int64_t)t * TM + row;
-                if (r < Q) a.out[r] = fmaxf(dot + part[row] + __ldg(a.w3 + NP - 1), 0.0f);
+                if (r < Q) a.out[r] = out_from_quarters(dot, part[row], dot1, part[2 * TM + row], __ldg(a.w3 + NP - 1));
             }
             ++tile_iter;
         }

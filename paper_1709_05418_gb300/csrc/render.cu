@@ -135,70 +135,121 @@ __global__ void k_composite(const float* __restrict__ sample_val, int64_t npix, 
     }
 }
 
-// Training records (Sec. 5.1); one thread per record.
+// Kahan-compensated FP32 running sum (hi + lo carries about twice FP32's precision)
+struct KahanF {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, lo);
+        const float t = __fadd_rn(hi, y);
+        lo = __fsub_rn(__fsub_rn(t, hi), y);
+        hi = t;
+    }
+    // the running sum plus a (small) partial sum, as one float
+    __device__ __forceinline__ float with(float v) const { return __fadd_rn(hi, __fsub_rn(v, lo)); }
+};
+
+// inclusive prefix sum over the warp's lanes
+__device__ __forceinline__ float warp_scan(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Training records (Sec. 5.1); one warp per record.  Lane 0 samples the record (direction,
+// origin on the bounding sphere's cross-section, free flight by delta tracking with
+// retries, light direction) and the warp traces its label paths 32 at a time, path j on
+// lane j % 32 with path j's own random stream.  After each round the stopping rule is
+// evaluated at every path count of the round in order -- n >= n_min and
+// 1.96 s / sqrt(n) <= rel_ci * mean -- from FP32 prefix sums of L and L^2 over the round
+// added to Kahan-compensated running totals; the first count that meets it (or n_max)
+// ends the record and its label is the mean of its first n paths.
 __global__ void __launch_bounds__(128)
 k_records(const VolumeView v, int64_t first, int64_t n, uint64_t seed, float rel_ci, int n_min,
           int n_max, float* __restrict__ xo, float* __restrict__ dout, float* __restrict__ wlo,
           float* __restrict__ label, int* __restrict__ npaths, uint32_t* status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t rec = (uint32_t)(first + i);
-    const float ext[3] = {v.ext[0], v.ext[1], v.ext[2]};
-    const float3 C = f3(0.5f * ext[0], 0.5f * ext[1], 0.5f * ext[2]);
-    const float R = 0.5f * sqrtf(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
-    float3 x = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
-    bool found = false;
-    for (uint32_t att = 0; att < (uint32_t)kRecordAttempts && !found; ++att) {
-        const float4 xi = make_rng(seed, rec, att, kDomRecord).draw(0);
-        const float cz = 1.0f - 2.0f * xi.x;
-        float sp, cp;
-        sincosf(2.0f * kPi * xi.y, &sp, &cp);
-        const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
-        d = f3(sz * cp, sz * sp, cz);
-        float3 b1, b2;
-        duff_basis(d, b1, b2);
-        const float rr = R * sqrtf(xi.z);
-        float s2, c2;
-        sincosf(2.0f * kPi * xi.w, &s2, &c2);
-        const float3 o = C + (rr * c2) * b1 + (rr * s2) * b2 + (-2.0f * R) * d;
-        uint32_t ctr = 0;
-        const int h = delta_track(v, o, d, make_rng(seed, rec, att, kDomRecTrack), ctr, x);
-        if (h < 0) raise_status(status, kStatIterLimit);
-        found = h == 1;
-    }
-    float3 wl;
-    {
-        const float4 xi = make_rng(seed, rec, 0, kDomLight).draw(0);
-        const float cz = 1.0f - 2.0f * xi.x;
-        float sp, cp;
-        sincosf(2.0f * kPi * xi.y, &sp, &cp);
-        const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
-        wl = f3(sz * cp, sz * sp, cz);
-    }
-    double mu = 0.0, m2 = 0.0;
-    int j = 0;
-    bool capped = false;
-    if (found) {
-        for (j = 0; j < n_max;) {
-            const float L = path_Li(v, x, d, wl, 1.0f, make_rng(seed, rec, (uint32_t)j, kDomLabel), capped);
-            const double delta = (double)L - mu;
-            mu += delta / (double)(j + 1);
-            m2 += delta * ((double)L - mu);
-            ++j;
-            if (j >= n_min && j > 1) {
-                const double hw = 1.96 * sqrt(m2 / (double)(j - 1) / (double)j);
-                if (mu > 0.0 && hw <= (double)rel_ci * mu) break;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
+        const uint32_t rec = (uint32_t)(first + i);
+        float3 x = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
+        int found = 0;
+        if (lane == 0) {
+            const float ext[3] = {v.ext[0], v.ext[1], v.ext[2]};
+            const float3 C = f3(0.5f * ext[0], 0.5f * ext[1], 0.5f * ext[2]);
+            const float R = 0.5f * sqrtf(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
+            for (uint32_t att = 0; att < (uint32_t)kRecordAttempts && !found; ++att) {
+                const float4 xi = make_rng(seed, rec, att, kDomRecord).draw(0);
+                const float cz = 1.0f - 2.0f * xi.x;
+                float sp, cp;
+                sincosf(2.0f * kPi * xi.y, &sp, &cp);
+                const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
+                d = f3(sz * cp, sz * sp, cz);
+                float3 b1, b2;
+                duff_basis(d, b1, b2);
+                const float rr = R * sqrtf(xi.z);
+                float s2, c2;
+                sincosf(2.0f * kPi * xi.w, &s2, &c2);
+                const float3 o = C + (rr * c2) * b1 + (rr * s2) * b2 + (-2.0f * R) * d;
+                uint32_t ctr = 0;
+                const int h = delta_track(v, o, d, make_rng(seed, rec, att, kDomRecTrack), ctr, x);
+                if (h < 0) raise_status(status, kStatIterLimit);
+                found = h == 1;
             }
         }
-    } else {
-        raise_status(status, kStatIterLimit);
+        found = __shfl_sync(0xffffffffu, found, 0);
+        x = f3(__shfl_sync(0xffffffffu, x.x, 0), __shfl_sync(0xffffffffu, x.y, 0), __shfl_sync(0xffffffffu, x.z, 0));
+        d = f3(__shfl_sync(0xffffffffu, d.x, 0), __shfl_sync(0xffffffffu, d.y, 0), __shfl_sync(0xffffffffu, d.z, 0));
+        float3 wl;
+        {
+            const float4 xi = make_rng(seed, rec, 0, kDomLight).draw(0);
+            const float cz = 1.0f - 2.0f * xi.x;
+            float sp, cp;
+            sincosf(2.0f * kPi * xi.y, &sp, &cp);
+            const float sz = sqrtf(fmaxf(0.0f, 1.0f - cz * cz));
+            wl = f3(sz * cp, sz * sp, cz);
+        }
+        float mean = 0.0f;
+        int np = 0;
+        bool capped = false;
+        if (found) {
+            KahanF S, Q;                               // running sums of L and L^2
+            for (int base = 0; base < n_max; base += 32) {
+                const int j = base + lane;
+                float L = 0.0f;
+                if (j < n_max) L = path_Li(v, x, d, wl, 1.0f, make_rng(seed, rec, (uint32_t)j, kDomLabel), capped);
+                const float pS = warp_scan(L, lane), pQ = warp_scan(L * L, lane);
+                const float cnt = (float)(j + 1);
+                const float s_j = S.with(pS), q_j = Q.with(pQ);
+                const float m_j = s_j / cnt;
+                const float var = fmaxf(q_j - s_j * m_j, 0.0f) / fmaxf(cnt - 1.0f, 1.0f);
+                const float hw = 1.96f * sqrtf(var / cnt);
+                const bool stop = j < n_max && ((j + 1 >= n_min && j > 0 && m_j > 0.0f && hw <= rel_ci * m_j) ||
+                                                j + 1 == n_max);
+                const uint32_t hit = __ballot_sync(0xffffffffu, stop);
+                if (hit) {
+                    const int f = __ffs(hit) - 1;
+                    mean = __shfl_sync(0xffffffffu, m_j, f);
+                    np = base + f + 1;
+                    break;
+                }
+                S.add(__shfl_sync(0xffffffffu, pS, 31));
+                Q.add(__shfl_sync(0xffffffffu, pQ, 31));
+            }
+        } else if (lane == 0) {
+            raise_status(status, kStatIterLimit);
+        }
+        if (__any_sync(0xffffffffu, capped) && lane == 0) raise_status(status, kStatIterLimit);
+        if (lane == 0) {
+            xo[3 * i] = x.x; xo[3 * i + 1] = x.y; xo[3 * i + 2] = x.z;
+            dout[3 * i] = d.x; dout[3 * i + 1] = d.y; dout[3 * i + 2] = d.z;
+            wlo[3 * i] = wl.x; wlo[3 * i + 1] = wl.y; wlo[3 * i + 2] = wl.z;
+            label[i] = mean;
+            npaths[i] = np;
+        }
     }
-    if (capped) raise_status(status, kStatIterLimit);
-    xo[3 * i] = x.x; xo[3 * i + 1] = x.y; xo[3 * i + 2] = x.z;
-    dout[3 * i] = d.x; dout[3 * i + 1] = d.y; dout[3 * i + 2] = d.z;
-    wlo[3 * i] = wl.x; wlo[3 * i + 1] = wl.y; wlo[3 * i + 2] = wl.z;
-    label[i] = (float)mu;
-    npaths[i] = j;
 }
 
 RenderArgs make_args(const rpnn_render_desc& rd) {
@@ -306,7 +357,8 @@ rpnn_status launch_chunk_counts(Ctx& c, const int* count, int64_t rows, int n, i
 rpnn_status launch_records(Ctx& c, const VolumeView& vv, int64_t first, int64_t n, uint64_t seed,
                            float rel_ci, int n_min, int n_max, float* x, float* d, float* wl,
                            float* label, int* npaths, cudaStream_t s) {
-    const int64_t blocks = (n + 127) / 128;
+    // one warp per record, four per block; at most a few waves of blocks (grid-stride)
+    const int64_t blocks = std::min<int64_t>((n + 3) / 4, (int64_t)c.num_sms * 16);
     k_records<<<(unsigned)blocks, 128, 0, s>>>(vv, first, n, seed, rel_ci, n_min, n_max, x, d, wl,
                                                label, npaths, c.status.as<uint32_t>());
     RPNN_CHECK_LAUNCH();

@@ -177,104 +177,123 @@ struct EpiArgs {
 // FP8: every kind dequantises, adds the FP32 bias and quantises its output (see the top).
 // Blocks B0 .. B0 + NB - 1 of the layer, whose accumulator chunks the caller has loaded
 // into v (chunk B0 + i at v[16 i ..]); epi_layer is the whole layer in one call.
-template <class F, int KIND, int B0, int NB>
-__device__ __forceinline__ void epi_blocks(const EpiArgs& e, float (&v)[NB * 16], float& dot, int l) {
-    float u = 1.0f, qs = 1.0f, ku = 1.0f;
+// One 16-column chunk of one layer for the warp's 32 rows: columns 32 b + 16 half .. +15,
+// accumulator values in w; u, qs, ku are the FP8 scales (1 for BF16).
+template <class F, int KIND>
+__device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, float* w, float& dot, float u, float qs,
+                                          float ku) {
+    const int c0 = 32 * b + 16 * half;
+    // accumulator columns 200..207 are exactly zero (zero weight rows and zero start
+    // values), so ReLU needs no column mask
+    if (c0 >= NP) return;
     if (F::FP8) {
-        const float4 sc = __ldg(reinterpret_cast<const float4*>(e.scale) + l);
-        u = sc.x; qs = sc.y; ku = sc.z;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] *= u;
     }
+    if (F::FP8 || KIND == EPI_FIRST) {
+        const float4* b4 = reinterpret_cast<const float4*>(e.bias + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 bb = __ldg(b4 + q);
+            w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
+        }
+    }
+    if (KIND == EPI_KEEP || KIND == EPI_LAST) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
+    }
+    if (KIND == EPI_KEEP && !F::FP8) tc::tmem_st16(e.taddr + 32u * b + 16u * (half - e.half), w);
+    if (KIND == EPI_LAST) {
+        const float4* w4 = reinterpret_cast<const float4*>(e.w3 + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 ww = __ldg(w4 + q);
+            dot = fmaf(w[4 * q], ww.x, dot); dot = fmaf(w[4 * q + 1], ww.y, dot);
+            dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
+        }
+    } else if (F::FP8) {
+        // 16 E4M3 bytes: byte c of the row's activation at 64-byte block c / 64,
+        // 16-byte unit (c % 64) / 16, swizzled like the BF16 layout
+        uint4 p;
+        p.x = pack_relu_e4m3x4(w[0] * qs, w[1] * qs, w[2] * qs, w[3] * qs);
+        p.y = pack_relu_e4m3x4(w[4] * qs, w[5] * qs, w[6] * qs, w[7] * qs);
+        p.z = pack_relu_e4m3x4(w[8] * qs, w[9] * qs, w[10] * qs, w[11] * qs);
+        p.w = pack_relu_e4m3x4(w[12] * qs, w[13] * qs, w[14] * qs, w[15] * qs);
+        unsigned char* rb = e.X + (b >> 1) * BLK_A + e.row * 64;
+        *reinterpret_cast<uint4*>(rb + (((2 * (b & 1) + half) ^ e.sw) << 4)) = p;
+        if (KIND == EPI_KEEP) {
+            // o^k in the units of the next second layer's accumulator
+#pragma unroll
+            for (int i = 0; i < 16; ++i) w[i] *= ku;
+            tc::tmem_st16(e.taddr + 32u * b + 16u * (half - e.half), w);
+        }
+    } else {
+        // BF16 pairs (ReLU folded into the conversion unless already applied)
+        uint4 p0, p1;
+        uint32_t* u0 = reinterpret_cast<uint32_t*>(&p0);
+        uint32_t* u1 = reinterpret_cast<uint32_t*>(&p1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (KIND == EPI_KEEP) {
+                u0[q] = pack_bf16x2(w[2 * q], w[2 * q + 1]);
+                u1[q] = pack_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
+            } else {
+                u0[q] = pack_relu_bf16x2(w[2 * q], w[2 * q + 1]);
+                u1[q] = pack_relu_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
+            }
+        }
+        // column 200 carries the constant 1 that multiplies the next layer's bias
+        if (c0 == 192) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
+        // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
+        unsigned char* rb = e.X + b * BLK_A + e.row * 64;
+        *reinterpret_cast<uint4*>(rb + (((2 * half) ^ e.sw) << 4)) = p0;
+        *reinterpret_cast<uint4*>(rb + (((2 * half + 1) ^ e.sw) << 4)) = p1;
+    }
+}
+
+// Publication p of a layer (activation bytes [128 p, 128 p + 128)) after the warp's stores:
+// make them visible to the tensor core and, before the last one, complete the accumulator
+// write-back (the MMAs that start from it wait for the last publication).
+template <int KIND>
+__device__ __forceinline__ void epi_publish(const EpiArgs& e, int p, bool last) {
+    tc::fence_proxy_async_smem();
+    if (last && KIND == EPI_KEEP) tc::tmem_wait_st();
+    tc::tc_fence_before();
+    __syncwarp();
+    if (e.lane == 0) tc::mbar_arrive(e.blk_bar + BAR_STRIDE * (uint32_t)p);
+}
+
+template <class F> __device__ __forceinline__ float4 epi_scales(const EpiArgs& e, int l) {
+    if (!F::FP8) return make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+    return __ldg(reinterpret_cast<const float4*>(e.scale) + l);
+}
+
+// Blocks B0 .. B0 + NB - 1 of the layer, whose accumulator chunks (column half e.half of
+// each 32-column block) the caller has loaded into v (chunk B0 + i at v[16 i ..]),
+// published as each 128-byte range of the activation is complete; epi_layer is the whole
+// layer in one call.  The output layer's dot product runs as two FMA chains, over the
+// even blocks (dot0) and the odd blocks (dot1), the column quarters of the sum below.
+template <class F, int KIND, int B0, int NB>
+__device__ __forceinline__ void epi_blocks(const EpiArgs& e, float (&v)[NB * 16], float& dot0, float& dot1, int l) {
+    const float4 sc = epi_scales<F>(e, l);
 #pragma unroll
     for (int b = B0; b < B0 + NB; ++b) {
-        const int c0 = 32 * b + 16 * e.half;
-        float* w = v + 16 * (b - B0);
-        // accumulator columns 200..207 are exactly zero (zero weight rows and zero start
-        // values), so ReLU needs no column mask
-        if (c0 < NP) {
-            if (F::FP8) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) w[i] *= u;
-            }
-            if (F::FP8 || KIND == EPI_FIRST) {
-                const float4* b4 = reinterpret_cast<const float4*>(e.bias + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 bb = __ldg(b4 + q);
-                    w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
-                }
-            }
-            if (KIND == EPI_KEEP || KIND == EPI_LAST) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
-            }
-            if (KIND == EPI_KEEP && !F::FP8) tc::tmem_st16(e.taddr + 32u * b, w);
-            if (KIND == EPI_LAST) {
-                const float4* w4 = reinterpret_cast<const float4*>(e.w3 + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 ww = __ldg(w4 + q);
-                    dot = fmaf(w[4 * q], ww.x, dot); dot = fmaf(w[4 * q + 1], ww.y, dot);
-                    dot = fmaf(w[4 * q + 2], ww.z, dot); dot = fmaf(w[4 * q + 3], ww.w, dot);
-                }
-            } else if (F::FP8) {
-                // 16 E4M3 bytes: byte c of the row's activation at 64-byte block c / 64,
-                // 16-byte unit (c % 64) / 16, swizzled like the BF16 layout
-                uint4 p;
-                p.x = pack_relu_e4m3x4(w[0] * qs, w[1] * qs, w[2] * qs, w[3] * qs);
-                p.y = pack_relu_e4m3x4(w[4] * qs, w[5] * qs, w[6] * qs, w[7] * qs);
-                p.z = pack_relu_e4m3x4(w[8] * qs, w[9] * qs, w[10] * qs, w[11] * qs);
-                p.w = pack_relu_e4m3x4(w[12] * qs, w[13] * qs, w[14] * qs, w[15] * qs);
-                unsigned char* rb = e.X + (b >> 1) * BLK_A + e.row * 64;
-                *reinterpret_cast<uint4*>(rb + (((2 * (b & 1) + e.half) ^ e.sw) << 4)) = p;
-                if (KIND == EPI_KEEP) {
-                    // o^k in the units of the next second layer's accumulator
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) w[i] *= ku;
-                    tc::tmem_st16(e.taddr + 32u * b, w);
-                }
-            } else {
-                // BF16 pairs (ReLU folded into the conversion unless already applied)
-                uint4 p0, p1;
-                uint32_t* u0 = reinterpret_cast<uint32_t*>(&p0);
-                uint32_t* u1 = reinterpret_cast<uint32_t*>(&p1);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (KIND == EPI_KEEP) {
-                        u0[q] = pack_bf16x2(w[2 * q], w[2 * q + 1]);
-                        u1[q] = pack_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
-                    } else {
-                        u0[q] = pack_relu_bf16x2(w[2 * q], w[2 * q + 1]);
-                        u1[q] = pack_relu_bf16x2(w[8 + 2 * q], w[9 + 2 * q]);
-                    }
-                }
-                // column 200 carries the constant 1 that multiplies the next layer's bias
-                if (b == NBLK - 1) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
-                // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
-                unsigned char* rb = e.X + b * BLK_A + e.row * 64;
-                *reinterpret_cast<uint4*>(rb + (((2 * e.half) ^ e.sw) << 4)) = p0;
-                *reinterpret_cast<uint4*>(rb + (((2 * e.half + 1) ^ e.sw) << 4)) = p1;
-            }
-        }
-        // publication p covers activation bytes [128 p, 128 p + 128): after chunk b when
-        // the chunk ends such a range, or is the last
-        constexpr int CB = 32 * F::EB;                    // activation bytes of one chunk
-        if (((b + 1) * CB) % SKB == 0 || b == NBLK - 1) {
-            const int p = (b * CB) / SKB;
-            // make the stores visible to the tensor core, and (last chunk) complete the
-            // accumulator write-back first, since the MMAs that start from it wait for the
-            // last publication
-            tc::fence_proxy_async_smem();
-            if (b == NBLK - 1 && KIND == EPI_KEEP) tc::tmem_wait_st();
-            tc::tc_fence_before();
-            __syncwarp();
-            if (e.lane == 0) tc::mbar_arrive(e.blk_bar + BAR_STRIDE * (uint32_t)p);
-        }
+        epi_chunk<F, KIND>(e, b, e.half, v + 16 * (b - B0), (b & 1) ? dot1 : dot0, sc.x, sc.y, sc.z);
+        constexpr int CB = 32 * F::EB;                    // activation bytes of one block
+        if (((b + 1) * CB) % SKB == 0 || b == NBLK - 1) epi_publish<KIND>(e, (b * CB) / SKB, b == NBLK - 1);
     }
 }
 
 template <class F, int KIND>
-__device__ __forceinline__ void epi_layer(const EpiArgs& e, float (&v)[NBLK * 16], float& dot, int l) {
-    epi_blocks<F, KIND, 0, NBLK>(e, v, dot, l);
+__device__ __forceinline__ void epi_layer(const EpiArgs& e, float (&v)[NBLK * 16], float& dot0, float& dot1, int l) {
+    epi_blocks<F, KIND, 0, NBLK>(e, v, dot0, dot1, l);
+}
+
+// The prediction g = relu(T3 . o12 + bT3) from the column quarters' partial dot products:
+// quarter q = 2 (block parity) + (half) holds the FMA chain over its 16-column chunks in
+// increasing block order; g = relu(((q0 + q1) + (q2 + q3)) + bT3) in both network kernels.
+__device__ __forceinline__ float out_from_quarters(float q0, float q1, float q2, float q3, float b) {
+    return fmaxf(__fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, q3)), b), 0.0f);
 }
 
 // Byte layout of a weight image: per layer its 64-byte blocks (208 rows each), then the

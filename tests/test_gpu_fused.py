@@ -27,12 +27,12 @@ def env():
 
 
 def _both(api, ctx, fn):
-    ctx.set_fused(False)
+    ref = fn().clone()
+    ctx.set_fused(True)
     try:
-        ref = fn().clone()
+        got = fn().clone()
     finally:
-        ctx.set_fused(True)
-    got = fn().clone()
+        ctx.set_fused(False)
     ctx.sync_status()
     return got, ref
 
@@ -91,8 +91,12 @@ def test_fused_render_matches_oracle(env):
     vol = ctx.load_volume(torch.from_numpy(dens).cuda())
     ctx.build_mips(vol)
     cam = W.camera(dens.shape, 40, 40, spp=1, seed=7, light_seed=8)
-    got = ctx.render(vol, cam, precision=api.BF16).cpu().numpy().ravel().astype(np.float64)
-    ctx.sync_status()
+    ctx.set_fused(True)
+    try:
+        got = ctx.render(vol, cam, precision=api.BF16).cpu().numpy().ravel().astype(np.float64)
+        ctx.sync_status()
+    finally:
+        ctx.set_fused(False)
     ref = oracle.Volume(dens).render_pixels(cam, np.arange(got.size), params=params.astype(np.float64))
     assert float(np.linalg.norm(got - ref) / np.linalg.norm(ref)) <= 1e-2
     scale = np.maximum(np.abs(ref), np.median(np.abs(ref[ref > 0])))

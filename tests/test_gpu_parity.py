@@ -409,6 +409,29 @@ def test_records_match_oracle(ctx, blob_vol, blob_orc):
     assert np.all(npaths >= 32) and np.all(npaths <= 2048)
 
 
+def test_records_stopping_rule_counts(ctx, blob_vol, blob_orc):
+    """The label rule is evaluated at every path count, not only at the end of the warp's
+    rounds of 32 paths: a loose rule stops each record with a positive label at n_min, an
+    unreachable one at n_max (neither a multiple of 32), and the label is then the mean of
+    exactly that many paths of the oracle's streams (within the paths' rounding)."""
+    n = 24
+    _, _, _, lab, npaths = [t.cpu().numpy() for t in
+                            ctx.gen_records(blob_vol, 0, n, 91, rel_ci=50.0, n_min=37, n_max=300)]
+    ctx.sync_status()
+    assert np.all(npaths[lab > 0] == 37)
+    _, _, _, lab2, np2 = [t.cpu().numpy() for t in
+                          ctx.gen_records(blob_vol, 0, n, 91, rel_ci=1e-7, n_min=5, n_max=70)]
+    ctx.sync_status()
+    assert np.all(np2[lab2 > 0] == 70)
+    # a path whose decision flips on an FP32 rounding (about 1 in 5,000 in the path-render
+    # test) changes its record's label, so one of the six may differ
+    close = 0
+    for i in range(6):
+        r = blob_orc.gen_record(91, i, rel_ci=1e-7, n_min=5, n_max=70)
+        close += abs(lab2[i] - r["label"]) <= 1e-3 * max(r["label"], 1e-6)
+    assert close >= 5, close
+
+
 # ---------------------------------------------------------------- full size, sampled
 @pytest.mark.slow
 def test_full_size_render_sampled_pixels(ctx, api, params):
