@@ -515,6 +515,62 @@ def run_train(args, ws, rank, local):
     ctx.close()
 
 
+RECORDS_WORKLOAD = ("training-record generation (Sec. 5.1): 32 fBm clouds (seeds 100-131, edges drawn from "
+                    "{128, 160, 192, 224, 256}, FP32 density), records per cloud as `config.records_per_cloud`: "
+                    "uniform direction, origin on the bounding-sphere disk, free flight by delta tracking, uniform "
+                    "light; L_i path traced until the 95% half-width is within 2% of the mean (64 to 65,536 paths)")
+
+
+def run_records(args, ws, rank, local):
+    """Label generation at the training configuration's cloud mix and the paper's stopping
+    rule: records/s, paths/s and the fraction of labels that met the rule before the cap."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_05418_gb300 import api
+    from paper_1709_05418_gb300 import workloads as W
+    rng = np.random.default_rng(2025)
+    edges = rng.choice([128, 160, 192, 224, 256], size=32)
+    ctx = api.Context()
+    per = args.records_per_cloud
+    n_max = args.records_max_paths
+    gen_ms, nps = 0.0, []
+    for i, edge in enumerate(edges):
+        vol = ctx.load_volume(torch.from_numpy(W.fbm_cloud(int(edge), seed=100 + i, device=dev)).to(dev))
+        ctx.build_mips(vol)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, _, _, lab, npa = ctx.gen_records(vol, 0, per, 1000 + i, rel_ci=0.02, n_min=64, n_max=n_max)
+        e1.record()
+        torch.cuda.synchronize()
+        gen_ms += e0.elapsed_time(e1)
+        nps.append(npa)
+        ctx.sync_status()
+    npa = torch.cat(nps).double()
+    nrec = int(npa.numel())
+    rate = nrec / (gen_ms / 1e3)
+    met = float((npa < n_max).double().mean())
+    line = {
+        "metric": "RPNN training records/s on 1 GB300 (labels path traced until +-2% at 95% confidence)",
+        "value": rate, "unit": "records/s", "n_gpus": ws, "steps": 1, "warmup": 0,
+        "ms_per_step": gen_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": RECORDS_WORKLOAD, "records_per_cloud": per, "records": nrec,
+                   "edges": [int(e) for e in edges]},
+        "paths_per_s": float(npa.sum()) / (gen_ms / 1e3),
+        "mean_paths_per_record": float(npa.mean()),
+        "median_paths_per_record": float(npa.median()),
+        "met_rule_fraction": met,
+        "capped_at_max_paths": int((npa >= n_max).sum()),
+        "seconds_for_2M_records": 2e6 / rate,
+        "gpu_launches": 32,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 ENV_WORKLOAD = ("environment lighting: the single-cloud render (256^3 fBm, 512x512, 1 spp) under a sun and "
                 "8 sky directions (seeded, upper hemisphere) standing in for a sun-sky model; every shading "
                 "point gets one next-event estimate and one BF16 network prediction per direction")
@@ -802,11 +858,17 @@ def main():
                     help="path cap of the records' stopping rule in the training workload")
     ap.add_argument("--cpu-rows", type=int, default=256,
                     help="records in the FP64 oracle's training step (training workload)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "large", "train", "env", "ttuv"],
+    ap.add_argument("--records-per-cloud", type=int, default=2048,
+                    help="records per cloud of the record-generation workload (32 clouds)")
+    ap.add_argument("--records-max-paths", type=int, default=65536,
+                    help="path cap of the record-generation workload's stopping rule")
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "large", "train", "records", "env", "ttuv"],
                     help="single: the 256^3 / 512x512 render (default); batch: 16 clouds in one batched "
                          "call; large: 1024^3 FP16 cloud at 1920x1080x4")
     ap.add_argument("--profile-only", action="store_true",
-                    help="one BF16, one FP32 and one FP8 render of the workload, no timing (for ncu captures)")
+                    help="one BF16, one FP32, one FP8 and one fused BF16 render of the workload, no timing "
+                         "(for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -822,6 +884,9 @@ def main():
         return
     if args.workload == "train":
         run_train(args, ws, rank, local)
+        return
+    if args.workload == "records":
+        run_records(args, ws, rank, local)
         return
     if args.workload == "env":
         run_env(args, ws, rank, local)
@@ -862,6 +927,9 @@ def main():
         wl = torch.as_tensor(np.asarray(cam["light_dir"], np.float32), device=dev)
         ctx.calibrate_fp8(ctx.extract_descriptors(vol, qx[sel].contiguous(), qd[sel].contiguous(), wl))
         ctx.render(vol, cam, precision=api.FP8)
+        ctx.set_fused(True)                 # the descriptor gather fused into the network
+        ctx.render(vol, cam, precision=api.BF16)
+        ctx.set_fused(False)
         ctx.sync_status()
         torch.cuda.synchronize()
         ctx.close()

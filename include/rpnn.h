@@ -352,6 +352,17 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dt
                             int32_t batch, const rpnn_adam_cfg* adam, int64_t step,
                             float* dev_params, float* dev_m, float* dev_v, double* dev_loss,
                             void* stream);
+/* Captured training steps (on by default; no counterpart in the paper): a step's ~100
+ * launches are the same from step to step, so the first rpnn_train_step of a configuration
+ * (batch, descriptor dtype, training precision, the parameter / moment / loss pointers,
+ * the Adam settings, the autotuner's table) runs them directly, the second captures them
+ * as a CUDA graph on a library-owned stream, and later steps copy the minibatch into
+ * context-owned staging buffers and replay the graph (one launch instead of ~100).  The
+ * results are those of the direct steps bit for bit.  Any device allocation by the
+ * context, a weight or volume change, or a tuning change makes the next step direct and
+ * the one after re-capture.  on == 0 runs every step directly and frees the graph. */
+rpnn_status rpnn_set_train_graphs(rpnn_ctx* ctx, int32_t on);
+
 /* ---- plain MLP of the architecture comparison (Sec. 7, Fig. 10) -------------------------
  * The paper compares its progressive network with "all-at-once" MLPs that take the whole
  * descriptor in the first layer: shallow-wide (hidden widths 400, 400, 200, 200, 200) and

@@ -120,6 +120,7 @@ def load():
                                 C.POINTER(i64), _vp],
             "rpnn_set_render_chunk": [_vp, i64],
             "rpnn_set_fused": [_vp, i32],
+            "rpnn_set_train_graphs": [_vp, i32],
             "rpnn_calibrate_fp8": [_vp, _vp, i64, _vp],
             "rpnn_trace_primary": [_vp, i32, C.POINTER(RenderDesc), _vp, _vp, _vp, _vp, _vp],
             "rpnn_gen_records": [_vp, i32, i64, i64, u64, f32, i32, i32, _vp, _vp, _vp, _vp,
@@ -451,6 +452,11 @@ class Context:
 
     def set_render_chunk(self, rows: int):
         self._check(self.L.rpnn_set_render_chunk(self.h, rows))
+
+    def set_train_graphs(self, on: bool):
+        """Capture the training step as a CUDA graph after its first run (default) or run
+        every step's launches directly."""
+        self._check(self.L.rpnn_set_train_graphs(self.h, 1 if on else 0))
 
     def set_fused(self, on: bool):
         """BF16 renders gather descriptors inside the network kernel (no descriptor buffer)

@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI declared in include/rpnn.h: argument checks, ownership, and the
 // sequencing of the kernels of each call.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -19,8 +20,12 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 
+static std::atomic<uint64_t> g_devbuf_generation{1};
+uint64_t devbuf_generation() { return g_devbuf_generation.load(); }
+
 rpnn_status DevBuf::reserve(size_t n) {
     if (n <= bytes) return RPNN_OK;
+    ++g_devbuf_generation;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -37,6 +42,7 @@ rpnn_status DevBuf::reserve(size_t n) {
 }
 
 void DevBuf::release() {
+    if (p) ++g_devbuf_generation;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -139,6 +145,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
     batch_release(*c);
+    train_graph_release(*c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     delete c;
@@ -799,6 +806,7 @@ rpnn_status rpnn_set_autotune_table(rpnn_ctx* ctx, const rpnn_tune_entry* entrie
             if (e.first == kc.first) { e.second = kc.second; found = true; }
         if (!found) c->tuner.table.push_back(kc);
     }
+    ++c->tuner.version;
     return RPNN_OK;
 }
 
@@ -814,7 +822,9 @@ rpnn_status rpnn_set_train_precision(rpnn_ctx* ctx, int32_t precision) {
 
 rpnn_status rpnn_set_autotune(rpnn_ctx* ctx, int32_t on) {
     CHECK_CTX(ctx);
-    reinterpret_cast<Ctx*>(ctx)->tuner.enabled = on != 0;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->tuner.enabled != (on != 0)) ++c->tuner.version;
+    c->tuner.enabled = on != 0;
     return RPNN_OK;
 }
 
@@ -893,6 +903,82 @@ rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_
     return train_backward(*c, d32, q, dev_dout, dev_dparams, s);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The arithmetic of one training step on q descriptor rows: forward, log-MSE loss,
+// backward, Adam, weight copies.  Adam's bias corrections come from step (host) or, when
+// cc is not null, from device memory (the captured form).
+rpnn_status train_step_body(Ctx& c, const void* desc, int32_t dtype, const float* target, int64_t q,
+                            const rpnn_adam_cfg& adam, int64_t step, const float* cc, float* params, float* m,
+                            float* v, double* loss, cudaStream_t s) {
+    const float* d32 = nullptr;
+    rpnn_status st = train_desc(c, desc, dtype, q, &d32, s);
+    if (!st) st = train_forward(c, desc, dtype, d32, q, s);
+    if (st) return st;
+    float* dg = c.sample_val.as<float>();
+    st = launch_loss(c.t_out.as<float>(), target, (int)q, loss, dg, s);
+    if (st) return st;
+    st = train_backward(c, d32, q, dg, c.t_grad.as<float>(), s);
+    if (st) return st;
+    st = cc ? launch_adam_dev(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, cc, adam, s)
+            : launch_adam(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, step, adam, s);
+    if (st) return st;
+    RPNN_CUDA_TRY(cudaMemcpyAsync(c.params32.p, params, (size_t)RPNN_NPARAMS * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s));
+    return mlp_build_bf16_image(c, s);
+}
+
+void drop_train_graph(TrainGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+}
+
+// Captures the step for configuration `key` on the library's stream, reading the minibatch
+// and Adam's corrections from the graph's staging buffers.
+rpnn_status capture_train_step(Ctx& c, const TrainGraphKey& key, const rpnn_adam_cfg& adam, float* params, float* m,
+                               float* v, double* loss) {
+    TrainGraph& G = c.tgraph;
+    drop_train_graph(G);
+    if (!c.capture_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = c.capture_stream;
+    RPNN_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const rpnn_status est = train_step_body(c, G.desc.p, key.desc_dtype, G.target.as<float>(), key.batch, adam, 1,
+                                            G.adam.as<float>(), params, m, v, loss, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (est || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (!est) set_error("stream capture of the training step failed: %s", cudaGetErrorString(ce));
+        return est ? est : RPNN_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+        return RPNN_ERR_CUDA;
+    }
+    G.graph = graph;
+    G.exec = exec;
+    G.key = key;
+    return RPNN_OK;
+}
+
+}  // namespace
+
+void train_graph_release(Ctx& c) {
+    drop_train_graph(c.tgraph);
+    c.tgraph.desc.release();
+    c.tgraph.target.release();
+    c.tgraph.adam.release();
+}
+
+extern "C" {
+
 rpnn_status rpnn_train_step(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dtype, const float* dev_target, int32_t batch,
                             const rpnn_adam_cfg* adam, int64_t step, float* dev_params, float* dev_m,
                             float* dev_v, double* dev_loss, void* stream) {
@@ -910,23 +996,56 @@ rpnn_status rpnn_train_step(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_dt
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t q = batch;
+    const size_t row_bytes = (size_t)RPNN_K * RPNN_DESC_STRIDE * (desc_dtype == RPNN_BF16 ? 2 : 4);
     st = c->t_grad.reserve((size_t)RPNN_NPARAMS * sizeof(float));
     if (!st) st = c->sample_val.reserve(q * sizeof(float));
+    if (!st && c->train_graphs) {
+        st = c->tgraph.desc.reserve((size_t)q * row_bytes);
+        if (!st) st = c->tgraph.target.reserve((size_t)q * sizeof(float));
+        if (!st) st = c->tgraph.adam.reserve(2 * sizeof(float));
+    }
     if (st) return st;
-    const float* d32 = nullptr;
-    st = train_desc(*c, dev_desc, desc_dtype, q, &d32, s);
-    if (!st) st = train_forward(*c, dev_desc, desc_dtype, d32, q, s);
+    if (!c->train_graphs)
+        return train_step_body(*c, dev_desc, desc_dtype, dev_target, q, *adam, step, nullptr, dev_params, dev_m, dev_v,
+                               dev_loss, s);
+    // The step's launches are the same from step to step: the first step of a configuration
+    // runs them directly (the GEMM autotuner decides its tiles there), the second captures
+    // them as a graph, later steps replay it after staging the minibatch and Adam's
+    // corrections.  The key holds everything the captured launches bake in.
+    TrainGraph& G = c->tgraph;
+    TrainGraphKey key;
+    key.batch = batch; key.desc_dtype = desc_dtype; key.precision = c->train_precision;
+    key.params = dev_params; key.m = dev_m; key.v = dev_v; key.loss = dev_loss;
+    key.lr = adam->lr; key.b1 = adam->beta1; key.b2 = adam->beta2; key.eps = adam->eps;
+    key.tuner_version = c->tuner.version; key.epoch = c->epoch; key.allocs = devbuf_generation();
+    if (!(G.exec && G.key == key)) {
+        if (!(G.have_seen && G.seen == key)) {
+            st = train_step_body(*c, dev_desc, desc_dtype, dev_target, q, *adam, step, nullptr, dev_params, dev_m,
+                                 dev_v, dev_loss, s);
+            key.tuner_version = c->tuner.version;      // the direct run may have tuned
+            key.allocs = devbuf_generation();
+            G.seen = key;
+            G.have_seen = true;
+            return st;
+        }
+        st = capture_train_step(*c, key, *adam, dev_params, dev_m, dev_v, dev_loss);
+        if (st) return st;
+    }
+    RPNN_CUDA_TRY(cudaMemcpyAsync(G.desc.p, dev_desc, (size_t)q * row_bytes, cudaMemcpyDeviceToDevice, s));
+    RPNN_CUDA_TRY(cudaMemcpyAsync(G.target.p, dev_target, (size_t)q * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    st = launch_adam_corrections(G.adam.as<float>(), step, *adam, s);
     if (st) return st;
-    float* dg = c->sample_val.as<float>();
-    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
-    if (st) return st;
-    st = train_backward(*c, d32, q, dg, c->t_grad.as<float>(), s);
-    if (st) return st;
-    st = launch_adam(dev_params, dev_m, dev_v, c->t_grad.as<float>(), RPNN_NPARAMS, step, *adam, s);
-    if (st) return st;
-    RPNN_CUDA_TRY(cudaMemcpyAsync(c->params32.p, dev_params, (size_t)RPNN_NPARAMS * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, s));
-    return mlp_build_bf16_image(*c, s);
+    RPNN_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+    return RPNN_OK;
+}
+
+rpnn_status rpnn_set_train_graphs(rpnn_ctx* ctx, int32_t on) {
+    CHECK_CTX(ctx);
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    c->train_graphs = on != 0;
+    if (!c->train_graphs) train_graph_release(*c);
+    c->tgraph.have_seen = false;
+    return RPNN_OK;
 }
 
 }  // extern "C"

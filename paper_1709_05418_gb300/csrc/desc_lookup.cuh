@@ -110,36 +110,6 @@ __device__ __forceinline__ float lookup(const float4* __restrict__ packed, const
     return lerp_rn(c0, c1, f2);
 }
 
-// lookup() without a branch, for kernels that issue many lookups back to back: a point
-// outside the level (or any point when `on` is false) reads the valid record `safe`
-// (geo_safe_record: cell (0, 0, 0)) and its result is replaced by 0 afterwards, so the
-// loads of independent lookups need not wait for one another's range tests.  The value
-// is lookup()'s, bit for bit.
-__device__ __forceinline__ float lookup_nb(const float4* __restrict__ packed, const LevelGeo& g, uint32_t safe,
-                                           bool on, float u0, float u1, float u2) {
-    const float t0 = __fadd_rd(u0, kFloorMagic), t1 = __fadd_rd(u1, kFloorMagic), t2 = __fadd_rd(u2, kFloorMagic);
-    const bool in = on && t0 >= kFloorMagic - 1.0f && t0 <= g.hx && t1 >= kFloorMagic - 1.0f && t1 <= g.hy &&
-                    t2 >= kFloorMagic - 1.0f && t2 <= g.hz;
-    const float f0 = __fsub_rn(u0, __fsub_rn(t0, kFloorMagic));
-    const float f1 = __fsub_rn(u1, __fsub_rn(t1, kFloorMagic));
-    const float f2 = __fsub_rn(u2, __fsub_rn(t2, kFloorMagic));
-    uint32_t r = g.rbias + (uint32_t)__float_as_int(t2) * g.sz + (uint32_t)__float_as_int(t1) * g.sy +
-                 (uint32_t)__float_as_int(t0);
-    r = in ? r : safe;
-    float c[8];
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
-        : "l"(packed + 2 * (size_t)r));
-    const float c00 = __fmaf_rn(f0, c[1], c[0]);
-    const float c10 = __fmaf_rn(f0, c[3], c[2]);
-    const float c01 = __fmaf_rn(f0, c[5], c[4]);
-    const float c11 = __fmaf_rn(f0, c[7], c[6]);
-    const float c0 = lerp_rn(c00, c10, f1);
-    const float c1 = lerp_rn(c01, c11, f1);
-    const float v = lerp_rn(c0, c1, f2);
-    return in ? v : 0.0f;
-}
-
 // lookup() for a point known to lie inside the level (stencil_class == kInside): the same
 // arithmetic without the range test.
 __device__ __forceinline__ float lookup_in(const float4* __restrict__ packed, const LevelGeo& g, float u0, float u1,
@@ -186,27 +156,6 @@ __device__ __forceinline__ int stencil_class(const LevelGeo& g, const float (&A)
     return outside ? kOutside : (inside ? kInside : kMixed);
 }
 
-// Where one stencil column lies in a level: its 9 points u = P + oz C, oz in [-1, 3], span
-// per axis the segment between P - C and P + 3C; same margin and classes as stencil_class.
-__device__ __forceinline__ int column_class(const LevelGeo& g, const float (&P)[3], const float (&C)[3]) {
-    constexpr float kMargin = 1.0f / 64.0f;
-    const float hi[3] = {g.hx - kFloorMagic + 1.0f, g.hy - kFloorMagic + 1.0f, g.hz - kFloorMagic + 1.0f};
-    bool inside = true, outside = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float e0 = P[a] - C[a], e1 = P[a] + 3.0f * C[a];
-        const float lo = fminf(e0, e1), up = fmaxf(e0, e1);
-        inside = inside && lo >= -1.0f + kMargin && up < hi[a] - kMargin;
-        outside = outside || up < -1.0f - kMargin || lo >= hi[a] + kMargin;
-    }
-    return outside ? kOutside : (inside ? kInside : kMixed);
-}
-
-// the record of cell (0, 0, 0) of a level (inside the level: a safe address for lookup_nb)
-__device__ __forceinline__ uint32_t geo_safe_record(const LevelGeo& g) {
-    const uint32_t mb = (uint32_t)__float_as_int(kFloorMagic);
-    return g.rbias + mb * (g.sz + g.sy + 1u);
-}
 
 // level k's constants of volume v
 __device__ __forceinline__ LevelGeo make_geo(const VolumeView& v, int m) {

@@ -35,9 +35,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(floa
 // barrier at the start).  The 250 column tasks (level k, stencil column (ix, iy)) are
 // dealt to the lanes in order; a task reads its level's constants from shared memory,
 // computes the (ox, oy) part of the coordinate once and walks the 9 points along z
-// (fully unrolled: oz = -1 + 0.5 iz are constants); a column whose segment lies outside
-// the level is written as zeros without lookups, one inside it skips the range tests
-// (column_class; the values are lookup()'s either way).  BF16 rows are assembled in a
+// (fully unrolled: oz = -1 + 0.5 iz are constants).  BF16 rows are assembled in a
 // per-warp shared buffer and written with 16-byte stores; FP32 rows are stored
 // directly (25 consecutive values per level and z-slice).
 //
@@ -140,25 +138,11 @@ k_descriptor(const VolumeView v, const float* __restrict__ xs, const float* __re
                     dst[iz * 25] = cvt_out<OutT>(lerp_rn(r0, r1, b.w));
                 }
             } else {
-                // where the column's segment lies in the level (column_class)
-                const int cls = column_class(g.g0, P, C);
-                if (cls == kOutside) {
 #pragma unroll
-                    for (int iz = 0; iz < 9; ++iz) dst[iz * 25] = cvt_out<OutT>(0.0f);
-                } else if (cls == kInside) {
-#pragma unroll 3
-                    for (int iz = 0; iz < 9; ++iz) {
-                        const float oz = -1.0f + 0.5f * (float)iz;  // exact: -1, -0.5, ..., 3
-                        dst[iz * 25] = cvt_out<OutT>(lookup_in(packed, g.g0, __fmaf_rn(oz, C[0], P[0]),
-                                                               __fmaf_rn(oz, C[1], P[1]), __fmaf_rn(oz, C[2], P[2])));
-                    }
-                } else {
-#pragma unroll
-                    for (int iz = 0; iz < 9; ++iz) {
-                        const float oz = -1.0f + 0.5f * (float)iz;
-                        dst[iz * 25] = cvt_out<OutT>(lookup(packed, g.g0, __fmaf_rn(oz, C[0], P[0]),
-                                                            __fmaf_rn(oz, C[1], P[1]), __fmaf_rn(oz, C[2], P[2])));
-                    }
+                for (int iz = 0; iz < 9; ++iz) {
+                    const float oz = -1.0f + 0.5f * (float)iz;      // exact: -1, -0.5, ..., 3
+                    dst[iz * 25] = cvt_out<OutT>(lookup(packed, g.g0, __fmaf_rn(oz, C[0], P[0]),
+                                                        __fmaf_rn(oz, C[1], P[1]), __fmaf_rn(oz, C[2], P[2])));
                 }
             }
         }

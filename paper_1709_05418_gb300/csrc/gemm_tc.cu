@@ -389,6 +389,7 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
                 if (us < best.us) { best.us = us; best.tile = cd.bn; best.splits = cd.sp; }
             }
             tu.table.emplace_back(key, best);
+            ++tu.version;
             bn = best.tile;
             splits = best.splits;
         }

@@ -52,6 +52,9 @@ struct DevBuf {
     void release();
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
+// advanced by every device allocation or release of a DevBuf (a captured graph's buffer
+// pointers stay valid while it is unchanged)
+uint64_t devbuf_generation();
 
 // Geometry of one level of the corner-packed pyramid: record (x,y,z) for x in
 // [-1, ax-1] holds the 8 trilinear corners of cell (x..x+1, y..y+1, z..z+1).
@@ -124,6 +127,7 @@ struct GemmChoice {
 };
 struct GemmTuner {
     bool enabled = true;
+    uint64_t version = 0;   // advanced by every change of the table or of `enabled`
     std::vector<std::pair<GemmKey, GemmChoice>> table;
     DevBuf scratch, ws;   // tuning output, split-K partial sums
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -176,6 +180,28 @@ struct BatchGraph {
     DevBuf x, d, ps, sample, count, off, desc, g, table;
 };
 
+// A captured training step (rpnn_train_step): the configuration it was captured for (the
+// cache key, seen once eagerly before capture), the graph, and the staging buffers its
+// kernels read the minibatch and Adam's bias corrections from.
+struct TrainGraphKey {
+    int32_t batch = 0, desc_dtype = 0, precision = 0;
+    const void *params = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    float lr = 0, b1 = 0, b2 = 0, eps = 0;
+    uint64_t tuner_version = 0, epoch = 0, allocs = 0;
+    bool operator==(const TrainGraphKey& o) const {
+        return batch == o.batch && desc_dtype == o.desc_dtype && precision == o.precision && params == o.params &&
+               m == o.m && v == o.v && loss == o.loss && lr == o.lr && b1 == o.b1 && b2 == o.b2 && eps == o.eps &&
+               tuner_version == o.tuner_version && epoch == o.epoch && allocs == o.allocs;
+    }
+};
+struct TrainGraph {
+    TrainGraphKey key, seen;
+    bool have_seen = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    DevBuf desc, target, adam;        // staged minibatch, {c1, c2} of Adam's bias correction
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 0;
@@ -200,6 +226,8 @@ struct Ctx {
     // batched render: a captured graph, the stream it is captured on, and an epoch that
     // volume loads, mip builds and weight updates advance (invalidating the graph)
     BatchGraph batch;
+    TrainGraph tgraph;               // captured training step
+    bool train_graphs = true;        // rpnn_set_train_graphs
     int64_t chunk_rows = 0;          // descriptor/network chunk of a render (0: kChunkRows)
     bool fused = false;              // BF16 renders gather descriptors inside the network kernel
     cudaStream_t capture_stream = nullptr;
@@ -215,6 +243,7 @@ struct Ctx {
 
 // ---- launchers implemented in the .cu files -------------------------------------------
 void batch_release(Ctx& c);           // frees the captured batch graph and its buffers
+void train_graph_release(Ctx& c);     // frees the captured training step and its buffers
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_brick_majorants(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s);
@@ -285,6 +314,11 @@ rpnn_status launch_loss(const float* g, const float* target, int batch, double* 
                         float* dg, cudaStream_t s);
 rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,
                         int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s);
+// Adam with its bias corrections {1 - b1^step, 1 - b2^step} read from device memory (cc,
+// two FP32 values as launch_adam computes them), and the launch that writes them
+rpnn_status launch_adam_dev(float* p, float* m, float* v, const float* grad, int64_t n, const float* cc,
+                            const rpnn_adam_cfg& cfg, cudaStream_t s);
+rpnn_status launch_adam_corrections(float* cc, int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s);
 
 // BF16 tensor-core GEMM (training): D = epilogue(A0 B0^T + A1 B1^T), A_s [M][K_s] and
 // B_s [N][K_s] BF16 with K contiguous (row pitches lda/ldb in elements, multiples of 8;

@@ -283,6 +283,7 @@ rpnn_status tune(Ctx& c, const GemmKey& key, int M, const int* M_dev, int N, con
         if (us < best.us) { best.us = us; best.tile = cd.t; best.splits = cd.sp; }
     }
     tu.table.emplace_back(key, best);
+    ++tu.version;
     *out = best;
     return RPNN_OK;
 }
@@ -350,6 +351,26 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     }
+}
+
+__global__ void k_adam_dev(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ grad, int64_t n, float lr, float b1, float b2, float eps,
+                           const float* __restrict__ cc) {
+    const float c1 = cc[0], c2 = cc[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void k_set2(float* __restrict__ cc, float a, float b) {
+    cc[0] = a;
+    cc[1] = b;
 }
 
 }  // namespace
@@ -670,6 +691,21 @@ rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t
     const double c2 = 1.0 - std::pow((double)cfg.beta2, (double)step);
     k_adam<<<1024, 256, 0, s>>>(p, m, v, grad, n, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, (float)c1,
                                 (float)c2);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_adam_corrections(float* cc, int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s) {
+    const double c1 = 1.0 - std::pow((double)cfg.beta1, (double)step);
+    const double c2 = 1.0 - std::pow((double)cfg.beta2, (double)step);
+    k_set2<<<1, 1, 0, s>>>(cc, (float)c1, (float)c2);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_adam_dev(float* p, float* m, float* v, const float* grad, int64_t n, const float* cc,
+                            const rpnn_adam_cfg& cfg, cudaStream_t s) {
+    k_adam_dev<<<1024, 256, 0, s>>>(p, m, v, grad, n, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, cc);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }
