@@ -905,6 +905,7 @@ rpnn_status rpnn_mlp_backward(rpnn_ctx* ctx, const void* dev_desc, int32_t desc_
 
 }  // extern "C"
 
+namespace rpnn {
 namespace {
 
 // The arithmetic of one training step on q descriptor rows: forward, log-MSE loss,
@@ -976,6 +977,8 @@ void train_graph_release(Ctx& c) {
     c.tgraph.target.release();
     c.tgraph.adam.release();
 }
+
+}  // namespace rpnn
 
 extern "C" {
 

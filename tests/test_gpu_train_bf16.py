@@ -204,3 +204,37 @@ def test_autograd_function_bf16_route(env, cloud_desc):
     with pytest.raises(TypeError):
         rpnn(p, zb.float(), ctx)
     ctx.set_weights(params)
+
+
+@pytest.mark.parametrize("precision", ["F32", "BF16"])
+def test_captured_training_steps_equal_direct_steps(env, cloud_desc, precision):
+    """rpnn_set_train_graphs: from the third step of a configuration on, a step replays a
+    captured graph after staging its minibatch; five steps over two alternating minibatches
+    give the parameters, moments and losses of five direct steps bit for bit."""
+    api, _, params = env
+    zb = torch.from_numpy(cloud_desc).cuda()
+    if precision == "BF16":
+        zb = zb.to(torch.bfloat16)
+    batches = [(zb[:200].contiguous(), torch.linspace(0.01, 0.5, 200, device="cuda")),
+               (zb[133:].contiguous(), torch.linspace(0.4, 0.02, 200, device="cuda"))]
+    out = []
+    for graphs in (False, True):
+        ctx = api.Context()
+        ctx.set_autotune(False)                 # both contexts use the default tiles
+        ctx.set_train_precision(getattr(api, precision))
+        ctx.set_train_graphs(graphs)
+        p = params.clone()
+        m, v = torch.zeros_like(p), torch.zeros_like(p)
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        ctx.set_weights(p)
+        losses = []
+        for step in range(1, 6):
+            z, t = batches[step % 2]
+            ctx.train_step(z, t, p, m, v, step, loss=loss)
+            losses.append(float(loss.item()))
+        ctx.sync_status()
+        out.append((losses, p, m, v))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    for a, b in zip(out[0][1:], out[1][1:]):
+        assert torch.equal(a, b)
