@@ -333,7 +333,7 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
     GemmTuner& tu = c.tuner;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
-    if (tu.enabled && cs == cudaStreamCaptureStatusNone) {
+    if (tu.enabled) {
         GemmKey key{M, N, s0.K, s1 ? s1->K : 0,
                     kTgFlag | (o.bias != nullptr) << 4 | (o.res != nullptr) << 5 | (o.mask != nullptr) << 6 |
                         (o.Cb != nullptr) << 9 | (o.Ct != nullptr) << 10};
@@ -341,7 +341,7 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
         if (hit) {
             bn = hit->tile;
             splits = hit->splits;
-        } else {
+        } else if (cs == cudaStreamCaptureStatusNone) {   // never time under stream capture
             // time every admissible (tile width, split) on the call's operands, writing the
             // FP32 result into scratch only
             struct Cand { int bn, sp; };

@@ -298,17 +298,16 @@ rpnn_status gemm(Ctx* c, int M, const int* M_dev, int N, const Seg& s0, const Se
     const Seg& s1r = s1 ? *s1 : s0;
     const int nseg = s1 ? 2 : 1;
     if (c && c->tuner.enabled) {
+        // a choice already made applies under stream capture too; timing new shapes does not
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
-        if (cs == cudaStreamCaptureStatusNone) {
-            const GemmKey key = make_key(M, N, s0, s1, e, M_dev != nullptr);
-            const GemmChoice* hit = c->tuner.find(key);
-            if (hit) {
-                ch = *hit;
-            } else {
-                rpnn_status st = tune(*c, key, M, M_dev, N, s0, s1r, nseg, e, s, &ch);
-                if (st) return st;
-            }
+        const GemmKey key = make_key(M, N, s0, s1, e, M_dev != nullptr);
+        const GemmChoice* hit = c->tuner.find(key);
+        if (hit) {
+            ch = *hit;
+        } else if (cs == cudaStreamCaptureStatusNone) {
+            rpnn_status st = tune(*c, key, M, M_dev, N, s0, s1r, nseg, e, s, &ch);
+            if (st) return st;
         }
     }
     float* ws = nullptr;

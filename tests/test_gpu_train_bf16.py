@@ -210,19 +210,22 @@ def test_autograd_function_bf16_route(env, cloud_desc):
 def test_captured_training_steps_equal_direct_steps(env, cloud_desc, precision):
     """rpnn_set_train_graphs: from the third step of a configuration on, a step replays a
     captured graph after staging its minibatch; five steps over two alternating minibatches
-    give the parameters, moments and losses of five direct steps bit for bit."""
+    give the parameters, moments and losses of five direct steps bit for bit, with the
+    autotuner's tile and split-K choices applied inside the captured GEMMs."""
     api, _, params = env
-    zb = torch.from_numpy(cloud_desc).cuda()
+    # 1,280-row minibatches: the weight gradients' inner size admits split-K
+    zb = torch.from_numpy(rows_of(cloud_desc, 2560)).cuda()
     if precision == "BF16":
         zb = zb.to(torch.bfloat16)
-    batches = [(zb[:200].contiguous(), torch.linspace(0.01, 0.5, 200, device="cuda")),
-               (zb[133:].contiguous(), torch.linspace(0.4, 0.02, 200, device="cuda"))]
-    out = []
+    batches = [(zb[:1280].contiguous(), torch.linspace(0.01, 0.5, 1280, device="cuda")),
+               (zb[1280:].contiguous(), torch.linspace(0.4, 0.02, 1280, device="cuda"))]
+    out, table = [], None
     for graphs in (False, True):
         ctx = api.Context()
-        ctx.set_autotune(False)                 # both contexts use the default tiles
         ctx.set_train_precision(getattr(api, precision))
         ctx.set_train_graphs(graphs)
+        if table is not None:
+            ctx.set_autotune_table(table)       # the direct context's tile and split choices
         p = params.clone()
         m, v = torch.zeros_like(p), torch.zeros_like(p)
         loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -234,6 +237,9 @@ def test_captured_training_steps_equal_direct_steps(env, cloud_desc, precision):
             losses.append(float(loss.item()))
         ctx.sync_status()
         out.append((losses, p, m, v))
+        if table is None:
+            table = ctx.autotune_table()
+            print(f"{precision}: {sum(e['splits'] > 1 for e in table)} of {len(table)} tuned shapes split K")
         ctx.close()
     assert out[0][0] == out[1][0]
     for a, b in zip(out[0][1:], out[1][1:]):
