@@ -1,12 +1,12 @@
 // batch.cu -- batched rendering of several clouds (uneven query counts) as one CUDA graph.
 //
 // No counterpart in the paper, whose renderer serves one cloud at a time: serving many
-// clouds per frame gathers the shading points of all of them into one descriptor launch
-// and one persistent network launch.  Per item the primary stage (Sec. 4.4) writes its
-// queries into its own region of the per-pixel-sample buffers; a one-thread prefix sum
+// clouds per frame runs every stage once for all of them.  One primary launch (Sec. 4.4)
+// covers the pixel samples of all items, each block working on one item and writing its
+// queries into that item's region of the per-pixel-sample buffers; a one-thread prefix sum
 // turns the per-item counts into offsets of the compacted query list; the descriptor
-// (Sec. 4.2) and network (Sec. 4.3) stages run once over that list; per item the
-// predictions are scattered back and the image composed.  The query counts are
+// (Sec. 4.2) and network (Sec. 4.3) stages run once over that list; one scatter adds every
+// item's predictions to its samples and one composite writes every item's image.  The query counts are
 // deterministic (Philox-keyed decisions), so the first call runs the primary stages once
 // to size the compacted buffers, then captures the whole sequence.
 #include <cmath>
@@ -60,37 +60,25 @@ void drop_graph(BatchGraph& B) {
 }
 
 // Enqueues the whole batched render on stream s (captured, or run directly).
-rpnn_status enqueue_batch(Ctx& c, const rpnn_batch_item* items, int n, const std::vector<int64_t>& region,
-                          cudaStream_t s) {
+rpnn_status enqueue_batch(Ctx& c, const rpnn_batch_item* items, int n, cudaStream_t s) {
     BatchGraph& B = c.batch;
     int* count = B.count.as<int>();
     int* off = B.off.as<int>();
     RPNN_CUDA_TRY(cudaMemsetAsync(count, 0, n * sizeof(int), s));
-    for (int i = 0; i < n; ++i) {
-        const Volume* v = c.vol(items[i].vol);
-        const int64_t o = region[i];
-        rpnn_status st = launch_primary(c, v->view(), items[i].desc, B.sample.as<float>() + o, B.x.as<float>() + 3 * o,
-                                        B.d.as<float>() + 3 * o, B.ps.as<uint32_t>() + o, count + i, nullptr, nullptr,
-                                        nullptr, nullptr, s);
-        if (st) return st;
-    }
+    rpnn_status st = launch_primary_batch(c, B.tables.p, n, B.blocks, B.sample.as<float>(), B.x.as<float>(),
+                                          B.d.as<float>(), B.ps.as<uint32_t>(), count, s);
+    if (st) return st;
     k_batch_offsets<<<1, 32, 0, s>>>(count, n, B.cap, off, c.status.as<uint32_t>());
     RPNN_CHECK_LAUNCH();
     bool blend = false;
     for (int i = 0; i < n; ++i) blend |= c.vol(items[i].vol)->mip_blend;
-    rpnn_status st = launch_descriptor_batch(c, B.table.as<BatchItemDev>(), n, B.x.as<float>(), B.d.as<float>(),
+    st = launch_descriptor_batch(c, B.table.as<BatchItemDev>(), n, B.x.as<float>(), B.d.as<float>(),
                                              off, B.cap, B.desc.p, blend, s);
     if (st) return st;
     st = mlp_forward_bf16(c, B.desc.p, B.cap, off + n, B.g.as<float>(), s);
     if (st) return st;
-    for (int i = 0; i < n; ++i) {
-        const Volume* v = c.vol(items[i].vol);
-        const int64_t o = region[i];
-        st = launch_scatter_composite(c, items[i].desc, v->albedo, B.g.as<float>(), B.ps.as<uint32_t>() + o, count + i,
-                                      B.sample.as<float>() + o, items[i].dev_image, true, s, off + i, off + n);
-        if (st) return st;
-    }
-    return RPNN_OK;
+    return launch_scatter_composite_batch(c, B.tables.p, n, B.pixels, B.g.as<float>(), B.ps.as<uint32_t>(), off,
+                                          B.sample.as<float>(), s);
 }
 
 // Sizes the buffers for this item list, learns the query counts with one direct run of
@@ -112,17 +100,18 @@ rpnn_status build_batch(Ctx& c, const rpnn_batch_item* items, int n, cudaStream_
     if (!st) st = B.count.reserve(RPNN_MAX_BATCH * sizeof(int));
     if (!st) st = B.off.reserve((RPNN_MAX_BATCH + 1) * sizeof(int));
     if (!st) st = B.table.reserve(RPNN_MAX_BATCH * sizeof(BatchItemDev));
+    if (!st) st = B.tables.reserve(batch_tables_bytes(RPNN_MAX_BATCH));
     if (st) return st;
+    // the items' tables for the batched primary, scatter and composite kernels
+    std::vector<unsigned char> ht;
+    batch_tables(c, items, n, region, ht, &B.blocks, &B.pixels);
+    RPNN_CUDA_TRY(cudaMemcpyAsync(B.tables.p, ht.data(), ht.size(), cudaMemcpyHostToDevice, s));
     // query counts of this item list
     int* count = B.count.as<int>();
     RPNN_CUDA_TRY(cudaMemsetAsync(count, 0, n * sizeof(int), s));
-    for (int i = 0; i < n; ++i) {
-        const int64_t o = region[i];
-        st = launch_primary(c, c.vol(items[i].vol)->view(), items[i].desc, B.sample.as<float>() + o,
-                            B.x.as<float>() + 3 * o, B.d.as<float>() + 3 * o, B.ps.as<uint32_t>() + o, count + i,
-                            nullptr, nullptr, nullptr, nullptr, s);
-        if (st) return st;
-    }
+    st = launch_primary_batch(c, B.tables.p, n, B.blocks, B.sample.as<float>(), B.x.as<float>(), B.d.as<float>(),
+                              B.ps.as<uint32_t>(), count, s);
+    if (st) return st;
     std::vector<int> h(n);
     RPNN_CUDA_TRY(cudaMemcpyAsync(h.data(), count, n * sizeof(int), cudaMemcpyDeviceToHost, s));
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
@@ -144,7 +133,7 @@ rpnn_status build_batch(Ctx& c, const rpnn_batch_item* items, int n, cudaStream_
     if (!c.capture_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
     cudaStream_t cs = c.capture_stream;
     RPNN_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const rpnn_status est = enqueue_batch(c, items, n, region, cs);
+    const rpnn_status est = enqueue_batch(c, items, n, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (est) {
@@ -175,7 +164,7 @@ rpnn_status build_batch(Ctx& c, const rpnn_batch_item* items, int n, cudaStream_
 void batch_release(Ctx& c) {
     BatchGraph& B = c.batch;
     drop_graph(B);
-    DevBuf* bufs[] = {&B.x, &B.d, &B.ps, &B.sample, &B.count, &B.off, &B.desc, &B.g, &B.table};
+    DevBuf* bufs[] = {&B.x, &B.d, &B.ps, &B.sample, &B.count, &B.off, &B.desc, &B.g, &B.table, &B.tables};
     for (DevBuf* b : bufs) b->release();
 }
 

@@ -177,7 +177,8 @@ struct BatchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t cap = 0;                 // capacity of the compacted query arrays
-    DevBuf x, d, ps, sample, count, off, desc, g, table;
+    int64_t blocks = 0, pixels = 0;  // primary blocks and image pixels of all items
+    DevBuf x, d, ps, sample, count, off, desc, g, table, tables;
 };
 
 // A captured training step (rpnn_train_step): the configuration it was captured for (the
@@ -243,6 +244,16 @@ struct Ctx {
 
 // ---- launchers implemented in the .cu files -------------------------------------------
 void batch_release(Ctx& c);           // frees the captured batch graph and its buffers
+// Batched render helpers (render.cu): the per-item tables of the batched primary, scatter and
+// composite kernels (host image of `batch_tables_bytes(n)` bytes, with the primary grid's
+// block count and the items' total pixel count), and their launches.
+size_t batch_tables_bytes(int n);
+void batch_tables(const Ctx& c, const rpnn_batch_item* items, int n, const std::vector<int64_t>& region,
+                  std::vector<unsigned char>& out, int64_t* blocks, int64_t* pixels);
+rpnn_status launch_primary_batch(Ctx& c, const void* tables, int n, int64_t blocks, float* sample_val, float* qx,
+                                 float* qd, uint32_t* qps, int* qcount, cudaStream_t s);
+rpnn_status launch_scatter_composite_batch(Ctx& c, const void* tables, int n, int64_t pixels, const float* g,
+                                           const uint32_t* qps, const int* off, float* sample_val, cudaStream_t s);
 void train_graph_release(Ctx& c);     // frees the captured training step and its buffers
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_brick_majorants(Ctx& c, Volume& v, cudaStream_t s);

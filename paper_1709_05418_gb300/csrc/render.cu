@@ -7,6 +7,8 @@
 // appended shading query for the descriptor + network stages, or (path mode) a
 // path-traced estimate of the indirect part.  Queries are compacted with one atomic per
 // warp so the list stays in pixel order within a warp.
+#include <vector>
+
 #include "common.cuh"
 
 namespace rpnn {
@@ -23,14 +25,51 @@ struct RenderArgs {
     int mode;   // RPNN_MODE_*
 };
 
+// One render of a batch for the batched primary pass: its volume, camera and light, its
+// pixel samples, where they start in the batch's per-sample buffers, and its first block.
+struct PrimaryItem {
+    VolumeView v;
+    RenderArgs a;
+    int64_t P, region, first_block;
+};
+
 // 6 blocks of 128 threads per SM (80 registers, no spills): more rays in flight to hide the
-// latency of the density gathers
-__global__ void __launch_bounds__(128, 6)
-k_primary(const VolumeView v, const RenderArgs a, int64_t P, float* __restrict__ sample_val,
+// latency of the density gathers (the batched form, which reads the volume from shared
+// memory, takes 5 and 96 registers).  BATCH: the grid covers the pixel samples of up to
+// RPNN_MAX_BATCH renders (items[i] from block first_block on); each block copies its item
+// into shared memory and works on that render's samples, writing into its region of the
+// per-sample buffers and appending its shading points to that region with its own count.
+template <bool BATCH>
+__global__ void __launch_bounds__(128, BATCH ? 5 : 6)
+k_primary(const VolumeView v_, const RenderArgs a_, int64_t P_, float* __restrict__ sample_val,
           float* __restrict__ qx, float* __restrict__ qd, uint32_t* __restrict__ qps,
           int* __restrict__ qcount, int* __restrict__ hit_out, float* __restrict__ x_out,
-          float* __restrict__ d_out, float* __restrict__ Ld_out, uint32_t* status) {
-    const int64_t ps = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+          float* __restrict__ d_out, float* __restrict__ Ld_out, uint32_t* status,
+          const PrimaryItem* __restrict__ items, int n_items) {
+    __shared__ __align__(16) PrimaryItem it;
+    __shared__ int s_item;
+    if (BATCH) {
+        if (threadIdx.x == 0) {
+            int i = 0;
+            while (i + 1 < n_items && items[i + 1].first_block <= (int64_t)blockIdx.x) ++i;
+            s_item = i;
+        }
+        __syncthreads();
+        const int* src = reinterpret_cast<const int*>(items + s_item);
+        int* dst = reinterpret_cast<int*>(&it);
+        for (int w = threadIdx.x; w < (int)(sizeof(PrimaryItem) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        const int64_t o = it.region;
+        sample_val += o;
+        qx += 3 * o;
+        qd += 3 * o;
+        qps += o;
+        qcount += s_item;
+    }
+    const VolumeView& v = BATCH ? it.v : v_;
+    const RenderArgs& a = BATCH ? it.a : a_;
+    const int64_t P = BATCH ? it.P : P_;
+    const int64_t ps = (blockIdx.x - (BATCH ? it.first_block : 0)) * (int64_t)blockDim.x + threadIdx.x;
     const bool active = ps < P;
     int hit = 0;
     float3 x = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f);
@@ -132,6 +171,46 @@ __global__ void k_composite(const float* __restrict__ sample_val, int64_t npix, 
         float acc = 0.0f;
         for (int s = 0; s < spp; ++s) acc += sample_val[p * spp + s];
         image[p] = acc / (float)spp;
+    }
+}
+
+// One render of a batch for the batched scatter and composite: its region of the per-sample
+// buffers, the weight of its predictions (albedo x irradiance), samples per pixel, pixel
+// count, first pixel in the batch's pixel numbering, and its image.
+struct OutItem {
+    int64_t region, npix, first_pixel;
+    float scale;
+    int spp;
+    float* image;
+};
+
+// Predictions of all items' shading points (compacted: item i's at off[i] .. off[i+1]) added to
+// their samples, sample_val[region_i + qps[region_i + j]] += scale_i g[off[i] + j]
+__global__ void k_scatter_batch(const float* __restrict__ g, const uint32_t* __restrict__ qps,
+                                const int* __restrict__ off, const OutItem* __restrict__ items, int n_items,
+                                float* __restrict__ sample_val) {
+    const int total = off[n_items];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int i = 0;
+        while (i + 1 < n_items && off[i + 1] <= q) ++i;
+        const int64_t o = items[i].region;
+        sample_val[o + qps[o + (q - off[i])]] += items[i].scale * g[q];
+    }
+}
+
+// every item's pixels: mean over its samples, summed in sample order (as k_composite)
+__global__ void k_composite_batch(const float* __restrict__ sample_val, const OutItem* __restrict__ items,
+                                  int n_items, int64_t total_pixels) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total_pixels;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int i = 0;
+        while (i + 1 < n_items && items[i + 1].first_pixel <= p) ++i;
+        const OutItem& it = items[i];
+        const int64_t px = p - it.first_pixel;
+        const float* sv = sample_val + it.region + px * it.spp;
+        float acc = 0.0f;
+        for (int s = 0; s < it.spp; ++s) acc += sv[s];
+        it.image[px] = acc / (float)it.spp;
     }
 }
 
@@ -270,13 +349,67 @@ RenderArgs make_args(const rpnn_render_desc& rd) {
 
 }  // namespace
 
+size_t batch_tables_bytes(int n) {
+    return ((size_t)n * sizeof(PrimaryItem) + 255) / 256 * 256 + (size_t)n * sizeof(OutItem);
+}
+
+void batch_tables(const Ctx& c, const rpnn_batch_item* items, int n, const std::vector<int64_t>& region,
+                  std::vector<unsigned char>& out, int64_t* blocks, int64_t* pixels) {
+    out.assign(batch_tables_bytes(n), 0);
+    PrimaryItem* pi = reinterpret_cast<PrimaryItem*>(out.data());
+    OutItem* oi = reinterpret_cast<OutItem*>(out.data() + ((size_t)n * sizeof(PrimaryItem) + 255) / 256 * 256);
+    int64_t b = 0, px = 0;
+    for (int i = 0; i < n; ++i) {
+        const rpnn_render_desc& rd = items[i].desc;
+        const Volume* v = c.vol(items[i].vol);
+        pi[i].v = v->view();
+        pi[i].a = make_args(rd);
+        pi[i].P = (int64_t)rd.width * rd.height * rd.spp;
+        pi[i].region = region[i];
+        pi[i].first_block = b;
+        b += (pi[i].P + 127) / 128;
+        oi[i].region = region[i];
+        oi[i].npix = (int64_t)rd.width * rd.height;
+        oi[i].first_pixel = px;
+        oi[i].scale = v->albedo * rd.light_E;
+        oi[i].spp = rd.spp;
+        oi[i].image = items[i].dev_image;
+        px += oi[i].npix;
+    }
+    *blocks = b;
+    *pixels = px;
+}
+
+rpnn_status launch_primary_batch(Ctx& c, const void* tables, int n, int64_t blocks, float* sample_val, float* qx,
+                                 float* qd, uint32_t* qps, int* qcount, cudaStream_t s) {
+    const PrimaryItem* pi = static_cast<const PrimaryItem*>(tables);
+    k_primary<true><<<(unsigned)blocks, 128, 0, s>>>(VolumeView{}, RenderArgs{}, 0, sample_val, qx, qd, qps, qcount,
+                                                     nullptr, nullptr, nullptr, nullptr, c.status.as<uint32_t>(), pi,
+                                                     n);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
+rpnn_status launch_scatter_composite_batch(Ctx& c, const void* tables, int n, int64_t pixels, const float* g,
+                                           const uint32_t* qps, const int* off, float* sample_val, cudaStream_t s) {
+    const OutItem* oi = reinterpret_cast<const OutItem*>(static_cast<const unsigned char*>(tables) +
+                                                         ((size_t)n * sizeof(PrimaryItem) + 255) / 256 * 256);
+    k_scatter_batch<<<c.num_sms * 8, 256, 0, s>>>(g, qps, off, oi, n, sample_val);
+    RPNN_CHECK_LAUNCH();
+    int64_t b = (pixels + 255) / 256;
+    if (b > c.num_sms * 16) b = c.num_sms * 16;
+    k_composite_batch<<<(unsigned)(b > 0 ? b : 1), 256, 0, s>>>(sample_val, oi, n, pixels);
+    RPNN_CHECK_LAUNCH();
+    return RPNN_OK;
+}
+
 rpnn_status launch_primary(Ctx& c, const VolumeView& vv, const rpnn_render_desc& rd,
                            float* sample_val, float* qx, float* qd, uint32_t* qps, int* qcount,
                            int* hit, float* xo, float* dout, float* Ld, cudaStream_t s) {
     const int64_t P = (int64_t)rd.width * rd.height * rd.spp;
     const int64_t blocks = (P + 127) / 128;
-    k_primary<<<(unsigned)blocks, 128, 0, s>>>(vv, make_args(rd), P, sample_val, qx, qd, qps, qcount,
-                                               hit, xo, dout, Ld, c.status.as<uint32_t>());
+    k_primary<false><<<(unsigned)blocks, 128, 0, s>>>(vv, make_args(rd), P, sample_val, qx, qd, qps, qcount,
+                                                      hit, xo, dout, Ld, c.status.as<uint32_t>(), nullptr, 0);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }
