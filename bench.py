@@ -322,7 +322,7 @@ def run_batch(args, ws, rank, local):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "queries_per_step": nq, "queries_per_cloud": [int(c) for c in counts],
                    "edges": [int(e) for e in edges], "l2": "flushed: 256 MB write between timed steps"},
-        "gpu_launches": (16 + 3 + 2 * 16) * args.steps,   # primaries, offsets, descriptor, network, scatters + composites
+        "gpu_launches": 6 * args.steps,   # primary (all items), offsets, descriptor, network, scatter, composite
         "e2e": {"value": q_total / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "clocks": clk,
     }

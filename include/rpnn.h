@@ -285,12 +285,12 @@ rpnn_status rpnn_set_render_chunk(rpnn_ctx* ctx, int64_t rows);
 rpnn_status rpnn_set_fused(rpnn_ctx* ctx, int32_t on);
 /* Batched serving (no counterpart in the paper: many clouds, uneven query counts, one
  * frame).  Item i renders volume items[i].vol with items[i].desc into items[i].dev_image
- * (FP32, caller-owned, width*height) exactly as rpnn_render would, bit for bit.  The
- * shading points of all items are compacted into one descriptor launch and one network
- * launch; the whole sequence (per-item primary stages, a prefix sum of the per-item query
- * counts, descriptor, network, per-item composites) is captured once as a CUDA graph on a
- * library-owned stream and replayed on `stream` while the item list (volumes,
- * descriptions, image pointers) is unchanged; loading a volume, building mips or setting
+ * (FP32, caller-owned, width*height) exactly as rpnn_render would, bit for bit.  Every
+ * stage runs once for all items: one primary launch over all items' pixel samples, a prefix
+ * sum of the per-item query counts, one descriptor and one network launch over the
+ * compacted shading points, one scatter and one composite; the sequence is captured once as
+ * a CUDA graph on a library-owned stream and replayed on `stream` while the item list
+ * (volumes, descriptions, image pointers) is unchanged; loading a volume, building mips or setting
  * weights invalidates the captured graph, and so do rpnn_set_mip_blend and
  * rpnn_set_iteration_cap.  Requirements: 1 <= n_items <= RPNN_MAX_BATCH, every item in
  * RPNN_MODE_RPNN with RPNN_BF16 precision.  out_num_queries (host, may be
