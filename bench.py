@@ -39,12 +39,12 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands), with the SHA-256 prefixes of the sources the
 # captured build was compiled from.  A kernel whose sources changed since reports null.
 NCU_TRAFFIC = {
-    "descriptor": {"bytes_per_query": (797.218816e6 + 5.808640e6) / 178675,
-                   "sources": {"descriptor.cu": "9285b6ec0284c9d8", "volume.cu:k_pack": "f1b80b6358e59e22"}},
-    "network": {"bytes_per_query": (882.251776e6 + 3.977472e6) / 178675,
-                "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
-    "network_fp8": {"bytes_per_query": (459.278080e6 + 5.133824e6) / 178675,
-                    "sources": {"mlp_tc.cu": "4386f33df5bfc878", "tc_ptx.cuh": "9a0a53d9fb55a2e9"}},
+    "descriptor": {"bytes_per_query": (795.414272e6 + 5.620736e6) / 178675,
+                   "sources": {"descriptor.cu": "05b2f345e006b04d", "desc_lookup.cuh": "96d43ff4040f8e82",
+                               "volume.cu:k_pack": "f1b80b6358e59e22"}},
+    "network": {"bytes_per_query": (881.125632e6 + 0.750080e6) / 178675,
+                "sources": {"mlp_tc.cu": "4dae00dd61e3e9e5", "tc_ptx.cuh": "b9a0d4742a5c0947",
+                            "tc_net.cuh": "f36fbe582afc7249"}},
 }
 
 
