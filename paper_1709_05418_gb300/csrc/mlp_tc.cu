@@ -70,9 +70,13 @@ constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 // barrier slots from OFF_BAR, BAR_STRIDE bytes apart; B_DONE completes its phase 0 at
 // setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
 enum {
-    B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES, B_ZEMPTY = B_ZFULL + Z_STAGES,
-    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DONE, B_DRAIN, B_COUNT
+    B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES,
+    B_ACC = B_ZFULL + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DONE, B_DRAIN, B_COUNT
 };
+// a descriptor slot is reused 8 or 11 stages after its reader (a first layer's z stages,
+// then the 4 stages of layer 1 or of the block's second layer and the first layer's x
+// stages); the weight ring proves stages at least W_STAGES + 1 back complete
+static_assert(W_STAGES + 1 <= 8 && Z_STAGES == 4, "descriptor slot reuse needs the weight ring's ordering");
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
 constexpr uint32_t OFF_PART = OFF_ABORT + 8;                  // 3 x 128 floats
@@ -96,7 +100,7 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     if (tid == 0) {
         *abort_flag = (base & 1023u) ? 1 : 0;
         for (int s = 0; s < W_STAGES; ++s) { tc::mbar_init(bar(B_WFULL + s), 1); tc::mbar_init(bar(B_WEMPTY + s), 1); }
-        for (int s = 0; s < Z_STAGES; ++s) { tc::mbar_init(bar(B_ZFULL + s), 1); tc::mbar_init(bar(B_ZEMPTY + s), 1); }
+        for (int s = 0; s < Z_STAGES; ++s) tc::mbar_init(bar(B_ZFULL + s), 1);
         tc::mbar_init(bar(B_ACC), 1);
         for (int b = 0; b < npub<F>(); ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
@@ -130,7 +134,11 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     const int KB = layer_kb<F>(l), zkb = layer_zkb<F>(l), nb = layer_blocks<F>(l);
                     for (int k0 = 0; k0 < KB; k0 += SKB) {
                         if (k0 < zkb) {
-                            if (!twait(bar(B_ZEMPTY + sz), pz ^ 1u)) break;
+                            // No wait for the slot: its previous reader is the same stage of
+                            // the previous block's first layer (tile's first layer: the previous
+                            // tile's last), at least 8 stages back, and the weight fill just
+                            // before this point waited for the MMAs of the stage W_STAGES + 1
+                            // back to complete (MMAs complete in issue order).
                             const uint32_t st = base + OFF_Z + sz * Z_STAGE;
                             // level l/2, bytes k0 .. k0+127 as two boxes of 64 bytes (x in elements)
                             const int x = ((l / 2) * F::KZB + k0) / F::EB;
@@ -195,13 +203,13 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     // publication parity of epilogue n-1: n and l share parity
                     const uint32_t pb = (uint32_t)(l & 1) ^ 1u;
                     if (l == 0) {
-                        issue_layer<W_STAGES, Z_STAGES, F::FP8, F::KZB, F::KZB, false>(S, acc, pb);
+                        issue_layer<W_STAGES, Z_STAGES, F::FP8, F::KZB, F::KZB, false, false>(S, acc, pb);
                         // a tile's first layer reads no activation; it still waits for the
                         // previous epilogue, so the issuer never runs two phases ahead of it
                         if (n > 0)
                             tc::mbar_wait_issuer(S.blk0 + BAR_STRIDE * (npub<F>() - 1), pb, tc::kSpinLimit, S.abort_addr);
                     } else if (l < 20 && !(l & 1)) {
-                        issue_layer<W_STAGES, Z_STAGES, F::FP8, F::KZB + F::XB, F::KZB, false>(S, acc, pb);
+                        issue_layer<W_STAGES, Z_STAGES, F::FP8, F::KZB + F::XB, F::KZB, false, false>(S, acc, pb);
                     } else if (layer_resid(l)) {
                         issue_layer<W_STAGES, Z_STAGES, F::FP8, F::XB, 0, true>(S, acc, pb);
                     } else {

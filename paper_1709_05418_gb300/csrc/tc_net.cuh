@@ -98,9 +98,12 @@ __device__ __forceinline__ void mma_lohi(uint32_t acc, uint32_t a_lo, uint32_t b
 
 // One layer of KB bytes of K, the first ZKB of them from the descriptor ring, in stages of
 // 128 bytes (four MMAs of 32 bytes).  RESID: the accumulator already holds o^{k-1}.
+// ZCOMMIT: signal each consumed descriptor stage on its "empty" barrier (a kernel whose
+// descriptor ring is refilled only after the weight ring proves the stage's MMAs done
+// passes false and saves that commit).
 // Activation byte c sits in 64-byte block c / 64 at half (c / 32) % 2; a stage reading
 // bytes up to c waits for publication c / 128 of the previous epilogue (parity pb).
-template <int W_STAGES, int Z_STAGES, bool FP8, int KB, int ZKB, bool RESID>
+template <int W_STAGES, int Z_STAGES, bool FP8, int KB, int ZKB, bool RESID, bool ZCOMMIT = true>
 __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_t pb) {
 #pragma unroll
     for (int k0 = 0; k0 < KB; k0 += SKB) {
@@ -131,7 +134,7 @@ __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_
         if (++S.sw == W_STAGES) { S.sw = 0; S.pw ^= 1u; S.w = S.w0; S.wbar = S.wbar0; }
         else { S.w += W_STAGE >> 4; S.wbar += BAR_STRIDE; }
         if (hz) {
-            tc::mma_commit(S.zbar + BAR_STRIDE * Z_STAGES);
+            if (ZCOMMIT) tc::mma_commit(S.zbar + BAR_STRIDE * Z_STAGES);
             if (++S.sz == Z_STAGES) { S.sz = 0; S.pz ^= 1u; S.z = S.z0; S.zbar = S.zbar0; }
             else { S.z += Z_STAGE >> 4; S.zbar += BAR_STRIDE; }
         }
