@@ -84,9 +84,11 @@ rpnn_status train_forward(Ctx& c, const void* desc, int dtype, const float* d32,
     return mlp_forward_f32(c, d32, q, nullptr, c.t_out.as<float>(), c.t_saved.as<float>(), s);
 }
 
-rpnn_status train_backward(Ctx& c, const float* d32, int64_t q, const float* dout, float* dP, cudaStream_t s) {
+// side: a second stream for the BF16 weight gradients (null: everything on s)
+rpnn_status train_backward(Ctx& c, const float* d32, int64_t q, const float* dout, float* dP, cudaStream_t s,
+                           cudaStream_t side = nullptr) {
     if (c.train_precision == RPNN_BF16)
-        return mlp_backward_bf16_train(c, q, c.t_saved.as<float>(), c.t_saved16.as<uint16_t>(), dout, dP, s);
+        return mlp_backward_bf16_train(c, q, c.t_saved.as<float>(), c.t_saved16.as<uint16_t>(), dout, dP, s, side);
     return mlp_backward_f32(c, d32, q, c.t_saved.as<float>(), dout, dP, s);
 }
 
@@ -140,13 +142,15 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
-                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_scr16, &c->t_desc32, &c->lm_table, &c->lmc_table};
+                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_gb32, &c->t_gb16, &c->t_desc32, &c->lm_table, &c->lmc_table};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
     batch_release(*c);
     train_graph_release(*c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    for (cudaEvent_t e : c->t_events) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     delete c;
     return RPNN_OK;
@@ -921,7 +925,15 @@ rpnn_status train_step_body(Ctx& c, const void* desc, int32_t dtype, const float
     float* dg = c.sample_val.as<float>();
     st = launch_loss(c.t_out.as<float>(), target, (int)q, loss, dg, s);
     if (st) return st;
-    st = train_backward(c, d32, q, dg, c.t_grad.as<float>(), s);
+    // a captured BF16 step runs the weight gradients on a second stream, beside the
+    // data-gradient chain (a direct step keeps one stream: it may time new GEMM shapes)
+    cudaStream_t side = nullptr;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cst));
+    if (cst == cudaStreamCaptureStatusActive && c.train_precision == RPNN_BF16 && c.side_stream &&
+        (int)c.t_events.size() >= kTrainEvents)
+        side = c.side_stream;
+    st = train_backward(c, d32, q, dg, c.t_grad.as<float>(), s, side);
     if (st) return st;
     st = cc ? launch_adam_dev(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, cc, adam, s)
             : launch_adam(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, step, adam, s);
@@ -945,6 +957,13 @@ rpnn_status capture_train_step(Ctx& c, const TrainGraphKey& key, const rpnn_adam
     TrainGraph& G = c.tgraph;
     drop_train_graph(G);
     if (!c.capture_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
+    // the weight-gradient stream and its events exist before the capture starts
+    if (!c.side_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
+    while ((int)c.t_events.size() < kTrainEvents) {
+        cudaEvent_t ev;
+        RPNN_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c.t_events.push_back(ev);
+    }
     cudaStream_t cs = c.capture_stream;
     RPNN_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const rpnn_status est = train_step_body(c, G.desc.p, key.desc_dtype, G.target.as<float>(), key.batch, adam, 1,

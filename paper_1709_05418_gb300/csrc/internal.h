@@ -203,6 +203,8 @@ struct TrainGraph {
     DevBuf desc, target, adam;        // staged minibatch, {c1, c2} of Adam's bias correction
 };
 
+constexpr int kTrainEvents = 24;   // 22 per-layer gradients, fork, join
+
 struct Ctx {
     int device = 0;
     int num_sms = 0;
@@ -217,7 +219,10 @@ struct Ctx {
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
-    DevBuf t_w16, t_saved16, t_scr16;   // BF16 training: weight image, activation copies, gradient scratch
+    DevBuf t_w16, t_saved16;            // BF16 training: weight image, activation copies
+    DevBuf t_gb32, t_gb16;              // BF16 training: per-layer gradients (FP32; BF16 and transposed BF16)
+    std::vector<cudaEvent_t> t_events;  // BF16 training: kTrainEvents gradient-ready / fork / join events
+    cudaStream_t side_stream = nullptr; // BF16 training: weight gradients beside the data-gradient chain
     DevBuf t_desc32;                    // FP32 widening of BF16 training descriptors (FP32 training form)
     int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
@@ -384,7 +389,7 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
 // exact FP32 widening of n BF16 values
 rpnn_status launch_bf16_to_f32(const void* in, float* out, int64_t n, int sms, cudaStream_t s);
 rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
-                                    float* dP, cudaStream_t s);
+                                    float* dP, cudaStream_t s, cudaStream_t side = nullptr);
 
 // BF16 tensor-core network
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);

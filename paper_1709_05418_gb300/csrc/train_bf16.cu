@@ -237,7 +237,7 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
 }
 
 rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
-                                    float* dP, cudaStream_t s) {
+                                    float* dP, cudaStream_t s, cudaStream_t side) {
     const ParamLayout& L = param_layout();
     const TrainImage& I = train_image();
     const int M = (int)q;
@@ -246,18 +246,21 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     auto slot = [&](int i) { return saved + (size_t)i * q * H; };
     auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
     const uint16_t* zt = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
-    rpnn_status st = c.act0.reserve((size_t)q * H * sizeof(float));
-    if (!st) st = c.act1.reserve((size_t)q * H * sizeof(float));
-    if (!st) st = c.act2.reserve((size_t)q * H * sizeof(float));
-    if (!st) st = c.t_scr16.reserve((size_t)3 * ((size_t)q * H + (size_t)H * ldq) * 2);
-    if (st) return st;
-    // three gradient buffers, each FP32 [q][200] + BF16 [q][200] + BF16 transposed [200][ldq]
-    struct Buf { float* f; uint16_t* b; uint16_t* t; };
-    uint16_t* sc = c.t_scr16.as<uint16_t>();
+    // one gradient buffer per layer, each FP32 [q][200] + BF16 [q][200] + BF16 transposed
+    // [200][ldq]: nothing is overwritten within a step, so the weight-gradient GEMMs and
+    // bias sums may run on `side` while the data-gradient chain continues on `s`
+    constexpr int NG = 22;
     const size_t per16 = (size_t)q * H + (size_t)H * ldq;
-    Buf A{c.act0.as<float>(), sc, sc + (size_t)q * H};
-    Buf B{c.act1.as<float>(), sc + per16, sc + per16 + (size_t)q * H};
-    Buf D{c.act2.as<float>(), sc + 2 * per16, sc + 2 * per16 + (size_t)q * H};
+    rpnn_status st = c.t_gb32.reserve((size_t)NG * q * H * sizeof(float));
+    if (!st) st = c.t_gb16.reserve((size_t)NG * per16 * 2);
+    if (st) return st;
+    static_assert(NG + 2 <= kTrainEvents, "gradient-ready events");
+    if (side && (int)c.t_events.size() < kTrainEvents) { set_error("weight-gradient stream events missing"); return RPNN_ERR_STATE; }
+    struct Buf { float* f; uint16_t* b; uint16_t* t; int id; };
+    auto buf = [&](int i) {
+        uint16_t* b16 = c.t_gb16.as<uint16_t>() + (size_t)i * per16;
+        return Buf{c.t_gb32.as<float>() + (size_t)i * q * H, b16, b16 + (size_t)q * H, i};
+    };
     auto out_to = [&](const Buf& b) {
         TgOut o;
         o.C = b.f; o.ldc = H;
@@ -265,58 +268,83 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         o.Ct = b.t; o.ldt = ldq;
         return o;
     };
+    cudaStream_t ws = side ? side : s;                 // the weight-gradient stream
+    // gradient buffer b is complete on s: let the weight-gradient stream use it
+    auto ready = [&](const Buf& b) -> rpnn_status {
+        if (!side) return RPNN_OK;
+        RPNN_CUDA_TRY(cudaEventRecord(c.t_events[b.id], s));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(side, c.t_events[b.id], 0));
+        return RPNN_OK;
+    };
     auto wgrad = [&](const uint16_t* at, const uint16_t* bt, int N, float* dst) {
         // dW[j][i] = sum_m a[m][j] x[m][i]: A = a^T [200][ldq], B = x^T [N][ldq], K = q
         const TgSeg sg{at, ldq, bt, ldq, M};
         TgOut o;
         o.C = dst; o.ldc = N;
-        return tc_gemm(c, H, N, sg, nullptr, o, s);
+        return tc_gemm(c, H, N, sg, nullptr, o, ws);
     };
+    if (side) {
+        // the weight-gradient stream starts after everything issued on s so far
+        RPNN_CUDA_TRY(cudaEventRecord(c.t_events[NG], s));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(side, c.t_events[NG], 0));
+    }
+    int next = 0;
+    Buf A = buf(next++);
     // output layer (CUDA cores): A.f = dl/d(pre-activation of o^12 ... ) masked, dT3, dbT3
     st = mlp_output_layer_backward_f32(c, slot(21), saved + (size_t)22 * q * H, dout, q, dP, A.f, s);
     if (st) return st;
     k_train_act<<<grid_for(q * H, c.num_sms), 256, 0, s>>>(A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b),
                                                         reinterpret_cast<__nv_bfloat16*>(A.t));
     RPNN_CHECK_LAUNCH();
+    if ((st = ready(A))) return st;
     // standard layers 2 (input o^11, slot 20) and 1 (input o^10, slot 9)
     for (int t = 1; t >= 0; --t) {
         const int in = t == 1 ? 20 : 9;
-        st = wgrad(A.t, slott(in), H, dP + L.T[t]);
-        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.bT[t], s);
-        if (st) return st;
+        Buf B = buf(next++);
         TgOut o = out_to(B);
         o.mask = slot(in); o.ldm = H;
         const TgSeg sd{A.b, H, W + I.TT[t], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
+        if (!st) st = ready(B);
+        if (!st) st = wgrad(A.t, slott(in), H, dP + L.T[t]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.bT[t], ws);
         if (st) return st;
-        std::swap(A, B);
+        A = B;
     }
     // blocks k = 10 .. 1; A = dl/d(pre-activation of o^k)
     for (int k = RPNN_K - 1; k >= 0; --k) {
-        st = wgrad(A.t, slott(10 + k), H, dP + L.W2[k]);
-        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.b2[k], s);
-        if (st) return st;
         // da1 = (dpre W2) * (F1 > 0)
+        Buf D = buf(next++);
         TgOut o = out_to(D);
         o.mask = slot(10 + k); o.ldm = H;
         const TgSeg sd{A.b, H, W + I.W2T[k], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
+        if (!st) st = ready(D);
         if (st) return st;
-        st = wgrad(D.t, zt + (size_t)k * RPNN_DIN * ldq, RPNN_DIN, dP + L.V[k]);
-        if (!st) st = colsum_f32(c, D.f, M, H, dP + L.b1[k], s);
-        if (st) return st;
+        Buf B{};
         if (k > 0) {
-            st = wgrad(D.t, slott(k - 1), H, dP + L.W1[k]);
-            if (st) return st;
             // dpre_{k-1} = (dpre_k + da1 W1) * (o^{k-1} > 0)
+            B = buf(next++);
             TgOut o2 = out_to(B);
             o2.res = A.f; o2.ldr = H;
             o2.mask = slot(k - 1); o2.ldm = H;
             const TgSeg s1{D.b, H, W + I.W1T[k], H, H};
             st = tc_gemm(c, M, H, s1, nullptr, o2, s);
+            if (!st) st = ready(B);
             if (st) return st;
-            std::swap(A, B);
         }
+        st = wgrad(A.t, slott(10 + k), H, dP + L.W2[k]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.b2[k], ws);
+        if (!st) st = wgrad(D.t, zt + (size_t)k * RPNN_DIN * ldq, RPNN_DIN, dP + L.V[k]);
+        if (!st) st = colsum_f32(c, D.f, M, H, dP + L.b1[k], ws);
+        if (!st && k > 0) st = wgrad(D.t, slott(k - 1), H, dP + L.W1[k]);
+        if (st) return st;
+        if (k > 0) A = B;
+    }
+    if (side) {
+        // s continues only after every weight gradient is written
+        RPNN_CUDA_TRY(cudaEventRecord(c.t_events[NG + 1], side));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(s, c.t_events[NG + 1], 0));
     }
     return RPNN_OK;
 }
