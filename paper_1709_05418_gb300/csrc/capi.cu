@@ -86,7 +86,7 @@ rpnn_status train_forward(Ctx& c, const void* desc, int dtype, const float* d32,
 
 // side: a second stream for the BF16 weight gradients (null: everything on s)
 rpnn_status train_backward(Ctx& c, const float* d32, int64_t q, const float* dout, float* dP, cudaStream_t s,
-                           cudaStream_t side = nullptr) {
+                           const cudaStream_t* side = nullptr) {
     if (c.train_precision == RPNN_BF16)
         return mlp_backward_bf16_train(c, q, c.t_saved.as<float>(), c.t_saved16.as<uint16_t>(), dout, dP, s, side);
     return mlp_backward_f32(c, d32, q, c.t_saved.as<float>(), dout, dP, s);
@@ -142,14 +142,15 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
                       &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
-                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_gb32, &c->t_gb16, &c->t_desc32, &c->lm_table, &c->lmc_table};
+                      &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_gb32, &c->t_gb16, &c->t_ws2, &c->t_desc32, &c->lm_table, &c->lmc_table};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
     if (c->tuner.ev1) cudaEventDestroy(c->tuner.ev1);
     batch_release(*c);
     train_graph_release(*c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    for (cudaStream_t ss : c->side_stream)
+        if (ss) cudaStreamDestroy(ss);
     for (cudaEvent_t e : c->t_events) cudaEventDestroy(e);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     delete c;
@@ -925,15 +926,19 @@ rpnn_status train_step_body(Ctx& c, const void* desc, int32_t dtype, const float
     float* dg = c.sample_val.as<float>();
     st = launch_loss(c.t_out.as<float>(), target, (int)q, loss, dg, s);
     if (st) return st;
-    // a captured BF16 step runs the weight gradients on a second stream, beside the
+    // a captured BF16 step runs the weight gradients on two more streams, beside the
     // data-gradient chain (a direct step keeps one stream: it may time new GEMM shapes)
-    cudaStream_t side = nullptr;
+    const cudaStream_t* side = nullptr;
     cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
     RPNN_CUDA_TRY(cudaStreamIsCapturing(s, &cst));
-    if (cst == cudaStreamCaptureStatusActive && c.train_precision == RPNN_BF16 && c.side_stream &&
+    if (cst == cudaStreamCaptureStatusActive && c.train_precision == RPNN_BF16 && c.side_stream[1] &&
         (int)c.t_events.size() >= kTrainEvents)
         side = c.side_stream;
     st = train_backward(c, d32, q, dg, c.t_grad.as<float>(), s, side);
+    // a direct step sizes the second weight-gradient stream's split-K workspace like the
+    // tuner's, so that a later capture allocates nothing
+    if (!st && cst == cudaStreamCaptureStatusNone && c.train_precision == RPNN_BF16 && c.tuner.ws.bytes > 0)
+        st = c.t_ws2.reserve(c.tuner.ws.bytes);
     if (st) return st;
     st = cc ? launch_adam_dev(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, cc, adam, s)
             : launch_adam(params, m, v, c.t_grad.as<float>(), RPNN_NPARAMS, step, adam, s);
@@ -957,8 +962,9 @@ rpnn_status capture_train_step(Ctx& c, const TrainGraphKey& key, const rpnn_adam
     TrainGraph& G = c.tgraph;
     drop_train_graph(G);
     if (!c.capture_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
-    // the weight-gradient stream and its events exist before the capture starts
-    if (!c.side_stream) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
+    // the weight-gradient streams and their events exist before the capture starts
+    for (cudaStream_t& ss : c.side_stream)
+        if (!ss) RPNN_CUDA_TRY(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking));
     while ((int)c.t_events.size() < kTrainEvents) {
         cudaEvent_t ev;
         RPNN_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));

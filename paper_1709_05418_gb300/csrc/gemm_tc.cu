@@ -325,7 +325,8 @@ rpnn_status launch_tg(Ctx& c, int bn, int splits, int M, int N, const TgSeg& s0,
 
 }  // namespace
 
-rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s) {
+rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s,
+                    DevBuf* split_ws) {
     if (M <= 0 || N <= 0) return RPNN_OK;
     const TgEpiDev e = to_dev(o);
     const int Ktot = s0.K + (s1 ? s1->K : 0);
@@ -396,9 +397,10 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
     }
     float* ws = nullptr;
     if (splits > 1) {
-        rpnn_status st = tu.ws.reserve((size_t)splits * M * N * sizeof(float));
+        DevBuf& wb = split_ws ? *split_ws : tu.ws;
+        rpnn_status st = wb.reserve((size_t)splits * M * N * sizeof(float));
         if (st) return st;
-        ws = tu.ws.as<float>();
+        ws = wb.as<float>();
     }
     return launch_tg(c, bn, splits, M, N, s0, s1, e, ws, s);
 }

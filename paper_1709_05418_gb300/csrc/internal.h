@@ -203,7 +203,7 @@ struct TrainGraph {
     DevBuf desc, target, adam;        // staged minibatch, {c1, c2} of Adam's bias correction
 };
 
-constexpr int kTrainEvents = 24;   // 22 per-layer gradients, fork, join
+constexpr int kTrainEvents = 25;   // 22 per-layer gradients, fork, two joins
 
 struct Ctx {
     int device = 0;
@@ -222,7 +222,8 @@ struct Ctx {
     DevBuf t_w16, t_saved16;            // BF16 training: weight image, activation copies
     DevBuf t_gb32, t_gb16;              // BF16 training: per-layer gradients (FP32; BF16 and transposed BF16)
     std::vector<cudaEvent_t> t_events;  // BF16 training: kTrainEvents gradient-ready / fork / join events
-    cudaStream_t side_stream = nullptr; // BF16 training: weight gradients beside the data-gradient chain
+    cudaStream_t side_stream[2] = {nullptr, nullptr};   // BF16 training: weight gradients beside the
+    DevBuf t_ws2;                       // data-gradient chain; the second stream's split-K workspace
     DevBuf t_desc32;                    // FP32 widening of BF16 training descriptors (FP32 training form)
     int train_precision = RPNN_F32;     // arithmetic of rpnn_train_step / rpnn_mlp_backward
     GemmTuner tuner;
@@ -362,7 +363,10 @@ struct TgOut {
     int64_t ldm = 0;
     int relu = 0;
 };
-rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s);
+// split_ws: the split-K workspace (null: the tuner's); GEMMs that may run at the same time
+// on different streams need different workspaces
+rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, const TgOut& o, cudaStream_t s,
+                    DevBuf* split_ws = nullptr);
 
 // FP32 output layer g = relu(T3 t1 + bT3) and its backward (da3 = dout * (g > 0); dT3, dbT3
 // into dP; da2 = (da3 T3) * (t1 > 0)); bias-gradient column sums
@@ -389,7 +393,7 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
 // exact FP32 widening of n BF16 values
 rpnn_status launch_bf16_to_f32(const void* in, float* out, int64_t n, int sms, cudaStream_t s);
 rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
-                                    float* dP, cudaStream_t s, cudaStream_t side = nullptr);
+                                    float* dP, cudaStream_t s, const cudaStream_t* side = nullptr);
 
 // BF16 tensor-core network
 rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s);

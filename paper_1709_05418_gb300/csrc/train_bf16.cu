@@ -237,7 +237,7 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
 }
 
 rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const uint16_t* s16, const float* dout,
-                                    float* dP, cudaStream_t s, cudaStream_t side) {
+                                    float* dP, cudaStream_t s, const cudaStream_t* side) {
     const ParamLayout& L = param_layout();
     const TrainImage& I = train_image();
     const int M = (int)q;
@@ -248,13 +248,15 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     const uint16_t* zt = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
     // one gradient buffer per layer, each FP32 [q][200] + BF16 [q][200] + BF16 transposed
     // [200][ldq]: nothing is overwritten within a step, so the weight-gradient GEMMs and
-    // bias sums may run on `side` while the data-gradient chain continues on `s`
+    // bias sums may run on the two `side` streams (those of W2 and T on side[0], of V and W1
+    // on side[1], each with its own split-K workspace) while the data-gradient chain
+    // continues on `s`
     constexpr int NG = 22;
     const size_t per16 = (size_t)q * H + (size_t)H * ldq;
     rpnn_status st = c.t_gb32.reserve((size_t)NG * q * H * sizeof(float));
     if (!st) st = c.t_gb16.reserve((size_t)NG * per16 * 2);
     if (st) return st;
-    static_assert(NG + 2 <= kTrainEvents, "gradient-ready events");
+    static_assert(NG + 3 <= kTrainEvents, "gradient-ready events");
     if (side && (int)c.t_events.size() < kTrainEvents) { set_error("weight-gradient stream events missing"); return RPNN_ERR_STATE; }
     struct Buf { float* f; uint16_t* b; uint16_t* t; int id; };
     auto buf = [&](int i) {
@@ -268,25 +270,28 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         o.Ct = b.t; o.ldt = ldq;
         return o;
     };
-    cudaStream_t ws = side ? side : s;                 // the weight-gradient stream
-    // gradient buffer b is complete on s: let the weight-gradient stream use it
-    auto ready = [&](const Buf& b) -> rpnn_status {
+    // the weight-gradient streams (both s when there are none)
+    const cudaStream_t ws[2] = {side ? side[0] : s, side ? side[1] : s};
+    DevBuf* wsb[2] = {nullptr, side ? &c.t_ws2 : nullptr};
+    // gradient buffer b is complete on s: let weight-gradient stream w use it
+    auto ready = [&](const Buf& b, int w) -> rpnn_status {
         if (!side) return RPNN_OK;
         RPNN_CUDA_TRY(cudaEventRecord(c.t_events[b.id], s));
-        RPNN_CUDA_TRY(cudaStreamWaitEvent(side, c.t_events[b.id], 0));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(ws[w], c.t_events[b.id], 0));
         return RPNN_OK;
     };
-    auto wgrad = [&](const uint16_t* at, const uint16_t* bt, int N, float* dst) {
+    auto wgrad = [&](int w, const uint16_t* at, const uint16_t* bt, int N, float* dst) {
         // dW[j][i] = sum_m a[m][j] x[m][i]: A = a^T [200][ldq], B = x^T [N][ldq], K = q
         const TgSeg sg{at, ldq, bt, ldq, M};
         TgOut o;
         o.C = dst; o.ldc = N;
-        return tc_gemm(c, H, N, sg, nullptr, o, ws);
+        return tc_gemm(c, H, N, sg, nullptr, o, ws[w], wsb[w]);
     };
     if (side) {
-        // the weight-gradient stream starts after everything issued on s so far
+        // the weight-gradient streams start after everything issued on s so far
         RPNN_CUDA_TRY(cudaEventRecord(c.t_events[NG], s));
-        RPNN_CUDA_TRY(cudaStreamWaitEvent(side, c.t_events[NG], 0));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(ws[0], c.t_events[NG], 0));
+        RPNN_CUDA_TRY(cudaStreamWaitEvent(ws[1], c.t_events[NG], 0));
     }
     int next = 0;
     Buf A = buf(next++);
@@ -296,7 +301,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     k_train_act<<<grid_for(q * H, c.num_sms), 256, 0, s>>>(A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b),
                                                         reinterpret_cast<__nv_bfloat16*>(A.t));
     RPNN_CHECK_LAUNCH();
-    if ((st = ready(A))) return st;
+    if ((st = ready(A, 0))) return st;
     // standard layers 2 (input o^11, slot 20) and 1 (input o^10, slot 9)
     for (int t = 1; t >= 0; --t) {
         const int in = t == 1 ? 20 : 9;
@@ -305,9 +310,9 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         o.mask = slot(in); o.ldm = H;
         const TgSeg sd{A.b, H, W + I.TT[t], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
-        if (!st) st = ready(B);
-        if (!st) st = wgrad(A.t, slott(in), H, dP + L.T[t]);
-        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.bT[t], ws);
+        if (!st) st = ready(B, 0);
+        if (!st) st = wgrad(0, A.t, slott(in), H, dP + L.T[t]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.bT[t], ws[0]);
         if (st) return st;
         A = B;
     }
@@ -319,7 +324,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         o.mask = slot(10 + k); o.ldm = H;
         const TgSeg sd{A.b, H, W + I.W2T[k], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
-        if (!st) st = ready(D);
+        if (!st) st = ready(D, 1);
         if (st) return st;
         Buf B{};
         if (k > 0) {
@@ -330,21 +335,23 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
             o2.mask = slot(k - 1); o2.ldm = H;
             const TgSeg s1{D.b, H, W + I.W1T[k], H, H};
             st = tc_gemm(c, M, H, s1, nullptr, o2, s);
-            if (!st) st = ready(B);
+            if (!st) st = ready(B, 0);
             if (st) return st;
         }
-        st = wgrad(A.t, slott(10 + k), H, dP + L.W2[k]);
-        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.b2[k], ws);
-        if (!st) st = wgrad(D.t, zt + (size_t)k * RPNN_DIN * ldq, RPNN_DIN, dP + L.V[k]);
-        if (!st) st = colsum_f32(c, D.f, M, H, dP + L.b1[k], ws);
-        if (!st && k > 0) st = wgrad(D.t, slott(k - 1), H, dP + L.W1[k]);
+        st = wgrad(0, A.t, slott(10 + k), H, dP + L.W2[k]);
+        if (!st) st = colsum_f32(c, A.f, M, H, dP + L.b2[k], ws[0]);
+        if (!st) st = wgrad(1, D.t, zt + (size_t)k * RPNN_DIN * ldq, RPNN_DIN, dP + L.V[k]);
+        if (!st) st = colsum_f32(c, D.f, M, H, dP + L.b1[k], ws[1]);
+        if (!st && k > 0) st = wgrad(1, D.t, slott(k - 1), H, dP + L.W1[k]);
         if (st) return st;
         if (k > 0) A = B;
     }
     if (side) {
         // s continues only after every weight gradient is written
-        RPNN_CUDA_TRY(cudaEventRecord(c.t_events[NG + 1], side));
-        RPNN_CUDA_TRY(cudaStreamWaitEvent(s, c.t_events[NG + 1], 0));
+        for (int w = 0; w < 2; ++w) {
+            RPNN_CUDA_TRY(cudaEventRecord(c.t_events[NG + 1 + w], ws[w]));
+            RPNN_CUDA_TRY(cudaStreamWaitEvent(s, c.t_events[NG + 1 + w], 0));
+        }
     }
     return RPNN_OK;
 }
