@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
-                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, a.scale, taddr};
+                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias + (size_t)l * NP, a.w3, a.scale, taddr};
                 // four rounds of two 32-column blocks (the last has one); each ends with its
                 // block pair's publication
                 auto rounds = [&](auto kind) {

@@ -405,6 +405,11 @@ rpnn_status fused_forward_bf16(Ctx& c, const VolumeView& vv, const float* xs, co
 rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev,
                              float* out, cudaStream_t s);
 // FP8 (E4M3) tensor-core network on [q][10][256] E4M3 descriptors; needs mlp_calibrate_fp8
+// The BF16 tensor-core network on descriptor rows as the training forward: FP32 biases,
+// every layer's ReLU output stored FP32 at saved + slot * q * 200 and BF16 transposed at
+// saved_t + slot * 200 * ldq (slots as the training form's), the prediction in out.
+rpnn_status mlp_forward_bf16_saving(Ctx& c, const void* desc_bf16, int64_t q, float* out, float* saved,
+                                    uint16_t* saved_t, int64_t ldq, cudaStream_t s);
 rpnn_status mlp_forward_fp8(Ctx& c, const void* desc_fp8, int64_t q, const int* q_dev, float* out,
                             cudaStream_t s);
 // Per-tensor scales from the FP32 network on q FP32 descriptors [q][10][240]; builds the

@@ -85,7 +85,9 @@ static_assert(OFF_W % 1024 == 0 && OFF_Z % 1024 == 0 && W_STAGE % 1024 == 0 && Z
               "swizzled operand blocks must stay 1024-byte aligned");
 static_assert(SMEM_BYTES <= 232448, "shared memory over the per-block limit");
 
-template <class F>
+// TRAIN: the training forward (BF16): FP32 biases in the epilogue, every layer's output
+// stored for the backward (TcArgs::tsave), no padding-column bias trick.
+template <class F, bool TRAIN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -210,7 +212,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                             tc::mbar_wait_issuer(S.blk0 + BAR_STRIDE * (npub<F>() - 1), pb, tc::kSpinLimit, S.abort_addr);
                     } else if (l < 20 && !(l & 1)) {
                         issue_layer<W_STAGES, Z_STAGES, F::FP8, F::KZB + F::XB, F::KZB, false, false>(S, acc, pb);
-                    } else if (layer_resid(l)) {
+                    } else if (layer_resid(l) && !TRAIN) {
+                        // (the training form adds the residual in its epilogue)
                         issue_layer<W_STAGES, Z_STAGES, F::FP8, F::XB, 0, true>(S, acc, pb);
                     } else {
                         issue_layer<W_STAGES, Z_STAGES, F::FP8, F::XB, 0, false>(S, acc, pb);
@@ -252,12 +255,28 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (n & 1u) * 256u + 16u * half;
                 float v[NBLK * 16];
                 tc::tmem_ld16x7(taddr, v);
-                const EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias, a.w3, a.scale, taddr};
+                // the FP32 bias row of layer l (BF16 renders add it only for layer 0; the E4M3
+                // and training forms for every layer)
+                EpiArgs ea{Xsm, row, sw, half, lane, bar(B_BLK), a.bias + (size_t)l * NP, a.w3, a.scale, taddr};
+                if (TRAIN) {
+                    const int64_t r = (int64_t)t * TM + row;
+                    // saved slot of layer l: F1^k (l = 2k - 2) at 10 + k - 1, o^k (l = 2k - 1)
+                    // at k - 1, o^11 and o^12 at 20 and 21
+                    const int slot = l >= 20 ? l : ((l & 1) ? (l >> 1) : 10 + (l >> 1));
+                    if (r < Q) {
+                        ea.tf = a.tsave + ((int64_t)slot * a.tq + r) * RPNN_H;
+                        ea.tt = a.tsave_t + (int64_t)slot * RPNN_H * a.tldq + r;
+                        ea.tldq = a.tldq;
+                        // second layers k >= 2 add o^{k-1} (slot k - 2), which this thread
+                        // stored two layers earlier
+                        if (layer_resid(l)) ea.tres = a.tsave + ((int64_t)((l >> 1) - 1) * a.tq + r) * RPNN_H;
+                    }
+                }
                 // one straight-line routine per layer kind
-                if (l == 0) epi_layer<F, EPI_FIRST>(ea, v, dot, dot1, l);
-                else if (l == 21) epi_layer<F, EPI_LAST>(ea, v, dot, dot1, l);
-                else if (layer_keeps_o(l)) epi_layer<F, EPI_KEEP>(ea, v, dot, dot1, l);
-                else epi_layer<F, EPI_PLAIN>(ea, v, dot, dot1, l);
+                if (l == 0) epi_layer<F, EPI_FIRST, TRAIN>(ea, v, dot, dot1, l);
+                else if (l == 21) epi_layer<F, EPI_LAST, TRAIN>(ea, v, dot, dot1, l);
+                else if (layer_keeps_o(l)) epi_layer<F, EPI_KEEP, TRAIN>(ea, v, dot, dot1, l);
+                else epi_layer<F, EPI_PLAIN, TRAIN>(ea, v, dot, dot1, l);
             }
             if (!ok) break;
             // combine the column quarters' partial dot products of the output layer: half 1
@@ -397,9 +416,10 @@ __global__ void k_slot_max(const float* __restrict__ saved, int64_t q, int nslot
 
 // Launch of the network kernel in format F on q descriptor rows (q_dev: device count, or
 // null).
-template <class F>
+// TRAIN: tsave / tsave_t / ldq receive the saved activations (TcArgs::tsave).
+template <class F, bool TRAIN = false>
 rpnn_status forward_tc(Ctx& c, const DevBuf& image, const void* desc, int64_t q, const int* q_dev, float* out,
-                       cudaStream_t s) {
+                       cudaStream_t s, float* tsave = nullptr, uint16_t* tsave_t = nullptr, int64_t ldq = 0) {
     if (q <= 0) return RPNN_OK;
     if ((reinterpret_cast<uintptr_t>(desc) & 15u) != 0) {
         set_error("descriptor rows must be 16-byte aligned");
@@ -429,14 +449,18 @@ rpnn_status forward_tc(Ctx& c, const DevBuf& image, const void* desc, int64_t q,
     a.q_dev = q_dev;
     a.out = out;
     a.status = c.status.as<uint32_t>();
+    a.tsave = tsave;
+    a.tsave_t = tsave_t;
+    a.tq = q;
+    a.tldq = ldq;
     static bool attr = false;
     if (!attr) {
-        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_rpnn_tc<F, TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
         attr = true;
     }
     const int64_t ntiles = (q + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, c.num_sms);
-    k_rpnn_tc<F><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
+    k_rpnn_tc<F, TRAIN><<<grid, NTHREADS, SMEM_BYTES, s>>>(zmap, a);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }
@@ -461,6 +485,12 @@ rpnn_status mlp_build_bf16_image(Ctx& c, cudaStream_t s) {
 rpnn_status mlp_forward_bf16(Ctx& c, const void* desc_bf16, int64_t q, const int* q_dev, float* out,
                              cudaStream_t s) {
     return forward_tc<FmtBF16>(c, c.wimg_bf16, desc_bf16, q, q_dev, out, s);
+}
+
+rpnn_status mlp_forward_bf16_saving(Ctx& c, const void* desc_bf16, int64_t q, float* out, float* saved,
+                                    uint16_t* saved_t, int64_t ldq, cudaStream_t s) {
+    if (q <= 0) return RPNN_OK;
+    return forward_tc<FmtBF16, true>(c, c.wimg_bf16, desc_bf16, q, nullptr, out, s, saved, saved_t, ldq);
 }
 
 rpnn_status mlp_forward_fp8(Ctx& c, const void* desc_fp8, int64_t q, const int* q_dev, float* out, cudaStream_t s) {

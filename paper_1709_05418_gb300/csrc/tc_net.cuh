@@ -50,6 +50,12 @@ struct TcArgs {
     const int* q_dev;
     float* out;
     uint32_t* status;
+    // training forward (k_rpnn_tc<FmtBF16, true>): every layer's ReLU output is also stored
+    // FP32 [slot][q][200] and BF16 transposed [slot][200][ldq] for the backward (slot: o^k
+    // at k - 1, F1^k at 10 + k - 1, o^11 at 20, o^12 at 21)
+    float* tsave;
+    uint16_t* tsave_t;
+    int64_t tq, tldq;
 };
 
 // K bytes of layer l: a block's first layer reads [z | o] (block 1 has no o), every other
@@ -168,10 +174,14 @@ struct EpiArgs {
     unsigned char* X;
     int row, sw, half, lane;
     uint32_t blk_bar;             // publication barrier 0 (the others follow at BAR_STRIDE)
-    const float* bias;            // FP32 bias table (BF16: block 1's first layer only)
+    const float* bias;            // this layer's FP32 biases (BF16 renders: used by layer 0 only)
     const float* w3;              // output layer weights
     const float* scale;           // FP8 per-layer scales, or null
     uint32_t taddr;               // the warp's accumulator columns
+    float* tf;                    // training forward: this row's FP32 output, or null
+    uint16_t* tt;                 // training forward: this row's column 0 of the transposed output
+    int64_t tldq;                 // its pitch
+    const float* tres;            // training forward: this row's FP32 residual o^{k-1}, or null
 };
 
 // KIND: EPI_PLAIN ReLU + BF16; EPI_KEEP also writes o^k back into the accumulator (the next
@@ -182,7 +192,11 @@ struct EpiArgs {
 // into v (chunk B0 + i at v[16 i ..]); epi_layer is the whole layer in one call.
 // One 16-column chunk of one layer for the warp's 32 rows: columns 32 b + 16 half .. +15,
 // accumulator values in w; u, qs, ku are the FP8 scales (1 for BF16).
-template <class F, int KIND>
+// TRAIN (training forward, BF16): biases are FP32 and added here for every layer (the
+// activation's padding column 200 stays 0), a second layer's residual is added here too
+// (from e.tres, after the bias, as the GEMM form adds it; the accumulator starts at zero),
+// and the ReLU output also goes to e.tf / e.tt.
+template <class F, int KIND, bool TRAIN = false>
 __device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, float* w, float& dot, float u, float qs,
                                           float ku) {
     const int c0 = 32 * b + 16 * half;
@@ -193,7 +207,7 @@ __device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, flo
 #pragma unroll
         for (int i = 0; i < 16; ++i) w[i] *= u;
     }
-    if (F::FP8 || KIND == EPI_FIRST) {
+    if (F::FP8 || KIND == EPI_FIRST || TRAIN) {
         const float4* b4 = reinterpret_cast<const float4*>(e.bias + c0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -201,11 +215,35 @@ __device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, flo
             w[4 * q] += bb.x; w[4 * q + 1] += bb.y; w[4 * q + 2] += bb.z; w[4 * q + 3] += bb.w;
         }
     }
-    if (KIND == EPI_KEEP || KIND == EPI_LAST) {
+    if (TRAIN && e.tres) {
+        const float4* r4 = reinterpret_cast<const float4*>(e.tres + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + 4 * q < RPNN_H) {
+                const float4 rr = r4[q];
+                w[4 * q] += rr.x; w[4 * q + 1] += rr.y; w[4 * q + 2] += rr.z; w[4 * q + 3] += rr.w;
+            }
+        }
+    }
+    if (KIND == EPI_KEEP || KIND == EPI_LAST || TRAIN) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
     }
-    if (KIND == EPI_KEEP && !F::FP8) tc::tmem_st16(e.taddr + 32u * b + 16u * (half - e.half), w);
+    if (TRAIN && e.tf) {
+        // columns c0 .. c0 + 15 of the row, the 200 real ones: FP32 row-major (16-byte
+        // stores) and BF16 transposed (a warp's 32 rows are 64 contiguous bytes per column)
+        float4* f4 = reinterpret_cast<float4*>(e.tf + c0);
+        f4[0] = make_float4(w[0], w[1], w[2], w[3]);
+        f4[1] = make_float4(w[4], w[5], w[6], w[7]);
+        if (c0 + 16 <= RPNN_H) {
+            f4[2] = make_float4(w[8], w[9], w[10], w[11]);
+            f4[3] = make_float4(w[12], w[13], w[14], w[15]);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (c0 + i < RPNN_H) e.tt[(int64_t)(c0 + i) * e.tldq] = __bfloat16_as_ushort(__float2bfloat16_rn(w[i]));
+    }
+    if (KIND == EPI_KEEP && !F::FP8 && !TRAIN) tc::tmem_st16(e.taddr + 32u * b + 16u * (half - e.half), w);
     if (KIND == EPI_LAST) {
         const float4* w4 = reinterpret_cast<const float4*>(e.w3 + c0);
 #pragma unroll
@@ -246,7 +284,7 @@ __device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, flo
             }
         }
         // column 200 carries the constant 1 that multiplies the next layer's bias
-        if (c0 == 192) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
+        if (!TRAIN && c0 == 192) u1[0] = (u1[0] & 0xFFFF0000u) | 0x3F80u;
         // 64-byte swizzled row: 16-byte unit u of row r at u ^ ((r >> 1) & 3)
         unsigned char* rb = e.X + b * BLK_A + e.row * 64;
         *reinterpret_cast<uint4*>(rb + (((2 * half) ^ e.sw) << 4)) = p0;
@@ -276,20 +314,20 @@ template <class F> __device__ __forceinline__ float4 epi_scales(const EpiArgs& e
 // published as each 128-byte range of the activation is complete; epi_layer is the whole
 // layer in one call.  The output layer's dot product runs as two FMA chains, over the
 // even blocks (dot0) and the odd blocks (dot1), the column quarters of the sum below.
-template <class F, int KIND, int B0, int NB>
+template <class F, int KIND, int B0, int NB, bool TRAIN = false>
 __device__ __forceinline__ void epi_blocks(const EpiArgs& e, float (&v)[NB * 16], float& dot0, float& dot1, int l) {
     const float4 sc = epi_scales<F>(e, l);
 #pragma unroll
     for (int b = B0; b < B0 + NB; ++b) {
-        epi_chunk<F, KIND>(e, b, e.half, v + 16 * (b - B0), (b & 1) ? dot1 : dot0, sc.x, sc.y, sc.z);
+        epi_chunk<F, KIND, TRAIN>(e, b, e.half, v + 16 * (b - B0), (b & 1) ? dot1 : dot0, sc.x, sc.y, sc.z);
         constexpr int CB = 32 * F::EB;                    // activation bytes of one block
         if (((b + 1) * CB) % SKB == 0 || b == NBLK - 1) epi_publish<KIND>(e, (b * CB) / SKB, b == NBLK - 1);
     }
 }
 
-template <class F, int KIND>
+template <class F, int KIND, bool TRAIN = false>
 __device__ __forceinline__ void epi_layer(const EpiArgs& e, float (&v)[NBLK * 16], float& dot0, float& dot1, int l) {
-    epi_blocks<F, KIND, 0, NBLK>(e, v, dot0, dot1, l);
+    epi_blocks<F, KIND, 0, NBLK, TRAIN>(e, v, dot0, dot1, l);
 }
 
 // The prediction g = relu(T3 . o12 + bT3) from the column quarters' partial dot products:

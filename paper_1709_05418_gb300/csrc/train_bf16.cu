@@ -1,14 +1,14 @@
 // train_bf16.cu -- mixed-precision training form of the network (Sec. 4.3 forward, Sec. 5.2
-// chain rule): every 200-wide layer and every weight gradient is a BF16 tensor-core GEMM
-// (gemm_tc.cu) with FP32 accumulation; biases, residual sums, ReLU masks, saved
-// activations, the loss, the gradients and the Adam step stay FP32 (FP32 master weights).
-// The 1-wide output layer and its gradients, which have a K or N of 1, run on the FP32
-// CUDA-core GEMM.
+// chain rule): the forward runs in the persistent tensor-core network kernel in its training
+// form (mlp_tc.cu); every data gradient and weight gradient is a BF16 tensor-core GEMM
+// (gemm_tc.cu) with FP32 accumulation; biases, residual sums, ReLU masks, saved activations,
+// the loss, the gradients and the Adam step stay FP32 (FP32 master weights).  The 1-wide
+// output layer's gradients, which have a K or N of 1, run on the FP32 CUDA-core GEMM.
 //
-// Each 200-wide activation is stored three times by the epilogue of the GEMM that makes
-// it: FP32 [q][200] (residual input, ReLU mask), BF16 [q][200] (A operand of the next
-// layer and of the data gradients) and BF16 transposed [200][ldq] (operand of the weight
-// gradients, which sum over the q rows); ldq = q rounded up to 8 elements.
+// Each 200-wide activation is stored twice by the forward: FP32 [q][200] (residual input,
+// ReLU mask) and BF16 transposed [200][ldq] (operand of the weight gradients, which sum over
+// the q rows); ldq = q rounded up to 8 elements.  (The BF16 [q][200] slots ahead of the
+// transposed ones in the saved buffer are no longer written.)
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -170,17 +170,10 @@ rpnn_status train_build_image(Ctx& c, cudaStream_t s) {
 // o^11, o^12, then g) in `saved`, BF16 copies in `s16` (train_bf16_saved_elems(q)).
 rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int64_t q, float* out, float* saved,
                                    uint16_t* s16, cudaStream_t s) {
-    const ParamLayout& L = param_layout();
-    const TrainImage& I = train_image();
-    const float* P = c.params32.as<float>();
-    const int M = (int)q;
     const int64_t ldq = train_ldq(q);
+    // the transposed weight image the backward reads
     rpnn_status st = train_build_image(c, s);
     if (st) return st;
-    const uint16_t* W = c.t_w16.as<uint16_t>();
-    auto slot = [&](int i) { return saved + (size_t)i * q * H; };
-    auto slotb = [&](int i) { return s16 + (size_t)i * q * H; };
-    auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
     uint16_t* zb = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq;
     uint16_t* zt = zb + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
     if (desc_dtype == RPNN_BF16)
@@ -192,45 +185,10 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
             static_cast<const float*>(desc), q, ldq, reinterpret_cast<__nv_bfloat16*>(zb),
             reinterpret_cast<__nv_bfloat16*>(zt));
     RPNN_CHECK_LAUNCH();
-    for (int k = 0; k < RPNN_K; ++k) {
-        // F1 = relu([z^k | o^{k-1}] [V^k | W1^k]^T + b1)
-        const TgSeg sz{zb + (size_t)k * RPNN_DESC_STRIDE, (int64_t)RPNN_K * RPNN_DESC_STRIDE, W + I.V[k], VLD, RPNN_DIN};
-        TgOut o1;
-        o1.C = slot(10 + k); o1.ldc = H;
-        o1.Cb = slotb(10 + k); o1.ldb = H;
-        o1.Ct = slott(10 + k); o1.ldt = ldq;
-        o1.bias = P + L.b1[k]; o1.relu = 1;
-        if (k > 0) {
-            const TgSeg so{slotb(k - 1), H, W + I.W1[k], H, H};
-            st = tc_gemm(c, M, H, sz, &so, o1, s);
-        } else {
-            st = tc_gemm(c, M, H, sz, nullptr, o1, s);
-        }
-        if (st) return st;
-        // o^k = relu(W2 F1 + b2 + o^{k-1})
-        const TgSeg sf{slotb(10 + k), H, W + I.W2[k], H, H};
-        TgOut o2;
-        o2.C = slot(k); o2.ldc = H;
-        o2.Cb = slotb(k); o2.ldb = H;
-        o2.Ct = slott(k); o2.ldt = ldq;
-        o2.bias = P + L.b2[k]; o2.relu = 1;
-        if (k > 0) { o2.res = slot(k - 1); o2.ldr = H; }
-        st = tc_gemm(c, M, H, sf, nullptr, o2, s);
-        if (st) return st;
-    }
-    // standard layers o^11 (slot 20), o^12 (slot 21), then the 1-wide output on CUDA cores
-    for (int t = 0; t < 2; ++t) {
-        const int in = t == 0 ? 9 : 20, outs = 20 + t;
-        const TgSeg sx{slotb(in), H, W + I.T[t], H, H};
-        TgOut o;
-        o.C = slot(outs); o.ldc = H;
-        o.Cb = slotb(outs); o.ldb = H;
-        o.Ct = slott(outs); o.ldt = ldq;
-        o.bias = P + L.bT[t]; o.relu = 1;
-        st = tc_gemm(c, M, H, sx, nullptr, o, s);
-        if (st) return st;
-    }
-    st = mlp_output_layer_f32(c, slot(21), q, out, s);
+    // the 22 layers in the persistent tensor-core network kernel (one 128-row tile per CTA,
+    // layer after layer in shared and tensor memory), in its training form: FP32 biases in
+    // the epilogue, every ReLU output stored FP32 and BF16 transposed for the backward
+    st = mlp_forward_bf16_saving(c, zb, q, out, saved, s16 + (size_t)22 * q * H, ldq, s);
     if (st) return st;
     RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return RPNN_OK;

@@ -80,9 +80,10 @@ def _queries(q, seed):
 def test_fp8_descriptor_is_e4m3_of_fp32(ctx, blob_vol):
     x, d, wl = _queries(257, seed=31)
     g32 = ctx.extract_descriptors(blob_vol, cuda(x), cuda(d), cuda(wl))
-    g8 = ctx.extract_descriptors(blob_vol, cuda(x), cuda(d), cuda(wl), dtype=torch.uint8)
+    g8 = ctx.extract_descriptors(blob_vol, cuda(x), cuda(d), cuda(wl), dtype=torch.uint8).cpu()
     assert g8.shape == (257, 10, 256)
-    ref = g32.to(torch.float8_e4m3fn).view(torch.uint8)
+    # the E4M3 rounding of the FP32 descriptor, taken on the CPU
+    ref = g32.cpu().to(torch.float8_e4m3fn).view(torch.uint8)
     assert torch.equal(g8[:, :, :240], ref)
     assert int(g8[:, :, 240:].sum()) == 0
 
@@ -141,3 +142,37 @@ def test_fp8_render_within_budget(ctx, api, blob, blob_vol, blob_orc, params, ca
     with capsys.disabled():
         print(f"\n[fp8] image rel L2 vs FP64 oracle: FP8 {err:.4f}, BF16 {_rel_l2(bf, ref):.4f}")
     assert err <= FP8_IMG_REL, err
+
+
+def test_networks_with_distinct_layer_biases(ctx, api, blob_vol, blob_orc):
+    """Every layer with its own nonzero biases (trained networks have them; He
+    initialisation sets them to zero): the E4M3 network, which adds each layer's FP32 bias
+    in its epilogue, and the BF16 one, whose weight image carries them, stay within their
+    budgets against the FP64 oracle."""
+    params = W.he_init(seed=5)
+    parts = W.split_params(params)
+    rng = np.random.default_rng(6)
+    flat, off = params.copy(), 0
+    for name, arr in parts.items():
+        if name.startswith("b"):
+            flat[off:off + arr.size] = rng.normal(0.0, 0.05, size=arr.size)
+        off += arr.size
+    ctx.set_weights(cuda(flat))
+    xc, dc, wlc = _queries(2048, seed=41)
+    ctx.calibrate_fp8(ctx.extract_descriptors(blob_vol, cuda(xc), cuda(dc), cuda(wlc)))
+    x, d, wl = _queries(333, seed=12)
+    z32 = blob_orc.descriptor(x, d, wl, f32=True)
+    ref = oracle.mlp_forward(flat.astype(np.float64), z32.astype(np.float64))
+    assert (ref > 0).mean() > 0.2
+    zp = np.zeros((333, 10, 256), np.float32)
+    zp[:, :, :226] = z32
+    z8 = torch.from_numpy(zp).to(torch.float8_e4m3fn).view(torch.uint8).cuda()
+    g8 = ctx.mlp_forward(z8, precision=api.FP8).cpu().numpy().astype(np.float64)
+    zb = torch.from_numpy(zp[:, :, :240].copy()).to(torch.bfloat16).cuda()
+    g16 = ctx.mlp_forward(zb, precision=api.BF16).cpu().numpy().astype(np.float64)
+    ctx.sync_status()
+    scale = np.maximum(np.abs(ref), np.median(np.abs(ref)))
+    assert _rel_l2(g8, ref) <= FP8_REL, _rel_l2(g8, ref)
+    assert np.all(np.abs(g8 - ref) <= FP8_ELEM * scale)
+    assert _rel_l2(g16, ref) <= 1e-2, _rel_l2(g16, ref)
+
