@@ -235,6 +235,16 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         // warps 2-5, 1 for warps 6-9).  All 7 chunks are loaded in one round trip; each
         // finished block pair is published on its own barrier so the next layer's MMAs can
         // start on it while later blocks are still being written.
+        // The E4M3 and training forms read a different FP32 bias row in every layer's
+        // epilogue; fetched from L2 there, each row's first use would sit on the layer chain.
+        // The table (22 x 208 floats, 18 KB) and the E4M3 scales go to L1 once, here.
+        if (F::FP8 || TRAIN) {
+            const int et = tid - 64;
+            for (int i = et; i < (int)(NLAYERS * NP * 4 / 128); i += 32 * EPI_WARPS)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(a.bias + 32 * i));
+            if (F::FP8 && et < (int)(NLAYERS * 16 + 127) / 128)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(a.scale + 32 * et));
+        }
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
