@@ -361,14 +361,14 @@ def run_batch(args, ws, rank, local):
 
 
 def train_launches(tab, bf16, batch):
-    """Kernels of one training step.  FP32: 23 forward GEMMs, the loss, 78 backward launches
+    """Kernels of one training step.  FP32: 23 forward GEMMs, the loss (2), 78 backward launches
     (GEMMs, bias-gradient sums, one mask), Adam and the BF16 render image.  BF16: the training
     weight image and descriptor conversion, the forward (one launch of the persistent
-    tensor-core network in its training form), the loss, 4 output-layer backward launches,
+    tensor-core network in its training form), the loss (2), 4 output-layer backward launches,
     1 conversion, 74 backward GEMMs and sums, Adam and the render image.  Plus one reduction
     per split-K weight-gradient GEMM: the 200 x 200 shape runs 21 times a step (T1, T2, W2 x 10,
     W1 x 9), the 200 x 226 one 10 times, the 1 x 200 once."""
-    n = 85 if bf16 else 104
+    n = 86 if bf16 else 105
     for e in tab:
         if e["splits"] <= 1 or e["K0"] != batch:
             continue

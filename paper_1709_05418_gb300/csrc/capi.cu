@@ -141,7 +141,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     }
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,
                       &c->q_count, &c->sample_val, &c->desc, &c->g_out, &c->act0, &c->act1,
-                      &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->light,
+                      &c->act2, &c->t_saved, &c->t_grad, &c->t_dg, &c->t_out, &c->t_loss, &c->t_lpart, &c->light,
                       &c->tuner.scratch, &c->tuner.ws, &c->t_w16, &c->t_saved16, &c->t_gb32, &c->t_gb16, &c->t_ws2, &c->t_desc32, &c->lm_table, &c->lmc_table};
     for (DevBuf* b : bufs) b->release();
     if (c->tuner.ev0) cudaEventDestroy(c->tuner.ev0);
@@ -672,7 +672,7 @@ rpnn_status rpnn_dense_train_step(rpnn_ctx* ctx, const int32_t* widths, int32_t 
     if (!st) st = dense_fwd_saved(*c, widths, n_hidden, din, dev_params, dev_in, batch, s);
     if (st) return st;
     float* dg = c->sample_val.as<float>();
-    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
+    st = launch_loss(*c, c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
     if (!st) st = dense_backward(*c, widths, n_hidden, din, dev_params, dev_in, batch, c->t_saved.as<float>(), dg,
                                  c->t_grad.as<float>(), s);
     if (st) return st;
@@ -768,7 +768,7 @@ rpnn_status rpnn_stencil_train_step(rpnn_ctx* ctx, int32_t n_xy, const float* de
     if (!st) st = stencil_fwd_saved(*c, nd, dev_params, dev_desc, batch, s);
     if (st) return st;
     float* dg = c->sample_val.as<float>();
-    st = launch_loss(c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
+    st = launch_loss(*c, c->t_out.as<float>(), dev_target, batch, dev_loss, dg, s);
     if (!st) st = rpnn_backward_f32(*c, nd, dev_params, dev_desc, batch, c->t_saved.as<float>(), dg,
                                     c->t_grad.as<float>(), s);
     if (st) return st;
@@ -924,7 +924,7 @@ rpnn_status train_step_body(Ctx& c, const void* desc, int32_t dtype, const float
     if (!st) st = train_forward(c, desc, dtype, d32, q, s);
     if (st) return st;
     float* dg = c.sample_val.as<float>();
-    st = launch_loss(c.t_out.as<float>(), target, (int)q, loss, dg, s);
+    st = launch_loss(c, c.t_out.as<float>(), target, (int)q, loss, dg, s);
     if (st) return st;
     // a captured BF16 step runs the weight gradients on two more streams, beside the
     // data-gradient chain (a direct step keeps one stream: it may time new GEMM shapes)

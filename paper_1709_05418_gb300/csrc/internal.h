@@ -219,6 +219,7 @@ struct Ctx {
     DevBuf q_x, q_d, q_ps, q_count, sample_val, desc, g_out, act0, act1, act2, light;
     // training scratch
     DevBuf t_saved, t_grad, t_dg, t_out, t_loss;
+    DevBuf t_lpart;                     // block sums of the loss
     DevBuf t_w16, t_saved16;            // BF16 training: weight image, activation copies
     DevBuf t_gb32, t_gb16;              // BF16 training: per-layer gradients (FP32; BF16 and transposed BF16)
     std::vector<cudaEvent_t> t_events;  // BF16 training: kTrainEvents gradient-ready / fork / join events
@@ -327,7 +328,7 @@ size_t mlp_saved_floats_per_row();
 void gemm_tile_shape(int tile, int* bm, int* bn, int* bk);
 // index of the tile (bm, bn, bk) in that table, or -1
 int gemm_tile_index(int bm, int bn, int bk);
-rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss,
+rpnn_status launch_loss(Ctx& c, const float* g, const float* target, int batch, double* loss,
                         float* dg, cudaStream_t s);
 rpnn_status launch_adam(float* p, float* m, float* v, const float* grad, int64_t n,
                         int64_t step, const rpnn_adam_cfg& cfg, cudaStream_t s);

@@ -320,22 +320,34 @@ rpnn_status gemm(Ctx* c, int M, const int* M_dev, int N, const Seg& s0, const Se
 }
 
 // Deterministic log-MSE loss (Sec. 5.2): one block; FP64 tree reduction.
-__global__ void k_loss(const float* __restrict__ g, const float* __restrict__ t, int B,
-                       double* loss, float* __restrict__ dg) {
-    __shared__ double red[1024];
+// log-MSE loss (Sec. 5.2): per element r = log1p(g) - log1p(t) and dl/dg = 2 r / ((1 + g) B)
+// in FP64, block sums of r^2 in a fixed tree, then the block sums in block order.  Spread
+// over blocks: an FP64 log1p per element on one SM took tens of microseconds per step.
+constexpr int kLossThreads = 256, kLossBlocks = 64;
+__global__ void k_loss_terms(const float* __restrict__ g, const float* __restrict__ t, int B,
+                             double* __restrict__ part, float* __restrict__ dg) {
+    __shared__ double red[kLossThreads];
     double s = 0.0;
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    for (int i = blockIdx.x * kLossThreads + threadIdx.x; i < B; i += gridDim.x * kLossThreads) {
         const double r = log1p((double)g[i]) - log1p((double)t[i]);
         s += r * r;
         dg[i] = (float)(2.0 * r / ((1.0 + (double)g[i]) * (double)B));
     }
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = red[0] / (double)B;
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_loss_sum(const double* __restrict__ part, int nb, int B, double* loss) {
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[b];
+        *loss = s / (double)B;
+    }
 }
 
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -677,9 +689,14 @@ rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const floa
     return RPNN_OK;
 }
 
-rpnn_status launch_loss(const float* g, const float* target, int batch, double* loss, float* dg,
+rpnn_status launch_loss(Ctx& c, const float* g, const float* target, int batch, double* loss, float* dg,
                         cudaStream_t s) {
-    k_loss<<<1, 1024, 0, s>>>(g, target, batch, loss, dg);
+    rpnn_status st = c.t_lpart.reserve(kLossBlocks * sizeof(double));
+    if (st) return st;
+    const int nb = std::max(1, std::min(kLossBlocks, (batch + kLossThreads - 1) / kLossThreads));
+    k_loss_terms<<<nb, kLossThreads, 0, s>>>(g, target, batch, c.t_lpart.as<double>(), dg);
+    RPNN_CHECK_LAUNCH();
+    k_loss_sum<<<1, 32, 0, s>>>(c.t_lpart.as<double>(), nb, batch, loss);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }

@@ -82,19 +82,37 @@ __device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 v) { return v; }
 
 // z [q][10][240] FP32 or BF16 -> zb [q][10][240] BF16 and zt [10][226][ldq] BF16 (per level,
 // transposed); FP32 values are rounded to nearest even, BF16 values copied
+// Training descriptors -> BF16 rows zb [q][10][240] (FP32 input only: BF16 input is used in
+// place) and the transposed copy zt [10 * 226][ldq] the V^k weight gradients read, through
+// 32 x 32 shared-memory tiles (rows m read along the columns, written along m).
 template <class T>
 __global__ void k_train_desc(const T* __restrict__ z, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ zb,
                              __nv_bfloat16* __restrict__ zt) {
     const int64_t row = (int64_t)RPNN_K * RPNN_DESC_STRIDE;
-    const int64_t total = q * row;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-        zb[i] = to_bf16(z[i]);
-    // transposed copy: consecutive threads take consecutive rows m of one (level, column)
-    const int64_t ttotal = (int64_t)RPNN_K * RPNN_DIN * q;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ttotal; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i % q, lc = i / q;
-        const int k = (int)(lc / RPNN_DIN), c = (int)(lc % RPNN_DIN);
-        zt[((int64_t)k * RPNN_DIN + c) * ldq + m] = to_bf16(z[m * row + (int64_t)k * RPNN_DESC_STRIDE + c]);
+    if (zb) {
+        const int64_t total = q * row;
+        const int64_t stride = (int64_t)gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+        const int64_t t0 = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+                           threadIdx.y * blockDim.x + threadIdx.x;
+        for (int64_t i = t0; i < total; i += stride) zb[i] = to_bf16(z[i]);
+    }
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int ncol = RPNN_K * RPNN_DIN;                      // 2260 transposed rows
+    const int lc0 = blockIdx.y * 32;
+    const int64_t m0 = (int64_t)blockIdx.x * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int64_t m = m0 + yy;
+        const int lc = lc0 + threadIdx.x;
+        if (m < q && lc < ncol) {
+            const int k = lc / RPNN_DIN, c = lc - k * RPNN_DIN;
+            tile[yy][threadIdx.x] = to_bf16(z[m * row + (int64_t)k * RPNN_DESC_STRIDE + c]);
+        }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int lc = lc0 + yy;
+        const int64_t m = m0 + threadIdx.x;
+        if (m < q && lc < ncol) zt[(int64_t)lc * ldq + m] = tile[threadIdx.x][yy];
     }
 }
 
@@ -103,15 +121,27 @@ __global__ void k_bf16_to_f32(const __nv_bfloat16* __restrict__ in, float* __res
         out[i] = __bfloat162float(in[i]);
 }
 
-// x [q][200] FP32 -> BF16 [q][200] and transposed BF16 [200][ldq]
+// x [q][200] FP32 -> BF16 [q][200] and transposed BF16 [200][ldq], through 32 x 32
+// shared-memory tiles
 __global__ void k_train_act(const float* __restrict__ x, int64_t q, int64_t ldq, __nv_bfloat16* __restrict__ xb,
                             __nv_bfloat16* __restrict__ xt) {
-    const int64_t total = q * H;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = i % q, n = i / q;
-        const __nv_bfloat16 b = __float2bfloat16_rn(x[m * H + n]);
-        xb[m * H + n] = b;
-        xt[n * ldq + m] = b;
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int n0 = blockIdx.y * 32;
+    const int64_t m0 = (int64_t)blockIdx.x * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int64_t m = m0 + yy;
+        const int n = n0 + threadIdx.x;
+        if (m < q && n < H) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(x[m * H + n]);
+            xb[m * H + n] = b;
+            tile[yy][threadIdx.x] = b;
+        }
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int n = n0 + yy;
+        const int64_t m = m0 + threadIdx.x;
+        if (m < q && n < H) xt[(int64_t)n * ldq + m] = tile[threadIdx.x][yy];
     }
 }
 
@@ -176,19 +206,23 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
     if (st) return st;
     uint16_t* zb = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq;
     uint16_t* zt = zb + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
-    if (desc_dtype == RPNN_BF16)
-        k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
-            static_cast<const __nv_bfloat16*>(desc), q, ldq, reinterpret_cast<__nv_bfloat16*>(zb),
-            reinterpret_cast<__nv_bfloat16*>(zt));
-    else
-        k_train_desc<<<grid_for(q * RPNN_K * RPNN_DESC_STRIDE, c.num_sms), 256, 0, s>>>(
-            static_cast<const float*>(desc), q, ldq, reinterpret_cast<__nv_bfloat16*>(zb),
-            reinterpret_cast<__nv_bfloat16*>(zt));
+    const dim3 tgrid((unsigned)((q + 31) / 32), (RPNN_K * RPNN_DIN + 31) / 32);
+    // BF16 records are the forward's operand as they are; FP32 ones are rounded into zb
+    const void* zfwd = desc;
+    if (desc_dtype == RPNN_BF16) {
+        k_train_desc<<<tgrid, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16*>(desc), q, ldq, nullptr,
+                                                  reinterpret_cast<__nv_bfloat16*>(zt));
+    } else {
+        k_train_desc<<<tgrid, dim3(32, 8), 0, s>>>(static_cast<const float*>(desc), q, ldq,
+                                                  reinterpret_cast<__nv_bfloat16*>(zb),
+                                                  reinterpret_cast<__nv_bfloat16*>(zt));
+        zfwd = zb;
+    }
     RPNN_CHECK_LAUNCH();
     // the 22 layers in the persistent tensor-core network kernel (one 128-row tile per CTA,
     // layer after layer in shared and tensor memory), in its training form: FP32 biases in
     // the epilogue, every ReLU output stored FP32 and BF16 transposed for the backward
-    st = mlp_forward_bf16_saving(c, zb, q, out, saved, s16 + (size_t)22 * q * H, ldq, s);
+    st = mlp_forward_bf16_saving(c, zfwd, q, out, saved, s16 + (size_t)22 * q * H, ldq, s);
     if (st) return st;
     RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return RPNN_OK;
@@ -256,8 +290,8 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     // output layer (CUDA cores): A.f = dl/d(pre-activation of o^12 ... ) masked, dT3, dbT3
     st = mlp_output_layer_backward_f32(c, slot(21), saved + (size_t)22 * q * H, dout, q, dP, A.f, s);
     if (st) return st;
-    k_train_act<<<grid_for(q * H, c.num_sms), 256, 0, s>>>(A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b),
-                                                        reinterpret_cast<__nv_bfloat16*>(A.t));
+    k_train_act<<<dim3((unsigned)((q + 31) / 32), (H + 31) / 32), dim3(32, 8), 0, s>>>(
+        A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b), reinterpret_cast<__nv_bfloat16*>(A.t));
     RPNN_CHECK_LAUNCH();
     if ((st = ready(A, 0))) return st;
     // standard layers 2 (input o^11, slot 20) and 1 (input o^10, slot 9)
