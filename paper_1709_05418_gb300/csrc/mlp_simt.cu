@@ -143,23 +143,30 @@ __global__ void k_mask(const float* __restrict__ x, const float* __restrict__ m,
     if (i < n) out[i] = m[i] > 0.0f ? x[i] : 0.0f;
 }
 
-// column sums: out[n] = sum_m X[m][n] (bias gradients).  Block of 32 x 32 threads per 32
-// columns: thread (x, y) sums rows y, y + 32, ... of column x in increasing order, then
-// the 32 partial sums are added in y order (a fixed order for given M).
-__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ X, int M, int N, int64_t ld,
-                                                 float* __restrict__ out) {
-    __shared__ float part[32][33];
-    const int n = blockIdx.x * 32 + threadIdx.x;
+// column sums: out[n] = sum_m X[m][n] (bias gradients).  Block of 8 x 128 threads per 8
+// columns (a warp reads 8 consecutive floats of 4 rows: whole 32-byte sectors): thread
+// (x, y) sums rows y, y + 128, ... of column x in increasing order, then the 128 partial sums
+// are added in y order (a fixed order for given M).
+constexpr int kColsumCols = 8, kColsumRows = 128;
+__global__ void __launch_bounds__(kColsumCols * kColsumRows) k_colsum(const float* __restrict__ X, int M, int N,
+                                                                   int64_t ld, float* __restrict__ out) {
+    __shared__ float part[kColsumRows][kColsumCols + 1];
+    const int n = blockIdx.x * kColsumCols + threadIdx.x;
     float s = 0.0f;
     if (n < N)
-        for (int m = threadIdx.y; m < M; m += 32) s += X[(int64_t)m * ld + n];
+        for (int m = threadIdx.y; m < M; m += kColsumRows) s += X[(int64_t)m * ld + n];
     part[threadIdx.y][threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.y == 0 && n < N) {
         float t = 0.0f;
-        for (int y = 0; y < 32; ++y) t += part[y][threadIdx.x];
+        for (int y = 0; y < kColsumRows; ++y) t += part[y][threadIdx.x];
         out[n] = t;
     }
+}
+
+void launch_colsum(const float* X, int M, int N, int64_t ld, float* out, cudaStream_t s) {
+    k_colsum<<<(unsigned)((N + kColsumCols - 1) / kColsumCols), dim3(kColsumCols, kColsumRows), 0, s>>>(X, M, N, ld,
+                                                                                                   out);
 }
 
 Seg seg(const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk, int64_t sbn, int K) {
@@ -490,14 +497,13 @@ rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const f
     float* bufB = c.act1.as<float>();
     float* da = c.act2.as<float>();
     float* da3 = c.t_dg.as<float>();
-    const dim3 cs_grid((RPNN_H + 31) / 32), cs_block(32, 32);
     // last layer: g = relu(T3 o12 + bT3): da3 = dout * (g > 0)
     k_mask<<<(M + 255) / 256, 256, 0, s>>>(dout, g, M, da3);
     RPNN_CHECK_LAUNCH();
     // dT3[0][j] = sum_m da3[m] o12[m][j]; dbT3 = sum_m da3
     st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, slot(21), H, 1, M), nullptr, epi(dP + L.T[2], H), s);
     if (st) return st;
-    k_colsum<<<1, cs_block, 0, s>>>(da3, M, 1, 1, dP + L.bT[2]);
+    launch_colsum(da3, M, 1, 1, dP + L.bT[2], s);
     RPNN_CHECK_LAUNCH();
     // da2 = (da3 T3) * (o12 > 0)
     st = gemm(&c, M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
@@ -509,7 +515,7 @@ rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const f
         // dT = da^T x_in; db = colsum(da)
         st = gemm(&c, RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, tin[t], H, 1, M), nullptr, epi(dP + L.T[t], H), s);
         if (st) return st;
-        k_colsum<<<cs_grid, cs_block, 0, s>>>(bufA, M, RPNN_H, H, dP + L.bT[t]);
+        launch_colsum(bufA, M, RPNN_H, H, dP + L.bT[t], s);
         RPNN_CHECK_LAUNCH();
         // d x_in = da T, masked by (x_in > 0) (x_in is a ReLU output)
         st = gemm(&c, M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.T[t], H, 1, RPNN_H), nullptr,
@@ -523,7 +529,7 @@ rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const f
         // dW2 = dpre^T F1; db2 = colsum(dpre)
         st = gemm(&c, RPNN_H, nullptr, RPNN_H, seg(bufA, 1, H, f1, H, 1, M), nullptr, epi(dP + L.W2[k], H), s);
         if (st) return st;
-        k_colsum<<<cs_grid, cs_block, 0, s>>>(bufA, M, RPNN_H, H, dP + L.b2[k]);
+        launch_colsum(bufA, M, RPNN_H, H, dP + L.b2[k], s);
         RPNN_CHECK_LAUNCH();
         // da1 = (dpre W2) * (F1 > 0)
         st = gemm(&c, M, nullptr, RPNN_H, seg(bufA, H, 1, P + L.W2[k], H, 1, RPNN_H), nullptr,
@@ -533,7 +539,7 @@ rpnn_status rpnn_backward_f32(Ctx& c, const NetDims& nd, const float* P, const f
         st = gemm(&c, RPNN_H, nullptr, nd.din, seg(da, 1, H, desc + k * nd.stride, ZS, 1, M), nullptr,
                   epi(dP + L.V[k], nd.din), s);
         if (st) return st;
-        k_colsum<<<cs_grid, cs_block, 0, s>>>(da, M, RPNN_H, H, dP + L.b1[k]);
+        launch_colsum(da, M, RPNN_H, H, dP + L.b1[k], s);
         RPNN_CHECK_LAUNCH();
         if (k > 0) {
             const float* oprev = slot(k - 1);
@@ -576,7 +582,7 @@ rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* 
     RPNN_CHECK_LAUNCH();
     st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, t1, H, 1, M), nullptr, epi(dP + L.T[2], H), s);
     if (st) return st;
-    k_colsum<<<1, dim3(32, 32), 0, s>>>(da3, M, 1, 1, dP + L.bT[2]);
+    launch_colsum(da3, M, 1, 1, dP + L.bT[2], s);
     RPNN_CHECK_LAUNCH();
     return gemm(&c, M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
                 epi(da2, H, nullptr, 0, nullptr, 0, t1, H), s);
@@ -584,7 +590,7 @@ rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* 
 
 rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s) {
     (void)c;
-    k_colsum<<<(N + 31) / 32, dim3(32, 32), 0, s>>>(X, M, N, N, out);
+    launch_colsum(X, M, N, N, out, s);
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
 }
@@ -662,7 +668,7 @@ rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const floa
     // output layer: dw_o = da^T h_last, db_o = sum da, dh_last = (da w_o) * (h_last > 0)
     st = gemm(&c, 1, nullptr, (int)wl, seg(da, 0, 1, hl, wl, 1, M), nullptr, epi(dP + poff[n], wl), s);
     if (st) return st;
-    k_colsum<<<1, dim3(32, 32), 0, s>>>(da, M, 1, 1, dP + poff[n] + wl);
+    launch_colsum(da, M, 1, 1, dP + poff[n] + wl, s);
     RPNN_CHECK_LAUNCH();
     if (n == 0) return RPNN_OK;
     float* cur = c.act0.as<float>();
@@ -676,7 +682,7 @@ rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const floa
         // dW_i = dh_i^T x_{i-1}; db_i = colsum(dh_i)
         st = gemm(&c, (int)w, nullptr, (int)pw, seg(cur, 1, w, xin, pw, 1, M), nullptr, epi(dP + poff[i], pw), s);
         if (st) return st;
-        k_colsum<<<(unsigned)((w + 31) / 32), dim3(32, 32), 0, s>>>(cur, M, (int)w, w, dP + poff[i] + w * pw);
+        launch_colsum(cur, M, (int)w, w, dP + poff[i] + w * pw, s);
         RPNN_CHECK_LAUNCH();
         if (i > 0) {
             // dh_{i-1} = (dh_i W_i) * (h_{i-1} > 0)
