@@ -120,9 +120,9 @@ __device__ __forceinline__ void issue_layer(IssueState& S, uint32_t acc, uint32_
         if (hz && need >= 0)
             tc::mbar_wait_issuer3(S.wbar, S.pw, S.zbar, S.pz, pub, pb, tc::kSpinLimit, S.abort_addr);
         else if (hz)
-            tc::mbar_wait_issuer3(S.wbar, S.pw, S.zbar, S.pz, S.none, 0u, tc::kSpinLimit, S.abort_addr);
+            tc::mbar_wait_issuer2(S.wbar, S.pw, S.zbar, S.pz, tc::kSpinLimit, S.abort_addr);
         else if (need >= 0)
-            tc::mbar_wait_issuer3(S.wbar, S.pw, pub, pb, S.none, 0u, tc::kSpinLimit, S.abort_addr);
+            tc::mbar_wait_issuer2(S.wbar, S.pw, pub, pb, tc::kSpinLimit, S.abort_addr);
         else
             tc::mbar_wait_issuer(S.wbar, S.pw, tc::kSpinLimit, S.abort_addr);
 #pragma unroll

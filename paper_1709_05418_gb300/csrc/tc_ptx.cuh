@@ -90,8 +90,8 @@ __device__ __forceinline__ void mbar_wait_issuer(uint32_t bar, uint32_t parity, 
 }
 
 // As mbar_wait_issuer, for three barriers at once (each with its own parity): the poll
-// succeeds when all three phases have completed.  A caller that needs fewer passes a
-// barrier whose phase 0 completed at setup, with parity 0, in the unused slots.
+// succeeds when all three phases have completed.  (Every try_wait costs the issuing thread
+// tens of nanoseconds, so a stage waits on exactly the barriers it needs: one, two or three.)
 __device__ __forceinline__ void mbar_wait_issuer3(uint32_t b0, uint32_t p0, uint32_t b1, uint32_t p1, uint32_t b2,
                                                   uint32_t p2, uint32_t limit, uint32_t abort_addr) {
     asm volatile(
@@ -116,6 +116,30 @@ __device__ __forceinline__ void mbar_wait_issuer3(uint32_t b0, uint32_t p0, uint
         "DONE_%=:\n"
         "}\n" ::"r"(b0), "r"(p0), "r"(b1), "r"(p1), "r"(b2), "r"(p2), "r"(limit), "r"(abort_addr),
           "r"(kPollHintNs) : "memory");
+}
+
+// As mbar_wait_issuer3, for two barriers.
+__device__ __forceinline__ void mbar_wait_issuer2(uint32_t b0, uint32_t p0, uint32_t b1, uint32_t p1, uint32_t limit,
+                                                  uint32_t abort_addr) {
+    asm volatile(
+        "{\n"
+        " .reg .pred P1, P2;\n"
+        " .reg .u32 c, f;\n"
+        " mov.u32 c, %4;\n"
+        "WAIT_%=:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%0], %1, %6;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P2, [%2], %3, %6;\n"
+        " and.pred P1, P1, P2;\n"
+        " @P1 bra DONE_%=;\n"
+        " ld.volatile.shared.u32 f, [%5];\n"
+        " setp.ne.u32 P1, f, 0;\n"
+        " @P1 bra DONE_%=;\n"
+        " sub.u32 c, c, 1;\n"
+        " setp.ne.u32 P1, c, 0;\n"
+        " @P1 bra WAIT_%=;\n"
+        " st.volatile.shared.u32 [%5], 1;\n"
+        "DONE_%=:\n"
+        "}\n" ::"r"(b0), "r"(p0), "r"(b1), "r"(p1), "r"(limit), "r"(abort_addr), "r"(kPollHintNs) : "memory");
 }
 
 // Bounded wait for the phase with the given parity.  Gives up (returns false) after
