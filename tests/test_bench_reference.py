@@ -31,3 +31,38 @@ def test_cpu_baseline_is_the_reference_measurement():
     assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
     assert cb["per_step_min"] <= cb["per_step_median"] <= cb["per_step_max"]
     assert "pyramid level built first" in cb["sample"]
+
+
+def test_clock_sampler_summarises_nvml_samples(monkeypatch):
+    """The timed-region clock record from a fake NVML (no GPU): median SM clock, maximum,
+    sample count and the union of the clock event reasons seen."""
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+
+    class FakeNvml:
+        def __init__(self):
+            self.n = 0
+
+        def sample(self):
+            self.n += 1
+            return (1980.0, 2070.0, ["sw_power_cap"]) if self.n % 2 else (2070.0, 2070.0, [])
+
+    monkeypatch.setattr(bench._Nvml, "open", classmethod(lambda cls, index: FakeNvml()))
+    c = bench.Clocks(0)
+    c.start()
+    time.sleep(0.05)
+    rec = c.stop()
+    assert rec["samples"] >= 3 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"] and 1980.0 <= rec["sm_mhz"] <= 2070.0
+    assert rec["sm_mhz_min"] == 1980.0
+
+
+def test_clock_sampler_without_nvml_or_nvidia_smi(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench._Nvml, "open", classmethod(lambda cls, index: None))
+    monkeypatch.setenv("PATH", "/nonexistent")
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop() is None
