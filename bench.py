@@ -42,12 +42,12 @@ NCU_TRAFFIC = {
     "descriptor": {"bytes_per_query": (795.414272e6 + 5.620736e6) / 178675,
                    "sources": {"descriptor.cu": "05b2f345e006b04d", "desc_lookup.cuh": "96d43ff4040f8e82",
                                "volume.cu:k_pack": "f1b80b6358e59e22"}},
-    "network": {"bytes_per_query": (885.058048e6 + 3.666432e6) / 178675,
-                "sources": {"mlp_tc.cu": "6016f5106e69ea65", "tc_ptx.cuh": "294268ada12e7cd2",
-                            "tc_net.cuh": "ffb2c1bf33d487a3"}},
-    "network_fp8": {"bytes_per_query": (460.987904e6 + 1.634048e6) / 178675,
-                    "sources": {"mlp_tc.cu": "6016f5106e69ea65", "tc_ptx.cuh": "294268ada12e7cd2",
-                                "tc_net.cuh": "ffb2c1bf33d487a3"}},
+    "network": {"bytes_per_query": (884.952320e6 + 3.613952e6) / 178675,
+                "sources": {"mlp_tc.cu": "71c4c33a1ac5f22e", "tc_ptx.cuh": "294268ada12e7cd2",
+                            "tc_net.cuh": "cc8bbc89187b00b1"}},
+    "network_fp8": {"bytes_per_query": (460.797696e6 + 1.595648e6) / 178675,
+                    "sources": {"mlp_tc.cu": "71c4c33a1ac5f22e", "tc_ptx.cuh": "294268ada12e7cd2",
+                                "tc_net.cuh": "cc8bbc89187b00b1"}},
 }
 
 

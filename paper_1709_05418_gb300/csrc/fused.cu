@@ -53,7 +53,7 @@ constexpr uint32_t OFF_Z = OFF_W + W_STAGES * W_STAGE;         // 137216
 constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 202752
 enum {
     B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES, B_ZEMPTY = B_ZFULL + Z_STAGES,
-    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DONE, B_DRAIN, B_COUNT
+    B_ACC = B_ZEMPTY + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DRAIN, B_COUNT
 };
 constexpr uint32_t OFF_TMEM_SLOT = OFF_BAR + BAR_STRIDE * B_COUNT;
 constexpr uint32_t OFF_ABORT = OFF_TMEM_SLOT + 8;
@@ -141,10 +141,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
         tc::mbar_init(bar(B_ACC), 1);
         for (int b = 0; b < npub<F>(); ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
-        tc::mbar_init(bar(B_DONE), 1);
         tc::mbar_init(bar(B_DRAIN), 1);
         tc::fence_mbar_init();
-        tc::mbar_arrive(bar(B_DONE));
     }
     if (warp == 1) {
         tc::tmem_alloc(base + OFF_TMEM_SLOT, 512);
@@ -189,7 +187,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_rpnn_fused(const __grid_constan
             IssueState S;
             S.idesc = tc::idesc_bf16(TM, NP);
             S.abort_addr = base + OFF_ABORT;
-            S.none = bar(B_DONE);
             S.hi = (uint32_t)(tc::smem_desc_sw64(base) >> 32);
             S.w0 = (uint32_t)tc::smem_desc_sw64(base + OFF_W);
             S.z0 = (uint32_t)tc::smem_desc_sw64(base + OFF_Z);

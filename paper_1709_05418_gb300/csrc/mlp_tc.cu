@@ -67,11 +67,10 @@ constexpr uint32_t OFF_BAR = OFF_Z + Z_STAGES * Z_STAGE;       // 229376
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 
-// barrier slots from OFF_BAR, BAR_STRIDE bytes apart; B_DONE completes its phase 0 at
-// setup and stands in for "nothing to wait for" in the issuer's three-barrier poll
+// barrier slots from OFF_BAR, BAR_STRIDE bytes apart
 enum {
     B_WFULL = 0, B_WEMPTY = B_WFULL + W_STAGES, B_ZFULL = B_WEMPTY + W_STAGES,
-    B_ACC = B_ZFULL + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DONE, B_DRAIN, B_COUNT
+    B_ACC = B_ZFULL + Z_STAGES, B_BLK, B_PART = B_BLK + NPUB_MAX, B_DRAIN, B_COUNT
 };
 // a descriptor slot is reused 8 or 11 stages after its reader (a first layer's z stages,
 // then the 4 stages of layer 1 or of the block's second layer and the first layer's x
@@ -106,10 +105,8 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
         tc::mbar_init(bar(B_ACC), 1);
         for (int b = 0; b < npub<F>(); ++b) tc::mbar_init(bar(B_BLK + b), EPI_WARPS);   // one arrival per warp
         tc::mbar_init(bar(B_PART), EPI_WARPS / 2);
-        tc::mbar_init(bar(B_DONE), 1);
         tc::mbar_init(bar(B_DRAIN), 1);
         tc::fence_mbar_init();
-        tc::mbar_arrive(bar(B_DONE));
     }
     if (warp == 1) {
         tc::tmem_alloc(base + OFF_TMEM_SLOT, 512);
@@ -183,7 +180,6 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
             IssueState S;
             S.idesc = F::FP8 ? tc::idesc_e4m3(TM, NP) : tc::idesc_bf16(TM, NP);
             S.abort_addr = base + OFF_ABORT;
-            S.none = bar(B_DONE);
             S.hi = (uint32_t)(tc::smem_desc_sw64(base) >> 32);
             S.w0 = (uint32_t)tc::smem_desc_sw64(base + OFF_W);
             S.z0 = (uint32_t)tc::smem_desc_sw64(base + OFF_Z);

@@ -76,7 +76,7 @@ __host__ __device__ constexpr bool layer_keeps_o(int l) { return (l & 1) && l < 
 // operand descriptors (start address in 16-byte units) and of the activation buffer, the
 // common high word, the current ring barriers, positions and phases.
 struct IssueState {
-    uint32_t idesc, abort_addr, none, hi;
+    uint32_t idesc, abort_addr, hi;
     uint32_t w0, z0, x0, w, z;
     uint32_t wbar0, zbar0, wbar, zbar, blk0;
     uint32_t sw, pw, sz, pz;
