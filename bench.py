@@ -42,12 +42,12 @@ NCU_TRAFFIC = {
     "descriptor": {"bytes_per_query": (795.414272e6 + 5.620736e6) / 178675,
                    "sources": {"descriptor.cu": "05b2f345e006b04d", "desc_lookup.cuh": "96d43ff4040f8e82",
                                "volume.cu:k_pack": "f1b80b6358e59e22"}},
-    "network": {"bytes_per_query": (884.952320e6 + 3.613952e6) / 178675,
-                "sources": {"mlp_tc.cu": "71c4c33a1ac5f22e", "tc_ptx.cuh": "294268ada12e7cd2",
-                            "tc_net.cuh": "cc8bbc89187b00b1"}},
-    "network_fp8": {"bytes_per_query": (460.797696e6 + 1.595648e6) / 178675,
-                    "sources": {"mlp_tc.cu": "71c4c33a1ac5f22e", "tc_ptx.cuh": "294268ada12e7cd2",
-                                "tc_net.cuh": "cc8bbc89187b00b1"}},
+    "network": {"bytes_per_query": (886.175488e6 + 3.624960e6) / 178675,
+                "sources": {"mlp_tc.cu": "57c21e9d2ae6b860", "tc_ptx.cuh": "294268ada12e7cd2",
+                            "tc_net.cuh": "84cfe3d7ca7bea66"}},
+    "network_fp8": {"bytes_per_query": (460.973824e6 + 1.656832e6) / 178675,
+                    "sources": {"mlp_tc.cu": "57c21e9d2ae6b860", "tc_ptx.cuh": "294268ada12e7cd2",
+                                "tc_net.cuh": "84cfe3d7ca7bea66"}},
 }
 
 

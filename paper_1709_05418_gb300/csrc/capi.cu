@@ -72,7 +72,9 @@ rpnn_status train_desc(Ctx& c, const void* desc, int dtype, int64_t q, const flo
 // Forward with saved activations in the context's training precision (FP32 CUDA cores,
 // or BF16 tensor-core GEMMs with FP32 master weights); the prediction goes to t_out.
 rpnn_status train_forward(Ctx& c, const void* desc, int dtype, const float* d32, int64_t q, cudaStream_t s) {
-    rpnn_status st = c.t_saved.reserve(mlp_saved_floats_per_row() * q * sizeof(float));
+    const size_t saved = c.train_precision == RPNN_BF16 ? train_bf16_saved32_floats(q)
+                                                        : mlp_saved_floats_per_row() * (size_t)q;
+    rpnn_status st = c.t_saved.reserve(saved * sizeof(float));
     if (!st) st = c.t_out.reserve(q * sizeof(float));
     if (st) return st;
     if (c.train_precision == RPNN_BF16) {

@@ -36,8 +36,9 @@ struct TgEpiDev {
     const float* bias;                    // [N] or null
     const float* res;                     // [M][ldr] or null
     int64_t ldr;
-    const float* mask;                    // multiply by (mask > 0): [M][ldm] or null
+    const float* mask;                    // multiply by (mask > 0): [M][ldm] (mask_t: [N][ldm]) or null
     int64_t ldm;
+    int mask_t;
     int relu;
     float* C;                             // FP32 [M][ldc] or null
     int64_t ldc;
@@ -60,7 +61,7 @@ struct TgCfg {
     static constexpr uint32_t BBOX = BN * 64;
     static constexpr uint32_t STAGE = 2 * ABOX + 2 * BBOX;
     static constexpr int STAGES = BN == 256 ? 3 : 4;
-    static_assert(4 * 32 * 17 * 4 <= STAGES * STAGE, "epilogue tiles reuse the stage ring");
+    static_assert(2 * 4 * 32 * 17 * 4 <= STAGES * STAGE, "epilogue tiles reuse the stage ring");
     static constexpr uint32_t OFF_BAR = STAGES * STAGE;
     static constexpr uint32_t SMEM = OFF_BAR + 256 + 1024;   // barriers, TMEM slot, alignment slack
 };
@@ -69,7 +70,7 @@ __device__ __forceinline__ void tg_store(const TgEpiDev& e, int m, int n, float 
     if (e.bias) v += e.bias[n];
     if (e.res) v += e.res[(int64_t)m * e.ldr + n];
     if (e.relu) v = fmaxf(v, 0.0f);
-    if (e.mask && !(e.mask[(int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
+    if (e.mask && !(e.mask[e.mask_t ? (int64_t)n * e.ldm + m : (int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
     if (e.C) e.C[(int64_t)m * e.ldc + n] = v;
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     if (e.Cb) e.Cb[(int64_t)m * e.ldb + n] = b;
@@ -160,8 +161,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtens
     // chunk goes through a per-warp shared tile (the stage ring is idle once the MMAs are
     // done): a row-major pass (half a warp per row, 16 consecutive columns) applies bias,
     // residual, ReLU and mask and makes the FP32 / BF16 / split-K stores coalesced; a
-    // column pass (one lane per row) makes the transposed BF16 store coalesced.
+    // column pass (one lane per row) makes the transposed BF16 store coalesced, and reads a
+    // transposed mask into a second tile the same way.
     float* stile = reinterpret_cast<float*>(sbase) + warp * (32 * 17);
+    float* mtile = reinterpret_cast<float*>(sbase) + (4 + warp) * (32 * 17);
     const int row0 = m0 + warp * 32, row = row0 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < BN && n0 + c0 < g.N; c0 += 16) {
@@ -174,6 +177,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtens
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) stile[lane * 17 + j] = v[j];
+        if (g.splits == 1 && g.e.mask && g.e.mask_t) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                const int n = n0 + c0 + jj;
+                mtile[lane * 17 + jj] = (row < g.M && n < g.N) ? g.e.mask[(int64_t)n * g.e.ldm + row] : 1.0f;
+            }
+        }
         __syncwarp();
         const int j = lane & 15, n = n0 + c0 + j;
         const bool ncol = n < g.N;
@@ -192,7 +202,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtens
                 const int m = row0 + 2 * it + (lane >> 4);
                 const bool in = m < g.M && ncol;
                 rv[it] = (g.e.res && in) ? g.e.res[(int64_t)m * g.e.ldr + n] : 0.0f;
-                mv[it] = (g.e.mask && in) ? g.e.mask[(int64_t)m * g.e.ldm + n] : 1.0f;
+                mv[it] = (g.e.mask && in) ? (g.e.mask_t ? mtile[(2 * it + (lane >> 4)) * 17 + j]
+                                                        : g.e.mask[(int64_t)m * g.e.ldm + n])
+                                          : 1.0f;
             }
 #pragma unroll
             for (int it = 0; it < 16; ++it) {
@@ -271,7 +283,8 @@ rpnn_status make_map(Ctx& c, CUtensorMap* m, const void* p, int64_t ld, int K, i
 
 TgEpiDev to_dev(const TgOut& o) {
     TgEpiDev e;
-    e.bias = o.bias; e.res = o.res; e.ldr = o.ldr; e.mask = o.mask; e.ldm = o.ldm; e.relu = o.relu;
+    e.bias = o.bias; e.res = o.res; e.ldr = o.ldr; e.mask = o.mask; e.ldm = o.ldm; e.mask_t = o.mask_t;
+    e.relu = o.relu;
     e.C = o.C; e.ldc = o.ldc;
     e.Cb = reinterpret_cast<__nv_bfloat16*>(o.Cb); e.ldb = o.ldb;
     e.Ct = reinterpret_cast<__nv_bfloat16*>(o.Ct); e.ldt = o.ldt;
@@ -337,7 +350,7 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
     if (tu.enabled) {
         GemmKey key{M, N, s0.K, s1 ? s1->K : 0,
                     kTgFlag | (o.bias != nullptr) << 4 | (o.res != nullptr) << 5 | (o.mask != nullptr) << 6 |
-                        (o.Cb != nullptr) << 9 | (o.Ct != nullptr) << 10};
+                        (o.Cb != nullptr) << 9 | (o.Ct != nullptr) << 10 | (o.mask_t != 0) << 11};
         const GemmChoice* hit = tu.find(key);
         if (hit) {
             bn = hit->tile;

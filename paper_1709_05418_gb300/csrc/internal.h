@@ -362,6 +362,7 @@ struct TgOut {
     int64_t ldr = 0;
     const float* mask = nullptr;
     int64_t ldm = 0;
+    int mask_t = 0;                  // mask stored transposed: element (m, n) at mask[n * ldm + m]
     int relu = 0;
 };
 // split_ws: the split-K workspace (null: the tuner's); GEMMs that may run at the same time
@@ -370,10 +371,11 @@ rpnn_status tc_gemm(Ctx& c, int M, int N, const TgSeg& s0, const TgSeg* s1, cons
                     DevBuf* split_ws = nullptr);
 
 // FP32 output layer g = relu(T3 t1 + bT3) and its backward (da3 = dout * (g > 0); dT3, dbT3
-// into dP; da2 = (da3 T3) * (t1 > 0)); bias-gradient column sums
+// into dP; da2 = (da3 T3) * (t1 > 0)); bias-gradient column sums.  The backward's t1 is
+// [q][200] row-major, or (ldt1 > 0) transposed [200][ldt1].
 rpnn_status mlp_output_layer_f32(Ctx& c, const float* t1, int64_t q, float* out, cudaStream_t s);
 rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* g, const float* dout, int64_t q,
-                                          float* dP, float* da2, cudaStream_t s);
+                                          float* dP, float* da2, cudaStream_t s, int64_t ldt1 = 0);
 rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s);
 
 // Plain ("all-at-once") MLP of the architecture comparison (Sec. 7): n hidden layers of
@@ -388,6 +390,9 @@ rpnn_status dense_backward(Ctx& c, const int* widths, int n, int din, const floa
 // activations): saved FP32 slots as mlp_forward_f32, BF16 copies in s16
 // (train_bf16_saved_elems(q) elements)
 size_t train_bf16_saved_elems(int64_t q);
+// FP32 floats of the BF16 training forward's saved activations (22 transposed [200][ldq]
+// slots, then g [q])
+size_t train_bf16_saved32_floats(int64_t q);
 // desc: q rows [10][240] of dtype desc_dtype (RPNN_F32 or RPNN_BF16)
 rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int64_t q, float* out, float* saved,
                                    uint16_t* s16, cudaStream_t s);

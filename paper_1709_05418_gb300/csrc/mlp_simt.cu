@@ -28,8 +28,8 @@ struct Epi {
     const float* bias;  // [N] or null
     const float* res;   // residual [M][ldr] or null
     int64_t ldr;
-    const float* mask;  // multiply by (mask > 0), [M][ldm] or null
-    int64_t ldm;
+    const float* mask;  // multiply by (mask > 0): element (m, n) at mask[m * ldm + n * mcs], or null
+    int64_t ldm, mcs;
     int relu;
     float* C;
     int64_t ldc;
@@ -39,7 +39,7 @@ __device__ __forceinline__ float epilogue(const Epi& e, int m, int n, float v) {
     if (e.bias) v += e.bias[n];
     if (e.res) v += e.res[(int64_t)m * e.ldr + n];
     if (e.relu) v = fmaxf(v, 0.0f);
-    if (e.mask && !(e.mask[(int64_t)m * e.ldm + n] > 0.0f)) v = 0.0f;
+    if (e.mask && !(e.mask[(int64_t)m * e.ldm + (int64_t)n * e.mcs] > 0.0f)) v = 0.0f;
     return v;
 }
 
@@ -176,10 +176,11 @@ Seg seg(const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk, i
 }
 
 Epi epi(float* C, int64_t ldc, const float* bias = nullptr, int relu = 0,
-        const float* res = nullptr, int64_t ldr = 0, const float* mask = nullptr, int64_t ldm = 0) {
+        const float* res = nullptr, int64_t ldr = 0, const float* mask = nullptr, int64_t ldm = 0,
+        int64_t mcs = 1) {
     Epi e;
     e.C = C; e.ldc = ldc; e.bias = bias; e.relu = relu; e.res = res; e.ldr = ldr;
-    e.mask = mask; e.ldm = ldm;
+    e.mask = mask; e.ldm = ldm; e.mcs = mcs;
     return e;
 }
 
@@ -570,7 +571,9 @@ rpnn_status mlp_output_layer_f32(Ctx& c, const float* t1, int64_t q, float* out,
 }
 
 rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* g, const float* dout, int64_t q,
-                                          float* dP, float* da2, cudaStream_t s) {
+                                          float* dP, float* da2, cudaStream_t s, int64_t ldt1) {
+    // t1 = o^12: [q][200] row-major, or (ldt1 > 0) transposed [200][ldt1]
+    const int64_t rs = ldt1 > 0 ? 1 : RPNN_H, cs = ldt1 > 0 ? ldt1 : 1;
     const ParamLayout& L = param_layout();
     const float* P = c.params32.as<float>();
     const int M = (int)q;
@@ -580,12 +583,12 @@ rpnn_status mlp_output_layer_backward_f32(Ctx& c, const float* t1, const float* 
     float* da3 = c.t_dg.as<float>();
     k_mask<<<(M + 255) / 256, 256, 0, s>>>(dout, g, M, da3);
     RPNN_CHECK_LAUNCH();
-    st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, t1, H, 1, M), nullptr, epi(dP + L.T[2], H), s);
+    st = gemm(&c, 1, nullptr, RPNN_H, seg(da3, 0, 1, t1, rs, cs, M), nullptr, epi(dP + L.T[2], H), s);
     if (st) return st;
     launch_colsum(da3, M, 1, 1, dP + L.bT[2], s);
     RPNN_CHECK_LAUNCH();
     return gemm(&c, M, nullptr, RPNN_H, seg(da3, 1, 1, P + L.T[2], H, 1, 1), nullptr,
-                epi(da2, H, nullptr, 0, nullptr, 0, t1, H), s);
+                epi(da2, H, nullptr, 0, nullptr, 0, t1, rs, cs), s);
 }
 
 rpnn_status colsum_f32(Ctx& c, const float* X, int M, int N, float* out, cudaStream_t s) {

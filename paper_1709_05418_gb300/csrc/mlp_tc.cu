@@ -270,12 +270,13 @@ k_rpnn_tc(const __grid_constant__ CUtensorMap zmap, const TcArgs a) {
                     // at k - 1, o^11 and o^12 at 20 and 21
                     const int slot = l >= 20 ? l : ((l & 1) ? (l >> 1) : 10 + (l >> 1));
                     if (r < Q) {
-                        ea.tf = a.tsave + ((int64_t)slot * a.tq + r) * RPNN_H;
+                        // both copies transposed [slot][200][ldq]: column j of row r at j * ldq
+                        ea.tf = a.tsave + (int64_t)slot * RPNN_H * a.tldq + r;
                         ea.tt = a.tsave_t + (int64_t)slot * RPNN_H * a.tldq + r;
                         ea.tldq = a.tldq;
                         // second layers k >= 2 add o^{k-1} (slot k - 2), which this thread
                         // stored two layers earlier
-                        if (layer_resid(l)) ea.tres = a.tsave + ((int64_t)((l >> 1) - 1) * a.tq + r) * RPNN_H;
+                        if (layer_resid(l)) ea.tres = a.tsave + (int64_t)((l >> 1) - 1) * RPNN_H * a.tldq + r;
                     }
                 }
                 // one straight-line routine per layer kind

@@ -51,8 +51,8 @@ struct TcArgs {
     float* out;
     uint32_t* status;
     // training forward (k_rpnn_tc<FmtBF16, true>): every layer's ReLU output is also stored
-    // FP32 [slot][q][200] and BF16 transposed [slot][200][ldq] for the backward (slot: o^k
-    // at k - 1, F1^k at 10 + k - 1, o^11 at 20, o^12 at 21)
+    // FP32 and BF16, both transposed [slot][200][ldq], for the backward (slot: o^k at k - 1,
+    // F1^k at 10 + k - 1, o^11 at 20, o^12 at 21)
     float* tsave;
     uint16_t* tsave_t;
     int64_t tq, tldq;
@@ -178,10 +178,10 @@ struct EpiArgs {
     const float* w3;              // output layer weights
     const float* scale;           // FP8 per-layer scales, or null
     uint32_t taddr;               // the warp's accumulator columns
-    float* tf;                    // training forward: this row's FP32 output, or null
-    uint16_t* tt;                 // training forward: this row's column 0 of the transposed output
-    int64_t tldq;                 // its pitch
-    const float* tres;            // training forward: this row's FP32 residual o^{k-1}, or null
+    float* tf;                    // training forward: this row's column 0 of the transposed FP32 output, or null
+    uint16_t* tt;                 // training forward: the same in the transposed BF16 output
+    int64_t tldq;                 // their column pitch
+    const float* tres;            // training forward: column 0 of this row's transposed FP32 residual o^{k-1}, or null
 };
 
 // KIND: EPI_PLAIN ReLU + BF16; EPI_KEEP also writes o^k back into the accumulator (the next
@@ -216,32 +216,28 @@ __device__ __forceinline__ void epi_chunk(const EpiArgs& e, int b, int half, flo
         }
     }
     if (TRAIN && e.tres) {
-        const float4* r4 = reinterpret_cast<const float4*>(e.tres + c0);
+        // one column at a time: the warp's 32 rows are 128 contiguous bytes; all loads first
+        float rr[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (c0 + 4 * q < RPNN_H) {
-                const float4 rr = r4[q];
-                w[4 * q] += rr.x; w[4 * q + 1] += rr.y; w[4 * q + 2] += rr.z; w[4 * q + 3] += rr.w;
-            }
-        }
+        for (int i = 0; i < 16; ++i) rr[i] = c0 + i < RPNN_H ? e.tres[(int64_t)(c0 + i) * e.tldq] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (c0 + i < RPNN_H) w[i] += rr[i];
     }
     if (KIND == EPI_KEEP || KIND == EPI_LAST || TRAIN) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) w[i] = fmaxf(w[i], 0.0f);
     }
     if (TRAIN && e.tf) {
-        // columns c0 .. c0 + 15 of the row, the 200 real ones: FP32 row-major (16-byte
-        // stores) and BF16 transposed (a warp's 32 rows are 64 contiguous bytes per column)
-        float4* f4 = reinterpret_cast<float4*>(e.tf + c0);
-        f4[0] = make_float4(w[0], w[1], w[2], w[3]);
-        f4[1] = make_float4(w[4], w[5], w[6], w[7]);
-        if (c0 + 16 <= RPNN_H) {
-            f4[2] = make_float4(w[8], w[9], w[10], w[11]);
-            f4[3] = make_float4(w[12], w[13], w[14], w[15]);
-        }
+        // columns c0 .. c0 + 15 of the row, the 200 real ones, FP32 and BF16, both transposed
+        // (a warp's 32 rows are 128 and 64 contiguous bytes per column)
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (c0 + i < RPNN_H) e.tt[(int64_t)(c0 + i) * e.tldq] = __bfloat16_as_ushort(__float2bfloat16_rn(w[i]));
+        for (int i = 0; i < 16; ++i) {
+            if (c0 + i < RPNN_H) {
+                e.tf[(int64_t)(c0 + i) * e.tldq] = w[i];
+                e.tt[(int64_t)(c0 + i) * e.tldq] = __bfloat16_as_ushort(__float2bfloat16_rn(w[i]));
+            }
+        }
     }
     if (KIND == EPI_KEEP && !F::FP8 && !TRAIN) tc::tmem_st16(e.taddr + 32u * b + 16u * (half - e.half), w);
     if (KIND == EPI_LAST) {

@@ -162,6 +162,8 @@ rpnn_status launch_bf16_to_f32(const void* in, float* out, int64_t n, int sms, c
     return RPNN_OK;
 }
 
+size_t train_bf16_saved32_floats(int64_t q) { return (size_t)22 * H * train_ldq(q) + (size_t)q; }
+
 size_t train_bf16_saved_elems(int64_t q) {
     // 22 activations as BF16 [q][200] and BF16 [200][ldq]; descriptors as BF16 [q][2400]
     // and [10][226][ldq]
@@ -196,8 +198,10 @@ rpnn_status train_build_image(Ctx& c, cudaStream_t s) {
     return RPNN_OK;
 }
 
-// Forward with saved activations: FP32 slots as the FP32 form (o^1..o^10, F1^1..F1^10,
-// o^11, o^12, then g) in `saved`, BF16 copies in `s16` (train_bf16_saved_elems(q)).
+// Forward with saved activations: FP32 slots in the FP32 form's order (o^1..o^10,
+// F1^1..F1^10, o^11, o^12), each transposed [200][ldq] so that a warp's 32 rows are 128
+// contiguous bytes per column, then g [q] (train_bf16_saved32_floats(q) floats in `saved`);
+// BF16 copies in `s16` (train_bf16_saved_elems(q)).
 rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int64_t q, float* out, float* saved,
                                    uint16_t* s16, cudaStream_t s) {
     const int64_t ldq = train_ldq(q);
@@ -224,7 +228,7 @@ rpnn_status mlp_forward_bf16_train(Ctx& c, const void* desc, int desc_dtype, int
     // the epilogue, every ReLU output stored FP32 and BF16 transposed for the backward
     st = mlp_forward_bf16_saving(c, zfwd, q, out, saved, s16 + (size_t)22 * q * H, ldq, s);
     if (st) return st;
-    RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * q * H, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    RPNN_CUDA_TRY(cudaMemcpyAsync(saved + (size_t)22 * H * ldq, out, q * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return RPNN_OK;
 }
 
@@ -235,7 +239,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     const int M = (int)q;
     const int64_t ldq = train_ldq(q);
     const uint16_t* W = c.t_w16.as<uint16_t>();
-    auto slot = [&](int i) { return saved + (size_t)i * q * H; };
+    auto slot = [&](int i) { return saved + (size_t)i * H * ldq; };       // transposed [200][ldq]
     auto slott = [&](int i) { return s16 + (size_t)22 * q * H + (size_t)i * H * ldq; };
     const uint16_t* zt = s16 + (size_t)22 * q * H + (size_t)22 * H * ldq + (size_t)q * RPNN_K * RPNN_DESC_STRIDE;
     // one gradient buffer per layer, each FP32 [q][200] + BF16 [q][200] + BF16 transposed
@@ -288,7 +292,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
     int next = 0;
     Buf A = buf(next++);
     // output layer (CUDA cores): A.f = dl/d(pre-activation of o^12 ... ) masked, dT3, dbT3
-    st = mlp_output_layer_backward_f32(c, slot(21), saved + (size_t)22 * q * H, dout, q, dP, A.f, s);
+    st = mlp_output_layer_backward_f32(c, slot(21), saved + (size_t)22 * H * ldq, dout, q, dP, A.f, s, ldq);
     if (st) return st;
     k_train_act<<<dim3((unsigned)((q + 31) / 32), (H + 31) / 32), dim3(32, 8), 0, s>>>(
         A.f, q, ldq, reinterpret_cast<__nv_bfloat16*>(A.b), reinterpret_cast<__nv_bfloat16*>(A.t));
@@ -299,7 +303,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         const int in = t == 1 ? 20 : 9;
         Buf B = buf(next++);
         TgOut o = out_to(B);
-        o.mask = slot(in); o.ldm = H;
+        o.mask = slot(in); o.ldm = ldq; o.mask_t = 1;
         const TgSeg sd{A.b, H, W + I.TT[t], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
         if (!st) st = ready(B, 0);
@@ -313,7 +317,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
         // da1 = (dpre W2) * (F1 > 0)
         Buf D = buf(next++);
         TgOut o = out_to(D);
-        o.mask = slot(10 + k); o.ldm = H;
+        o.mask = slot(10 + k); o.ldm = ldq; o.mask_t = 1;
         const TgSeg sd{A.b, H, W + I.W2T[k], H, H};
         st = tc_gemm(c, M, H, sd, nullptr, o, s);
         if (!st) st = ready(D, 1);
@@ -324,7 +328,7 @@ rpnn_status mlp_backward_bf16_train(Ctx& c, int64_t q, const float* saved, const
             B = buf(next++);
             TgOut o2 = out_to(B);
             o2.res = A.f; o2.ldr = H;
-            o2.mask = slot(k - 1); o2.ldm = H;
+            o2.mask = slot(k - 1); o2.ldm = ldq; o2.mask_t = 1;
             const TgSeg s1{D.b, H, W + I.W1T[k], H, H};
             st = tc_gemm(c, M, H, s1, nullptr, o2, s);
             if (!st) st = ready(B, 0);
