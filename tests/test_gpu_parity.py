@@ -355,8 +355,8 @@ def test_render_bf16_matches_oracle(ctx, api, blob_vol, blob_orc, cam64, params)
 
 
 def test_path_render_matches_oracle(ctx, api, blob_vol, blob_orc, cam64):
-    """RPNN_MODE_PATH, the plain Monte Carlo path tracer (Henyey-Greenstein phase function)
-    that judges per-pixel error: the same Philox streams make the GPU follow the oracle's
+    """RPNN_MODE_PATH, the plain Monte Carlo path tracer (Henyey-Greenstein phase function),
+    compared pixel by pixel: the same Philox streams make the GPU follow the oracle's
     paths decision by decision; a path whose decision flips on an FP32 rounding differs."""
     img = ctx.render(blob_vol, cam64, precision=api.F32, mode=api.MODE_PATH)
     ctx.sync_status()
