@@ -102,9 +102,41 @@ __global__ void k_mip_pass(const float* __restrict__ in, float* __restrict__ out
         // only the taps that land inside the grid contribute (zero outside): the same terms
         // in the same ascending order, without visiting the rest
         const int mlo = max(0, -t0), mhi = min(T, n - t0);
+        // (unrolled so that several taps' loads are in flight ahead of the serial sum)
+#pragma unroll 4
         for (int m = mlo; m < mhi; ++m)
             acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), __ldg(in + base + (int64_t)(t0 + m) * stride)));
         out[o] = apply_scale ? __fmul_rn(acc, scale) : acc;
+    }
+}
+
+// The x pass of k_mip_pass, staged: a block copies R consecutive x lines of the fine grid
+// (contiguous in memory) into shared memory with coalesced loads (line pitch nx + 1 floats),
+// then its threads compute the decimated outputs (line r, index j) with r fastest, so a
+// warp's lanes read different lines at one position (different banks) instead of 32
+// scattered global lines per tap.  Each output's taps in ascending m, acc = acc + w*v: the
+// same terms in the same order as k_mip_pass.
+__global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ out, int nx, int64_t nrows,
+                             int ax, int st, int off, const float* __restrict__ w, int T, int R) {
+    extern __shared__ float lines[];
+    const int pitch = nx + 1;
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < nrows; r0 += (int64_t)gridDim.x * R) {
+        const int nr = (int)min((int64_t)R, nrows - r0);
+        __syncthreads();                       // the previous lines' readers are done
+        const float* src = in + r0 * nx;
+        for (int r = 0; r < nr; ++r)
+            for (int x = threadIdx.x; x < nx; x += blockDim.x) lines[r * pitch + x] = __ldg(src + (int64_t)r * nx + x);
+        __syncthreads();
+        for (int task = threadIdx.x; task < R * ax; task += blockDim.x) {
+            const int r = task % R, j = task / R;
+            if (r >= nr) continue;
+            const float* line = lines + r * pitch;
+            const int t0 = j * st + off;
+            const int mlo = max(0, -t0), mhi = min(T, nx - t0);
+            float acc = 0.0f;
+            for (int m = mlo; m < mhi; ++m) acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), line[t0 + m]));
+            out[(r0 + r) * ax + j] = acc;
+        }
     }
 }
 
@@ -281,8 +313,20 @@ rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStr
     RPNN_CUDA_TRY(cudaMemcpyAsync(dw, w.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
     const int st = 1 << level;
     const float scale = v.info.inv_mean_f;
-    k_mip_pass<<<grid_for((int64_t)ax * ny * nz, 256, c.num_sms), 256, 0, s>>>(
-        v.raw.as<float>(), A, nx, ny, nz, ax, ny, nz, 0, st, off, dw, T, scale, 0);
+    {
+        // x pass from shared memory: R lines of nx floats per block, at most 64 KB
+        constexpr int kLineBytes = 64 * 1024;
+        const int R = std::max(1, std::min(32, kLineBytes / ((nx + 1) * (int)sizeof(float))));
+        const int smem = R * (nx + 1) * (int)sizeof(float);
+        static bool attr = false;
+        if (!attr) {
+            RPNN_CUDA_TRY(cudaFuncSetAttribute(k_mip_pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, kLineBytes));
+            attr = true;
+        }
+        const int64_t nrows = (int64_t)ny * nz;
+        k_mip_pass_x<<<grid_for((nrows + R - 1) / R, 1, c.num_sms), 256, smem, s>>>(v.raw.as<float>(), A, nx, nrows, ax,
+                                                                                st, off, dw, T, R);
+    }
     k_mip_pass<<<grid_for((int64_t)ax * ay * nz, 256, c.num_sms), 256, 0, s>>>(
         A, B, ax, ny, nz, ax, ay, nz, 1, st, off, dw, T, scale, 0);
     k_mip_pass<<<grid_for((int64_t)ax * ay * az, 256, c.num_sms), 256, 0, s>>>(

@@ -68,7 +68,9 @@ def test_brick_majorants_bit_exact(ctx, shape, seed):
     assert (ref == 0).any() or seed == 1
 
 
-@pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9)])
+# (29, 23, 37): the x pass's last 32-line tile is partial; (5, 6, 600): fewer than 32 lines
+# of 600 fit its shared memory
+@pytest.mark.parametrize("shape,seed", [((64, 64, 64), 1), ((40, 24, 48), 9), ((29, 23, 37), 4), ((5, 6, 600), 5)])
 def test_stats_and_mips_bit_exact(ctx, shape, seed):
     dens = W.fbm_cloud(shape=shape, seed=seed, coverage=0.35) if seed != 1 else W.blob_cloud(64, seed=1)
     v = ctx.load_volume(cuda(dens))
