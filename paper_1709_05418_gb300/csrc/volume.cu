@@ -123,9 +123,24 @@ __global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ o
     for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < nrows; r0 += (int64_t)gridDim.x * R) {
         const int nr = (int)min((int64_t)R, nrows - r0);
         __syncthreads();                       // the previous lines' readers are done
+        // the nr lines are nr * nx consecutive floats: eight loads per thread in flight at once
         const float* src = in + r0 * nx;
-        for (int r = 0; r < nr; ++r)
-            for (int x = threadIdx.x; x < nx; x += blockDim.x) lines[r * pitch + x] = __ldg(src + (int64_t)r * nx + x);
+        const int total = nr * nx, nb = (int)blockDim.x;
+        int e = threadIdx.x;
+        for (; e + 7 * nb < total; e += 8 * nb) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(src + e + k * nb);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int ee = e + k * nb, r = ee / nx;
+                lines[r * pitch + ee - r * nx] = v[k];
+            }
+        }
+        for (; e < total; e += nb) {
+            const int r = e / nx;
+            lines[r * pitch + e - r * nx] = __ldg(src + e);
+        }
         __syncthreads();
         for (int task = threadIdx.x; task < R * ax; task += blockDim.x) {
             const int r = task % R, j = task / R;
@@ -134,6 +149,7 @@ __global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ o
             const int t0 = j * st + off;
             const int mlo = max(0, -t0), mhi = min(T, nx - t0);
             float acc = 0.0f;
+#pragma unroll 4
             for (int m = mlo; m < mhi; ++m) acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), line[t0 + m]));
             out[(r0 + r) * ax + j] = acc;
         }
@@ -224,7 +240,12 @@ __global__ void k_brick_majorant(const float* __restrict__ raw, int nx, int ny, 
         for (int z = max(z0, 0); z <= min(z0 + kBrick + 1, nz - 1); ++z)
             for (int y = max(y0, 0); y <= min(y0 + kBrick + 1, ny - 1); ++y) {
                 const float* r = raw + ((int64_t)z * ny + y) * nx;
-                for (int x = max(x0, 0); x <= min(x0 + kBrick + 1, nx - 1); ++x) m = fmaxf(m, __ldg(r + x));
+                // a fixed-length line with in-grid predicates: its loads are in flight together
+#pragma unroll
+                for (int dx = 0; dx < kBrick + 2; ++dx) {
+                    const int x = x0 + dx;
+                    if (x >= 0 && x < nx) m = fmaxf(m, __ldg(r + x));
+                }
             }
         out[i] = m;
     }
