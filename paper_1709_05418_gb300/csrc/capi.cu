@@ -138,7 +138,7 @@ rpnn_status rpnn_destroy(rpnn_ctx* ctx) {
     for (Volume* v : c->vols) {
         if (!v) continue;
         v->raw.release(); v->packed.release(); v->stats.release(); v->bmaj.release();
-        v->mip_a.release(); v->mip_b.release(); v->mip_w.release(); v->stencil_mips.release();
+        v->mip_a.release(); v->mip_b.release(); v->mip_w.release(); v->mip_d.release(); v->stencil_mips.release();
         delete v;
     }
     DevBuf* bufs[] = {&c->status, &c->params32, &c->wimg_bf16, &c->wimg_fp8, &c->q_x, &c->q_d, &c->q_ps,

@@ -94,6 +94,7 @@ struct Volume {
     DevBuf stats;            // device-side statistics scratch
     DevBuf bmaj;             // per-brick tracking majorants
     DevBuf mip_a, mip_b, mip_w;   // separable-pass scratch and taps of the pyramid build
+    DevBuf mip_d;                 // the levels the descriptor reads, before corner packing
     int nb[3] = {0, 0, 0};
     bool mip_blend = false;  // descriptor blends levels m_k and m_k + 1
     uint32_t track_cap = 0;  // 0: the default cap (rpnn_set_iteration_cap)
@@ -265,6 +266,8 @@ void train_graph_release(Ctx& c);     // frees the captured training step and it
 rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_brick_majorants(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s);
+// levels[0..n-1] into dst[0..n-1] (each [az][ay][ax] FP32), their y and z passes in shared launches
+rpnn_status volume_build_levels(Ctx& c, Volume& v, const int* levels, int n, float* const* dst, cudaStream_t s);
 rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s);
 rpnn_status load_density(Ctx& c, Volume& v, const void* src, int dtype, cudaStream_t s);
 

@@ -79,43 +79,55 @@ __global__ void k_stats_sum(const float* __restrict__ v, int64_t n, DevStats* st
     if ((threadIdx.x & 31) == 0) atomicAdd(&st->isum, s);
 }
 
-// One separable pass of the Gaussian filter along `axis` with decimation: output index
-// j along the axis reads fine indices j*st + off + m, m = 0..T-1 (zero outside),
-// accumulated in ascending m as acc = acc + w*v (no contraction); the final pass
-// multiplies by `scale` (1/mean).
-__global__ void k_mip_pass(const float* __restrict__ in, float* __restrict__ out, int ix, int iy,
-                           int iz, int ox, int oy, int oz, int axis, int st, int off,
-                           const float* __restrict__ w, int T, float scale, int apply_scale) {
-    const int64_t total = (int64_t)ox * oy * oz;
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+// One separable pass of the Gaussian filter along one axis with decimation: output index
+// j along the axis reads fine indices j*st + off + m, m = 0..T-1 (zero outside, so only the
+// taps inside the grid are visited), accumulated in ascending m as acc = acc + w*v (no
+// contraction); the final pass multiplies by `scale` (1/mean).
+// The y or z passes of several levels in one launch (outputs of job j at flattened indices
+// first[j] .. first[j+1] - 1), so that the deep levels' few long tap chains run beside the
+// others instead of after them.
+struct MipJob {
+    const float* in;
+    float* out;
+    const float* w;
+    int ix, iy, iz, ox, oy, oz, st, off, T;
+    int64_t first;
+};
+struct MipJobs {
+    MipJob j[kMaxLevels];
+    int n, axis, apply_scale;
+    float scale;
+    int64_t total;
+};
+__global__ void k_mip_pass_multi(const __grid_constant__ MipJobs J) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < J.total;
          o += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(o % ox);
-        const int y = (int)((o / ox) % oy);
-        const int z = (int)(o / ((int64_t)ox * oy));
+        int k = 0;
+        while (k + 1 < J.n && J.j[k + 1].first <= o) ++k;
+        const MipJob& b = J.j[k];
+        const int64_t q = o - b.first;
+        const int x = (int)(q % b.ox);
+        const int y = (int)((q / b.ox) % b.oy);
+        const int z = (int)(q / ((int64_t)b.ox * b.oy));
         int j, n;
         int64_t base, stride;
-        if (axis == 0) { j = x; n = ix; base = ((int64_t)z * iy + y) * ix; stride = 1; }
-        else if (axis == 1) { j = y; n = iy; base = (int64_t)z * iy * ix + x; stride = ix; }
-        else { j = z; n = iz; base = (int64_t)y * ix + x; stride = (int64_t)ix * iy; }
+        if (J.axis == 1) { j = y; n = b.iy; base = (int64_t)z * b.iy * b.ix + x; stride = b.ix; }
+        else { j = z; n = b.iz; base = (int64_t)y * b.ix + x; stride = (int64_t)b.ix * b.iy; }
         float acc = 0.0f;
-        const int t0 = j * st + off;
-        // only the taps that land inside the grid contribute (zero outside): the same terms
-        // in the same ascending order, without visiting the rest
-        const int mlo = max(0, -t0), mhi = min(T, n - t0);
-        // (unrolled so that several taps' loads are in flight ahead of the serial sum)
+        const int t0 = j * b.st + b.off;
+        const int mlo = max(0, -t0), mhi = min(b.T, n - t0);
 #pragma unroll 4
         for (int m = mlo; m < mhi; ++m)
-            acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), __ldg(in + base + (int64_t)(t0 + m) * stride)));
-        out[o] = apply_scale ? __fmul_rn(acc, scale) : acc;
+            acc = __fadd_rn(acc, __fmul_rn(__ldg(b.w + m), __ldg(b.in + base + (int64_t)(t0 + m) * stride)));
+        b.out[q] = J.apply_scale ? __fmul_rn(acc, J.scale) : acc;
     }
 }
 
-// The x pass of k_mip_pass, staged: a block copies R consecutive x lines of the fine grid
+// The x pass, staged: a block copies R consecutive x lines of the fine grid
 // (contiguous in memory) into shared memory with coalesced loads (line pitch nx + 1 floats),
 // then its threads compute the decimated outputs (line r, index j) with r fastest, so a
 // warp's lanes read different lines at one position (different banks) instead of 32
-// scattered global lines per tap.  Each output's taps in ascending m, acc = acc + w*v: the
-// same terms in the same order as k_mip_pass.
+// scattered global lines per tap.  Each output's taps in ascending m, acc = acc + w*v.
 __global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ out, int nx, int64_t nrows,
                              int ax, int st, int off, const float* __restrict__ w, int T, int R) {
     extern __shared__ float lines[];
@@ -316,44 +328,84 @@ rpnn_status volume_stats(Ctx& c, Volume& v, cudaStream_t s) {
     return RPNN_OK;
 }
 
-rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s) {
-    if (level < 0 || level >= v.levels) { set_error("mip level %d out of range", level); return RPNN_ERR_ARG; }
-    int off = 0;
-    std::vector<float> w = gauss_taps(level, &off);
-    const int T = (int)w.size();
+rpnn_status volume_build_levels(Ctx& c, Volume& v, const int* levels, int nlev, float* const* dst, cudaStream_t s) {
+    if (nlev <= 0) return RPNN_OK;
+    if (nlev > kMaxLevels) { set_error("too many mip levels (%d)", nlev); return RPNN_ERR_ARG; }
     const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
-    const int ax = v.dims[level][0], ay = v.dims[level][1], az = v.dims[level][2];
-    // volume-owned scratch (grows, never shrinks): no allocation or synchronisation per level
-    rpnn_status rs = v.mip_w.reserve(T * sizeof(float));
-    if (!rs) rs = v.mip_a.reserve((size_t)ax * ny * nz * sizeof(float));
-    if (!rs) rs = v.mip_b.reserve((size_t)ax * ay * nz * sizeof(float));
+    // deepest level first: its long tap chains start with the launch
+    std::vector<int> ord(levels, levels + nlev);
+    for (int l : ord)
+        if (l < 0 || l >= v.levels) { set_error("mip level %d out of range", l); return RPNN_ERR_ARG; }
+    std::sort(ord.begin(), ord.end(), [](int a, int b) { return a > b; });
+    // taps and scratch of every level side by side (offsets in floats, 16-float aligned);
+    // volume-owned, grows and never shrinks: no allocation or synchronisation per build
+    std::vector<float> taps;
+    std::vector<int> offs(nlev), toff(nlev), T(nlev);
+    std::vector<int64_t> aoff(nlev), boff(nlev);
+    int64_t asz = 0, bsz = 0;
+    for (int k = 0; k < nlev; ++k) {
+        const int l = ord[k];
+        std::vector<float> w = gauss_taps(l, &offs[k]);
+        T[k] = (int)w.size();
+        toff[k] = (int)taps.size();
+        taps.insert(taps.end(), w.begin(), w.end());
+        taps.resize((taps.size() + 15) / 16 * 16, 0.0f);
+        aoff[k] = asz; asz += ((int64_t)v.dims[l][0] * ny * nz + 15) / 16 * 16;
+        boff[k] = bsz; bsz += ((int64_t)v.dims[l][0] * v.dims[l][1] * nz + 15) / 16 * 16;
+    }
+    rpnn_status rs = v.mip_w.reserve(taps.size() * sizeof(float));
+    if (!rs) rs = v.mip_a.reserve((size_t)asz * sizeof(float));
+    if (!rs) rs = v.mip_b.reserve((size_t)bsz * sizeof(float));
     if (rs) return rs;
     float* dw = v.mip_w.as<float>();
     float* A = v.mip_a.as<float>();
     float* B = v.mip_b.as<float>();
-    RPNN_CUDA_TRY(cudaMemcpyAsync(dw, w.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
-    const int st = 1 << level;
-    const float scale = v.info.inv_mean_f;
-    {
-        // x pass from shared memory: R lines of nx floats per block, at most 64 KB
-        constexpr int kLineBytes = 64 * 1024;
-        const int R = std::max(1, std::min(32, kLineBytes / ((nx + 1) * (int)sizeof(float))));
-        const int smem = R * (nx + 1) * (int)sizeof(float);
-        static bool attr = false;
-        if (!attr) {
-            RPNN_CUDA_TRY(cudaFuncSetAttribute(k_mip_pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, kLineBytes));
-            attr = true;
-        }
-        const int64_t nrows = (int64_t)ny * nz;
-        k_mip_pass_x<<<grid_for((nrows + R - 1) / R, 1, c.num_sms), 256, smem, s>>>(v.raw.as<float>(), A, nx, nrows, ax,
-                                                                                st, off, dw, T, R);
+    RPNN_CUDA_TRY(cudaMemcpyAsync(dw, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    // x passes, one launch per level (each reads the whole fine grid), R lines of nx floats
+    // per block in at most 64 KB of shared memory
+    constexpr int kLineBytes = 64 * 1024;
+    const int R = std::max(1, std::min(32, kLineBytes / ((nx + 1) * (int)sizeof(float))));
+    const int smem = R * (nx + 1) * (int)sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        RPNN_CUDA_TRY(cudaFuncSetAttribute(k_mip_pass_x, cudaFuncAttributeMaxDynamicSharedMemorySize, kLineBytes));
+        attr = true;
     }
-    k_mip_pass<<<grid_for((int64_t)ax * ay * nz, 256, c.num_sms), 256, 0, s>>>(
-        A, B, ax, ny, nz, ax, ay, nz, 1, st, off, dw, T, scale, 0);
-    k_mip_pass<<<grid_for((int64_t)ax * ay * az, 256, c.num_sms), 256, 0, s>>>(
-        B, dst, ax, ay, nz, ax, ay, az, 2, st, off, dw, T, scale, 1);
+    const int64_t nrows = (int64_t)ny * nz;
+    for (int k = 0; k < nlev; ++k) {
+        const int l = ord[k];
+        k_mip_pass_x<<<grid_for((nrows + R - 1) / R, 1, c.num_sms), 256, smem, s>>>(
+            v.raw.as<float>(), A + aoff[k], nx, nrows, v.dims[l][0], 1 << l, offs[k], dw + toff[k], T[k], R);
+    }
+    // y passes of every level in one launch, then the z passes (with the 1/mean scale)
+    for (int axis = 1; axis <= 2; ++axis) {
+        MipJobs J{};
+        J.n = nlev; J.axis = axis; J.apply_scale = axis == 2; J.scale = v.info.inv_mean_f;
+        int64_t first = 0;
+        for (int k = 0; k < nlev; ++k) {
+            const int l = ord[k], ax = v.dims[l][0], ay = v.dims[l][1], az = v.dims[l][2];
+            MipJob& b = J.j[k];
+            b.w = dw + toff[k]; b.st = 1 << l; b.off = offs[k]; b.T = T[k];
+            if (axis == 1) {
+                b.in = A + aoff[k]; b.out = B + boff[k];
+                b.ix = ax; b.iy = ny; b.iz = nz; b.ox = ax; b.oy = ay; b.oz = nz;
+            } else {
+                const int kk = (int)(std::find(levels, levels + nlev, l) - levels);
+                b.in = B + boff[k]; b.out = dst[kk];
+                b.ix = ax; b.iy = ay; b.iz = nz; b.ox = ax; b.oy = ay; b.oz = az;
+            }
+            b.first = first;
+            first += (int64_t)b.ox * b.oy * b.oz;
+        }
+        J.total = first;
+        k_mip_pass_multi<<<grid_for(J.total, 256, c.num_sms), 256, 0, s>>>(J);
+    }
     RPNN_CHECK_LAUNCH();
     return RPNN_OK;
+}
+
+rpnn_status volume_build_level(Ctx& c, Volume& v, int level, float* dst, cudaStream_t s) {
+    return volume_build_levels(c, v, &level, 1, &dst, s);
 }
 
 rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s) {
@@ -371,25 +423,29 @@ rpnn_status volume_pack_levels(Ctx& c, Volume& v, cudaStream_t s) {
     }
     rpnn_status st = v.packed.reserve(total * 2 * sizeof(float4));
     if (st) return st;
-    float* tmp = nullptr;
-    size_t tmp_bytes = 0;
+    // the needed levels, built together, each into its own part of a volume-owned buffer
+    int lv[kMaxLevels], nl = 0;
+    int64_t doff[kMaxLevels], dsz = 0;
     for (int i = 0; i < v.levels; ++i) {
         if (!need[i]) continue;
-        const size_t b = (size_t)v.dims[i][0] * v.dims[i][1] * v.dims[i][2] * sizeof(float);
-        if (b > tmp_bytes) {
-            if (tmp) cudaFree(tmp);
-            RPNN_CUDA_TRY(cudaMalloc(&tmp, b));
-            tmp_bytes = b;
-        }
-        st = volume_build_level(c, v, i, tmp, s);
-        if (st) { cudaFree(tmp); return st; }
+        doff[nl] = dsz;
+        dsz += ((int64_t)v.dims[i][0] * v.dims[i][1] * v.dims[i][2] + 15) / 16 * 16;
+        lv[nl++] = i;
+    }
+    st = v.mip_d.reserve((size_t)std::max<int64_t>(dsz, 1) * sizeof(float));
+    if (st) return st;
+    float* dst[kMaxLevels];
+    for (int k = 0; k < nl; ++k) dst[k] = v.mip_d.as<float>() + doff[k];
+    st = volume_build_levels(c, v, lv, nl, dst, s);
+    if (st) return st;
+    for (int k = 0; k < nl; ++k) {
+        const int i = lv[k];
         const int64_t nrec = (int64_t)(v.dims[i][0] + 1) * (v.dims[i][1] + 1) * (v.dims[i][2] + 1);
         k_pack<<<grid_for(nrec, 256, c.num_sms), 256, 0, s>>>(
-            tmp, v.packed.as<float4>() + 2 * v.lvl[i].rec_offset, v.dims[i][0], v.dims[i][1], v.dims[i][2]);
+            dst[k], v.packed.as<float4>() + 2 * v.lvl[i].rec_offset, v.dims[i][0], v.dims[i][1], v.dims[i][2]);
         RPNN_CHECK_LAUNCH();
     }
     RPNN_CUDA_TRY(cudaStreamSynchronize(s));
-    if (tmp) cudaFree(tmp);
     v.built = true;
     v.stencil_ready = false;
     return RPNN_OK;
