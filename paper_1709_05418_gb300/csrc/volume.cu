@@ -27,16 +27,24 @@ __global__ void k_f16_to_f32(const __half* __restrict__ in, float* __restrict__ 
         out[i] = __half2float(in[i]);
 }
 
+// The grid is read as 16-byte vectors (the allocation is 256-byte aligned), the last n % 4
+// voxels one by one; max, count and the fixed-point sum below are exact in any order.
+__device__ __forceinline__ void stats_max_one(float x, unsigned int& mx, unsigned int& bad, unsigned int& cnt) {
+    if (!(x >= 0.0f) || isinf(x)) { bad = 1; return; }
+    mx = max(mx, __float_as_uint(x));
+    cnt += x > 0.0f;
+}
 __global__ void k_stats_max(const float* __restrict__ v, int64_t n, DevStats* st) {
-    unsigned int mx = 0, bad = 0;
-    unsigned long long cnt = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float x = v[i];
-        if (!(x >= 0.0f) || isinf(x)) { bad = 1; continue; }
-        mx = max(mx, __float_as_uint(x));
-        cnt += x > 0.0f;
+    unsigned int mx = 0, bad = 0, c32 = 0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    for (int64_t i = tid; i < n / 4; i += nt) {
+        const float4 q = __ldg(v4 + i);
+        stats_max_one(q.x, mx, bad, c32); stats_max_one(q.y, mx, bad, c32);
+        stats_max_one(q.z, mx, bad, c32); stats_max_one(q.w, mx, bad, c32);
     }
+    for (int64_t i = n / 4 * 4 + tid; i < n; i += nt) stats_max_one(v[i], mx, bad, c32);
+    unsigned long long cnt = c32;       // a thread counts at most n / threads + 4 voxels
     for (int o = 16; o; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
@@ -70,8 +78,16 @@ __global__ void k_stats_sum(const float* __restrict__ v, int64_t n, DevStats* st
     frexpf(__uint_as_float(st->max_bits), &e);
     const int S = 32 - e;
     unsigned long long s = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    for (int64_t i = tid; i < n / 4; i += nt) {
+        const float4 q = __ldg(v4 + i);
+        if (q.x > 0.0f) s += fixed_point(q.x, S);
+        if (q.y > 0.0f) s += fixed_point(q.y, S);
+        if (q.z > 0.0f) s += fixed_point(q.z, S);
+        if (q.w > 0.0f) s += fixed_point(q.w, S);
+    }
+    for (int64_t i = n / 4 * 4 + tid; i < n; i += nt) {
         const float x = v[i];
         if (x > 0.0f) s += fixed_point(x, S);
     }

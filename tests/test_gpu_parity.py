@@ -94,6 +94,31 @@ def test_stats_and_mips_bit_exact(ctx, shape, seed):
         assert np.abs(g - r64).max() <= 2e-6 * max(1.0, np.abs(r64).max())
 
 
+@pytest.mark.parametrize("where", ["vector", "tail"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -1e-3])
+def test_invalid_densities_are_rejected(ctx, api, bad, where):
+    """A NaN, infinite or negative voxel fails the build with RPNN_ERR_NONFINITE, whether it
+    sits in the part of the grid read as 16-byte vectors or in the last n % 4 voxels read one
+    by one (315 voxels: 78 vectors and a tail of 3); the context stays usable."""
+    dens = np.full((5, 7, 9), 0.5, dtype=np.float32)
+    flat = dens.reshape(-1)
+    flat[17 if where == "vector" else 313] = bad
+    v = ctx.load_volume(cuda(dens))
+    with pytest.raises(api.RPNNError) as e:
+        ctx.build_mips(v)
+    assert e.value.code == -6
+    ok = ctx.load_volume(cuda(np.full((5, 7, 9), 0.5, dtype=np.float32)))
+    ctx.build_mips(ok)
+    assert ctx.get_volume_info(ok)["nonzero"] == 315
+
+
+def test_all_zero_density_is_rejected(ctx, api):
+    v = ctx.load_volume(cuda(np.zeros((5, 7, 9), dtype=np.float32)))
+    with pytest.raises(api.RPNNError) as e:
+        ctx.build_mips(v)
+    assert e.value.code == -1
+
+
 def test_stats_mean_exact_over_the_exponent_range(ctx):
     """The fixed-point mean (32 fraction bits below the majorant's exponent, truncated per
     voxel, summed exactly) over values spread across every float exponent, subnormals
