@@ -139,13 +139,23 @@ __global__ void k_mip_pass_multi(const __grid_constant__ MipJobs J) {
     }
 }
 
-// The x pass, staged: a block copies R consecutive x lines of the fine grid
-// (contiguous in memory) into shared memory with coalesced loads (line pitch nx + 1 floats),
-// then its threads compute the decimated outputs (line r, index j) with r fastest, so a
-// warp's lanes read different lines at one position (different banks) instead of 32
-// scattered global lines per tap.  Each output's taps in ascending m, acc = acc + w*v.
-__global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ out, int nx, int64_t nrows,
-                             int ax, int st, int off, const float* __restrict__ w, int T, int R) {
+// The x passes of several levels, staged: a block copies R consecutive x lines of the fine
+// grid (contiguous in memory) into shared memory once, with coalesced loads (line pitch
+// nx + 1 floats), and computes every level's decimated outputs (line r, index j) from them
+// with r fastest, so a warp's lanes read different lines at one position (different banks)
+// instead of 32 scattered global lines per tap.  Each output's taps in ascending m,
+// acc = acc + w*v.
+struct MipXJob {
+    float* out;
+    const float* w;
+    int ax, st, off, T;
+};
+struct MipXJobs {
+    MipXJob j[kMaxLevels];
+    int n;
+};
+__global__ void k_mip_pass_x(const float* __restrict__ in, int nx, int64_t nrows, int R,
+                             const __grid_constant__ MipXJobs J) {
     extern __shared__ float lines[];
     const int pitch = nx + 1;
     for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < nrows; r0 += (int64_t)gridDim.x * R) {
@@ -170,16 +180,19 @@ __global__ void k_mip_pass_x(const float* __restrict__ in, float* __restrict__ o
             lines[r * pitch + e - r * nx] = __ldg(src + e);
         }
         __syncthreads();
-        for (int task = threadIdx.x; task < R * ax; task += blockDim.x) {
-            const int r = task % R, j = task / R;
-            if (r >= nr) continue;
-            const float* line = lines + r * pitch;
-            const int t0 = j * st + off;
-            const int mlo = max(0, -t0), mhi = min(T, nx - t0);
-            float acc = 0.0f;
+        for (int k = 0; k < J.n; ++k) {
+            const MipXJob& b = J.j[k];
+            for (int task = threadIdx.x; task < R * b.ax; task += blockDim.x) {
+                const int r = task % R, j = task / R;
+                if (r >= nr) continue;
+                const float* line = lines + r * pitch;
+                const int t0 = j * b.st + b.off;
+                const int mlo = max(0, -t0), mhi = min(b.T, nx - t0);
+                float acc = 0.0f;
 #pragma unroll 4
-            for (int m = mlo; m < mhi; ++m) acc = __fadd_rn(acc, __fmul_rn(__ldg(w + m), line[t0 + m]));
-            out[(r0 + r) * ax + j] = acc;
+                for (int m = mlo; m < mhi; ++m) acc = __fadd_rn(acc, __fmul_rn(__ldg(b.w + m), line[t0 + m]));
+                b.out[(r0 + r) * b.ax + j] = acc;
+            }
         }
     }
 }
@@ -377,8 +390,8 @@ rpnn_status volume_build_levels(Ctx& c, Volume& v, const int* levels, int nlev, 
     float* A = v.mip_a.as<float>();
     float* B = v.mip_b.as<float>();
     RPNN_CUDA_TRY(cudaMemcpyAsync(dw, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    // x passes, one launch per level (each reads the whole fine grid), R lines of nx floats
-    // per block in at most 64 KB of shared memory
+    // the x passes of every level in one launch (the fine grid is read once), R lines of nx
+    // floats per block in at most 64 KB of shared memory
     constexpr int kLineBytes = 64 * 1024;
     const int R = std::max(1, std::min(32, kLineBytes / ((nx + 1) * (int)sizeof(float))));
     const int smem = R * (nx + 1) * (int)sizeof(float);
@@ -388,11 +401,13 @@ rpnn_status volume_build_levels(Ctx& c, Volume& v, const int* levels, int nlev, 
         attr = true;
     }
     const int64_t nrows = (int64_t)ny * nz;
+    MipXJobs XJ{};
+    XJ.n = nlev;
     for (int k = 0; k < nlev; ++k) {
         const int l = ord[k];
-        k_mip_pass_x<<<grid_for((nrows + R - 1) / R, 1, c.num_sms), 256, smem, s>>>(
-            v.raw.as<float>(), A + aoff[k], nx, nrows, v.dims[l][0], 1 << l, offs[k], dw + toff[k], T[k], R);
+        XJ.j[k] = MipXJob{A + aoff[k], dw + toff[k], v.dims[l][0], 1 << l, offs[k], T[k]};
     }
+    k_mip_pass_x<<<grid_for((nrows + R - 1) / R, 1, c.num_sms), 256, smem, s>>>(v.raw.as<float>(), nx, nrows, R, XJ);
     // y passes of every level in one launch, then the z passes (with the 1/mean scale)
     for (int axis = 1; axis <= 2; ++axis) {
         MipJobs J{};
