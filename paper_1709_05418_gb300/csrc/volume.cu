@@ -132,7 +132,7 @@ __global__ void k_mip_pass_multi(const __grid_constant__ MipJobs J) {
         float acc = 0.0f;
         const int t0 = j * b.st + b.off;
         const int mlo = max(0, -t0), mhi = min(b.T, n - t0);
-#pragma unroll 4
+#pragma unroll 8
         for (int m = mlo; m < mhi; ++m)
             acc = __fadd_rn(acc, __fmul_rn(__ldg(b.w + m), __ldg(b.in + base + (int64_t)(t0 + m) * stride)));
         b.out[q] = J.apply_scale ? __fmul_rn(acc, J.scale) : acc;
